@@ -1,0 +1,250 @@
+"""Seeded synthetic inputs shared by the tests, the benchmark and the oracle
+checks.  This module holds no arithmetic of the solver itself: it only
+samples maps (nodal coordinates), coefficient fields and right-hand sides.
+
+Grid convention: ``n = 2**k + 1`` nodes per side on the computational
+square/cube ``[0,1]^d``; numpy arrays are C ordered with the fastest axis
+last, i.e. ``coords[c, j, i]`` / ``coords[c, k, j, i]``; ``kappa`` holds one
+value per cell, indexed by the cell's lower corner.
+
+Workloads (the paper's Sec. 4 domains that have analytic maps):
+  * quarter annulus r in [1/2, 1], theta in [0, pi/2] (Sec. 4.1, quarter
+    annulus, rotated to the first quadrant);
+  * octant of the spherical shell r in [1/2, 1] (the 3-D analogue);
+  * unit square with a smooth bump map x = s + a sin(pi s) sin(pi t),
+    y = t + b sin(pi s) sin(pi t) (the batched family);
+  * the identity map with the discontinuous coefficients of Sec. 4.1
+    (circle, checkerboard, thin layer).
+"""
+from __future__ import annotations
+
+import math
+from dataclasses import dataclass, field
+
+import numpy as np
+
+
+def _axis(n: int) -> np.ndarray:
+    return np.linspace(0.0, 1.0, n)
+
+
+# ------------------------------------------------------------------ maps
+def coords_quarter_annulus(n: int) -> np.ndarray:
+    """x = (1/2 + s/2) cos(pi t / 2), y = (1/2 + s/2) sin(pi t / 2)."""
+    s = _axis(n)[None, :]
+    t = _axis(n)[:, None]
+    r = 0.5 + 0.5 * s
+    th = 0.5 * math.pi * t
+    return np.stack([r * np.cos(th), r * np.sin(th)]).astype(np.float64)
+
+
+def coords_shell_octant(n: int) -> np.ndarray:
+    """Spherical coordinates r = 1/2 + s/2, theta = pi t / 2, phi = pi w / 2:
+    x = r sin(theta) cos(phi), y = r sin(theta) sin(phi), z = r cos(theta).
+    The face t = 0 collapses onto the z axis (a Dirichlet face)."""
+    s = _axis(n)[None, None, :]
+    t = _axis(n)[None, :, None]
+    w = _axis(n)[:, None, None]
+    r = 0.5 + 0.5 * s
+    th = 0.5 * math.pi * t
+    ph = 0.5 * math.pi * w
+    x = r * np.sin(th) * np.cos(ph)
+    y = r * np.sin(th) * np.sin(ph)
+    z = r * np.cos(th) * np.ones_like(ph)
+    return np.stack(np.broadcast_arrays(x, y, z)).astype(np.float64)
+
+
+def coords_bump(n: int, a: float, b: float) -> np.ndarray:
+    """x = s + a sin(pi s) sin(pi t), y = t + b sin(pi s) sin(pi t)."""
+    s = _axis(n)[None, :]
+    t = _axis(n)[:, None]
+    bump = np.sin(math.pi * s) * np.sin(math.pi * t)
+    return np.stack([s + a * bump, t + b * bump]).astype(np.float64)
+
+
+def coords_identity(n: int, dim: int = 2) -> np.ndarray:
+    """x = s (and y = t, z = w)."""
+    return np.stack([_identity_component(n, dim, c) for c in range(dim)])
+
+
+def _identity_component(n: int, dim: int, c: int) -> np.ndarray:
+    shape = [1] * dim
+    shape[dim - 1 - c] = n          # component c varies along numpy axis dim-1-c
+    v = _axis(n).reshape(shape)
+    return np.ascontiguousarray(np.broadcast_to(v, (n,) * dim), dtype=np.float64)
+
+
+def cell_centroids(coords: np.ndarray) -> np.ndarray:
+    """Mean of each cell's 2**d nodal coordinates, shape (d, n-1, ...)."""
+    d = coords.shape[0]
+    acc = 0.0
+    for corner in range(1 << d):
+        sl = [slice(None)] * (d + 1)
+        for a in range(d):                      # a = 0 is the fastest (last) axis
+            bit = (corner >> a) & 1
+            sl[d - a] = slice(1, None) if bit else slice(0, -1)
+        acc = acc + coords[tuple(sl)]
+    return acc / float(1 << d)
+
+
+# ------------------------------------------------------------------ fields
+@dataclass
+class GaussianField:
+    """Random-Fourier-feature sample of a zero-mean Gaussian field with
+    covariance sigma^2 exp(-|dx|^2 / (2 ell^2)):
+    g(x) = sigma sqrt(2/M) sum_m cos(omega_m . x + phi_m),
+    omega_m ~ N(0, ell^-2 I), phi_m ~ U[0, 2 pi)."""
+    omega: np.ndarray      # (M, d)
+    phase: np.ndarray      # (M,)
+    sigma: float = 1.0
+
+    @classmethod
+    def draw(cls, rng: np.random.Generator, dim: int, modes: int = 64, ell: float = 0.05,
+             sigma: float = 1.0) -> "GaussianField":
+        omega = rng.normal(0.0, 1.0 / ell, size=(modes, dim))
+        phase = rng.uniform(0.0, 2.0 * math.pi, size=modes)
+        return cls(omega, phase, sigma)
+
+    def __call__(self, pts: np.ndarray, chunk: int = 1 << 22) -> np.ndarray:
+        """pts shape (d, ...) -> g shape (...)."""
+        d = pts.shape[0]
+        flat = pts.reshape(d, -1)
+        out = np.empty(flat.shape[1])
+        M = self.omega.shape[0]
+        scale = self.sigma * math.sqrt(2.0 / M)
+        for s0 in range(0, flat.shape[1], chunk):
+            blk = flat[:, s0:s0 + chunk]
+            arg = self.omega @ blk + self.phase[:, None]
+            out[s0:s0 + chunk] = scale * np.cos(arg).sum(axis=0)
+        return out.reshape(pts.shape[1:])
+
+
+def rhs_uniform(rng: np.random.Generator, shape) -> np.ndarray:
+    """f ~ U[-1, 1] per node, boundary entries zero (they are ignored)."""
+    f = rng.uniform(-1.0, 1.0, size=shape)
+    zero_boundary(f)
+    return f
+
+
+def zero_boundary(v: np.ndarray) -> np.ndarray:
+    for ax in range(v.ndim):
+        idx = [slice(None)] * v.ndim
+        idx[ax] = 0
+        v[tuple(idx)] = 0.0
+        idx[ax] = -1
+        v[tuple(idx)] = 0.0
+    return v
+
+
+# ------------------------------------------------------------------ workloads
+@dataclass
+class Problem:
+    name: str
+    dim: int
+    n: int
+    coords: np.ndarray
+    kappa: np.ndarray
+    rhs: np.ndarray                      # (nrhs, n, n[, n]) or (n, n[, n])
+    extra: dict = field(default_factory=dict)
+
+    @property
+    def unknowns(self) -> int:
+        return (self.n - 2) ** self.dim
+
+
+def annulus_plain(n: int = 65, seed: int = 0) -> Problem:
+    """Quarter annulus, kappa = 1, f ~ U[-1,1] per node (seed 0)."""
+    rng = np.random.default_rng(seed)
+    coords = coords_quarter_annulus(n)
+    kappa = np.ones((n - 1, n - 1))
+    f = rhs_uniform(rng, (n, n))
+    return Problem(f"annulus_plain_n{n}", 2, n, coords, kappa, f)
+
+
+def annulus_lognormal(n: int = 4097, seed: int = 1) -> Problem:
+    """Quarter annulus, kappa = exp(g), g a Gaussian field with 64 random
+    Fourier modes (sigma 1, correlation length 0.05) evaluated at the cell
+    centroids; f ~ U[-1,1].  Draw order: omega, phase, then f."""
+    rng = np.random.default_rng(seed)
+    coords = coords_quarter_annulus(n)
+    gf = GaussianField.draw(rng, 2)
+    kappa = np.exp(gf(cell_centroids(coords)))
+    f = rhs_uniform(rng, (n, n))
+    return Problem(f"annulus_lognormal_n{n}", 2, n, coords, kappa, f, {"field": gf})
+
+
+def shell_two_layer(n: int = 257, seed: int = 2) -> Problem:
+    """Spherical-shell octant, kappa = 1 for r < 3/4 and 1000 for r >= 3/4,
+    r taken at the cell centre in computational coordinates
+    (r = 1/2 + s/2, so r = 3/4 is the grid plane s = 1/2); f ~ U[-1,1]."""
+    rng = np.random.default_rng(seed)
+    coords = coords_shell_octant(n)
+    sc = (np.arange(n - 1) + 0.5) / (n - 1)
+    r = 0.5 + 0.5 * sc
+    kap_1d = np.where(r < 0.75, 1.0, 1000.0)
+    kappa = np.broadcast_to(kap_1d[None, None, :], (n - 1,) * 3).copy()
+    f = rhs_uniform(rng, (n, n, n))
+    return Problem(f"shell_two_layer_n{n}", 3, n, coords, kappa, f)
+
+
+def annulus_adjoint(n: int = 1025, batch: int = 8, seed_m: int = 3, seed_obs: int = 4) -> list:
+    """Per-cell parameter m ~ N(0, 0.5^2) (seed 3), kappa = exp(m); u_obs and
+    f ~ U[-1,1] (seed 4, u_obs first).  One Problem per batch member."""
+    rng_m = np.random.default_rng(seed_m)
+    rng_o = np.random.default_rng(seed_obs)
+    coords = coords_quarter_annulus(n)
+    out = []
+    ms = [rng_m.normal(0.0, 0.5, size=(n - 1, n - 1)) for _ in range(batch)]
+    for b in range(batch):
+        u_obs = rhs_uniform(rng_o, (n, n))
+        f = rhs_uniform(rng_o, (n, n))
+        out.append(Problem(f"annulus_adjoint_n{n}_b{b}", 2, n, coords, np.exp(ms[b]), f,
+                           {"m": ms[b], "u_obs": u_obs}))
+    return out
+
+
+def bump_batch(count: int = 512, seed: int = 5, kmin: int = 6, kmax: int = 10, nrhs: int = 4,
+               first: int = 0, limit: int | None = None) -> list:
+    """Independent unit-square bump-map problems with n = 2**k + 1, k uniform
+    in {kmin..kmax}; a, b ~ U[-0.15, 0.15]; log-normal kappa as in the
+    annulus workload; nrhs right-hand sides ~ U[-1,1].  Problem p draws, in
+    order: k, a, b, omega, phase, then its right-hand sides."""
+    rng = np.random.default_rng(seed)
+    probs = []
+    stop = count if limit is None else min(count, first + limit)
+    for p in range(count):
+        k = int(rng.integers(kmin, kmax + 1))
+        a, b = rng.uniform(-0.15, 0.15, size=2)
+        n = (1 << k) + 1
+        gf = GaussianField.draw(rng, 2)
+        if p < first or p >= stop:
+            rng.uniform(-1.0, 1.0, size=(nrhs, n, n))     # keep the stream aligned
+            continue
+        coords = coords_bump(n, a, b)
+        kappa = np.exp(gf(cell_centroids(coords)))
+        rhs = rng.uniform(-1.0, 1.0, size=(nrhs, n, n))
+        for r in range(nrhs):
+            zero_boundary(rhs[r])
+        probs.append(Problem(f"bump_{p}_n{n}", 2, n, coords, kappa, rhs, {"a": a, "b": b, "k": k}))
+    return probs
+
+
+def identity_coefficient(n: int, kind: str, seed: int = 0) -> Problem:
+    """Identity map on [0,1]^2 with a Sec. 4.1 coefficient evaluated at the
+    cell centre: 'circle' (100 inside r < 3/5, else 1), 'checkerboard'
+    (100 where floor(4x)+floor(4y) is even, else 1), 'thin_layer' (1e-10 for
+    0 <= x < 0.06, else 2)."""
+    rng = np.random.default_rng(seed)
+    coords = coords_identity(n, 2)
+    c = cell_centroids(coords)
+    x, y = c[0], c[1]
+    if kind == "circle":
+        kappa = np.where(np.hypot(x, y) < 0.6, 100.0, 1.0)
+    elif kind == "checkerboard":
+        kappa = np.where((np.floor(4 * x) + np.floor(4 * y)) % 2 == 0, 100.0, 1.0)
+    elif kind == "thin_layer":
+        kappa = np.where(x < 0.06, 1e-10, 2.0)
+    else:
+        raise ValueError(kind)
+    f = rhs_uniform(rng, (n, n))
+    return Problem(f"identity_{kind}_n{n}", 2, n, coords, kappa, f)

@@ -1,0 +1,530 @@
+"""Pins of the oracle against facts fixed by the paper and by the mathematics
+(closed forms, invariants, dense definitions, brute force).  CPU only.
+
+Each test names the property it pins and the passage it comes from.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2509_08109_gb300 import inputs
+
+
+def _affine_coords(n, M, c, dim):
+    base = inputs.coords_identity(n, dim)
+    flat = base.reshape(dim, -1)
+    out = (np.asarray(M) @ flat) + np.asarray(c)[:, None]
+    return np.ascontiguousarray(out.reshape(base.shape))
+
+
+# ------------------------------------------------------------------ P1
+def test_affine_stencil_closed_form_2d():
+    """Q1 stencil of a constant metric G (affine map, Sec. 2.1): integrating
+    the bilinear basis products on the unit cell by hand gives
+    C = 4/3(g11+g22), W = E = -2/3 g11 + 1/3 g22, S = N = 1/3 g11 - 2/3 g22,
+    SW = NE = -(g11+g22)/6 - g12/2, NW = SE = -(g11+g22)/6 + g12/2."""
+    rng = np.random.default_rng(11)
+    n = 9
+    M = np.array([[1.3, 0.4], [-0.2, 0.9]])
+    kap = 2.7
+    coords = _affine_coords(n, M, [0.3, -1.0], 2)
+    A = oracle.assemble(coords, np.full((n - 1, n - 1), kap))
+    # G in reference coordinates: J = M h, G = kappa det J J^-1 J^-T (h cancels in 2-D)
+    G = kap * np.linalg.det(M) * np.linalg.inv(M) @ np.linalg.inv(M).T
+    g11, g12, g22 = G[0, 0], G[0, 1], G[1, 1]
+    expect = np.zeros(9)
+    expect[4] = 4 / 3 * (g11 + g22)
+    expect[3] = expect[5] = -2 / 3 * g11 + 1 / 3 * g22
+    expect[1] = expect[7] = 1 / 3 * g11 - 2 / 3 * g22
+    expect[0] = expect[8] = -(g11 + g22) / 6 - g12 / 2
+    expect[6] = expect[2] = -(g11 + g22) / 6 + g12 / 2
+    for j in range(2, n - 2):
+        for i in range(2, n - 2):
+            np.testing.assert_allclose(A[j, i], expect, rtol=0, atol=1e-13 * expect[4])
+    del rng
+
+
+def test_identity_stencil_3d():
+    """Trilinear Q1 Laplacian on a cube of side h: h * (8/3 centre, 0 faces,
+    -1/6 edges, -1/12 corners)."""
+    n = 9
+    h = 1.0 / (n - 1)
+    coords = inputs.coords_identity(n, 3)
+    A = oracle.assemble(coords, np.ones((n - 1,) * 3))
+    row = A[4, 4, 4]
+    for o in range(27):
+        d = [(o % 3) - 1, (o // 3) % 3 - 1, o // 9 - 1]
+        nz = sum(abs(x) for x in d)
+        want = {0: 8 / 3, 1: 0.0, 2: -1 / 6, 3: -1 / 12}[nz] * h
+        assert abs(row[o] - want) < 1e-14, (o, row[o], want)
+
+
+# ------------------------------------------------------------------ P2, P3
+def test_annulus_metric_closed_form():
+    """Quarter annulus x = r cos(pi t/2), y = r sin(pi t/2), r = 1/2 + s/2:
+    det(dx/ds) = pi r / 4 and D_c = diag(pi r, 1/(pi r)) (Sec. 2.1's D_c with
+    D = I).  The isoparametric (bilinear) map reproduces det J and the
+    diagonal to O(h^2) at every Gauss point; its off-diagonal shear varies
+    linearly across a cell, so it is O(h) pointwise and cancels in the mean
+    over the cell's four Gauss points (the map is a rotation times a
+    diagonal scaling)."""
+    e2, e1, em = [], [], []
+    for n in (17, 33, 65):
+        h = 1.0 / (n - 1)
+        coords = inputs.coords_quarter_annulus(n)
+        xq = oracle.gauss_points(coords)
+        w2 = w1 = wm = 0.0
+        for e in [0, (n - 1) * (n - 1) // 2 + 3, (n - 1) ** 2 - 1]:
+            cj, ci = divmod(e, n - 1)
+            xe = np.stack([coords[c][[cj, cj, cj + 1, cj + 1], [ci, ci + 1, ci, ci + 1]] for c in range(2)])
+            det, Dc = oracle.metric(xe, 1.0, h)
+            for q in range(4):
+                r = math.hypot(*xq[e, q])
+                w2 = max(w2, abs(det[q] - math.pi * r / 4) / (math.pi * r / 4))
+                w2 = max(w2, abs(Dc[q, 0, 0] - math.pi * r) / (math.pi * r))
+                w2 = max(w2, abs(Dc[q, 1, 1] - 1 / (math.pi * r)) * math.pi * r)
+                w1 = max(w1, abs(Dc[q, 0, 1]), abs(Dc[q, 1, 0]))
+            wm = max(wm, abs(Dc[:, 0, 1].mean()))
+        e2.append(w2); e1.append(w1); em.append(wm)
+    assert e2[-1] < 2e-4 and max(em) < 1e-12
+    for i in range(2):
+        assert e2[i] / e2[i + 1] > 3.5, e2
+        assert 1.8 < e1[i] / e1[i + 1] < 2.2, e1
+
+
+def test_shell_metric_closed_form():
+    """Spherical octant r = 1/2 + s/2, theta = pi t/2, phi = pi w/2:
+    det = pi^2 r^2 sin(theta) / 8, D_c = diag(pi^2 r^2 sin th / 2, sin th / 2,
+    1 / (2 sin th)).  Diagonal and det to O(h^2) at each Gauss point; the
+    off-diagonal shear of the trilinear map is O(h) pointwise."""
+    n = 33
+    h = 1.0 / (n - 1)
+    coords = inputs.coords_shell_octant(n)
+    ck, cj, ci = 10, 12, 7
+    idx = [(ck + ((a >> 2) & 1), cj + ((a >> 1) & 1), ci + (a & 1)) for a in range(8)]
+    xe = np.stack([[coords[c][t] for t in idx] for c in range(3)])
+    det, Dc = oracle.metric(xe, 1.0, h)
+    g = 0.5 + 0.5 / math.sqrt(3)
+    gl = 0.5 - 0.5 / math.sqrt(3)
+    for q in range(8):
+        s = (ci + (g if q & 1 else gl)) * h
+        t = (cj + (g if q & 2 else gl)) * h
+        r = 0.5 + 0.5 * s
+        th = 0.5 * math.pi * t
+        want_det = math.pi ** 2 * r ** 2 * math.sin(th) / 8
+        want = np.diag([math.pi ** 2 * r ** 2 * math.sin(th) / 2, math.sin(th) / 2, 1 / (2 * math.sin(th))])
+        assert abs(det[q] - want_det) / want_det < 5e-3
+        np.testing.assert_allclose(np.diag(Dc[q]), np.diag(want), rtol=5e-3)
+        off = Dc[q] - np.diag(np.diag(Dc[q]))
+        assert np.abs(off).max() < 0.5 * h * want.max()
+
+
+@pytest.mark.parametrize("dim", [2, 3])
+def test_cond_bound_is_tight_for_scalar_kappa(dim):
+    """cond(D_c) <= cond(J_T)^2 cond(D) (Sec. 2.1) holds with equality when D
+    is a scalar multiple of I."""
+    rng = np.random.default_rng(5 + dim)
+    for _ in range(5):
+        M = rng.normal(size=(dim, dim)) + 2 * np.eye(dim)
+        if np.linalg.det(M) < 0:
+            M[:, 0] *= -1
+        n = 5
+        coords = _affine_coords(n, M, np.zeros(dim), dim)
+        xe = np.stack([coords[c].reshape(-1)[[0, 1, n, n + 1, n * n, n * n + 1, n * n + n, n * n + n + 1][: 1 << dim]]
+                       for c in range(dim)])
+        _, Dc = oracle.metric(xe, 3.5, 1.0 / (n - 1))
+        cD = np.linalg.cond(Dc[0])
+        cJ = np.linalg.cond(M)
+        assert abs(cD - cJ ** 2) / cJ ** 2 < 1e-9   # rounding grows with cond
+
+
+# ------------------------------------------------------------------ P4
+def _full_symmetry_error(A):
+    d = A.ndim - 1
+    n = A.shape[0]
+    err = 0.0
+    it = np.ndindex(*A.shape[:-1])
+    for pos in it:
+        ijk = np.array(pos[::-1])
+        if np.any(ijk < 1) or np.any(ijk > n - 2):
+            continue
+        for o in range(3 ** d):
+            off = np.array([(o % 3) - 1, (o // 3) % 3 - 1, o // 9 - 1][:d])
+            q = ijk + off
+            if np.any(q < 1) or np.any(q > n - 2):
+                assert A[pos + (o,)] == 0.0
+                continue
+            o2 = 3 ** d - 1 - o
+            err = max(err, abs(A[pos + (o,)] - A[tuple(q[::-1]) + (o2,)]))
+    return err
+
+
+@pytest.mark.parametrize("dim,n", [(2, 17), (3, 9)])
+def test_levels_symmetric_and_zero_row_sums(dim, n):
+    """Every level's operator is symmetric (Galerkin P^T A P of a symmetric
+    A) and rows at distance >= 2 from the Dirichlet boundary have zero row
+    sum (constants are in the kernel of the pure diffusion operator and
+    operator-induced interpolation reproduces them)."""
+    rng = np.random.default_rng(21)
+    if dim == 2:
+        coords = inputs.coords_bump(n, 0.12, -0.09)
+    else:
+        coords = inputs.coords_shell_octant(n)
+        coords = coords + 0.0
+    kappa = np.exp(rng.normal(0, 0.7, size=(n - 1,) * dim))
+    A = oracle.assemble(coords, kappa)
+    H = oracle.Hierarchy(A)
+    for l in range(H.nlev):
+        Al = H.A(l)
+        nl = H.level_n(l)
+        scale = np.abs(Al[..., (3 ** dim - 1) // 2]).max()
+        assert _full_symmetry_error(Al) <= 1e-13 * scale
+        if nl >= 7:
+            inner = Al[(slice(2, nl - 2),) * dim].sum(axis=-1)
+            assert np.abs(inner).max() <= 1e-13 * scale
+
+
+# ------------------------------------------------------------------ P5
+@pytest.mark.parametrize("dim,n", [(2, 17), (3, 9)])
+def test_identity_map_galerkin_equals_rediscretisation(dim, n):
+    """Identity map, kappa = 1: the collapse gives exactly (bi/tri)linear
+    interpolation and, Q1 spaces being nested, P^T A_h P is the Q1 operator of
+    the coarse grid (the same stencil in 2-D; twice the fine one in 3-D,
+    where the stencil scales with h)."""
+    coords = inputs.coords_identity(n, dim)
+    A = oracle.assemble(coords, np.ones((n - 1,) * dim))
+    P = oracle.interp(A)
+    # (bi/tri)linear weights: 2^-(number of odd coordinates), interior coarse only
+    for pos in np.ndindex(*P.shape[:-1]):
+        ijk = np.array(pos[::-1])
+        if np.any(ijk < 1) or np.any(ijk > n - 2):
+            assert np.all(P[pos] == 0.0)
+            continue
+        nodd = int(np.sum(ijk & 1))
+        for s in range(1 << dim):
+            K = (ijk >> 1) + np.array([(s >> a) & 1 for a in range(dim)])
+            bits = np.array([(s >> a) & 1 for a in range(dim)])
+            valid = np.all((ijk & 1) | (bits == 0))   # even axes use only slot 0
+            interior = np.all(K >= 1) and np.all(K <= (n + 1) // 2 - 2)
+            want = 2.0 ** (-nodd) if (valid and interior) else 0.0
+            assert abs(P[pos + (s,)] - want) < 1e-14, (pos, s, P[pos + (s,)], want)
+    Ac = oracle.rap(A, P)
+    nc = (n + 1) // 2
+    A2 = oracle.assemble(inputs.coords_identity(nc, dim), np.ones((nc - 1,) * dim))
+    np.testing.assert_allclose(Ac, A2, atol=1e-13)
+    ctr = (3 ** dim - 1) // 2
+    mid = (slice(2, 3),) * dim
+    ratio = Ac[(slice(2, 3),) * dim][..., ctr] / A[mid][..., ctr]
+    assert abs(float(ratio.ravel()[0]) - (1.0 if dim == 2 else 2.0)) < 1e-13
+
+
+# ------------------------------------------------------------------ interpolation definition
+@pytest.mark.parametrize("dim,n", [(2, 17), (3, 9)])
+def test_interpolation_solves_fine_equation_at_all_odd_points(dim, n):
+    """Operator-induced interpolation (Sec. 2.2) fills the points with all
+    coordinates odd by solving the fine equation there: (A P v)_i = 0 for
+    every coarse v.  Edge points satisfy the collapsed (line) equation."""
+    rng = np.random.default_rng(3)
+    coords = inputs.coords_bump(n, -0.1, 0.13) if dim == 2 else inputs.coords_shell_octant(n)
+    A = oracle.assemble(coords, np.exp(rng.normal(0, 1.0, size=(n - 1,) * dim)))
+    P = oracle.interp(A)
+    Ad = oracle.dense_operator(A)
+    Pd = oracle.dense_interp(P)
+    AP = Ad @ Pd
+    m = oracle.interior_mask(n, dim)
+    pos = np.argwhere(m)[:, ::-1]                     # (i, j[, k]) per interior unknown
+    allodd = np.all(pos & 1, axis=1)
+    assert np.abs(AP[allodd]).max() < 1e-12 * np.abs(Ad).max()
+    # line points: collapsed 3-point equation along the odd axis
+    S = 3 ** dim
+    ones = [(pos[:, a] & 1) for a in range(dim)]
+    nodd = sum(ones)
+    line = np.nonzero(nodd == 1)[0]
+    v = rng.normal(size=Pd.shape[1])
+    u = Pd @ v                                       # interpolated fine values
+    uf = np.zeros((n,) * dim)
+    uf[m] = u
+    for r in line[:50]:
+        ijk = pos[r]
+        a = int(np.argmax(ijk & 1))
+        coef = {-1: 0.0, 0: 0.0, 1: 0.0}
+        for o in range(S):
+            off = [(o % 3) - 1, (o // 3) % 3 - 1, o // 9 - 1][:dim]
+            coef[off[a]] += A[tuple(ijk[::-1]) + (o,)]
+        lo = ijk.copy(); lo[a] -= 1
+        hi = ijk.copy(); hi[a] += 1
+        res = coef[-1] * uf[tuple(lo[::-1])] + coef[0] * uf[tuple(ijk[::-1])] + coef[1] * uf[tuple(hi[::-1])]
+        assert abs(res) < 1e-12 * (abs(coef[0]) * np.abs(uf).max() + 1e-300)
+
+
+# ------------------------------------------------------------------ P6
+@pytest.mark.parametrize("dim,n", [(2, 9), (2, 17), (3, 9)])
+def test_rap_equals_dense_triple_product(dim, n):
+    rng = np.random.default_rng(8 + n + dim)
+    coords = inputs.coords_bump(n, 0.14, 0.1) if dim == 2 else inputs.coords_shell_octant(n)
+    A = oracle.assemble(coords, np.exp(rng.normal(0, 1.0, size=(n - 1,) * dim)))
+    P = oracle.interp(A)
+    Ac = oracle.rap(A, P)
+    dense = oracle.dense_interp(P).T @ oracle.dense_operator(A) @ oracle.dense_interp(P)
+    np.testing.assert_allclose(oracle.dense_operator(Ac), dense, atol=1e-13 * np.abs(dense).max())
+
+
+def test_restrict_and_prolong_are_transposes():
+    """R = P^T (Sec. 2.3) and prolongation is x + P xc."""
+    rng = np.random.default_rng(4)
+    n = 17
+    A = oracle.assemble(inputs.coords_quarter_annulus(n), np.exp(rng.normal(size=(n - 1, n - 1))))
+    P = oracle.interp(A)
+    Pd = oracle.dense_interp(P)
+    r = inputs.zero_boundary(rng.normal(size=(n, n)))
+    bc = oracle.restrict(P, r)
+    np.testing.assert_allclose(bc[1:-1, 1:-1].ravel(), Pd.T @ r[1:-1, 1:-1].ravel(), atol=1e-14)
+    xc = inputs.zero_boundary(rng.normal(size=(9, 9)))
+    x = inputs.zero_boundary(rng.normal(size=(n, n)))
+    y = oracle.prolong(P, xc, x)
+    np.testing.assert_allclose(y[1:-1, 1:-1].ravel(), x[1:-1, 1:-1].ravel() + Pd @ xc[1:-1, 1:-1].ravel(),
+                               atol=1e-14)
+
+
+# ------------------------------------------------------------------ smoother
+@pytest.mark.parametrize("dim,n,reverse", [(2, 9, False), (2, 9, True), (3, 5, False), (3, 5, True)])
+def test_multicolour_gs_is_gauss_seidel_in_colour_order(dim, n, reverse):
+    """A multicolour sweep is Gauss-Seidel on the matrix with unknowns ordered
+    by colour: x_new = (D + L)^-1 (b - U x_old) in that ordering."""
+    rng = np.random.default_rng(9)
+    coords = inputs.coords_bump(n, 0.1, 0.1) if dim == 2 else inputs.coords_shell_octant(n)
+    A = oracle.assemble(coords, np.exp(rng.normal(size=(n - 1,) * dim)))
+    m = oracle.interior_mask(n, dim)
+    pos = np.argwhere(m)[:, ::-1]
+    colour = sum((pos[:, a] & 1) << a for a in range(dim))
+    if reverse:
+        colour = (1 << dim) - 1 - colour
+    order = np.argsort(colour, kind="stable")
+    Ad = oracle.dense_operator(A)[np.ix_(order, order)]
+    b = inputs.zero_boundary(rng.normal(size=(n,) * dim))
+    x0 = inputs.zero_boundary(rng.normal(size=(n,) * dim))
+    x1 = oracle.smooth(A, b, x0, reverse=reverse)
+    L = np.tril(Ad)
+    U = Ad - L
+    want = np.linalg.solve(L, b[m][order] - U @ x0[m][order])
+    np.testing.assert_allclose(x1[m][order], want, atol=1e-13 * np.abs(want).max())
+
+
+# ------------------------------------------------------------------ V-cycle
+def _dense_vcycle_matrix(H, l):
+    """M_l = (I - E_l) A_l^-1 with E_l = S_post (I - P M_{l+1} P^T A) S_pre,
+    S = I - B^-1 A, B the colour-ordered GS matrix (forward / reverse):
+    the error-propagation form of the V(1,1)-cycle."""
+    Al = H.A(l)
+    dim = H.dim
+    Ad = oracle.dense_operator(Al)
+    N = Ad.shape[0]
+    if l == H.nlev - 1:
+        return np.linalg.inv(Ad)
+    n = H.level_n(l)
+    pos = np.argwhere(oracle.interior_mask(n, dim))[:, ::-1]
+    colour = sum((pos[:, a] & 1) << a for a in range(dim))
+
+    def gs_matrix(rev):
+        key = (1 << dim) - 1 - colour if rev else colour
+        rank = np.empty(N, dtype=np.int64)
+        rank[np.argsort(key, kind="stable")] = np.arange(N)
+        Bm = np.where(rank[:, None] >= rank[None, :], Ad, 0.0)
+        return Bm
+
+    I = np.eye(N)
+    Spre = I - np.linalg.solve(gs_matrix(False), Ad)
+    Spost = I - np.linalg.solve(gs_matrix(True), Ad)
+    Pd = oracle.dense_interp(H.P(l))
+    Mc = _dense_vcycle_matrix(H, l + 1)
+    E = Spost @ (I - Pd @ Mc @ Pd.T @ Ad) @ Spre
+    return (I - E) @ np.linalg.inv(Ad)
+
+
+@pytest.mark.parametrize("dim,n", [(2, 9), (2, 17), (3, 9)])
+def test_vcycle_matches_error_propagation_form(dim, n):
+    rng = np.random.default_rng(17)
+    coords = inputs.coords_quarter_annulus(n) if dim == 2 else inputs.coords_shell_octant(n)
+    A = oracle.assemble(coords, np.exp(rng.normal(0, 0.5, size=(n - 1,) * dim)))
+    H = oracle.Hierarchy(A)
+    M = _dense_vcycle_matrix(H, 0)
+    m = oracle.interior_mask(n, dim)
+    for _ in range(3):
+        r = inputs.zero_boundary(rng.normal(size=(n,) * dim))
+        z = H.vcycle(r)
+        want = M @ r[m]
+        np.testing.assert_allclose(z[m], want, atol=1e-12 * np.abs(want).max())
+        assert np.all(z[~m] == 0.0)
+
+
+@pytest.mark.parametrize("dim,n", [(2, 33), (3, 9)])
+def test_vcycle_symmetric_positive(dim, n):
+    """The forward/reverse colour order makes M symmetric positive definite,
+    so it is a valid CG preconditioner: <Mx,y> = <x,My>, <Mx,x> > 0."""
+    rng = np.random.default_rng(23)
+    coords = inputs.coords_quarter_annulus(n) if dim == 2 else inputs.coords_shell_octant(n)
+    A = oracle.assemble(coords, np.exp(rng.normal(0, 0.5, size=(n - 1,) * dim)))
+    H = oracle.Hierarchy(A)
+    for _ in range(3):
+        x = inputs.zero_boundary(rng.normal(size=(n,) * dim))
+        y = inputs.zero_boundary(rng.normal(size=(n,) * dim))
+        Mx, My = H.vcycle(x), H.vcycle(y)
+        a, b = float(np.sum(Mx * y)), float(np.sum(x * My))
+        assert abs(a - b) <= 1e-13 * (abs(a) + abs(b)) + 1e-300
+        assert float(np.sum(Mx * x)) > 0
+
+
+# ------------------------------------------------------------------ P7
+@pytest.mark.parametrize("dim,n", [(2, 9), (3, 9)])
+@pytest.mark.parametrize("flexible", [False, True])
+def test_pcg_matches_brute_force_solve(dim, n, flexible):
+    rng = np.random.default_rng(31)
+    coords = inputs.coords_quarter_annulus(n) if dim == 2 else inputs.coords_shell_octant(n)
+    A = oracle.assemble(coords, np.exp(rng.normal(0, 0.5, size=(n - 1,) * dim)))
+    b = inputs.rhs_uniform(rng, (n,) * dim)
+    H = oracle.Hierarchy(A)
+    x, it, hist, trr, st = H.pcg(b, tol=1e-14, maxit=200, flexible=flexible)
+    assert st == 0 and trr <= 1e-14
+    m = oracle.interior_mask(n, dim)
+    xs = np.linalg.solve(oracle.dense_operator(A), b[m])
+    assert np.abs(x[m] - xs).max() / np.abs(xs).max() < 1e-12
+    assert np.all(np.diff(hist[:3]) < 0)
+
+
+def test_pcg_zero_rhs_and_fixed_iterations():
+    n = 17
+    A = oracle.assemble(inputs.coords_quarter_annulus(n), np.ones((n - 1, n - 1)))
+    H = oracle.Hierarchy(A)
+    x, it, hist, trr, st = H.pcg(np.zeros((n, n)), tol=1e-10)
+    assert st == 0 and it == 0 and np.all(x == 0)
+    b = inputs.rhs_uniform(np.random.default_rng(0), (n, n))
+    x, it, hist, trr, st = H.pcg(b, tol=0.0, maxit=3)
+    assert st == 0 and it == 3 and len(hist) == 4
+
+
+# ------------------------------------------------------------------ P8
+def test_manufactured_solution_2d_second_order():
+    """u = (r-1/2)(1-r) sin(2 theta) on the quarter annulus; -Lap u =
+    (9r-4) sin(2 theta) / (2 r^2).  Nodal errors of the Q1 solution fall by
+    about 4 per halving of h."""
+    errs = []
+    for n in (17, 33, 65):
+        coords = inputs.coords_quarter_annulus(n)
+        xq = oracle.gauss_points(coords)
+        r = np.hypot(xq[..., 0], xq[..., 1])
+        th = np.arctan2(xq[..., 1], xq[..., 0])
+        fq = (9 * r - 4) * np.sin(2 * th) / (2 * r * r)
+        b = oracle.load_vector(coords, fq)
+        A = oracle.assemble(coords, np.ones((n - 1, n - 1)))
+        x, it, _, trr, st = oracle.Hierarchy(A).pcg(b, tol=1e-13, maxit=100)
+        assert st == 0
+        R = np.hypot(coords[0], coords[1])
+        TH = np.arctan2(coords[1], coords[0])
+        u = (R - 0.5) * (1 - R) * np.sin(2 * TH)
+        errs.append(np.abs(x - u).max())
+    ratios = [errs[i] / errs[i + 1] for i in range(2)]
+    assert 3.5 < ratios[-1] < 4.5, (errs, ratios)
+
+
+def test_manufactured_solution_3d_second_order():
+    """u = (r-1/2)(1-r) x y z / r^3 on the shell octant (zero on all six
+    faces); f = -Lap u derived symbolically."""
+    sympy = pytest.importorskip("sympy")
+    X, Y, Z = sympy.symbols("x y z", real=True)
+    R = sympy.sqrt(X ** 2 + Y ** 2 + Z ** 2)
+    U = (R - sympy.Rational(1, 2)) * (1 - R) * X * Y * Z / R ** 3
+    F = -(sympy.diff(U, X, 2) + sympy.diff(U, Y, 2) + sympy.diff(U, Z, 2))
+    f = sympy.lambdify((X, Y, Z), sympy.simplify(F), "numpy")
+    u = sympy.lambdify((X, Y, Z), U, "numpy")
+    errs = []
+    for n in (9, 17, 33):
+        coords = inputs.coords_shell_octant(n)
+        xq = oracle.gauss_points(coords)
+        fq = f(xq[..., 0], xq[..., 1], xq[..., 2])
+        b = oracle.load_vector(coords, fq)
+        A = oracle.assemble(coords, np.ones((n - 1,) * 3))
+        x, it, _, trr, st = oracle.Hierarchy(A).pcg(b, tol=1e-12, maxit=300)
+        assert st == 0
+        m = oracle.interior_mask(n, 3)
+        ue = u(coords[0], coords[1], coords[2])
+        errs.append(np.abs(x[m] - ue[m]).max())
+    ratio = errs[1] / errs[2]
+    assert 3.0 < ratio < 5.0, errs
+
+
+# ------------------------------------------------------------------ P10, P11
+def test_iterations_roughly_size_independent():
+    """D-MG iteration counts stay consistent as the grid is refined (Sec. 4.3)."""
+    its = []
+    for n in (33, 65, 129):
+        p = inputs.annulus_plain(n)
+        A = oracle.assemble(p.coords, p.kappa)
+        _, it, _, _, st = oracle.Hierarchy(A).pcg(p.rhs, tol=1e-10, maxit=100)
+        assert st == 0
+        its.append(it)
+    assert max(its) - min(its) <= 3, its
+
+
+def test_grid_and_operator_complexity():
+    """GC = sum N_l / N_1 (Sec. 4) is below 4/3 in 2-D and 8/7 in 3-D; with
+    symmetric storage (5 values per DoF, Sec. 4.1) OC stays below 5*4/3."""
+    for dim, n in [(2, 65), (3, 17)]:
+        A = oracle.assemble(inputs.coords_identity(n, dim), np.ones((n - 1,) * dim))
+        H = oracle.Hierarchy(A)
+        N = [(H.level_n(l) - 2) ** dim for l in range(H.nlev)]
+        gc = sum(N) / N[0]
+        assert gc < (4 / 3 if dim == 2 else 8 / 7)
+        nnz = [int(np.count_nonzero(H.A(l))) for l in range(H.nlev)]
+        assert sum(nnz) / nnz[0] < (4 / 3 if dim == 2 else 8 / 7) + 1e-12
+
+
+# ------------------------------------------------------------------ P12
+def test_adjoint_gradient_matches_dense_and_central_differences():
+    """dL/dm_e = kappa_e * (-lambda_e^T K_e^0 u_e) with A lambda = u - u_obs,
+    L = 1/2 |u - u_obs|^2, kappa = exp(m): against central differences of the
+    loss (dense solves) on a 9x9 grid."""
+    n = 9
+    rng = np.random.default_rng(3)
+    coords = inputs.coords_quarter_annulus(n)
+    mpar = rng.normal(0, 0.5, size=(n - 1, n - 1))
+    u_obs = inputs.rhs_uniform(rng, (n, n))
+    f = inputs.rhs_uniform(rng, (n, n))
+    msk = oracle.interior_mask(n, 2)
+
+    def solve(mm):
+        Ad = oracle.dense_operator(oracle.assemble(coords, np.exp(mm)))
+        u = np.zeros((n, n))
+        u[msk] = np.linalg.solve(Ad, f[msk])
+        return u, Ad
+
+    u, Ad = solve(mpar)
+    lam = np.zeros((n, n))
+    lam[msk] = np.linalg.solve(Ad, (u - u_obs)[msk])
+    g = np.exp(mpar) * oracle.adjoint_grad(coords, u, lam)
+    eps = 1e-4
+    for e in [(0, 0), (3, 4), (7, 7), (2, 6)]:
+        mp = mpar.copy(); mp[e] += eps
+        mm = mpar.copy(); mm[e] -= eps
+        up, _ = solve(mp)
+        um, _ = solve(mm)
+        # L(+) - L(-) = 1/2 sum (u+ - u-)(u+ + u- - 2 u_obs)
+        dL = 0.5 * np.sum((up - um) * (up + um - 2 * u_obs))
+        fd = dL / (2 * eps)
+        assert abs(fd - g[e]) <= 1e-6 * max(abs(g[e]), 1e-3 * np.abs(g).max()), (e, fd, g[e])
+
+
+def test_symmetric_solve_identity():
+    """<A^-1 a, b> = <a, A^-1 b> through the oracle's PCG (the adjoint solve
+    reuses the forward hierarchy because A is symmetric)."""
+    n = 17
+    rng = np.random.default_rng(12)
+    A = oracle.assemble(inputs.coords_quarter_annulus(n), np.exp(rng.normal(size=(n - 1, n - 1))))
+    H = oracle.Hierarchy(A)
+    a = inputs.rhs_uniform(rng, (n, n))
+    b = inputs.rhs_uniform(rng, (n, n))
+    xa = H.pcg(a, tol=1e-14, maxit=200)[0]
+    xb = H.pcg(b, tol=1e-14, maxit=200)[0]
+    s1, s2 = float(np.sum(xa * b)), float(np.sum(a * xb))
+    assert abs(s1 - s2) <= 1e-12 * abs(s1)
