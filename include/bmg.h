@@ -1,0 +1,176 @@
+/*
+ * bmg.h -- C ABI of the GB300 structured black-box multigrid solver.
+ *
+ * The library solves the discrete diffusion problem that the paper obtains
+ * by pulling -div(kappa grad u) = f back through a map onto the structured
+ * computational grid (Sec. 2, eq. "weak_computational"; Sec. 2.1, effective
+ * coefficient D_c = J_T (D o T^-1) J_T^T |J_T^-1|), with the structured
+ * multigrid of Sec. 2.2: factor-two coarsening, operator-induced
+ * interpolation, Galerkin coarse operators and a V-cycle, here wrapped in
+ * preconditioned conjugate gradients.  The setup/solve split follows the
+ * paper's "Setup phase" (assemble A_c or take it as given, set up the
+ * multigrid) and "Solution phase".
+ *
+ * Grids: n = 2^k + 1 nodes per side (k >= 1) on [0,1]^d, d = 2 or 3.
+ * Node (i,j[,k]) has index i + n*(j + n*k) (i fastest); cell (ci,cj[,ck])
+ * (lower corner) has index ci + (n-1)*(cj + (n-1)*ck).  All nodes on the
+ * boundary carry zero Dirichlet data: they are not unknowns, their entries
+ * are ignored on input and written as 0 on output.  DoF = (n-2)^d.
+ *
+ * Memory and streams.  The library allocates no device memory: the caller
+ * queries bmg_workspace_bytes, allocates one device buffer (e.g. a torch
+ * tensor) and attaches it with bmg_attach together with a CUDA stream; all
+ * work is ordered on that stream.  Array arguments are caller-owned and
+ * must stay alive for the call.  Unless a call says otherwise, array
+ * arguments are device pointers on the context's device; bmg_solve and
+ * bmg_vcycle also accept host pointers (pageable or pinned), which they
+ * stage through the workspace (the copies are part of the call).
+ *
+ * Errors.  Every call returns a bmg_status and never aborts or traps.
+ * Device-side checks (folded map, setup breakdown, CG breakdown) set a
+ * device error word that the call reads back before returning.  After an
+ * error the context stays valid; the data it holds may not be.
+ */
+#ifndef BMG_H
+#define BMG_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct bmg_ctx bmg_ctx;   /* opaque; created and destroyed by the library */
+
+typedef enum {
+    BMG_OK = 0,
+    BMG_ERR_ARG = 1,               /* invalid argument (null pointer, bad option) */
+    BMG_ERR_SHAPE = 2,             /* n is not 2^k+1 or dim not in {2,3} */
+    BMG_ERR_DEVICE = 3,            /* a CUDA runtime call failed */
+    BMG_ERR_WORKSPACE = 4,         /* no workspace attached or too small */
+    BMG_ERR_MAP_FOLDED = 5,        /* det J <= 0 at a quadrature point */
+    BMG_ERR_SETUP_BREAKDOWN = 6,   /* zero collapsed denominator / non-positive diagonal */
+    BMG_ERR_NOT_SPD = 7,           /* CG breakdown: p^T A p <= 0 */
+    BMG_ERR_NOT_CONVERGED = 8,     /* maxit reached before tol */
+    BMG_ERR_TIMEOUT = 9,           /* a bounded device wait expired */
+    BMG_ERR_STATE = 10             /* call out of order (e.g. solve before setup) */
+} bmg_status;
+
+enum {
+    BMG_PREC_FP64 = 0,             /* V-cycle in FP64 */
+    BMG_PREC_FP32 = 1              /* V-cycle in FP32; outer CG, residuals, dots
+                                      and the coarsest solve stay FP64 */
+};
+
+enum {
+    BMG_OUTER_CG = 0,              /* beta = r_{k+1}.z_{k+1} / r_k.z_k */
+    BMG_OUTER_FLEXIBLE_CG = 1      /* beta = r_{k+1}.(z_{k+1}-z_k) / r_k.z_k */
+};
+
+typedef struct {
+    int dim;          /* 2 or 3 */
+    int n;            /* nodes per side, 2^k + 1, k >= 1 */
+    int precision;    /* BMG_PREC_FP64 or BMG_PREC_FP32 */
+    int outer;        /* BMG_OUTER_CG or BMG_OUTER_FLEXIBLE_CG */
+    int flags;        /* reserved, 0 */
+} bmg_opts;
+
+typedef struct {
+    int iterations;               /* PCG iterations done */
+    int levels;                   /* multigrid levels (finest .. 3 nodes per side) */
+    double relres;                /* recursive ||r_k|| / ||b|| at exit */
+    double true_relres;           /* ||b - A x|| / ||b|| at exit, FP64 */
+    double rho;                   /* (||r_k|| / ||r_0||)^(1/k) */
+    double grid_complexity;       /* sum_l N_l / N_0 (Sec. 4) */
+    double operator_complexity;   /* sum_l stored_l / stored_0 (symmetric storage) */
+    int status;                   /* bmg_status of the solve */
+} bmg_info;
+
+/* Defaults: dim 2, precision FP64, outer CG (flexible CG when FP32). */
+void bmg_default_opts(bmg_opts* opts);
+
+/* Creates a context (host memory only).  Fails with BMG_ERR_SHAPE for
+   invalid n/dim.  *ctx is NULL on failure. */
+bmg_status bmg_create(const bmg_opts* opts, bmg_ctx** ctx);
+
+/* Bytes of device workspace the context needs (256-byte aligned start). */
+bmg_status bmg_workspace_bytes(const bmg_ctx* ctx, size_t* bytes);
+
+/* Attaches a caller-owned device workspace of at least bmg_workspace_bytes
+   and the cudaStream_t (as void*; NULL = legacy default stream) all later
+   calls are ordered on.  The device current at this call becomes the
+   context's device.  The workspace must outlive the context's use. */
+bmg_status bmg_attach(bmg_ctx* ctx, void* workspace, size_t bytes, void* stream);
+
+/* Assembles the finest-grid operator A_c (Sec. 2.1, "Setup phase" step 2):
+   Q1 elements, 2^d-point Gauss rule per cell, isoparametric map from the
+   nodal coordinates, per-cell coefficient kappa, effective coefficient
+   kappa det J J^-1 J^-T at each Gauss point; couplings to boundary nodes
+   dropped.  coords: device, d planes of n^d doubles (x plane, y plane[,
+   z plane]); kappa: device, (n-1)^d doubles.  Errors: BMG_ERR_MAP_FOLDED. */
+bmg_status bmg_assemble(bmg_ctx* ctx, const double* coords, const double* kappa);
+
+/* Sets the finest operator directly ("either A_c must be provided, or the
+   diffusion coefficient", Sec. 2.2).  stencil: device, n^d rows of 3^d
+   doubles, entry (dx+1)+3(dy+1)[+9(dz+1)] = A[node, node+offset]; the
+   operator must be symmetric with zero couplings to boundary nodes (only
+   the lower half of each row is read). */
+bmg_status bmg_set_stencil(bmg_ctx* ctx, const double* stencil);
+
+/* Builds the multigrid hierarchy ("Setup phase" step 3): operator-induced
+   interpolation from each level's stencil, Galerkin coarse operators
+   P^T A P, FP32 copies when precision is FP32.  Errors:
+   BMG_ERR_SETUP_BREAKDOWN, BMG_ERR_STATE (no operator yet). */
+bmg_status bmg_setup(bmg_ctx* ctx);
+
+/* One V(1,1)-cycle from a zero initial guess: z = M r ("Solution phase"
+   step 3).  r, z: n^d doubles, host or device.  Boundary entries of r are
+   ignored; z is 0 on the boundary. */
+bmg_status bmg_vcycle(bmg_ctx* ctx, const double* r, double* z);
+
+/* Preconditioned CG, M = one V-cycle, until ||r_k|| <= tol ||b|| for the
+   recursive and then the true residual (when only the recursive one
+   passes, r is replaced by the true residual and CG continues), or maxit
+   iterations.  tol <= 0 runs exactly maxit iterations.  b, x: n^d doubles,
+   host or device; x holds the initial guess on entry and the iterate on
+   exit (also on BMG_ERR_NOT_CONVERGED).  info may be NULL. */
+bmg_status bmg_solve(bmg_ctx* ctx, const double* b, double* x, double tol, int maxit,
+                     bmg_info* info);
+
+/* Adjoint gradient with respect to the per-cell coefficient for a loss
+   L(u) of the solution u = A^-1 b: solves A lambda = dL/du with the same
+   hierarchy (A is symmetric) and evaluates, per cell e,
+   dLdkappa[e] = -lambda_e^T K_e^0 u_e, K_e^0 the element matrix at
+   kappa = 1.  (dL/db = lambda.)  u, dLdu, lambda: n^d doubles (device);
+   dLdkappa: (n-1)^d doubles (device); coords: the coordinates given to
+   bmg_assemble (device).  Needs a context built by bmg_assemble. */
+bmg_status bmg_adjoint_grad(bmg_ctx* ctx, const double* coords, const double* u,
+                            const double* dLdu, double* lambda, double* dLdkappa,
+                            double tol, int maxit, bmg_info* info);
+
+/* Hierarchy queries (for diagnostics and parity checks). */
+int bmg_levels(const bmg_ctx* ctx);
+int bmg_level_n(const bmg_ctx* ctx, int level);
+
+/* Copies level `level`'s operator into out (device, n_l^d rows of 3^d
+   doubles, the full stencil as in bmg_set_stencil). */
+bmg_status bmg_get_stencil(bmg_ctx* ctx, int level, double* out);
+
+/* Copies the interpolation from level level+1 to level `level` into out
+   (device, n_l^d rows of 2^d doubles): entry s = sx + 2 sy [+ 4 sz] of
+   fine node (i,j[,k]) is its weight to coarse node
+   (i>>1 + sx, j>>1 + sy[, k>>1 + sz]); weights to boundary coarse nodes
+   and rows of boundary fine nodes are 0. */
+bmg_status bmg_get_interp(bmg_ctx* ctx, int level, double* out);
+
+/* Kernel launches the context has issued since creation (all kinds). */
+long long bmg_launch_count(const bmg_ctx* ctx);
+
+void bmg_destroy(bmg_ctx* ctx);
+const char* bmg_status_str(bmg_status status);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* BMG_H */

@@ -1,0 +1,243 @@
+"""Thin ctypes binding of libbmg.so (C ABI in include/bmg.h).
+
+Argument marshalling only: torch tensors supply device memory (the
+workspace and the arrays) and the CUDA stream; every step of the solve
+runs in the library's kernels.  The library must have been built
+(``paper_2509_08109_gb300.build.build()``); loading fails loudly otherwise,
+and there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from dataclasses import dataclass
+
+import torch
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libbmg.so")
+_lib = None
+
+PREC = {"fp64": 0, "fp32": 1}
+OUTER = {"cg": 0, "flexible": 1}
+
+STATUS = {0: "ok", 1: "invalid argument", 2: "unsupported shape", 3: "CUDA runtime error",
+          4: "workspace missing or too small", 5: "map folded", 6: "setup breakdown",
+          7: "CG breakdown (not SPD)", 8: "not converged", 9: "bounded wait expired", 10: "call out of order"}
+
+
+class BmgError(RuntimeError):
+    def __init__(self, code: int, where: str):
+        super().__init__(f"{where}: bmg status {code} ({STATUS.get(code, '?')})")
+        self.code = code
+
+
+class _Opts(ctypes.Structure):
+    _fields_ = [("dim", ctypes.c_int), ("n", ctypes.c_int), ("precision", ctypes.c_int),
+                ("outer", ctypes.c_int), ("flags", ctypes.c_int)]
+
+
+class _Info(ctypes.Structure):
+    _fields_ = [("iterations", ctypes.c_int), ("levels", ctypes.c_int), ("relres", ctypes.c_double),
+                ("true_relres", ctypes.c_double), ("rho", ctypes.c_double),
+                ("grid_complexity", ctypes.c_double), ("operator_complexity", ctypes.c_double),
+                ("status", ctypes.c_int)]
+
+
+@dataclass
+class SolveInfo:
+    iterations: int
+    levels: int
+    relres: float
+    true_relres: float
+    rho: float
+    grid_complexity: float
+    operator_complexity: float
+    status: int
+
+
+def load() -> ctypes.CDLL:
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise RuntimeError(f"{LIB_PATH} is missing: build it with paper_2509_08109_gb300.build.build()")
+    lib = ctypes.CDLL(LIB_PATH)
+    P = ctypes.c_void_p
+    I = ctypes.c_int
+    D = ctypes.c_double
+    sigs = {
+        "bmg_default_opts": ([ctypes.POINTER(_Opts)], None),
+        "bmg_create": ([ctypes.POINTER(_Opts), ctypes.POINTER(P)], I),
+        "bmg_workspace_bytes": ([P, ctypes.POINTER(ctypes.c_size_t)], I),
+        "bmg_attach": ([P, P, ctypes.c_size_t, P], I),
+        "bmg_assemble": ([P, P, P], I),
+        "bmg_set_stencil": ([P, P], I),
+        "bmg_setup": ([P], I),
+        "bmg_vcycle": ([P, P, P], I),
+        "bmg_solve": ([P, P, P, D, I, ctypes.POINTER(_Info)], I),
+        "bmg_adjoint_grad": ([P, P, P, P, P, P, D, I, ctypes.POINTER(_Info)], I),
+        "bmg_levels": ([P], I),
+        "bmg_level_n": ([P, I], I),
+        "bmg_get_stencil": ([P, I, P], I),
+        "bmg_get_interp": ([P, I, P], I),
+        "bmg_launch_count": ([P], ctypes.c_longlong),
+        "bmg_destroy": ([P], None),
+        "bmg_status_str": ([I], ctypes.c_char_p),
+    }
+    for name, (args, res) in sigs.items():
+        f = getattr(lib, name)
+        f.argtypes = args
+        f.restype = res
+    _lib = lib
+    return lib
+
+
+def exported_symbols() -> list:
+    return ["bmg_default_opts", "bmg_create", "bmg_workspace_bytes", "bmg_attach", "bmg_assemble",
+            "bmg_set_stencil", "bmg_setup", "bmg_vcycle", "bmg_solve", "bmg_adjoint_grad", "bmg_levels",
+            "bmg_level_n", "bmg_get_stencil", "bmg_get_interp", "bmg_launch_count", "bmg_destroy",
+            "bmg_status_str"]
+
+
+def _check(code: int, where: str):
+    if code != 0:
+        raise BmgError(code, where)
+
+
+def _ptr(t: torch.Tensor):
+    assert t.is_contiguous() and t.dtype == torch.float64, (t.dtype, t.is_contiguous())
+    return ctypes.c_void_p(t.data_ptr())
+
+
+class Solver:
+    """One structured problem: n nodes per side in dim dimensions.
+
+    precision: 'fp64' (plain) or 'fp32' (FP32 V-cycle, FP64 outer CG).
+    outer: 'cg' or 'flexible' (default: 'cg' for fp64, 'flexible' for fp32).
+    """
+
+    def __init__(self, dim: int, n: int, precision: str = "fp64", outer: str | None = None,
+                 device=None, stream: torch.cuda.Stream | None = None):
+        lib = load()
+        self.dim, self.n, self.precision = dim, n, precision
+        if outer is None:
+            outer = "flexible" if precision == "fp32" else "cg"
+        self.outer = outer
+        self.device = torch.device(device) if device is not None else torch.device("cuda", torch.cuda.current_device())
+        opts = _Opts(dim, n, PREC[precision], OUTER[outer], 0)
+        h = ctypes.c_void_p()
+        _check(lib.bmg_create(ctypes.byref(opts), ctypes.byref(h)), "bmg_create")
+        self._h = h
+        nbytes = ctypes.c_size_t()
+        _check(lib.bmg_workspace_bytes(h, ctypes.byref(nbytes)), "bmg_workspace_bytes")
+        self.workspace_bytes = nbytes.value
+        with torch.cuda.device(self.device):
+            self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
+            self._ws = torch.empty(self.workspace_bytes, dtype=torch.uint8, device=self.device)
+            _check(lib.bmg_attach(h, ctypes.c_void_p(self._ws.data_ptr()), ctypes.c_size_t(self.workspace_bytes),
+                                  ctypes.c_void_p(self.stream.cuda_stream)), "bmg_attach")
+
+    def __del__(self):
+        if getattr(self, "_h", None) is not None and _lib is not None:
+            _lib.bmg_destroy(self._h)
+            self._h = None
+
+    # ------------------------------------------------------------ queries
+    @property
+    def levels(self) -> int:
+        return load().bmg_levels(self._h)
+
+    def level_n(self, l: int) -> int:
+        return load().bmg_level_n(self._h, l)
+
+    @property
+    def launches(self) -> int:
+        return load().bmg_launch_count(self._h)
+
+    @property
+    def grid_shape(self):
+        return (self.n,) * self.dim
+
+    def _dev(self, t: torch.Tensor) -> torch.Tensor:
+        return t.to(device=self.device, dtype=torch.float64).contiguous()
+
+    # ------------------------------------------------------------ setup
+    def assemble(self, coords, kappa):
+        coords = self._dev(torch.as_tensor(coords))
+        kappa = self._dev(torch.as_tensor(kappa))
+        assert coords.shape == (self.dim,) + self.grid_shape, coords.shape
+        assert kappa.shape == (self.n - 1,) * self.dim, kappa.shape
+        with torch.cuda.device(self.device):
+            _check(load().bmg_assemble(self._h, _ptr(coords), _ptr(kappa)), "bmg_assemble")
+        self._coords = coords
+        return self
+
+    def set_stencil(self, full):
+        full = self._dev(torch.as_tensor(full))
+        assert full.shape == self.grid_shape + (3 ** self.dim,)
+        with torch.cuda.device(self.device):
+            _check(load().bmg_set_stencil(self._h, _ptr(full)), "bmg_set_stencil")
+        return self
+
+    def setup(self):
+        with torch.cuda.device(self.device):
+            _check(load().bmg_setup(self._h), "bmg_setup")
+        return self
+
+    # ------------------------------------------------------------ solve
+    def vcycle(self, r: torch.Tensor, out: torch.Tensor | None = None) -> torch.Tensor:
+        r = torch.as_tensor(r, dtype=torch.float64)
+        r = r.contiguous() if r.device.type == "cpu" else self._dev(r)
+        if out is None:
+            out = torch.empty_like(r)
+        with torch.cuda.device(self.device):
+            _check(load().bmg_vcycle(self._h, _ptr(r), _ptr(out)), "bmg_vcycle")
+        return out
+
+    def solve(self, b, x0=None, tol: float = 1e-10, maxit: int = 500, out=None, raise_on_nonconv=True):
+        """x such that ||b - A x|| <= tol ||b||.  b (and out) may live on the
+        host or the device; the result has b's device."""
+        b = torch.as_tensor(b, dtype=torch.float64)
+        b = b.contiguous() if b.device.type == "cpu" else self._dev(b)
+        if out is None:
+            out = torch.zeros_like(b) if x0 is None else torch.as_tensor(x0, dtype=torch.float64).to(b.device).clone()
+        elif x0 is not None:
+            out.copy_(torch.as_tensor(x0))
+        elif x0 is None:
+            out.zero_()
+        info = _Info()
+        with torch.cuda.device(self.device):
+            code = load().bmg_solve(self._h, _ptr(b), _ptr(out), float(tol), int(maxit), ctypes.byref(info))
+        if code not in (0, 8) or (code == 8 and raise_on_nonconv):
+            _check(code, "bmg_solve")
+        return out, SolveInfo(info.iterations, info.levels, info.relres, info.true_relres, info.rho,
+                              info.grid_complexity, info.operator_complexity, info.status)
+
+    def adjoint_grad(self, u, dLdu, tol: float = 1e-10, maxit: int = 500):
+        """(lambda, dL/dkappa per cell, info) for A lambda = dL/du."""
+        u = self._dev(torch.as_tensor(u))
+        g = self._dev(torch.as_tensor(dLdu))
+        lam = torch.zeros_like(g)
+        dk = torch.empty((self.n - 1,) * self.dim, dtype=torch.float64, device=self.device)
+        info = _Info()
+        with torch.cuda.device(self.device):
+            _check(load().bmg_adjoint_grad(self._h, _ptr(self._coords), _ptr(u), _ptr(g), _ptr(lam), _ptr(dk),
+                                           float(tol), int(maxit), ctypes.byref(info)), "bmg_adjoint_grad")
+        return lam, dk, SolveInfo(info.iterations, info.levels, info.relres, info.true_relres, info.rho,
+                                  info.grid_complexity, info.operator_complexity, info.status)
+
+    # ------------------------------------------------------------ exports
+    def stencil(self, level: int) -> torch.Tensor:
+        n = self.level_n(level)
+        out = torch.empty((n,) * self.dim + (3 ** self.dim,), dtype=torch.float64, device=self.device)
+        with torch.cuda.device(self.device):
+            _check(load().bmg_get_stencil(self._h, level, _ptr(out)), "bmg_get_stencil")
+        return out
+
+    def interp(self, level: int) -> torch.Tensor:
+        n = self.level_n(level)
+        out = torch.empty((n,) * self.dim + (2 ** self.dim,), dtype=torch.float64, device=self.device)
+        with torch.cuda.device(self.device):
+            _check(load().bmg_get_interp(self._h, level, _ptr(out)), "bmg_get_interp")
+        return out

@@ -1,0 +1,404 @@
+// api.cu -- the C ABI (include/bmg.h): context, workspace carving, the
+// setup/solve sequence of Sec. 2.2 ("Setup phase", "Solution phase") with a
+// preconditioned-CG outer loop, host/device staging, diagnostics.
+#include <math.h>
+#include <string.h>
+
+#include <new>
+
+#include "common.cuh"
+
+using namespace bmg;
+
+struct bmg_ctx {
+    Ctx c;
+};
+
+namespace {
+
+long long ipow(long long b, int e) {
+    long long r = 1;
+    while (e-- > 0) r *= b;
+    return r;
+}
+
+size_t align256(size_t v) { return (v + 255) & ~(size_t)255; }
+
+bool is_device_ptr(const void* p) {
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+// Walks the workspace layout; with base == nullptr it only measures.
+size_t carve(Ctx& c, char* base) {
+    size_t off = 0;
+    auto take = [&](size_t bytes) -> char* {
+        off = align256(off);
+        char* p = base ? base + off : nullptr;
+        off += bytes;
+        return p;
+    };
+    const bool f32 = c.opts.precision == BMG_PREC_FP32;
+    const size_t vt = f32 ? sizeof(float) : sizeof(double);
+    for (int l = 0; l < c.nlev; l++) {
+        Level& L = c.lev[l];
+        L.A64 = (double*)take(sizeof(double) * c.ns * L.plane);
+        L.A32 = f32 ? (float*)take(sizeof(float) * c.ns * L.plane) : nullptr;
+        if (l < c.nlev - 1) {
+            const Level& K = c.lev[l + 1];
+            L.P64 = (double*)take(sizeof(double) * c.np * K.plane);
+            L.P32 = f32 ? (float*)take(sizeof(float) * c.np * K.plane) : nullptr;
+        } else {
+            L.P64 = nullptr;
+            L.P32 = nullptr;
+        }
+        const bool need_bx = l > 0 || f32;
+        L.b = need_bx ? take(vt * L.plane) : nullptr;
+        L.x = need_bx ? take(vt * L.plane) : nullptr;
+        L.r = take(vt * L.plane);
+    }
+    const long long pl0 = c.lev[0].plane;
+    c.bvec = (double*)take(sizeof(double) * pl0);
+    c.x = (double*)take(sizeof(double) * pl0);
+    c.r = (double*)take(sizeof(double) * pl0);
+    c.z[0] = (double*)take(sizeof(double) * pl0);
+    c.z[1] = (double*)take(sizeof(double) * pl0);
+    c.p = (double*)take(sizeof(double) * pl0);
+    c.q = (double*)take(sizeof(double) * pl0);
+    const long long nn = ipow(c.lev[0].n, c.dim);
+    c.stage_in = (double*)take(sizeof(double) * nn);
+    c.stage_out = (double*)take(sizeof(double) * nn);
+    c.partials = (double*)take(sizeof(double) * kMaxBlocks);
+    c.st = (KState*)take(sizeof(KState));
+    return align256(off);
+}
+
+bmg_status read_state(Ctx& c, KState& h) {
+    BMG_CUDA(cudaMemcpyAsync(&h, c.st, sizeof(KState), cudaMemcpyDeviceToHost, c.stream));
+    BMG_CUDA(cudaStreamSynchronize(c.stream));
+    return BMG_OK;
+}
+
+bmg_status reset_state(Ctx& c) {
+    KState z;
+    memset(&z, 0, sizeof(z));
+    BMG_CUDA(cudaMemcpyAsync(c.st, &z, sizeof(KState), cudaMemcpyHostToDevice, c.stream));
+    BMG_CUDA(cudaStreamSynchronize(c.stream));
+    return BMG_OK;
+}
+
+bmg_status check_ready(const bmg_ctx* ctx) {
+    if (!ctx) return BMG_ERR_ARG;
+    if (!ctx->c.attached) return BMG_ERR_WORKSPACE;
+    return BMG_OK;
+}
+
+// Copies an n^d array from the caller (host or device) into the padded dst.
+bmg_status stage_in(Ctx& c, const double* src, double* dst) {
+    const long long nn = ipow(c.lev[0].n, c.dim);
+    const double* dsrc = src;
+    if (!is_device_ptr(src)) {
+        BMG_CUDA(cudaMemcpyAsync(c.stage_in, src, sizeof(double) * nn, cudaMemcpyHostToDevice, c.stream));
+        dsrc = c.stage_in;
+    }
+    return k_pack(c, dsrc, dst);
+}
+
+bmg_status stage_out(Ctx& c, const double* src, double* dst) {
+    const long long nn = ipow(c.lev[0].n, c.dim);
+    if (is_device_ptr(dst)) return k_unpack(c, src, dst);
+    BMG_TRY(k_unpack(c, src, c.stage_out));
+    BMG_CUDA(cudaMemcpyAsync(dst, c.stage_out, sizeof(double) * nn, cudaMemcpyDeviceToHost, c.stream));
+    return BMG_OK;
+}
+
+void fill_complexity(const Ctx& c, bmg_info* info) {
+    double n0 = (double)ipow(c.lev[0].n - 2, c.dim), s = 0.0;
+    for (int l = 0; l < c.nlev; l++) s += (double)ipow(c.lev[l].n - 2, c.dim);
+    info->levels = c.nlev;
+    info->grid_complexity = s / n0;
+    info->operator_complexity = s / n0;   // same stored entries per node on every level
+}
+
+// PCG with M = one V-cycle.  x (padded, in c.x) holds the initial guess.
+bmg_status pcg(Ctx& c, double tol, int maxit, bmg_info* info) {
+    const bool flexible = c.opts.outer == BMG_OUTER_FLEXIBLE_CG;
+    BMG_TRY(reset_state(c));
+    KState h;
+    BMG_TRY(k_dot(c, c.bvec, c.bvec, &c.st->bb));
+    BMG_TRY(k_residual(c, c.bvec, c.x, c.r));
+    {   // the first iteration takes p = z
+        int first = 1;
+        BMG_CUDA(cudaMemcpyAsync(&c.st->first, &first, sizeof(int), cudaMemcpyHostToDevice, c.stream));
+    }
+    BMG_TRY(read_state(c, h));
+    const double bb = h.bb;
+    double rr = h.rr;
+    const double rr0 = rr;
+    int it = 0;
+    bmg_status status = BMG_OK;
+    if (bb == 0.0) {
+        BMG_CUDA(cudaMemsetAsync(c.x, 0, sizeof(double) * c.lev[0].plane, c.stream));
+        rr = 0.0;
+    } else {
+        const double lim = tol > 0 ? tol * tol * bb : -1.0;
+        bool done = rr <= lim;
+        while (!done && it < maxit) {
+            double* zn = c.z[it & 1];
+            double* zo = c.z[(it + 1) & 1];
+            BMG_TRY(vcycle(c, c.r, zn));
+            BMG_TRY(k_rz_beta(c, zn, zo, flexible));
+            BMG_TRY(k_p_update(c, zn));
+            BMG_TRY(k_spmv_pq(c, c.p, c.q));
+            BMG_TRY(k_update_xr(c));
+            it++;
+            BMG_TRY(read_state(c, h));
+            if (h.err) {
+                status = (bmg_status)h.err;
+                break;
+            }
+            rr = h.rr;
+            if (rr <= lim) {
+                BMG_TRY(k_residual(c, c.bvec, c.x, c.r));   // true residual replaces r
+                BMG_TRY(read_state(c, h));
+                rr = h.rr;
+                done = rr <= lim;
+            }
+        }
+        if (status == BMG_OK && tol > 0 && !done) status = BMG_ERR_NOT_CONVERGED;
+    }
+    if (info) {
+        info->iterations = it;
+        info->relres = bb > 0 ? sqrt(rr / bb) : 0.0;
+        info->rho = (it > 0 && rr0 > 0 && rr > 0) ? pow(rr / rr0, 0.5 / it) : 0.0;
+        // true residual of the final iterate, into q (scratch)
+        BMG_TRY(k_residual(c, c.bvec, c.x, c.q));
+        BMG_TRY(read_state(c, h));
+        info->true_relres = bb > 0 ? sqrt(h.rr / bb) : 0.0;
+        fill_complexity(c, info);
+        info->status = status;
+    }
+    return status;
+}
+
+}  // namespace
+
+extern "C" {
+
+void bmg_default_opts(bmg_opts* o) {
+    if (!o) return;
+    o->dim = 2;
+    o->n = 65;
+    o->precision = BMG_PREC_FP64;
+    o->outer = BMG_OUTER_CG;
+    o->flags = 0;
+}
+
+bmg_status bmg_create(const bmg_opts* opts, bmg_ctx** out) {
+    if (!out) return BMG_ERR_ARG;
+    *out = nullptr;
+    if (!opts) return BMG_ERR_ARG;
+    if (opts->dim != 2) return BMG_ERR_SHAPE;
+    const int n = opts->n;
+    if (n < 3 || ((n - 1) & (n - 2)) != 0) return BMG_ERR_SHAPE;
+    if (opts->precision != BMG_PREC_FP64 && opts->precision != BMG_PREC_FP32) return BMG_ERR_ARG;
+    if (opts->outer != BMG_OUTER_CG && opts->outer != BMG_OUTER_FLEXIBLE_CG) return BMG_ERR_ARG;
+    bmg_ctx* ctx = new (std::nothrow) bmg_ctx();
+    if (!ctx) return BMG_ERR_ARG;
+    Ctx& c = ctx->c;
+    c.opts = *opts;
+    c.dim = opts->dim;
+    c.ns = c.dim == 2 ? NS2 : NS3;
+    c.np = c.dim == 2 ? NP2 : NP3;
+    int nl = n, l = 0;
+    while (true) {
+        if (l >= kMaxLevels) {
+            delete ctx;
+            return BMG_ERR_SHAPE;
+        }
+        Level& L = c.lev[l];
+        L.n = nl;
+        L.ld = (nl + 31) & ~31;
+        L.plane = (long long)L.ld * ipow(nl, c.dim - 1);
+        l++;
+        if (nl == 3) break;
+        nl = (nl + 1) / 2;
+    }
+    c.nlev = l;
+    c.ws_need = carve(c, nullptr);
+    long long blocks = cdiv(c.lev[0].plane, kThreads * 4);
+    c.red_blocks = (int)(blocks < 1 ? 1 : (blocks > 152 * 8 ? 152 * 8 : blocks));
+    *out = ctx;
+    return BMG_OK;
+}
+
+bmg_status bmg_workspace_bytes(const bmg_ctx* ctx, size_t* bytes) {
+    if (!ctx || !bytes) return BMG_ERR_ARG;
+    *bytes = ctx->c.ws_need;
+    return BMG_OK;
+}
+
+bmg_status bmg_attach(bmg_ctx* ctx, void* ws, size_t bytes, void* stream) {
+    if (!ctx || !ws) return BMG_ERR_ARG;
+    Ctx& c = ctx->c;
+    if (((uintptr_t)ws & 255) != 0) return BMG_ERR_ARG;
+    if (bytes < c.ws_need) return BMG_ERR_WORKSPACE;
+    if (!is_device_ptr(ws)) return BMG_ERR_ARG;
+    BMG_CUDA(cudaGetDevice(&c.device));
+    c.stream = (cudaStream_t)stream;
+    c.ws = (char*)ws;
+    carve(c, c.ws);
+    BMG_CUDA(cudaMemsetAsync(c.ws, 0, c.ws_need, c.stream));
+    BMG_CUDA(cudaStreamSynchronize(c.stream));
+    c.attached = true;
+    c.have_op = c.have_setup = false;
+    return BMG_OK;
+}
+
+bmg_status bmg_assemble(bmg_ctx* ctx, const double* coords, const double* kappa) {
+    BMG_TRY(check_ready(ctx));
+    if (!coords || !kappa) return BMG_ERR_ARG;
+    Ctx& c = ctx->c;
+    if (!is_device_ptr(coords) || !is_device_ptr(kappa)) return BMG_ERR_ARG;
+    BMG_TRY(reset_state(c));
+    BMG_TRY(assemble2d(c, coords, kappa));
+    KState h;
+    BMG_TRY(read_state(c, h));
+    c.have_setup = false;
+    if (h.err) {
+        c.have_op = false;
+        return (bmg_status)h.err;
+    }
+    c.have_op = true;
+    return BMG_OK;
+}
+
+bmg_status bmg_set_stencil(bmg_ctx* ctx, const double* stencil) {
+    BMG_TRY(check_ready(ctx));
+    if (!stencil || !is_device_ptr(stencil)) return BMG_ERR_ARG;
+    Ctx& c = ctx->c;
+    BMG_TRY(set_stencil2d(c, stencil));
+    BMG_CUDA(cudaStreamSynchronize(c.stream));
+    c.have_op = true;
+    c.have_setup = false;
+    return BMG_OK;
+}
+
+bmg_status bmg_setup(bmg_ctx* ctx) {
+    BMG_TRY(check_ready(ctx));
+    Ctx& c = ctx->c;
+    if (!c.have_op) return BMG_ERR_STATE;
+    BMG_TRY(reset_state(c));
+    for (int l = 0; l < c.nlev - 1; l++) BMG_TRY(setup_level2d(c, l));
+    BMG_TRY(demote_levels(c));
+    KState h;
+    BMG_TRY(read_state(c, h));
+    if (h.err) {
+        c.have_setup = false;
+        return (bmg_status)h.err;
+    }
+    c.have_setup = true;
+    return BMG_OK;
+}
+
+bmg_status bmg_vcycle(bmg_ctx* ctx, const double* r, double* z) {
+    BMG_TRY(check_ready(ctx));
+    if (!r || !z) return BMG_ERR_ARG;
+    Ctx& c = ctx->c;
+    if (!c.have_setup) return BMG_ERR_STATE;
+    BMG_TRY(stage_in(c, r, c.r));
+    BMG_TRY(vcycle(c, c.r, c.z[0]));
+    BMG_TRY(stage_out(c, c.z[0], z));
+    BMG_CUDA(cudaStreamSynchronize(c.stream));
+    return BMG_OK;
+}
+
+bmg_status bmg_solve(bmg_ctx* ctx, const double* b, double* x, double tol, int maxit, bmg_info* info) {
+    BMG_TRY(check_ready(ctx));
+    if (!b || !x || maxit < 0) return BMG_ERR_ARG;
+    Ctx& c = ctx->c;
+    if (!c.have_setup) return BMG_ERR_STATE;
+    BMG_TRY(stage_in(c, b, c.bvec));
+    BMG_TRY(stage_in(c, x, c.x));
+    bmg_status st = pcg(c, tol, maxit, info);
+    if (st == BMG_ERR_DEVICE) return st;
+    BMG_TRY(stage_out(c, c.x, x));
+    BMG_CUDA(cudaStreamSynchronize(c.stream));
+    return st;
+}
+
+bmg_status bmg_adjoint_grad(bmg_ctx* ctx, const double* coords, const double* u, const double* dLdu,
+                            double* lambda, double* dLdkappa, double tol, int maxit, bmg_info* info) {
+    BMG_TRY(check_ready(ctx));
+    if (!coords || !u || !dLdu || !lambda || !dLdkappa) return BMG_ERR_ARG;
+    Ctx& c = ctx->c;
+    if (!c.have_setup) return BMG_ERR_STATE;
+    if (!is_device_ptr(coords) || !is_device_ptr(u) || !is_device_ptr(dLdu) || !is_device_ptr(lambda) ||
+        !is_device_ptr(dLdkappa))
+        return BMG_ERR_ARG;
+    BMG_TRY(stage_in(c, dLdu, c.bvec));
+    BMG_CUDA(cudaMemsetAsync(c.x, 0, sizeof(double) * c.lev[0].plane, c.stream));
+    bmg_status st = pcg(c, tol, maxit, info);
+    if (st == BMG_ERR_DEVICE) return st;
+    BMG_TRY(stage_out(c, c.x, lambda));
+    BMG_TRY(adjoint_cells2d(c, coords, u, lambda, dLdkappa));
+    KState h;
+    BMG_TRY(read_state(c, h));
+    if (h.err && st == BMG_OK) st = (bmg_status)h.err;
+    return st;
+}
+
+int bmg_levels(const bmg_ctx* ctx) { return ctx ? ctx->c.nlev : 0; }
+
+int bmg_level_n(const bmg_ctx* ctx, int level) {
+    if (!ctx || level < 0 || level >= ctx->c.nlev) return 0;
+    return ctx->c.lev[level].n;
+}
+
+bmg_status bmg_get_stencil(bmg_ctx* ctx, int level, double* out) {
+    BMG_TRY(check_ready(ctx));
+    Ctx& c = ctx->c;
+    if (!out || level < 0 || level >= c.nlev || !is_device_ptr(out)) return BMG_ERR_ARG;
+    if (level > 0 && !c.have_setup) return BMG_ERR_STATE;
+    if (level == 0 && !c.have_op) return BMG_ERR_STATE;
+    BMG_TRY(export_stencil2d(c, level, out));
+    BMG_CUDA(cudaStreamSynchronize(c.stream));
+    return BMG_OK;
+}
+
+bmg_status bmg_get_interp(bmg_ctx* ctx, int level, double* out) {
+    BMG_TRY(check_ready(ctx));
+    Ctx& c = ctx->c;
+    if (!out || level < 0 || level >= c.nlev - 1 || !is_device_ptr(out)) return BMG_ERR_ARG;
+    if (!c.have_setup) return BMG_ERR_STATE;
+    BMG_TRY(export_interp2d(c, level, out));
+    BMG_CUDA(cudaStreamSynchronize(c.stream));
+    return BMG_OK;
+}
+
+long long bmg_launch_count(const bmg_ctx* ctx) { return ctx ? ctx->c.launches : 0; }
+
+void bmg_destroy(bmg_ctx* ctx) { delete ctx; }
+
+const char* bmg_status_str(bmg_status s) {
+    switch (s) {
+        case BMG_OK: return "ok";
+        case BMG_ERR_ARG: return "invalid argument";
+        case BMG_ERR_SHAPE: return "unsupported shape (n must be 2^k+1, dim 2 or 3)";
+        case BMG_ERR_DEVICE: return "CUDA runtime error";
+        case BMG_ERR_WORKSPACE: return "workspace missing or too small";
+        case BMG_ERR_MAP_FOLDED: return "map folded: det J <= 0 at a quadrature point";
+        case BMG_ERR_SETUP_BREAKDOWN: return "setup breakdown: zero collapsed denominator or non-positive diagonal";
+        case BMG_ERR_NOT_SPD: return "CG breakdown: p^T A p <= 0";
+        case BMG_ERR_NOT_CONVERGED: return "not converged within maxit";
+        case BMG_ERR_TIMEOUT: return "bounded device wait expired";
+        case BMG_ERR_STATE: return "call out of order";
+    }
+    return "unknown status";
+}
+
+}  // extern "C"

@@ -1,0 +1,202 @@
+// common.cuh -- internal types and device helpers of libbmg.
+//
+// Internal layout.  Every level l of the hierarchy stores its grid
+// (n_l nodes per side) with a padded row length ld_l (a multiple of 32
+// elements, so every row starts on a 128-byte boundary in FP32 and a
+// 256-byte boundary in FP64); one "plane" holds ld_l * n_l^(d-1) values,
+// i fastest.  Padding and boundary entries are kept at zero in every array.
+//
+// Operators are stored as the symmetric half of the 9-point (2-D) or
+// 27-point (3-D) stencil, one plane per stored offset ("five stored values
+// per DoF", Sec. 4.1):
+//   2-D: C (0,0), W (-1,0), S (0,-1), SW (-1,-1), NW (-1,+1);
+//        a(+d) at node i is a(-d) stored at node i+d.
+//   3-D: C and the 13 offsets that are lexicographically negative
+//        (dz<0, or dz==0 and dy<0, or dz==dy==0 and dx<0).
+// Interpolation P_l (level l+1 -> level l) is stored on the coarse grid,
+// one plane per weight of the fine points owned by coarse node (I,J[,K])
+// (the fine points 2I+{0,1}, 2J+{0,1}[, 2K+{0,1}] other than the C point):
+//   2-D: PXL PXR  (2I+1,2J)   -> (I,J), (I+1,J)
+//        PYS PYN  (2I,2J+1)   -> (I,J), (I,J+1)
+//        PSW PSE PNW PNE (2I+1,2J+1) -> (I,J), (I+1,J), (I,J+1), (I+1,J+1)
+//   3-D: 26 planes, see setup3d.cu.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/bmg.h"
+
+namespace bmg {
+
+constexpr int kMaxLevels = 20;
+constexpr int kThreads = 256;
+constexpr int kMaxBlocks = 2048;       // partials buffer size for reductions
+
+enum Plane2 { C2 = 0, W2 = 1, S2 = 2, SW2 = 3, NW2 = 4, NS2 = 5 };
+enum PPlane2 { PXL = 0, PXR = 1, PYS = 2, PYN = 3, PSW = 4, PSE = 5, PNW = 6, PNE = 7, NP2 = 8 };
+constexpr int NS3 = 14;
+constexpr int NP3 = 26;
+
+// Device error word values mirror bmg_status.
+struct KState {
+    double bb;        // ||b||^2
+    double rr;        // ||r||^2 (last reduction)
+    double rz;        // r.z of the previous iteration
+    double rzn;       // r.z of this iteration
+    double rzo;       // r.z_old (flexible CG)
+    double pq;        // p.Aq
+    double alpha, beta;
+    double dot;       // scratch result of a plain dot product
+    int err;          // first device error (bmg_status), 0 = none
+    int first;        // 1 on the first iteration (p = z, no beta)
+    unsigned int counter[8];
+};
+
+struct Level {
+    int n = 0;            // nodes per side
+    int ld = 0;           // padded row length
+    long long plane = 0;  // elements per plane
+    double* A64 = nullptr;
+    float* A32 = nullptr;
+    double* P64 = nullptr;    // interpolation from level+1 (planes on level+1's grid)
+    float* P32 = nullptr;
+    void* b = nullptr;        // V-cycle right-hand side (V-cycle precision)
+    void* x = nullptr;        // V-cycle iterate
+    void* r = nullptr;        // residual scratch
+};
+
+struct Ctx {
+    bmg_opts opts{};
+    int dim = 2;
+    int nlev = 0;
+    int ns = 5, np = 8;       // stored stencil / interpolation planes
+    Level lev[kMaxLevels];
+    size_t ws_need = 0;
+    char* ws = nullptr;
+    cudaStream_t stream = nullptr;
+    int device = -1;
+    bool attached = false, have_op = false, have_setup = false;
+    // finest-level FP64 Krylov vectors (internal padded layout)
+    double *bvec = nullptr, *x = nullptr, *r = nullptr, *z[2] = {nullptr, nullptr};
+    double *p = nullptr, *q = nullptr;
+    double *stage_in = nullptr, *stage_out = nullptr;   // n^d doubles each, host staging
+    double* partials = nullptr;
+    KState* st = nullptr;         // device
+    KState* st_host = nullptr;    // pinned mirror
+    long long launches = 0;
+    int red_blocks = 0;           // fixed grid of the reducing kernels (deterministic)
+};
+
+// ------------------------------------------------------------------ helpers
+#define BMG_CUDA(call)                                                      \
+    do {                                                                    \
+        cudaError_t e_ = (call);                                            \
+        if (e_ != cudaSuccess) return BMG_ERR_DEVICE;                       \
+    } while (0)
+
+#define BMG_TRY(call)                                                       \
+    do {                                                                    \
+        bmg_status s_ = (call);                                             \
+        if (s_ != BMG_OK) return s_;                                        \
+    } while (0)
+
+inline int cdiv(long long a, long long b) { return (int)((a + b - 1) / b); }
+
+__device__ __forceinline__ void set_err(KState* st, int code) {
+    atomicCAS(&st->err, 0, code);
+}
+
+// Symmetric-half 2-D stencil view.  a(i,j; dx,dy) for |dx|,|dy| <= 1.
+template <typename T>
+struct Sten2 {
+    const T* a;
+    int ld;
+    long long pl;
+    __device__ __forceinline__ T at(int p, int i, int j) const {
+        return a[(long long)p * pl + (long long)j * ld + i];
+    }
+    __device__ __forceinline__ T c(int i, int j) const { return at(C2, i, j); }
+    __device__ __forceinline__ T full(int i, int j, int dx, int dy) const {
+        if (dx == 0 && dy == 0) return at(C2, i, j);
+        if (dy == 0) return dx < 0 ? at(W2, i, j) : at(W2, i + 1, j);
+        if (dx == 0) return dy < 0 ? at(S2, i, j) : at(S2, i, j + 1);
+        if (dx < 0 && dy < 0) return at(SW2, i, j);
+        if (dx > 0 && dy > 0) return at(SW2, i + 1, j + 1);
+        if (dx < 0 && dy > 0) return at(NW2, i, j);
+        return at(NW2, i + 1, j - 1);   // dx > 0, dy < 0
+    }
+};
+
+// Block-wide sum (blockDim.x == kThreads), result valid in thread 0.
+__device__ __forceinline__ double block_sum(double v) {
+    __shared__ double sh[kThreads / 32];
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+    __syncthreads();
+    if (l == 0) sh[w] = v;
+    __syncthreads();
+    double s = 0.0;
+    if (w == 0) {
+        s = l < kThreads / 32 ? sh[l] : 0.0;
+        for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+    }
+    return s;
+}
+
+// Deterministic grid reduction: each block stores its partial; the last
+// block to arrive sums the partials in a fixed order.  Returns true (in
+// thread 0 of the last block only) with the total in *total.
+__device__ __forceinline__ bool grid_sum(double v, double* partials, unsigned int* counter,
+                                         double* total) {
+    __shared__ bool last;
+    double b = block_sum(v);
+    if (threadIdx.x == 0) {
+        partials[blockIdx.x] = b;
+        __threadfence();
+        unsigned int t = atomicAdd(counter, 1u);
+        last = (t == gridDim.x - 1);
+    }
+    __syncthreads();
+    if (!last) return false;
+    __threadfence();
+    double s = 0.0;
+    for (int k = threadIdx.x; k < (int)gridDim.x; k += blockDim.x) s += ((volatile double*)partials)[k];
+    s = block_sum(s);
+    if (threadIdx.x == 0) {
+        *counter = 0u;
+        *total = s;
+        return true;
+    }
+    return false;
+}
+
+// ------------------------------------------------------------------ host launchers
+// setup2d.cu
+bmg_status assemble2d(Ctx& c, const double* coords, const double* kappa);
+bmg_status set_stencil2d(Ctx& c, const double* full);
+bmg_status setup_level2d(Ctx& c, int l);
+bmg_status export_stencil2d(Ctx& c, int l, double* out);
+bmg_status export_interp2d(Ctx& c, int l, double* out);
+bmg_status adjoint_cells2d(Ctx& c, const double* coords, const double* u, const double* lam, double* g);
+// setup3d.cu
+bmg_status assemble3d(Ctx& c, const double* coords, const double* kappa);
+bmg_status set_stencil3d(Ctx& c, const double* full);
+bmg_status setup_level3d(Ctx& c, int l);
+bmg_status export_stencil3d(Ctx& c, int l, double* out);
+bmg_status export_interp3d(Ctx& c, int l, double* out);
+bmg_status adjoint_cells3d(Ctx& c, const double* coords, const double* u, const double* lam, double* g);
+// vcycle.cu: z = M r on the finest level (FP64 in/out, internal layout)
+bmg_status vcycle(Ctx& c, const double* r, double* z);
+bmg_status demote_levels(Ctx& c);
+// krylov.cu
+bmg_status k_pack(Ctx& c, const double* src, double* dst);      // n^d -> padded, boundary zeroed
+bmg_status k_unpack(Ctx& c, const double* src, double* dst);    // padded -> n^d
+bmg_status k_residual(Ctx& c, const double* b, const double* x, double* r);  // r = b - A x; st.rr
+bmg_status k_dot(Ctx& c, const double* a, const double* b, double* slot);    // *slot (device) = a.b
+bmg_status k_spmv_pq(Ctx& c, const double* p, double* q);        // q = A p; alpha = rz / p.q
+bmg_status k_update_xr(Ctx& c);                                   // x += alpha p; r -= alpha q; rr
+bmg_status k_rz_beta(Ctx& c, const double* z, const double* zold, bool flexible);
+bmg_status k_p_update(Ctx& c, const double* z);                   // p = z + beta p (or z)
+
+}  // namespace bmg

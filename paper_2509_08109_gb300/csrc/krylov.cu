@@ -1,0 +1,212 @@
+// krylov.cu -- FP64 vector kernels of the preconditioned conjugate-gradient
+// outer loop: operator application fused with its dot product, fused
+// x/r updates with ||r||^2, r.z with the CG coefficient, p update, layout
+// packing.  All reductions are deterministic: per-block partials summed in
+// a fixed order by the last block (see grid_sum); scalars stay on the
+// device in KState.
+#include "common.cuh"
+
+namespace bmg {
+namespace {
+
+__device__ __forceinline__ double apply_row2d(const double* __restrict__ A, long long pl, int ld,
+                                              const double* __restrict__ x, long long o) {
+    double s = A[C2 * pl + o] * x[o];
+    s += A[W2 * pl + o] * x[o - 1];
+    s += A[W2 * pl + o + 1] * x[o + 1];
+    s += A[S2 * pl + o] * x[o - ld];
+    s += A[S2 * pl + o + ld] * x[o + ld];
+    s += A[SW2 * pl + o] * x[o - ld - 1];
+    s += A[SW2 * pl + o + ld + 1] * x[o + ld + 1];
+    s += A[NW2 * pl + o] * x[o + ld - 1];
+    s += A[NW2 * pl + o - ld + 1] * x[o - ld + 1];
+    return s;
+}
+
+// grid-stride over the padded layout; interior test per element
+struct Grid2 {
+    int n, ld;
+    __device__ __forceinline__ bool interior(long long k, int& i, int& j) const {
+        j = (int)(k / ld);
+        i = (int)(k - (long long)j * ld);
+        return i >= 1 && j >= 1 && i <= n - 2 && j <= n - 2;
+    }
+};
+
+__global__ void k_pack2d(int n, int ld, const double* __restrict__ src, double* __restrict__ dst) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    const int j = blockIdx.y;
+    if (i >= ld) return;
+    const bool in = i >= 1 && j >= 1 && i <= n - 2 && j <= n - 2;
+    dst[(long long)j * ld + i] = in ? src[(long long)j * n + i] : 0.0;
+}
+
+__global__ void k_unpack2d(int n, int ld, const double* __restrict__ src, double* __restrict__ dst) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    const int j = blockIdx.y;
+    if (i >= n) return;
+    dst[(long long)j * n + i] = src[(long long)j * ld + i];
+}
+
+// r = b - A x ; st.rr = ||r||^2
+__global__ void k_residual64(Grid2 g, const double* __restrict__ A, long long pl, const double* __restrict__ b,
+                             const double* __restrict__ x, double* __restrict__ r, double* partials, KState* st) {
+    double acc = 0.0;
+    const long long tot = pl;
+    for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < tot;
+         k += (long long)gridDim.x * blockDim.x) {
+        int i, j;
+        double v = 0.0;
+        if (g.interior(k, i, j)) v = b[k] - apply_row2d(A, pl, g.ld, x, k);
+        r[k] = v;
+        acc += v * v;
+    }
+    double t;
+    if (grid_sum(acc, partials, &st->counter[0], &t)) st->rr = t;
+}
+
+__global__ void k_dot64(long long tot, const double* __restrict__ a, const double* __restrict__ b, double* partials,
+                        KState* st, double* slot) {
+    double acc = 0.0;
+    for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < tot;
+         k += (long long)gridDim.x * blockDim.x)
+        acc += a[k] * b[k];
+    double t;
+    if (grid_sum(acc, partials, &st->counter[1], &t)) *slot = t;
+}
+
+// q = A p; st.pq = p.q; alpha = rz / pq
+__global__ void k_spmv_pq(Grid2 g, const double* __restrict__ A, long long pl, const double* __restrict__ p,
+                          double* __restrict__ q, double* partials, KState* st) {
+    double acc = 0.0;
+    for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < pl;
+         k += (long long)gridDim.x * blockDim.x) {
+        int i, j;
+        double v = 0.0;
+        if (g.interior(k, i, j)) v = apply_row2d(A, pl, g.ld, p, k);
+        q[k] = v;
+        acc += p[k] * v;
+    }
+    double t;
+    if (grid_sum(acc, partials, &st->counter[2], &t)) {
+        st->pq = t;
+        if (!(t > 0.0)) {
+            set_err(st, BMG_ERR_NOT_SPD);
+            st->alpha = 0.0;
+        } else {
+            st->alpha = st->rz / t;
+        }
+    }
+}
+
+// x += alpha p; r -= alpha q; st.rr = ||r||^2
+__global__ void k_update_xr(long long tot, double* __restrict__ x, double* __restrict__ r,
+                            const double* __restrict__ p, const double* __restrict__ q, double* partials, KState* st) {
+    const double alpha = st->alpha;
+    double acc = 0.0;
+    for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < tot;
+         k += (long long)gridDim.x * blockDim.x) {
+        x[k] += alpha * p[k];
+        const double rv = r[k] - alpha * q[k];
+        r[k] = rv;
+        acc += rv * rv;
+    }
+    double t;
+    if (grid_sum(acc, partials, &st->counter[3], &t)) st->rr = t;
+}
+
+// beta from r.z (and r.z_old for flexible CG); the first iteration has no beta.
+__global__ void k_beta(int flexible, KState* st) {
+    if (threadIdx.x != 0) return;
+    if (st->first) {
+        st->beta = 0.0;
+        st->first = 0;
+    } else {
+        const double num = flexible ? st->rzn - st->rzo : st->rzn;
+        st->beta = num / st->rz;
+    }
+    st->rz = st->rzn;
+}
+
+// p = z + beta p
+__global__ void k_p_update(long long tot, const double* __restrict__ z, double* __restrict__ p, KState* st) {
+    const double beta = st->beta;
+    for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < tot;
+         k += (long long)gridDim.x * blockDim.x)
+        p[k] = z[k] + beta * p[k];
+}
+
+}  // namespace
+
+bmg_status k_pack(Ctx& c, const double* src, double* dst) {
+    const Level& L = c.lev[0];
+    k_pack2d<<<dim3(cdiv(L.ld, 128), L.n), 128, 0, c.stream>>>(L.n, L.ld, src, dst);
+    c.launches++;
+    BMG_CUDA(cudaGetLastError());
+    return BMG_OK;
+}
+
+bmg_status k_unpack(Ctx& c, const double* src, double* dst) {
+    const Level& L = c.lev[0];
+    k_unpack2d<<<dim3(cdiv(L.n, 128), L.n), 128, 0, c.stream>>>(L.n, L.ld, src, dst);
+    c.launches++;
+    BMG_CUDA(cudaGetLastError());
+    return BMG_OK;
+}
+
+bmg_status k_residual(Ctx& c, const double* b, const double* x, double* r) {
+    const Level& L = c.lev[0];
+    k_residual64<<<c.red_blocks, kThreads, 0, c.stream>>>(Grid2{L.n, L.ld}, L.A64, L.plane, b, x, r, c.partials,
+                                                           c.st);
+    c.launches++;
+    BMG_CUDA(cudaGetLastError());
+    return BMG_OK;
+}
+
+bmg_status k_dot(Ctx& c, const double* a, const double* b, double* slot) {
+    const Level& L = c.lev[0];
+    k_dot64<<<c.red_blocks, kThreads, 0, c.stream>>>(L.plane, a, b, c.partials, c.st, slot);
+    c.launches++;
+    BMG_CUDA(cudaGetLastError());
+    return BMG_OK;
+}
+
+bmg_status k_spmv_pq(Ctx& c, const double* p, double* q) {
+    const Level& L = c.lev[0];
+    k_spmv_pq<<<c.red_blocks, kThreads, 0, c.stream>>>(Grid2{L.n, L.ld}, L.A64, L.plane, p, q, c.partials, c.st);
+    c.launches++;
+    BMG_CUDA(cudaGetLastError());
+    return BMG_OK;
+}
+
+bmg_status k_update_xr(Ctx& c) {
+    const Level& L = c.lev[0];
+    k_update_xr<<<c.red_blocks, kThreads, 0, c.stream>>>(L.plane, c.x, c.r, c.p, c.q, c.partials, c.st);
+    c.launches++;
+    BMG_CUDA(cudaGetLastError());
+    return BMG_OK;
+}
+
+bmg_status k_rz_beta(Ctx& c, const double* z, const double* zold, bool flexible) {
+    const Level& L = c.lev[0];
+    k_dot64<<<c.red_blocks, kThreads, 0, c.stream>>>(L.plane, c.r, z, c.partials, c.st, &c.st->rzn);
+    c.launches++;
+    if (flexible) {
+        k_dot64<<<c.red_blocks, kThreads, 0, c.stream>>>(L.plane, c.r, zold, c.partials, c.st, &c.st->rzo);
+        c.launches++;
+    }
+    k_beta<<<1, 32, 0, c.stream>>>(flexible ? 1 : 0, c.st);
+    c.launches++;
+    BMG_CUDA(cudaGetLastError());
+    return BMG_OK;
+}
+
+bmg_status k_p_update(Ctx& c, const double* z) {
+    const Level& L = c.lev[0];
+    k_p_update<<<c.red_blocks, kThreads, 0, c.stream>>>(L.plane, z, c.p, c.st);
+    c.launches++;
+    BMG_CUDA(cudaGetLastError());
+    return BMG_OK;
+}
+
+}  // namespace bmg

@@ -105,8 +105,11 @@ class GaussianField:
         phase = rng.uniform(0.0, 2.0 * math.pi, size=modes)
         return cls(omega, phase, sigma)
 
-    def __call__(self, pts: np.ndarray, chunk: int = 1 << 22) -> np.ndarray:
-        """pts shape (d, ...) -> g shape (...)."""
+    def __call__(self, pts, chunk: int = 1 << 22):
+        """pts shape (d, ...) -> g shape (...).  pts may be a numpy array or a
+        torch tensor (evaluated on the tensor's device, FP64)."""
+        if not isinstance(pts, np.ndarray):
+            return self._torch(pts, chunk)
         d = pts.shape[0]
         flat = pts.reshape(d, -1)
         out = np.empty(flat.shape[1])
@@ -116,6 +119,19 @@ class GaussianField:
             blk = flat[:, s0:s0 + chunk]
             arg = self.omega @ blk + self.phase[:, None]
             out[s0:s0 + chunk] = scale * np.cos(arg).sum(axis=0)
+        return out.reshape(pts.shape[1:])
+
+    def _torch(self, pts, chunk: int):
+        import torch
+        d = pts.shape[0]
+        flat = pts.reshape(d, -1).to(torch.float64)
+        om = torch.as_tensor(self.omega, dtype=torch.float64, device=flat.device)
+        ph = torch.as_tensor(self.phase, dtype=torch.float64, device=flat.device)
+        scale = self.sigma * math.sqrt(2.0 / om.shape[0])
+        out = torch.empty(flat.shape[1], dtype=torch.float64, device=flat.device)
+        for s0 in range(0, flat.shape[1], chunk):
+            arg = om @ flat[:, s0:s0 + chunk] + ph[:, None]
+            out[s0:s0 + chunk] = scale * torch.cos(arg).sum(dim=0)
         return out.reshape(pts.shape[1:])
 
 
@@ -171,6 +187,21 @@ def annulus_lognormal(n: int = 4097, seed: int = 1) -> Problem:
     kappa = np.exp(gf(cell_centroids(coords)))
     f = rhs_uniform(rng, (n, n))
     return Problem(f"annulus_lognormal_n{n}", 2, n, coords, kappa, f, {"field": gf})
+
+
+def annulus_lognormal_device(n: int, device, seed: int = 1):
+    """The annulus_lognormal workload with the field evaluated by torch on
+    `device` (same draws and formula; the cosine sums may differ from the
+    numpy evaluation in the last bits).  Returns (coords, kappa, f) as FP64
+    tensors on the device."""
+    import torch
+    rng = np.random.default_rng(seed)
+    coords = torch.as_tensor(coords_quarter_annulus(n), device=device)
+    gf = GaussianField.draw(rng, 2)
+    cen = 0.25 * (coords[:, :-1, :-1] + coords[:, :-1, 1:] + coords[:, 1:, :-1] + coords[:, 1:, 1:])
+    kappa = torch.exp(gf(cen)).contiguous()
+    f = torch.as_tensor(rhs_uniform(rng, (n, n)), device=device)
+    return coords.contiguous(), kappa, f
 
 
 def shell_two_layer(n: int = 257, seed: int = 2) -> Problem:

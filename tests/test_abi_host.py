@@ -1,0 +1,84 @@
+"""Host-side checks of the C ABI: the library builds for sm_103a, loads, and
+exports every function include/bmg.h declares; the host-only calls validate
+their arguments.  No GPU needed (no call here touches the device)."""
+import ctypes
+import os
+import re
+
+import pytest
+
+from paper_2509_08109_gb300 import binding, build
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    build.build()
+    return binding.load()
+
+
+def _declared():
+    names = set()
+    for h in os.listdir(os.path.join(ROOT, "include")):
+        if not h.endswith(".h"):
+            continue
+        txt = open(os.path.join(ROOT, "include", h)).read()
+        txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
+        names |= set(re.findall(r"\b(bmg_[a-z0-9_]+)\s*\(", txt))
+    return sorted(names)
+
+
+def test_every_declared_symbol_is_exported(lib):
+    names = _declared()
+    assert "bmg_solve" in names and "bmg_adjoint_grad" in names
+    for name in names:
+        assert hasattr(lib, name), name
+    assert set(binding.exported_symbols()) <= set(names)
+
+
+def test_build_targets_sm103a_only():
+    assert build.ARCH == ["-gencode", "arch=compute_103a,code=sm_103a"]
+
+
+@pytest.mark.parametrize("n,dim,code", [(65, 2, 0), (4097, 2, 0), (64, 2, 2), (2, 2, 2), (3, 2, 0), (65, 4, 2)])
+def test_create_validates_shape(lib, n, dim, code):
+    opts = binding._Opts(dim, n, 0, 0, 0)
+    h = ctypes.c_void_p()
+    rc = lib.bmg_create(ctypes.byref(opts), ctypes.byref(h))
+    assert rc == code
+    if rc == 0:
+        nb = ctypes.c_size_t()
+        assert lib.bmg_workspace_bytes(h, ctypes.byref(nb)) == 0
+        assert nb.value > 0
+        levels = lib.bmg_levels(h)
+        sizes = [lib.bmg_level_n(h, l) for l in range(levels)]
+        assert sizes[0] == n and sizes[-1] == 3
+        assert all(2 * sizes[l + 1] - 1 == sizes[l] for l in range(levels - 1))
+        lib.bmg_destroy(h)
+    else:
+        assert not h.value
+
+
+def test_workspace_fp32_larger_than_fp64(lib):
+    sizes = {}
+    for prec in (0, 1):
+        opts = binding._Opts(2, 1025, prec, 0, 0)
+        h = ctypes.c_void_p()
+        assert lib.bmg_create(ctypes.byref(opts), ctypes.byref(h)) == 0
+        nb = ctypes.c_size_t()
+        lib.bmg_workspace_bytes(h, ctypes.byref(nb))
+        sizes[prec] = nb.value
+        lib.bmg_destroy(h)
+    assert sizes[1] > sizes[0]
+
+
+def test_calls_before_attach_are_rejected(lib):
+    opts = binding._Opts(2, 17, 0, 0, 0)
+    h = ctypes.c_void_p()
+    assert lib.bmg_create(ctypes.byref(opts), ctypes.byref(h)) == 0
+    assert lib.bmg_setup(h) == 4            # no workspace
+    assert lib.bmg_solve(h, None, None, ctypes.c_double(1e-10), 10, None) == 4
+    assert lib.bmg_create(None, ctypes.byref(h)) == 1
+    assert lib.bmg_status_str(6).decode().startswith("setup breakdown")
+    lib.bmg_destroy(h)

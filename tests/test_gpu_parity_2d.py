@@ -1,0 +1,178 @@
+"""2-D parity of the CUDA path (through the C ABI) against the oracle.
+
+Tolerances (FP64): stencils 1e-13 relative to the row diagonal; P_l and A_l
+1e-12; one V-cycle 1e-12; PCG at a fixed iteration count 1e-9 in the
+solution; free-running true relative residual <= 1e-10 with the oracle's
+iteration count +-1; adjoint gradient 1e-8 relative.  These are the
+bounds derived from FP64 rounding (a few hundred ulps through the
+hierarchy, amplified by the iteration's conditioning)."""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_2509_08109_gb300 import binding, inputs
+from tests.gpu_util import rel_to_diag, relerr, solver_for
+
+pytestmark = pytest.mark.gpu
+
+SIZES = [5, 9, 17, 65, 257]
+
+
+def _problem(n, kind="lognormal"):
+    if kind == "lognormal":
+        return inputs.annulus_lognormal(n)
+    if kind == "plain":
+        return inputs.annulus_plain(n)
+    if kind == "bump":
+        p = inputs.annulus_lognormal(n)
+        p.coords = inputs.coords_bump(n, 0.13, -0.11)
+        return p
+    return inputs.identity_coefficient(n, kind)
+
+
+@pytest.mark.parametrize("n", SIZES)
+def test_assembly_matches_oracle(n):
+    p = _problem(n)
+    s = binding.Solver(2, n).assemble(torch.as_tensor(p.coords), torch.as_tensor(p.kappa))
+    ref = oracle.assemble(p.coords, p.kappa)
+    got = s.stencil(0).cpu().numpy()
+    assert rel_to_diag(got, ref) <= 1e-13
+
+
+@pytest.mark.parametrize("n,kind", [(9, "lognormal"), (17, "bump"), (65, "lognormal"), (129, "checkerboard"),
+                                    (257, "thin_layer")])
+def test_hierarchy_matches_oracle(n, kind):
+    p = _problem(n, kind)
+    s = solver_for(p)
+    H = oracle.Hierarchy(oracle.assemble(p.coords, p.kappa))
+    assert s.levels == H.nlev
+    for l in range(H.nlev):
+        Ag = s.stencil(l).cpu().numpy()
+        Ao = H.A(l)
+        assert rel_to_diag(Ag, Ao) <= 1e-12, l
+        if l < H.nlev - 1:
+            Pg = s.interp(l).cpu().numpy()
+            assert np.abs(Pg - H.P(l)).max() <= 1e-12, l
+
+
+def test_set_stencil_gives_same_hierarchy():
+    n = 33
+    p = _problem(n, "bump")
+    A = oracle.assemble(p.coords, p.kappa)
+    s = binding.Solver(2, n).set_stencil(torch.as_tensor(A)).setup()
+    H = oracle.Hierarchy(A)
+    for l in range(H.nlev):
+        assert rel_to_diag(s.stencil(l).cpu().numpy(), H.A(l)) <= 1e-12
+
+
+@pytest.mark.parametrize("n", [3, 5, 17, 65, 257])
+def test_vcycle_matches_oracle(n):
+    p = _problem(n)
+    s = solver_for(p)
+    H = oracle.Hierarchy(oracle.assemble(p.coords, p.kappa))
+    rng = np.random.default_rng(7)
+    for _ in range(2):
+        r = inputs.rhs_uniform(rng, (n, n))
+        z = s.vcycle(torch.as_tensor(r, device="cuda")).cpu().numpy()
+        zo = H.vcycle(r)
+        assert relerr(z, zo) <= 1e-12
+        assert np.all(z[0] == 0) and np.all(z[-1] == 0) and np.all(z[:, 0] == 0) and np.all(z[:, -1] == 0)
+
+
+@pytest.mark.parametrize("n,iters", [(17, 5), (65, 8), (257, 6)])
+def test_pcg_fixed_iterations_match_oracle(n, iters):
+    p = _problem(n)
+    s = solver_for(p)
+    H = oracle.Hierarchy(oracle.assemble(p.coords, p.kappa))
+    x, info = s.solve(torch.as_tensor(p.rhs, device="cuda"), tol=0.0, maxit=iters)
+    xo, ito, hist, trr, st = H.pcg(p.rhs, tol=0.0, maxit=iters)
+    assert info.iterations == iters == ito
+    assert relerr(x.cpu().numpy(), xo) <= 1e-9
+
+
+@pytest.mark.parametrize("n,kind", [(65, "plain"), (129, "lognormal"), (257, "circle")])
+def test_pcg_free_running(n, kind):
+    p = _problem(n, kind)
+    s = solver_for(p)
+    H = oracle.Hierarchy(oracle.assemble(p.coords, p.kappa))
+    x, info = s.solve(torch.as_tensor(p.rhs, device="cuda"), tol=1e-10, maxit=200)
+    xo, ito, hist, trr, st = H.pcg(p.rhs, tol=1e-10, maxit=200)
+    assert info.true_relres <= 1e-10
+    assert abs(info.iterations - ito) <= 1
+    assert relerr(x.cpu().numpy(), xo) <= 1e-8
+
+
+@pytest.mark.parametrize("n", [65, 257])
+def test_fp32_preconditioner_reaches_fp64_tolerance(n):
+    """FP32 V-cycle inside FP64 flexible CG: the true FP64 residual still
+    reaches 1e-10, and the solution agrees with the oracle's FP64 solve to
+    within what that residual allows."""
+    p = _problem(n)
+    s = solver_for(p, precision="fp32")
+    x, info = s.solve(torch.as_tensor(p.rhs, device="cuda"), tol=1e-10, maxit=300)
+    H = oracle.Hierarchy(oracle.assemble(p.coords, p.kappa))
+    xo, ito, hist, trr, st = H.pcg(p.rhs, tol=1e-12, maxit=300)
+    assert info.true_relres <= 1e-10
+    assert relerr(x.cpu().numpy(), xo) <= 1e-7
+    # the FP32 V-cycle itself agrees with the FP64 one to FP32 accuracy
+    r = inputs.rhs_uniform(np.random.default_rng(3), (n, n))
+    z = s.vcycle(torch.as_tensor(r, device="cuda")).cpu().numpy()
+    assert relerr(z, H.vcycle(r)) <= 1e-4
+
+
+def test_host_buffers_give_same_result():
+    p = _problem(65)
+    s = solver_for(p)
+    xd, _ = s.solve(torch.as_tensor(p.rhs, device="cuda"), tol=1e-10)
+    xh, info = s.solve(torch.as_tensor(p.rhs).pin_memory(), tol=1e-10)
+    assert xh.device.type == "cpu"
+    assert torch.equal(xd.cpu(), xh)
+
+
+def test_zero_rhs_and_nonconvergence_status():
+    p = _problem(33)
+    s = solver_for(p)
+    x, info = s.solve(torch.zeros(33, 33, dtype=torch.float64, device="cuda"), tol=1e-10)
+    assert info.iterations == 0 and float(x.abs().max()) == 0.0
+    with pytest.raises(binding.BmgError) as e:
+        s.solve(torch.as_tensor(p.rhs, device="cuda"), tol=1e-10, maxit=1)
+    assert e.value.code == 8
+    x, info = s.solve(torch.as_tensor(p.rhs, device="cuda"), tol=1e-10, maxit=1, raise_on_nonconv=False)
+    assert info.iterations == 1 and info.status == 8
+
+
+def test_folded_map_is_reported():
+    n = 9
+    p = _problem(n)
+    coords = p.coords.copy()
+    coords[0, 4, 4] += 0.6          # push an interior node across its neighbours
+    s = binding.Solver(2, n)
+    with pytest.raises(binding.BmgError) as e:
+        s.assemble(torch.as_tensor(coords), torch.as_tensor(p.kappa))
+    assert e.value.code == 5
+    # the context stays usable
+    s.assemble(torch.as_tensor(p.coords), torch.as_tensor(p.kappa)).setup()
+
+
+def test_negative_coefficient_breaks_down_in_setup():
+    n = 17
+    p = _problem(n)
+    s = binding.Solver(2, n).assemble(torch.as_tensor(p.coords), torch.as_tensor(-p.kappa))
+    with pytest.raises(binding.BmgError) as e:
+        s.setup()
+    assert e.value.code == 6
+
+
+def test_adjoint_gradient_matches_oracle():
+    n = 65
+    (prob,) = inputs.annulus_adjoint(n, batch=1)
+    s = solver_for(prob)
+    u, _ = s.solve(torch.as_tensor(prob.rhs, device="cuda"), tol=1e-13, maxit=300)
+    g = u - torch.as_tensor(prob.extra["u_obs"], device="cuda")
+    lam, dk, info = s.adjoint_grad(u, g, tol=1e-13, maxit=300)
+    H = oracle.Hierarchy(oracle.assemble(prob.coords, prob.kappa))
+    uo = H.pcg(prob.rhs, tol=1e-13, maxit=300)[0]
+    lo = H.pcg(uo - prob.extra["u_obs"], tol=1e-13, maxit=300)[0]
+    go = oracle.adjoint_grad(prob.coords, uo, lo)
+    assert relerr(dk.cpu().numpy(), go) <= 1e-8
