@@ -1,0 +1,333 @@
+#!/usr/bin/env python
+"""Solve throughput of the structured multigrid solver on one GB300.
+
+Workload (default): the quarter annulus r in [1/2, 1] mapped from [0,1]^2,
+4097 x 4097 nodes (16,769,025 interior DoF), kappa = exp(g) with g a
+64-mode random-Fourier Gaussian field (sigma 1, correlation length 0.05,
+seed 1), f ~ U[-1,1].  One step = one solve of A x = f from x0 = 0 to a
+verified relative residual of 1e-10 (FP32 V(1,1)-cycle preconditioner,
+FP64 flexible CG); the hierarchy is built once, before timing.  The plain
+FP64 V-cycle solve is timed the same way and reported beside it.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+
+Prints one JSON line (rank 0).  With N > 1 (torchrun), every rank solves
+its own replica (no data-path collective): weak scaling.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "DoF/s to 1e-10 rel. residual, FP32-precond vs FP64 on same GB300; % HBM peak"
+UNIT = "DoF/s"
+TOL = 1e-10
+KERNEL_FILES = ["paper_2509_08109_gb300/csrc/vcycle.cu", "paper_2509_08109_gb300/csrc/krylov.cu",
+                "paper_2509_08109_gb300/csrc/fused2d.cu"]
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="own", choices=["own", "reference"])
+    ap.add_argument("--n", type=int, default=4097)
+    ap.add_argument("--cpu-sample-n", type=int, default=1025)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+def peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        d = json.load(open(path))
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+def config_for(n: int) -> dict:
+    stencil_mb = 5 * 8 * n * n / 1e6
+    return {"workload": f"quarter_annulus_lognormal_kappa_n{n}", "nodes_per_side": n, "dof": (n - 2) ** 2,
+            "map": "x=(1/2+s/2)cos(pi t/2), y=(1/2+s/2)sin(pi t/2)",
+            "kappa": "exp(64-mode Gaussian field, sigma 1, corr 0.05, seed 1)", "rhs": "U[-1,1] seed 1",
+            "cycle": "V(1,1), 4-colour GS, operator-induced P, Galerkin RAP, coarsest 3x3",
+            "outer": "FP64 flexible CG, FP32 V-cycle (headline); FP64 CG + FP64 V-cycle (fp64 field)",
+            "tol": TOL, "l2": f"inputs larger than L2 (FP64 stencil {stencil_mb:.0f} MB > 129 MB), no flush"}
+
+
+# ---------------------------------------------------------------- clocks
+class Clocks:
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.QUERY}",
+                                          "--format=csv,noheader,nounits", "-lms", "50"],
+                                         stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def stop(self) -> dict | None:
+        if self.proc is None:
+            return None
+        time.sleep(0.12)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, smax, reasons = [], 0.0, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax = max(smax, float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        os.unlink(self.path)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": smax, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ---------------------------------------------------------------- helpers
+def kernel_hash() -> str:
+    h = hashlib.sha1()
+    for f in KERNEL_FILES:
+        p = os.path.join(ROOT, f)
+        if os.path.exists(p):
+            h.update(open(p, "rb").read())
+    return h.hexdigest()[:12]
+
+
+def traffic_for(kernel: str, n: int):
+    """DRAM bytes per launch of `kernel` from the committed ncu summary, if
+    it was taken on the current kernel sources (else None)."""
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    if not os.path.exists(path):
+        return None
+    try:
+        d = json.load(open(path))
+    except ValueError:
+        return None
+    if d.get("kernel_hash") != kernel_hash():
+        return None
+    ent = d.get("kernels", {}).get(kernel)
+    if not ent or ent.get("n") != n:
+        return None
+    return ent.get("dram_bytes_per_launch")
+
+
+def cpu_baseline(n_sample: int) -> dict:
+    """The oracle (plain FP64 C, single thread) on a bounded sample of the
+    same workload: the same map/coefficient/rhs recipe at n_sample nodes per
+    side; time of the PCG solve to 1e-10 (hierarchy built beforehand)."""
+    import oracle
+    from paper_2509_08109_gb300 import inputs
+    p = inputs.annulus_lognormal(n_sample)
+    H = oracle.Hierarchy(oracle.assemble(p.coords, p.kappa))
+    t = time.perf_counter()
+    x, it, hist, trr, st = H.pcg(p.rhs, tol=TOL, maxit=500)
+    dt = time.perf_counter() - t
+    assert st == 0 and trr <= TOL, (st, trr)
+    return {"value": p.unknowns / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"one PCG solve to 1e-10 of the same recipe at n={n_sample} "
+                      f"({p.unknowns} DoF, {it} iterations, {dt:.2f} s), single-threaded C oracle"}
+
+
+# ---------------------------------------------------------------- own arm
+def run_own(args):
+    import torch
+    import torch.distributed as dist
+
+    from paper_2509_08109_gb300 import binding, inputs
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=dev)
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+
+    def max_over_ranks(v: float) -> float:
+        if world == 1:
+            return v
+        t = torch.tensor([v], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        return float(t.item())
+
+    n = args.n
+    dof = (n - 2) ** 2
+    coords, kappa, f = inputs.annulus_lognormal_device(n, dev)
+    stream = torch.cuda.current_stream(dev)
+
+    def build(prec):
+        s = binding.Solver(2, n, precision=prec, device=dev)
+        e0, e1, e2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+        e0.record(stream)
+        s.assemble(coords, kappa)
+        e1.record(stream)
+        s.setup()
+        e2.record(stream)
+        torch.cuda.synchronize(dev)
+        return s, e0.elapsed_time(e1), e1.elapsed_time(e2)
+
+    s32, asm32, set32 = build("fp32")
+    s64, asm64, set64 = build("fp64")
+    x = torch.zeros_like(f)
+
+    def timed(s, k, profile=False, clocks=None):
+        for _ in range(args.warmup):
+            s.solve(f, tol=TOL, out=x)
+        if profile:
+            s.profile(True)
+        l0 = s.launches
+        barrier()
+        torch.cuda.synchronize(dev)
+        if clocks:
+            clocks.start()
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        infos = []
+        a.record(stream)
+        for _ in range(k):
+            _, info = s.solve(f, tol=TOL, out=x)
+            infos.append(info)
+        b.record(stream)
+        torch.cuda.synchronize(dev)
+        barrier()
+        ck = clocks.stop() if clocks else None
+        ms = a.elapsed_time(b)
+        prof = s.profile_read() if profile else {}
+        if profile:
+            s.profile(False)
+        return max_over_ranks(ms), s.launches - l0, infos, prof, ck
+
+    clk = Clocks(local)
+    ms32, launches32, infos32, prof32, ck = timed(s32, args.steps, profile=True, clocks=clk)
+    ms64, launches64, infos64, _, _ = timed(s64, args.steps)
+    assert all(i.true_relres <= TOL for i in infos32 + infos64)
+    t32 = ms32 / args.steps
+    t64 = ms64 / args.steps
+    value = world * dof / (t32 * 1e-3)
+
+    # end to end through the public API with host (pinned) buffers
+    fh = f.cpu().pin_memory()
+    xh = torch.zeros_like(fh).pin_memory()
+    for _ in range(args.warmup):
+        s32.solve(fh, tol=TOL, out=xh)
+    barrier()
+    torch.cuda.synchronize(dev)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        xh.zero_()
+        s32.solve(fh, tol=TOL, out=xh)
+    torch.cuda.synchronize(dev)
+    e2e_s = max_over_ranks(time.perf_counter() - t0)
+    e2e = {"value": world * dof * args.steps / e2e_s, "unit": UNIT,
+           "h2d_bytes_per_step": 2 * fh.numel() * 8, "d2h_bytes_per_step": xh.numel() * 8}
+
+    # roofline of the dominant kernel class of the finest level
+    hbm, peak_kind = peaks()
+    dom = max(prof32.items(), key=lambda kv: kv[1][0]) if prof32 else None
+    roof = None
+    if dom:
+        name, (kms, nl, kbytes) = dom
+        achieved = kbytes / (kms * 1e-3) / 1e9
+        roof = {"bound": "hbm", "kernel": name, "achieved": round(achieved, 1), "peak": hbm,
+                "peak_source": f"{peak_kind} hbm_gbs", "unit": "GB/s", "frac": round(achieved / hbm, 4),
+                "traffic": traffic_for(name, n), "launches": nl, "avg_launch_ms": round(kms / nl, 4),
+                "algorithmic_bytes_per_launch": kbytes / nl,
+                "share_of_step": round(kms / ms32, 4)}
+    kclasses = {k: {"ms_per_step": round(v[0] / args.steps, 4), "launches_per_step": v[1] / args.steps,
+                    "GB/s": round(v[2] / (v[0] * 1e-3) / 1e9, 1)} for k, v in prof32.items()}
+
+    out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+           "warmup": args.warmup, "ms_per_step": t32, "higher_is_better": True, "scaling": "weak",
+           "vs_baseline": None, "dtype": "f32 V-cycle / f64 CG", "data": "synthetic",
+           "config": config_for(n), "e2e": e2e, "gpu_launches": launches32,
+           "iterations": infos32[-1].iterations, "true_relres": infos32[-1].true_relres,
+           "fp64": {"value": world * dof / (t64 * 1e-3), "ms_per_step": t64, "iterations": infos64[-1].iterations,
+                    "gpu_launches": launches64, "true_relres": infos64[-1].true_relres},
+           "fp32_over_fp64": t64 / t32,
+           "setup_ms": {"fp32": {"assemble": asm32, "setup": set32}, "fp64": {"assemble": asm64, "setup": set64}},
+           "roofline": roof, "kernel_classes_finest_level": kclasses, "clocks": ck}
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        out["cpu_baseline"] = cpu_baseline(args.cpu_sample_n)
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
+# ---------------------------------------------------------------- reference arm
+def run_reference(args):
+    """The oracle, as it stands, on the host cores: each step is one PCG
+    solve to 1e-10 of a bounded sample of the workload (same recipe at
+    n = 513 nodes per side)."""
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    import oracle
+    from paper_2509_08109_gb300 import inputs
+    n_s = 513
+    p = inputs.annulus_lognormal(n_s)
+    H = oracle.Hierarchy(oracle.assemble(p.coords, p.kappa))
+    for _ in range(args.warmup):
+        H.pcg(p.rhs, tol=TOL, maxit=500)
+    t = time.perf_counter()
+    for _ in range(args.steps):
+        x, it, hist, trr, st = H.pcg(p.rhs, tol=TOL, maxit=500)
+        assert st == 0
+    dt = time.perf_counter() - t
+    value = p.unknowns * args.steps / dt
+    sample = f"one single-threaded oracle PCG solve to 1e-10 per step, same recipe at n={n_s} ({p.unknowns} DoF)"
+    out = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+           "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3,
+           "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+           "config": config_for(args.n),
+           "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+           "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out), flush=True)
+
+
+if __name__ == "__main__":
+    a = parse()
+    if a.impl == "reference":
+        run_reference(a)
+    else:
+        run_own(a)

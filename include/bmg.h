@@ -164,6 +164,31 @@ bmg_status bmg_get_stencil(bmg_ctx* ctx, int level, double* out);
    and rows of boundary fine nodes are 0. */
 bmg_status bmg_get_interp(bmg_ctx* ctx, int level, double* out);
 
+/* Kernel classes timed by the profiler (finest level only). */
+enum {
+    BMG_PROF_SMOOTH = 0,          /* Gauss-Seidel sweeps */
+    BMG_PROF_RESIDUAL = 1,        /* residual r = f - A x */
+    BMG_PROF_RESTRICT = 2,        /* b_c = P^T r */
+    BMG_PROF_PROLONG = 3,         /* x += P x_c */
+    BMG_PROF_SPMV = 4,            /* q = A p with p.q (outer CG) */
+    BMG_PROF_UPDATE = 5,          /* x += alpha p, r -= alpha q, r.r */
+    BMG_PROF_VDOWN = 6,           /* fused pre-smooth + residual + restriction */
+    BMG_PROF_VUP = 7,             /* fused prolongation + post-smooth */
+    BMG_PROF_KINDS = 8
+};
+
+/* Starts (enable=1, clearing earlier records) or stops (enable=0) timing:
+   while on, every launch of a profiled class on the finest level is
+   bracketed by CUDA events recorded on the context's stream, and the
+   library adds that launch's algorithmic bytes (the compulsory HBM
+   traffic of its data: each stencil, vector and interpolation value read
+   or written once). */
+bmg_status bmg_profile(bmg_ctx* ctx, int enable);
+
+/* Reads the accumulated device time (ms), launch count and algorithmic
+   bytes of one class (synchronises the stream). */
+bmg_status bmg_profile_read(bmg_ctx* ctx, int kind, double* ms, long long* launches, double* bytes);
+
 /* Kernel launches the context has issued since creation (all kinds). */
 long long bmg_launch_count(const bmg_ctx* ctx);
 

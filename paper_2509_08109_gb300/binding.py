@@ -82,6 +82,8 @@ def load() -> ctypes.CDLL:
         "bmg_get_stencil": ([P, I, P], I),
         "bmg_get_interp": ([P, I, P], I),
         "bmg_launch_count": ([P], ctypes.c_longlong),
+        "bmg_profile": ([P, I], I),
+        "bmg_profile_read": ([P, I, ctypes.POINTER(D), ctypes.POINTER(ctypes.c_longlong), ctypes.POINTER(D)], I),
         "bmg_destroy": ([P], None),
         "bmg_status_str": ([I], ctypes.c_char_p),
     }
@@ -96,8 +98,8 @@ def load() -> ctypes.CDLL:
 def exported_symbols() -> list:
     return ["bmg_default_opts", "bmg_create", "bmg_workspace_bytes", "bmg_attach", "bmg_assemble",
             "bmg_set_stencil", "bmg_setup", "bmg_vcycle", "bmg_solve", "bmg_adjoint_grad", "bmg_levels",
-            "bmg_level_n", "bmg_get_stencil", "bmg_get_interp", "bmg_launch_count", "bmg_destroy",
-            "bmg_status_str"]
+            "bmg_level_n", "bmg_get_stencil", "bmg_get_interp", "bmg_launch_count", "bmg_profile",
+            "bmg_profile_read", "bmg_destroy", "bmg_status_str"]
 
 
 def _check(code: int, where: str):
@@ -226,6 +228,26 @@ class Solver:
                                            float(tol), int(maxit), ctypes.byref(info)), "bmg_adjoint_grad")
         return lam, dk, SolveInfo(info.iterations, info.levels, info.relres, info.true_relres, info.rho,
                                   info.grid_complexity, info.operator_complexity, info.status)
+
+    # ------------------------------------------------------------ profiling
+    PROF_KINDS = {"smooth": 0, "residual": 1, "restrict": 2, "prolong": 3, "spmv": 4, "update": 5,
+                  "vdown": 6, "vup": 7}
+
+    def profile(self, enable: bool):
+        _check(load().bmg_profile(self._h, int(enable)), "bmg_profile")
+
+    def profile_read(self) -> dict:
+        """{kind: (device ms, launches, algorithmic bytes)} of the finest level."""
+        out = {}
+        for name, k in self.PROF_KINDS.items():
+            ms = ctypes.c_double()
+            nl = ctypes.c_longlong()
+            by = ctypes.c_double()
+            _check(load().bmg_profile_read(self._h, k, ctypes.byref(ms), ctypes.byref(nl), ctypes.byref(by)),
+                   "bmg_profile_read")
+            if nl.value:
+                out[name] = (ms.value, nl.value, by.value)
+        return out
 
     # ------------------------------------------------------------ exports
     def stencil(self, level: int) -> torch.Tensor:

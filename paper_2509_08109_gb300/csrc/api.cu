@@ -380,9 +380,47 @@ bmg_status bmg_get_interp(bmg_ctx* ctx, int level, double* out) {
     return BMG_OK;
 }
 
+bmg_status bmg_profile(bmg_ctx* ctx, int enable) {
+    if (!ctx) return BMG_ERR_ARG;
+    Ctx& c = ctx->c;
+    if (enable) {
+        if (c.attached) BMG_CUDA(cudaStreamSynchronize(c.stream));
+        for (int k = 0; k < BMG_PROF_KINDS; k++) {
+            c.prof[k].used = 0;
+            c.prof[k].bytes = 0.0;
+        }
+    }
+    c.prof_on = enable != 0;
+    return BMG_OK;
+}
+
+bmg_status bmg_profile_read(bmg_ctx* ctx, int kind, double* ms, long long* launches, double* bytes) {
+    if (!ctx || kind < 0 || kind >= BMG_PROF_KINDS) return BMG_ERR_ARG;
+    Ctx& c = ctx->c;
+    ProfSlot& s = c.prof[kind];
+    double tot = 0.0;
+    if (s.used > 0) {
+        BMG_CUDA(cudaStreamSynchronize(c.stream));
+        for (int i = 0; i < s.used; i++) {
+            float t = 0.f;
+            BMG_CUDA(cudaEventElapsedTime(&t, s.ev[2 * i], s.ev[2 * i + 1]));
+            tot += t;
+        }
+    }
+    if (ms) *ms = tot;
+    if (launches) *launches = s.used;
+    if (bytes) *bytes = s.bytes;
+    return BMG_OK;
+}
+
 long long bmg_launch_count(const bmg_ctx* ctx) { return ctx ? ctx->c.launches : 0; }
 
-void bmg_destroy(bmg_ctx* ctx) { delete ctx; }
+void bmg_destroy(bmg_ctx* ctx) {
+    if (!ctx) return;
+    for (int k = 0; k < BMG_PROF_KINDS; k++)
+        for (cudaEvent_t e : ctx->c.prof[k].ev) cudaEventDestroy(e);
+    delete ctx;
+}
 
 const char* bmg_status_str(bmg_status s) {
     switch (s) {

@@ -25,6 +25,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <vector>
+
 #include "../../include/bmg.h"
 
 namespace bmg {
@@ -66,6 +68,12 @@ struct Level {
     void* r = nullptr;        // residual scratch
 };
 
+struct ProfSlot {
+    std::vector<cudaEvent_t> ev;   // start/end pairs
+    int used = 0;
+    double bytes = 0.0;
+};
+
 struct Ctx {
     bmg_opts opts{};
     int dim = 2;
@@ -86,7 +94,31 @@ struct Ctx {
     KState* st_host = nullptr;    // pinned mirror
     long long launches = 0;
     int red_blocks = 0;           // fixed grid of the reducing kernels (deterministic)
+    bool prof_on = false;
+    ProfSlot prof[BMG_PROF_KINDS];
 };
+
+// Event brackets around profiled launches (finest level only).
+inline void prof_begin(Ctx& c, int kind, int level) {
+    if (!c.prof_on || level != 0) return;
+    ProfSlot& s = c.prof[kind];
+    if ((size_t)(2 * s.used + 2) > s.ev.size()) {
+        cudaEvent_t a, b;
+        cudaEventCreate(&a);
+        cudaEventCreate(&b);
+        s.ev.push_back(a);
+        s.ev.push_back(b);
+    }
+    cudaEventRecord(s.ev[2 * s.used], c.stream);
+}
+
+inline void prof_end(Ctx& c, int kind, int level, double bytes) {
+    if (!c.prof_on || level != 0) return;
+    ProfSlot& s = c.prof[kind];
+    cudaEventRecord(s.ev[2 * s.used + 1], c.stream);
+    s.used++;
+    s.bytes += bytes;
+}
 
 // ------------------------------------------------------------------ helpers
 #define BMG_CUDA(call)                                                      \

@@ -173,7 +173,10 @@ bmg_status k_dot(Ctx& c, const double* a, const double* b, double* slot) {
 
 bmg_status k_spmv_pq(Ctx& c, const double* p, double* q) {
     const Level& L = c.lev[0];
+    const double N = (double)(L.n - 2) * (L.n - 2);
+    prof_begin(c, BMG_PROF_SPMV, 0);
     k_spmv_pq<<<c.red_blocks, kThreads, 0, c.stream>>>(Grid2{L.n, L.ld}, L.A64, L.plane, p, q, c.partials, c.st);
+    prof_end(c, BMG_PROF_SPMV, 0, (c.ns + 2) * 8.0 * N);
     c.launches++;
     BMG_CUDA(cudaGetLastError());
     return BMG_OK;
@@ -181,7 +184,10 @@ bmg_status k_spmv_pq(Ctx& c, const double* p, double* q) {
 
 bmg_status k_update_xr(Ctx& c) {
     const Level& L = c.lev[0];
+    const double N = (double)(L.n - 2) * (L.n - 2);
+    prof_begin(c, BMG_PROF_UPDATE, 0);
     k_update_xr<<<c.red_blocks, kThreads, 0, c.stream>>>(L.plane, c.x, c.r, c.p, c.q, c.partials, c.st);
+    prof_end(c, BMG_PROF_UPDATE, 0, 6 * 8.0 * N);
     c.launches++;
     BMG_CUDA(cudaGetLastError());
     return BMG_OK;

@@ -130,10 +130,17 @@ const double* Pof<double>(const Level& L) { return L.P64; }
 template <>
 const float* Pof<float>(const Level& L) { return L.P32; }
 
+// Interior unknowns of a level (the unit of the algorithmic byte counts).
+inline double dofs(const Ctx& c, int l) {
+    const double m = c.lev[l].n - 2;
+    return c.dim == 2 ? m * m : m * m * m;
+}
+
 template <typename T>
 bmg_status vcycle2d_impl(Ctx& c, const T* b0, T* x0) {
     cudaStream_t s = c.stream;
     const int L = c.nlev;
+    const double sz = sizeof(T);
     auto bl = [&](int l) { return l == 0 ? b0 : (const T*)c.lev[l].b; };
     auto xl = [&](int l) { return l == 0 ? x0 : (T*)c.lev[l].x; };
     for (int l = 0; l < L - 1; l++) {
@@ -142,12 +149,19 @@ bmg_status vcycle2d_impl(Ctx& c, const T* b0, T* x0) {
         LV<T> v{Aof<T>(F), F.n, F.ld, F.plane};
         BMG_CUDA(cudaMemsetAsync(xl(l), 0, sizeof(T) * F.plane, s));
         const dim3 gc(cdiv((F.n + 1) / 2, 128), (F.n + 1) / 2);
+        const double N = dofs(c, l);
         for (int col = 0; col < 4; col++) {
+            prof_begin(c, BMG_PROF_SMOOTH, l);
             k_gs_colour2d<T><<<gc, 128, 0, s>>>(v, bl(l), xl(l), col & 1, col >> 1);
+            prof_end(c, BMG_PROF_SMOOTH, l, (c.ns + 3) * sz * N / 4);
         }
+        prof_begin(c, BMG_PROF_RESIDUAL, l);
         k_residual2d<T><<<rows(F.n, F.n), 128, 0, s>>>(v, bl(l), xl(l), (T*)F.r);
+        prof_end(c, BMG_PROF_RESIDUAL, l, (c.ns + 3) * sz * N);
+        prof_begin(c, BMG_PROF_RESTRICT, l);
         k_restrict2d<T><<<rows(K.n, K.n), 128, 0, s>>>(F.n, F.ld, (const T*)F.r, Pof<T>(F), K.n, K.ld, K.plane,
                                                       (T*)K.b);
+        prof_end(c, BMG_PROF_RESTRICT, l, (1.0 + c.np / 4.0 + 0.25) * sz * N);
         c.launches += 6;
     }
     {
@@ -161,10 +175,15 @@ bmg_status vcycle2d_impl(Ctx& c, const T* b0, T* x0) {
         const Level& F = c.lev[l];
         const Level& K = c.lev[l + 1];
         LV<T> v{Aof<T>(F), F.n, F.ld, F.plane};
+        const double N = dofs(c, l);
+        prof_begin(c, BMG_PROF_PROLONG, l);
         k_prolong2d<T><<<rows(F.n, F.n), 128, 0, s>>>(F.n, F.ld, xl(l), Pof<T>(F), K.ld, K.plane, xl(l + 1));
+        prof_end(c, BMG_PROF_PROLONG, l, (2.0 + c.np / 4.0 + 0.25) * sz * N);
         const dim3 gc(cdiv((F.n + 1) / 2, 128), (F.n + 1) / 2);
         for (int col = 3; col >= 0; col--) {
+            prof_begin(c, BMG_PROF_SMOOTH, l);
             k_gs_colour2d<T><<<gc, 128, 0, s>>>(v, bl(l), xl(l), col & 1, col >> 1);
+            prof_end(c, BMG_PROF_SMOOTH, l, (c.ns + 3) * sz * N / 4);
         }
         c.launches += 5;
     }
