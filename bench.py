@@ -223,12 +223,14 @@ def run_own(args):
         a = torch.cuda.Event(enable_timing=True)
         b = torch.cuda.Event(enable_timing=True)
         infos = []
+        torch.cuda.nvtx.range_push(f"timed_{s.precision}")
         a.record(stream)
         for _ in range(k):
             _, info = s.solve(f, tol=TOL, out=x)
             infos.append(info)
         b.record(stream)
         torch.cuda.synchronize(dev)
+        torch.cuda.nvtx.range_pop()
         barrier()
         ck = clocks.stop() if clocks else None
         ms = a.elapsed_time(b)

@@ -68,12 +68,18 @@ enum {
     BMG_OUTER_FLEXIBLE_CG = 1      /* beta = r_{k+1}.(z_{k+1}-z_k) / r_k.z_k */
 };
 
+enum {
+    BMG_FLAG_UNFUSED = 1           /* V-cycle from separate per-colour, residual,
+                                      restriction and prolongation kernels instead
+                                      of the streaming fused kernels (2-D) */
+};
+
 typedef struct {
     int dim;          /* 2 or 3 */
     int n;            /* nodes per side, 2^k + 1, k >= 1 */
     int precision;    /* BMG_PREC_FP64 or BMG_PREC_FP32 */
     int outer;        /* BMG_OUTER_CG or BMG_OUTER_FLEXIBLE_CG */
-    int flags;        /* reserved, 0 */
+    int flags;        /* BMG_FLAG_* bits, 0 by default */
 } bmg_opts;
 
 typedef struct {

@@ -56,9 +56,8 @@ size_t carve(Ctx& c, char* base) {
             L.P64 = nullptr;
             L.P32 = nullptr;
         }
-        const bool need_bx = l > 0 || f32;
-        L.b = need_bx ? take(vt * L.plane) : nullptr;
-        L.x = need_bx ? take(vt * L.plane) : nullptr;
+        L.b = (l > 0 || f32) ? take(vt * L.plane) : nullptr;
+        L.x = take(vt * L.plane);
         L.r = take(vt * L.plane);
     }
     const long long pl0 = c.lev[0].plane;
@@ -254,6 +253,8 @@ bmg_status bmg_attach(bmg_ctx* ctx, void* ws, size_t bytes, void* stream) {
     carve(c, c.ws);
     BMG_CUDA(cudaMemsetAsync(c.ws, 0, c.ws_need, c.stream));
     BMG_CUDA(cudaStreamSynchronize(c.stream));
+    c.use_fused = c.dim == 2 && !(c.opts.flags & BMG_FLAG_UNFUSED) && c.nlev >= 2;
+    if (c.use_fused) BMG_TRY(fused_prepare(c));
     c.attached = true;
     c.have_op = c.have_setup = false;
     return BMG_OK;

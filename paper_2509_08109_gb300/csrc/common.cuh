@@ -28,6 +28,7 @@
 #include <vector>
 
 #include "../../include/bmg.h"
+#include "fused2d.cuh"
 
 namespace bmg {
 
@@ -96,6 +97,8 @@ struct Ctx {
     int red_blocks = 0;           // fixed grid of the reducing kernels (deterministic)
     bool prof_on = false;
     ProfSlot prof[BMG_PROF_KINDS];
+    bool use_fused = false;       // streaming V-cycle kernels (2-D)
+    FusedLevel fused[kMaxLevels];
 };
 
 // Event brackets around profiled launches (finest level only).
@@ -220,6 +223,13 @@ bmg_status export_interp3d(Ctx& c, int l, double* out);
 bmg_status adjoint_cells3d(Ctx& c, const double* coords, const double* u, const double* lam, double* g);
 // vcycle.cu: z = M r on the finest level (FP64 in/out, internal layout)
 bmg_status vcycle(Ctx& c, const double* r, double* z);
+// fused2d.cu / tmaps.cu
+int fused_down_smem(bool f32, bool f64in, int wc);
+int fused_up_smem(bool f32, bool f64in, int wc);
+bmg_status fused_occupancy(bool f32, bool f64in, int wc, int* down_blocks, int* up_blocks);
+bmg_status fused_down(Ctx& c, int l);
+bmg_status fused_up(Ctx& c, int l, void* out);
+bmg_status fused_prepare(Ctx& c);
 bmg_status demote_levels(Ctx& c);
 // krylov.cu
 bmg_status k_pack(Ctx& c, const double* src, double* dst);      // n^d -> padded, boundary zeroed

@@ -191,6 +191,39 @@ bmg_status vcycle2d_impl(Ctx& c, const T* b0, T* x0) {
     return BMG_OK;
 }
 
+// Streaming path: one down kernel and one up kernel per level pair.
+template <typename T>
+bmg_status vcycle2d_fused(Ctx& c, double* z) {
+    cudaStream_t s = c.stream;
+    const int L = c.nlev;
+    const double sz = sizeof(T);
+    const bool f32 = sizeof(T) == 4;
+    for (int l = 0; l < L - 1; l++) {
+        const double N = dofs(c, l);
+        const double szf = l == 0 ? 8.0 : sz;
+        prof_begin(c, BMG_PROF_VDOWN, l);
+        BMG_TRY(fused_down(c, l));
+        prof_end(c, BMG_PROF_VDOWN, l, N * (c.ns * sz + szf + sz + c.np / 4.0 * sz + sz / 4));
+    }
+    {
+        const Level& C = c.lev[L - 1];
+        LV<T> v{Aof<T>(C), C.n, C.ld, C.plane};
+        k_coarsest2d<T><<<1, 1, 0, s>>>(v, C.A64, (const T*)C.b, (T*)C.r);
+        c.launches++;
+    }
+    for (int l = L - 2; l >= 0; l--) {
+        const double N = dofs(c, l);
+        const double szf = l == 0 ? 8.0 : sz;
+        const double szo = l == 0 ? 8.0 : sz;
+        prof_begin(c, BMG_PROF_VUP, l);
+        BMG_TRY(fused_up(c, l, l == 0 ? (void*)z : c.lev[l].r));
+        prof_end(c, BMG_PROF_VUP, l, N * (c.ns * sz + szf + sz + c.np / 4.0 * sz + sz / 4 + szo));
+    }
+    (void)f32;
+    BMG_CUDA(cudaGetLastError());
+    return BMG_OK;
+}
+
 }  // namespace
 
 bmg_status demote_levels(Ctx& c) {
@@ -211,6 +244,11 @@ bmg_status demote_levels(Ctx& c) {
 
 bmg_status vcycle(Ctx& c, const double* r, double* z) {
     if (c.dim != 2) return BMG_ERR_SHAPE;
+    if (c.use_fused && c.nlev >= 2) {
+        if (r != c.r) return BMG_ERR_ARG;   // the level-0 tensor map streams c.r
+        if (c.opts.precision == BMG_PREC_FP64) return vcycle2d_fused<double>(c, z);
+        return vcycle2d_fused<float>(c, z);
+    }
     if (c.opts.precision == BMG_PREC_FP64) return vcycle2d_impl<double>(c, r, z);
     Level& F = c.lev[0];
     k_convert<double, float><<<1216, 256, 0, c.stream>>>(F.plane, r, (float*)F.b);

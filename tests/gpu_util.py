@@ -6,8 +6,8 @@ import oracle
 from paper_2509_08109_gb300 import binding
 
 
-def solver_for(problem, precision="fp64", outer=None):
-    s = binding.Solver(problem.dim, problem.n, precision=precision, outer=outer)
+def solver_for(problem, precision="fp64", outer=None, unfused=False):
+    s = binding.Solver(problem.dim, problem.n, precision=precision, outer=outer, unfused=unfused)
     s.assemble(torch.as_tensor(problem.coords), torch.as_tensor(problem.kappa))
     s.setup()
     return s

@@ -176,3 +176,45 @@ def test_adjoint_gradient_matches_oracle():
     lo = H.pcg(uo - prob.extra["u_obs"], tol=1e-13, maxit=300)[0]
     go = oracle.adjoint_grad(prob.coords, uo, lo)
     assert relerr(dk.cpu().numpy(), go) <= 1e-8
+
+
+# ------------------------------------------------------------------ streaming (fused) V-cycle
+@pytest.mark.parametrize("n", [5, 9, 33, 129, 513])
+@pytest.mark.parametrize("unfused", [False, True])
+def test_both_vcycle_paths_match_oracle(n, unfused):
+    """Tile widths 8/16/32 coarse columns, ragged last tiles, several row
+    chunks per strip; both kernel paths against the oracle's V-cycle."""
+    p = _problem(n)
+    s = solver_for(p, unfused=unfused)
+    H = oracle.Hierarchy(oracle.assemble(p.coords, p.kappa))
+    r = inputs.rhs_uniform(np.random.default_rng(n), (n, n))
+    z = s.vcycle(torch.as_tensor(r, device="cuda")).cpu().numpy()
+    assert relerr(z, H.vcycle(r)) <= 1e-12
+
+
+@pytest.mark.parametrize("n", [2049])
+def test_fused_matches_unfused_large(n):
+    """64-column tiles (the benchmark's shape) against the per-colour path."""
+    p = inputs.annulus_lognormal(n)
+    fu = solver_for(p)
+    un = solver_for(p, unfused=True)
+    r = torch.as_tensor(inputs.rhs_uniform(np.random.default_rng(1), (n, n)), device="cuda")
+    za = fu.vcycle(r)
+    zb = un.vcycle(r)
+    assert float((za - zb).norm() / zb.norm()) <= 1e-13
+    for prec in ("fp32",):
+        a = solver_for(p, precision=prec)
+        b = solver_for(p, precision=prec, unfused=True)
+        za, zb = a.vcycle(r), b.vcycle(r)
+        assert float((za - zb).norm() / zb.norm()) <= 1e-5
+
+
+def test_fused_fp32_solve_matches_unfused_iterations():
+    p = _problem(257)
+    a = solver_for(p, precision="fp32")
+    b = solver_for(p, precision="fp32", unfused=True)
+    f = torch.as_tensor(p.rhs, device="cuda")
+    xa, ia = a.solve(f, tol=1e-10)
+    xb, ib = b.solve(f, tol=1e-10)
+    assert ia.true_relres <= 1e-10 and ib.true_relres <= 1e-10
+    assert abs(ia.iterations - ib.iterations) <= 1
