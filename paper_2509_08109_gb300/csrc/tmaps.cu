@@ -49,7 +49,9 @@ bmg_status fused_prepare(Ctx& c) {
         FusedLevel& F = c.fused[l];
         const Level& Lf = c.lev[l];
         const Level& Lc = c.lev[l + 1];
-        const int m = Lc.n - 2;   // interior coarse nodes per side
+        // Tiles cover coarse indices 1 .. nc-1: coarse index J owns the fine rows
+        // 2J-1 and 2J, so the boundary index nc-1 still owns fine row nf-2.
+        const int m = Lc.n - 1;
         F.wc = m >= 512 ? 64 : m >= 128 ? 32 : m >= 32 ? 16 : 8;
         F.tiles_x = cdiv(m, F.wc);
         int od = 0, ou = 0;
