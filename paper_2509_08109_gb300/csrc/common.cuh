@@ -224,6 +224,7 @@ bmg_status adjoint_cells3d(Ctx& c, const double* coords, const double* u, const 
 // vcycle.cu: z = M r on the finest level (FP64 in/out, internal layout)
 bmg_status vcycle(Ctx& c, const double* r, double* z);
 // fused2d.cu / tmaps.cu
+int fused_rows_per_step(bool f32);
 int fused_down_smem(bool f32, bool f64in, int wc);
 int fused_up_smem(bool f32, bool f64in, int wc);
 bmg_status fused_occupancy(bool f32, bool f64in, int wc, int* down_blocks, int* up_blocks);

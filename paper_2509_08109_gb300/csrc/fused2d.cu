@@ -17,11 +17,16 @@
 // even row needs its two finished odd rows.  So one pass over the rows, with
 // a window of a few rows in shared memory, finishes every row; a column halo
 // of 8-9 fine points (recomputed by both neighbours) covers the horizontal
-// dependencies.  Rows arrive by TMA (cp.async.bulk.tensor) into a ring of
-// RP row-pair slots, each completed by an mbarrier with an expected byte
-// count, prefetched RP-3 pairs ahead; one thread issues all copies.  Every
-// mbarrier wait is bounded by the global timer; on expiry the CTA records
-// BMG_ERR_TIMEOUT, drains its outstanding copies (bounded) and returns.
+// dependencies.  A step handles K row pairs at once: thread (x, y) owns
+// the column pair (2x, 2x+1) of row pair y, so every colour phase keeps all
+// threads busy and a step costs six block barriers for 2K fine rows.  Rows
+// arrive by TMA (cp.async.bulk.tensor) into a ring of RP = 2K+2 row-pair
+// slots, each completed by an mbarrier with an expected byte count; the
+// next K pairs are in flight while a step computes; one thread issues all
+// copies.  Interpolation weights go straight from global memory into
+// registers (each is used by one thread).  Every mbarrier wait is bounded
+// by the global timer; on expiry the CTA records BMG_ERR_TIMEOUT, drains its
+// outstanding copies (bounded) and returns.
 #include <cuda.h>
 
 #include "common.cuh"
@@ -88,439 +93,447 @@ __device__ __forceinline__ void tma3d(void* dst, const CUtensorMap* m, uint64_t*
 }
 
 
-// ------------------------------------------------------------------ down
-template <typename T, typename TF, int RP>
-struct DownSmem {
-    int WW, WWc, sA, sF, sP;   // slot strides in bytes
-    __host__ __device__ DownSmem(int wc) {
+// ------------------------------------------------------------------ layout
+__host__ __device__ constexpr int r128(int b) { return (b + 127) & ~127; }
+
+template <typename T>
+__device__ __forceinline__ T divide(T s, T d) { return s / d; }
+template <>
+__device__ __forceinline__ float divide<float>(float s, float d) { return __fdividef(s, d); }
+
+// Shared-memory layout: RP ring slots of one row pair each (stencil planes,
+// right-hand side, and for the up kernel the pre-smoothed iterate and one
+// coarse row of the coarse iterate), then a 16-row ring of the iterate X
+// and (down) an equal ring of the residual R, then the mbarriers.
+template <typename T, typename TF, int K, bool UP>
+struct Lay {
+    static constexpr int RP = 2 * K + 2;
+    static constexpr int XR = K <= 2 ? 8 : 16;   // rows of the X / R rings (>= 2K + 4)
+    int WW, WWc, sA, sF, sXp, sC;
+    __host__ __device__ Lay(int wc) {
         WW = 2 * wc + 16;
         WWc = wc + 8;
-        sA = (10 * WW * (int)sizeof(T) + 127) & ~127;
-        sF = (2 * WW * (int)sizeof(TF) + 127) & ~127;
-        sP = (8 * WWc * (int)sizeof(T) + 127) & ~127;
+        sA = r128(10 * WW * (int)sizeof(T));
+        sF = r128(2 * WW * (int)sizeof(TF));
+        sXp = UP ? r128(2 * WW * (int)sizeof(T)) : 0;
+        sC = UP ? r128(WWc * (int)sizeof(T)) : 0;
     }
+    __host__ __device__ int slot() const { return sA + sF + sXp + sC; }
     __host__ __device__ int bytes() const {
-        return RP * (sA + sF + sP) + 8 * WW * (int)sizeof(T) + 4 * WW * (int)sizeof(T) + RP * 8 + 128;
+        return 128 + RP * slot() + (UP ? 1 : 2) * XR * WW * (int)sizeof(T) + RP * 8;
+    }
+    __host__ __device__ uint32_t tx() const {
+        return (uint32_t)(10 * WW * sizeof(T) + 2 * WW * sizeof(TF) +
+                          (UP ? 2 * WW * sizeof(T) + WWc * sizeof(T) : 0));
     }
 };
 
-template <typename T, typename TF, int RP>
-__global__ void __launch_bounds__(kNT) k_vdown2d(const __grid_constant__ CUtensorMap tmA,
-                                                 const __grid_constant__ CUtensorMap tmF,
-                                                 const __grid_constant__ CUtensorMap tmP, FusedArgs p) {
-    extern __shared__ __align__(128) unsigned char smem[];
-    const DownSmem<T, TF, RP> L(p.wc);
-    const int WW = L.WW, WWc = L.WWc;
-    unsigned char* base = (unsigned char*)(((uintptr_t)smem + 127) & ~(uintptr_t)127);
-    unsigned char* pA = base;
-    unsigned char* pF = pA + RP * L.sA;
-    unsigned char* pP = pF + RP * L.sF;
-    T* sX = (T*)(pP + RP * L.sP);
-    T* sR = sX + 8 * WW;
-    uint64_t* bars = (uint64_t*)(((uintptr_t)(sR + 4 * WW) + 7) & ~(uintptr_t)7);
-    const int tid = threadIdx.x;
+// Row-pair ring shared by both kernels.  Pair q (local index, q >= 0) is
+// the fine rows 2(q0+q)+1 and 2(q0+q)+2 and, for the up kernel, coarse row
+// q0+q+1 of the coarse iterate.
+template <typename T, typename TF, int K, bool UP>
+struct Ring {
+    unsigned char *pA, *pF, *pXp, *pC;
+    uint64_t* bars;
+    int q0, WW, sA, sF, sXp, sC;
+    __device__ __forceinline__ int slot_of_row(int j) const { return ((((j - 1) >> 1) - q0)) % Lay<T, TF, K, UP>::RP; }
+    __device__ __forceinline__ const T* A(int j) const {      // plane 0 of fine row j
+        return (const T*)(pA + slot_of_row(j) * sA) + ((j - 1) & 1) * WW;
+    }
+    __device__ __forceinline__ const TF* F(int j) const {
+        return (const TF*)(pF + slot_of_row(j) * sF) + ((j - 1) & 1) * WW;
+    }
+    __device__ __forceinline__ const T* Xp(int j) const {
+        return (const T*)(pXp + slot_of_row(j) * sXp) + ((j - 1) & 1) * WW;
+    }
+    __device__ __forceinline__ const T* C(int J) const {      // coarse row J (carried by pair J-1)
+        return (const T*)(pC + ((J - 1 - q0) % Lay<T, TF, K, UP>::RP) * sC);
+    }
+};
+
+// bounded wait for pairs [qa, qb); returns false (in every thread) on expiry
+template <int RP>
+__device__ __forceinline__ bool wait_pairs(uint64_t* bars, int qa, int qb) {
+    bool mine = true;
+    for (int q = qa; q < qb; q++) mine = mine && mbar_wait(bars + (q % RP), (uint32_t)((q / RP) & 1));
+    return __syncthreads_and(mine) != 0;
+}
+
+// ------------------------------------------------------------------ node updates
+// Symmetric-half stencil rows: plane p of row j is A(j) + p * 2 * WW.
+// Offsets: W(c) couples (c-1), W(c+1) couples (c+1) of the row; S(j) couples
+// row j-1, S(j+1) row j+1; SW(j,c) couples (c-1, j-1), SW(j+1,c+1) (c+1, j+1);
+// NW(j,c) couples (c-1, j+1), NW(j-1,c+1) (c+1, j-1).
+template <typename T>
+struct Rows {
+    const T *a, *an, *as;   // stencil rows j, j+1, j-1 (plane 0)
+    const T *x, *xn, *xs;   // iterate rows j, j+1, j-1
+    int PL;                 // plane stride
+    __device__ __forceinline__ T offdiag(int c) const {
+        T s = a[W2 * PL + c] * x[c - 1];
+        s += a[W2 * PL + c + 1] * x[c + 1];
+        s += a[S2 * PL + c] * xs[c];
+        s += an[S2 * PL + c] * xn[c];
+        s += a[SW2 * PL + c] * xs[c - 1];
+        s += an[SW2 * PL + c + 1] * xn[c + 1];
+        s += a[NW2 * PL + c] * xn[c - 1];
+        s += as[NW2 * PL + c + 1] * xs[c + 1];
+        return s;
+    }
+    // forward sweep, colour 2: the (c +- 1, j) neighbours are still zero
+    __device__ __forceinline__ T offdiag_no_row(int c) const {
+        T s = a[S2 * PL + c] * xs[c];
+        s += an[S2 * PL + c] * xn[c];
+        s += a[SW2 * PL + c] * xs[c - 1];
+        s += an[SW2 * PL + c + 1] * xn[c + 1];
+        s += a[NW2 * PL + c] * xn[c - 1];
+        s += as[NW2 * PL + c + 1] * xs[c + 1];
+        return s;
+    }
+    __device__ __forceinline__ T diag(int c) const { return a[C2 * PL + c]; }
+};
+
+// ------------------------------------------------------------------ down kernel
+template <typename T, typename TF, int K>
+__global__ void __launch_bounds__(72 * K) k_vdown2d(const __grid_constant__ CUtensorMap tmA,
+                                                    const __grid_constant__ CUtensorMap tmF, FusedArgs p) {
+    using LY = Lay<T, TF, K, false>;
+    constexpr int RP = LY::RP;
+    extern __shared__ unsigned char smem_raw[];
+    const LY L(p.wc);
+    const int WW = L.WW, PL = 2 * WW;
+    unsigned char* base = (unsigned char*)(((uintptr_t)smem_raw + 127) & ~(uintptr_t)127);
+    Ring<T, TF, K, false> rg;
+    rg.pA = base;
+    rg.pF = base + RP * L.sA;
+    rg.pXp = rg.pC = nullptr;
+    constexpr int XR = LY::XR;
+    T* sX = (T*)(base + RP * L.slot());
+    T* sR = sX + XR * WW;
+    rg.bars = (uint64_t*)(sR + XR * WW);
+    rg.WW = WW;
+    rg.sA = L.sA;
+    rg.sF = L.sF;
+    rg.sXp = rg.sC = 0;
+    const int tx = threadIdx.x, ty = threadIdx.y;
+    const bool lead = tx == 0 && ty == 0;
     const int I0 = 1 + blockIdx.x * p.wc, J0 = 1 + blockIdx.y * p.hc;
     const int x0 = 2 * I0 - 10, xc0 = I0 - 5;
-    const int q0 = J0 - 2, npairs = p.hc + 2;
+    rg.q0 = J0 - 2;
+    const int npairs = p.hc + 2;
     const int nf = p.nf, nc = p.nc;
-    const uint32_t tx_bytes = (uint32_t)(10 * WW * sizeof(T) + 2 * WW * sizeof(TF) + 8 * WWc * sizeof(T));
-
+    const uint32_t txb = L.tx();
     auto issue = [&](int q) {
-        const int s = q % RP, Jp = q0 + q;
-        uint64_t* bar = bars + s;
-        mbar_expect_tx(bar, tx_bytes);
-        tma3d(pA + s * L.sA, &tmA, bar, x0, 2 * Jp + 1, 0);
-        tma2d(pF + s * L.sF, &tmF, bar, x0, 2 * Jp + 1);
-        tma3d(pP + s * L.sP, &tmP, bar, xc0, Jp + 1, 0);
+        const int s = q % RP, Jp = rg.q0 + q;
+        uint64_t* bar = rg.bars + s;
+        mbar_expect_tx(bar, txb);
+        tma3d(rg.pA + s * L.sA, &tmA, bar, x0, 2 * Jp + 1, 0);
+        tma2d(rg.pF + s * L.sF, &tmF, bar, x0, 2 * Jp + 1);
     };
-    if (tid == 0) {
-        for (int s = 0; s < RP; s++) mbar_init(bars + s, 1);
+    if (lead) {
+        for (int s = 0; s < RP; s++) mbar_init(rg.bars + s, 1);
         fence_mbar_init();
     }
     __syncthreads();
-    int issued = 0, waited = 0;
-    if (tid == 0)
-        for (; issued < RP && issued < npairs; issued++) issue(issued);
-    issued = min(RP, npairs);
+    int issued = npairs < RP ? npairs : RP, waited = 0;
+    if (lead)
+        for (int q = 0; q < issued; q++) issue(q);
 
-    // accessors -------------------------------------------------------
-    auto slotA = [&](int j) -> const T* {       // fine row j -> its stencil row (plane 0)
-        const int q = ((j - 1) >> 1) - q0;
-        return (const T*)(pA + (q % RP) * L.sA) + ((j - 1) & 1) * WW;
-    };
-    auto Fr = [&](int j) -> const TF* {
-        const int q = ((j - 1) >> 1) - q0;
-        return (const TF*)(pF + (q % RP) * L.sF) + ((j - 1) & 1) * WW;
-    };
-    auto Pr = [&](int J) -> const T* {          // coarse row J of P (plane 0)
-        const int q = J - 1 - q0;
-        return (const T*)(pP + (q % RP) * L.sP);
-    };
-    auto Xr = [&](int j) -> T* { return sX + (j & 7) * WW; };
-    auto Rr = [&](int j) -> T* { return sR + (j & 3) * WW; };
-    const int PL = 2 * WW;  // plane stride inside a stencil slot
+    // per-thread columns: the even/odd pair (2 tx, 2 tx + 1) of the window
+    const int ce = 2 * tx, co = ce + 1;
+    const int ie = x0 + ce;
+    const bool ve = ce >= 1 && ce <= WW - 2 && ie >= 1 && ie <= nf - 2;
+    const bool vo = co <= WW - 2 && ie + 1 >= 1 && ie + 1 <= nf - 2;
+    const bool own_e = ve && ce >= 9 && ce < 9 + 2 * p.wc;
+    const bool own_o = vo && co >= 9 && co < 9 + 2 * p.wc;
+    const int I = xc0 + tx;
+    const bool vres = tx >= 5 && tx < 5 + p.wc && I >= 1 && I <= nc - 2;
     auto inrow = [&](int j) { return j >= 1 && j <= nf - 2; };
-    auto incol = [&](int c) { const int i = x0 + c; return c >= 1 && c <= WW - 2 && i >= 1 && i <= nf - 2; };
-
-    bool ok = true;
-    auto wait_pair = [&](int q) {
-        bool mine = mbar_wait(bars + (q % RP), (uint32_t)((q / RP) & 1));
-        ok = __syncthreads_and(mine) != 0;
-        waited = q + 1;
+    auto X = [&](int j) { return sX + (j & (XR - 1)) * WW; };
+    auto R = [&](int j) { return sR + (j & (XR - 1)) * WW; };
+    auto rows = [&](int j) {
+        return Rows<T>{rg.A(j), rg.A(j + 1), rg.A(j - 1), X(j), X(j + 1), X(j - 1), PL};
     };
-
-    // even row j: colour 0 (even c) then colour 1 (odd c); zero initial guess
-    auto even_row = [&](int j) {
-        const T* A = slotA(j);
-        const TF* F = Fr(j);
-        T* X = Xr(j);
-        const bool rj = inrow(j);
-        for (int c = 2 * tid; c < WW; c += 2 * kNT)
-            X[c] = (rj && incol(c)) ? (T)F[c] / A[C2 * PL + c] : (T)0;
-        __syncthreads();
-        for (int c = 2 * tid + 1; c < WW; c += 2 * kNT) {
-            T v = 0;
-            if (rj && incol(c)) {
-                const T s = (T)F[c] - A[W2 * PL + c] * X[c - 1] - A[W2 * PL + c + 1] * X[c + 1];
-                v = s / A[C2 * PL + c];
-            }
-            X[c] = v;
-        }
-    };
-    // odd row j: colour 2 (even c) then colour 3 (odd c)
-    auto odd_row = [&](int j) {
-        const T* A = slotA(j);
-        const T* An = slotA(j + 1);
-        const T* As = slotA(j - 1);
-        const TF* F = Fr(j);
-        T* X = Xr(j);
-        const T* Xs = Xr(j - 1);
-        const T* Xn = Xr(j + 1);
-        const bool rj = inrow(j);
-        for (int c = 2 * tid; c < WW; c += 2 * kNT) {
-            T v = 0;
-            if (rj && incol(c)) {
-                T s = (T)F[c];
-                s -= A[S2 * PL + c] * Xs[c];
-                s -= An[S2 * PL + c] * Xn[c];
-                s -= A[SW2 * PL + c] * Xs[c - 1];
-                s -= An[SW2 * PL + c + 1] * Xn[c + 1];
-                s -= A[NW2 * PL + c] * Xn[c - 1];
-                s -= As[NW2 * PL + c + 1] * Xs[c + 1];
-                v = s / A[C2 * PL + c];
-            }
-            X[c] = v;
-        }
-        __syncthreads();
-        for (int c = 2 * tid + 1; c < WW; c += 2 * kNT) {
-            T v = 0;
-            if (rj && incol(c)) {
-                T s = (T)F[c];
-                s -= A[W2 * PL + c] * X[c - 1];
-                s -= A[W2 * PL + c + 1] * X[c + 1];
-                s -= A[S2 * PL + c] * Xs[c];
-                s -= An[S2 * PL + c] * Xn[c];
-                s -= A[SW2 * PL + c] * Xs[c - 1];
-                s -= An[SW2 * PL + c + 1] * Xn[c + 1];
-                s -= A[NW2 * PL + c] * Xn[c - 1];
-                s -= As[NW2 * PL + c + 1] * Xs[c + 1];
-                v = s / A[C2 * PL + c];
-            }
-            X[c] = v;
-        }
-    };
-    // residual of row j; the last colour (odd, odd) has zero residual by construction
-    auto resid_row = [&](int j) {
-        const T* A = slotA(j);
-        const T* An = slotA(j + 1);
-        const T* As = slotA(j - 1);
-        const TF* F = Fr(j);
-        const T* X = Xr(j);
-        const T* Xs = Xr(j - 1);
-        const T* Xn = Xr(j + 1);
-        T* R = Rr(j);
-        const bool rj = inrow(j);
-        const bool oddj = j & 1;
-        for (int c = tid; c < WW; c += kNT) {
-            T v = 0;
-            if (rj && incol(c) && !(oddj && (c & 1))) {
-                T s = (T)F[c] - A[C2 * PL + c] * X[c];
-                s -= A[W2 * PL + c] * X[c - 1];
-                s -= A[W2 * PL + c + 1] * X[c + 1];
-                s -= A[S2 * PL + c] * Xs[c];
-                s -= An[S2 * PL + c] * Xn[c];
-                s -= A[SW2 * PL + c] * Xs[c - 1];
-                s -= An[SW2 * PL + c + 1] * Xn[c + 1];
-                s -= A[NW2 * PL + c] * Xn[c - 1];
-                s -= As[NW2 * PL + c + 1] * Xs[c + 1];
-                v = s;
-            }
-            R[c] = v;
-        }
-    };
-
+    const T* Pg = (const T*)p.P;
     T* xg = (T*)p.x;
     T* bcg = (T*)p.bc;
-    const int cown0 = 9, cown1 = 9 + 2 * p.wc;
 
-    // pre-roll: rows 2J0-2 .. 2J0 final, residual of row 2J0-1
-    wait_pair(0);
-    if (ok) wait_pair(1);
-    if (ok) {
-        even_row(2 * J0 - 2);
+    // colour 0 / 1 of even row j, colour 2 / 3 of odd row j, residual of row j
+    auto c0 = [&](int j) {
+        const Rows<T> r = rows(j);
+        X(j)[ce] = (ve && inrow(j)) ? divide<T>((T)rg.F(j)[ce], r.diag(ce)) : (T)0;
+    };
+    auto c1 = [&](int j) {
+        const Rows<T> r = rows(j);
+        T v = 0;
+        if (vo && inrow(j)) {
+            const T s = (T)rg.F(j)[co] - r.a[W2 * PL + co] * r.x[co - 1] - r.a[W2 * PL + co + 1] * r.x[co + 1];
+            v = divide<T>(s, r.diag(co));
+        }
+        X(j)[co] = v;
+    };
+    auto c2 = [&](int j) {
+        const Rows<T> r = rows(j);
+        X(j)[ce] = (ve && inrow(j)) ? divide<T>((T)rg.F(j)[ce] - r.offdiag_no_row(ce), r.diag(ce)) : (T)0;
+    };
+    auto c3 = [&](int j) {
+        const Rows<T> r = rows(j);
+        X(j)[co] = (vo && inrow(j)) ? divide<T>((T)rg.F(j)[co] - r.offdiag(co), r.diag(co)) : (T)0;
+    };
+    auto resid = [&](int j) {
+        const Rows<T> r = rows(j);
+        const TF* F = rg.F(j);
+        T* Rj = R(j);
+        const bool rj = inrow(j);
+        Rj[ce] = (ve && rj) ? (T)F[ce] - r.diag(ce) * r.x[ce] - r.offdiag(ce) : (T)0;
+        // the last colour (odd column on an odd row) has zero residual by construction
+        Rj[co] = (vo && rj && !(j & 1)) ? (T)F[co] - r.diag(co) * r.x[co] - r.offdiag(co) : (T)0;
+    };
+
+    bool ok = wait_pairs<RP>(rg.bars, 0, 2);
+    waited = ok ? 2 : 0;
+    if (ok) {   // pre-roll: rows 2J0-2 .. 2J0 final, residual of row 2J0-1
+        if (ty == 0) { c0(2 * J0 - 2); c0(2 * J0); }
         __syncthreads();
-        even_row(2 * J0);
+        if (ty == 0) { c1(2 * J0 - 2); c1(2 * J0); }
         __syncthreads();
-        odd_row(2 * J0 - 1);
+        if (ty == 0) c2(2 * J0 - 1);
         __syncthreads();
-        resid_row(2 * J0 - 1);
+        if (ty == 0) c3(2 * J0 - 1);
+        __syncthreads();
+        if (ty == 0) resid(2 * J0 - 1);
         __syncthreads();
     }
-    for (int J = J0; ok && J < J0 + p.hc; J++) {
-        wait_pair(J - q0);
+    for (int J = J0; ok && J < J0 + p.hc; J += K) {
+        const int qa = J - rg.q0;
+        ok = wait_pairs<RP>(rg.bars, qa, qa + K);
         if (!ok) break;
-        even_row(2 * J + 2);
-        __syncthreads();
-        odd_row(2 * J + 1);
-        __syncthreads();
-        resid_row(2 * J);
-        resid_row(2 * J + 1);
-        __syncthreads();
-        // restriction b_c(I, J) = sum_i P(i,(I,J)) r_i
-        if (J <= nc - 2) {
-            const T* Pj = Pr(J);
-            const T* Pm = Pr(J - 1);
-            const T* R0 = Rr(2 * J);
-            const T* Rs = Rr(2 * J - 1);
-            const T* Rn = Rr(2 * J + 1);
-            for (int cc = 5 + tid; cc < 5 + p.wc; cc += kNT) {
-                const int I = xc0 + cc;
-                if (I < 1 || I > nc - 2) continue;
-                const int c = 2 * cc;
-                T b = R0[c];
-                b += Pj[PXR * WWc + cc - 1] * R0[c - 1];
-                b += Pj[PXL * WWc + cc] * R0[c + 1];
-                b += Pm[PYN * WWc + cc] * Rs[c];
-                b += Pj[PYS * WWc + cc] * Rn[c];
-                b += Pm[PNE * WWc + cc - 1] * Rs[c - 1];
-                b += Pm[PNW * WWc + cc] * Rs[c + 1];
-                b += Pj[PSE * WWc + cc - 1] * Rn[c - 1];
-                b += Pj[PSW * WWc + cc] * Rn[c + 1];
-                bcg[(long long)J * p.ldc + I] = b;
-            }
+        waited = qa + K;
+        const int Jp = J + ty, jm = 2 * Jp, jo = jm + 1, je = jm + 2;
+        // interpolation weights of coarse node (I, Jp) for the restriction
+        T w[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+        const bool do_res = vres && Jp <= nc - 2;
+        if (do_res) {
+            const long long o = (long long)Jp * p.ldc + I;
+            w[0] = Pg[PXR * p.plc + o - 1];
+            w[1] = Pg[PXL * p.plc + o];
+            w[2] = Pg[PYN * p.plc + o - p.ldc];
+            w[3] = Pg[PYS * p.plc + o];
+            w[4] = Pg[PNE * p.plc + o - p.ldc - 1];
+            w[5] = Pg[PNW * p.plc + o - p.ldc];
+            w[6] = Pg[PSE * p.plc + o - 1];
+            w[7] = Pg[PSW * p.plc + o];
         }
-        // finished rows 2J-1, 2J of the owned columns
-        for (int r = 0; r < 2; r++) {
-            const int j = 2 * J - 1 + r;
-            if (!inrow(j)) continue;
-            const T* X = Xr(j);
-            for (int c = cown0 + tid; c < cown1; c += kNT) {
-                const int i = x0 + c;
-                if (i >= 1 && i <= nf - 2) xg[(long long)j * p.ldf + i] = X[c];
-            }
+        c0(je);
+        __syncthreads();
+        c1(je);
+        __syncthreads();
+        c2(jo);
+        __syncthreads();
+        c3(jo);
+        __syncthreads();
+        resid(jm);
+        resid(jo);
+        __syncthreads();
+        if (do_res) {
+            const T* Rm = R(jm);
+            const T* Rs = R(jm - 1);
+            const T* Rn = R(jo);
+            const int c = ce;
+            T b = Rm[c];
+            b += w[0] * Rm[c - 1];
+            b += w[1] * Rm[c + 1];
+            b += w[2] * Rs[c];
+            b += w[3] * Rn[c];
+            b += w[4] * Rs[c - 1];
+            b += w[5] * Rs[c + 1];
+            b += w[6] * Rn[c - 1];
+            b += w[7] * Rn[c + 1];
+            bcg[(long long)Jp * p.ldc + I] = b;
+        }
+        // finished rows 2Jp-1 and 2Jp of the owned columns
+        if (inrow(jm - 1)) {
+            const T* Xr = X(jm - 1);
+            if (own_e) xg[(long long)(jm - 1) * p.ldf + ie] = Xr[ce];
+            if (own_o) xg[(long long)(jm - 1) * p.ldf + ie + 1] = Xr[co];
+        }
+        if (inrow(jm)) {
+            const T* Xr = X(jm);
+            if (own_e) xg[(long long)jm * p.ldf + ie] = Xr[ce];
+            if (own_o) xg[(long long)jm * p.ldf + ie + 1] = Xr[co];
         }
         __syncthreads();
-        if (tid == 0 && J - J0 + RP < npairs) issue(J - J0 + RP);
-        issued = min(npairs, J - J0 + RP + 1) > issued ? min(npairs, J - J0 + RP + 1) : issued;
+        if (lead)
+            for (int t = 0; t < K; t++) {
+                const int q = qa - 2 + t + RP;
+                if (q < npairs) issue(q);
+            }
+        issued = min(npairs, qa - 2 + K + RP);
     }
     if (!ok) {
-        if (tid == 0) {
+        if (lead) {
             set_err(p.st, BMG_ERR_TIMEOUT);
-            for (int q = waited; q < issued; q++) mbar_wait(bars + (q % RP), (uint32_t)((q / RP) & 1));
+            for (int q = waited; q < issued; q++) mbar_wait(rg.bars + (q % RP), (uint32_t)((q / RP) & 1));
         }
         __syncthreads();
     }
 }
 
-// ------------------------------------------------------------------ up
-template <typename T, typename TF, int RP>
-struct UpSmem {
-    int WW, WWc, sA, sF, sX, sP, sC;
-    __host__ __device__ UpSmem(int wc) {
-        WW = 2 * wc + 16;
-        WWc = wc + 8;
-        sA = (10 * WW * (int)sizeof(T) + 127) & ~127;
-        sF = (2 * WW * (int)sizeof(TF) + 127) & ~127;
-        sX = (2 * WW * (int)sizeof(T) + 127) & ~127;
-        sP = (8 * WWc * (int)sizeof(T) + 127) & ~127;
-        sC = (WWc * (int)sizeof(T) + 127) & ~127;
-    }
-    __host__ __device__ int bytes() const {
-        return RP * (sA + sF + sX + sP + sC) + 8 * WW * (int)sizeof(T) + RP * 8 + 128;
-    }
-};
-
-template <typename T, typename TF, typename TO, int RP>
-__global__ void __launch_bounds__(kNT) k_vup2d(const __grid_constant__ CUtensorMap tmA,
-                                               const __grid_constant__ CUtensorMap tmF,
-                                               const __grid_constant__ CUtensorMap tmX,
-                                               const __grid_constant__ CUtensorMap tmP,
-                                               const __grid_constant__ CUtensorMap tmC, FusedArgs p) {
-    extern __shared__ __align__(128) unsigned char smem[];
-    const UpSmem<T, TF, RP> L(p.wc);
-    const int WW = L.WW, WWc = L.WWc;
-    unsigned char* pA = (unsigned char*)(((uintptr_t)smem + 127) & ~(uintptr_t)127);
-    unsigned char* pF = pA + RP * L.sA;
-    unsigned char* pXp = pF + RP * L.sF;
-    unsigned char* pP = pXp + RP * L.sX;
-    unsigned char* pC = pP + RP * L.sP;
-    T* sX = (T*)(pC + RP * L.sC);
-    uint64_t* bars = (uint64_t*)(((uintptr_t)(sX + 8 * WW) + 7) & ~(uintptr_t)7);
-    const int tid = threadIdx.x;
+// ------------------------------------------------------------------ up kernel
+template <typename T, typename TF, typename TO, int K>
+__global__ void __launch_bounds__(72 * K) k_vup2d(const __grid_constant__ CUtensorMap tmA,
+                                                  const __grid_constant__ CUtensorMap tmF,
+                                                  const __grid_constant__ CUtensorMap tmX,
+                                                  const __grid_constant__ CUtensorMap tmC, FusedArgs p) {
+    using LY = Lay<T, TF, K, true>;
+    constexpr int RP = LY::RP;
+    extern __shared__ unsigned char smem_raw[];
+    const LY L(p.wc);
+    const int WW = L.WW, PL = 2 * WW;
+    unsigned char* base = (unsigned char*)(((uintptr_t)smem_raw + 127) & ~(uintptr_t)127);
+    Ring<T, TF, K, true> rg;
+    rg.pA = base;
+    rg.pF = rg.pA + RP * L.sA;
+    rg.pXp = rg.pF + RP * L.sF;
+    rg.pC = rg.pXp + RP * L.sXp;
+    constexpr int XR = LY::XR;
+    T* sX = (T*)(base + RP * L.slot());
+    rg.bars = (uint64_t*)(sX + XR * WW);
+    rg.WW = WW;
+    rg.sA = L.sA;
+    rg.sF = L.sF;
+    rg.sXp = L.sXp;
+    rg.sC = L.sC;
+    const int tx = threadIdx.x, ty = threadIdx.y;
+    const bool lead = tx == 0 && ty == 0;
     const int I0 = 1 + blockIdx.x * p.wc, J0 = 1 + blockIdx.y * p.hc;
     const int x0 = 2 * I0 - 10, xc0 = I0 - 5;
-    const int q0 = J0 - 2, npairs = p.hc + 2;
-    const int nf = p.nf;
-    const uint32_t tx_bytes =
-        (uint32_t)(10 * WW * sizeof(T) + 2 * WW * sizeof(TF) + 2 * WW * sizeof(T) + 8 * WWc * sizeof(T) +
-                   WWc * sizeof(T));
-
+    rg.q0 = J0 - 2;
+    const int npairs = p.hc + 2;
+    const int nf = p.nf, nc = p.nc;
+    const uint32_t txb = L.tx();
     auto issue = [&](int q) {
-        const int s = q % RP, Jp = q0 + q;
-        uint64_t* bar = bars + s;
-        mbar_expect_tx(bar, tx_bytes);
-        tma3d(pA + s * L.sA, &tmA, bar, x0, 2 * Jp + 1, 0);
-        tma2d(pF + s * L.sF, &tmF, bar, x0, 2 * Jp + 1);
-        tma2d(pXp + s * L.sX, &tmX, bar, x0, 2 * Jp + 1);
-        tma3d(pP + s * L.sP, &tmP, bar, xc0, Jp + 1, 0);
-        tma2d(pC + s * L.sC, &tmC, bar, xc0, Jp + 1);
+        const int s = q % RP, Jp = rg.q0 + q;
+        uint64_t* bar = rg.bars + s;
+        mbar_expect_tx(bar, txb);
+        tma3d(rg.pA + s * L.sA, &tmA, bar, x0, 2 * Jp + 1, 0);
+        tma2d(rg.pF + s * L.sF, &tmF, bar, x0, 2 * Jp + 1);
+        tma2d(rg.pXp + s * L.sXp, &tmX, bar, x0, 2 * Jp + 1);
+        tma2d(rg.pC + s * L.sC, &tmC, bar, xc0, Jp + 1);
     };
-    if (tid == 0) {
-        for (int s = 0; s < RP; s++) mbar_init(bars + s, 1);
+    if (lead) {
+        for (int s = 0; s < RP; s++) mbar_init(rg.bars + s, 1);
         fence_mbar_init();
     }
     __syncthreads();
-    int issued = min(RP, npairs), waited = 0;
-    if (tid == 0)
+    int issued = npairs < RP ? npairs : RP, waited = 0;
+    if (lead)
         for (int q = 0; q < issued; q++) issue(q);
 
-    auto slotA = [&](int j) -> const T* {
-        const int q = ((j - 1) >> 1) - q0;
-        return (const T*)(pA + (q % RP) * L.sA) + ((j - 1) & 1) * WW;
-    };
-    auto Fr = [&](int j) -> const TF* {
-        const int q = ((j - 1) >> 1) - q0;
-        return (const TF*)(pF + (q % RP) * L.sF) + ((j - 1) & 1) * WW;
-    };
-    auto XPr = [&](int j) -> const T* {
-        const int q = ((j - 1) >> 1) - q0;
-        return (const T*)(pXp + (q % RP) * L.sX) + ((j - 1) & 1) * WW;
-    };
-    auto Pr = [&](int J) -> const T* { return (const T*)(pP + ((J - 1 - q0) % RP) * L.sP); };
-    auto Cr = [&](int J) -> const T* { return (const T*)(pC + ((J - 1 - q0) % RP) * L.sC); };
-    auto Xr = [&](int j) -> T* { return sX + (j & 7) * WW; };
-    const int PL = 2 * WW;
+    const int ce = 2 * tx, co = ce + 1;
+    const int ie = x0 + ce;
+    const bool ve = ce >= 1 && ce <= WW - 2 && ie >= 1 && ie <= nf - 2;
+    const bool vo = co <= WW - 2 && ie + 1 >= 1 && ie + 1 <= nf - 2;
+    const bool own_e = ve && ce >= 9 && ce < 9 + 2 * p.wc;
+    const bool own_o = vo && co >= 9 && co < 9 + 2 * p.wc;
+    const int I = xc0 + tx;                      // coarse column of the thread's column pair
+    const bool vI = I >= 0 && I <= nc - 1;
     auto inrow = [&](int j) { return j >= 1 && j <= nf - 2; };
-    auto incol = [&](int c) { const int i = x0 + c; return c >= 1 && c <= WW - 2 && i >= 1 && i <= nf - 2; };
-
-    bool ok = true;
-    auto wait_pair = [&](int q) {
-        bool mine = mbar_wait(bars + (q % RP), (uint32_t)((q / RP) & 1));
-        ok = __syncthreads_and(mine) != 0;
-        waited = q + 1;
+    auto X = [&](int j) { return sX + (j & (XR - 1)) * WW; };
+    auto rows = [&](int j) {
+        return Rows<T>{rg.A(j), rg.A(j + 1), rg.A(j - 1), X(j), X(j + 1), X(j - 1), PL};
     };
-
-    // corrected iterate of row j: x_pre + P x_c
-    auto corrected = [&](int j) {
-        const T* Xp = XPr(j);
-        T* X = Xr(j);
-        const bool rj = inrow(j);
-        const int Jc = j >> 1;
-        const T* P0 = Pr(Jc);
-        const T* C0 = Cr(Jc);
-        const T* C1 = Cr(Jc + 1);
-        const bool oddj = j & 1;
-        for (int c = tid; c < WW; c += kNT) {
-            T v = 0;
-            if (rj && incol(c)) {
-                const int cc = c >> 1;
-                T pv;
-                if (!(c & 1) && !oddj) {
-                    pv = C0[cc];
-                } else if ((c & 1) && !oddj) {
-                    pv = P0[PXL * WWc + cc] * C0[cc] + P0[PXR * WWc + cc] * C0[cc + 1];
-                } else if (!(c & 1) && oddj) {
-                    pv = P0[PYS * WWc + cc] * C0[cc] + P0[PYN * WWc + cc] * C1[cc];
-                } else {
-                    pv = P0[PSW * WWc + cc] * C0[cc] + P0[PSE * WWc + cc] * C0[cc + 1] + P0[PNW * WWc + cc] * C1[cc] +
-                         P0[PNE * WWc + cc] * C1[cc + 1];
-                }
-                v = Xp[c] + pv;
-            }
-            X[c] = v;
-        }
-    };
-    // Gauss-Seidel update of the nodes of row j with column parity par
-    auto gs = [&](int j, int par) {
-        const T* A = slotA(j);
-        const T* An = slotA(j + 1);
-        const T* As = slotA(j - 1);
-        const TF* F = Fr(j);
-        T* X = Xr(j);
-        const T* Xs = Xr(j - 1);
-        const T* Xn = Xr(j + 1);
-        const bool rj = inrow(j);
-        for (int c = 2 * tid + par; c < WW; c += 2 * kNT) {
-            if (!(rj && incol(c))) continue;
-            T s = (T)F[c];
-            s -= A[W2 * PL + c] * X[c - 1];
-            s -= A[W2 * PL + c + 1] * X[c + 1];
-            s -= A[S2 * PL + c] * Xs[c];
-            s -= An[S2 * PL + c] * Xn[c];
-            s -= A[SW2 * PL + c] * Xs[c - 1];
-            s -= An[SW2 * PL + c + 1] * Xn[c + 1];
-            s -= A[NW2 * PL + c] * Xn[c - 1];
-            s -= As[NW2 * PL + c + 1] * Xs[c + 1];
-            X[c] = s / A[C2 * PL + c];
-        }
-    };
-
+    const T* Pg = (const T*)p.P;
     TO* out = (TO*)p.x;
-    const int cown0 = 9, cown1 = 9 + 2 * p.wc;
+    auto pw = [&](int plane, int Jc) -> T {
+        return (vI && Jc >= 0 && Jc <= nc - 1) ? Pg[plane * p.plc + (long long)Jc * p.ldc + I] : (T)0;
+    };
 
-    wait_pair(0);
-    if (ok) wait_pair(1);
-    if (ok) {
-        corrected(2 * J0 - 2);
-        corrected(2 * J0 - 1);
-        corrected(2 * J0);
+    // corrected iterate x_pre + P x_c of the thread's two columns of row j,
+    // weights w (even row: PXL, PXR of coarse row j/2; odd row: PYS, PYN,
+    // PSW, PSE, PNW, PNE of coarse row (j-1)/2)
+    auto corr_even = [&](int j, T wxl, T wxr) {
+        const bool rj = inrow(j);
+        const T* C0 = rg.C(j >> 1);
+        const T* xp = rg.Xp(j);
+        T* x = X(j);
+        x[ce] = (ve && rj) ? xp[ce] + C0[tx] : (T)0;
+        x[co] = (vo && rj) ? xp[co] + wxl * C0[tx] + wxr * C0[tx + 1] : (T)0;
+    };
+    auto corr_odd = [&](int j, const T* wy) {
+        const bool rj = inrow(j);
+        const T* C0 = rg.C(j >> 1);
+        const T* C1 = rg.C((j >> 1) + 1);
+        const T* xp = rg.Xp(j);
+        T* x = X(j);
+        x[ce] = (ve && rj) ? xp[ce] + wy[0] * C0[tx] + wy[1] * C1[tx] : (T)0;
+        x[co] = (vo && rj) ? xp[co] + wy[2] * C0[tx] + wy[3] * C0[tx + 1] + wy[4] * C1[tx] + wy[5] * C1[tx + 1]
+                           : (T)0;
+    };
+    auto gs = [&](int j, int c, bool v) {      // one Gauss-Seidel update
+        if (!(v && inrow(j))) return;
+        const Rows<T> r = rows(j);
+        X(j)[c] = divide<T>((T)rg.F(j)[c] - r.offdiag(c), r.diag(c));
+    };
+
+    bool ok = wait_pairs<RP>(rg.bars, 0, 2);
+    waited = ok ? 2 : 0;
+    if (ok) {   // pre-roll: corrected rows 2J0-2 .. 2J0, odd row 2J0-1 smoothed
+        if (ty == 0) {
+            const int Jm = J0 - 1;
+            const T wy[6] = {pw(PYS, Jm), pw(PYN, Jm), pw(PSW, Jm), pw(PSE, Jm), pw(PNW, Jm), pw(PNE, Jm)};
+            corr_even(2 * J0 - 2, pw(PXL, Jm), pw(PXR, Jm));
+            corr_odd(2 * J0 - 1, wy);
+            corr_even(2 * J0, pw(PXL, J0), pw(PXR, J0));
+        }
         __syncthreads();
-        gs(2 * J0 - 1, 1);   // colour 3
+        if (ty == 0) gs(2 * J0 - 1, co, vo);     // colour 3
         __syncthreads();
-        gs(2 * J0 - 1, 0);   // colour 2
+        if (ty == 0) gs(2 * J0 - 1, ce, ve);     // colour 2
         __syncthreads();
     }
-    for (int J = J0; ok && J < J0 + p.hc; J++) {
-        wait_pair(J - q0);
+    for (int J = J0; ok && J < J0 + p.hc; J += K) {
+        const int qa = J - rg.q0;
+        // weights for the corrected values of this thread's rows (loaded before the wait)
+        const int Jp = J + ty, jm = 2 * Jp, jo = jm + 1, je = jm + 2;
+        const T wy[6] = {pw(PYS, Jp), pw(PYN, Jp), pw(PSW, Jp), pw(PSE, Jp), pw(PNW, Jp), pw(PNE, Jp)};
+        const T wxl = pw(PXL, Jp + 1), wxr = pw(PXR, Jp + 1);
+        ok = wait_pairs<RP>(rg.bars, qa, qa + K);
         if (!ok) break;
-        corrected(2 * J + 1);
-        corrected(2 * J + 2);
+        waited = qa + K;
+        corr_odd(jo, wy);
+        corr_even(je, wxl, wxr);
         __syncthreads();
-        gs(2 * J + 1, 1);    // colour 3
+        gs(jo, co, vo);      // colour 3
         __syncthreads();
-        gs(2 * J + 1, 0);    // colour 2
+        gs(jo, ce, ve);      // colour 2
         __syncthreads();
-        gs(2 * J, 1);        // colour 1
+        gs(jm, co, vo);      // colour 1
         __syncthreads();
-        gs(2 * J, 0);        // colour 0
+        gs(jm, ce, ve);      // colour 0
         __syncthreads();
-        for (int r = 0; r < 2; r++) {
-            const int j = 2 * J - 1 + r;
-            if (!inrow(j)) continue;
-            const T* X = Xr(j);
-            for (int c = cown0 + tid; c < cown1; c += kNT) {
-                const int i = x0 + c;
-                if (i >= 1 && i <= nf - 2) out[(long long)j * p.ldf + i] = (TO)X[c];
-            }
+        if (inrow(jm - 1)) {
+            const T* Xr = X(jm - 1);
+            if (own_e) out[(long long)(jm - 1) * p.ldf + ie] = (TO)Xr[ce];
+            if (own_o) out[(long long)(jm - 1) * p.ldf + ie + 1] = (TO)Xr[co];
+        }
+        if (inrow(jm)) {
+            const T* Xr = X(jm);
+            if (own_e) out[(long long)jm * p.ldf + ie] = (TO)Xr[ce];
+            if (own_o) out[(long long)jm * p.ldf + ie + 1] = (TO)Xr[co];
         }
         __syncthreads();
-        if (tid == 0 && J - J0 + RP < npairs) issue(J - J0 + RP);
-        issued = max(issued, min(npairs, J - J0 + RP + 1));
+        if (lead)
+            for (int t = 0; t < K; t++) {
+                const int q = qa - 2 + t + RP;
+                if (q < npairs) issue(q);
+            }
+        issued = min(npairs, qa - 2 + K + RP);
     }
     if (!ok) {
-        if (tid == 0) {
+        if (lead) {
             set_err(p.st, BMG_ERR_TIMEOUT);
-            for (int q = waited; q < issued; q++) mbar_wait(bars + (q % RP), (uint32_t)((q / RP) & 1));
+            for (int q = waited; q < issued; q++) mbar_wait(rg.bars + (q % RP), (uint32_t)((q / RP) & 1));
         }
         __syncthreads();
     }
@@ -528,40 +541,40 @@ __global__ void __launch_bounds__(kNT) k_vup2d(const __grid_constant__ CUtensorM
 
 // ------------------------------------------------------------------ host side
 template <typename T>
-constexpr int rp_of() { return sizeof(T) == 4 ? 8 : 6; }
+constexpr int k_of() { return sizeof(T) == 4 ? 4 : 2; }
 
 template <typename T, typename TF>
-int down_smem(int wc) { return DownSmem<T, TF, rp_of<T>()>(wc).bytes(); }
+int down_smem(int wc) { return Lay<T, TF, k_of<T>(), false>(wc).bytes(); }
 template <typename T, typename TF>
-int up_smem(int wc) { return UpSmem<T, TF, rp_of<T>()>(wc).bytes(); }
+int up_smem(int wc) { return Lay<T, TF, k_of<T>(), true>(wc).bytes(); }
 
 template <typename T, typename TF>
 bmg_status launch_down(Ctx& c, const FusedLevel& F, cudaStream_t s) {
-    auto kern = k_vdown2d<T, TF, rp_of<T>()>;
+    auto kern = k_vdown2d<T, TF, k_of<T>()>;
     const int smem = down_smem<T, TF>(F.wc);
     if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) != cudaSuccess)
         return BMG_ERR_DEVICE;
-    dim3 grid(F.tiles_x, F.tiles_y);
-    kern<<<grid, kNT, smem, s>>>(F.mA, F.mF, F.mP, F.down);
+    kern<<<dim3(F.tiles_x, F.tiles_y), dim3(F.wc + 8, k_of<T>()), smem, s>>>(F.mA, F.mF, F.down);
     c.launches++;
     return cudaGetLastError() == cudaSuccess ? BMG_OK : BMG_ERR_DEVICE;
 }
 
 template <typename T, typename TF, typename TO>
 bmg_status launch_up(Ctx& c, const FusedLevel& F, cudaStream_t s, void* out) {
-    auto kern = k_vup2d<T, TF, TO, rp_of<T>()>;
+    auto kern = k_vup2d<T, TF, TO, k_of<T>()>;
     const int smem = up_smem<T, TF>(F.wc);
     if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) != cudaSuccess)
         return BMG_ERR_DEVICE;
-    dim3 grid(F.tiles_x, F.tiles_y);
     FusedArgs a = F.up;
     a.x = out;
-    kern<<<grid, kNT, smem, s>>>(F.mA, F.mF, F.mXp, F.mP, F.mXc, a);
+    kern<<<dim3(F.tiles_x, F.tiles_y), dim3(F.wc + 8, k_of<T>()), smem, s>>>(F.mA, F.mF, F.mXp, F.mXc, a);
     c.launches++;
     return cudaGetLastError() == cudaSuccess ? BMG_OK : BMG_ERR_DEVICE;
 }
 
 }  // namespace
+
+int fused_rows_per_step(bool f32) { return f32 ? k_of<float>() : k_of<double>(); }
 
 int fused_down_smem(bool f32, bool f64in, int wc) {
     if (!f32) return down_smem<double, double>(wc);
@@ -577,26 +590,29 @@ bmg_status fused_occupancy(bool f32, bool f64in, int wc, int* down_blocks, int* 
     const int sd = fused_down_smem(f32, f64in, wc), su = fused_up_smem(f32, f64in, wc);
     cudaError_t e1, e2, e3, e4;
     if (!f32) {
-        auto kd = k_vdown2d<double, double, rp_of<double>()>;
-        auto ku = k_vup2d<double, double, double, rp_of<double>()>;
+        auto kd = k_vdown2d<double, double, k_of<double>()>;
+        auto ku = k_vup2d<double, double, double, k_of<double>()>;
+        const int nt = (wc + 8) * k_of<double>();
         e1 = cudaFuncSetAttribute(kd, cudaFuncAttributeMaxDynamicSharedMemorySize, sd);
         e2 = cudaFuncSetAttribute(ku, cudaFuncAttributeMaxDynamicSharedMemorySize, su);
-        e3 = cudaOccupancyMaxActiveBlocksPerMultiprocessor(down_blocks, kd, kNT, sd);
-        e4 = cudaOccupancyMaxActiveBlocksPerMultiprocessor(up_blocks, ku, kNT, su);
+        e3 = cudaOccupancyMaxActiveBlocksPerMultiprocessor(down_blocks, kd, nt, sd);
+        e4 = cudaOccupancyMaxActiveBlocksPerMultiprocessor(up_blocks, ku, nt, su);
     } else if (f64in) {
-        auto kd = k_vdown2d<float, double, rp_of<float>()>;
-        auto ku = k_vup2d<float, double, double, rp_of<float>()>;
+        auto kd = k_vdown2d<float, double, k_of<float>()>;
+        auto ku = k_vup2d<float, double, double, k_of<float>()>;
+        const int nt = (wc + 8) * k_of<float>();
         e1 = cudaFuncSetAttribute(kd, cudaFuncAttributeMaxDynamicSharedMemorySize, sd);
         e2 = cudaFuncSetAttribute(ku, cudaFuncAttributeMaxDynamicSharedMemorySize, su);
-        e3 = cudaOccupancyMaxActiveBlocksPerMultiprocessor(down_blocks, kd, kNT, sd);
-        e4 = cudaOccupancyMaxActiveBlocksPerMultiprocessor(up_blocks, ku, kNT, su);
+        e3 = cudaOccupancyMaxActiveBlocksPerMultiprocessor(down_blocks, kd, nt, sd);
+        e4 = cudaOccupancyMaxActiveBlocksPerMultiprocessor(up_blocks, ku, nt, su);
     } else {
-        auto kd = k_vdown2d<float, float, rp_of<float>()>;
-        auto ku = k_vup2d<float, float, float, rp_of<float>()>;
+        auto kd = k_vdown2d<float, float, k_of<float>()>;
+        auto ku = k_vup2d<float, float, float, k_of<float>()>;
+        const int nt = (wc + 8) * k_of<float>();
         e1 = cudaFuncSetAttribute(kd, cudaFuncAttributeMaxDynamicSharedMemorySize, sd);
         e2 = cudaFuncSetAttribute(ku, cudaFuncAttributeMaxDynamicSharedMemorySize, su);
-        e3 = cudaOccupancyMaxActiveBlocksPerMultiprocessor(down_blocks, kd, kNT, sd);
-        e4 = cudaOccupancyMaxActiveBlocksPerMultiprocessor(up_blocks, ku, kNT, su);
+        e3 = cudaOccupancyMaxActiveBlocksPerMultiprocessor(down_blocks, kd, nt, sd);
+        e4 = cudaOccupancyMaxActiveBlocksPerMultiprocessor(up_blocks, ku, nt, su);
     }
     if (e1 || e2 || e3 || e4) return BMG_ERR_DEVICE;
     return BMG_OK;

@@ -14,6 +14,8 @@ struct FusedArgs {
     int wc, hc;      // coarse columns / rows owned by one CTA
     void* x;         // down: pre-smoothed fine iterate (out); up: final fine iterate (out)
     void* bc;        // down: coarse right-hand side (out)
+    const void* P;   // interpolation planes (coarse grid)
+    long long plc;   // plane stride of P
     KState* st;
 };
 
@@ -24,7 +26,6 @@ struct FusedLevel {
     CUtensorMap mA;    // stencil planes, 3-D box (2*wc+16) x 2 rows x planes
     CUtensorMap mF;    // right-hand side rows
     CUtensorMap mXp;   // pre-smoothed iterate rows
-    CUtensorMap mP;    // interpolation planes on the coarse grid
     CUtensorMap mXc;   // coarse final iterate rows
     FusedArgs down, up;
 };

@@ -59,10 +59,11 @@ bmg_status fused_prepare(Ctx& c) {
         const int occ = od < ou ? od : ou;
         if (occ < 1) return BMG_ERR_DEVICE;
         const long long slots = (long long)occ * sms;
-        // rows per CTA: minimise waves x (rows + pre-roll)
+        // rows per CTA (a multiple of the rows per step): minimise waves x (rows + pre-roll)
+        const int K = fused_rows_per_step(f32);
         long long best = -1;
         for (int ty = 1; ty <= m; ty++) {
-            const int hc = cdiv(m, ty);
+            const int hc = cdiv(cdiv(m, ty), K) * K;
             const int tyr = cdiv(m, hc);
             const long long waves = cdiv((long long)F.tiles_x * tyr, slots);
             const long long cost = waves * (2LL * hc + 3);
@@ -80,11 +81,10 @@ bmg_status fused_prepare(Ctx& c) {
         bool ok = make_map(&F.mA, !f32, A, Lf.ld, Lf.n, c.ns, Lf.plane, WW, 2);
         ok = ok && make_map(&F.mF, f_is64, f, Lf.ld, Lf.n, 1, Lf.plane, WW, 2);
         ok = ok && make_map(&F.mXp, !f32, Lf.x, Lf.ld, Lf.n, 1, Lf.plane, WW, 2);
-        ok = ok && make_map(&F.mP, !f32, P, Lc.ld, Lc.n, c.np, Lc.plane, WWc, 1);
         ok = ok && make_map(&F.mXc, !f32, Lc.r, Lc.ld, Lc.n, 1, Lc.plane, WWc, 1);
         if (!ok) return BMG_ERR_DEVICE;
-        F.down = FusedArgs{Lf.n, Lc.n, Lf.ld, Lc.ld, F.wc, F.hc, Lf.x, Lc.b, c.st};
-        F.up = FusedArgs{Lf.n, Lc.n, Lf.ld, Lc.ld, F.wc, F.hc, nullptr, nullptr, c.st};
+        F.down = FusedArgs{Lf.n, Lc.n, Lf.ld, Lc.ld, F.wc, F.hc, Lf.x, Lc.b, P, Lc.plane, c.st};
+        F.up = FusedArgs{Lf.n, Lc.n, Lf.ld, Lc.ld, F.wc, F.hc, nullptr, nullptr, P, Lc.plane, c.st};
         F.ready = true;
     }
     return BMG_OK;
