@@ -65,7 +65,12 @@ enum {
 
 enum {
     BMG_OUTER_CG = 0,              /* beta = r_{k+1}.z_{k+1} / r_k.z_k */
-    BMG_OUTER_FLEXIBLE_CG = 1      /* beta = r_{k+1}.(z_{k+1}-z_k) / r_k.z_k */
+    BMG_OUTER_FLEXIBLE_CG = 1,     /* beta = r_{k+1}.(z_{k+1}-z_k) / r_k.z_k */
+    BMG_OUTER_REFINEMENT = 2       /* iterative refinement (needs BMG_PREC_FP32):
+                                      FP64 residual r = b - A x, an inner FP32
+                                      flexible CG on A d = r preconditioned by the
+                                      FP32 V-cycle, x += d in FP64; repeated until
+                                      the FP64 residual meets tol */
 };
 
 enum {
@@ -78,12 +83,12 @@ typedef struct {
     int dim;          /* 2 or 3 */
     int n;            /* nodes per side, 2^k + 1, k >= 1 */
     int precision;    /* BMG_PREC_FP64 or BMG_PREC_FP32 */
-    int outer;        /* BMG_OUTER_CG or BMG_OUTER_FLEXIBLE_CG */
+    int outer;        /* BMG_OUTER_CG, BMG_OUTER_FLEXIBLE_CG or BMG_OUTER_REFINEMENT */
     int flags;        /* BMG_FLAG_* bits, 0 by default */
 } bmg_opts;
 
 typedef struct {
-    int iterations;               /* PCG iterations done */
+    int iterations;               /* PCG iterations done (inner ones for refinement) */
     int levels;                   /* multigrid levels (finest .. 3 nodes per side) */
     double relres;                /* recursive ||r_k|| / ||b|| at exit */
     double true_relres;           /* ||b - A x|| / ||b|| at exit, FP64 */
@@ -91,6 +96,8 @@ typedef struct {
     double grid_complexity;       /* sum_l N_l / N_0 (Sec. 4) */
     double operator_complexity;   /* sum_l stored_l / stored_0 (symmetric storage) */
     int status;                   /* bmg_status of the solve */
+    int refinements;              /* FP64 residual evaluations after the first
+                                     (BMG_OUTER_REFINEMENT), else 0 */
 } bmg_info;
 
 /* Defaults: dim 2, precision FP64, outer CG (flexible CG when FP32). */

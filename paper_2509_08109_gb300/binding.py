@@ -19,7 +19,7 @@ LIB_PATH = os.path.join(_HERE, "libbmg.so")
 _lib = None
 
 PREC = {"fp64": 0, "fp32": 1}
-OUTER = {"cg": 0, "flexible": 1}
+OUTER = {"cg": 0, "flexible": 1, "refine": 2}
 
 STATUS = {0: "ok", 1: "invalid argument", 2: "unsupported shape", 3: "CUDA runtime error",
           4: "workspace missing or too small", 5: "map folded", 6: "setup breakdown",
@@ -41,7 +41,7 @@ class _Info(ctypes.Structure):
     _fields_ = [("iterations", ctypes.c_int), ("levels", ctypes.c_int), ("relres", ctypes.c_double),
                 ("true_relres", ctypes.c_double), ("rho", ctypes.c_double),
                 ("grid_complexity", ctypes.c_double), ("operator_complexity", ctypes.c_double),
-                ("status", ctypes.c_int)]
+                ("status", ctypes.c_int), ("refinements", ctypes.c_int)]
 
 
 @dataclass
@@ -54,6 +54,7 @@ class SolveInfo:
     grid_complexity: float
     operator_complexity: float
     status: int
+    refinements: int = 0
 
 
 def load() -> ctypes.CDLL:
@@ -115,8 +116,10 @@ def _ptr(t: torch.Tensor):
 class Solver:
     """One structured problem: n nodes per side in dim dimensions.
 
-    precision: 'fp64' (plain) or 'fp32' (FP32 V-cycle, FP64 outer CG).
-    outer: 'cg' or 'flexible' (default: 'cg' for fp64, 'flexible' for fp32).
+    precision: 'fp64' (plain) or 'fp32' (FP32 V-cycle).
+    outer: 'cg', 'flexible' (FP64 flexible CG around the FP32 V-cycle) or
+    'refine' (FP64 iterative refinement around an FP32 CG; fp32 only).
+    Default: 'cg' for fp64, 'flexible' for fp32.
     """
 
     def __init__(self, dim: int, n: int, precision: str = "fp64", outer: str | None = None,
@@ -214,7 +217,7 @@ class Solver:
         if code not in (0, 8) or (code == 8 and raise_on_nonconv):
             _check(code, "bmg_solve")
         return out, SolveInfo(info.iterations, info.levels, info.relres, info.true_relres, info.rho,
-                              info.grid_complexity, info.operator_complexity, info.status)
+                              info.grid_complexity, info.operator_complexity, info.status, info.refinements)
 
     def adjoint_grad(self, u, dLdu, tol: float = 1e-10, maxit: int = 500):
         """(lambda, dL/dkappa per cell, info) for A lambda = dL/du."""

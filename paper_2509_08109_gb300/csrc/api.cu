@@ -68,6 +68,14 @@ size_t carve(Ctx& c, char* base) {
     c.z[1] = (double*)take(sizeof(double) * pl0);
     c.p = (double*)take(sizeof(double) * pl0);
     c.q = (double*)take(sizeof(double) * pl0);
+    if (c.opts.outer == BMG_OUTER_REFINEMENT) {
+        c.r32 = (float*)take(sizeof(float) * pl0);
+        c.d32 = (float*)take(sizeof(float) * pl0);
+        c.z32[0] = (float*)take(sizeof(float) * pl0);
+        c.z32[1] = (float*)take(sizeof(float) * pl0);
+        c.p32 = (float*)take(sizeof(float) * pl0);
+        c.q32 = (float*)take(sizeof(float) * pl0);
+    }
     const long long nn = ipow(c.lev[0].n, c.dim);
     c.stage_in = (double*)take(sizeof(double) * nn);
     c.stage_out = (double*)take(sizeof(double) * nn);
@@ -123,8 +131,78 @@ void fill_complexity(const Ctx& c, bmg_info* info) {
     info->operator_complexity = s / n0;   // same stored entries per node on every level
 }
 
+// Iterative refinement: FP64 residual, inner FP32 flexible CG (FP32 V-cycle)
+// on A d = r for m iterations, x += d; m is chosen from the contraction seen
+// so far so that one inner solve aims at the remaining reduction (bounded
+// below by what FP32 can deliver).  maxit caps the total inner iterations.
+bmg_status pcg_ir(Ctx& c, double tol, int maxit, bmg_info* info) {
+    KState h;
+    BMG_TRY(reset_state(c));
+    BMG_TRY(k_dot(c, c.bvec, c.bvec, &c.st->bb));
+    BMG_CUDA(cudaMemsetAsync(c.d32, 0, sizeof(float) * c.lev[0].plane, c.stream));
+    BMG_TRY(k_residual_to32(c));
+    BMG_TRY(read_state(c, h));
+    const double bb = h.bb;
+    double rr = h.rr;
+    const double rr0 = rr;
+    int it = 0, refinements = 0;
+    bmg_status status = BMG_OK;
+    double rho = 0.3;                 // contraction per inner iteration, updated as we go
+    const double floor_red = 1e-6;    // reduction one FP32 inner solve can deliver
+    if (bb == 0.0) {
+        BMG_CUDA(cudaMemsetAsync(c.x, 0, sizeof(double) * c.lev[0].plane, c.stream));
+        rr = 0.0;
+    } else {
+        const double lim = tol > 0 ? tol * tol * bb : -1.0;
+        while (!(rr <= lim) && it < maxit) {
+            double want = tol > 0 ? sqrt(lim / rr) : floor_red;
+            if (want < floor_red) want = floor_red;
+            int m = (int)ceil(log(want) / log(rho)) + 1;
+            if (m < 2) m = 2;
+            if (m > 40) m = 40;
+            if (m > maxit - it) m = maxit - it;
+            for (int k = 0; k < m; k++) {
+                float* zn = c.z32[(it + k) & 1];
+                float* zo = c.z32[(it + k + 1) & 1];
+                BMG_TRY(vcycle_f32(c, zn));
+                BMG_TRY(k_rz_beta32(c, zn, zo));
+                BMG_TRY(k_p_update32(c, zn));
+                BMG_TRY(k_spmv_pq32(c));
+                BMG_TRY(k_update_dr32(c));
+            }
+            it += m;
+            BMG_TRY(k_add_correction(c));
+            BMG_TRY(k_residual_to32(c));
+            BMG_TRY(read_state(c, h));
+            refinements++;
+            if (h.err) {
+                status = (bmg_status)h.err;
+                break;
+            }
+            const double red = sqrt(h.rr / rr);
+            if (red > 0 && red < 1) {
+                const double r1 = pow(red, 1.0 / m);
+                if (r1 > 0.02 && r1 < 0.95) rho = r1;
+            }
+            rr = h.rr;
+        }
+        if (status == BMG_OK && tol > 0 && !(rr <= lim)) status = BMG_ERR_NOT_CONVERGED;
+    }
+    if (info) {
+        info->iterations = it;
+        info->refinements = refinements;
+        info->relres = bb > 0 ? sqrt(rr / bb) : 0.0;
+        info->true_relres = info->relres;   // the FP64 residual of the final iterate
+        info->rho = (it > 0 && rr0 > 0 && rr > 0) ? pow(rr / rr0, 0.5 / it) : 0.0;
+        fill_complexity(c, info);
+        info->status = status;
+    }
+    return status;
+}
+
 // PCG with M = one V-cycle.  x (padded, in c.x) holds the initial guess.
 bmg_status pcg(Ctx& c, double tol, int maxit, bmg_info* info) {
+    if (c.opts.outer == BMG_OUTER_REFINEMENT) return pcg_ir(c, tol, maxit, info);
     const bool flexible = c.opts.outer == BMG_OUTER_FLEXIBLE_CG;
     BMG_TRY(reset_state(c));
     KState h;
@@ -172,6 +250,7 @@ bmg_status pcg(Ctx& c, double tol, int maxit, bmg_info* info) {
     }
     if (info) {
         info->iterations = it;
+        info->refinements = 0;
         info->relres = bb > 0 ? sqrt(rr / bb) : 0.0;
         info->rho = (it > 0 && rr0 > 0 && rr > 0) ? pow(rr / rr0, 0.5 / it) : 0.0;
         // true residual of the final iterate, into q (scratch)
@@ -205,7 +284,9 @@ bmg_status bmg_create(const bmg_opts* opts, bmg_ctx** out) {
     const int n = opts->n;
     if (n < 3 || ((n - 1) & (n - 2)) != 0) return BMG_ERR_SHAPE;
     if (opts->precision != BMG_PREC_FP64 && opts->precision != BMG_PREC_FP32) return BMG_ERR_ARG;
-    if (opts->outer != BMG_OUTER_CG && opts->outer != BMG_OUTER_FLEXIBLE_CG) return BMG_ERR_ARG;
+    if (opts->outer != BMG_OUTER_CG && opts->outer != BMG_OUTER_FLEXIBLE_CG && opts->outer != BMG_OUTER_REFINEMENT)
+        return BMG_ERR_ARG;
+    if (opts->outer == BMG_OUTER_REFINEMENT && opts->precision != BMG_PREC_FP32) return BMG_ERR_ARG;
     bmg_ctx* ctx = new (std::nothrow) bmg_ctx();
     if (!ctx) return BMG_ERR_ARG;
     Ctx& c = ctx->c;

@@ -34,7 +34,7 @@ namespace bmg {
 
 constexpr int kMaxLevels = 20;
 constexpr int kThreads = 256;
-constexpr int kMaxBlocks = 2048;       // partials buffer size for reductions
+constexpr int kMaxBlocks = 4096;       // partials buffer size for reductions (two sums per block)
 
 enum Plane2 { C2 = 0, W2 = 1, S2 = 2, SW2 = 3, NW2 = 4, NS2 = 5 };
 enum PPlane2 { PXL = 0, PXR = 1, PYS = 2, PYN = 3, PSW = 4, PSE = 5, PNW = 6, PNE = 7, NP2 = 8 };
@@ -90,6 +90,9 @@ struct Ctx {
     double *bvec = nullptr, *x = nullptr, *r = nullptr, *z[2] = {nullptr, nullptr};
     double *p = nullptr, *q = nullptr;
     double *stage_in = nullptr, *stage_out = nullptr;   // n^d doubles each, host staging
+    // iterative refinement: FP32 inner CG vectors
+    float *r32 = nullptr, *d32 = nullptr, *z32[2] = {nullptr, nullptr}, *p32 = nullptr, *q32 = nullptr;
+    FusedLevel fused_ir0;         // level-0 streaming kernels reading r32 (FP32)
     double* partials = nullptr;
     KState* st = nullptr;         // device
     KState* st_host = nullptr;    // pinned mirror
@@ -179,6 +182,38 @@ __device__ __forceinline__ double block_sum(double v) {
     return s;
 }
 
+// Two sums at once (same scheme as grid_sum; partials holds 2 per block).
+__device__ __forceinline__ bool grid_sum2(double v1, double v2, double* partials, unsigned int* counter,
+                                          double* t1, double* t2) {
+    __shared__ bool last2;
+    double b1 = block_sum(v1);
+    double b2 = block_sum(v2);
+    if (threadIdx.x == 0) {
+        partials[2 * blockIdx.x] = b1;
+        partials[2 * blockIdx.x + 1] = b2;
+        __threadfence();
+        unsigned int t = atomicAdd(counter, 1u);
+        last2 = (t == gridDim.x - 1);
+    }
+    __syncthreads();
+    if (!last2) return false;
+    __threadfence();
+    double s1 = 0.0, s2 = 0.0;
+    for (int k = threadIdx.x; k < (int)gridDim.x; k += blockDim.x) {
+        s1 += ((volatile double*)partials)[2 * k];
+        s2 += ((volatile double*)partials)[2 * k + 1];
+    }
+    s1 = block_sum(s1);
+    s2 = block_sum(s2);
+    if (threadIdx.x == 0) {
+        *counter = 0u;
+        *t1 = s1;
+        *t2 = s2;
+        return true;
+    }
+    return false;
+}
+
 // Deterministic grid reduction: each block stores its partial; the last
 // block to arrive sums the partials in a fixed order.  Returns true (in
 // thread 0 of the last block only) with the total in *total.
@@ -228,8 +263,9 @@ int fused_rows_per_step(bool f32);
 int fused_down_smem(bool f32, bool f64in, int wc);
 int fused_up_smem(bool f32, bool f64in, int wc);
 bmg_status fused_occupancy(bool f32, bool f64in, int wc, int* down_blocks, int* up_blocks);
-bmg_status fused_down(Ctx& c, int l);
-bmg_status fused_up(Ctx& c, int l, void* out);
+bmg_status fused_down(Ctx& c, int l, bool ir = false);
+bmg_status fused_up(Ctx& c, int l, void* out, bool ir = false);
+bmg_status vcycle_f32(Ctx& c, float* z32);       // z32 = M r32 (FP32 in and out)
 bmg_status fused_prepare(Ctx& c);
 bmg_status demote_levels(Ctx& c);
 // krylov.cu
@@ -241,5 +277,12 @@ bmg_status k_spmv_pq(Ctx& c, const double* p, double* q);        // q = A p; alp
 bmg_status k_update_xr(Ctx& c);                                   // x += alpha p; r -= alpha q; rr
 bmg_status k_rz_beta(Ctx& c, const double* z, const double* zold, bool flexible);
 bmg_status k_p_update(Ctx& c, const double* z);                   // p = z + beta p (or z)
+// FP32 inner CG of the refinement mode
+bmg_status k_residual_to32(Ctx& c);             // r32 = (float)(b - A x); rr; resets the inner CG state
+bmg_status k_add_correction(Ctx& c);            // x += d32; d32 = 0
+bmg_status k_rz_beta32(Ctx& c, const float* z, const float* zo);
+bmg_status k_p_update32(Ctx& c, const float* z);
+bmg_status k_spmv_pq32(Ctx& c);
+bmg_status k_update_dr32(Ctx& c);
 
 }  // namespace bmg

@@ -35,7 +35,6 @@
 namespace bmg {
 namespace {
 
-constexpr int kNT = 128;                      // threads per CTA
 constexpr unsigned long long kWaitNs = 2000000000ull;   // 2 s
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
@@ -618,19 +617,19 @@ bmg_status fused_occupancy(bool f32, bool f64in, int wc, int* down_blocks, int* 
     return BMG_OK;
 }
 
-bmg_status fused_down(Ctx& c, int l) {
-    const FusedLevel& F = c.fused[l];
+bmg_status fused_down(Ctx& c, int l, bool ir) {
+    const FusedLevel& F = (ir && l == 0) ? c.fused_ir0 : c.fused[l];
     const bool f32 = c.opts.precision == BMG_PREC_FP32;
     if (!f32) return launch_down<double, double>(c, F, c.stream);
-    if (l == 0) return launch_down<float, double>(c, F, c.stream);
+    if (l == 0 && !ir) return launch_down<float, double>(c, F, c.stream);
     return launch_down<float, float>(c, F, c.stream);
 }
 
-bmg_status fused_up(Ctx& c, int l, void* out) {
-    const FusedLevel& F = c.fused[l];
+bmg_status fused_up(Ctx& c, int l, void* out, bool ir) {
+    const FusedLevel& F = (ir && l == 0) ? c.fused_ir0 : c.fused[l];
     const bool f32 = c.opts.precision == BMG_PREC_FP32;
     if (!f32) return launch_up<double, double, double>(c, F, c.stream, out);
-    if (l == 0) return launch_up<float, double, double>(c, F, c.stream, out);
+    if (l == 0 && !ir) return launch_up<float, double, double>(c, F, c.stream, out);
     return launch_up<float, float, float>(c, F, c.stream, out);
 }
 

@@ -136,7 +136,171 @@ __global__ void k_p_update(long long tot, const double* __restrict__ z, double* 
         p[k] = z[k] + beta * p[k];
 }
 
+// ---------------------------------------------------------------- refinement (FP32 inner CG)
+// r32 = (float)(b - A x), ||r||^2 in FP64; resets the inner CG to its first step.
+__global__ void k_residual_to32(Grid2 g, const double* __restrict__ A, long long pl, const double* __restrict__ b,
+                                const double* __restrict__ x, float* __restrict__ r32, double* partials, KState* st) {
+    double acc = 0.0;
+    for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < pl;
+         k += (long long)gridDim.x * blockDim.x) {
+        int i, j;
+        double v = 0.0;
+        if (g.interior(k, i, j)) v = b[k] - apply_row2d(A, pl, g.ld, x, k);
+        r32[k] = (float)v;
+        acc += v * v;
+    }
+    double t;
+    if (grid_sum(acc, partials, &st->counter[0], &t)) {
+        st->rr = t;
+        st->first = 1;
+    }
+}
+
+// x += d (FP64 += FP32), d = 0
+__global__ void k_add_correction(long long tot, double* __restrict__ x, float* __restrict__ d) {
+    for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < tot;
+         k += (long long)gridDim.x * blockDim.x) {
+        x[k] += (double)d[k];
+        d[k] = 0.0f;
+    }
+}
+
+__device__ __forceinline__ float apply_row2d_f(const float* __restrict__ A, long long pl, int ld,
+                                               const float* __restrict__ x, long long o) {
+    float s = A[C2 * pl + o] * x[o];
+    s += A[W2 * pl + o] * x[o - 1];
+    s += A[W2 * pl + o + 1] * x[o + 1];
+    s += A[S2 * pl + o] * x[o - ld];
+    s += A[S2 * pl + o + ld] * x[o + ld];
+    s += A[SW2 * pl + o] * x[o - ld - 1];
+    s += A[SW2 * pl + o + ld + 1] * x[o + ld + 1];
+    s += A[NW2 * pl + o] * x[o + ld - 1];
+    s += A[NW2 * pl + o - ld + 1] * x[o - ld + 1];
+    return s;
+}
+
+// q = A p (FP32 operator), alpha = rz / p.q; per-thread sums in FP32, block and
+// grid sums in FP64.
+__global__ void k_spmv_pq32(Grid2 g, const float* __restrict__ A, long long pl, const float* __restrict__ p,
+                            float* __restrict__ q, double* partials, KState* st) {
+    float acc = 0.0f;
+    for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < pl;
+         k += (long long)gridDim.x * blockDim.x) {
+        int i, j;
+        float v = 0.0f;
+        if (g.interior(k, i, j)) v = apply_row2d_f(A, pl, g.ld, p, k);
+        q[k] = v;
+        acc += p[k] * v;
+    }
+    double t;
+    if (grid_sum((double)acc, partials, &st->counter[2], &t)) {
+        st->pq = t;
+        if (!(t > 0.0)) {
+            set_err(st, BMG_ERR_NOT_SPD);
+            st->alpha = 0.0;
+        } else {
+            st->alpha = st->rz / t;
+        }
+    }
+}
+
+// d += alpha p; r -= alpha q
+__global__ void k_update_dr32(long long tot, float* __restrict__ d, float* __restrict__ r,
+                              const float* __restrict__ p, const float* __restrict__ q, const KState* st) {
+    const float alpha = (float)st->alpha;
+    for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < tot;
+         k += (long long)gridDim.x * blockDim.x) {
+        d[k] += alpha * p[k];
+        r[k] -= alpha * q[k];
+    }
+}
+
+// r.z and r.z_old in one pass; the last block forms the flexible-CG beta
+__global__ void k_rz_beta32(long long tot, const float* __restrict__ r, const float* __restrict__ z,
+                            const float* __restrict__ zo, double* partials, KState* st) {
+    float a1 = 0.0f, a2 = 0.0f;
+    for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < tot;
+         k += (long long)gridDim.x * blockDim.x) {
+        const float rv = r[k];
+        a1 += rv * z[k];
+        a2 += rv * zo[k];
+    }
+    double t1, t2;
+    if (grid_sum2((double)a1, (double)a2, partials, &st->counter[4], &t1, &t2)) {
+        if (st->first) {
+            st->beta = 0.0;
+            st->first = 0;
+        } else {
+            st->beta = (t1 - t2) / st->rz;
+        }
+        st->rz = t1;
+    }
+}
+
+__global__ void k_p_update32(long long tot, const float* __restrict__ z, float* __restrict__ p, const KState* st) {
+    const float beta = (float)st->beta;
+    for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < tot;
+         k += (long long)gridDim.x * blockDim.x)
+        p[k] = z[k] + beta * p[k];
+}
+
 }  // namespace
+
+bmg_status k_residual_to32(Ctx& c) {
+    const Level& L = c.lev[0];
+    k_residual_to32<<<c.red_blocks, kThreads, 0, c.stream>>>(Grid2{L.n, L.ld}, L.A64, L.plane, c.bvec, c.x, c.r32,
+                                                              c.partials, c.st);
+    c.launches++;
+    BMG_CUDA(cudaGetLastError());
+    return BMG_OK;
+}
+
+bmg_status k_add_correction(Ctx& c) {
+    const Level& L = c.lev[0];
+    k_add_correction<<<c.red_blocks, kThreads, 0, c.stream>>>(L.plane, c.x, c.d32);
+    c.launches++;
+    BMG_CUDA(cudaGetLastError());
+    return BMG_OK;
+}
+
+bmg_status k_rz_beta32(Ctx& c, const float* z, const float* zo) {
+    const Level& L = c.lev[0];
+    k_rz_beta32<<<c.red_blocks, kThreads, 0, c.stream>>>(L.plane, c.r32, z, zo, c.partials, c.st);
+    c.launches++;
+    BMG_CUDA(cudaGetLastError());
+    return BMG_OK;
+}
+
+bmg_status k_p_update32(Ctx& c, const float* z) {
+    const Level& L = c.lev[0];
+    k_p_update32<<<c.red_blocks, kThreads, 0, c.stream>>>(L.plane, z, c.p32, c.st);
+    c.launches++;
+    BMG_CUDA(cudaGetLastError());
+    return BMG_OK;
+}
+
+bmg_status k_spmv_pq32(Ctx& c) {
+    const Level& L = c.lev[0];
+    const double N = (double)(L.n - 2) * (L.n - 2);
+    prof_begin(c, BMG_PROF_SPMV, 0);
+    k_spmv_pq32<<<c.red_blocks, kThreads, 0, c.stream>>>(Grid2{L.n, L.ld}, L.A32, L.plane, c.p32, c.q32, c.partials,
+                                                          c.st);
+    prof_end(c, BMG_PROF_SPMV, 0, (c.ns + 2) * 4.0 * N);
+    c.launches++;
+    BMG_CUDA(cudaGetLastError());
+    return BMG_OK;
+}
+
+bmg_status k_update_dr32(Ctx& c) {
+    const Level& L = c.lev[0];
+    const double N = (double)(L.n - 2) * (L.n - 2);
+    prof_begin(c, BMG_PROF_UPDATE, 0);
+    k_update_dr32<<<c.red_blocks, kThreads, 0, c.stream>>>(L.plane, c.d32, c.r32, c.p32, c.q32, c.st);
+    prof_end(c, BMG_PROF_UPDATE, 0, 6 * 4.0 * N);
+    c.launches++;
+    BMG_CUDA(cudaGetLastError());
+    return BMG_OK;
+}
 
 bmg_status k_pack(Ctx& c, const double* src, double* dst) {
     const Level& L = c.lev[0];

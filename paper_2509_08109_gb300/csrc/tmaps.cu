@@ -86,6 +86,14 @@ bmg_status fused_prepare(Ctx& c) {
         F.down = FusedArgs{Lf.n, Lc.n, Lf.ld, Lc.ld, F.wc, F.hc, Lf.x, Lc.b, P, Lc.plane, c.st};
         F.up = FusedArgs{Lf.n, Lc.n, Lf.ld, Lc.ld, F.wc, F.hc, nullptr, nullptr, P, Lc.plane, c.st};
         F.ready = true;
+        if (l == 0 && c.r32) {
+            // refinement mode: the level-0 kernels read the FP32 inner residual
+            FusedLevel& G = c.fused_ir0;
+            G = F;
+            int od2 = 0, ou2 = 0;
+            BMG_TRY(fused_occupancy(true, false, F.wc, &od2, &ou2));
+            if (!make_map(&G.mF, false, c.r32, Lf.ld, Lf.n, 1, Lf.plane, WW, 2)) return BMG_ERR_DEVICE;
+        }
     }
     return BMG_OK;
 }

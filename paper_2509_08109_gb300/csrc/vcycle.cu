@@ -193,16 +193,16 @@ bmg_status vcycle2d_impl(Ctx& c, const T* b0, T* x0) {
 
 // Streaming path: one down kernel and one up kernel per level pair.
 template <typename T>
-bmg_status vcycle2d_fused(Ctx& c, double* z) {
+bmg_status vcycle2d_fused(Ctx& c, void* z, bool ir = false) {
     cudaStream_t s = c.stream;
     const int L = c.nlev;
     const double sz = sizeof(T);
     const bool f32 = sizeof(T) == 4;
     for (int l = 0; l < L - 1; l++) {
         const double N = dofs(c, l);
-        const double szf = l == 0 ? 8.0 : sz;
+        const double szf = (l == 0 && !ir) ? 8.0 : sz;
         prof_begin(c, BMG_PROF_VDOWN, l);
-        BMG_TRY(fused_down(c, l));
+        BMG_TRY(fused_down(c, l, ir));
         prof_end(c, BMG_PROF_VDOWN, l, N * (c.ns * sz + szf + sz + c.np / 4.0 * sz + sz / 4));
     }
     {
@@ -213,10 +213,10 @@ bmg_status vcycle2d_fused(Ctx& c, double* z) {
     }
     for (int l = L - 2; l >= 0; l--) {
         const double N = dofs(c, l);
-        const double szf = l == 0 ? 8.0 : sz;
-        const double szo = l == 0 ? 8.0 : sz;
+        const double szf = (l == 0 && !ir) ? 8.0 : sz;
+        const double szo = (l == 0 && !ir) ? 8.0 : sz;
         prof_begin(c, BMG_PROF_VUP, l);
-        BMG_TRY(fused_up(c, l, l == 0 ? (void*)z : c.lev[l].r));
+        BMG_TRY(fused_up(c, l, l == 0 ? z : c.lev[l].r, ir));
         prof_end(c, BMG_PROF_VUP, l, N * (c.ns * sz + szf + sz + c.np / 4.0 * sz + sz / 4 + szo));
     }
     (void)f32;
@@ -240,6 +240,12 @@ bmg_status demote_levels(Ctx& c) {
     }
     BMG_CUDA(cudaGetLastError());
     return BMG_OK;
+}
+
+bmg_status vcycle_f32(Ctx& c, float* z32) {
+    if (c.dim != 2 || c.opts.precision != BMG_PREC_FP32) return BMG_ERR_STATE;
+    if (c.use_fused && c.nlev >= 2) return vcycle2d_fused<float>(c, z32, true);
+    return vcycle2d_impl<float>(c, c.r32, z32);
 }
 
 bmg_status vcycle(Ctx& c, const double* r, double* z) {

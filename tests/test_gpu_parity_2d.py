@@ -218,3 +218,24 @@ def test_fused_fp32_solve_matches_unfused_iterations():
     xb, ib = b.solve(f, tol=1e-10)
     assert ia.true_relres <= 1e-10 and ib.true_relres <= 1e-10
     assert abs(ia.iterations - ib.iterations) <= 1
+
+
+# ------------------------------------------------------------------ iterative refinement
+@pytest.mark.parametrize("n,unfused", [(65, False), (257, False), (257, True), (1025, False)])
+def test_refinement_reaches_fp64_tolerance(n, unfused):
+    """FP32 inner CG + FP32 V-cycle, FP64 residual and update: the FP64 true
+    residual meets 1e-10 and the solution agrees with the oracle's."""
+    p = _problem(n)
+    s = solver_for(p, precision="fp32", outer="refine", unfused=unfused)
+    x, info = s.solve(torch.as_tensor(p.rhs, device="cuda"), tol=1e-10, maxit=300)
+    assert info.true_relres <= 1e-10 and info.refinements >= 2
+    if n <= 257:
+        H = oracle.Hierarchy(oracle.assemble(p.coords, p.kappa))
+        xo = H.pcg(p.rhs, tol=1e-12, maxit=300)[0]
+        assert relerr(x.cpu().numpy(), xo) <= 1e-7
+    # the reported residual is the FP64 one: recompute it with the oracle operator
+    if n <= 257:
+        A = oracle.assemble(p.coords, p.kappa)
+        r = p.rhs - oracle.apply(A, x.cpu().numpy())
+        r[0, :] = r[-1, :] = r[:, 0] = r[:, -1] = 0
+        assert np.linalg.norm(r) / np.linalg.norm(p.rhs) <= 1.01e-10
