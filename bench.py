@@ -288,7 +288,7 @@ def run_own(args):
 
     out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
            "warmup": args.warmup, "ms_per_step": t32, "higher_is_better": True, "scaling": "weak",
-           "vs_baseline": None, "dtype": "f32 V-cycle / f64 CG", "data": "synthetic",
+           "vs_baseline": None, "dtype": "f32 V-cycle / f64 residual", "data": "synthetic",
            "config": config_for(n), "e2e": e2e, "gpu_launches": launches32,
            "headline_variant": head,
            "iterations": infos32[-1].iterations, "true_relres": infos32[-1].true_relres,
