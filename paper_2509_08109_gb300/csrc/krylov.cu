@@ -23,14 +23,9 @@ __device__ __forceinline__ double apply_row2d(const double* __restrict__ A, long
     return s;
 }
 
-// grid-stride over the padded layout; interior test per element
+// row-wise traversal of the padded layout (row j, column i)
 struct Grid2 {
     int n, ld;
-    __device__ __forceinline__ bool interior(long long k, int& i, int& j) const {
-        j = (int)(k / ld);
-        i = (int)(k - (long long)j * ld);
-        return i >= 1 && j >= 1 && i <= n - 2 && j <= n - 2;
-    }
 };
 
 __global__ void k_pack2d(int n, int ld, const double* __restrict__ src, double* __restrict__ dst) {
@@ -52,14 +47,15 @@ __global__ void k_unpack2d(int n, int ld, const double* __restrict__ src, double
 __global__ void k_residual64(Grid2 g, const double* __restrict__ A, long long pl, const double* __restrict__ b,
                              const double* __restrict__ x, double* __restrict__ r, double* partials, KState* st) {
     double acc = 0.0;
-    const long long tot = pl;
-    for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < tot;
-         k += (long long)gridDim.x * blockDim.x) {
-        int i, j;
-        double v = 0.0;
-        if (g.interior(k, i, j)) v = b[k] - apply_row2d(A, pl, g.ld, x, k);
-        r[k] = v;
-        acc += v * v;
+    for (int j = blockIdx.x; j < g.n; j += gridDim.x) {
+        const bool rj = j >= 1 && j <= g.n - 2;
+        for (int i = threadIdx.x; i < g.ld; i += blockDim.x) {
+            const long long k = (long long)j * g.ld + i;
+            double v = 0.0;
+            if (rj && i >= 1 && i <= g.n - 2) v = b[k] - apply_row2d(A, pl, g.ld, x, k);
+            r[k] = v;
+            acc += v * v;
+        }
     }
     double t;
     if (grid_sum(acc, partials, &st->counter[0], &t)) st->rr = t;
@@ -79,13 +75,15 @@ __global__ void k_dot64(long long tot, const double* __restrict__ a, const doubl
 __global__ void k_spmv_pq(Grid2 g, const double* __restrict__ A, long long pl, const double* __restrict__ p,
                           double* __restrict__ q, double* partials, KState* st) {
     double acc = 0.0;
-    for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < pl;
-         k += (long long)gridDim.x * blockDim.x) {
-        int i, j;
-        double v = 0.0;
-        if (g.interior(k, i, j)) v = apply_row2d(A, pl, g.ld, p, k);
-        q[k] = v;
-        acc += p[k] * v;
+    for (int j = blockIdx.x; j < g.n; j += gridDim.x) {
+        const bool rj = j >= 1 && j <= g.n - 2;
+        for (int i = threadIdx.x; i < g.ld; i += blockDim.x) {
+            const long long k = (long long)j * g.ld + i;
+            double v = 0.0;
+            if (rj && i >= 1 && i <= g.n - 2) v = apply_row2d(A, pl, g.ld, p, k);
+            q[k] = v;
+            acc += p[k] * v;
+        }
     }
     double t;
     if (grid_sum(acc, partials, &st->counter[2], &t)) {
@@ -141,13 +139,15 @@ __global__ void k_p_update(long long tot, const double* __restrict__ z, double* 
 __global__ void k_residual_to32(Grid2 g, const double* __restrict__ A, long long pl, const double* __restrict__ b,
                                 const double* __restrict__ x, float* __restrict__ r32, double* partials, KState* st) {
     double acc = 0.0;
-    for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < pl;
-         k += (long long)gridDim.x * blockDim.x) {
-        int i, j;
-        double v = 0.0;
-        if (g.interior(k, i, j)) v = b[k] - apply_row2d(A, pl, g.ld, x, k);
-        r32[k] = (float)v;
-        acc += v * v;
+    for (int j = blockIdx.x; j < g.n; j += gridDim.x) {
+        const bool rj = j >= 1 && j <= g.n - 2;
+        for (int i = threadIdx.x; i < g.ld; i += blockDim.x) {
+            const long long k = (long long)j * g.ld + i;
+            double v = 0.0;
+            if (rj && i >= 1 && i <= g.n - 2) v = b[k] - apply_row2d(A, pl, g.ld, x, k);
+            r32[k] = (float)v;
+            acc += v * v;
+        }
     }
     double t;
     if (grid_sum(acc, partials, &st->counter[0], &t)) {
@@ -184,13 +184,15 @@ __device__ __forceinline__ float apply_row2d_f(const float* __restrict__ A, long
 __global__ void k_spmv_pq32(Grid2 g, const float* __restrict__ A, long long pl, const float* __restrict__ p,
                             float* __restrict__ q, double* partials, KState* st) {
     float acc = 0.0f;
-    for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < pl;
-         k += (long long)gridDim.x * blockDim.x) {
-        int i, j;
-        float v = 0.0f;
-        if (g.interior(k, i, j)) v = apply_row2d_f(A, pl, g.ld, p, k);
-        q[k] = v;
-        acc += p[k] * v;
+    for (int j = blockIdx.x; j < g.n; j += gridDim.x) {
+        const bool rj = j >= 1 && j <= g.n - 2;
+        for (int i = threadIdx.x; i < g.ld; i += blockDim.x) {
+            const long long k = (long long)j * g.ld + i;
+            float v = 0.0f;
+            if (rj && i >= 1 && i <= g.n - 2) v = apply_row2d_f(A, pl, g.ld, p, k);
+            q[k] = v;
+            acc += p[k] * v;
+        }
     }
     double t;
     if (grid_sum((double)acc, partials, &st->counter[2], &t)) {
