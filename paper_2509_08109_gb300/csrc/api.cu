@@ -75,6 +75,7 @@ size_t carve(Ctx& c, char* base) {
         c.z32[1] = (float*)take(sizeof(float) * pl0);
         c.p32 = (float*)take(sizeof(float) * pl0);
         c.q32 = (float*)take(sizeof(float) * pl0);
+        c.rs32 = (float*)take(sizeof(float) * pl0);
     }
     const long long nn = ipow(c.lev[0].n, c.dim);
     c.stage_in = (double*)take(sizeof(double) * nn);
@@ -377,6 +378,7 @@ bmg_status bmg_setup(bmg_ctx* ctx) {
     BMG_TRY(reset_state(c));
     for (int l = 0; l < c.nlev - 1; l++) BMG_TRY(setup_level2d(c, l));
     BMG_TRY(demote_levels(c));
+    if (c.rs32) BMG_TRY(k_row_sums32(c));
     KState h;
     BMG_TRY(read_state(c, h));
     if (h.err) {

@@ -92,6 +92,7 @@ struct Ctx {
     double *stage_in = nullptr, *stage_out = nullptr;   // n^d doubles each, host staging
     // iterative refinement: FP32 inner CG vectors
     float *r32 = nullptr, *d32 = nullptr, *z32[2] = {nullptr, nullptr}, *p32 = nullptr, *q32 = nullptr;
+    float* rs32 = nullptr;        // FP32 row sums of the finest operator (difference-form products)
     FusedLevel fused_ir0;         // level-0 streaming kernels reading r32 (FP32)
     double* partials = nullptr;
     KState* st = nullptr;         // device
@@ -278,6 +279,7 @@ bmg_status k_update_xr(Ctx& c);                                   // x += alpha 
 bmg_status k_rz_beta(Ctx& c, const double* z, const double* zold, bool flexible);
 bmg_status k_p_update(Ctx& c, const double* z);                   // p = z + beta p (or z)
 // FP32 inner CG of the refinement mode
+bmg_status k_row_sums32(Ctx& c);                // rs32 = row sums of A (computed in FP64)
 bmg_status k_residual_to32(Ctx& c);             // r32 = (float)(b - A x); rr; resets the inner CG state
 bmg_status k_add_correction(Ctx& c);            // x += d32; d32 = 0
 bmg_status k_rz_beta32(Ctx& c, const float* z, const float* zo);

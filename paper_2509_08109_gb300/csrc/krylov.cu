@@ -165,31 +165,50 @@ __global__ void k_add_correction(long long tot, double* __restrict__ x, float* _
     }
 }
 
-__device__ __forceinline__ float apply_row2d_f(const float* __restrict__ A, long long pl, int ld,
-                                               const float* __restrict__ x, long long o) {
-    float s = A[C2 * pl + o] * x[o];
-    s += A[W2 * pl + o] * x[o - 1];
-    s += A[W2 * pl + o + 1] * x[o + 1];
-    s += A[S2 * pl + o] * x[o - ld];
-    s += A[S2 * pl + o + ld] * x[o + ld];
-    s += A[SW2 * pl + o] * x[o - ld - 1];
-    s += A[SW2 * pl + o + ld + 1] * x[o + ld + 1];
-    s += A[NW2 * pl + o] * x[o + ld - 1];
-    s += A[NW2 * pl + o - ld + 1] * x[o - ld + 1];
+// Row sums s_i = sum_j a_ij of the FP64 operator, stored in FP32.
+__global__ void k_row_sums32(Grid2 g, const double* __restrict__ A, long long pl, float* __restrict__ rs) {
+    for (int j = blockIdx.x; j < g.n; j += gridDim.x)
+        for (int i = threadIdx.x; i < g.ld; i += blockDim.x) {
+            const long long o = (long long)j * g.ld + i;
+            double s = 0.0;
+            if (j >= 1 && j <= g.n - 2 && i >= 1 && i <= g.n - 2) {
+                s = A[C2 * pl + o] + A[W2 * pl + o] + A[W2 * pl + o + 1] + A[S2 * pl + o] + A[S2 * pl + o + g.ld] +
+                    A[SW2 * pl + o] + A[SW2 * pl + o + g.ld + 1] + A[NW2 * pl + o] + A[NW2 * pl + o - g.ld + 1];
+            }
+            rs[o] = (float)s;
+        }
+}
+
+// (A p)_i in difference form: s_i p_i + sum_{j != i} a_ij (p_j - p_i).  The
+// operator's rows nearly sum to zero, so the plain FP32 product loses the
+// smooth part of A p to cancellation; the differences keep FP32 relative
+// accuracy on every mode.
+__device__ __forceinline__ float apply_row2d_diff(const float* __restrict__ A, const float* __restrict__ rs,
+                                                  long long pl, int ld, const float* __restrict__ x, long long o) {
+    const float xo = x[o];
+    float s = rs[o] * xo;
+    s += A[W2 * pl + o] * (x[o - 1] - xo);
+    s += A[W2 * pl + o + 1] * (x[o + 1] - xo);
+    s += A[S2 * pl + o] * (x[o - ld] - xo);
+    s += A[S2 * pl + o + ld] * (x[o + ld] - xo);
+    s += A[SW2 * pl + o] * (x[o - ld - 1] - xo);
+    s += A[SW2 * pl + o + ld + 1] * (x[o + ld + 1] - xo);
+    s += A[NW2 * pl + o] * (x[o + ld - 1] - xo);
+    s += A[NW2 * pl + o - ld + 1] * (x[o - ld + 1] - xo);
     return s;
 }
 
-// q = A p (FP32 operator), alpha = rz / p.q; per-thread sums in FP32, block and
-// grid sums in FP64.
-__global__ void k_spmv_pq32(Grid2 g, const float* __restrict__ A, long long pl, const float* __restrict__ p,
-                            float* __restrict__ q, double* partials, KState* st) {
+// q = A p (FP32 operator, difference form), alpha = rz / p.q; per-thread sums
+// in FP32, block and grid sums in FP64.
+__global__ void k_spmv_pq32(Grid2 g, const float* __restrict__ A, const float* __restrict__ rs, long long pl,
+                            const float* __restrict__ p, float* __restrict__ q, double* partials, KState* st) {
     float acc = 0.0f;
     for (int j = blockIdx.x; j < g.n; j += gridDim.x) {
         const bool rj = j >= 1 && j <= g.n - 2;
         for (int i = threadIdx.x; i < g.ld; i += blockDim.x) {
             const long long k = (long long)j * g.ld + i;
             float v = 0.0f;
-            if (rj && i >= 1 && i <= g.n - 2) v = apply_row2d_f(A, pl, g.ld, p, k);
+            if (rj && i >= 1 && i <= g.n - 2) v = apply_row2d_diff(A, rs, pl, g.ld, p, k);
             q[k] = v;
             acc += p[k] * v;
         }
@@ -257,6 +276,14 @@ bmg_status k_residual_to32(Ctx& c) {
     return BMG_OK;
 }
 
+bmg_status k_row_sums32(Ctx& c) {
+    const Level& L = c.lev[0];
+    k_row_sums32<<<c.red_blocks, kThreads, 0, c.stream>>>(Grid2{L.n, L.ld}, L.A64, L.plane, c.rs32);
+    c.launches++;
+    BMG_CUDA(cudaGetLastError());
+    return BMG_OK;
+}
+
 bmg_status k_add_correction(Ctx& c) {
     const Level& L = c.lev[0];
     k_add_correction<<<c.red_blocks, kThreads, 0, c.stream>>>(L.plane, c.x, c.d32);
@@ -285,8 +312,8 @@ bmg_status k_spmv_pq32(Ctx& c) {
     const Level& L = c.lev[0];
     const double N = (double)(L.n - 2) * (L.n - 2);
     prof_begin(c, BMG_PROF_SPMV, 0);
-    k_spmv_pq32<<<c.red_blocks, kThreads, 0, c.stream>>>(Grid2{L.n, L.ld}, L.A32, L.plane, c.p32, c.q32, c.partials,
-                                                          c.st);
+    k_spmv_pq32<<<c.red_blocks, kThreads, 0, c.stream>>>(Grid2{L.n, L.ld}, L.A32, c.rs32, L.plane, c.p32, c.q32,
+                                                          c.partials, c.st);
     prof_end(c, BMG_PROF_SPMV, 0, (c.ns + 2) * 4.0 * N);
     c.launches++;
     BMG_CUDA(cudaGetLastError());
