@@ -113,17 +113,27 @@ __global__ void k_update_xr(long long tot, double* __restrict__ x, double* __res
     if (grid_sum(acc, partials, &st->counter[3], &t)) st->rr = t;
 }
 
-// beta from r.z (and r.z_old for flexible CG); the first iteration has no beta.
-__global__ void k_beta(int flexible, KState* st) {
-    if (threadIdx.x != 0) return;
-    if (st->first) {
-        st->beta = 0.0;
-        st->first = 0;
-    } else {
-        const double num = flexible ? st->rzn - st->rzo : st->rzn;
-        st->beta = num / st->rz;
+// r.z and (flexible) r.z_old in one pass, then beta in the last block; the
+// first iteration has no beta.
+__global__ void k_rz_beta64(long long tot, const double* __restrict__ r, const double* __restrict__ z,
+                            const double* __restrict__ zo, int flexible, double* partials, KState* st) {
+    double a1 = 0.0, a2 = 0.0;
+    for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < tot;
+         k += (long long)gridDim.x * blockDim.x) {
+        const double rv = r[k];
+        a1 += rv * z[k];
+        if (flexible) a2 += rv * zo[k];
     }
-    st->rz = st->rzn;
+    double t1, t2;
+    if (grid_sum2(a1, a2, partials, &st->counter[5], &t1, &t2)) {
+        if (st->first) {
+            st->beta = 0.0;
+            st->first = 0;
+        } else {
+            st->beta = (flexible ? t1 - t2 : t1) / st->rz;
+        }
+        st->rz = t1;
+    }
 }
 
 // p = z + beta p
@@ -135,6 +145,18 @@ __global__ void k_p_update(long long tot, const double* __restrict__ z, double* 
 }
 
 // ---------------------------------------------------------------- refinement (FP32 inner CG)
+// Compensated (Neumaier) FP32 accumulator: the inner CG's dot products mix
+// signs heavily, and a plain FP32 running sum loses the small total.
+struct Acc32 {
+    float s = 0.0f, c = 0.0f;
+    __device__ __forceinline__ void add(float x) {
+        const float t = s + x;
+        c += fabsf(s) >= fabsf(x) ? (s - t) + x : (x - t) + s;
+        s = t;
+    }
+    __device__ __forceinline__ double value() const { return (double)s + (double)c; }
+};
+
 // r32 = (float)(b - A x), ||r||^2 in FP64; resets the inner CG to its first step.
 __global__ void k_residual_to32(Grid2 g, const double* __restrict__ A, long long pl, const double* __restrict__ b,
                                 const double* __restrict__ x, float* __restrict__ r32, double* partials, KState* st) {
@@ -202,7 +224,7 @@ __device__ __forceinline__ float apply_row2d_diff(const float* __restrict__ A, c
 // in FP32, block and grid sums in FP64.
 __global__ void k_spmv_pq32(Grid2 g, const float* __restrict__ A, const float* __restrict__ rs, long long pl,
                             const float* __restrict__ p, float* __restrict__ q, double* partials, KState* st) {
-    float acc = 0.0f;
+    Acc32 acc;
     for (int j = blockIdx.x; j < g.n; j += gridDim.x) {
         const bool rj = j >= 1 && j <= g.n - 2;
         for (int i = threadIdx.x; i < g.ld; i += blockDim.x) {
@@ -210,11 +232,11 @@ __global__ void k_spmv_pq32(Grid2 g, const float* __restrict__ A, const float* _
             float v = 0.0f;
             if (rj && i >= 1 && i <= g.n - 2) v = apply_row2d_diff(A, rs, pl, g.ld, p, k);
             q[k] = v;
-            acc += p[k] * v;
+            acc.add(p[k] * v);
         }
     }
     double t;
-    if (grid_sum((double)acc, partials, &st->counter[2], &t)) {
+    if (grid_sum(acc.value(), partials, &st->counter[2], &t)) {
         st->pq = t;
         if (!(t > 0.0)) {
             set_err(st, BMG_ERR_NOT_SPD);
@@ -239,15 +261,15 @@ __global__ void k_update_dr32(long long tot, float* __restrict__ d, float* __res
 // r.z and r.z_old in one pass; the last block forms the flexible-CG beta
 __global__ void k_rz_beta32(long long tot, const float* __restrict__ r, const float* __restrict__ z,
                             const float* __restrict__ zo, double* partials, KState* st) {
-    float a1 = 0.0f, a2 = 0.0f;
+    Acc32 a1, a2;
     for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < tot;
          k += (long long)gridDim.x * blockDim.x) {
         const float rv = r[k];
-        a1 += rv * z[k];
-        a2 += rv * zo[k];
+        a1.add(rv * z[k]);
+        a2.add(rv * zo[k]);
     }
     double t1, t2;
-    if (grid_sum2((double)a1, (double)a2, partials, &st->counter[4], &t1, &t2)) {
+    if (grid_sum2(a1.value(), a2.value(), partials, &st->counter[4], &t1, &t2)) {
         if (st->first) {
             st->beta = 0.0;
             st->first = 0;
@@ -388,13 +410,7 @@ bmg_status k_update_xr(Ctx& c) {
 
 bmg_status k_rz_beta(Ctx& c, const double* z, const double* zold, bool flexible) {
     const Level& L = c.lev[0];
-    k_dot64<<<c.red_blocks, kThreads, 0, c.stream>>>(L.plane, c.r, z, c.partials, c.st, &c.st->rzn);
-    c.launches++;
-    if (flexible) {
-        k_dot64<<<c.red_blocks, kThreads, 0, c.stream>>>(L.plane, c.r, zold, c.partials, c.st, &c.st->rzo);
-        c.launches++;
-    }
-    k_beta<<<1, 32, 0, c.stream>>>(flexible ? 1 : 0, c.st);
+    k_rz_beta64<<<c.red_blocks, kThreads, 0, c.stream>>>(L.plane, c.r, z, zold, flexible ? 1 : 0, c.partials, c.st);
     c.launches++;
     BMG_CUDA(cudaGetLastError());
     return BMG_OK;
