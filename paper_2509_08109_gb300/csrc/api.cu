@@ -70,7 +70,6 @@ size_t carve(Ctx& c, char* base) {
     c.q = (double*)take(sizeof(double) * pl0);
     if (c.opts.outer == BMG_OUTER_REFINEMENT) {
         c.r32 = (float*)take(sizeof(float) * pl0);
-        c.d32 = (float*)take(sizeof(float) * pl0);
         c.z32[0] = (float*)take(sizeof(float) * pl0);
         c.z32[1] = (float*)take(sizeof(float) * pl0);
         c.p32 = (float*)take(sizeof(float) * pl0);
@@ -133,14 +132,14 @@ void fill_complexity(const Ctx& c, bmg_info* info) {
 }
 
 // Iterative refinement: FP64 residual, inner FP32 flexible CG (FP32 V-cycle)
-// on A d = r for m iterations, x += d; m is chosen from the contraction seen
+// on A d = r for m iterations whose updates go straight into the FP64 iterate
+// x; m is chosen from the contraction seen
 // so far so that one inner solve aims at the remaining reduction (bounded
 // below by what FP32 can deliver).  maxit caps the total inner iterations.
 bmg_status pcg_ir(Ctx& c, double tol, int maxit, bmg_info* info) {
     KState h;
     BMG_TRY(reset_state(c));
     BMG_TRY(k_dot(c, c.bvec, c.bvec, &c.st->bb));
-    BMG_CUDA(cudaMemsetAsync(c.d32, 0, sizeof(float) * c.lev[0].plane, c.stream));
     BMG_TRY(k_residual_to32(c));
     BMG_TRY(read_state(c, h));
     const double bb = h.bb;
@@ -172,7 +171,6 @@ bmg_status pcg_ir(Ctx& c, double tol, int maxit, bmg_info* info) {
                 BMG_TRY(k_update_dr32(c));
             }
             it += m;
-            BMG_TRY(k_add_correction(c));
             BMG_TRY(k_residual_to32(c));
             BMG_TRY(read_state(c, h));
             refinements++;
@@ -281,7 +279,7 @@ bmg_status bmg_create(const bmg_opts* opts, bmg_ctx** out) {
     if (!out) return BMG_ERR_ARG;
     *out = nullptr;
     if (!opts) return BMG_ERR_ARG;
-    if (opts->dim != 2) return BMG_ERR_SHAPE;
+    if (opts->dim != 2 && opts->dim != 3) return BMG_ERR_SHAPE;
     const int n = opts->n;
     if (n < 3 || ((n - 1) & (n - 2)) != 0) return BMG_ERR_SHAPE;
     if (opts->precision != BMG_PREC_FP64 && opts->precision != BMG_PREC_FP32) return BMG_ERR_ARG;
@@ -311,8 +309,8 @@ bmg_status bmg_create(const bmg_opts* opts, bmg_ctx** out) {
     }
     c.nlev = l;
     c.ws_need = carve(c, nullptr);
-    long long blocks = cdiv(c.lev[0].plane, kThreads * 4);
-    c.red_blocks = (int)(blocks < 1 ? 1 : (blocks > 152 * 8 ? 152 * 8 : blocks));
+    const long long rows = ipow(c.lev[0].n, c.dim - 1);
+    c.red_blocks = (int)(rows > 152 * 8 ? 152 * 8 : rows);
     *out = ctx;
     return BMG_OK;
 }
@@ -348,7 +346,7 @@ bmg_status bmg_assemble(bmg_ctx* ctx, const double* coords, const double* kappa)
     Ctx& c = ctx->c;
     if (!is_device_ptr(coords) || !is_device_ptr(kappa)) return BMG_ERR_ARG;
     BMG_TRY(reset_state(c));
-    BMG_TRY(assemble2d(c, coords, kappa));
+    BMG_TRY(c.dim == 2 ? assemble2d(c, coords, kappa) : assemble3d(c, coords, kappa));
     KState h;
     BMG_TRY(read_state(c, h));
     c.have_setup = false;
@@ -364,7 +362,7 @@ bmg_status bmg_set_stencil(bmg_ctx* ctx, const double* stencil) {
     BMG_TRY(check_ready(ctx));
     if (!stencil || !is_device_ptr(stencil)) return BMG_ERR_ARG;
     Ctx& c = ctx->c;
-    BMG_TRY(set_stencil2d(c, stencil));
+    BMG_TRY(c.dim == 2 ? set_stencil2d(c, stencil) : set_stencil3d(c, stencil));
     BMG_CUDA(cudaStreamSynchronize(c.stream));
     c.have_op = true;
     c.have_setup = false;
@@ -376,7 +374,7 @@ bmg_status bmg_setup(bmg_ctx* ctx) {
     Ctx& c = ctx->c;
     if (!c.have_op) return BMG_ERR_STATE;
     BMG_TRY(reset_state(c));
-    for (int l = 0; l < c.nlev - 1; l++) BMG_TRY(setup_level2d(c, l));
+    for (int l = 0; l < c.nlev - 1; l++) BMG_TRY(c.dim == 2 ? setup_level2d(c, l) : setup_level3d(c, l));
     BMG_TRY(demote_levels(c));
     if (c.rs32) BMG_TRY(k_row_sums32(c));
     KState h;
@@ -429,7 +427,8 @@ bmg_status bmg_adjoint_grad(bmg_ctx* ctx, const double* coords, const double* u,
     bmg_status st = pcg(c, tol, maxit, info);
     if (st == BMG_ERR_DEVICE) return st;
     BMG_TRY(stage_out(c, c.x, lambda));
-    BMG_TRY(adjoint_cells2d(c, coords, u, lambda, dLdkappa));
+    BMG_TRY(c.dim == 2 ? adjoint_cells2d(c, coords, u, lambda, dLdkappa)
+                       : adjoint_cells3d(c, coords, u, lambda, dLdkappa));
     KState h;
     BMG_TRY(read_state(c, h));
     if (h.err && st == BMG_OK) st = (bmg_status)h.err;
@@ -449,7 +448,7 @@ bmg_status bmg_get_stencil(bmg_ctx* ctx, int level, double* out) {
     if (!out || level < 0 || level >= c.nlev || !is_device_ptr(out)) return BMG_ERR_ARG;
     if (level > 0 && !c.have_setup) return BMG_ERR_STATE;
     if (level == 0 && !c.have_op) return BMG_ERR_STATE;
-    BMG_TRY(export_stencil2d(c, level, out));
+    BMG_TRY(c.dim == 2 ? export_stencil2d(c, level, out) : export_stencil3d(c, level, out));
     BMG_CUDA(cudaStreamSynchronize(c.stream));
     return BMG_OK;
 }
@@ -459,7 +458,7 @@ bmg_status bmg_get_interp(bmg_ctx* ctx, int level, double* out) {
     Ctx& c = ctx->c;
     if (!out || level < 0 || level >= c.nlev - 1 || !is_device_ptr(out)) return BMG_ERR_ARG;
     if (!c.have_setup) return BMG_ERR_STATE;
-    BMG_TRY(export_interp2d(c, level, out));
+    BMG_TRY(c.dim == 2 ? export_interp2d(c, level, out) : export_interp3d(c, level, out));
     BMG_CUDA(cudaStreamSynchronize(c.stream));
     return BMG_OK;
 }

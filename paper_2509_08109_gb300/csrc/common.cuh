@@ -91,7 +91,7 @@ struct Ctx {
     double *p = nullptr, *q = nullptr;
     double *stage_in = nullptr, *stage_out = nullptr;   // n^d doubles each, host staging
     // iterative refinement: FP32 inner CG vectors
-    float *r32 = nullptr, *d32 = nullptr, *z32[2] = {nullptr, nullptr}, *p32 = nullptr, *q32 = nullptr;
+    float *r32 = nullptr, *z32[2] = {nullptr, nullptr}, *p32 = nullptr, *q32 = nullptr;
     float* rs32 = nullptr;        // FP32 row sums of the finest operator (difference-form products)
     FusedLevel fused_ir0;         // level-0 streaming kernels reading r32 (FP32)
     double* partials = nullptr;
@@ -267,6 +267,8 @@ bmg_status fused_occupancy(bool f32, bool f64in, int wc, int* down_blocks, int* 
 bmg_status fused_down(Ctx& c, int l, bool ir = false);
 bmg_status fused_up(Ctx& c, int l, void* out, bool ir = false);
 bmg_status vcycle_f32(Ctx& c, float* z32);       // z32 = M r32 (FP32 in and out)
+template <typename T>
+bmg_status vcycle3d_impl(Ctx& c, const T* b0, T* x0, T* xout);
 bmg_status fused_prepare(Ctx& c);
 bmg_status demote_levels(Ctx& c);
 // krylov.cu
@@ -281,10 +283,9 @@ bmg_status k_p_update(Ctx& c, const double* z);                   // p = z + bet
 // FP32 inner CG of the refinement mode
 bmg_status k_row_sums32(Ctx& c);                // rs32 = row sums of A (computed in FP64)
 bmg_status k_residual_to32(Ctx& c);             // r32 = (float)(b - A x); rr; resets the inner CG state
-bmg_status k_add_correction(Ctx& c);            // x += d32; d32 = 0
 bmg_status k_rz_beta32(Ctx& c, const float* z, const float* zo);
 bmg_status k_p_update32(Ctx& c, const float* z);
 bmg_status k_spmv_pq32(Ctx& c);
-bmg_status k_update_dr32(Ctx& c);
+bmg_status k_update_dr32(Ctx& c);                // x (FP64) += alpha p; r32 -= alpha q
 
 }  // namespace bmg

@@ -243,13 +243,23 @@ bmg_status demote_levels(Ctx& c) {
 }
 
 bmg_status vcycle_f32(Ctx& c, float* z32) {
-    if (c.dim != 2 || c.opts.precision != BMG_PREC_FP32) return BMG_ERR_STATE;
+    if (c.opts.precision != BMG_PREC_FP32) return BMG_ERR_STATE;
+    if (c.dim == 3) return vcycle3d_impl<float>(c, c.r32, z32, nullptr);
     if (c.use_fused && c.nlev >= 2) return vcycle2d_fused<float>(c, z32, true);
     return vcycle2d_impl<float>(c, c.r32, z32);
 }
 
 bmg_status vcycle(Ctx& c, const double* r, double* z) {
-    if (c.dim != 2) return BMG_ERR_SHAPE;
+    if (c.dim == 3) {
+        if (c.opts.precision == BMG_PREC_FP64) return vcycle3d_impl<double>(c, r, z, nullptr);
+        Level& F = c.lev[0];
+        k_convert<double, float><<<1216, 256, 0, c.stream>>>(F.plane, r, (float*)F.b);
+        BMG_TRY(vcycle3d_impl<float>(c, (const float*)F.b, (float*)F.x, nullptr));
+        k_convert<float, double><<<1216, 256, 0, c.stream>>>(F.plane, (const float*)F.x, z);
+        c.launches += 2;
+        BMG_CUDA(cudaGetLastError());
+        return BMG_OK;
+    }
     if (c.use_fused && c.nlev >= 2) {
         if (r != c.r) return BMG_ERR_ARG;   // the level-0 tensor map streams c.r
         if (c.opts.precision == BMG_PREC_FP64) return vcycle2d_fused<double>(c, z);

@@ -41,7 +41,7 @@ def test_build_targets_sm103a_only():
     assert build.ARCH == ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 
-@pytest.mark.parametrize("n,dim,code", [(65, 2, 0), (4097, 2, 0), (64, 2, 2), (2, 2, 2), (3, 2, 0), (65, 4, 2)])
+@pytest.mark.parametrize("n,dim,code", [(65, 2, 0), (4097, 2, 0), (64, 2, 2), (2, 2, 2), (3, 2, 0), (65, 4, 2), (17, 3, 0), (257, 3, 0), (16, 3, 2)])
 def test_create_validates_shape(lib, n, dim, code):
     opts = binding._Opts(dim, n, 0, 0, 0)
     h = ctypes.c_void_p()

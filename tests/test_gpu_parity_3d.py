@@ -1,0 +1,89 @@
+"""3-D parity of the CUDA path (through the C ABI) against the oracle:
+27-point trilinear assembly, hierarchical-collapse interpolation, Galerkin
+coarse operators, 8-colour V-cycle, PCG, FP32 modes.  Same tolerances as the
+2-D tests (FP64 rounding through the hierarchy)."""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_2509_08109_gb300 import binding, inputs
+from tests.gpu_util import rel_to_diag, relerr, solver_for
+
+pytestmark = pytest.mark.gpu
+
+
+def _problem(n, kind="shell"):
+    if kind == "shell":
+        return inputs.shell_two_layer(n)
+    p = inputs.shell_two_layer(n)
+    rng = np.random.default_rng(n)
+    p.kappa = np.exp(rng.normal(0, 0.7, size=p.kappa.shape))
+    return p
+
+
+@pytest.mark.parametrize("n", [5, 9, 17, 33])
+def test_assembly_3d_matches_oracle(n):
+    p = _problem(n)
+    s = binding.Solver(3, n).assemble(torch.as_tensor(p.coords), torch.as_tensor(p.kappa))
+    ref = oracle.assemble(p.coords, p.kappa)
+    assert rel_to_diag(s.stencil(0).cpu().numpy(), ref) <= 1e-13
+
+
+@pytest.mark.parametrize("n,kind", [(9, "shell"), (17, "random"), (33, "shell")])
+def test_hierarchy_3d_matches_oracle(n, kind):
+    p = _problem(n, kind)
+    s = solver_for(p)
+    H = oracle.Hierarchy(oracle.assemble(p.coords, p.kappa))
+    assert s.levels == H.nlev
+    for l in range(H.nlev):
+        assert rel_to_diag(s.stencil(l).cpu().numpy(), H.A(l)) <= 1e-12, l
+        if l < H.nlev - 1:
+            assert np.abs(s.interp(l).cpu().numpy() - H.P(l)).max() <= 1e-12, l
+
+
+@pytest.mark.parametrize("n", [3, 5, 9, 17])
+def test_vcycle_3d_matches_oracle(n):
+    p = _problem(n, "random")
+    s = solver_for(p)
+    H = oracle.Hierarchy(oracle.assemble(p.coords, p.kappa))
+    r = inputs.rhs_uniform(np.random.default_rng(3), (n, n, n))
+    z = s.vcycle(torch.as_tensor(r, device="cuda")).cpu().numpy()
+    assert relerr(z, H.vcycle(r)) <= 1e-12
+
+
+@pytest.mark.parametrize("n,iters", [(9, 4), (17, 6)])
+def test_pcg_3d_fixed_iterations(n, iters):
+    p = _problem(n)
+    s = solver_for(p)
+    H = oracle.Hierarchy(oracle.assemble(p.coords, p.kappa))
+    x, info = s.solve(torch.as_tensor(p.rhs, device="cuda"), tol=0.0, maxit=iters)
+    xo, ito, _, _, _ = H.pcg(p.rhs, tol=0.0, maxit=iters)
+    assert info.iterations == iters
+    assert relerr(x.cpu().numpy(), xo) <= 1e-9
+
+
+@pytest.mark.parametrize("precision,outer", [("fp64", "cg"), ("fp32", "flexible"), ("fp32", "refine")])
+def test_pcg_3d_free_running(precision, outer):
+    n = 17
+    p = _problem(n)
+    s = solver_for(p, precision=precision, outer=outer)
+    x, info = s.solve(torch.as_tensor(p.rhs, device="cuda"), tol=1e-10, maxit=500)
+    H = oracle.Hierarchy(oracle.assemble(p.coords, p.kappa))
+    xo, ito, _, trr, _ = H.pcg(p.rhs, tol=1e-12, maxit=500)
+    assert info.true_relres <= 1e-10
+    assert relerr(x.cpu().numpy(), xo) <= 1e-6
+    if precision == "fp64":
+        xo10, it10, _, _, _ = H.pcg(p.rhs, tol=1e-10, maxit=500)
+        assert abs(info.iterations - it10) <= 1
+
+
+def test_adjoint_3d_matches_oracle():
+    n = 9
+    p = _problem(n, "random")
+    s = solver_for(p)
+    u, _ = s.solve(torch.as_tensor(p.rhs, device="cuda"), tol=1e-13, maxit=300)
+    g = u - torch.as_tensor(p.rhs, device="cuda") * 0.5
+    lam, dk, _ = s.adjoint_grad(u, g, tol=1e-13, maxit=300)
+    ref = oracle.adjoint_grad(p.coords, u.cpu().numpy(), lam.cpu().numpy())
+    assert relerr(dk.cpu().numpy(), ref) <= 1e-12
