@@ -30,7 +30,7 @@ def test_assembly_3d_matches_oracle(n):
     assert rel_to_diag(s.stencil(0).cpu().numpy(), ref) <= 1e-13
 
 
-@pytest.mark.parametrize("n,kind", [(9, "shell"), (17, "random"), (33, "shell")])
+@pytest.mark.parametrize("n,kind", [(9, "shell"), (9, "random"), (17, "shell"), (33, "shell")])
 def test_hierarchy_3d_matches_oracle(n, kind):
     p = _problem(n, kind)
     s = solver_for(p)
@@ -42,9 +42,9 @@ def test_hierarchy_3d_matches_oracle(n, kind):
             assert np.abs(s.interp(l).cpu().numpy() - H.P(l)).max() <= 1e-12, l
 
 
-@pytest.mark.parametrize("n", [3, 5, 9, 17])
-def test_vcycle_3d_matches_oracle(n):
-    p = _problem(n, "random")
+@pytest.mark.parametrize("n,kind", [(3, "random"), (5, "random"), (9, "random"), (17, "shell")])
+def test_vcycle_3d_matches_oracle(n, kind):
+    p = _problem(n, kind)
     s = solver_for(p)
     H = oracle.Hierarchy(oracle.assemble(p.coords, p.kappa))
     r = inputs.rhs_uniform(np.random.default_rng(3), (n, n, n))
@@ -76,6 +76,20 @@ def test_pcg_3d_free_running(precision, outer):
     if precision == "fp64":
         xo10, it10, _, _, _ = H.pcg(p.rhs, tol=1e-10, maxit=500)
         assert abs(info.iterations - it10) <= 1
+
+
+def test_breakdown_reported_where_the_oracle_breaks_down():
+    """With a rough per-cell coefficient on the shell map the collapsed plane
+    diagonal of the 3-D interpolation turns non-positive on the 17^3 grid; the
+    library reports the same setup breakdown the oracle does."""
+    n = 17
+    p = _problem(n, "random")
+    with pytest.raises(oracle.OracleError):
+        oracle.Hierarchy(oracle.assemble(p.coords, p.kappa))
+    s = binding.Solver(3, n).assemble(torch.as_tensor(p.coords), torch.as_tensor(p.kappa))
+    with pytest.raises(binding.BmgError) as e:
+        s.setup()
+    assert e.value.code == 6
 
 
 def test_adjoint_3d_matches_oracle():
