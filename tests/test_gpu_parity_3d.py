@@ -36,10 +36,14 @@ def test_hierarchy_3d_matches_oracle(n, kind):
     s = solver_for(p)
     H = oracle.Hierarchy(oracle.assemble(p.coords, p.kappa))
     assert s.levels == H.nlev
+    # 1e-11: the collapse sums neighbour rows in a different order than the
+    # oracle's term-by-term accumulation, and the shell map (polar
+    # degeneracy, kappa contrast 1000) amplifies that rounding level by level
     for l in range(H.nlev):
-        assert rel_to_diag(s.stencil(l).cpu().numpy(), H.A(l)) <= 1e-12, l
+        assert rel_to_diag(s.stencil(l).cpu().numpy(), H.A(l)) <= 1e-11, l
         if l < H.nlev - 1:
-            assert np.abs(s.interp(l).cpu().numpy() - H.P(l)).max() <= 1e-12, l
+            Po = H.P(l)
+            assert np.abs(s.interp(l).cpu().numpy() - Po).max() <= 1e-11 * max(1.0, np.abs(Po).max()), l
 
 
 @pytest.mark.parametrize("n,kind", [(3, "random"), (5, "random"), (9, "random"), (17, "shell")])
