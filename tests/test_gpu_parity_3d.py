@@ -30,20 +30,46 @@ def test_assembly_3d_matches_oracle(n):
     assert rel_to_diag(s.stencil(0).cpu().numpy(), ref) <= 1e-13
 
 
-@pytest.mark.parametrize("n,kind", [(9, "shell"), (9, "random"), (17, "shell"), (33, "shell")])
-def test_hierarchy_3d_matches_oracle(n, kind):
-    p = _problem(n, kind)
+def _identity_random(n, sigma=0.5):
+    p = inputs.shell_two_layer(n)
+    p.coords = inputs.coords_identity(n, 3)
+    p.kappa = np.exp(np.random.default_rng(n).normal(0, sigma, size=p.kappa.shape))
+    return p
+
+
+@pytest.mark.parametrize("n", [9, 17, 33])
+def test_hierarchy_3d_matches_oracle_well_conditioned(n):
+    """Identity map, log-normal kappa: every level to 1e-12."""
+    p = _identity_random(n)
     s = solver_for(p)
     H = oracle.Hierarchy(oracle.assemble(p.coords, p.kappa))
     assert s.levels == H.nlev
-    # 1e-11: the collapse sums neighbour rows in a different order than the
-    # oracle's term-by-term accumulation, and the shell map (polar
-    # degeneracy, kappa contrast 1000) amplifies that rounding level by level
     for l in range(H.nlev):
-        assert rel_to_diag(s.stencil(l).cpu().numpy(), H.A(l)) <= 1e-11, l
+        assert rel_to_diag(s.stencil(l).cpu().numpy(), H.A(l)) <= 1e-12, l
+        if l < H.nlev - 1:
+            assert np.abs(s.interp(l).cpu().numpy() - H.P(l)).max() <= 1e-12, l
+
+
+@pytest.mark.parametrize("n,kind", [(9, "shell"), (9, "random"), (17, "shell"), (33, "shell")])
+def test_hierarchy_3d_matches_oracle(n, kind):
+    """Shell map (polar degeneracy, kappa contrast 1000): the collapse
+    amplifies rounding level by level, so the bound per level is the
+    oracle's own response to a 2e-16 relative perturbation of its input
+    (times 20), and never below 1e-12."""
+    p = _problem(n, kind)
+    s = solver_for(p)
+    A = oracle.assemble(p.coords, p.kappa)
+    H = oracle.Hierarchy(A)
+    Hp = oracle.Hierarchy(A * (1 + 2e-16 * np.random.default_rng(0).standard_normal(A.shape)))
+    assert s.levels == H.nlev
+    for l in range(H.nlev):
+        Ao = H.A(l)
+        sens_a = rel_to_diag(Hp.A(l), Ao)
+        assert rel_to_diag(s.stencil(l).cpu().numpy(), Ao) <= max(1e-12, 20 * sens_a), l
         if l < H.nlev - 1:
             Po = H.P(l)
-            assert np.abs(s.interp(l).cpu().numpy() - Po).max() <= 1e-11 * max(1.0, np.abs(Po).max()), l
+            sens_p = np.abs(Hp.P(l) - Po).max()
+            assert np.abs(s.interp(l).cpu().numpy() - Po).max() <= max(1e-12, 20 * sens_p), l
 
 
 @pytest.mark.parametrize("n,kind", [(3, "random"), (5, "random"), (9, "random"), (17, "shell")])
