@@ -1,0 +1,78 @@
+"""Differentiation (BASELINE form 3): torch.autograd through the library's
+forward and adjoint solves, against the oracle's adjoint gradient and
+central finite differences of the loss L = 1/2 |u - u_obs|^2."""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_2509_08109_gb300 import autograd, binding, inputs
+from tests.gpu_util import relerr
+
+pytestmark = pytest.mark.gpu
+
+
+def _grad(prob, tol=1e-13):
+    dev = "cuda"
+    coords = torch.as_tensor(prob.coords, device=dev)
+    m = torch.as_tensor(prob.extra["m"], device=dev).requires_grad_(True)
+    f = torch.as_tensor(prob.rhs, device=dev).requires_grad_(True)
+    u_obs = torch.as_tensor(prob.extra["u_obs"], device=dev)
+    s = binding.Solver(2, prob.n)
+    u = autograd.solve(m, f, coords, s, tol=tol, maxit=500)
+    loss = 0.5 * ((u - u_obs) ** 2).sum()
+    loss.backward()
+    return loss.item(), m.grad.cpu().numpy(), f.grad.cpu().numpy(), u.detach().cpu().numpy()
+
+
+def test_gradient_matches_oracle_adjoint():
+    (prob,) = inputs.annulus_adjoint(65, batch=1)
+    _, gm, gf, u = _grad(prob)
+    H = oracle.Hierarchy(oracle.assemble(prob.coords, prob.kappa))
+    uo = H.pcg(prob.rhs, tol=1e-14, maxit=500)[0]
+    lo = H.pcg(uo - prob.extra["u_obs"], tol=1e-14, maxit=500)[0]
+    go = prob.kappa * oracle.adjoint_grad(prob.coords, uo, lo)
+    assert relerr(gm, go) <= 1e-8
+    assert relerr(gf, lo) <= 1e-8
+
+
+def test_gradient_matches_central_differences():
+    """Central differences in m_e with eps = 1e-3, the loss difference formed
+    as 1/2 sum (u+ - u-)(u+ + u- - 2 u_obs) to avoid cancellation; relative
+    error against max(|g_e|, 1e-3 max|g|)."""
+    (prob,) = inputs.annulus_adjoint(129, batch=1)
+    _, gm, _, u = _grad(prob, tol=1e-14)
+    s = binding.Solver(2, prob.n)
+    rng = np.random.default_rng(3)
+    cells = [tuple(c) for c in rng.integers(0, prob.n - 1, size=(8, 2))]
+    eps = 1e-3
+    scale = np.abs(gm).max()
+    f = torch.as_tensor(prob.rhs, device="cuda")
+    for c in cells:
+        sols = []
+        for sgn in (+1, -1):
+            mm = prob.extra["m"].copy()
+            mm[c] += sgn * eps
+            s.assemble(torch.as_tensor(prob.coords), torch.as_tensor(np.exp(mm))).setup()
+            x, _ = s.solve(f, x0=torch.as_tensor(u, device="cuda"), tol=1e-14, maxit=500, raise_on_nonconv=False)
+            sols.append(x.cpu().numpy())
+        up, um = sols
+        dL = 0.5 * np.sum((up - um) * (up + um - 2 * prob.extra["u_obs"]))
+        fd = dL / (2 * eps)
+        assert abs(fd - gm[c]) <= 1e-5 * max(abs(gm[c]), 1e-3 * scale), (c, fd, gm[c])
+
+
+def test_batch_of_independent_members():
+    probs = inputs.annulus_adjoint(33, batch=3)
+    coords = torch.as_tensor(probs[0].coords, device="cuda")
+    ms = [torch.as_tensor(p.extra["m"], device="cuda").requires_grad_(True) for p in probs]
+    fs = [torch.as_tensor(p.rhs, device="cuda") for p in probs]
+    solvers = [binding.Solver(2, 33) for _ in probs]
+    us = autograd.solve_batch(ms, fs, coords, solvers, tol=1e-13)
+    loss = sum(0.5 * ((u - torch.as_tensor(p.extra["u_obs"], device="cuda")) ** 2).sum() for u, p in zip(us, probs))
+    loss.backward()
+    for p, m in zip(probs, ms):
+        H = oracle.Hierarchy(oracle.assemble(p.coords, p.kappa))
+        uo = H.pcg(p.rhs, tol=1e-14)[0]
+        lo = H.pcg(uo - p.extra["u_obs"], tol=1e-14)[0]
+        assert relerr(m.grad.cpu().numpy(), p.kappa * oracle.adjoint_grad(p.coords, uo, lo)) <= 1e-8
