@@ -131,6 +131,64 @@ void fill_complexity(const Ctx& c, bmg_info* info) {
     info->operator_complexity = s / n0;   // same stored entries per node on every level
 }
 
+// One iteration's launches on c.stream: refinement mode (FP32 inner CG) or
+// the FP64 outer CG.  parity selects the z buffer written this iteration.
+bmg_status enqueue_iteration(Ctx& c, int parity) {
+    if (c.opts.outer == BMG_OUTER_REFINEMENT) {
+        float* zn = c.z32[parity];
+        float* zo = c.z32[parity ^ 1];
+        BMG_TRY(vcycle_f32(c, zn));
+        BMG_TRY(k_rz_beta32(c, zn, zo));
+        BMG_TRY(k_p_update32(c, zn));
+        BMG_TRY(k_spmv_pq32(c));
+        BMG_TRY(k_update_dr32(c));
+    } else {
+        double* zn = c.z[parity];
+        double* zo = c.z[parity ^ 1];
+        BMG_TRY(vcycle(c, c.r, zn));
+        BMG_TRY(k_rz_beta(c, zn, zo, c.opts.outer == BMG_OUTER_FLEXIBLE_CG));
+        BMG_TRY(k_p_update(c, zn));
+        BMG_TRY(k_spmv_pq(c, c.p, c.q));
+        BMG_TRY(k_update_xr(c));
+    }
+    return BMG_OK;
+}
+
+// Launches one iteration, from a CUDA graph captured on first use (one per
+// parity) unless profiling is on (per-launch events) or graphs are disabled.
+bmg_status run_iteration(Ctx& c, int parity) {
+    if (!c.use_graphs || c.prof_on) return enqueue_iteration(c, parity);
+    if (!c.it_exec[parity]) {
+        if (!c.cap_stream) BMG_CUDA(cudaStreamCreateWithFlags(&c.cap_stream, cudaStreamNonBlocking));
+        cudaStream_t user = c.stream;
+        // order the capture stream after the user's stream (nothing is captured yet)
+        BMG_CUDA(cudaStreamSynchronize(user));
+        c.stream = c.cap_stream;
+        cudaGraph_t g = nullptr;
+        bmg_status st = BMG_OK;
+        if (cudaStreamBeginCapture(c.cap_stream, cudaStreamCaptureModeRelaxed) != cudaSuccess) st = BMG_ERR_DEVICE;
+        const long long before = c.launches;
+        if (st == BMG_OK) st = enqueue_iteration(c, parity);
+        c.it_kernels[parity] = c.launches - before;
+        c.launches = before;
+        cudaError_t e = cudaStreamEndCapture(c.cap_stream, &g);
+        c.stream = user;
+        if (st != BMG_OK) {
+            if (g) cudaGraphDestroy(g);
+            return st;
+        }
+        if (e != cudaSuccess) return BMG_ERR_DEVICE;
+        cudaGraphExec_t ex = nullptr;
+        e = cudaGraphInstantiate(&ex, g, 0);
+        cudaGraphDestroy(g);
+        if (e != cudaSuccess) return BMG_ERR_DEVICE;
+        c.it_exec[parity] = ex;
+    }
+    BMG_CUDA(cudaGraphLaunch(c.it_exec[parity], c.stream));
+    c.launches += c.it_kernels[parity];   // kernels the graph replays
+    return BMG_OK;
+}
+
 // Iterative refinement: FP64 residual, inner FP32 flexible CG (FP32 V-cycle)
 // on A d = r for m iterations whose updates go straight into the FP64 iterate
 // x; m is chosen from the contraction seen
@@ -161,15 +219,7 @@ bmg_status pcg_ir(Ctx& c, double tol, int maxit, bmg_info* info) {
             if (m < 2) m = 2;
             if (m > 40) m = 40;
             if (m > maxit - it) m = maxit - it;
-            for (int k = 0; k < m; k++) {
-                float* zn = c.z32[(it + k) & 1];
-                float* zo = c.z32[(it + k + 1) & 1];
-                BMG_TRY(vcycle_f32(c, zn));
-                BMG_TRY(k_rz_beta32(c, zn, zo));
-                BMG_TRY(k_p_update32(c, zn));
-                BMG_TRY(k_spmv_pq32(c));
-                BMG_TRY(k_update_dr32(c));
-            }
+            for (int k = 0; k < m; k++) BMG_TRY(run_iteration(c, (it + k) & 1));
             it += m;
             BMG_TRY(k_residual_to32(c));
             BMG_TRY(read_state(c, h));
@@ -202,7 +252,6 @@ bmg_status pcg_ir(Ctx& c, double tol, int maxit, bmg_info* info) {
 // PCG with M = one V-cycle.  x (padded, in c.x) holds the initial guess.
 bmg_status pcg(Ctx& c, double tol, int maxit, bmg_info* info) {
     if (c.opts.outer == BMG_OUTER_REFINEMENT) return pcg_ir(c, tol, maxit, info);
-    const bool flexible = c.opts.outer == BMG_OUTER_FLEXIBLE_CG;
     BMG_TRY(reset_state(c));
     KState h;
     BMG_TRY(k_dot(c, c.bvec, c.bvec, &c.st->bb));
@@ -224,13 +273,7 @@ bmg_status pcg(Ctx& c, double tol, int maxit, bmg_info* info) {
         const double lim = tol > 0 ? tol * tol * bb : -1.0;
         bool done = rr <= lim;
         while (!done && it < maxit) {
-            double* zn = c.z[it & 1];
-            double* zo = c.z[(it + 1) & 1];
-            BMG_TRY(vcycle(c, c.r, zn));
-            BMG_TRY(k_rz_beta(c, zn, zo, flexible));
-            BMG_TRY(k_p_update(c, zn));
-            BMG_TRY(k_spmv_pq(c, c.p, c.q));
-            BMG_TRY(k_update_xr(c));
+            BMG_TRY(run_iteration(c, it & 1));
             it++;
             BMG_TRY(read_state(c, h));
             if (h.err) {
@@ -334,6 +377,7 @@ bmg_status bmg_attach(bmg_ctx* ctx, void* ws, size_t bytes, void* stream) {
     BMG_CUDA(cudaMemsetAsync(c.ws, 0, c.ws_need, c.stream));
     BMG_CUDA(cudaStreamSynchronize(c.stream));
     c.use_fused = c.dim == 2 && !(c.opts.flags & BMG_FLAG_UNFUSED) && c.nlev >= 2;
+    c.use_graphs = !(c.opts.flags & BMG_FLAG_NO_GRAPHS);
     if (c.use_fused) BMG_TRY(fused_prepare(c));
     c.attached = true;
     c.have_op = c.have_setup = false;
@@ -500,6 +544,9 @@ long long bmg_launch_count(const bmg_ctx* ctx) { return ctx ? ctx->c.launches : 
 
 void bmg_destroy(bmg_ctx* ctx) {
     if (!ctx) return;
+    for (int p = 0; p < 2; p++)
+        if (ctx->c.it_exec[p]) cudaGraphExecDestroy(ctx->c.it_exec[p]);
+    if (ctx->c.cap_stream) cudaStreamDestroy(ctx->c.cap_stream);
     for (int k = 0; k < BMG_PROF_KINDS; k++)
         for (cudaEvent_t e : ctx->c.prof[k].ev) cudaEventDestroy(e);
     delete ctx;

@@ -102,6 +102,11 @@ struct Ctx {
     bool prof_on = false;
     ProfSlot prof[BMG_PROF_KINDS];
     bool use_fused = false;       // streaming V-cycle kernels (2-D)
+    // CUDA graphs of one inner/outer iteration (two, for the alternating z buffers)
+    cudaStream_t cap_stream = nullptr;
+    cudaGraphExec_t it_exec[2] = {nullptr, nullptr};
+    long long it_kernels[2] = {0, 0};
+    bool use_graphs = true;
     FusedLevel fused[kMaxLevels];
 };
 
