@@ -155,6 +155,20 @@ bmg_status bmg_vcycle(bmg_ctx* ctx, const double* r, double* z);
 bmg_status bmg_solve(bmg_ctx* ctx, const double* b, double* x, double tol, int maxit,
                      bmg_info* info);
 
+/* Solves count independent problems, nrhs right-hand sides each, to a
+   relative FP64 residual of tol (> 0), running them concurrently: every
+   context must have been set up with BMG_OUTER_REFINEMENT and should be
+   attached to a stream of its own (contexts sharing a stream serialise).
+   A host-side scheduler keeps every problem's refinement loop in flight
+   (iteration graphs, asynchronous residual checks, event polling) instead
+   of waiting on one problem at a time.  b[p*nrhs + r], x[p*nrhs + r]:
+   problem p's r-th right-hand side / initial guess and solution, n_p^d
+   doubles on the host or the device.  infos: count*nrhs entries or NULL.
+   The right-hand sides of one problem are solved one after the other with
+   its hierarchy.  Returns the first non-OK status of any solve. */
+bmg_status bmg_solve_many(bmg_ctx* const* ctxs, int count, int nrhs, const double* const* b, double* const* x,
+                          double tol, int maxit, bmg_info* infos);
+
 /* Adjoint gradient with respect to the per-cell coefficient for a loss
    L(u) of the solution u = A^-1 b: solves A lambda = dL/du with the same
    hierarchy (A is symmetric) and evaluates, per cell e,

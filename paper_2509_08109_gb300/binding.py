@@ -78,6 +78,7 @@ def load() -> ctypes.CDLL:
         "bmg_vcycle": ([P, P, P], I),
         "bmg_solve": ([P, P, P, D, I, ctypes.POINTER(_Info)], I),
         "bmg_adjoint_grad": ([P, P, P, P, P, P, D, I, ctypes.POINTER(_Info)], I),
+        "bmg_solve_many": ([P, I, I, P, P, D, I, P], I),
         "bmg_levels": ([P], I),
         "bmg_level_n": ([P, I], I),
         "bmg_get_stencil": ([P, I, P], I),
@@ -98,7 +99,8 @@ def load() -> ctypes.CDLL:
 
 def exported_symbols() -> list:
     return ["bmg_default_opts", "bmg_create", "bmg_workspace_bytes", "bmg_attach", "bmg_assemble",
-            "bmg_set_stencil", "bmg_setup", "bmg_vcycle", "bmg_solve", "bmg_adjoint_grad", "bmg_levels",
+            "bmg_set_stencil", "bmg_setup", "bmg_vcycle", "bmg_solve", "bmg_solve_many", "bmg_adjoint_grad",
+            "bmg_levels",
             "bmg_level_n", "bmg_get_stencil", "bmg_get_interp", "bmg_launch_count", "bmg_profile",
             "bmg_profile_read", "bmg_destroy", "bmg_status_str"]
 
@@ -111,6 +113,39 @@ def _check(code: int, where: str):
 def _ptr(t: torch.Tensor):
     assert t.is_contiguous() and t.dtype == torch.float64, (t.dtype, t.is_contiguous())
     return ctypes.c_void_p(t.data_ptr())
+
+
+def _info_of(i: "_Info") -> SolveInfo:
+    return SolveInfo(i.iterations, i.levels, i.relres, i.true_relres, i.rho, i.grid_complexity,
+                     i.operator_complexity, i.status, i.refinements)
+
+
+def solve_many(solvers, bs, xs, tol: float = 1e-10, maxit: int = 500):
+    """Concurrent independent solves (library scheduler).  solvers: Solver
+    objects built with precision='fp32', outer='refine', each attached to its
+    own stream; bs[p] / xs[p]: lists of nrhs tensors (host or device) for
+    problem p; xs hold the initial guesses and receive the solutions.
+    Returns a list (per problem) of lists of SolveInfo."""
+    lib = load()
+    count = len(solvers)
+    nrhs = len(bs[0]) if count else 1
+    hs = (ctypes.c_void_p * count)(*[s._h.value for s in solvers])
+    bp = (ctypes.c_void_p * (count * nrhs))()
+    xp = (ctypes.c_void_p * (count * nrhs))()
+    keep = []
+    for p in range(count):
+        assert len(bs[p]) == nrhs and len(xs[p]) == nrhs
+        for r in range(nrhs):
+            b = bs[p][r]
+            x = xs[p][r]
+            assert b.dtype == torch.float64 and x.dtype == torch.float64 and b.is_contiguous() and x.is_contiguous()
+            keep += [b, x]
+            bp[p * nrhs + r] = b.data_ptr()
+            xp[p * nrhs + r] = x.data_ptr()
+    infos = (_Info * (count * nrhs))()
+    code = lib.bmg_solve_many(hs, count, nrhs, bp, xp, float(tol), int(maxit), infos)
+    _check(code, "bmg_solve_many")
+    return [[_info_of(infos[p * nrhs + r]) for r in range(nrhs)] for p in range(count)]
 
 
 class Solver:

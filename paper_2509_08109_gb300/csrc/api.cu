@@ -5,6 +5,7 @@
 #include <string.h>
 
 #include <new>
+#include <vector>
 
 #include "common.cuh"
 
@@ -104,8 +105,11 @@ bmg_status check_ready(const bmg_ctx* ctx) {
     return BMG_OK;
 }
 
+}  // namespace
+
+namespace bmg {
 // Copies an n^d array from the caller (host or device) into the padded dst.
-bmg_status stage_in(Ctx& c, const double* src, double* dst) {
+bmg_status stage_in_async(Ctx& c, const double* src, double* dst) {
     const long long nn = ipow(c.lev[0].n, c.dim);
     const double* dsrc = src;
     if (!is_device_ptr(src)) {
@@ -115,7 +119,7 @@ bmg_status stage_in(Ctx& c, const double* src, double* dst) {
     return k_pack(c, dsrc, dst);
 }
 
-bmg_status stage_out(Ctx& c, const double* src, double* dst) {
+bmg_status stage_out_async(Ctx& c, const double* src, double* dst) {
     const long long nn = ipow(c.lev[0].n, c.dim);
     if (is_device_ptr(dst)) return k_unpack(c, src, dst);
     BMG_TRY(k_unpack(c, src, c.stage_out));
@@ -123,13 +127,23 @@ bmg_status stage_out(Ctx& c, const double* src, double* dst) {
     return BMG_OK;
 }
 
-void fill_complexity(const Ctx& c, bmg_info* info) {
+void fill_complexity_info(const Ctx& c, bmg_info* info) {
     double n0 = (double)ipow(c.lev[0].n - 2, c.dim), s = 0.0;
     for (int l = 0; l < c.nlev; l++) s += (double)ipow(c.lev[l].n - 2, c.dim);
     info->levels = c.nlev;
     info->grid_complexity = s / n0;
     info->operator_complexity = s / n0;   // same stored entries per node on every level
 }
+}  // namespace bmg
+
+namespace {
+bmg_status stage_in(Ctx& c, const double* src, double* dst) { return stage_in_async(c, src, dst); }
+bmg_status stage_out(Ctx& c, const double* src, double* dst) { return stage_out_async(c, src, dst); }
+void fill_complexity(const Ctx& c, bmg_info* info) { fill_complexity_info(c, info); }
+
+}  // namespace
+
+namespace bmg {
 
 // One iteration's launches on c.stream: refinement mode (FP32 inner CG) or
 // the FP64 outer CG.  parity selects the z buffer written this iteration.
@@ -154,40 +168,54 @@ bmg_status enqueue_iteration(Ctx& c, int parity) {
     return BMG_OK;
 }
 
-// Launches one iteration, from a CUDA graph captured on first use (one per
-// parity) unless profiling is on (per-launch events) or graphs are disabled.
+// Captures one iteration into a CUDA graph (one per parity) on the library's
+// capture stream; a no-op when graphs are off or already captured.
+bmg_status capture_iteration(Ctx& c, int parity) {
+    if (!c.use_graphs || c.prof_on || c.it_exec[parity]) return BMG_OK;
+    if (!c.cap_stream) BMG_CUDA(cudaStreamCreateWithFlags(&c.cap_stream, cudaStreamNonBlocking));
+    cudaStream_t user = c.stream;
+    c.stream = c.cap_stream;
+    cudaGraph_t g = nullptr;
+    bmg_status st = BMG_OK;
+    if (cudaStreamBeginCapture(c.cap_stream, cudaStreamCaptureModeRelaxed) != cudaSuccess) st = BMG_ERR_DEVICE;
+    const long long before = c.launches;
+    if (st == BMG_OK) st = enqueue_iteration(c, parity);
+    c.it_kernels[parity] = c.launches - before;
+    c.launches = before;
+    cudaError_t e = cudaStreamEndCapture(c.cap_stream, &g);
+    c.stream = user;
+    if (st != BMG_OK) {
+        if (g) cudaGraphDestroy(g);
+        return st;
+    }
+    if (e != cudaSuccess) return BMG_ERR_DEVICE;
+    cudaGraphExec_t ex = nullptr;
+    e = cudaGraphInstantiate(&ex, g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) return BMG_ERR_DEVICE;
+    c.it_exec[parity] = ex;
+    return BMG_OK;
+}
+
+// Launches one iteration: a replay of its graph, or the kernels themselves
+// while profiling (per-launch events) or with graphs disabled.
 bmg_status run_iteration(Ctx& c, int parity) {
     if (!c.use_graphs || c.prof_on) return enqueue_iteration(c, parity);
-    if (!c.it_exec[parity]) {
-        if (!c.cap_stream) BMG_CUDA(cudaStreamCreateWithFlags(&c.cap_stream, cudaStreamNonBlocking));
-        cudaStream_t user = c.stream;
-        // order the capture stream after the user's stream (nothing is captured yet)
-        BMG_CUDA(cudaStreamSynchronize(user));
-        c.stream = c.cap_stream;
-        cudaGraph_t g = nullptr;
-        bmg_status st = BMG_OK;
-        if (cudaStreamBeginCapture(c.cap_stream, cudaStreamCaptureModeRelaxed) != cudaSuccess) st = BMG_ERR_DEVICE;
-        const long long before = c.launches;
-        if (st == BMG_OK) st = enqueue_iteration(c, parity);
-        c.it_kernels[parity] = c.launches - before;
-        c.launches = before;
-        cudaError_t e = cudaStreamEndCapture(c.cap_stream, &g);
-        c.stream = user;
-        if (st != BMG_OK) {
-            if (g) cudaGraphDestroy(g);
-            return st;
-        }
-        if (e != cudaSuccess) return BMG_ERR_DEVICE;
-        cudaGraphExec_t ex = nullptr;
-        e = cudaGraphInstantiate(&ex, g, 0);
-        cudaGraphDestroy(g);
-        if (e != cudaSuccess) return BMG_ERR_DEVICE;
-        c.it_exec[parity] = ex;
-    }
+    BMG_TRY(capture_iteration(c, parity));
     BMG_CUDA(cudaGraphLaunch(c.it_exec[parity], c.stream));
     c.launches += c.it_kernels[parity];   // kernels the graph replays
     return BMG_OK;
 }
+
+bmg_status stage_in_async(Ctx& c, const double* src, double* dst);
+bmg_status stage_out_async(Ctx& c, const double* src, double* dst);
+void fill_complexity_info(const Ctx& c, bmg_info* info);
+bmg_status solve_many(Ctx** cs, int count, int nrhs, const double* const* b, double* const* x, double tol,
+                      int maxit, bmg_info* infos);
+
+}  // namespace bmg
+
+namespace {
 
 // Iterative refinement: FP64 residual, inner FP32 flexible CG (FP32 V-cycle)
 // on A d = r for m iterations whose updates go straight into the FP64 iterate
@@ -372,6 +400,7 @@ bmg_status bmg_attach(bmg_ctx* ctx, void* ws, size_t bytes, void* stream) {
     if (!is_device_ptr(ws)) return BMG_ERR_ARG;
     BMG_CUDA(cudaGetDevice(&c.device));
     c.stream = (cudaStream_t)stream;
+    if (!c.st_host) BMG_CUDA(cudaMallocHost((void**)&c.st_host, sizeof(KState)));
     c.ws = (char*)ws;
     carve(c, c.ws);
     BMG_CUDA(cudaMemsetAsync(c.ws, 0, c.ws_need, c.stream));
@@ -479,6 +508,22 @@ bmg_status bmg_adjoint_grad(bmg_ctx* ctx, const double* coords, const double* u,
     return st;
 }
 
+bmg_status bmg_solve_many(bmg_ctx* const* ctxs, int count, int nrhs, const double* const* b, double* const* x,
+                          double tol, int maxit, bmg_info* infos) {
+    if (!ctxs || count < 0 || nrhs < 1 || !b || !x || maxit < 0 || !(tol > 0)) return BMG_ERR_ARG;
+    std::vector<Ctx*> cs(count);
+    for (int p = 0; p < count; p++) {
+        BMG_TRY(check_ready(ctxs[p]));
+        Ctx& c = ctxs[p]->c;
+        if (!c.have_setup) return BMG_ERR_STATE;
+        if (c.opts.outer != BMG_OUTER_REFINEMENT) return BMG_ERR_ARG;
+        for (int r = 0; r < nrhs; r++)
+            if (!b[(long long)p * nrhs + r] || !x[(long long)p * nrhs + r]) return BMG_ERR_ARG;
+        cs[p] = &c;
+    }
+    return solve_many(cs.data(), count, nrhs, b, x, tol, maxit, infos);
+}
+
 int bmg_levels(const bmg_ctx* ctx) { return ctx ? ctx->c.nlev : 0; }
 
 int bmg_level_n(const bmg_ctx* ctx, int level) {
@@ -547,6 +592,7 @@ void bmg_destroy(bmg_ctx* ctx) {
     for (int p = 0; p < 2; p++)
         if (ctx->c.it_exec[p]) cudaGraphExecDestroy(ctx->c.it_exec[p]);
     if (ctx->c.cap_stream) cudaStreamDestroy(ctx->c.cap_stream);
+    if (ctx->c.st_host) cudaFreeHost(ctx->c.st_host);
     for (int k = 0; k < BMG_PROF_KINDS; k++)
         for (cudaEvent_t e : ctx->c.prof[k].ev) cudaEventDestroy(e);
     delete ctx;
