@@ -47,6 +47,10 @@ def parse():
     ap.add_argument("--n", type=int, default=4097)
     ap.add_argument("--cpu-sample-n", type=int, default=1025)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--workload", default="annulus", choices=["annulus", "annulus65", "shell", "batch", "adjoint"],
+                    help="annulus: the 4097^2 quarter annulus (default, the headline); annulus65: 65^2 plain; "
+                         "shell: 257^3 spherical-shell octant; batch: 512 bump-map problems x 4 rhs; "
+                         "adjoint: 1025^2 annulus, batch 8, forward + adjoint")
     return ap.parse_args()
 
 
@@ -348,9 +352,158 @@ def run_reference(args):
     print(json.dumps(out), flush=True)
 
 
+# ---------------------------------------------------------------- other workloads
+def _timed_solves(torch, s, f, steps, warmup, tol=TOL):
+    x = torch.zeros_like(f)
+    for _ in range(warmup):
+        s.solve(f, tol=tol, out=x)
+    torch.cuda.synchronize()
+    l0 = s.launches
+    a = torch.cuda.Event(enable_timing=True)
+    b = torch.cuda.Event(enable_timing=True)
+    infos = []
+    a.record()
+    for _ in range(steps):
+        _, info = s.solve(f, tol=tol, out=x)
+        infos.append(info)
+    b.record()
+    torch.cuda.synchronize()
+    return a.elapsed_time(b) / steps, s.launches - l0, infos
+
+
+def run_single(args, dim, n, problem, name):
+    """FP32-preconditioned (refinement) against plain FP64 on one problem."""
+    import torch
+    from paper_2509_08109_gb300 import binding
+    torch.cuda.set_device(0)
+    out = {"metric": METRIC, "unit": UNIT, "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+           "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "data": "synthetic",
+           "config": {"workload": name, "nodes_per_side": n, "dim": dim, "dof": (n - 2) ** dim, "tol": TOL}}
+    f = torch.as_tensor(problem.rhs, device="cuda")
+    res = {}
+    for prec, outer in (("fp32", "refine"), ("fp32", "flexible"), ("fp64", "cg")):
+        s = binding.Solver(dim, n, precision=prec, outer=outer)
+        t0 = time.perf_counter()
+        s.assemble(torch.as_tensor(problem.coords), torch.as_tensor(problem.kappa)).setup()
+        torch.cuda.synchronize()
+        setup_s = time.perf_counter() - t0
+        ms, launches, infos = _timed_solves(torch, s, f, args.steps, args.warmup)
+        assert all(i.true_relres <= TOL for i in infos)
+        res[f"{prec}_{outer}"] = {"value": (n - 2) ** dim / (ms * 1e-3), "ms_per_step": ms,
+                                  "iterations": infos[-1].iterations, "true_relres": infos[-1].true_relres,
+                                  "gpu_launches": launches, "setup_s": setup_s}
+        del s
+    head = max(("fp32_refine", "fp32_flexible"), key=lambda k: res[k]["value"])
+    out.update({"value": res[head]["value"], "ms_per_step": res[head]["ms_per_step"], "headline_variant": head,
+                "dtype": "f32 V-cycle / f64 residual", "variants": res,
+                "fp32_over_fp64": res["fp64_cg"]["ms_per_step"] / res[head]["ms_per_step"]})
+    print(json.dumps(out), flush=True)
+
+
+def run_batch(args):
+    """512 independent bump-map problems (n = 2^k+1, k in 6..10), 4 rhs each,
+    FP32 refinement, solved concurrently by bmg_solve_many."""
+    os.environ.setdefault("CUDA_DEVICE_MAX_CONNECTIONS", "32")
+    import torch
+    from paper_2509_08109_gb300 import binding, inputs
+    torch.cuda.set_device(0)
+    probs = inputs.bump_batch(count=512, nrhs=4)
+    t0 = time.perf_counter()
+    solvers, bs, xs = [], [], []
+    for p in probs:
+        st = torch.cuda.Stream()
+        s = binding.Solver(2, p.n, precision="fp32", outer="refine", stream=st)
+        s.assemble(torch.as_tensor(p.coords), torch.as_tensor(p.kappa)).setup()
+        solvers.append(s)
+        bs.append([torch.as_tensor(p.rhs[r], device="cuda").contiguous() for r in range(4)])
+        xs.append([torch.zeros_like(b) for b in bs[-1]])
+    torch.cuda.synchronize()
+    setup_s = time.perf_counter() - t0
+    dof = sum((p.n - 2) ** 2 for p in probs) * 4
+    for _ in range(args.warmup):
+        for row in xs:
+            for x in row:
+                x.zero_()
+        binding.solve_many(solvers, bs, xs, tol=TOL)
+    torch.cuda.synchronize()
+    times = []
+    l0 = sum(s.launches for s in solvers)
+    for _ in range(args.steps):
+        for row in xs:
+            for x in row:
+                x.zero_()
+        torch.cuda.synchronize()
+        t = time.perf_counter()
+        infos = binding.solve_many(solvers, bs, xs, tol=TOL)
+        torch.cuda.synchronize()
+        times.append(time.perf_counter() - t)
+    launches = sum(s.launches for s in solvers) - l0
+    worst = max(i.true_relres for row in infos for i in row)
+    assert worst <= TOL
+    its = [i.iterations for row in infos for i in row]
+    ms = statistics.median(times) * 1e3
+    out = {"metric": METRIC, "value": dof / (ms * 1e-3), "unit": UNIT, "n_gpus": 1, "steps": args.steps,
+           "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+           "vs_baseline": None, "dtype": "f32 V-cycle / f64 residual", "data": "synthetic",
+           "config": {"workload": "bump_batch_512x4", "problems": 512, "rhs_per_problem": 4,
+                      "dof_total_all_rhs": dof, "sizes": "n=2^k+1, k~U{6..10}, seed 5", "tol": TOL,
+                      "timing": "host wall clock around bmg_solve_many (device synchronised), median"},
+           "gpu_launches": launches // args.steps, "iterations_min_max": [min(its), max(its)],
+           "worst_true_relres": worst, "setup_s": setup_s}
+    print(json.dumps(out), flush=True)
+
+
+def run_adjoint(args):
+    """1025^2 annulus, per-cell m ~ N(0, 0.5^2), kappa = exp(m), batch 8:
+    forward solve + adjoint gradient per member through torch.autograd."""
+    import torch
+    from paper_2509_08109_gb300 import autograd, binding, inputs
+    torch.cuda.set_device(0)
+    probs = inputs.annulus_adjoint(1025, batch=8)
+    coords = torch.as_tensor(probs[0].coords, device="cuda")
+    ms_ = [torch.as_tensor(p.extra["m"], device="cuda") for p in probs]
+    fs = [torch.as_tensor(p.rhs, device="cuda") for p in probs]
+    uo = [torch.as_tensor(p.extra["u_obs"], device="cuda") for p in probs]
+    solvers = [binding.Solver(2, 1025, precision="fp64", outer="cg") for _ in probs]
+
+    def step():
+        ms = [m.clone().requires_grad_(True) for m in ms_]
+        us = autograd.solve_batch(ms, fs, coords, solvers, tol=TOL)
+        loss = sum(0.5 * ((u - o) ** 2).sum() for u, o in zip(us, uo))
+        loss.backward()
+        return [m.grad for m in ms]
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    times = []
+    for _ in range(args.steps):
+        t = time.perf_counter()
+        step()
+        torch.cuda.synchronize()
+        times.append(time.perf_counter() - t)
+    ms = statistics.median(times) * 1e3
+    dof = 8 * 1023 ** 2
+    out = {"metric": "forward+adjoint DoF/s (batch 8, each member: assemble, setup, solve, adjoint solve, dA/dkappa)",
+           "value": dof / (ms * 1e-3), "unit": UNIT, "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+           "ms_per_step": ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+           "data": "synthetic", "config": {"workload": "annulus_adjoint_n1025_batch8", "tol": TOL}}
+    print(json.dumps(out), flush=True)
+
+
 if __name__ == "__main__":
     a = parse()
     if a.impl == "reference":
         run_reference(a)
-    else:
+    elif a.workload == "annulus":
         run_own(a)
+    elif a.workload == "annulus65":
+        from paper_2509_08109_gb300 import inputs as _inp
+        run_single(a, 2, 65, _inp.annulus_plain(65), "quarter_annulus_plain_n65")
+    elif a.workload == "shell":
+        from paper_2509_08109_gb300 import inputs as _inp
+        run_single(a, 3, 257, _inp.shell_two_layer(257), "shell_octant_two_layer_n257")
+    elif a.workload == "batch":
+        run_batch(a)
+    else:
+        run_adjoint(a)
