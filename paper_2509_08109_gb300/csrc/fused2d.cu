@@ -303,26 +303,37 @@ __global__ void __launch_bounds__(72 * K) k_vdown2d(const __grid_constant__ CUte
         if (ty == 0) resid(2 * J0 - 1);
         __syncthreads();
     }
+    // interpolation weights of the thread's coarse node for the restriction,
+    // loaded one step ahead
+    T w[8];
+    auto load_w = [&](int Jp) {
+        const bool d = vres && Jp <= nc - 2;
+        const long long o = (long long)Jp * p.ldc + I;
+        w[0] = d ? Pg[PXR * p.plc + o - 1] : (T)0;
+        w[1] = d ? Pg[PXL * p.plc + o] : (T)0;
+        w[2] = d ? Pg[PYN * p.plc + o - p.ldc] : (T)0;
+        w[3] = d ? Pg[PYS * p.plc + o] : (T)0;
+        w[4] = d ? Pg[PNE * p.plc + o - p.ldc - 1] : (T)0;
+        w[5] = d ? Pg[PNW * p.plc + o - p.ldc] : (T)0;
+        w[6] = d ? Pg[PSE * p.plc + o - 1] : (T)0;
+        w[7] = d ? Pg[PSW * p.plc + o] : (T)0;
+    };
+    load_w(J0 + ty);
     for (int J = J0; ok && J < J0 + p.hc; J += K) {
         const int qa = J - rg.q0;
         ok = wait_pairs<RP>(rg.bars, qa, qa + K);
         if (!ok) break;
         waited = qa + K;
+        // every thread is past the previous step: refill its freed slots with
+        // the next step's row pairs
+        if (lead && J > J0)
+            for (int t = 0; t < K; t++) {
+                const int q = qa + K + t;
+                if (q < npairs) issue(q);
+            }
+        issued = max(issued, min(npairs, qa + 2 * K));
         const int Jp = J + ty, jm = 2 * Jp, jo = jm + 1, je = jm + 2;
-        // interpolation weights of coarse node (I, Jp) for the restriction
-        T w[8] = {0, 0, 0, 0, 0, 0, 0, 0};
         const bool do_res = vres && Jp <= nc - 2;
-        if (do_res) {
-            const long long o = (long long)Jp * p.ldc + I;
-            w[0] = Pg[PXR * p.plc + o - 1];
-            w[1] = Pg[PXL * p.plc + o];
-            w[2] = Pg[PYN * p.plc + o - p.ldc];
-            w[3] = Pg[PYS * p.plc + o];
-            w[4] = Pg[PNE * p.plc + o - p.ldc - 1];
-            w[5] = Pg[PNW * p.plc + o - p.ldc];
-            w[6] = Pg[PSE * p.plc + o - 1];
-            w[7] = Pg[PSW * p.plc + o];
-        }
         c0(je);
         __syncthreads();
         c1(je);
@@ -350,6 +361,7 @@ __global__ void __launch_bounds__(72 * K) k_vdown2d(const __grid_constant__ CUte
             b += w[7] * Rn[c + 1];
             bcg[(long long)Jp * p.ldc + I] = b;
         }
+        load_w(Jp + K);
         // finished rows 2Jp-1 and 2Jp of the owned columns
         if (inrow(jm - 1)) {
             const T* Xr = X(jm - 1);
@@ -361,13 +373,9 @@ __global__ void __launch_bounds__(72 * K) k_vdown2d(const __grid_constant__ CUte
             if (own_e) xg[(long long)jm * p.ldf + ie] = Xr[ce];
             if (own_o) xg[(long long)jm * p.ldf + ie + 1] = Xr[co];
         }
-        __syncthreads();
-        if (lead)
-            for (int t = 0; t < K; t++) {
-                const int q = qa - 2 + t + RP;
-                if (q < npairs) issue(q);
-            }
-        issued = min(npairs, qa - 2 + K + RP);
+        // no barrier here: the next step's writes (rows 2Jp+2K+1.. of the X and R
+        // rings) do not alias rows read above, and slots are refilled only after
+        // the next step's first barrier
     }
     if (!ok) {
         if (lead) {
@@ -491,17 +499,34 @@ __global__ void __launch_bounds__(72 * K) k_vup2d(const __grid_constant__ CUtens
         if (ty == 0) gs(2 * J0 - 1, ce, ve);     // colour 2
         __syncthreads();
     }
+    // weights for the corrected values of this thread's rows, loaded one step ahead
+    T wy[6], wxl, wxr;
+    auto load_w = [&](int Jp) {
+        wy[0] = pw(PYS, Jp);
+        wy[1] = pw(PYN, Jp);
+        wy[2] = pw(PSW, Jp);
+        wy[3] = pw(PSE, Jp);
+        wy[4] = pw(PNW, Jp);
+        wy[5] = pw(PNE, Jp);
+        wxl = pw(PXL, Jp + 1);
+        wxr = pw(PXR, Jp + 1);
+    };
+    load_w(J0 + ty);
     for (int J = J0; ok && J < J0 + p.hc; J += K) {
         const int qa = J - rg.q0;
-        // weights for the corrected values of this thread's rows (loaded before the wait)
         const int Jp = J + ty, jm = 2 * Jp, jo = jm + 1, je = jm + 2;
-        const T wy[6] = {pw(PYS, Jp), pw(PYN, Jp), pw(PSW, Jp), pw(PSE, Jp), pw(PNW, Jp), pw(PNE, Jp)};
-        const T wxl = pw(PXL, Jp + 1), wxr = pw(PXR, Jp + 1);
         ok = wait_pairs<RP>(rg.bars, qa, qa + K);
         if (!ok) break;
         waited = qa + K;
+        if (lead && J > J0)
+            for (int t = 0; t < K; t++) {
+                const int q = qa + K + t;
+                if (q < npairs) issue(q);
+            }
+        issued = max(issued, min(npairs, qa + 2 * K));
         corr_odd(jo, wy);
         corr_even(je, wxl, wxr);
+        load_w(Jp + K);
         __syncthreads();
         gs(jo, co, vo);      // colour 3
         __syncthreads();
@@ -521,13 +546,6 @@ __global__ void __launch_bounds__(72 * K) k_vup2d(const __grid_constant__ CUtens
             if (own_e) out[(long long)jm * p.ldf + ie] = (TO)Xr[ce];
             if (own_o) out[(long long)jm * p.ldf + ie + 1] = (TO)Xr[co];
         }
-        __syncthreads();
-        if (lead)
-            for (int t = 0; t < K; t++) {
-                const int q = qa - 2 + t + RP;
-                if (q < npairs) issue(q);
-            }
-        issued = min(npairs, qa - 2 + K + RP);
     }
     if (!ok) {
         if (lead) {

@@ -12,7 +12,7 @@ from tests.gpu_util import relerr
 pytestmark = pytest.mark.gpu
 
 
-def _grad(prob, tol=1e-13):
+def _grad(prob, tol=1e-12):
     dev = "cuda"
     coords = torch.as_tensor(prob.coords, device=dev)
     m = torch.as_tensor(prob.extra["m"], device=dev).requires_grad_(True)
@@ -41,7 +41,7 @@ def test_gradient_matches_central_differences():
     as 1/2 sum (u+ - u-)(u+ + u- - 2 u_obs) to avoid cancellation; relative
     error against max(|g_e|, 1e-3 max|g|)."""
     (prob,) = inputs.annulus_adjoint(129, batch=1)
-    _, gm, _, u = _grad(prob, tol=1e-14)
+    _, gm, _, u = _grad(prob, tol=1e-12)
     s = binding.Solver(2, prob.n)
     rng = np.random.default_rng(3)
     cells = [tuple(c) for c in rng.integers(0, prob.n - 1, size=(8, 2))]
@@ -54,7 +54,7 @@ def test_gradient_matches_central_differences():
             mm = prob.extra["m"].copy()
             mm[c] += sgn * eps
             s.assemble(torch.as_tensor(prob.coords), torch.as_tensor(np.exp(mm))).setup()
-            x, _ = s.solve(f, x0=torch.as_tensor(u, device="cuda"), tol=1e-14, maxit=500, raise_on_nonconv=False)
+            x, _ = s.solve(f, x0=torch.as_tensor(u, device="cuda"), tol=1e-12, maxit=500)
             sols.append(x.cpu().numpy())
         up, um = sols
         dL = 0.5 * np.sum((up - um) * (up + um - 2 * prob.extra["u_obs"]))
@@ -68,7 +68,7 @@ def test_batch_of_independent_members():
     ms = [torch.as_tensor(p.extra["m"], device="cuda").requires_grad_(True) for p in probs]
     fs = [torch.as_tensor(p.rhs, device="cuda") for p in probs]
     solvers = [binding.Solver(2, 33) for _ in probs]
-    us = autograd.solve_batch(ms, fs, coords, solvers, tol=1e-13)
+    us = autograd.solve_batch(ms, fs, coords, solvers, tol=1e-12)
     loss = sum(0.5 * ((u - torch.as_tensor(p.extra["u_obs"], device="cuda")) ** 2).sum() for u, p in zip(us, probs))
     loss.backward()
     for p, m in zip(probs, ms):
