@@ -220,6 +220,20 @@ bmg_status bmg_profile(bmg_ctx* ctx, int enable);
    bytes of one class (synchronises the stream). */
 bmg_status bmg_profile_read(bmg_ctx* ctx, int kind, double* ms, long long* launches, double* bytes);
 
+/* Tile shape of the streaming 2-D V-cycle kernels on level `level` (the
+   kernels that go from level to level+1 and back): wc coarse columns and
+   hc coarse rows per CTA.  set: wc in {8,16,32,64}, hc a positive multiple
+   of the rows per step (4 in FP32, 2 in FP64); BMG_ERR_ARG otherwise or when
+   the context does not use the streaming kernels. */
+bmg_status bmg_get_tiles(const bmg_ctx* ctx, int level, int* wc, int* hc);
+bmg_status bmg_set_tiles(bmg_ctx* ctx, int level, int wc, int hc);
+
+/* Autotuner: after bmg_setup, times candidate tile shapes of every level on
+   the device (the level's down and up kernels, best of reps runs) and keeps
+   the fastest; *ms (may be NULL) receives the sum of the chosen times.  The
+   choice can be read back with bmg_get_tiles and cached by the caller. */
+bmg_status bmg_autotune(bmg_ctx* ctx, int reps, double* ms);
+
 /* Kernel launches the context has issued since creation (all kinds). */
 long long bmg_launch_count(const bmg_ctx* ctx);
 

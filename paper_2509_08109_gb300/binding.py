@@ -84,6 +84,9 @@ def load() -> ctypes.CDLL:
         "bmg_get_stencil": ([P, I, P], I),
         "bmg_get_interp": ([P, I, P], I),
         "bmg_launch_count": ([P], ctypes.c_longlong),
+        "bmg_get_tiles": ([P, I, ctypes.POINTER(I), ctypes.POINTER(I)], I),
+        "bmg_set_tiles": ([P, I, I, I], I),
+        "bmg_autotune": ([P, I, ctypes.POINTER(D)], I),
         "bmg_profile": ([P, I], I),
         "bmg_profile_read": ([P, I, ctypes.POINTER(D), ctypes.POINTER(ctypes.c_longlong), ctypes.POINTER(D)], I),
         "bmg_destroy": ([P], None),
@@ -101,7 +104,8 @@ def exported_symbols() -> list:
     return ["bmg_default_opts", "bmg_create", "bmg_workspace_bytes", "bmg_attach", "bmg_assemble",
             "bmg_set_stencil", "bmg_setup", "bmg_vcycle", "bmg_solve", "bmg_solve_many", "bmg_adjoint_grad",
             "bmg_levels",
-            "bmg_level_n", "bmg_get_stencil", "bmg_get_interp", "bmg_launch_count", "bmg_profile",
+            "bmg_level_n", "bmg_get_stencil", "bmg_get_interp", "bmg_launch_count", "bmg_get_tiles",
+            "bmg_set_tiles", "bmg_autotune", "bmg_profile",
             "bmg_profile_read", "bmg_destroy", "bmg_status_str"]
 
 
@@ -266,6 +270,47 @@ class Solver:
                                            float(tol), int(maxit), ctypes.byref(info)), "bmg_adjoint_grad")
         return lam, dk, SolveInfo(info.iterations, info.levels, info.relres, info.true_relres, info.rho,
                                   info.grid_complexity, info.operator_complexity, info.status)
+
+    # ------------------------------------------------------------ tile shapes
+    def tiles(self) -> list:
+        """[(wc, hc)] per level pair of the streaming kernels ([] if unused)."""
+        out = []
+        for l in range(self.levels - 1):
+            wc, hc = ctypes.c_int(), ctypes.c_int()
+            if load().bmg_get_tiles(self._h, l, ctypes.byref(wc), ctypes.byref(hc)) != 0:
+                return []
+            out.append((wc.value, hc.value))
+        return out
+
+    def set_tiles(self, tiles):
+        for l, (wc, hc) in enumerate(tiles):
+            _check(load().bmg_set_tiles(self._h, l, int(wc), int(hc)), "bmg_set_tiles")
+
+    def autotune(self, reps: int = 3, cache: str | None = None) -> list:
+        """Device-timed choice of the tile shapes (bmg_autotune).  With a
+        cache file (JSON), reuse the choice stored for this GPU, grid and
+        precision, or store the new one."""
+        import json
+        key = f"{torch.cuda.get_device_name(self.device)}|d{self.dim}|n{self.n}|{self.precision}|{self.outer}"
+        table = {}
+        if cache and os.path.exists(cache):
+            try:
+                table = json.load(open(cache))
+            except ValueError:
+                table = {}
+            if key in table:
+                self.set_tiles(table[key])
+                return self.tiles()
+        ms = ctypes.c_double()
+        with torch.cuda.device(self.device):
+            _check(load().bmg_autotune(self._h, int(reps), ctypes.byref(ms)), "bmg_autotune")
+        t = self.tiles()
+        if cache:
+            table[key] = t
+            tmp = cache + f".tmp{os.getpid()}"
+            json.dump(table, open(tmp, "w"), indent=1)
+            os.replace(tmp, cache)
+        return t
 
     # ------------------------------------------------------------ profiling
     PROF_KINDS = {"smooth": 0, "residual": 1, "restrict": 2, "prolong": 3, "spmv": 4, "update": 5,

@@ -585,6 +585,39 @@ bmg_status bmg_profile_read(bmg_ctx* ctx, int kind, double* ms, long long* launc
     return BMG_OK;
 }
 
+bmg_status bmg_get_tiles(const bmg_ctx* ctx, int level, int* wc, int* hc) {
+    if (!ctx || !wc || !hc) return BMG_ERR_ARG;
+    const Ctx& c = ctx->c;
+    if (!c.use_fused || level < 0 || level >= c.nlev - 1) return BMG_ERR_ARG;
+    *wc = c.fused[level].wc;
+    *hc = c.fused[level].hc;
+    return BMG_OK;
+}
+
+bmg_status bmg_set_tiles(bmg_ctx* ctx, int level, int wc, int hc) {
+    BMG_TRY(check_ready(ctx));
+    Ctx& c = ctx->c;
+    if (!c.use_fused || level < 0 || level >= c.nlev - 1) return BMG_ERR_ARG;
+    BMG_CUDA(cudaStreamSynchronize(c.stream));
+    return fused_configure(c, level, wc, hc);
+}
+
+bmg_status bmg_autotune(bmg_ctx* ctx, int reps, double* ms) {
+    BMG_TRY(check_ready(ctx));
+    Ctx& c = ctx->c;
+    if (!c.have_setup) return BMG_ERR_STATE;
+    if (reps < 1) return BMG_ERR_ARG;
+    BMG_CUDA(cudaStreamSynchronize(c.stream));
+    const bool prof = c.prof_on;
+    c.prof_on = false;
+    bmg_status st = fused_autotune(c, reps, ms);
+    c.prof_on = prof;
+    if (st != BMG_OK) return st;
+    KState h;
+    BMG_TRY(read_state(c, h));
+    return h.err ? (bmg_status)h.err : BMG_OK;
+}
+
 long long bmg_launch_count(const bmg_ctx* ctx) { return ctx ? ctx->c.launches : 0; }
 
 void bmg_destroy(bmg_ctx* ctx) {

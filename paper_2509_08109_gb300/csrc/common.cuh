@@ -275,6 +275,8 @@ bmg_status vcycle_f32(Ctx& c, float* z32);       // z32 = M r32 (FP32 in and out
 template <typename T>
 bmg_status vcycle3d_impl(Ctx& c, const T* b0, T* x0, T* xout);
 bmg_status fused_prepare(Ctx& c);
+bmg_status fused_configure(Ctx& c, int l, int wc, int hc);
+bmg_status fused_autotune(Ctx& c, int reps, double* best_ms_total);
 bmg_status demote_levels(Ctx& c);
 // krylov.cu
 bmg_status k_pack(Ctx& c, const double* src, double* dst);      // n^d -> padded, boundary zeroed

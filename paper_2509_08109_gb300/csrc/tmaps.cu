@@ -41,60 +41,148 @@ bool make_map(CUtensorMap* m, bool f64, const void* base, int ld, int rows, int 
 
 }  // namespace
 
-bmg_status fused_prepare(Ctx& c) {
+// Rows per CTA (a multiple of the rows per step) for a given column width:
+// minimise waves x (rows + pre-roll) with the kernels' occupancy.
+bmg_status model_rows(Ctx& c, int l, int wc, int* hc_out, int* tiles_y_out) {
     const bool f32 = c.opts.precision == BMG_PREC_FP32;
     int sms = 0;
     BMG_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, c.device));
-    for (int l = 0; l + 1 < c.nlev; l++) {
-        FusedLevel& F = c.fused[l];
-        const Level& Lf = c.lev[l];
-        const Level& Lc = c.lev[l + 1];
-        // Tiles cover coarse indices 1 .. nc-1: coarse index J owns the fine rows
-        // 2J-1 and 2J, so the boundary index nc-1 still owns fine row nf-2.
-        const int m = Lc.n - 1;
-        F.wc = m >= 512 ? 64 : m >= 128 ? 32 : m >= 32 ? 16 : 8;
-        F.tiles_x = cdiv(m, F.wc);
-        int od = 0, ou = 0;
-        BMG_TRY(fused_occupancy(f32, f32 && l == 0, F.wc, &od, &ou));
-        const int occ = od < ou ? od : ou;
-        if (occ < 1) return BMG_ERR_DEVICE;
-        const long long slots = (long long)occ * sms;
-        // rows per CTA (a multiple of the rows per step): minimise waves x (rows + pre-roll)
-        const int K = fused_rows_per_step(f32);
-        long long best = -1;
-        for (int ty = 1; ty <= m; ty++) {
-            const int hc = cdiv(cdiv(m, ty), K) * K;
-            const int tyr = cdiv(m, hc);
-            const long long waves = cdiv((long long)F.tiles_x * tyr, slots);
-            const long long cost = waves * (2LL * hc + 3);
-            if (best < 0 || cost < best) {
-                best = cost;
-                F.hc = hc;
-                F.tiles_y = tyr;
-            }
-        }
-        const int WW = 2 * F.wc + 16, WWc = F.wc + 8;
-        const void* A = f32 ? (const void*)Lf.A32 : (const void*)Lf.A64;
-        const void* P = f32 ? (const void*)Lf.P32 : (const void*)Lf.P64;
-        const void* f = l == 0 ? (const void*)c.r : Lf.b;
-        const bool f_is64 = l == 0 || !f32;
-        bool ok = make_map(&F.mA, !f32, A, Lf.ld, Lf.n, c.ns, Lf.plane, WW, 2);
-        ok = ok && make_map(&F.mF, f_is64, f, Lf.ld, Lf.n, 1, Lf.plane, WW, 2);
-        ok = ok && make_map(&F.mXp, !f32, Lf.x, Lf.ld, Lf.n, 1, Lf.plane, WW, 2);
-        ok = ok && make_map(&F.mXc, !f32, Lc.r, Lc.ld, Lc.n, 1, Lc.plane, WWc, 1);
-        if (!ok) return BMG_ERR_DEVICE;
-        F.down = FusedArgs{Lf.n, Lc.n, Lf.ld, Lc.ld, F.wc, F.hc, Lf.x, Lc.b, P, Lc.plane, c.st};
-        F.up = FusedArgs{Lf.n, Lc.n, Lf.ld, Lc.ld, F.wc, F.hc, nullptr, nullptr, P, Lc.plane, c.st};
-        F.ready = true;
-        if (l == 0 && c.r32) {
-            // refinement mode: the level-0 kernels read the FP32 inner residual
-            FusedLevel& G = c.fused_ir0;
-            G = F;
-            int od2 = 0, ou2 = 0;
-            BMG_TRY(fused_occupancy(true, false, F.wc, &od2, &ou2));
-            if (!make_map(&G.mF, false, c.r32, Lf.ld, Lf.n, 1, Lf.plane, WW, 2)) return BMG_ERR_DEVICE;
+    const int m = c.lev[l + 1].n - 1;
+    const int tiles_x = cdiv(m, wc);
+    int od = 0, ou = 0;
+    BMG_TRY(fused_occupancy(f32, f32 && l == 0, wc, &od, &ou));
+    const int occ = od < ou ? od : ou;
+    if (occ < 1) return BMG_ERR_DEVICE;
+    const long long slots = (long long)occ * sms;
+    const int K = fused_rows_per_step(f32);
+    long long best = -1;
+    for (int ty = 1; ty <= m; ty++) {
+        const int hc = cdiv(cdiv(m, ty), K) * K;
+        const int tyr = cdiv(m, hc);
+        const long long waves = cdiv((long long)tiles_x * tyr, slots);
+        const long long cost = waves * (2LL * hc + 3);
+        if (best < 0 || cost < best) {
+            best = cost;
+            *hc_out = hc;
+            *tiles_y_out = tyr;
         }
     }
+    return BMG_OK;
+}
+
+// Tile shape (wc coarse columns, hc coarse rows per CTA) of level l: kernel
+// arguments and the TMA maps, whose boxes depend on wc.
+bmg_status fused_configure(Ctx& c, int l, int wc, int hc) {
+    const bool f32 = c.opts.precision == BMG_PREC_FP32;
+    const int K = fused_rows_per_step(f32);
+    if (wc != 8 && wc != 16 && wc != 32 && wc != 64) return BMG_ERR_ARG;
+    if (hc < K || hc % K) return BMG_ERR_ARG;
+    FusedLevel& F = c.fused[l];
+    const Level& Lf = c.lev[l];
+    const Level& Lc = c.lev[l + 1];
+    // Tiles cover coarse indices 1 .. nc-1: coarse index J owns the fine rows
+    // 2J-1 and 2J, so the boundary index nc-1 still owns fine row nf-2.
+    const int m = Lc.n - 1;
+    F.wc = wc;
+    F.hc = hc;
+    F.tiles_x = cdiv(m, wc);
+    F.tiles_y = cdiv(m, hc);
+    const int WW = 2 * F.wc + 16, WWc = F.wc + 8;
+    const void* A = f32 ? (const void*)Lf.A32 : (const void*)Lf.A64;
+    const void* P = f32 ? (const void*)Lf.P32 : (const void*)Lf.P64;
+    const void* f = l == 0 ? (const void*)c.r : Lf.b;
+    const bool f_is64 = l == 0 || !f32;
+    bool ok = make_map(&F.mA, !f32, A, Lf.ld, Lf.n, c.ns, Lf.plane, WW, 2);
+    ok = ok && make_map(&F.mF, f_is64, f, Lf.ld, Lf.n, 1, Lf.plane, WW, 2);
+    ok = ok && make_map(&F.mXp, !f32, Lf.x, Lf.ld, Lf.n, 1, Lf.plane, WW, 2);
+    ok = ok && make_map(&F.mXc, !f32, Lc.r, Lc.ld, Lc.n, 1, Lc.plane, WWc, 1);
+    if (!ok) return BMG_ERR_DEVICE;
+    F.down = FusedArgs{Lf.n, Lc.n, Lf.ld, Lc.ld, F.wc, F.hc, Lf.x, Lc.b, P, Lc.plane, c.st};
+    F.up = FusedArgs{Lf.n, Lc.n, Lf.ld, Lc.ld, F.wc, F.hc, nullptr, nullptr, P, Lc.plane, c.st};
+    F.ready = true;
+    if (l == 0 && c.r32) {
+        // refinement mode: the level-0 kernels read the FP32 inner residual
+        FusedLevel& G = c.fused_ir0;
+        G = F;
+        int od2 = 0, ou2 = 0;
+        BMG_TRY(fused_occupancy(true, false, F.wc, &od2, &ou2));
+        if (!make_map(&G.mF, false, c.r32, Lf.ld, Lf.n, 1, Lf.plane, WW, 2)) return BMG_ERR_DEVICE;
+    }
+    // captured iteration graphs hold the old launch shapes
+    for (int p = 0; p < 2; p++)
+        if (c.it_exec[p]) {
+            cudaGraphExecDestroy(c.it_exec[p]);
+            c.it_exec[p] = nullptr;
+        }
+    return BMG_OK;
+}
+
+bmg_status fused_prepare(Ctx& c) {
+    for (int l = 0; l + 1 < c.nlev; l++) {
+        const int m = c.lev[l + 1].n - 1;
+        const int wc = m >= 512 ? 64 : m >= 128 ? 32 : m >= 32 ? 16 : 8;
+        int hc = 0, ty = 0;
+        BMG_TRY(model_rows(c, l, wc, &hc, &ty));
+        BMG_TRY(fused_configure(c, l, wc, hc));
+    }
+    return BMG_OK;
+}
+
+// Measures candidate tile shapes of every level (down + up kernel pair,
+// CUDA events, best of reps) and keeps the fastest.  Candidates: each legal
+// column width with the modelled row count, half and twice that count.
+// Runs the kernels on the context's scratch vectors (they hold no state
+// between V-cycles).
+bmg_status fused_autotune(Ctx& c, int reps, double* best_ms_total) {
+    if (!c.use_fused) return BMG_OK;
+    const bool f32 = c.opts.precision == BMG_PREC_FP32;
+    const int K = fused_rows_per_step(f32);
+    cudaEvent_t e0, e1;
+    BMG_CUDA(cudaEventCreate(&e0));
+    BMG_CUDA(cudaEventCreate(&e1));
+    double total = 0.0;
+    const bool ir = c.opts.outer == BMG_OUTER_REFINEMENT;
+    void* out0 = ir ? (void*)c.z32[0] : (void*)c.z[0];
+    for (int l = 0; l + 1 < c.nlev; l++) {
+        const int m = c.lev[l + 1].n - 1;
+        int best_wc = c.fused[l].wc, best_hc = c.fused[l].hc;
+        float best = -1.f;
+        for (int wc = 8; wc <= 64; wc *= 2) {
+            if (cdiv(m, wc) < 1 || (wc > 8 && m < wc / 2)) continue;
+            int hc0 = 0, ty = 0;
+            BMG_TRY(model_rows(c, l, wc, &hc0, &ty));
+            const int cands[3] = {hc0, (hc0 / 2 / K) * K, hc0 * 2};
+            for (int ci = 0; ci < 3; ci++) {
+                const int hc = cands[ci];
+                if (hc < K || (ci > 0 && hc == hc0) || hc > cdiv(m, K) * K + K) continue;
+                BMG_TRY(fused_configure(c, l, wc, hc));
+                void* out = l == 0 ? out0 : c.lev[l].r;
+                BMG_TRY(fused_down(c, l, ir));
+                BMG_TRY(fused_up(c, l, out, ir));
+                float tbest = -1.f;
+                for (int r = 0; r < reps; r++) {
+                    BMG_CUDA(cudaEventRecord(e0, c.stream));
+                    BMG_TRY(fused_down(c, l, ir));
+                    BMG_TRY(fused_up(c, l, out, ir));
+                    BMG_CUDA(cudaEventRecord(e1, c.stream));
+                    BMG_CUDA(cudaEventSynchronize(e1));
+                    float t = 0.f;
+                    BMG_CUDA(cudaEventElapsedTime(&t, e0, e1));
+                    if (tbest < 0 || t < tbest) tbest = t;
+                }
+                if (best < 0 || tbest < best) {
+                    best = tbest;
+                    best_wc = wc;
+                    best_hc = hc;
+                }
+            }
+        }
+        BMG_TRY(fused_configure(c, l, best_wc, best_hc));
+        total += best;
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (best_ms_total) *best_ms_total = total;
     return BMG_OK;
 }
 

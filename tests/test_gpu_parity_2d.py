@@ -239,3 +239,27 @@ def test_refinement_reaches_fp64_tolerance(n, unfused):
         r = p.rhs - oracle.apply(A, x.cpu().numpy())
         r[0, :] = r[-1, :] = r[:, 0] = r[:, -1] = 0
         assert np.linalg.norm(r) / np.linalg.norm(p.rhs) <= 1.01e-10
+
+
+# ------------------------------------------------------------------ tile autotuner
+def test_autotune_keeps_results_bitwise(tmp_path):
+    """Tile shapes change only which CTA computes a node (halo columns are
+    recomputed identically), so the V-cycle and the solve are bitwise
+    unchanged; the choice round-trips through the cache file."""
+    p = _problem(1025)
+    for prec, outer in (("fp64", "cg"), ("fp32", "refine")):
+        s = solver_for(p, precision=prec, outer=outer)
+        r = torch.as_tensor(inputs.rhs_uniform(np.random.default_rng(9), (1025, 1025)), device="cuda")
+        z0 = s.vcycle(r).clone()
+        x0, i0 = s.solve(r, tol=1e-10)
+        before = s.tiles()
+        cache = str(tmp_path / "tiles.json")
+        after = s.autotune(reps=2, cache=cache)
+        assert len(after) == len(before) == s.levels - 1
+        assert torch.equal(s.vcycle(r), z0)
+        x1, i1 = s.solve(r, tol=1e-10)
+        assert torch.equal(x1, x0) and i1.iterations == i0.iterations
+        s2 = solver_for(p, precision=prec, outer=outer)
+        assert s2.autotune(cache=cache) == after
+    with pytest.raises(binding.BmgError):
+        s.set_tiles([(24, 4)])
