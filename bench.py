@@ -170,6 +170,15 @@ def cpu_baseline(n_sample: int) -> dict:
                       f"({p.unknowns} DoF, {it} iterations, {dt:.2f} s), single-threaded C oracle"}
 
 
+# ---------------------------------------------------------------- replicas
+def whole_job_throughput(local_ms: float, dof_per_rank: int, steps: int, world: int, reduce_max) -> tuple:
+    """Weak-scaling replicas: every rank solves its own copy; the job's time
+    is the slowest rank's, and the job's throughput counts every rank's
+    unknowns.  reduce_max(v) returns the maximum of v over the ranks."""
+    ms = reduce_max(local_ms)
+    return world * dof_per_rank * steps / (ms * 1e-3), ms
+
+
 # ---------------------------------------------------------------- own arm
 def run_own(args):
     import torch
@@ -262,7 +271,7 @@ def run_own(args):
     ms32, launches32, infos32, prof32, ck, shead = variants[head]
     t32 = ms32 / args.steps
     t64 = ms64 / args.steps
-    value = world * dof / (t32 * 1e-3)
+    value, _ = whole_job_throughput(t32, dof, 1, world, lambda v: v)   # ms32 is already the max over ranks
 
     # end to end through the public API with host (pinned) buffers
     fh = f.cpu().pin_memory()
