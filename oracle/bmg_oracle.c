@@ -10,7 +10,11 @@
  * operators, V-cycle).  The paper does not spell out BoxMG's formulas (it
  * cites Dendy 1982); the readings used here are the textbook ones:
  *   - interpolation by collapsing the fine stencil onto lines (edge points)
- *     and solving the fine equation at interior points;
+ *     and solving the fine equation at interior points; where a collapsed
+ *     denominator is not positive (the collapse assumption fails on
+ *     operators with strong positive couplings, e.g. coarse Galerkin
+ *     operators of a degenerate map), that point uses its own uncollapsed
+ *     couplings instead (the diagonal of an SPD operator is positive);
  *   - restriction R = P^T (Sec. 2.3, the transpose relation derived through
  *     Riesz maps);
  *   - coarse operators A_{l+1} = P^T A_l P, formed here by the definition,
@@ -455,7 +459,16 @@ int or_interp(int dim, int nf, const double* A, double* pw) {
                 double AL = collapsed(dim, A, f, 1 << a, km);
                 double A0 = collapsed(dim, A, f, 1 << a, k0);
                 double AR = collapsed(dim, A, f, 1 << a, kp);
-                if (!(fabs(A0) > 1e-300)) return OR_ERR_BREAKDOWN;
+                if (!(A0 > 0.0)) {
+                    /* collapse not usable: the point's own couplings along the axis */
+                    int S = (int)pw_int(3, dim), ctr = (S - 1) / 2;
+                    int dm[3] = {0, 0, 0}, dp[3] = {0, 0, 0};
+                    dm[a] = -1; dp[a] = 1;
+                    AL = A[f * S + slot_of(dim, dm)];
+                    AR = A[f * S + slot_of(dim, dp)];
+                    A0 = A[f * S + ctr];
+                    if (!(A0 > 0.0)) return OR_ERR_BREAKDOWN;
+                }
                 int cl[3] = {c[0], c[1], c[2]}, cr[3] = {c[0], c[1], c[2]};
                 cl[a] -= 1; cr[a] += 1;
                 int kl[3] = {cl[0] / 2, cl[1] / 2, cl[2] / 2}, kr[3] = {cr[0] / 2, cr[1] / 2, cr[2] / 2};
@@ -479,6 +492,17 @@ int or_interp(int dim, int nf, const double* A, double* pw) {
                     coef[slot_of(dim, dp)] += A[f * S + o];
                 }
                 diag = coef[ctr];
+                if (!(diag > 0.0) && evenmask) {
+                    /* collapse not usable: the point's own in-plane couplings */
+                    for (int o = 0; o < S; o++) {
+                        int d[3], inplane = 1;
+                        offset_of(dim, o, d);
+                        for (int a = 0; a < dim; a++)
+                            if (((evenmask >> a) & 1) && d[a] != 0) inplane = 0;
+                        coef[o] = inplane ? A[f * S + o] : 0.0;
+                    }
+                    diag = coef[ctr];
+                }
                 if (!(diag > 0.0)) return OR_ERR_BREAKDOWN;
                 for (int o = 0; o < S; o++) {
                     if (o == ctr || coef[o] == 0.0) continue;

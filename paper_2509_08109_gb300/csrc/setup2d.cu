@@ -126,6 +126,8 @@ __global__ void k_set_stencil2d(int n, int ld, long long pl, const double* __res
 // Edge points of the fine grid, owned by coarse node (I,J):
 //   (2I+1, 2J): collapse the stencil over dy -> weights -A_L/A_0, -A_R/A_0
 //   (2I, 2J+1): collapse over dx               -> weights -A_S/A_0, -A_N/A_0
+// Where the collapsed denominator A_0 is not positive the point uses its own
+// couplings along the line instead (A_0 = a_00 > 0 for an SPD operator).
 // Weights to boundary coarse nodes and rows of boundary fine points are 0.
 __global__ void k_interp_edges2d(Sten2<double> F, int nf, int nc, int ldc, long long plc,
                                  double* __restrict__ P, KState* st) {
@@ -137,10 +139,15 @@ __global__ void k_interp_edges2d(Sten2<double> F, int nf, int nc, int ldc, long 
     {   // x-edge point
         const int i = 2 * I + 1, j = 2 * J;
         if (i <= nf - 2 && j >= 1 && j <= nf - 2) {
-            const double AL = F.full(i, j, -1, -1) + F.full(i, j, -1, 0) + F.full(i, j, -1, 1);
-            const double A0 = F.full(i, j, 0, -1) + F.full(i, j, 0, 0) + F.full(i, j, 0, 1);
-            const double AR = F.full(i, j, 1, -1) + F.full(i, j, 1, 0) + F.full(i, j, 1, 1);
-            if (!(fabs(A0) > 1e-300)) set_err(st, BMG_ERR_SETUP_BREAKDOWN);
+            double AL = F.full(i, j, -1, -1) + F.full(i, j, -1, 0) + F.full(i, j, -1, 1);
+            double A0 = F.full(i, j, 0, -1) + F.full(i, j, 0, 0) + F.full(i, j, 0, 1);
+            double AR = F.full(i, j, 1, -1) + F.full(i, j, 1, 0) + F.full(i, j, 1, 1);
+            if (!(A0 > 0.0)) {
+                AL = F.full(i, j, -1, 0);
+                AR = F.full(i, j, 1, 0);
+                A0 = F.c(i, j);
+            }
+            if (!(A0 > 0.0)) set_err(st, BMG_ERR_SETUP_BREAKDOWN);
             xl = (I >= 1) ? -AL / A0 : 0.0;
             xr = (I + 1 <= nc - 2) ? -AR / A0 : 0.0;
         }
@@ -148,10 +155,15 @@ __global__ void k_interp_edges2d(Sten2<double> F, int nf, int nc, int ldc, long 
     {   // y-edge point
         const int i = 2 * I, j = 2 * J + 1;
         if (i >= 1 && i <= nf - 2 && j <= nf - 2) {
-            const double AS = F.full(i, j, -1, -1) + F.full(i, j, 0, -1) + F.full(i, j, 1, -1);
-            const double A0 = F.full(i, j, -1, 0) + F.full(i, j, 0, 0) + F.full(i, j, 1, 0);
-            const double AN = F.full(i, j, -1, 1) + F.full(i, j, 0, 1) + F.full(i, j, 1, 1);
-            if (!(fabs(A0) > 1e-300)) set_err(st, BMG_ERR_SETUP_BREAKDOWN);
+            double AS = F.full(i, j, -1, -1) + F.full(i, j, 0, -1) + F.full(i, j, 1, -1);
+            double A0 = F.full(i, j, -1, 0) + F.full(i, j, 0, 0) + F.full(i, j, 1, 0);
+            double AN = F.full(i, j, -1, 1) + F.full(i, j, 0, 1) + F.full(i, j, 1, 1);
+            if (!(A0 > 0.0)) {
+                AS = F.full(i, j, 0, -1);
+                AN = F.full(i, j, 0, 1);
+                A0 = F.c(i, j);
+            }
+            if (!(A0 > 0.0)) set_err(st, BMG_ERR_SETUP_BREAKDOWN);
             ys = (J >= 1) ? -AS / A0 : 0.0;
             yn = (J + 1 <= nc - 2) ? -AN / A0 : 0.0;
         }

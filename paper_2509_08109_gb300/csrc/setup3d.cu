@@ -143,7 +143,8 @@ struct CoarseDims {
 };
 
 // Line points (one odd coordinate): collapse the 27-point row over the plane
-// perpendicular to the odd axis.
+// perpendicular to the odd axis.  Where the collapsed denominator is not
+// positive the point uses its own couplings along the axis (a_000 > 0).
 __global__ void k_interp_lines3d(Sten3<double> F, CoarseDims D, double* __restrict__ P, KState* st) {
     const int I = blockIdx.x * blockDim.x + threadIdx.x;
     const int J = blockIdx.y, K = blockIdx.z;
@@ -158,7 +159,13 @@ __global__ void k_interp_lines3d(Sten3<double> F, CoarseDims D, double* __restri
                 const int d = a == 0 ? off_x(o) : a == 1 ? off_y(o) : off_z(o);
                 S[d + 1] += F.full(fi, fj, fk, o);
             }
-            if (!(fabs(S[1]) > 1e-300)) set_err(st, BMG_ERR_SETUP_BREAKDOWN);
+            if (!(S[1] > 0.0)) {
+                const int step = a == 0 ? 1 : a == 1 ? 3 : 9;   // offset of +e_a in the 27-numbering
+                S[0] = F.full(fi, fj, fk, 13 - step);
+                S[1] = F.full(fi, fj, fk, 13);
+                S[2] = F.full(fi, fj, fk, 13 + step);
+            }
+            if (!(S[1] > 0.0)) set_err(st, BMG_ERR_SETUP_BREAKDOWN);
             const int ax[3] = {I, J, K};
             lo = ax[a] >= 1 ? -S[0] / S[1] : 0.0;
             hi = ax[a] + 1 <= D.nc - 2 ? -S[2] / S[1] : 0.0;
@@ -171,6 +178,8 @@ __global__ void k_interp_lines3d(Sten3<double> F, CoarseDims D, double* __restri
 
 // Plane points (two odd coordinates): collapse over the even axis, then solve
 // the collapsed plane equation with the in-plane neighbours interpolated.
+// Where the collapsed diagonal is not positive the point uses its own
+// in-plane couplings (no collapse; the diagonal a_000 > 0).
 __global__ void k_interp_planes3d(Sten3<double> F, CoarseDims D, double* __restrict__ P, KState* st) {
     const int I = blockIdx.x * blockDim.x + threadIdx.x;
     const int J = blockIdx.y, K = blockIdx.z;
@@ -191,6 +200,12 @@ __global__ void k_interp_planes3d(Sten3<double> F, CoarseDims D, double* __restr
                 if (e == 1) dy = 0;
                 if (e == 2) dz = 0;
                 cf[(dx + 1) + 3 * (dy + 1) + 9 * (dz + 1)] += F.full(fi, fj, fk, o);
+            }
+            if (!(cf[13] > 0.0)) {
+                for (int o = 0; o < 27; o++) {
+                    const int de = e == 0 ? off_x(o) : e == 1 ? off_y(o) : off_z(o);
+                    cf[o] = de == 0 ? F.full(fi, fj, fk, o) : 0.0;
+                }
             }
             const double d0 = cf[13];
             if (!(d0 > 0.0)) set_err(st, BMG_ERR_SETUP_BREAKDOWN);

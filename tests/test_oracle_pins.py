@@ -259,6 +259,29 @@ def test_interpolation_solves_fine_equation_at_all_odd_points(dim, n):
         assert abs(res) < 1e-12 * (abs(coef[0]) * np.abs(uf).max() + 1e-300)
 
 
+def test_collapse_fallback_keeps_interpolation_defined():
+    """A line point whose collapsed denominator is not positive uses its own
+    couplings along the line: with a hand-made row whose perpendicular
+    couplings outweigh its diagonal, the weights are -a(-1,0)/a00 and
+    -a(+1,0)/a00."""
+    n = 5
+    A = np.zeros((n, n, 9))
+    for j in range(1, n - 1):
+        for i in range(1, n - 1):
+            A[j, i] = [-0.1, -2.0, -0.1, -1.0, 3.0, -1.0, -0.1, -2.0, -0.1]   # collapse over dy: 3 - 4 < 0
+    A = A * oracle.interior_mask(n, 2)[..., None]
+    for j in range(1, n - 1):
+        for i in range(1, n - 1):
+            for o in range(9):
+                dx, dy = o % 3 - 1, o // 3 - 1
+                if not (1 <= i + dx <= n - 2 and 1 <= j + dy <= n - 2):
+                    A[j, i, o] = 0.0
+    P = oracle.interp(A)
+    # x-edge point (1, 2): weight to coarse (1, 1) is -a(+1,0)/a00 = 1/3
+    assert abs(P[2, 1, 1] - 1.0 / 3.0) < 1e-15
+    assert P[2, 1, 0] == 0.0          # the coarse node (0, 1) is a boundary node
+
+
 # ------------------------------------------------------------------ P6
 @pytest.mark.parametrize("dim,n", [(2, 9), (2, 17), (3, 9)])
 def test_rap_equals_dense_triple_product(dim, n):
