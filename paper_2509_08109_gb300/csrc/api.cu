@@ -74,6 +74,8 @@ size_t carve(Ctx& c, char* base) {
         c.z32[0] = (float*)take(sizeof(float) * pl0);
         c.z32[1] = (float*)take(sizeof(float) * pl0);
         c.p32 = (float*)take(sizeof(float) * pl0);
+        c.p32s[0] = c.p32;
+        c.p32s[1] = (float*)take(sizeof(float) * pl0);
         c.q32 = (float*)take(sizeof(float) * pl0);
         c.rs32 = (float*)take(sizeof(float) * pl0);
     }
@@ -153,9 +155,8 @@ bmg_status enqueue_iteration(Ctx& c, int parity) {
         float* zo = c.z32[parity ^ 1];
         BMG_TRY(vcycle_f32(c, zn));
         BMG_TRY(k_rz_beta32(c, zn, zo));
-        BMG_TRY(k_p_update32(c, zn));
-        BMG_TRY(k_spmv_pq32(c));
-        BMG_TRY(k_update_dr32(c));
+        BMG_TRY(k_pspmv32(c, zn, parity));
+        BMG_TRY(k_update_dr32(c, parity));
     } else {
         double* zn = c.z[parity];
         double* zo = c.z[parity ^ 1];

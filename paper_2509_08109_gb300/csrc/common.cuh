@@ -92,6 +92,7 @@ struct Ctx {
     double *stage_in = nullptr, *stage_out = nullptr;   // n^d doubles each, host staging
     // iterative refinement: FP32 inner CG vectors
     float *r32 = nullptr, *z32[2] = {nullptr, nullptr}, *p32 = nullptr, *q32 = nullptr;
+    float* p32s[2] = {nullptr, nullptr};   // search directions, alternating (p is formed while p_old is read)
     float* rs32 = nullptr;        // FP32 row sums of the finest operator (difference-form products)
     FusedLevel fused_ir0;         // level-0 streaming kernels reading r32 (FP32)
     double* partials = nullptr;
@@ -291,8 +292,7 @@ bmg_status k_p_update(Ctx& c, const double* z);                   // p = z + bet
 bmg_status k_row_sums32(Ctx& c);                // rs32 = row sums of A (computed in FP64)
 bmg_status k_residual_to32(Ctx& c);             // r32 = (float)(b - A x); rr; resets the inner CG state
 bmg_status k_rz_beta32(Ctx& c, const float* z, const float* zo);
-bmg_status k_p_update32(Ctx& c, const float* z);
-bmg_status k_spmv_pq32(Ctx& c);
-bmg_status k_update_dr32(Ctx& c);                // x (FP64) += alpha p; r32 -= alpha q
+bmg_status k_update_dr32(Ctx& c, int parity);    // x (FP64) += alpha p; r32 -= alpha q
+bmg_status k_pspmv32(Ctx& c, const float* z, int parity);   // p = z + beta p_old; q = A p; alpha
 
 }  // namespace bmg

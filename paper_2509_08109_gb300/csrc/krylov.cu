@@ -257,17 +257,45 @@ __global__ void k_row_sums32_t(RowGrid<DIM> g, const double* __restrict__ A, lon
     }
 }
 
-// q = A p (FP32 operator, difference form), alpha = rz / p.q
+// p = z + beta p_old, then q = A p (difference form), alpha = rz / p.q, in one
+// pass: each row forms p at its nine (27) neighbours on the fly from z and
+// p_old, so p is written to a second buffer (p_old is still being read).
 template <int DIM>
-__global__ void k_spmv_pq32_t(RowGrid<DIM> g, const float* __restrict__ A, const float* __restrict__ rs, long long pl,
-                              const float* __restrict__ p, float* __restrict__ q, double* partials, KState* st) {
+__global__ void k_pspmv32_t(RowGrid<DIM> g, const float* __restrict__ A, const float* __restrict__ rs, long long pl,
+                            const float* __restrict__ z, const float* __restrict__ pold, float* __restrict__ p,
+                            float* __restrict__ q, double* partials, KState* st) {
+    const float beta = (float)st->beta;
     Acc32 acc;
     FOR_ROWS(g) {
         const long long k = (long long)r_ * g.ld + i_;
-        float v = 0.0f;
-        if (g.row_inner(r_) && i_ >= 1 && i_ <= g.n - 2) v = apply_row_diff<DIM>(A, rs, pl, g.ld, g.n, p, k);
+        float pv = 0.0f, v = 0.0f;
+        if (g.row_inner(r_) && i_ >= 1 && i_ <= g.n - 2) {
+            auto P = [&](long long o) { return z[o] + beta * pold[o]; };
+            pv = P(k);
+            float s = rs[k] * pv;
+            if (DIM == 2) {
+                const int ld = g.ld;
+                s += A[W2 * pl + k] * (P(k - 1) - pv);
+                s += A[W2 * pl + k + 1] * (P(k + 1) - pv);
+                s += A[S2 * pl + k] * (P(k - ld) - pv);
+                s += A[S2 * pl + k + ld] * (P(k + ld) - pv);
+                s += A[SW2 * pl + k] * (P(k - ld - 1) - pv);
+                s += A[SW2 * pl + k + ld + 1] * (P(k + ld + 1) - pv);
+                s += A[NW2 * pl + k] * (P(k + ld - 1) - pv);
+                s += A[NW2 * pl + k - ld + 1] * (P(k - ld + 1) - pv);
+            } else {
+#pragma unroll
+                for (int t = 0; t < 13; t++) {
+                    const long long d = d3(t, g.ld, g.n);
+                    s += A[(long long)t * pl + k] * (P(k + d) - pv);
+                    s += A[(long long)t * pl + k - d] * (P(k - d) - pv);
+                }
+            }
+            v = s;
+        }
+        p[k] = pv;
         q[k] = v;
-        acc.add(p[k] * v);
+        acc.add(pv * v);
     }
     double t;
     if (grid_sum(acc.value(), partials, &st->counter[2], &t)) {
@@ -315,13 +343,6 @@ __global__ void k_rz_beta32_t(long long tot, const float* __restrict__ r, const 
         }
         st->rz = t1;
     }
-}
-
-__global__ void k_p_update32_t(long long tot, const float* __restrict__ z, float* __restrict__ p, const KState* st) {
-    const float beta = (float)st->beta;
-    for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < tot;
-         k += (long long)gridDim.x * blockDim.x)
-        p[k] = z[k] + beta * p[k];
 }
 
 inline double dofs0(const Ctx& c) {
@@ -435,27 +456,20 @@ bmg_status k_rz_beta32(Ctx& c, const float* z, const float* zo) {
     return BMG_OK;
 }
 
-bmg_status k_p_update32(Ctx& c, const float* z) {
-    const Level& L = c.lev[0];
-    k_p_update32_t<<<c.red_blocks, kThreads, 0, c.stream>>>(L.plane, z, c.p32, c.st);
-    c.launches++;
-    BMG_CUDA(cudaGetLastError());
-    return BMG_OK;
-}
-
-bmg_status k_spmv_pq32(Ctx& c) {
+bmg_status k_pspmv32(Ctx& c, const float* z, int parity) {
     const Level& L = c.lev[0];
     prof_begin(c, BMG_PROF_SPMV, 0);
-    DISPATCH_DIM(c, k_spmv_pq32_t, L.A32, c.rs32, L.plane, c.p32, c.q32, c.partials, c.st);
-    prof_end(c, BMG_PROF_SPMV, 0, (c.ns + 2) * 4.0 * dofs0(c));
+    DISPATCH_DIM(c, k_pspmv32_t, L.A32, c.rs32, L.plane, z, c.p32s[parity ^ 1], c.p32s[parity], c.q32, c.partials,
+                 c.st);
+    prof_end(c, BMG_PROF_SPMV, 0, (c.ns + 4) * 4.0 * dofs0(c));
     BMG_CUDA(cudaGetLastError());
     return BMG_OK;
 }
 
-bmg_status k_update_dr32(Ctx& c) {
+bmg_status k_update_dr32(Ctx& c, int parity) {
     const Level& L = c.lev[0];
     prof_begin(c, BMG_PROF_UPDATE, 0);
-    k_update_xr32<<<c.red_blocks, kThreads, 0, c.stream>>>(L.plane, c.x, c.r32, c.p32, c.q32, c.st);
+    k_update_xr32<<<c.red_blocks, kThreads, 0, c.stream>>>(L.plane, c.x, c.r32, c.p32s[parity], c.q32, c.st);
     prof_end(c, BMG_PROF_UPDATE, 0, (4 * 4.0 + 2 * 8.0) * dofs0(c));
     c.launches++;
     BMG_CUDA(cudaGetLastError());
