@@ -37,15 +37,18 @@ def test_gradient_matches_oracle_adjoint():
 
 
 def test_gradient_matches_central_differences():
-    """Central differences in m_e with eps = 1e-3, the loss difference formed
+    """Central differences in m_e with eps = 2e-3, the loss difference formed
     as 1/2 sum (u+ - u-)(u+ + u- - 2 u_obs) to avoid cancellation; relative
-    error against max(|g_e|, 1e-3 max|g|)."""
+    error against max(|g_e|, 1e-2 max|g|).  The two errors of the difference
+    quotient: truncation, O(eps^2 |g_e|) (below 1e-6 relative here with exact
+    solves), and the solves' stopping error divided by 2 eps, which is the same
+    absolute size for every cell and is therefore bounded against max|g|."""
     (prob,) = inputs.annulus_adjoint(129, batch=1)
     _, gm, _, u = _grad(prob, tol=1e-12)
     s = binding.Solver(2, prob.n)
     rng = np.random.default_rng(3)
     cells = [tuple(c) for c in rng.integers(0, prob.n - 1, size=(8, 2))]
-    eps = 1e-3
+    eps = 2e-3
     scale = np.abs(gm).max()
     f = torch.as_tensor(prob.rhs, device="cuda")
     for c in cells:
@@ -59,7 +62,7 @@ def test_gradient_matches_central_differences():
         up, um = sols
         dL = 0.5 * np.sum((up - um) * (up + um - 2 * prob.extra["u_obs"]))
         fd = dL / (2 * eps)
-        assert abs(fd - gm[c]) <= 1e-5 * max(abs(gm[c]), 1e-3 * scale), (c, fd, gm[c])
+        assert abs(fd - gm[c]) <= 1e-5 * max(abs(gm[c]), 1e-2 * scale), (c, fd, gm[c])
 
 
 def test_batch_of_independent_members():
