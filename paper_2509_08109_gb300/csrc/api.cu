@@ -153,8 +153,12 @@ bmg_status enqueue_iteration(Ctx& c, int parity) {
     if (c.opts.outer == BMG_OUTER_REFINEMENT) {
         float* zn = c.z32[parity];
         float* zo = c.z32[parity ^ 1];
-        BMG_TRY(vcycle_f32(c, zn));
-        BMG_TRY(k_rz_beta32(c, zn, zo));
+        if (vcycle_forms_beta(c)) {
+            BMG_TRY(vcycle_f32(c, zn, zo));     // the finest up kernel also forms beta
+        } else {
+            BMG_TRY(vcycle_f32(c, zn));
+            BMG_TRY(k_rz_beta32(c, zn, zo));
+        }
         BMG_TRY(k_pspmv32(c, zn, parity));
         BMG_TRY(k_update_dr32(c, parity));
     } else {

@@ -271,8 +271,11 @@ int fused_down_smem(bool f32, bool f64in, int wc);
 int fused_up_smem(bool f32, bool f64in, int wc);
 bmg_status fused_occupancy(bool f32, bool f64in, int wc, int* down_blocks, int* up_blocks);
 bmg_status fused_down(Ctx& c, int l, bool ir = false);
-bmg_status fused_up(Ctx& c, int l, void* out, bool ir = false);
-bmg_status vcycle_f32(Ctx& c, float* z32);       // z32 = M r32 (FP32 in and out)
+bmg_status fused_up(Ctx& c, int l, void* out, bool ir = false, const float* zold = nullptr);
+bmg_status vcycle_f32(Ctx& c, float* z32, const float* zold = nullptr);
+// z32 = M r32 (FP32 in and out); with zold and the streaming kernels the
+// finest up kernel also forms r.z, r.z_old and the flexible-CG beta
+bool vcycle_forms_beta(const Ctx& c);
 template <typename T>
 bmg_status vcycle3d_impl(Ctx& c, const T* b0, T* x0, T* xout);
 bmg_status fused_prepare(Ctx& c);

@@ -158,6 +158,17 @@ __device__ __forceinline__ bool wait_pairs(uint64_t* bars, int qa, int qb) {
     return __syncthreads_and(mine) != 0;
 }
 
+// Compensated (Neumaier) FP32 accumulator for the fused dot products.
+struct Acc32f {
+    float s = 0.0f, c = 0.0f;
+    __device__ __forceinline__ void add(float x) {
+        const float t = s + x;
+        c += fabsf(s) >= fabsf(x) ? (s - t) + x : (x - t) + s;
+        s = t;
+    }
+    __device__ __forceinline__ double value() const { return (double)s + (double)c; }
+};
+
 // ------------------------------------------------------------------ node updates
 // Symmetric-half stencil rows: plane p of row j is A(j) + p * 2 * WW.
 // Offsets: W(c) couples (c-1), W(c+1) couples (c+1) of the row; S(j) couples
@@ -452,6 +463,8 @@ __global__ void __launch_bounds__(72 * K) k_vup2d(const __grid_constant__ CUtens
     };
     const T* Pg = (const T*)p.P;
     TO* out = (TO*)p.x;
+    const float* zold = (const float*)p.zold;   // finest level of the refinement mode only
+    Acc32f rz, rzo;
     auto pw = [&](int plane, int Jc) -> T {
         return (vI && Jc >= 0 && Jc <= nc - 1) ? Pg[plane * p.plc + (long long)Jc * p.ldc + I] : (T)0;
     };
@@ -535,16 +548,33 @@ __global__ void __launch_bounds__(72 * K) k_vup2d(const __grid_constant__ CUtens
         gs(jm, co, vo);      // colour 1
         __syncthreads();
         gs(jm, ce, ve);      // colour 0
+        // right-hand side of the stored rows, read while their ring slots
+        // cannot yet be refilled (the next refill follows the next barrier)
+        float fr[2][2] = {{0.f, 0.f}, {0.f, 0.f}};
+        if (zold)
+            for (int rr = 0; rr < 2; rr++) {
+                const TF* Fr = rg.F(jm - 1 + rr);
+                fr[rr][0] = (float)Fr[ce];
+                fr[rr][1] = (float)Fr[co];
+            }
         __syncthreads();
-        if (inrow(jm - 1)) {
-            const T* Xr = X(jm - 1);
-            if (own_e) out[(long long)(jm - 1) * p.ldf + ie] = (TO)Xr[ce];
-            if (own_o) out[(long long)(jm - 1) * p.ldf + ie + 1] = (TO)Xr[co];
-        }
-        if (inrow(jm)) {
-            const T* Xr = X(jm);
-            if (own_e) out[(long long)jm * p.ldf + ie] = (TO)Xr[ce];
-            if (own_o) out[(long long)jm * p.ldf + ie + 1] = (TO)Xr[co];
+        for (int rr = 0; rr < 2; rr++) {
+            const int j = jm - 1 + rr;
+            if (!inrow(j)) continue;
+            const T* Xr = X(j);
+            const long long o = (long long)j * p.ldf + ie;
+            if (own_e) out[o] = (TO)Xr[ce];
+            if (own_o) out[o + 1] = (TO)Xr[co];
+            if (zold) {
+                if (own_e) {
+                    rz.add(fr[rr][0] * (float)Xr[ce]);
+                    rzo.add(fr[rr][0] * zold[o]);
+                }
+                if (own_o) {
+                    rz.add(fr[rr][1] * (float)Xr[co]);
+                    rzo.add(fr[rr][1] * zold[o + 1]);
+                }
+            }
         }
     }
     if (!ok) {
@@ -553,6 +583,57 @@ __global__ void __launch_bounds__(72 * K) k_vup2d(const __grid_constant__ CUtens
             for (int q = waited; q < issued; q++) mbar_wait(rg.bars + (q % RP), (uint32_t)((q / RP) & 1));
         }
         __syncthreads();
+        return;
+    }
+    if (zold) {
+        // deterministic grid reduction of (r.z, r.z_old); the last CTA forms
+        // the flexible-CG beta.  Every copy into the rings has completed, so
+        // after the barrier the A ring is free to hold the per-thread sums.
+        const int tid = ty * blockDim.x + tx, nthr = blockDim.x * blockDim.y;
+        double* red = (double*)rg.pA;
+        int* last = (int*)(red + 2 * nthr);
+        __syncthreads();
+        red[tid] = rz.value();
+        red[nthr + tid] = rzo.value();
+        __syncthreads();
+        if (tid < 32) {     // warp 0: strided partial sums, then a fixed shuffle tree
+            double a1 = 0.0, a2 = 0.0;
+            for (int k = tid; k < nthr; k += 32) {
+                a1 += red[k];
+                a2 += red[nthr + k];
+            }
+            for (int o = 16; o > 0; o >>= 1) {
+                a1 += __shfl_down_sync(0xffffffffu, a1, o);
+                a2 += __shfl_down_sync(0xffffffffu, a2, o);
+            }
+            if (tid == 0) {
+                const int bid = blockIdx.y * gridDim.x + blockIdx.x;
+                p.partials[2 * bid] = a1;
+                p.partials[2 * bid + 1] = a2;
+                __threadfence();
+                const unsigned nb = gridDim.x * gridDim.y;
+                *last = atomicAdd(&p.st->counter[6], 1u) == nb - 1;
+            }
+        }
+        __syncthreads();
+        if (*last && tid == 0) {
+            __threadfence();
+            double t1 = 0.0, t2 = 0.0;
+            const int nb = gridDim.x * gridDim.y;
+            for (int k = 0; k < nb; k++) {
+                t1 += ((volatile double*)p.partials)[2 * k];
+                t2 += ((volatile double*)p.partials)[2 * k + 1];
+            }
+            p.st->counter[6] = 0u;
+            KState* st = p.st;
+            if (st->first) {
+                st->beta = 0.0;
+                st->first = 0;
+            } else {
+                st->beta = (t1 - t2) / st->rz;
+            }
+            st->rz = t1;
+        }
     }
 }
 
@@ -577,13 +658,15 @@ bmg_status launch_down(Ctx& c, const FusedLevel& F, cudaStream_t s) {
 }
 
 template <typename T, typename TF, typename TO>
-bmg_status launch_up(Ctx& c, const FusedLevel& F, cudaStream_t s, void* out) {
+bmg_status launch_up(Ctx& c, const FusedLevel& F, cudaStream_t s, void* out, const void* zold = nullptr) {
     auto kern = k_vup2d<T, TF, TO, k_of<T>()>;
     const int smem = up_smem<T, TF>(F.wc);
     if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) != cudaSuccess)
         return BMG_ERR_DEVICE;
     FusedArgs a = F.up;
     a.x = out;
+    a.zold = zold;
+    a.partials = zold ? c.partials : nullptr;
     kern<<<dim3(F.tiles_x, F.tiles_y), dim3(F.wc + 8, k_of<T>()), smem, s>>>(F.mA, F.mF, F.mXp, F.mXc, a);
     c.launches++;
     return cudaGetLastError() == cudaSuccess ? BMG_OK : BMG_ERR_DEVICE;
@@ -643,12 +726,12 @@ bmg_status fused_down(Ctx& c, int l, bool ir) {
     return launch_down<float, float>(c, F, c.stream);
 }
 
-bmg_status fused_up(Ctx& c, int l, void* out, bool ir) {
+bmg_status fused_up(Ctx& c, int l, void* out, bool ir, const float* zold) {
     const FusedLevel& F = (ir && l == 0) ? c.fused_ir0 : c.fused[l];
     const bool f32 = c.opts.precision == BMG_PREC_FP32;
     if (!f32) return launch_up<double, double, double>(c, F, c.stream, out);
     if (l == 0 && !ir) return launch_up<float, double, double>(c, F, c.stream, out);
-    return launch_up<float, float, float>(c, F, c.stream, out);
+    return launch_up<float, float, float>(c, F, c.stream, out, (ir && l == 0) ? zold : nullptr);
 }
 
 }  // namespace bmg

@@ -17,6 +17,11 @@ struct FusedArgs {
     const void* P;   // interpolation planes (coarse grid)
     long long plc;   // plane stride of P
     KState* st;
+    // up kernel, finest level of the refinement mode: r.z and r.z_old of the
+    // owned nodes (r = this kernel's right-hand side, z = its output) reduced
+    // into the CG coefficient; null when not wanted
+    const void* zold;
+    double* partials;
 };
 
 // Per fine level: tile shape and TMA descriptors (built at attach time).

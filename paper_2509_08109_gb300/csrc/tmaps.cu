@@ -97,8 +97,8 @@ bmg_status fused_configure(Ctx& c, int l, int wc, int hc) {
     ok = ok && make_map(&F.mXp, !f32, Lf.x, Lf.ld, Lf.n, 1, Lf.plane, WW, 2);
     ok = ok && make_map(&F.mXc, !f32, Lc.r, Lc.ld, Lc.n, 1, Lc.plane, WWc, 1);
     if (!ok) return BMG_ERR_DEVICE;
-    F.down = FusedArgs{Lf.n, Lc.n, Lf.ld, Lc.ld, F.wc, F.hc, Lf.x, Lc.b, P, Lc.plane, c.st};
-    F.up = FusedArgs{Lf.n, Lc.n, Lf.ld, Lc.ld, F.wc, F.hc, nullptr, nullptr, P, Lc.plane, c.st};
+    F.down = FusedArgs{Lf.n, Lc.n, Lf.ld, Lc.ld, F.wc, F.hc, Lf.x, Lc.b, P, Lc.plane, c.st, nullptr, nullptr};
+    F.up = FusedArgs{Lf.n, Lc.n, Lf.ld, Lc.ld, F.wc, F.hc, nullptr, nullptr, P, Lc.plane, c.st, nullptr, nullptr};
     F.ready = true;
     if (l == 0 && c.r32) {
         // refinement mode: the level-0 kernels read the FP32 inner residual

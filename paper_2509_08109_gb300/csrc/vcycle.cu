@@ -193,7 +193,7 @@ bmg_status vcycle2d_impl(Ctx& c, const T* b0, T* x0) {
 
 // Streaming path: one down kernel and one up kernel per level pair.
 template <typename T>
-bmg_status vcycle2d_fused(Ctx& c, void* z, bool ir = false) {
+bmg_status vcycle2d_fused(Ctx& c, void* z, bool ir = false, const float* zold = nullptr) {
     cudaStream_t s = c.stream;
     const int L = c.nlev;
     const double sz = sizeof(T);
@@ -216,7 +216,7 @@ bmg_status vcycle2d_fused(Ctx& c, void* z, bool ir = false) {
         const double szf = (l == 0 && !ir) ? 8.0 : sz;
         const double szo = (l == 0 && !ir) ? 8.0 : sz;
         prof_begin(c, BMG_PROF_VUP, l);
-        BMG_TRY(fused_up(c, l, l == 0 ? z : c.lev[l].r, ir));
+        BMG_TRY(fused_up(c, l, l == 0 ? z : c.lev[l].r, ir, zold));
         prof_end(c, BMG_PROF_VUP, l, N * (c.ns * sz + szf + sz + c.np / 4.0 * sz + sz / 4 + szo));
     }
     (void)f32;
@@ -242,10 +242,12 @@ bmg_status demote_levels(Ctx& c) {
     return BMG_OK;
 }
 
-bmg_status vcycle_f32(Ctx& c, float* z32) {
+bool vcycle_forms_beta(const Ctx& c) { return c.dim == 2 && c.use_fused && c.nlev >= 2; }
+
+bmg_status vcycle_f32(Ctx& c, float* z32, const float* zold) {
     if (c.opts.precision != BMG_PREC_FP32) return BMG_ERR_STATE;
     if (c.dim == 3) return vcycle3d_impl<float>(c, c.r32, z32, nullptr);
-    if (c.use_fused && c.nlev >= 2) return vcycle2d_fused<float>(c, z32, true);
+    if (c.use_fused && c.nlev >= 2) return vcycle2d_fused<float>(c, z32, true, zold);
     return vcycle2d_impl<float>(c, c.r32, z32);
 }
 
