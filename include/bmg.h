@@ -128,8 +128,8 @@ bmg_status bmg_attach(bmg_ctx* ctx, void* workspace, size_t bytes, void* stream)
    z plane]); kappa: device, (n-1)^d doubles.  Errors: BMG_ERR_MAP_FOLDED. */
 bmg_status bmg_assemble(bmg_ctx* ctx, const double* coords, const double* kappa);
 
-/* Sets the finest operator directly ("either A_c must be provided, or the
-   diffusion coefficient", Sec. 2.2).  stencil: device, n^d rows of 3^d
+/* Sets the finest operator directly, the alternative Sec. 2.2 allows to
+   assembling it from the coefficient.  stencil: device, n^d rows of 3^d
    doubles, entry (dx+1)+3(dy+1)[+9(dz+1)] = A[node, node+offset]; the
    operator must be symmetric with zero couplings to boundary nodes (only
    the lower half of each row is read). */

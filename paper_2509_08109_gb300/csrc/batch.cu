@@ -1,4 +1,4 @@
-// batch.cu -- many independent solves at once (BASELINE batching form): a
+// batch.cu -- many independent solves at once (a batch of mapped problems): a
 // host-side scheduler drives every context's refinement loop as a small
 // state machine.  Each context works on its own stream; each refinement step
 // is enqueued without blocking (iteration graphs, then the FP64 residual and

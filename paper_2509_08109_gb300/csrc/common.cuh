@@ -7,8 +7,8 @@
 // i fastest.  Padding and boundary entries are kept at zero in every array.
 //
 // Operators are stored as the symmetric half of the 9-point (2-D) or
-// 27-point (3-D) stencil, one plane per stored offset ("five stored values
-// per DoF", Sec. 4.1):
+// 27-point (3-D) stencil, one plane per stored offset (the symmetric
+// storage of Sec. 4.1: five values per node in 2-D):
 //   2-D: C (0,0), W (-1,0), S (0,-1), SW (-1,-1), NW (-1,+1);
 //        a(+d) at node i is a(-d) stored at node i+d.
 //   3-D: C and the 13 offsets that are lexicographically negative

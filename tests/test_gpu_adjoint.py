@@ -1,4 +1,4 @@
-"""Differentiation (BASELINE form 3): torch.autograd through the library's
+"""Differentiation: torch.autograd through the library's
 forward and adjoint solves, against the oracle's adjoint gradient and
 central finite differences of the loss L = 1/2 |u - u_obs|^2."""
 import numpy as np

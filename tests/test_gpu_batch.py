@@ -1,4 +1,4 @@
-"""Batching (BASELINE batching form): many independent mapped problems of
+"""Batching: many independent mapped problems of
 uneven sizes and several right-hand sides, solved concurrently through
 bmg_solve_many; every solution is checked against the oracle or against
 the single-problem path."""
