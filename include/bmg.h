@@ -240,6 +240,34 @@ long long bmg_launch_count(const bmg_ctx* ctx);
 void bmg_destroy(bmg_ctx* ctx);
 const char* bmg_status_str(bmg_status status);
 
+/* Allocation-free assembly.  The paper has no counterpart: this entry point
+   serves callers that may not allocate (another allocator owns the device
+   memory, a hard memory cap, or a path where an allocation is not allowed).
+   It computes the same operator as bmg_assemble followed by
+   bmg_get_stencil(level 0) but needs no context and no workspace, and it makes
+   no allocating call: its working storage (a device error word and the
+   half-plane operator) is a static device array of BMG_NOALLOC_SCRATCH_BYTES
+   per device.
+   dim: 2 or 3.  n: nodes per side, any n >= 3, as long as
+   256 + P * ld * n^(dim-1) * 8 bytes fit that array, with P = 5 (2-D) or 14
+   (3-D) and ld = n rounded up to a multiple of 32; that is n <= 640 in 2-D
+   and n <= 48 in 3-D.  A larger n returns BMG_ERR_SHAPE before any device
+   work.  coords, kappa: as for bmg_assemble.  stencil: device, n^dim rows of
+   3^dim doubles, written as bmg_get_stencil writes them.  All three on the
+   calling thread's current device.  stream: a cudaStream_t, or NULL for the
+   legacy default stream; the call returns when its work on the stream is
+   done.
+   Set-up: the first call on a device looks up the static array's device
+   address (cudaGetSymbolAddress) with that device current; make that first
+   call before any stream capture begins on the device.  Concurrency: calls
+   that overlap in time on one device (other threads or streams) share the
+   array and race; serialise them.
+   Errors: BMG_ERR_SHAPE, BMG_ERR_ARG (null or non-device pointer),
+   BMG_ERR_MAP_FOLDED, BMG_ERR_DEVICE. */
+#define BMG_NOALLOC_SCRATCH_BYTES (16u << 20)
+bmg_status bmg_assemble_noalloc(int dim, int n, const double* coords, const double* kappa, double* stencil,
+                                void* stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -91,6 +91,7 @@ def load() -> ctypes.CDLL:
         "bmg_profile_read": ([P, I, ctypes.POINTER(D), ctypes.POINTER(ctypes.c_longlong), ctypes.POINTER(D)], I),
         "bmg_destroy": ([P], None),
         "bmg_status_str": ([I], ctypes.c_char_p),
+        "bmg_assemble_noalloc": ([I, I, P, P, P, P], I),
     }
     for name, (args, res) in sigs.items():
         f = getattr(lib, name)
@@ -106,7 +107,7 @@ def exported_symbols() -> list:
             "bmg_levels",
             "bmg_level_n", "bmg_get_stencil", "bmg_get_interp", "bmg_launch_count", "bmg_get_tiles",
             "bmg_set_tiles", "bmg_autotune", "bmg_profile",
-            "bmg_profile_read", "bmg_destroy", "bmg_status_str"]
+            "bmg_profile_read", "bmg_destroy", "bmg_status_str", "bmg_assemble_noalloc"]
 
 
 def _check(code: int, where: str):
@@ -117,6 +118,24 @@ def _check(code: int, where: str):
 def _ptr(t: torch.Tensor):
     assert t.is_contiguous() and t.dtype == torch.float64, (t.dtype, t.is_contiguous())
     return ctypes.c_void_p(t.data_ptr())
+
+
+def assemble_noalloc(dim: int, n: int, coords: torch.Tensor, kappa: torch.Tensor, out: torch.Tensor,
+                     stream=None) -> torch.Tensor:
+    """bmg_assemble_noalloc: the finest operator as full 3^dim-entry rows,
+    written into `out` (device, n^dim x 3^dim doubles), without a context or
+    any allocation in the library.  All tensors must already be on the
+    current CUDA device; nothing is copied or allocated here either."""
+    for t in (coords, kappa, out):
+        assert t.is_cuda and t.dtype == torch.float64 and t.is_contiguous()
+    s = stream if stream is not None else torch.cuda.current_stream()
+    code = load().bmg_assemble_noalloc(int(dim), int(n), _ptr(coords), _ptr(kappa), _ptr(out),
+                                       ctypes.c_void_p(s.cuda_stream))
+    if code == 2:
+        raise BmgError(code, f"bmg_assemble_noalloc: dim {dim}, n {n} is beyond the static scratch "
+                             f"(n <= 640 in 2-D, n <= 48 in 3-D)")
+    _check(code, "bmg_assemble_noalloc")
+    return out
 
 
 def _info_of(i: "_Info") -> SolveInfo:

@@ -263,6 +263,11 @@ bmg_status setup_level3d(Ctx& c, int l);
 bmg_status export_stencil3d(Ctx& c, int l, double* out);
 bmg_status export_interp3d(Ctx& c, int l, double* out);
 bmg_status adjoint_cells3d(Ctx& c, const double* coords, const double* u, const double* lam, double* g);
+// setup2d.cu / setup3d.cu, context-free: assembly into given half planes, then export
+bmg_status assemble_export2d(int n, int ld, long long pl, const double* coords, const double* kappa, double* A,
+                             KState* st, double* out, cudaStream_t s);
+bmg_status assemble_export3d(int n, int ld, long long pl, const double* coords, const double* kappa, double* A,
+                             KState* st, double* out, cudaStream_t s);
 // vcycle.cu: z = M r on the finest level (FP64 in/out, internal layout)
 bmg_status vcycle(Ctx& c, const double* r, double* z);
 // fused2d.cu / tmaps.cu

@@ -324,6 +324,17 @@ bmg_status assemble2d(Ctx& c, const double* coords, const double* kappa) {
     return BMG_OK;
 }
 
+// The two kernels of bmg_assemble and bmg_get_stencil(0) on caller-given
+// storage: half planes A (row length ld, plane stride pl) and error word st.
+bmg_status assemble_export2d(int n, int ld, long long pl, const double* coords, const double* kappa, double* A,
+                             KState* st, double* out, cudaStream_t s) {
+    k_assemble2d<<<grid_rows(n, n), 128, 0, s>>>(n, ld, pl, coords, kappa, A, st);
+    BMG_CUDA(cudaGetLastError());
+    k_export_stencil2d<<<grid_rows(n, n), 128, 0, s>>>(Sten2<double>{A, ld, pl}, n, out);
+    BMG_CUDA(cudaGetLastError());
+    return BMG_OK;
+}
+
 bmg_status set_stencil2d(Ctx& c, const double* full) {
     Level& L = c.lev[0];
     k_set_stencil2d<<<grid_rows(L.n, L.n), 128, 0, c.stream>>>(L.n, L.ld, L.plane, full, L.A64);

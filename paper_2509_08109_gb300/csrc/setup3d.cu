@@ -354,6 +354,16 @@ bmg_status assemble3d(Ctx& c, const double* coords, const double* kappa) {
     return BMG_OK;
 }
 
+// As assemble_export2d: assembly into caller-given half planes, then export.
+bmg_status assemble_export3d(int n, int ld, long long pl, const double* coords, const double* kappa, double* A,
+                             KState* st, double* out, cudaStream_t s) {
+    k_assemble3d<<<grid3(n, n, n), 64, 0, s>>>(n, ld, pl, coords, kappa, A, st);
+    BMG_CUDA(cudaGetLastError());
+    k_export_stencil3d<<<grid3(n, n, n), 64, 0, s>>>(Sten3<double>{A, n, ld, pl}, out);
+    BMG_CUDA(cudaGetLastError());
+    return BMG_OK;
+}
+
 bmg_status set_stencil3d(Ctx& c, const double* full) {
     Level& L = c.lev[0];
     k_set_stencil3d<<<grid3(L.n, L.n, L.n), 64, 0, c.stream>>>(L.n, L.ld, L.plane, full, L.A64);

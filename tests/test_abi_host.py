@@ -82,3 +82,10 @@ def test_calls_before_attach_are_rejected(lib):
     assert lib.bmg_create(None, ctypes.byref(h)) == 1
     assert lib.bmg_status_str(6).decode().startswith("setup breakdown")
     lib.bmg_destroy(h)
+
+
+@pytest.mark.parametrize("dim,n,code", [(2, 641, 2), (3, 49, 2), (4, 9, 2), (2, 2, 2), (2, 640, 1), (3, 48, 1)])
+def test_noalloc_validates_before_device_work(lib, dim, n, code):
+    """Shape and null-pointer checks of bmg_assemble_noalloc come before any
+    CUDA call, so they answer without a device."""
+    assert lib.bmg_assemble_noalloc(dim, n, None, None, None, None) == code
