@@ -362,10 +362,10 @@ def run_reference(args):
 
 
 # ---------------------------------------------------------------- other workloads
-def _timed_solves(torch, s, f, steps, warmup, tol=TOL):
+def _timed_solves(torch, s, f, steps, warmup, tol=TOL, maxit=500):
     x = torch.zeros_like(f)
     for _ in range(warmup):
-        s.solve(f, tol=tol, out=x)
+        s.solve(f, tol=tol, out=x, maxit=maxit)
     torch.cuda.synchronize()
     l0 = s.launches
     a = torch.cuda.Event(enable_timing=True)
@@ -373,7 +373,7 @@ def _timed_solves(torch, s, f, steps, warmup, tol=TOL):
     infos = []
     a.record()
     for _ in range(steps):
-        _, info = s.solve(f, tol=tol, out=x)
+        _, info = s.solve(f, tol=tol, out=x, maxit=maxit)
         infos.append(info)
     b.record()
     torch.cuda.synchronize()
@@ -396,7 +396,9 @@ def run_single(args, dim, n, problem, name):
         s.assemble(torch.as_tensor(problem.coords), torch.as_tensor(problem.kappa)).setup()
         torch.cuda.synchronize()
         setup_s = time.perf_counter() - t0
-        ms, launches, infos = _timed_solves(torch, s, f, args.steps, args.warmup)
+        # point Gauss-Seidel on the shell octant loses h-independence (cells
+        # degenerate at the polar edge): PCG iterations double per refinement
+        ms, launches, infos = _timed_solves(torch, s, f, args.steps, args.warmup, maxit=500 if dim == 2 else 4000)
         assert all(i.true_relres <= TOL for i in infos)
         res[f"{prec}_{outer}"] = {"value": (n - 2) ** dim / (ms * 1e-3), "ms_per_step": ms,
                                   "iterations": infos[-1].iterations, "true_relres": infos[-1].true_relres,

@@ -455,6 +455,7 @@ bmg_status bmg_setup(bmg_ctx* ctx) {
     for (int l = 0; l < c.nlev - 1; l++) BMG_TRY(c.dim == 2 ? setup_level2d(c, l) : setup_level3d(c, l));
     BMG_TRY(demote_levels(c));
     if (c.rs32) BMG_TRY(k_row_sums32(c));
+    BMG_TRY(pspmv_prepare(c));
     KState h;
     BMG_TRY(read_state(c, h));
     if (h.err) {

@@ -100,6 +100,7 @@ struct Ctx {
     KState* st_host = nullptr;    // pinned mirror
     long long launches = 0;
     int red_blocks = 0;           // fixed grid of the reducing kernels (deterministic)
+    int spmv_h = 0, spmv_tiles_x = 0, spmv_tiles = 0;   // tiles of the 2-D refinement-mode operator product
     bool prof_on = false;
     ProfSlot prof[BMG_PROF_KINDS];
     bool use_fused = false;       // streaming V-cycle kernels (2-D)
@@ -301,6 +302,7 @@ bmg_status k_row_sums32(Ctx& c);                // rs32 = row sums of A (compute
 bmg_status k_residual_to32(Ctx& c);             // r32 = (float)(b - A x); rr; resets the inner CG state
 bmg_status k_rz_beta32(Ctx& c, const float* z, const float* zo);
 bmg_status k_update_dr32(Ctx& c, int parity);    // x (FP64) += alpha p; r32 -= alpha q
+bmg_status pspmv_prepare(Ctx& c);                // tile shape of the 2-D operator product
 bmg_status k_pspmv32(Ctx& c, const float* z, int parity);   // p = z + beta p_old; q = A p; alpha
 
 }  // namespace bmg

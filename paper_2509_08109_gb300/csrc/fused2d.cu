@@ -525,6 +525,19 @@ __global__ void __launch_bounds__(72 * K) k_vup2d(const __grid_constant__ CUtens
         wxr = pw(PXR, Jp + 1);
     };
     load_w(J0 + ty);
+    // previous preconditioned residual at this thread's stored nodes of the
+    // rows 2Jp-1, 2Jp, also loaded one step ahead (refinement mode only)
+    float zo_nx[2][2] = {{0.f, 0.f}, {0.f, 0.f}};
+    auto load_zo = [&](int Jp) {
+        for (int rr = 0; rr < 2; rr++) {
+            const int j = 2 * Jp - 1 + rr;
+            const long long o = (long long)j * p.ldf + ie;
+            const bool rj = inrow(j);
+            zo_nx[rr][0] = (rj && own_e) ? zold[o] : 0.f;
+            zo_nx[rr][1] = (rj && own_o) ? zold[o + 1] : 0.f;
+        }
+    };
+    if (zold) load_zo(J0 + ty);
     for (int J = J0; ok && J < J0 + p.hc; J += K) {
         const int qa = J - rg.q0;
         const int Jp = J + ty, jm = 2 * Jp, jo = jm + 1, je = jm + 2;
@@ -540,6 +553,8 @@ __global__ void __launch_bounds__(72 * K) k_vup2d(const __grid_constant__ CUtens
         corr_odd(jo, wy);
         corr_even(je, wxl, wxr);
         load_w(Jp + K);
+        float zo_now[2][2] = {{zo_nx[0][0], zo_nx[0][1]}, {zo_nx[1][0], zo_nx[1][1]}};
+        if (zold) load_zo(Jp + K);
         __syncthreads();
         gs(jo, co, vo);      // colour 3
         __syncthreads();
@@ -568,11 +583,11 @@ __global__ void __launch_bounds__(72 * K) k_vup2d(const __grid_constant__ CUtens
             if (zold) {
                 if (own_e) {
                     rz.add(fr[rr][0] * (float)Xr[ce]);
-                    rzo.add(fr[rr][0] * zold[o]);
+                    rzo.add(fr[rr][0] * zo_now[rr][0]);
                 }
                 if (own_o) {
                     rz.add(fr[rr][1] * (float)Xr[co]);
-                    rzo.add(fr[rr][1] * zold[o + 1]);
+                    rzo.add(fr[rr][1] * zo_now[rr][1]);
                 }
             }
         }
@@ -592,47 +607,57 @@ __global__ void __launch_bounds__(72 * K) k_vup2d(const __grid_constant__ CUtens
         const int tid = ty * blockDim.x + tx, nthr = blockDim.x * blockDim.y;
         double* red = (double*)rg.pA;
         int* last = (int*)(red + 2 * nthr);
-        __syncthreads();
-        red[tid] = rz.value();
-        red[nthr + tid] = rzo.value();
-        __syncthreads();
-        if (tid < 32) {     // warp 0: strided partial sums, then a fixed shuffle tree
-            double a1 = 0.0, a2 = 0.0;
-            for (int k = tid; k < nthr; k += 32) {
-                a1 += red[k];
-                a2 += red[nthr + k];
+        // sum of v1 / v2 over the CTA's threads, in a fixed order; valid in thread 0
+        auto block_sum2 = [&](double v1, double v2, double& s1, double& s2) {
+            __syncthreads();
+            red[tid] = v1;
+            red[nthr + tid] = v2;
+            __syncthreads();
+            if (tid < 32) {     // warp 0: strided partial sums, then a fixed shuffle tree
+                double a1 = 0.0, a2 = 0.0;
+                for (int k = tid; k < nthr; k += 32) {
+                    a1 += red[k];
+                    a2 += red[nthr + k];
+                }
+                for (int o = 16; o > 0; o >>= 1) {
+                    a1 += __shfl_down_sync(0xffffffffu, a1, o);
+                    a2 += __shfl_down_sync(0xffffffffu, a2, o);
+                }
+                s1 = a1;
+                s2 = a2;
             }
-            for (int o = 16; o > 0; o >>= 1) {
-                a1 += __shfl_down_sync(0xffffffffu, a1, o);
-                a2 += __shfl_down_sync(0xffffffffu, a2, o);
-            }
-            if (tid == 0) {
-                const int bid = blockIdx.y * gridDim.x + blockIdx.x;
-                p.partials[2 * bid] = a1;
-                p.partials[2 * bid + 1] = a2;
-                __threadfence();
-                const unsigned nb = gridDim.x * gridDim.y;
-                *last = atomicAdd(&p.st->counter[6], 1u) == nb - 1;
-            }
+        };
+        double b1 = 0.0, b2 = 0.0;
+        block_sum2(rz.value(), rzo.value(), b1, b2);
+        const int nb = gridDim.x * gridDim.y;
+        if (tid == 0) {
+            const int bid = blockIdx.y * gridDim.x + blockIdx.x;
+            p.partials[2 * bid] = b1;
+            p.partials[2 * bid + 1] = b2;
+            __threadfence();
+            *last = atomicAdd(&p.st->counter[6], 1u) == (unsigned)nb - 1;
         }
         __syncthreads();
-        if (*last && tid == 0) {
+        if (*last) {
             __threadfence();
+            double v1 = 0.0, v2 = 0.0;
+            for (int k = tid; k < nb; k += nthr) {
+                v1 += ((volatile double*)p.partials)[2 * k];
+                v2 += ((volatile double*)p.partials)[2 * k + 1];
+            }
             double t1 = 0.0, t2 = 0.0;
-            const int nb = gridDim.x * gridDim.y;
-            for (int k = 0; k < nb; k++) {
-                t1 += ((volatile double*)p.partials)[2 * k];
-                t2 += ((volatile double*)p.partials)[2 * k + 1];
+            block_sum2(v1, v2, t1, t2);
+            if (tid == 0) {
+                p.st->counter[6] = 0u;
+                KState* st = p.st;
+                if (st->first) {
+                    st->beta = 0.0;
+                    st->first = 0;
+                } else {
+                    st->beta = (t1 - t2) / st->rz;
+                }
+                st->rz = t1;
             }
-            p.st->counter[6] = 0u;
-            KState* st = p.st;
-            if (st->first) {
-                st->beta = 0.0;
-                st->first = 0;
-            } else {
-                st->beta = (t1 - t2) / st->rz;
-            }
-            st->rz = t1;
         }
     }
 }

@@ -441,6 +441,115 @@ bmg_status k_residual_to32(Ctx& c) {
     return BMG_OK;
 }
 
+// 2-D form of k_pspmv32_t: one CTA per tile of kThreads interior columns x H
+// rows, marching up the rows.  Every value of z, p_old and of the stored
+// planes is loaded once (plus a one-column, two-row halo) into a four-row
+// ring in shared memory; the loads of row j+2 are in flight while row j is
+// formed, with one barrier per row.  Same arithmetic, in the same order, as
+// k_pspmv32_t<2>.
+__global__ void __launch_bounds__(kThreads) k_pspmv2d_tiled(int n, int ld, long long pl, int H, int tiles_x,
+                                                            const float* __restrict__ A,
+                                                            const float* __restrict__ rs,
+                                                            const float* __restrict__ z,
+                                                            const float* __restrict__ pold, float* __restrict__ p,
+                                                            float* __restrict__ q, double* partials, KState* st) {
+    constexpr int TW = kThreads;
+    __shared__ float sP[4][TW + 2];    // p at columns i0-1 .. i0+TW
+    __shared__ float sW[4][TW + 1];    // stored planes at columns i0 .. i0+TW
+    __shared__ float sSW[4][TW + 1];
+    __shared__ float sNW[4][TW + 1];
+    const float beta = (float)st->beta;
+    const int t = threadIdx.x;
+    const int i0 = 1 + (int)(blockIdx.x % tiles_x) * TW;
+    const int j0 = 1 + (int)(blockIdx.x / tiles_x) * H;
+    const int j1 = min(j0 + H, n - 1);
+    const int i = i0 + t;
+    const bool act = i <= n - 2;
+    const int il = i0 - 1, ir = i0 + TW;    // halo columns (thread 0: left, thread 1: right)
+    struct Row {
+        float p, w, sw, nw, s, r, hp, hw, hsw, hnw;
+    };
+    auto load = [&](int j, Row& v) {
+        v = Row{0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+        if (j < 1 || j > n - 2) return;
+        const long long kr = (long long)j * ld;
+        if (act) {
+            const long long k = kr + i;
+            v.p = z[k] + beta * pold[k];
+            v.w = A[W2 * pl + k];
+            v.sw = A[SW2 * pl + k];
+            v.nw = A[NW2 * pl + k];
+            v.s = A[S2 * pl + k];
+            v.r = rs[k];
+        }
+        if (t == 0 && il >= 1) v.hp = z[kr + il] + beta * pold[kr + il];
+        if (t == 1 && ir <= n - 2) {
+            const long long k = kr + ir;
+            v.hp = z[k] + beta * pold[k];
+            v.hw = A[W2 * pl + k];
+            v.hsw = A[SW2 * pl + k];
+            v.hnw = A[NW2 * pl + k];
+        }
+    };
+    auto put = [&](int j, const Row& v) {
+        const int sl = j & 3;
+        sP[sl][t + 1] = v.p;
+        sW[sl][t] = v.w;
+        sSW[sl][t] = v.sw;
+        sNW[sl][t] = v.nw;
+        if (t == 0) sP[sl][0] = v.hp;
+        if (t == 1) {
+            sP[sl][TW + 1] = v.hp;
+            sW[sl][TW] = v.hw;
+            sSW[sl][TW] = v.hsw;
+            sNW[sl][TW] = v.hnw;
+        }
+    };
+    Row nx;
+    load(j0 - 1, nx);
+    put(j0 - 1, nx);
+    load(j0, nx);
+    put(j0, nx);
+    float rs_j = nx.r, s_j = nx.s;
+    load(j0 + 1, nx);
+    Acc32 acc;
+    for (int j = j0; j < j1; j++) {
+        put(j + 1, nx);
+        const float s_n = nx.s, rs_n = nx.r;
+        load(j + 2, nx);
+        __syncthreads();
+        if (act) {
+            const int sm = (j - 1) & 3, s0 = j & 3, sp = (j + 1) & 3;
+            const float pv = sP[s0][t + 1];
+            float v = rs_j * pv;
+            v += sW[s0][t] * (sP[s0][t] - pv);
+            v += sW[s0][t + 1] * (sP[s0][t + 2] - pv);
+            v += s_j * (sP[sm][t + 1] - pv);
+            v += s_n * (sP[sp][t + 1] - pv);
+            v += sSW[s0][t] * (sP[sm][t] - pv);
+            v += sSW[sp][t + 1] * (sP[sp][t + 2] - pv);
+            v += sNW[s0][t] * (sP[sp][t] - pv);
+            v += sNW[sm][t + 1] * (sP[sm][t + 2] - pv);
+            const long long k = (long long)j * ld + i;
+            p[k] = pv;
+            q[k] = v;
+            acc.add(pv * v);
+        }
+        rs_j = rs_n;
+        s_j = s_n;
+    }
+    double tot;
+    if (grid_sum(acc.value(), partials, &st->counter[2], &tot)) {
+        st->pq = tot;
+        if (!(tot > 0.0)) {
+            set_err(st, BMG_ERR_NOT_SPD);
+            st->alpha = 0.0;
+        } else {
+            st->alpha = st->rz / tot;
+        }
+    }
+}
+
 bmg_status k_row_sums32(Ctx& c) {
     const Level& L = c.lev[0];
     DISPATCH_DIM(c, k_row_sums32_t, L.A64, L.plane, c.rs32);
@@ -456,11 +565,44 @@ bmg_status k_rz_beta32(Ctx& c, const float* z, const float* zo) {
     return BMG_OK;
 }
 
+// Rows per tile of k_pspmv2d_tiled: minimise waves x (rows + 2 halo rows)
+// at the kernel's occupancy, with at most kMaxBlocks tiles.
+bmg_status pspmv_prepare(Ctx& c) {
+    if (c.dim != 2 || !c.rs32) return BMG_OK;
+    int sms = 0, occ = 0;
+    BMG_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, c.device));
+    BMG_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_pspmv2d_tiled, kThreads, 0));
+    if (occ < 1) return BMG_ERR_DEVICE;
+    const int m = c.lev[0].n - 2;
+    const int tx = cdiv(m, kThreads);
+    const long long slots = (long long)sms * occ;
+    long long best = -1;
+    for (int h = 1; h <= m; h++) {
+        const long long tiles = (long long)tx * cdiv(m, h);
+        if (tiles > kMaxBlocks) continue;
+        const long long cost = cdiv(tiles, slots) * (h + 2LL);
+        if (best < 0 || cost < best) {
+            best = cost;
+            c.spmv_h = h;
+            c.spmv_tiles_x = tx;
+            c.spmv_tiles = (int)tiles;
+        }
+    }
+    return best < 0 ? BMG_ERR_SHAPE : BMG_OK;
+}
+
 bmg_status k_pspmv32(Ctx& c, const float* z, int parity) {
     const Level& L = c.lev[0];
     prof_begin(c, BMG_PROF_SPMV, 0);
-    DISPATCH_DIM(c, k_pspmv32_t, L.A32, c.rs32, L.plane, z, c.p32s[parity ^ 1], c.p32s[parity], c.q32, c.partials,
-                 c.st);
+    if (c.dim == 2 && c.spmv_h > 0) {
+        k_pspmv2d_tiled<<<c.spmv_tiles, kThreads, 0, c.stream>>>(L.n, L.ld, L.plane, c.spmv_h, c.spmv_tiles_x,
+                                                                 L.A32, c.rs32, z, c.p32s[parity ^ 1],
+                                                                 c.p32s[parity], c.q32, c.partials, c.st);
+        c.launches++;
+    } else {
+        DISPATCH_DIM(c, k_pspmv32_t, L.A32, c.rs32, L.plane, z, c.p32s[parity ^ 1], c.p32s[parity], c.q32,
+                     c.partials, c.st);
+    }
     prof_end(c, BMG_PROF_SPMV, 0, (c.ns + 4) * 4.0 * dofs0(c));
     BMG_CUDA(cudaGetLastError());
     return BMG_OK;
