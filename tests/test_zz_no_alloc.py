@@ -40,11 +40,14 @@ def test_twice_in_a_row_matches_existing_entry_point(dim, n):
 
 
 def test_largest_accepted_size_matches_oracle():
+    """Against the oracle the bound grows with n: the Jacobian is formed from
+    coordinate differences of size 1/(n-1), whose relative rounding is about
+    (n-1) eps, so the entries agree to a few n eps of the diagonal."""
     n = 640    # not 2^k+1: the entry point needs no hierarchy
     p = inputs.annulus_plain(n)
     out = torch.empty((n, n, 9), dtype=torch.float64, device="cuda")
     got = _noalloc(p, out)
-    assert rel_to_diag(got, oracle.assemble(p.coords, p.kappa)) <= TOL
+    assert rel_to_diag(got, oracle.assemble(p.coords, p.kappa)) <= 4 * n * np.finfo(float).eps
 
 
 @pytest.mark.parametrize("dim,n", [(2, 641), (3, 49)])
