@@ -47,6 +47,9 @@ def parse():
     ap.add_argument("--n", type=int, default=4097)
     ap.add_argument("--cpu-sample-n", type=int, default=1025)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-graphs", action="store_true",
+                    help="launch every kernel on the stream instead of replaying the per-iteration CUDA graphs "
+                         "(for profilers that replay single kernels)")
     ap.add_argument("--workload", default="annulus", choices=["annulus", "annulus65", "shell", "batch", "adjoint"],
                     help="annulus: the 4097^2 quarter annulus (default, the headline); annulus65: 65^2 plain; "
                          "shell: 257^3 spherical-shell octant; batch: 512 bump-map problems x 4 rhs; "
@@ -62,7 +65,7 @@ def peaks():
     return 6800.0, "fallback"
 
 
-def config_for(n: int) -> dict:
+def config_for(n: int, graphs: bool = True) -> dict:
     stencil_mb = 5 * 8 * n * n / 1e6
     return {"workload": f"quarter_annulus_lognormal_kappa_n{n}", "nodes_per_side": n, "dof": (n - 2) ** 2,
             "map": "x=(1/2+s/2)cos(pi t/2), y=(1/2+s/2)sin(pi t/2)",
@@ -71,7 +74,8 @@ def config_for(n: int) -> dict:
             "outer": "FP32 V-cycle preconditioner with FP64 residual: iterative refinement (FP32 inner CG) or "
                      "FP64 flexible CG, the faster is the headline (headline_variant); plain FP64 CG + FP64 "
                      "V-cycle in the fp64 field",
-            "tol": TOL, "l2": f"inputs larger than L2 (FP64 stencil {stencil_mb:.0f} MB > 129 MB), no flush"}
+            "tol": TOL, "l2": f"inputs larger than L2 (FP64 stencil {stencil_mb:.0f} MB > 129 MB), no flush",
+            "launch": "per-iteration CUDA graphs" if graphs else "stream launches (no graphs)"}
 
 
 # ---------------------------------------------------------------- clocks
@@ -211,7 +215,7 @@ def run_own(args):
     stream = torch.cuda.current_stream(dev)
 
     def build(prec, outer=None):
-        s = binding.Solver(2, n, precision=prec, outer=outer, device=dev)
+        s = binding.Solver(2, n, precision=prec, outer=outer, device=dev, graphs=not args.no_graphs)
         e0, e1, e2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
         e0.record(stream)
         s.assemble(coords, kappa)
@@ -308,7 +312,7 @@ def run_own(args):
     out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
            "warmup": args.warmup, "ms_per_step": t32, "higher_is_better": True, "scaling": "weak",
            "vs_baseline": None, "dtype": "f32 V-cycle / f64 residual", "data": "synthetic",
-           "config": config_for(n), "e2e": e2e, "gpu_launches": launches32,
+           "config": config_for(n, not args.no_graphs), "e2e": e2e, "gpu_launches": launches32,
            "headline_variant": head,
            "iterations": infos32[-1].iterations, "true_relres": infos32[-1].true_relres,
            "fp32_variants": {k: {"value": world * dof / (v[0] / args.steps * 1e-3), "ms_per_step": v[0] / args.steps,

@@ -181,14 +181,15 @@ class Solver:
     """
 
     def __init__(self, dim: int, n: int, precision: str = "fp64", outer: str | None = None,
-                 device=None, stream: torch.cuda.Stream | None = None, unfused: bool = False):
+                 device=None, stream: torch.cuda.Stream | None = None, unfused: bool = False,
+                 graphs: bool = True):
         lib = load()
         self.dim, self.n, self.precision = dim, n, precision
         if outer is None:
             outer = "flexible" if precision == "fp32" else "cg"
         self.outer = outer
         self.device = torch.device(device) if device is not None else torch.device("cuda", torch.cuda.current_device())
-        opts = _Opts(dim, n, PREC[precision], OUTER[outer], 1 if unfused else 0)
+        opts = _Opts(dim, n, PREC[precision], OUTER[outer], (1 if unfused else 0) | (0 if graphs else 2))
         h = ctypes.c_void_p()
         _check(lib.bmg_create(ctypes.byref(opts), ctypes.byref(h)), "bmg_create")
         self._h = h
