@@ -315,8 +315,9 @@ __global__ void __launch_bounds__(72 * K) k_vdown2d(const __grid_constant__ CUte
         __syncthreads();
     }
     // interpolation weights of the thread's coarse node for the restriction,
-    // loaded one step ahead
-    T w[8];
+    // loaded one step ahead.  After colour 3 the odd-odd fine points have
+    // zero residual, so their four weights are not needed.
+    T w[4];
     auto load_w = [&](int Jp) {
         const bool d = vres && Jp <= nc - 2;
         const long long o = (long long)Jp * p.ldc + I;
@@ -324,10 +325,6 @@ __global__ void __launch_bounds__(72 * K) k_vdown2d(const __grid_constant__ CUte
         w[1] = d ? Pg[PXL * p.plc + o] : (T)0;
         w[2] = d ? Pg[PYN * p.plc + o - p.ldc] : (T)0;
         w[3] = d ? Pg[PYS * p.plc + o] : (T)0;
-        w[4] = d ? Pg[PNE * p.plc + o - p.ldc - 1] : (T)0;
-        w[5] = d ? Pg[PNW * p.plc + o - p.ldc] : (T)0;
-        w[6] = d ? Pg[PSE * p.plc + o - 1] : (T)0;
-        w[7] = d ? Pg[PSW * p.plc + o] : (T)0;
     };
     load_w(J0 + ty);
     for (int J = J0; ok && J < J0 + p.hc; J += K) {
@@ -366,10 +363,6 @@ __global__ void __launch_bounds__(72 * K) k_vdown2d(const __grid_constant__ CUte
             b += w[1] * Rm[c + 1];
             b += w[2] * Rs[c];
             b += w[3] * Rn[c];
-            b += w[4] * Rs[c - 1];
-            b += w[5] * Rs[c + 1];
-            b += w[6] * Rn[c - 1];
-            b += w[7] * Rn[c + 1];
             bcg[(long long)Jp * p.ldc + I] = b;
         }
         load_w(Jp + K);

@@ -203,7 +203,9 @@ bmg_status vcycle2d_fused(Ctx& c, void* z, bool ir = false, const float* zold = 
         const double szf = (l == 0 && !ir) ? 8.0 : sz;
         prof_begin(c, BMG_PROF_VDOWN, l);
         BMG_TRY(fused_down(c, l, ir));
-        prof_end(c, BMG_PROF_VDOWN, l, N * (c.ns * sz + szf + sz + c.np / 4.0 * sz + sz / 4));
+        // restriction reads the four edge weights of each coarse node (the
+        // odd-odd fine points carry no residual after the last colour)
+        prof_end(c, BMG_PROF_VDOWN, l, N * (c.ns * sz + szf + sz + (c.np / 2) / 4.0 * sz + sz / 4));
     }
     {
         const Level& C = c.lev[L - 1];
@@ -217,7 +219,8 @@ bmg_status vcycle2d_fused(Ctx& c, void* z, bool ir = false, const float* zold = 
         const double szo = (l == 0 && !ir) ? 8.0 : sz;
         prof_begin(c, BMG_PROF_VUP, l);
         BMG_TRY(fused_up(c, l, l == 0 ? z : c.lev[l].r, ir, zold));
-        prof_end(c, BMG_PROF_VUP, l, N * (c.ns * sz + szf + sz + c.np / 4.0 * sz + sz / 4 + szo));
+        const double szz = (l == 0 && ir && zold) ? 4.0 : 0.0;   // z_old read for the fused beta
+        prof_end(c, BMG_PROF_VUP, l, N * (c.ns * sz + szf + sz + c.np / 4.0 * sz + sz / 4 + szo + szz));
     }
     (void)f32;
     BMG_CUDA(cudaGetLastError());
