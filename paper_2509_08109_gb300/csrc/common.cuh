@@ -279,6 +279,12 @@ bmg_status fused_occupancy(bool f32, bool f64in, int wc, int* down_blocks, int* 
 bmg_status fused_down(Ctx& c, int l, bool ir = false);
 bmg_status fused_up(Ctx& c, int l, void* out, bool ir = false, const float* zold = nullptr);
 bmg_status vcycle_f32(Ctx& c, float* z32, const float* zold = nullptr);
+// tail2d.cu: the levels from the first one with n <= kTailMaxN (at least
+// level 1) down to the coarsest, in one single-CTA launch
+constexpr int kTailMaxN = 33;
+int tail_first_level(const Ctx& c);
+size_t tail_smem_bytes(const Ctx& c, int t);
+bmg_status tail_vcycle(Ctx& c, int t);
 // z32 = M r32 (FP32 in and out); with zold and the streaming kernels the
 // finest up kernel also forms r.z, r.z_old and the flexible-CG beta
 bool vcycle_forms_beta(const Ctx& c);

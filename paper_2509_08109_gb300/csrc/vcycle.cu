@@ -191,14 +191,14 @@ bmg_status vcycle2d_impl(Ctx& c, const T* b0, T* x0) {
     return BMG_OK;
 }
 
-// Streaming path: one down kernel and one up kernel per level pair.
+// Streaming path: one down kernel and one up kernel per level pair above
+// the tail, and one single-CTA kernel for the tail levels.
 template <typename T>
 bmg_status vcycle2d_fused(Ctx& c, void* z, bool ir = false, const float* zold = nullptr) {
-    cudaStream_t s = c.stream;
-    const int L = c.nlev;
     const double sz = sizeof(T);
-    const bool f32 = sizeof(T) == 4;
-    for (int l = 0; l < L - 1; l++) {
+    // levels t.. (n <= kTailMaxN) run in one single-CTA launch
+    const int t = tail_first_level(c);
+    for (int l = 0; l < t; l++) {
         const double N = dofs(c, l);
         const double szf = (l == 0 && !ir) ? 8.0 : sz;
         prof_begin(c, BMG_PROF_VDOWN, l);
@@ -207,13 +207,8 @@ bmg_status vcycle2d_fused(Ctx& c, void* z, bool ir = false, const float* zold = 
         // odd-odd fine points carry no residual after the last colour)
         prof_end(c, BMG_PROF_VDOWN, l, N * (c.ns * sz + szf + sz + (c.np / 2) / 4.0 * sz + sz / 4));
     }
-    {
-        const Level& C = c.lev[L - 1];
-        LV<T> v{Aof<T>(C), C.n, C.ld, C.plane};
-        k_coarsest2d<T><<<1, 1, 0, s>>>(v, C.A64, (const T*)C.b, (T*)C.r);
-        c.launches++;
-    }
-    for (int l = L - 2; l >= 0; l--) {
+    BMG_TRY(tail_vcycle(c, t));
+    for (int l = t - 1; l >= 0; l--) {
         const double N = dofs(c, l);
         const double szf = (l == 0 && !ir) ? 8.0 : sz;
         const double szo = (l == 0 && !ir) ? 8.0 : sz;
@@ -222,7 +217,6 @@ bmg_status vcycle2d_fused(Ctx& c, void* z, bool ir = false, const float* zold = 
         const double szz = (l == 0 && ir && zold) ? 4.0 : 0.0;   // z_old read for the fused beta
         prof_end(c, BMG_PROF_VUP, l, N * (c.ns * sz + szf + sz + c.np / 4.0 * sz + sz / 4 + szo + szz));
     }
-    (void)f32;
     BMG_CUDA(cudaGetLastError());
     return BMG_OK;
 }
