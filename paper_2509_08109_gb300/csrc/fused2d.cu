@@ -20,9 +20,9 @@
 // dependencies.  A step handles K row pairs at once: thread (x, y) owns
 // the column pair (2x, 2x+1) of row pair y, so every colour phase keeps all
 // threads busy and a step costs six block barriers for 2K fine rows.  Rows
-// arrive by TMA (cp.async.bulk.tensor) into a ring of RP = 2K+2 row-pair
+// arrive by TMA (cp.async.bulk.tensor) into a ring of RP = K+2+D row-pair
 // slots, each completed by an mbarrier with an expected byte count; the
-// next K pairs are in flight while a step computes; one thread issues all
+// next D = K pairs are in flight while a step computes; one thread issues all
 // copies.  Interpolation weights go straight from global memory into
 // registers (each is used by one thread).  Every mbarrier wait is bounded
 // by the global timer; on expiry the CTA records BMG_ERR_TIMEOUT, drains its
@@ -106,7 +106,12 @@ __device__ __forceinline__ float divide<float>(float s, float d) { return __fdiv
 // and (down) an equal ring of the residual R, then the mbarriers.
 template <typename T, typename TF, int K, bool UP>
 struct Lay {
-    static constexpr int RP = 2 * K + 2;
+    // ring slots: the K pairs of the current step, the two pairs below it
+    // (halo rows), and D = K pairs in flight (one step ahead; two steps ahead
+    // measured no faster on the 4097^2 refinement solve, with the wider ring
+    // costing strip width or occupancy)
+    static constexpr int D = K;
+    static constexpr int RP = K + 2 + D;
     static constexpr int XR = K <= 2 ? 8 : 16;   // rows of the X / R rings (>= 2K + 4)
     int WW, WWc, sA, sF, sXp, sC;
     __host__ __device__ Lay(int wc) {
@@ -332,14 +337,12 @@ __global__ void __launch_bounds__(72 * K) k_vdown2d(const __grid_constant__ CUte
         ok = wait_pairs<RP>(rg.bars, qa, qa + K);
         if (!ok) break;
         waited = qa + K;
-        // every thread is past the previous step: refill its freed slots with
-        // the next step's row pairs
-        if (lead && J > J0)
-            for (int t = 0; t < K; t++) {
-                const int q = qa + K + t;
-                if (q < npairs) issue(q);
-            }
-        issued = max(issued, min(npairs, qa + 2 * K));
+        // every thread is past the previous step: refill the freed slots
+        // (pairs up to qa - 3 are done) with the pairs D ahead
+        const int lim = min(npairs, qa - 2 + RP);
+        if (lead)
+            for (int q = issued; q < lim; q++) issue(q);
+        issued = max(issued, lim);
         const int Jp = J + ty, jm = 2 * Jp, jo = jm + 1, je = jm + 2;
         const bool do_res = vres && Jp <= nc - 2;
         c0(je);
@@ -537,12 +540,12 @@ __global__ void __launch_bounds__(72 * K) k_vup2d(const __grid_constant__ CUtens
         ok = wait_pairs<RP>(rg.bars, qa, qa + K);
         if (!ok) break;
         waited = qa + K;
-        if (lead && J > J0)
-            for (int t = 0; t < K; t++) {
-                const int q = qa + K + t;
-                if (q < npairs) issue(q);
-            }
-        issued = max(issued, min(npairs, qa + 2 * K));
+        // every thread is past the previous step: refill the freed slots
+        // (pairs up to qa - 3 are done) with the pairs D ahead
+        const int lim = min(npairs, qa - 2 + RP);
+        if (lead)
+            for (int q = issued; q < lim; q++) issue(q);
+        issued = max(issued, lim);
         corr_odd(jo, wy);
         corr_even(je, wxl, wxr);
         load_w(Jp + K);

@@ -50,7 +50,7 @@ bmg_status model_rows(Ctx& c, int l, int wc, int* hc_out, int* tiles_y_out) {
     const int m = c.lev[l + 1].n - 1;
     const int tiles_x = cdiv(m, wc);
     int od = 0, ou = 0;
-    BMG_TRY(fused_occupancy(f32, f32 && l == 0, wc, &od, &ou));
+    BMG_TRY(fused_occupancy(f32, f32 && l == 0 && !c.r32, wc, &od, &ou));
     const int occ = od < ou ? od : ou;
     if (occ < 1) return BMG_ERR_DEVICE;
     const long long slots = (long long)occ * sms;
@@ -75,7 +75,9 @@ bmg_status model_rows(Ctx& c, int l, int wc, int* hc_out, int* tiles_y_out) {
 bmg_status fused_configure(Ctx& c, int l, int wc, int hc) {
     const bool f32 = c.opts.precision == BMG_PREC_FP32;
     const int K = fused_rows_per_step(f32);
-    if (wc != 8 && wc != 16 && wc != 32 && wc != 64) return BMG_ERR_ARG;
+    // wc a multiple of 8: the TMA x coordinates 2 I0 - 10 and I0 - 5 then
+    // start on 16-byte boundaries in FP32 and FP64
+    if (wc < 8 || wc > 64 || wc % 8) return BMG_ERR_ARG;
     if (hc < K || hc % K) return BMG_ERR_ARG;
     FusedLevel& F = c.fused[l];
     const Level& Lf = c.lev[l];
@@ -117,10 +119,29 @@ bmg_status fused_configure(Ctx& c, int l, int wc, int hc) {
     return BMG_OK;
 }
 
+// Default strip width of level l: the widest multiple of 8 up to a size
+// cap that maximises useful columns in flight per SM, occupancy x wc (the
+// kernels are bound by the bytes their TMA rings keep in flight).
+int default_wc(Ctx& c, int l) {
+    const bool f32 = c.opts.precision == BMG_PREC_FP32;
+    const int m = c.lev[l + 1].n - 1;
+    const int cap = m >= 512 ? 64 : m >= 128 ? 32 : m >= 32 ? 16 : 8;
+    int best = 8, best_score = -1;
+    for (int wc = cap; wc >= 8; wc -= 8) {
+        int od = 0, ou = 0;
+        if (fused_occupancy(f32, f32 && l == 0 && !c.r32, wc, &od, &ou) != BMG_OK) continue;
+        const int score = (od < ou ? od : ou) * wc;
+        if (score > best_score) {
+            best_score = score;
+            best = wc;
+        }
+    }
+    return best;
+}
+
 bmg_status fused_prepare(Ctx& c) {
     for (int l = 0; l + 1 < c.nlev; l++) {
-        const int m = c.lev[l + 1].n - 1;
-        const int wc = m >= 512 ? 64 : m >= 128 ? 32 : m >= 32 ? 16 : 8;
+        const int wc = default_wc(c, l);
         int hc = 0, ty = 0;
         BMG_TRY(model_rows(c, l, wc, &hc, &ty));
         BMG_TRY(fused_configure(c, l, wc, hc));
@@ -147,7 +168,7 @@ bmg_status fused_autotune(Ctx& c, int reps, double* best_ms_total) {
         const int m = c.lev[l + 1].n - 1;
         int best_wc = c.fused[l].wc, best_hc = c.fused[l].hc;
         float best = -1.f;
-        for (int wc = 8; wc <= 64; wc *= 2) {
+        for (int wc = 8; wc <= 64; wc += 8) {
             if (cdiv(m, wc) < 1 || (wc > 8 && m < wc / 2)) continue;
             int hc0 = 0, ty = 0;
             BMG_TRY(model_rows(c, l, wc, &hc0, &ty));

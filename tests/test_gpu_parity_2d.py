@@ -244,8 +244,11 @@ def test_refinement_reaches_fp64_tolerance(n, unfused):
 # ------------------------------------------------------------------ tile autotuner
 def test_autotune_keeps_results_bitwise(tmp_path):
     """Tile shapes change only which CTA computes a node (halo columns are
-    recomputed identically), so the V-cycle and the solve are bitwise
-    unchanged; the choice round-trips through the cache file."""
+    recomputed identically), so the V-cycle is bitwise unchanged, and so is
+    the FP64 solve.  In the refinement mode the finest up kernel also sums
+    r.z per CTA, so there the solve takes the same iterations to the same
+    tolerance but may differ in the last bits.  The choice round-trips
+    through the cache file."""
     p = _problem(1025)
     for prec, outer in (("fp64", "cg"), ("fp32", "refine")):
         s = solver_for(p, precision=prec, outer=outer)
@@ -258,8 +261,12 @@ def test_autotune_keeps_results_bitwise(tmp_path):
         assert len(after) == len(before) == s.levels - 1
         assert torch.equal(s.vcycle(r), z0)
         x1, i1 = s.solve(r, tol=1e-10)
-        assert torch.equal(x1, x0) and i1.iterations == i0.iterations
+        assert i1.iterations == i0.iterations and i1.true_relres <= 1e-10
+        if outer == "cg":
+            assert torch.equal(x1, x0)
+        else:
+            assert relerr(x1.cpu().numpy(), x0.cpu().numpy()) <= 1e-8
         s2 = solver_for(p, precision=prec, outer=outer)
         assert s2.autotune(cache=cache) == after
     with pytest.raises(binding.BmgError):
-        s.set_tiles([(24, 4)])
+        s.set_tiles([(20, 4)])     # strip widths are multiples of 8
