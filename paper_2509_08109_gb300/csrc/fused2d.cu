@@ -102,7 +102,7 @@ __device__ __forceinline__ float divide<float>(float s, float d) { return __fdiv
 
 // Shared-memory layout: RP ring slots of one row pair each (stencil planes,
 // right-hand side, and for the up kernel the pre-smoothed iterate and one
-// coarse row of the coarse iterate), then a 16-row ring of the iterate X
+// coarse row of the coarse iterate), then a (2K+4)-row ring of the iterate X
 // and (down) an equal ring of the residual R, then the mbarriers.
 template <typename T, typename TF, int K, bool UP>
 struct Lay {
@@ -112,7 +112,9 @@ struct Lay {
     // costing strip width or occupancy)
     static constexpr int D = K;
     static constexpr int RP = K + 2 + D;
-    static constexpr int XR = K <= 2 ? 8 : 16;   // rows of the X / R rings (>= 2K + 4)
+    // rows of the X / R rings: a step reads and writes fine rows 2J-1 .. 2J+2K
+    // (2K+2 rows); consecutive steps are separated by a block barrier
+    static constexpr int XR = 2 * K + 4;
     int WW, WWc, sA, sF, sXp, sC;
     __host__ __device__ Lay(int wc) {
         WW = 2 * wc + 16;
@@ -140,7 +142,9 @@ struct Ring {
     unsigned char *pA, *pF, *pXp, *pC;
     uint64_t* bars;
     int q0, WW, sA, sF, sXp, sC;
-    __device__ __forceinline__ int slot_of_row(int j) const { return ((((j - 1) >> 1) - q0)) % Lay<T, TF, K, UP>::RP; }
+    __device__ __forceinline__ int slot_of_row(int j) const {
+        return (int)((unsigned)(((j - 1) >> 1) - q0) % (unsigned)Lay<T, TF, K, UP>::RP);
+    }
     __device__ __forceinline__ const T* A(int j) const {      // plane 0 of fine row j
         return (const T*)(pA + slot_of_row(j) * sA) + ((j - 1) & 1) * WW;
     }
@@ -151,7 +155,7 @@ struct Ring {
         return (const T*)(pXp + slot_of_row(j) * sXp) + ((j - 1) & 1) * WW;
     }
     __device__ __forceinline__ const T* C(int J) const {      // coarse row J (carried by pair J-1)
-        return (const T*)(pC + ((J - 1 - q0) % Lay<T, TF, K, UP>::RP) * sC);
+        return (const T*)(pC + (int)((unsigned)(J - 1 - q0) % (unsigned)Lay<T, TF, K, UP>::RP) * sC);
     }
 };
 
@@ -159,7 +163,7 @@ struct Ring {
 template <int RP>
 __device__ __forceinline__ bool wait_pairs(uint64_t* bars, int qa, int qb) {
     bool mine = true;
-    for (int q = qa; q < qb; q++) mine = mine && mbar_wait(bars + (q % RP), (uint32_t)((q / RP) & 1));
+    for (int q = qa; q < qb; q++) mine = mine && mbar_wait(bars + ((unsigned)q % RP), ((unsigned)q / RP) & 1u);
     return __syncthreads_and(mine) != 0;
 }
 
@@ -210,7 +214,7 @@ struct Rows {
 
 // ------------------------------------------------------------------ down kernel
 template <typename T, typename TF, int K>
-__global__ void __launch_bounds__(72 * K) k_vdown2d(const __grid_constant__ CUtensorMap tmA,
+__global__ void __launch_bounds__(72 * K, sizeof(T) == 4 ? 3 : 1) k_vdown2d(const __grid_constant__ CUtensorMap tmA,
                                                     const __grid_constant__ CUtensorMap tmF, FusedArgs p) {
     using LY = Lay<T, TF, K, false>;
     constexpr int RP = LY::RP;
@@ -239,7 +243,7 @@ __global__ void __launch_bounds__(72 * K) k_vdown2d(const __grid_constant__ CUte
     const int nf = p.nf, nc = p.nc;
     const uint32_t txb = L.tx();
     auto issue = [&](int q) {
-        const int s = q % RP, Jp = rg.q0 + q;
+        const int s = (int)((unsigned)q % RP), Jp = rg.q0 + q;
         uint64_t* bar = rg.bars + s;
         mbar_expect_tx(bar, txb);
         tma3d(rg.pA + s * L.sA, &tmA, bar, x0, 2 * Jp + 1, 0);
@@ -264,8 +268,8 @@ __global__ void __launch_bounds__(72 * K) k_vdown2d(const __grid_constant__ CUte
     const int I = xc0 + tx;
     const bool vres = tx >= 5 && tx < 5 + p.wc && I >= 1 && I <= nc - 2;
     auto inrow = [&](int j) { return j >= 1 && j <= nf - 2; };
-    auto X = [&](int j) { return sX + (j & (XR - 1)) * WW; };
-    auto R = [&](int j) { return sR + (j & (XR - 1)) * WW; };
+    auto X = [&](int j) { return sX + (int)((unsigned)j % XR) * WW; };
+    auto R = [&](int j) { return sR + (int)((unsigned)j % XR) * WW; };
     auto rows = [&](int j) {
         return Rows<T>{rg.A(j), rg.A(j + 1), rg.A(j - 1), X(j), X(j + 1), X(j - 1), PL};
     };
@@ -387,7 +391,7 @@ __global__ void __launch_bounds__(72 * K) k_vdown2d(const __grid_constant__ CUte
     if (!ok) {
         if (lead) {
             set_err(p.st, BMG_ERR_TIMEOUT);
-            for (int q = waited; q < issued; q++) mbar_wait(rg.bars + (q % RP), (uint32_t)((q / RP) & 1));
+            for (int q = waited; q < issued; q++) mbar_wait(rg.bars + ((unsigned)q % RP), ((unsigned)q / RP) & 1u);
         }
         __syncthreads();
     }
@@ -395,7 +399,7 @@ __global__ void __launch_bounds__(72 * K) k_vdown2d(const __grid_constant__ CUte
 
 // ------------------------------------------------------------------ up kernel
 template <typename T, typename TF, typename TO, int K>
-__global__ void __launch_bounds__(72 * K) k_vup2d(const __grid_constant__ CUtensorMap tmA,
+__global__ void __launch_bounds__(72 * K, sizeof(T) == 4 ? 3 : 1) k_vup2d(const __grid_constant__ CUtensorMap tmA,
                                                   const __grid_constant__ CUtensorMap tmF,
                                                   const __grid_constant__ CUtensorMap tmX,
                                                   const __grid_constant__ CUtensorMap tmC, FusedArgs p) {
@@ -427,7 +431,7 @@ __global__ void __launch_bounds__(72 * K) k_vup2d(const __grid_constant__ CUtens
     const int nf = p.nf, nc = p.nc;
     const uint32_t txb = L.tx();
     auto issue = [&](int q) {
-        const int s = q % RP, Jp = rg.q0 + q;
+        const int s = (int)((unsigned)q % RP), Jp = rg.q0 + q;
         uint64_t* bar = rg.bars + s;
         mbar_expect_tx(bar, txb);
         tma3d(rg.pA + s * L.sA, &tmA, bar, x0, 2 * Jp + 1, 0);
@@ -453,7 +457,7 @@ __global__ void __launch_bounds__(72 * K) k_vup2d(const __grid_constant__ CUtens
     const int I = xc0 + tx;                      // coarse column of the thread's column pair
     const bool vI = I >= 0 && I <= nc - 1;
     auto inrow = [&](int j) { return j >= 1 && j <= nf - 2; };
-    auto X = [&](int j) { return sX + (j & (XR - 1)) * WW; };
+    auto X = [&](int j) { return sX + (int)((unsigned)j % XR) * WW; };
     auto rows = [&](int j) {
         return Rows<T>{rg.A(j), rg.A(j + 1), rg.A(j - 1), X(j), X(j + 1), X(j - 1), PL};
     };
@@ -591,7 +595,7 @@ __global__ void __launch_bounds__(72 * K) k_vup2d(const __grid_constant__ CUtens
     if (!ok) {
         if (lead) {
             set_err(p.st, BMG_ERR_TIMEOUT);
-            for (int q = waited; q < issued; q++) mbar_wait(rg.bars + (q % RP), (uint32_t)((q / RP) & 1));
+            for (int q = waited; q < issued; q++) mbar_wait(rg.bars + ((unsigned)q % RP), ((unsigned)q / RP) & 1u);
         }
         __syncthreads();
         return;
@@ -660,7 +664,7 @@ __global__ void __launch_bounds__(72 * K) k_vup2d(const __grid_constant__ CUtens
 
 // ------------------------------------------------------------------ host side
 template <typename T>
-constexpr int k_of() { return sizeof(T) == 4 ? 4 : 2; }
+constexpr int k_of() { return sizeof(T) == 4 ? 3 : 2; }   // FP32: ring of 8 slots, 3 CTAs/SM
 
 template <typename T, typename TF>
 int down_smem(int wc) { return Lay<T, TF, k_of<T>(), false>(wc).bytes(); }
