@@ -57,6 +57,9 @@ size_t carve(Ctx& c, char* base) {
             L.P64 = nullptr;
             L.P32 = nullptr;
         }
+        L.cb = (f32 && c.dim == 3 && l < c.nlev - 1)
+                   ? (float*)take(sizeof(float) * 27 * ipow(L.n - 2, 3))
+                   : nullptr;
         L.b = (l > 0 || f32) ? take(vt * L.plane) : nullptr;
         L.x = take(vt * L.plane);
         L.r = take(vt * L.plane);
@@ -250,7 +253,7 @@ bmg_status pcg_ir(Ctx& c, double tol, int maxit, bmg_info* info) {
             if (want < floor_red) want = floor_red;
             int m = (int)ceil(log(want) / log(rho)) + 1;
             if (m < 2) m = 2;
-            if (m > 40) m = 40;
+            if (m > kMaxInner) m = kMaxInner;
             if (m > maxit - it) m = maxit - it;
             for (int k = 0; k < m; k++) BMG_TRY(run_iteration(c, (it + k) & 1));
             it += m;
@@ -264,7 +267,7 @@ bmg_status pcg_ir(Ctx& c, double tol, int maxit, bmg_info* info) {
             const double red = sqrt(h.rr / rr);
             if (red > 0 && red < 1) {
                 const double r1 = pow(red, 1.0 / m);
-                if (r1 > 0.02 && r1 < 0.95) rho = r1;
+                if (r1 > 0.02 && r1 < 0.999) rho = r1;
             }
             rr = h.rr;
         }

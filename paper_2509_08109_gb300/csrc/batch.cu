@@ -99,7 +99,7 @@ bmg_status advance(Job& j, double tol, int maxit) {
         const double red = sqrt(h.rr / j.rr);
         if (red > 0 && red < 1) {
             const double r1 = pow(red, 1.0 / j.m);
-            if (r1 > 0.02 && r1 < 0.95) j.rho = r1;
+            if (r1 > 0.02 && r1 < 0.999) j.rho = r1;
         }
         j.rr = h.rr;
         j.refinements++;
@@ -114,7 +114,7 @@ bmg_status advance(Job& j, double tol, int maxit) {
     if (want < 1e-6) want = 1e-6;
     int m = (int)ceil(log(want) / log(j.rho)) + 1;
     if (m < 2) m = 2;
-    if (m > 40) m = 40;
+    if (m > kMaxInner) m = kMaxInner;
     if (m > maxit - j.it) m = maxit - j.it;
     for (int k = 0; k < m; k++) BMG_TRY(run_iteration(c, (j.it + k) & 1));
     j.it += m;

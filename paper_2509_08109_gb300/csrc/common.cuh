@@ -35,6 +35,9 @@ namespace bmg {
 constexpr int kMaxLevels = 20;
 constexpr int kThreads = 256;
 constexpr int kMaxBlocks = 4096;       // partials buffer size for reductions (two sums per block)
+// refinement mode: most FP32 inner iterations between two FP64 residuals
+// (slowly converging problems, e.g. the 3-D shell, need hundreds per solve)
+constexpr int kMaxInner = 400;
 
 enum Plane2 { C2 = 0, W2 = 1, S2 = 2, SW2 = 3, NW2 = 4, NS2 = 5 };
 enum PPlane2 { PXL = 0, PXR = 1, PYS = 2, PYN = 3, PSW = 4, PSE = 5, PNW = 6, PNE = 7, NP2 = 8 };
@@ -67,6 +70,7 @@ struct Level {
     void* b = nullptr;        // V-cycle right-hand side (V-cycle precision)
     void* x = nullptr;        // V-cycle iterate
     void* r = nullptr;        // residual scratch
+    float* cb = nullptr;      // 3-D FP32: full 27-entry rows in colour blocks (smoother)
 };
 
 struct ProfSlot {
@@ -279,6 +283,19 @@ bmg_status fused_occupancy(bool f32, bool f64in, int wc, int* down_blocks, int* 
 bmg_status fused_down(Ctx& c, int l, bool ir = false);
 bmg_status fused_up(Ctx& c, int l, void* out, bool ir = false, const float* zold = nullptr);
 bmg_status vcycle_f32(Ctx& c, float* z32, const float* zold = nullptr);
+// vcycle3d.cu: colour-blocked full rows of the FP32 levels (after demotion)
+bmg_status colour_blocks3d(Ctx& c);
+// interior nodes of colour col (parities col&1, col>>1&1, col>>2) on an n-grid,
+// and the offset of that colour's block (27 entries per node) in Level::cb
+__host__ __device__ inline int cb_side(int n, int parity) { return parity ? (n - 1) / 2 : (n - 2) / 2; }
+__host__ __device__ inline long long cb_count(int n, int col) {
+    return (long long)cb_side(n, col & 1) * cb_side(n, (col >> 1) & 1) * cb_side(n, col >> 2);
+}
+__host__ __device__ inline long long cb_offset(int n, int col) {
+    long long o = 0;
+    for (int q = 0; q < col; q++) o += 27 * cb_count(n, q);
+    return o;
+}
 // tail2d.cu: the levels from the first one with n <= kTailMaxN (at least
 // level 1) down to the coarsest, in one single-CTA launch
 constexpr int kTailMaxN = 33;

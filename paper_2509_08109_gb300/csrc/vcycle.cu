@@ -236,6 +236,7 @@ bmg_status demote_levels(Ctx& c) {
         }
     }
     BMG_CUDA(cudaGetLastError());
+    if (c.dim == 3) BMG_TRY(colour_blocks3d(c));
     return BMG_OK;
 }
 

@@ -42,6 +42,47 @@ __global__ void k_gs_colour3d(L3<T> L, const T* __restrict__ f, T* __restrict__ 
     x[o] = (f[o] - offdiag3(L, x, i, j, k)) / L.A[13 * L.pl + o];
 }
 
+// Colour-blocked rows: node t of colour col (t runs i fastest over that
+// colour's interior nodes) keeps its 27 full-row entries at
+// cb[cb_offset(col) + e * count(col) + t], so a colour sweep reads them
+// coalesced instead of at stride 2 from the symmetric-half planes.
+__global__ void k_cblocks3d(Sten3<float> S, float* __restrict__ cb) {
+    const int n = S.n;
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    const int j = blockIdx.y, k = blockIdx.z;
+    if (i < 1 || j < 1 || k < 1 || i > n - 2 || j > n - 2 || k > n - 2) return;
+    const int col = (i & 1) | ((j & 1) << 1) | ((k & 1) << 2);
+    const int ni = cb_side(n, i & 1), nj = cb_side(n, j & 1);
+    // first interior index of parity p is 2 - p
+    const long long t = (long long)((i - (2 - (i & 1))) >> 1) +
+                        (long long)ni * (((j - (2 - (j & 1))) >> 1) + (long long)nj * ((k - (2 - (k & 1))) >> 1));
+    const long long nc = cb_count(n, col);
+    float* b = cb + cb_offset(n, col) + t;
+    for (int e = 0; e < 27; e++) b[e * nc] = S.full(i, j, k, e);
+}
+
+// One colour of the FP32 smoother from the colour blocks: the same products
+// summed in the same order as k_gs_colour3d (offset t, then its mirror).
+__global__ void k_gs_colour3d_cb(const float* __restrict__ blk, long long nc, int ni, int nj, int i0, int j0,
+                                 int k0, int n, int ld, const float* __restrict__ f, float* __restrict__ x) {
+    const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (t >= nc) return;
+    const int a = (int)(t % ni);
+    const long long r = t / ni;
+    const int b = (int)(r % nj), cz = (int)(r / nj);
+    const int i = i0 + 2 * a, j = j0 + 2 * b, k = k0 + 2 * cz;
+    const long long o = (long long)i + (long long)ld * (j + (long long)n * k);
+    const long long sy = ld, sz = (long long)ld * n;
+    float s = 0.f;
+#pragma unroll
+    for (int e = 0; e < 13; e++) {
+        const long long d = off_x(e) + sy * off_y(e) + sz * off_z(e);
+        s += blk[e * nc + t] * x[o + d];
+        s += blk[(26 - e) * nc + t] * x[o - d];
+    }
+    x[o] = (f[o] - s) / blk[13 * nc + t];
+}
+
 template <typename T>
 __global__ void k_residual3d(L3<T> L, const T* __restrict__ f, const T* __restrict__ x, T* __restrict__ r) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
@@ -51,36 +92,66 @@ __global__ void k_residual3d(L3<T> L, const T* __restrict__ f, const T* __restri
     r[o] = f[o] - (L.A[13 * L.pl + o] * x[o] + offdiag3(L, x, i, j, k));
 }
 
-// b_c(K) = sum over the 27 fine neighbours of 2K of P(f, K) r_f
+// b_c(K) = sum over the 27 fine neighbours f = 2K + d of P(f, K) r_f, in the
+// order of d.  For an interior coarse node every such f is an interior fine
+// node; its weight to K sits at the coarse node owning f (K - 1 in each
+// direction where d = -1), in the plane of f's parity mask m and of the
+// corner K - owner.  All of that is fixed by d, so the loop unrolls to plain
+// loads.
 template <typename T>
 __global__ void k_restrict3d(int nf, int ldf, const T* __restrict__ r, const T* __restrict__ P, int nc, int ldc,
                              long long plc, T* __restrict__ bc) {
     const int I = blockIdx.x * blockDim.x + threadIdx.x;
     const int J = blockIdx.y, K = blockIdx.z;
     if (I < 1 || J < 1 || K < 1 || I > nc - 2 || J > nc - 2 || K > nc - 2) return;
+    const long long oc = (long long)I + (long long)ldc * (J + (long long)nc * K);
+    const long long of = 2LL * I + (long long)ldf * (2 * J + (long long)nf * 2 * K);
     T s = 0;
+#pragma unroll
     for (int o = 0; o < 27; o++) {
-        const int fi = 2 * I + off_x(o), fj = 2 * J + off_y(o), fk = 2 * K + off_z(o);
-        const T w = pweight3<T>(P, ldc, nc, plc, nf, fi, fj, fk, I, J, K);
-        if (w != (T)0) s += w * r[(long long)fi + (long long)ldf * (fj + (long long)nf * fk)];
+        const int dx = off_x(o), dy = off_y(o), dz = off_z(o);
+        const int m = (dx != 0) | ((dy != 0) << 1) | ((dz != 0) << 2);
+        T w = (T)1;
+        if (m) {
+            const int sb = (dx < 0) | ((dy < 0) << 1) | ((dz < 0) << 2);
+            const long long own = oc - (dx < 0) - (long long)ldc * ((dy < 0) + (long long)nc * (dz < 0));
+            w = P[(long long)(kPBase(m) + compress3(sb, m)) * plc + own];
+        }
+        s += w * r[of + dx + (long long)ldf * (dy + (long long)nf * dz)];
     }
-    bc[(long long)I + (long long)ldc * (J + (long long)nc * K)] = s;
+    bc[oc] = s;
 }
 
-// x_f += P x_c
+// x_f += sum over s subset of m of P(f, (I,J,K) + s) x_c((I,J,K) + s) for the
+// eight fine points f = 2(I,J,K) + b (parity mask m = b) that coarse node
+// (I,J,K) owns: one thread per coarse node, the 26 weights of its cell read
+// once and contiguously across the warp.  Summation over s ascending, as the
+// weights' own numbering.
 template <typename T>
 __global__ void k_prolong3d(int nf, int ldf, T* __restrict__ x, const T* __restrict__ P, int nc, int ldc,
                             long long plc, const T* __restrict__ xc) {
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    const int j = blockIdx.y, k = blockIdx.z;
-    if (i < 1 || j < 1 || k < 1 || i > nf - 2 || j > nf - 2 || k > nf - 2) return;
-    T v = 0;
-    for (int s = 0; s < 8; s++) {
-        const int KI = (i >> 1) + (s & 1), KJ = (j >> 1) + ((s >> 1) & 1), KK = (k >> 1) + (s >> 2);
-        const T w = pweight3<T>(P, ldc, nc, plc, nf, i, j, k, KI, KJ, KK);
-        if (w != (T)0) v += w * xc[(long long)KI + (long long)ldc * (KJ + (long long)nc * KK)];
+    const int I = blockIdx.x * blockDim.x + threadIdx.x;
+    const int J = blockIdx.y, K = blockIdx.z;
+    if (I > nc - 2 || J > nc - 2 || K > nc - 2) return;
+    const long long oc = (long long)I + (long long)ldc * (J + (long long)nc * K);
+    const long long sy = ldc, sz = (long long)ldc * nc;
+    T c8[8];
+#pragma unroll
+    for (int q = 0; q < 8; q++) c8[q] = xc[oc + (q & 1) + sy * ((q >> 1) & 1) + sz * (q >> 2)];
+#pragma unroll
+    for (int b = 0; b < 8; b++) {
+        const int fi = 2 * I + (b & 1), fj = 2 * J + ((b >> 1) & 1), fk = 2 * K + (b >> 2);
+        if (fi < 1 || fj < 1 || fk < 1 || fi > nf - 2 || fj > nf - 2 || fk > nf - 2) continue;
+        T v = 0;
+        if (b == 0) {
+            v = c8[0];
+        } else {
+#pragma unroll
+            for (int q = 0; q < 8; q++)
+                if ((q & ~b) == 0) v += P[(long long)(kPBase(b) + compress3(q, b)) * plc + oc] * c8[q];
+        }
+        x[(long long)fi + (long long)ldf * (fj + (long long)nf * fk)] += v;
     }
-    x[(long long)i + (long long)ldf * (j + (long long)nf * k)] += v;
 }
 
 template <typename T>
@@ -101,7 +172,44 @@ const T* A_of(const Level& L) { return (const T*)(sizeof(T) == 4 ? (const void*)
 template <typename T>
 const T* P_of(const Level& L) { return (const T*)(sizeof(T) == 4 ? (const void*)L.P32 : (const void*)L.P64); }
 
+// one colour of the smoother on level l: colour blocks when the level has
+// them (FP32), otherwise the symmetric-half planes
+template <typename T>
+bmg_status colour_sweep(Ctx& c, int l, const L3<T>& v, const T* f, T* x, int col, int h) {
+    const Level& F = c.lev[l];
+    const double N = dofs3(c, l);
+    prof_begin(c, BMG_PROF_SMOOTH, l);
+    if constexpr (sizeof(T) == 4) {
+        if (F.cb) {
+            const int pi = col & 1, pj = (col >> 1) & 1, pk = col >> 2;
+            const long long nc = cb_count(F.n, col);
+            const unsigned blocks = (unsigned)((nc + 255) / 256);
+            k_gs_colour3d_cb<<<blocks, 256, 0, c.stream>>>(F.cb + cb_offset(F.n, col), nc, cb_side(F.n, pi),
+                                                           cb_side(F.n, pj), 2 - pi, 2 - pj, 2 - pk, F.n, F.ld, f, x);
+            c.launches++;
+            prof_end(c, BMG_PROF_SMOOTH, l, (27.0 + 3.0) * sizeof(T) * N / 8);
+            return BMG_OK;
+        }
+    }
+    k_gs_colour3d<T><<<g3(h, h, h), 64, 0, c.stream>>>(v, f, x, col & 1, (col >> 1) & 1, col >> 2);
+    c.launches++;
+    prof_end(c, BMG_PROF_SMOOTH, l, (c.ns + 3) * sizeof(T) * N / 8);
+    return BMG_OK;
+}
+
 }  // namespace
+
+bmg_status colour_blocks3d(Ctx& c) {
+    if (c.opts.precision != BMG_PREC_FP32 || c.dim != 3) return BMG_OK;
+    for (int l = 0; l + 1 < c.nlev; l++) {
+        const Level& L = c.lev[l];
+        if (!L.cb) continue;
+        k_cblocks3d<<<g3(L.n, L.n, L.n), 64, 0, c.stream>>>(Sten3<float>{L.A32, L.n, L.ld, L.plane}, L.cb);
+        c.launches++;
+    }
+    BMG_CUDA(cudaGetLastError());
+    return BMG_OK;
+}
 
 template <typename T>
 bmg_status vcycle3d_impl(Ctx& c, const T* b0, T* x0, T* xout) {
@@ -117,11 +225,7 @@ bmg_status vcycle3d_impl(Ctx& c, const T* b0, T* x0, T* xout) {
         BMG_CUDA(cudaMemsetAsync(xl(l), 0, sizeof(T) * F.plane, s));
         const int h = (F.n + 1) / 2;
         const double N = dofs3(c, l);
-        for (int col = 0; col < 8; col++) {
-            prof_begin(c, BMG_PROF_SMOOTH, l);
-            k_gs_colour3d<T><<<g3(h, h, h), 64, 0, s>>>(v, bl(l), xl(l), col & 1, (col >> 1) & 1, col >> 2);
-            prof_end(c, BMG_PROF_SMOOTH, l, (c.ns + 3) * sz * N / 8);
-        }
+        for (int col = 0; col < 8; col++) BMG_TRY(colour_sweep<T>(c, l, v, bl(l), xl(l), col, h));
         prof_begin(c, BMG_PROF_RESIDUAL, l);
         k_residual3d<T><<<g3(F.n, F.n, F.n), 64, 0, s>>>(v, bl(l), xl(l), (T*)F.r);
         prof_end(c, BMG_PROF_RESIDUAL, l, (c.ns + 3) * sz * N);
@@ -129,7 +233,7 @@ bmg_status vcycle3d_impl(Ctx& c, const T* b0, T* x0, T* xout) {
         k_restrict3d<T><<<g3(K.n, K.n, K.n), 64, 0, s>>>(F.n, F.ld, (const T*)F.r, P_of<T>(F), K.n, K.ld, K.plane,
                                                         (T*)K.b);
         prof_end(c, BMG_PROF_RESTRICT, l, (1.0 + c.np / 8.0 + 0.125) * sz * N);
-        c.launches += 10;
+        c.launches += 2;   // residual, restriction (the colours count themselves)
     }
     {
         const Level& C = c.lev[L - 1];
@@ -144,15 +248,12 @@ bmg_status vcycle3d_impl(Ctx& c, const T* b0, T* x0, T* xout) {
         L3<T> v{A_of<T>(F), F.n, F.ld, F.plane};
         const double N = dofs3(c, l);
         prof_begin(c, BMG_PROF_PROLONG, l);
-        k_prolong3d<T><<<g3(F.n, F.n, F.n), 64, 0, s>>>(F.n, F.ld, xl(l), P_of<T>(F), K.n, K.ld, K.plane, xl(l + 1));
+        k_prolong3d<T><<<g3(K.n - 1, K.n - 1, K.n - 1), 64, 0, s>>>(F.n, F.ld, xl(l), P_of<T>(F), K.n, K.ld,
+                                                                     K.plane, xl(l + 1));
         prof_end(c, BMG_PROF_PROLONG, l, (2.0 + c.np / 8.0 + 0.125) * sz * N);
         const int h = (F.n + 1) / 2;
-        for (int col = 7; col >= 0; col--) {
-            prof_begin(c, BMG_PROF_SMOOTH, l);
-            k_gs_colour3d<T><<<g3(h, h, h), 64, 0, s>>>(v, bl(l), xl(l), col & 1, (col >> 1) & 1, col >> 2);
-            prof_end(c, BMG_PROF_SMOOTH, l, (c.ns + 3) * sz * N / 8);
-        }
-        c.launches += 9;
+        for (int col = 7; col >= 0; col--) BMG_TRY(colour_sweep<T>(c, l, v, bl(l), xl(l), col, h));
+        c.launches += 1;   // prolongation
     }
     (void)xout;
     BMG_CUDA(cudaGetLastError());
