@@ -99,11 +99,9 @@ __global__ void k_residual3d(L3<T> L, const T* __restrict__ f, const T* __restri
 // corner K - owner.  All of that is fixed by d, so the loop unrolls to plain
 // loads.
 template <typename T>
-__global__ void k_restrict3d(int nf, int ldf, const T* __restrict__ r, const T* __restrict__ P, int nc, int ldc,
-                             long long plc, T* __restrict__ bc) {
-    const int I = blockIdx.x * blockDim.x + threadIdx.x;
-    const int J = blockIdx.y, K = blockIdx.z;
-    if (I < 1 || J < 1 || K < 1 || I > nc - 2 || J > nc - 2 || K > nc - 2) return;
+__device__ __forceinline__ void restrict_node3d(int nf, int ldf, const T* __restrict__ r, const T* __restrict__ P,
+                                                int nc, int ldc, long long plc, T* __restrict__ bc, int I, int J,
+                                                int K) {
     const long long oc = (long long)I + (long long)ldc * (J + (long long)nc * K);
     const long long of = 2LL * I + (long long)ldf * (2 * J + (long long)nf * 2 * K);
     T s = 0;
@@ -122,17 +120,23 @@ __global__ void k_restrict3d(int nf, int ldf, const T* __restrict__ r, const T* 
     bc[oc] = s;
 }
 
+template <typename T>
+__global__ void k_restrict3d(int nf, int ldf, const T* __restrict__ r, const T* __restrict__ P, int nc, int ldc,
+                             long long plc, T* __restrict__ bc) {
+    const int I = blockIdx.x * blockDim.x + threadIdx.x;
+    const int J = blockIdx.y, K = blockIdx.z;
+    if (I < 1 || J < 1 || K < 1 || I > nc - 2 || J > nc - 2 || K > nc - 2) return;
+    restrict_node3d<T>(nf, ldf, r, P, nc, ldc, plc, bc, I, J, K);
+}
+
 // x_f += sum over s subset of m of P(f, (I,J,K) + s) x_c((I,J,K) + s) for the
 // eight fine points f = 2(I,J,K) + b (parity mask m = b) that coarse node
 // (I,J,K) owns: one thread per coarse node, the 26 weights of its cell read
 // once and contiguously across the warp.  Summation over s ascending, as the
 // weights' own numbering.
 template <typename T>
-__global__ void k_prolong3d(int nf, int ldf, T* __restrict__ x, const T* __restrict__ P, int nc, int ldc,
-                            long long plc, const T* __restrict__ xc) {
-    const int I = blockIdx.x * blockDim.x + threadIdx.x;
-    const int J = blockIdx.y, K = blockIdx.z;
-    if (I > nc - 2 || J > nc - 2 || K > nc - 2) return;
+__device__ __forceinline__ void prolong_node3d(int nf, int ldf, T* __restrict__ x, const T* __restrict__ P, int nc,
+                                               int ldc, long long plc, const T* __restrict__ xc, int I, int J, int K) {
     const long long oc = (long long)I + (long long)ldc * (J + (long long)nc * K);
     const long long sy = ldc, sz = (long long)ldc * nc;
     T c8[8];
@@ -155,12 +159,113 @@ __global__ void k_prolong3d(int nf, int ldf, T* __restrict__ x, const T* __restr
 }
 
 template <typename T>
+__global__ void k_prolong3d(int nf, int ldf, T* __restrict__ x, const T* __restrict__ P, int nc, int ldc,
+                            long long plc, const T* __restrict__ xc) {
+    const int I = blockIdx.x * blockDim.x + threadIdx.x;
+    const int J = blockIdx.y, K = blockIdx.z;
+    if (I > nc - 2 || J > nc - 2 || K > nc - 2) return;
+    prolong_node3d<T>(nf, ldf, x, P, nc, ldc, plc, xc, I, J, K);
+}
+
+template <typename T>
 __global__ void k_coarsest3d(L3<T> L, const double* __restrict__ A64, const T* __restrict__ b, T* __restrict__ x) {
     const long long o = L.idx(1, 1, 1);
     x[o] = (T)((double)b[o] / A64[13 * L.pl + o]);
 }
 
 inline dim3 g3(int ni, int nj, int nk) { return dim3(cdiv(ni, 64), nj, nk); }
+
+// ---------------------------------------------------------------- tail
+// The coarse end of the 3-D V-cycle (levels with n <= kTail3MaxN down to the
+// 3^3 grid and back) in one launch of one CTA: the same per-node steps as the
+// kernels above, each phase a block-strided loop followed by a block barrier,
+// on the levels' arrays in global memory (a few hundred KB, L2-resident).
+constexpr int kTail3Threads = 1024;
+constexpr int kTail3MaxN = 17;   // first tail level: n <= 17
+
+template <typename T>
+struct Tail3Level {
+    L3<T> A;
+    const T* P;        // interpolation from the next level (its grid: ldc, plane plc)
+    int ldc;
+    long long plc;
+    const T* b;
+    T* x;
+    T* r;
+};
+
+template <typename T>
+struct Tail3Args {
+    int nlev;
+    Tail3Level<T> lv[kMaxLevels];
+    const double* a64c;    // FP64 centre entry of the coarsest operator at (1,1,1)
+};
+
+template <typename T>
+__global__ void __launch_bounds__(kTail3Threads) k_vtail3d(Tail3Args<T> a) {
+    const int tid = threadIdx.x, nth = blockDim.x;
+    const int L = a.nlev;
+    auto colour = [&](const Tail3Level<T>& v, int col) {
+        const int n = v.A.n;
+        const int pi = col & 1, pj = (col >> 1) & 1, pk = col >> 2;
+        const int ni = cb_side(n, pi), nj = cb_side(n, pj), nk = cb_side(n, pk);
+        for (int t = tid; t < ni * nj * nk; t += nth) {
+            const int i = 2 - pi + 2 * (t % ni), j = 2 - pj + 2 * ((t / ni) % nj), k = 2 - pk + 2 * (t / (ni * nj));
+            const long long o = v.A.idx(i, j, k);
+            v.x[o] = (v.b[o] - offdiag3(v.A, v.x, i, j, k)) / v.A.A[13 * v.A.pl + o];
+        }
+    };
+    for (int l = 0; l + 1 < L; l++) {
+        const Tail3Level<T>& v = a.lv[l];
+        const Tail3Level<T>& w = a.lv[l + 1];
+        const int n = v.A.n, m = n - 2;
+        for (long long q = tid; q < (long long)v.A.ld * n * n; q += nth) v.x[q] = (T)0;
+        __syncthreads();
+        for (int col = 0; col < 8; col++) {
+            colour(v, col);
+            __syncthreads();
+        }
+        for (int q = tid; q < m * m * m; q += nth) {
+            const int i = 1 + q % m, j = 1 + (q / m) % m, k = 1 + q / (m * m);
+            const long long o = v.A.idx(i, j, k);
+            v.r[o] = v.b[o] - (v.A.A[13 * v.A.pl + o] * v.x[o] + offdiag3(v.A, v.x, i, j, k));
+        }
+        __syncthreads();
+        const int nc = w.A.n, mc = nc - 2;
+        for (int q = tid; q < mc * mc * mc; q += nth) {
+            const int I = 1 + q % mc, J = 1 + (q / mc) % mc, K = 1 + q / (mc * mc);
+            restrict_node3d<T>(n, v.A.ld, v.r, v.P, nc, v.ldc, v.plc, (T*)w.b, I, J, K);
+        }
+        __syncthreads();
+    }
+    {   // coarsest: one unknown, exact in FP64; the rest of its iterate is zero
+        const Tail3Level<T>& v = a.lv[L - 1];
+        const int n = v.A.n;
+        for (long long q = tid; q < (long long)v.A.ld * n * n; q += nth) v.x[q] = (T)0;
+        __syncthreads();
+        if (tid == 0) {
+            const long long o = v.A.idx(1, 1, 1);
+            v.x[o] = (T)((double)v.b[o] / *a.a64c);
+        }
+        __syncthreads();
+    }
+    for (int l = L - 2; l >= 0; l--) {
+        const Tail3Level<T>& v = a.lv[l];
+        const Tail3Level<T>& w = a.lv[l + 1];
+        const int n = v.A.n, nc = w.A.n, mc = nc - 1;
+        for (int q = tid; q < mc * mc * mc; q += nth) {
+            const int I = q % mc, J = (q / mc) % mc, K = q / (mc * mc);
+            prolong_node3d<T>(n, v.A.ld, v.x, v.P, nc, v.ldc, v.plc, w.x, I, J, K);
+        }
+        __syncthreads();
+        for (int col = 7; col >= 0; col--) {
+            colour(v, col);
+            __syncthreads();
+        }
+    }
+}
+
+
 
 inline double dofs3(const Ctx& c, int l) {
     const double m = c.lev[l].n - 2;
@@ -218,7 +323,10 @@ bmg_status vcycle3d_impl(Ctx& c, const T* b0, T* x0, T* xout) {
     const double sz = sizeof(T);
     auto bl = [&](int l) { return l == 0 ? b0 : (const T*)c.lev[l].b; };
     auto xl = [&](int l) { return l == 0 ? x0 : (T*)c.lev[l].x; };
-    for (int l = 0; l < L - 1; l++) {
+    // levels t .. L-1 (n <= kTail3MaxN) run in the single-CTA tail
+    int t = L - 1;
+    while (t > 0 && c.lev[t - 1].n <= kTail3MaxN) t--;
+    for (int l = 0; l < t; l++) {
         const Level& F = c.lev[l];
         const Level& K = c.lev[l + 1];
         L3<T> v{A_of<T>(F), F.n, F.ld, F.plane};
@@ -236,13 +344,26 @@ bmg_status vcycle3d_impl(Ctx& c, const T* b0, T* x0, T* xout) {
         c.launches += 2;   // residual, restriction (the colours count themselves)
     }
     {
+        Tail3Args<T> a{};
+        a.nlev = L - t;
+        for (int q = 0; q < a.nlev; q++) {
+            const int l = t + q;
+            const Level& F = c.lev[l];
+            Tail3Level<T>& g = a.lv[q];
+            g.A = L3<T>{A_of<T>(F), F.n, F.ld, F.plane};
+            g.P = l + 1 < L ? P_of<T>(F) : nullptr;
+            g.ldc = l + 1 < L ? c.lev[l + 1].ld : 0;
+            g.plc = l + 1 < L ? c.lev[l + 1].plane : 0;
+            g.b = bl(l);
+            g.x = xl(l);
+            g.r = (T*)F.r;
+        }
         const Level& C = c.lev[L - 1];
-        L3<T> v{A_of<T>(C), C.n, C.ld, C.plane};
-        BMG_CUDA(cudaMemsetAsync(xl(L - 1), 0, sizeof(T) * C.plane, s));
-        k_coarsest3d<T><<<1, 1, 0, s>>>(v, C.A64, bl(L - 1), xl(L - 1));
+        a.a64c = C.A64 + 13 * C.plane + (long long)C.ld * (1 + (long long)C.n) + 1;
+        k_vtail3d<T><<<1, kTail3Threads, 0, s>>>(a);
         c.launches++;
     }
-    for (int l = L - 2; l >= 0; l--) {
+    for (int l = t - 1; l >= 0; l--) {
         const Level& F = c.lev[l];
         const Level& K = c.lev[l + 1];
         L3<T> v{A_of<T>(F), F.n, F.ld, F.plane};
