@@ -402,7 +402,7 @@ def run_single(args, dim, n, problem, name):
     f = torch.as_tensor(problem.rhs, device="cuda")
     res = {}
     for prec, outer in (("fp32", "refine"), ("fp32", "flexible"), ("fp64", "cg")):
-        s = binding.Solver(dim, n, precision=prec, outer=outer)
+        s = binding.Solver(dim, n, precision=prec, outer=outer, graphs=not args.no_graphs)
         t0 = time.perf_counter()
         s.assemble(torch.as_tensor(problem.coords), torch.as_tensor(problem.kappa)).setup()
         torch.cuda.synchronize()
