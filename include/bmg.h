@@ -128,6 +128,17 @@ bmg_status bmg_attach(bmg_ctx* ctx, void* workspace, size_t bytes, void* stream)
    z plane]); kappa: device, (n-1)^d doubles.  Errors: BMG_ERR_MAP_FOLDED. */
 bmg_status bmg_assemble(bmg_ctx* ctx, const double* coords, const double* kappa);
 
+/* As bmg_assemble with an SPD diffusion tensor per cell instead of a scalar
+   (the general coefficient of Sec. 2, Eq. pde): the effective coefficient
+   at each Gauss point is det J J^-1 D J^-T (Sec. 2.1).  D: device, the
+   upper triangle of each cell's tensor as planes of (n-1)^d doubles,
+   D11, D12, D22 in 2-D and D11, D12, D13, D22, D23, D33 in 3-D (cells in
+   the order of kappa).  Errors: BMG_ERR_MAP_FOLDED.  An indefinite D is not
+   detected here; it shows up in bmg_setup or bmg_solve.  bmg_adjoint_grad
+   (a gradient with respect to a scalar kappa) returns BMG_ERR_STATE on such
+   a context. */
+bmg_status bmg_assemble_tensor(bmg_ctx* ctx, const double* coords, const double* D);
+
 /* Sets the finest operator directly, the alternative Sec. 2.2 allows to
    assembling it from the coefficient.  stencil: device, n^d rows of 3^d
    doubles, entry (dx+1)+3(dy+1)[+9(dz+1)] = A[node, node+offset]; the

@@ -11,6 +11,8 @@ Array conventions (numpy, C order, so the last axis is the fastest, i):
   grid vectors   shape (n, n) or (n, n, n)          [j, i] / [k, j, i]
   coords         shape (d, n, n[, n])               physical component first
   kappa          shape (n-1, n-1[, n-1])            one value per cell
+  tensor         shape (3 | 6, n-1, n-1[, n-1])     upper triangle per cell:
+                 D11, D12, D22 (2-D); D11, D12, D13, D22, D23, D33 (3-D)
   full stencil   shape (n, n[, n], 3**d)            slot (dx+1)+3(dy+1)+9(dz+1)
   interpolation  shape (n, n[, n], 2**d)            weight of a fine node to the
                  coarse node (i>>1 + sx, j>>1 + sy, k>>1 + sz), s = sx+2sy+4sz
@@ -78,6 +80,8 @@ def _load():
             ("or_vcycle", [P, P, P], None),
             ("or_pcg", [P, P, P, D, I, I, P, P, P], I),
             ("or_adjoint_grad", [I, I, P, P, P, P], I),
+            ("or_element_tensor", [I, P, P, P], I),
+            ("or_assemble_tensor", [I, I, P, P, P], I),
         ]:
             f = getattr(lib, name)
             f.argtypes = args
@@ -115,6 +119,31 @@ def element(xe, kappa: float) -> np.ndarray:
     K = np.zeros((1 << d, 1 << d))
     _check(_load().or_element(d, _ptr(xe), float(kappa), _ptr(K)))
     return K
+
+
+def element_tensor(xe, D) -> np.ndarray:
+    """Q1 element stiffness with a constant SPD tensor D (d x d) on one cell:
+    the effective coefficient det J J^-1 D J^-T (Sec. 2.1) at each Gauss
+    point."""
+    xe = _f64(xe)
+    d = xe.shape[0]
+    Dm = np.zeros((3, 3))
+    Dm[:d, :d] = np.asarray(D, dtype=np.float64)
+    K = np.zeros((1 << d, 1 << d))
+    _check(_load().or_element_tensor(d, _ptr(xe), _ptr(Dm), _ptr(K)))
+    return K
+
+
+def assemble_tensor(coords, D) -> np.ndarray:
+    """Full stencils with an SPD diffusion tensor per cell (Sec. 2, Eq. pde),
+    D given as its upper-triangle planes (see the module docstring)."""
+    coords = _f64(coords)
+    D = _f64(D)
+    d, n = _dim_n(coords.shape[1:])
+    assert D.shape == ((3 if d == 2 else 6),) + (n - 1,) * d, D.shape
+    A = np.zeros(coords.shape[1:] + (3 ** d,))
+    _check(_load().or_assemble_tensor(d, n, _ptr(coords), _ptr(D), _ptr(A)))
+    return A
 
 
 def metric(xe, kappa: float, h: float):

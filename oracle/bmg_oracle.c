@@ -266,6 +266,102 @@ int or_assemble(int dim, int n, const double* coords, const double* kappa, doubl
     return OR_OK;
 }
 
+/* ------------------------------------------------------------------ */
+/* Tensor coefficient (Sec. 2, Eq. pde; Sec. 2.1): an SPD diffusion     */
+/* tensor D per cell, effective coefficient det J J^-1 D J^-T            */
+/* ------------------------------------------------------------------ */
+
+/* Upper triangle of cell e's tensor from planes of ne values each:
+   2-D: D11, D12, D22; 3-D: D11, D12, D13, D22, D23, D33. */
+static void cell_tensor(int dim, long ne, long e, const double* Dt, double D[3][3]) {
+    for (int r = 0; r < 3; r++)
+        for (int c = 0; c < 3; c++) D[r][c] = 0.0;
+    if (dim == 2) {
+        D[0][0] = Dt[0 * ne + e];
+        D[0][1] = D[1][0] = Dt[1 * ne + e];
+        D[1][1] = Dt[2 * ne + e];
+        return;
+    }
+    D[0][0] = Dt[0 * ne + e];
+    D[0][1] = D[1][0] = Dt[1 * ne + e];
+    D[0][2] = D[2][0] = Dt[2 * ne + e];
+    D[1][1] = Dt[3 * ne + e];
+    D[1][2] = D[2][1] = Dt[4 * ne + e];
+    D[2][2] = Dt[5 * ne + e];
+}
+
+/* G = det J * J^-1 D J^-T at quadrature point q; returns det J. */
+static double metric_tensor(int dim, const double* xe, double D[3][3], int q, double G[3][3]) {
+    double xi[3], J[3][3], Ji[3][3];
+    quad_point(dim, q, xi);
+    double det = jacobian(dim, xe, xi, J);
+    if (!(det > 0.0)) return det;
+    inverse(dim, J, det, Ji);
+    for (int m = 0; m < dim; m++)
+        for (int p = 0; p < dim; p++) {
+            double s = 0.0;
+            for (int r = 0; r < dim; r++)
+                for (int c = 0; c < dim; c++) s += Ji[m][r] * D[r][c] * Ji[p][c];
+            G[m][p] = det * s;
+        }
+    return det;
+}
+
+/* Element stiffness with a constant tensor D (row-major 3x3). */
+int or_element_tensor(int dim, const double* xe, const double* Dm, double* K) {
+    if (dim != 2 && dim != 3) return OR_ERR_ARG;
+    int na = 1 << dim, nq = 1 << dim;
+    double w = 1.0 / (double)nq, D[3][3];
+    for (int r = 0; r < 3; r++)
+        for (int c = 0; c < 3; c++) D[r][c] = Dm[r * 3 + c];
+    for (int t = 0; t < na * na; t++) K[t] = 0.0;
+    for (int q = 0; q < nq; q++) {
+        double G[3][3], xi[3];
+        double det = metric_tensor(dim, xe, D, q, G);
+        if (!(det > 0.0)) return OR_ERR_FOLDED;
+        quad_point(dim, q, xi);
+        double gr[8][3];
+        for (int a = 0; a < na; a++) basis(dim, a, xi, gr[a]);
+        for (int a = 0; a < na; a++)
+            for (int b = 0; b < na; b++) {
+                double s = 0.0;
+                for (int m = 0; m < dim; m++)
+                    for (int p = 0; p < dim; p++) s += gr[a][m] * G[m][p] * gr[b][p];
+                K[a * na + b] += w * s;
+            }
+    }
+    return OR_OK;
+}
+
+/* Assembly with a tensor per cell (planes as in cell_tensor), otherwise as
+   or_assemble. */
+int or_assemble_tensor(int dim, int n, const double* coords, const double* Dt, double* A) {
+    if ((dim != 2 && dim != 3) || n < 3) return OR_ERR_ARG;
+    int S = (int)pw_int(3, dim), na = 1 << dim;
+    long nn = pw_int(n, dim), ne = pw_int(n - 1, dim);
+    memset(A, 0, sizeof(double) * nn * S);
+    for (long e = 0; e < ne; e++) {
+        int cc[3];
+        double xe[24], K[64], D[3][3];
+        cell_coords(dim, n, e, cc);
+        gather_cell(dim, n, coords, cc, xe);
+        cell_tensor(dim, ne, e, Dt, D);
+        int st = or_element_tensor(dim, xe, &D[0][0], K);
+        if (st) return st;
+        for (int a = 0; a < na; a++) {
+            int ca[3] = {cc[0] + (a & 1), cc[1] + ((a >> 1) & 1), cc[2] + ((a >> 2) & 1)};
+            if (!is_interior(dim, n, ca)) continue;
+            for (int b = 0; b < na; b++) {
+                int cb[3] = {cc[0] + (b & 1), cc[1] + ((b >> 1) & 1), cc[2] + ((b >> 2) & 1)};
+                if (!is_interior(dim, n, cb)) continue;
+                int d[3] = {cb[0] - ca[0], cb[1] - ca[1], cb[2] - ca[2]};
+                A[node_id(dim, n, ca) * S + slot_of(dim, d)] += K[a * na + b];
+            }
+        }
+    }
+    return OR_OK;
+}
+
 /* Physical coordinates of every quadrature point: xq[(e*2^d + q)*dim + r] */
 int or_gauss_points(int dim, int n, const double* coords, double* xq) {
     if ((dim != 2 && dim != 3) || n < 2) return OR_ERR_ARG;

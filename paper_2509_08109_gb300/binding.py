@@ -92,6 +92,7 @@ def load() -> ctypes.CDLL:
         "bmg_destroy": ([P], None),
         "bmg_status_str": ([I], ctypes.c_char_p),
         "bmg_assemble_noalloc": ([I, I, P, P, P, P], I),
+        "bmg_assemble_tensor": ([P, P, P], I),
     }
     for name, (args, res) in sigs.items():
         f = getattr(lib, name)
@@ -107,7 +108,7 @@ def exported_symbols() -> list:
             "bmg_levels",
             "bmg_level_n", "bmg_get_stencil", "bmg_get_interp", "bmg_launch_count", "bmg_get_tiles",
             "bmg_set_tiles", "bmg_autotune", "bmg_profile",
-            "bmg_profile_read", "bmg_destroy", "bmg_status_str", "bmg_assemble_noalloc"]
+            "bmg_profile_read", "bmg_destroy", "bmg_status_str", "bmg_assemble_noalloc", "bmg_assemble_tensor"]
 
 
 def _check(code: int, where: str):
@@ -234,6 +235,18 @@ class Solver:
         assert kappa.shape == (self.n - 1,) * self.dim, kappa.shape
         with torch.cuda.device(self.device):
             _check(load().bmg_assemble(self._h, _ptr(coords), _ptr(kappa)), "bmg_assemble")
+        self._coords = coords
+        return self
+
+    def assemble_tensor(self, coords, D):
+        """bmg_assemble_tensor: D of shape (3, n-1, n-1) in 2-D (D11, D12,
+        D22) or (6, n-1, n-1, n-1) in 3-D (D11, D12, D13, D22, D23, D33)."""
+        coords = self._dev(torch.as_tensor(coords))
+        D = self._dev(torch.as_tensor(D))
+        assert coords.shape == (self.dim,) + self.grid_shape, coords.shape
+        assert D.shape == ((3 if self.dim == 2 else 6),) + (self.n - 1,) * self.dim, D.shape
+        with torch.cuda.device(self.device):
+            _check(load().bmg_assemble_tensor(self._h, _ptr(coords), _ptr(D)), "bmg_assemble_tensor")
         self._coords = coords
         return self
 

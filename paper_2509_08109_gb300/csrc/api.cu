@@ -431,6 +431,26 @@ bmg_status bmg_assemble(bmg_ctx* ctx, const double* coords, const double* kappa)
     KState h;
     BMG_TRY(read_state(c, h));
     c.have_setup = false;
+    c.op_tensor = false;
+    if (h.err) {
+        c.have_op = false;
+        return (bmg_status)h.err;
+    }
+    c.have_op = true;
+    return BMG_OK;
+}
+
+bmg_status bmg_assemble_tensor(bmg_ctx* ctx, const double* coords, const double* D) {
+    BMG_TRY(check_ready(ctx));
+    if (!coords || !D) return BMG_ERR_ARG;
+    Ctx& c = ctx->c;
+    if (!is_device_ptr(coords) || !is_device_ptr(D)) return BMG_ERR_ARG;
+    BMG_TRY(reset_state(c));
+    BMG_TRY(c.dim == 2 ? assemble_tensor2d(c, coords, D) : assemble_tensor3d(c, coords, D));
+    KState h;
+    BMG_TRY(read_state(c, h));
+    c.have_setup = false;
+    c.op_tensor = true;
     if (h.err) {
         c.have_op = false;
         return (bmg_status)h.err;
@@ -500,7 +520,7 @@ bmg_status bmg_adjoint_grad(bmg_ctx* ctx, const double* coords, const double* u,
     BMG_TRY(check_ready(ctx));
     if (!coords || !u || !dLdu || !lambda || !dLdkappa) return BMG_ERR_ARG;
     Ctx& c = ctx->c;
-    if (!c.have_setup) return BMG_ERR_STATE;
+    if (!c.have_setup || c.op_tensor) return BMG_ERR_STATE;
     if (!is_device_ptr(coords) || !is_device_ptr(u) || !is_device_ptr(dLdu) || !is_device_ptr(lambda) ||
         !is_device_ptr(dLdkappa))
         return BMG_ERR_ARG;

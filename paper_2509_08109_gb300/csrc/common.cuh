@@ -90,6 +90,7 @@ struct Ctx {
     cudaStream_t stream = nullptr;
     int device = -1;
     bool attached = false, have_op = false, have_setup = false;
+    bool op_tensor = false;       // operator assembled from a diffusion tensor (no dL/dkappa)
     // finest-level FP64 Krylov vectors (internal padded layout)
     double *bvec = nullptr, *x = nullptr, *r = nullptr, *z[2] = {nullptr, nullptr};
     double *p = nullptr, *q = nullptr;
@@ -256,6 +257,7 @@ __device__ __forceinline__ bool grid_sum(double v, double* partials, unsigned in
 // ------------------------------------------------------------------ host launchers
 // setup2d.cu
 bmg_status assemble2d(Ctx& c, const double* coords, const double* kappa);
+bmg_status assemble_tensor2d(Ctx& c, const double* coords, const double* D);
 bmg_status set_stencil2d(Ctx& c, const double* full);
 bmg_status setup_level2d(Ctx& c, int l);
 bmg_status export_stencil2d(Ctx& c, int l, double* out);
@@ -263,6 +265,7 @@ bmg_status export_interp2d(Ctx& c, int l, double* out);
 bmg_status adjoint_cells2d(Ctx& c, const double* coords, const double* u, const double* lam, double* g);
 // setup3d.cu
 bmg_status assemble3d(Ctx& c, const double* coords, const double* kappa);
+bmg_status assemble_tensor3d(Ctx& c, const double* coords, const double* D);
 bmg_status set_stencil3d(Ctx& c, const double* full);
 bmg_status setup_level3d(Ctx& c, int l);
 bmg_status export_stencil3d(Ctx& c, int l, double* out);

@@ -10,12 +10,40 @@ namespace {
 constexpr double kG0 = 0.21132486540518711775;
 constexpr double kG1 = 0.78867513459481288225;
 
+// Coefficient of a cell, as the metric it induces from adj(J) = det J J^-1.
+// Scalar kappa: G = (kappa / det J) adj adj^T.  SPD tensor D (Sec. 2, Eq.
+// pde): G = (1 / det J) adj D adj^T, i.e. det J J^-1 D J^-T (Sec. 2.1).
+struct Scalar2 {
+    double kap;
+    __device__ __forceinline__ void metric(double J11, double J12, double J21, double J22, double det, double& G11,
+                                           double& G12, double& G22) const {
+        const double s = 0.25 * kap / det;
+        G11 = s * (J22 * J22 + J12 * J12);
+        G12 = -s * (J22 * J21 + J12 * J11);
+        G22 = s * (J21 * J21 + J11 * J11);
+    }
+};
+struct Tensor2 {
+    double d11, d12, d22;
+    __device__ __forceinline__ void metric(double J11, double J12, double J21, double J22, double det, double& G11,
+                                           double& G12, double& G22) const {
+        const double a11 = J22, a12 = -J12, a21 = -J21, a22 = J11;   // adj(J)
+        const double t11 = a11 * d11 + a12 * d12, t12 = a11 * d12 + a12 * d22;
+        const double t21 = a21 * d11 + a22 * d12, t22 = a21 * d12 + a22 * d22;
+        const double s = 0.25 / det;
+        G11 = s * (t11 * a11 + t12 * a12);
+        G12 = s * (t11 * a21 + t12 * a22);
+        G22 = s * (t21 * a21 + t22 * a22);
+    }
+};
+
 // Q1 element matrix of cell (ci,cj): K[a][b] = sum_q 1/4 grad(phi_a)^T G grad(phi_b),
-// G = kappa det J J^-1 J^-T = (kappa / det J) adj(J) adj(J)^T, J = dx/dxi on the
-// reference cell (isoparametric map of the four nodal coordinates).
-// Corner a = ax + 2 ay sits at node (ci+ax, cj+ay).  Returns false if det J <= 0.
-__device__ bool element2d(const double* __restrict__ X, const double* __restrict__ Y, int n,
-                          int ci, int cj, double kap, double K[4][4]) {
+// G from the cell's coefficient (above), J = dx/dxi on the reference cell
+// (isoparametric map of the four nodal coordinates).  Corner a = ax + 2 ay
+// sits at node (ci+ax, cj+ay).  Returns false if det J <= 0.
+template <class C>
+__device__ bool element2d(const double* __restrict__ X, const double* __restrict__ Y, int n, int ci, int cj,
+                          const C& coef, double K[4][4]) {
     double xa[4], ya[4];
 #pragma unroll
     for (int a = 0; a < 4; a++) {
@@ -43,10 +71,8 @@ __device__ bool element2d(const double* __restrict__ X, const double* __restrict
         }
         const double det = J11 * J22 - J12 * J21;
         if (!(det > 0.0)) ok = false;
-        const double s = 0.25 * kap / det;
-        const double G11 = s * (J22 * J22 + J12 * J12);
-        const double G12 = -s * (J22 * J21 + J12 * J11);
-        const double G22 = s * (J21 * J21 + J11 * J11);
+        double G11, G12, G22;
+        coef.metric(J11, J12, J21, J22, det, G11, G12, G22);
 #pragma unroll
         for (int a = 0; a < 4; a++) {
             const double ga = G11 * dxi[a] + G12 * det_[a];
@@ -60,8 +86,19 @@ __device__ bool element2d(const double* __restrict__ X, const double* __restrict
 
 // Gather assembly: one thread per node sums the element matrices of its
 // four cells (no atomics).  Couplings to boundary nodes are dropped.
+// coefficient of cell e: kappa[e], or the tensor planes D11, D12, D22 (ne cells each)
+template <bool TENSOR>
+__device__ __forceinline__ auto cell_coef2(const double* __restrict__ c, long long ne, long long e) {
+    if constexpr (TENSOR)
+        return Tensor2{c[e], c[ne + e], c[2 * ne + e]};
+    else
+        return Scalar2{c[e]};
+}
+
+template <bool TENSOR>
 __global__ void k_assemble2d(int n, int ld, long long pl, const double* __restrict__ coords,
                              const double* __restrict__ kappa, double* __restrict__ A, KState* st) {
+    const long long ne = (long long)(n - 1) * (n - 1);
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     const int j = blockIdx.y;
     if (i >= n) return;
@@ -73,22 +110,22 @@ __global__ void k_assemble2d(int n, int ld, long long pl, const double* __restri
         double K[4][4];
         bool ok = true;
         // cell (i-1,j-1): node is corner 3
-        ok &= element2d(X, Y, n, i - 1, j - 1, kappa[(long long)(j - 1) * (n - 1) + (i - 1)], K);
+        ok &= element2d(X, Y, n, i - 1, j - 1, cell_coef2<TENSOR>(kappa, ne, (long long)(j - 1) * (n - 1) + (i - 1)), K);
         C += K[3][3];
         if (i - 1 >= 1) W += K[3][2];
         if (j - 1 >= 1) S += K[3][1];
         if (i - 1 >= 1 && j - 1 >= 1) SW += K[3][0];
         // cell (i,j-1): node is corner 2
-        ok &= element2d(X, Y, n, i, j - 1, kappa[(long long)(j - 1) * (n - 1) + i], K);
+        ok &= element2d(X, Y, n, i, j - 1, cell_coef2<TENSOR>(kappa, ne, (long long)(j - 1) * (n - 1) + i), K);
         C += K[2][2];
         if (j - 1 >= 1) S += K[2][0];
         // cell (i-1,j): node is corner 1
-        ok &= element2d(X, Y, n, i - 1, j, kappa[(long long)j * (n - 1) + (i - 1)], K);
+        ok &= element2d(X, Y, n, i - 1, j, cell_coef2<TENSOR>(kappa, ne, (long long)j * (n - 1) + (i - 1)), K);
         C += K[1][1];
         if (i - 1 >= 1) W += K[1][0];
         if (i - 1 >= 1 && j + 1 <= n - 2) NW += K[1][2];
         // cell (i,j): node is corner 0
-        ok &= element2d(X, Y, n, i, j, kappa[(long long)j * (n - 1) + i], K);
+        ok &= element2d(X, Y, n, i, j, cell_coef2<TENSOR>(kappa, ne, (long long)j * (n - 1) + i), K);
         C += K[0][0];
         if (!ok) set_err(st, BMG_ERR_MAP_FOLDED);
     }
@@ -291,7 +328,7 @@ __global__ void k_adjoint_cells2d(int n, const double* __restrict__ coords, cons
     const int cj = blockIdx.y;
     if (ci >= n - 1) return;
     double K[4][4];
-    if (!element2d(coords, coords + (long long)n * n, n, ci, cj, 1.0, K)) set_err(st, BMG_ERR_MAP_FOLDED);
+    if (!element2d(coords, coords + (long long)n * n, n, ci, cj, Scalar2{1.0}, K)) set_err(st, BMG_ERR_MAP_FOLDED);
     double ue[4], le[4];
 #pragma unroll
     for (int a = 0; a < 4; a++) {
@@ -318,7 +355,7 @@ inline dim3 grid_rows(int ni, int nj) { return dim3(cdiv(ni, 128), nj); }
 
 bmg_status assemble2d(Ctx& c, const double* coords, const double* kappa) {
     Level& L = c.lev[0];
-    k_assemble2d<<<grid_rows(L.n, L.n), 128, 0, c.stream>>>(L.n, L.ld, L.plane, coords, kappa, L.A64, c.st);
+    k_assemble2d<false><<<grid_rows(L.n, L.n), 128, 0, c.stream>>>(L.n, L.ld, L.plane, coords, kappa, L.A64, c.st);
     c.launches++;
     BMG_CUDA(cudaGetLastError());
     return BMG_OK;
@@ -328,9 +365,17 @@ bmg_status assemble2d(Ctx& c, const double* coords, const double* kappa) {
 // storage: half planes A (row length ld, plane stride pl) and error word st.
 bmg_status assemble_export2d(int n, int ld, long long pl, const double* coords, const double* kappa, double* A,
                              KState* st, double* out, cudaStream_t s) {
-    k_assemble2d<<<grid_rows(n, n), 128, 0, s>>>(n, ld, pl, coords, kappa, A, st);
+    k_assemble2d<false><<<grid_rows(n, n), 128, 0, s>>>(n, ld, pl, coords, kappa, A, st);
     BMG_CUDA(cudaGetLastError());
     k_export_stencil2d<<<grid_rows(n, n), 128, 0, s>>>(Sten2<double>{A, ld, pl}, n, out);
+    BMG_CUDA(cudaGetLastError());
+    return BMG_OK;
+}
+
+bmg_status assemble_tensor2d(Ctx& c, const double* coords, const double* D) {
+    Level& L = c.lev[0];
+    k_assemble2d<true><<<grid_rows(L.n, L.n), 128, 0, c.stream>>>(L.n, L.ld, L.plane, coords, D, L.A64, c.st);
+    c.launches++;
     BMG_CUDA(cudaGetLastError());
     return BMG_OK;
 }

@@ -12,10 +12,43 @@ namespace {
 constexpr double kG0 = 0.21132486540518711775;
 constexpr double kG1 = 0.78867513459481288225;
 
+// Coefficient of a cell, as the metric it induces from adj(J) = det J J^-1
+// (the 1/8 is the Gauss weight).  Scalar kappa: G = (kappa / det J) adj
+// adj^T.  SPD tensor D (Sec. 2, Eq. pde): G = (1 / det J) adj D adj^T.
+struct Scalar3 {
+    double kap;
+    __device__ __forceinline__ void metric(const double adj[3][3], double det, double G[3][3]) const {
+        const double s = 0.125 * kap / det;
+#pragma unroll
+        for (int m = 0; m < 3; m++)
+#pragma unroll
+            for (int p = 0; p < 3; p++)
+                G[m][p] = s * (adj[m][0] * adj[p][0] + adj[m][1] * adj[p][1] + adj[m][2] * adj[p][2]);
+    }
+};
+struct Tensor3 {
+    double d[3][3];
+    __device__ __forceinline__ void metric(const double adj[3][3], double det, double G[3][3]) const {
+        const double s = 0.125 / det;
+        double t[3][3];   // adj D
+#pragma unroll
+        for (int m = 0; m < 3; m++)
+#pragma unroll
+            for (int c = 0; c < 3; c++) t[m][c] = adj[m][0] * d[0][c] + adj[m][1] * d[1][c] + adj[m][2] * d[2][c];
+#pragma unroll
+        for (int m = 0; m < 3; m++)
+#pragma unroll
+            for (int p = 0; p < 3; p++)
+                G[m][p] = s * (t[m][0] * adj[p][0] + t[m][1] * adj[p][1] + t[m][2] * adj[p][2]);
+    }
+};
+
 // Row `a` of the trilinear element matrix of cell (ci,cj,ck):
-// Krow[b] = sum_q 1/8 grad(phi_a)^T G grad(phi_b), G = (kappa/det J) adj(J) adj(J)^T.
-// Corner b = bx + 2 by + 4 bz sits at node (ci+bx, cj+by, ck+bz).
-__device__ bool element_row3d(const double* __restrict__ coords, int n, int ci, int cj, int ck, double kap, int a,
+// Krow[b] = sum_q 1/8 grad(phi_a)^T G grad(phi_b), G from the cell's
+// coefficient (above).  Corner b = bx + 2 by + 4 bz sits at node
+// (ci+bx, cj+by, ck+bz).
+template <class C>
+__device__ bool element_row3d(const double* __restrict__ coords, int n, int ci, int cj, int ck, const C& coef, int a,
                               double Krow[8]) {
     const long long nn = (long long)n * n * n;
     double xa[3][8];
@@ -61,13 +94,8 @@ __device__ bool element_row3d(const double* __restrict__ coords, int n, int ci, 
         adj[2][2] = J[0][0] * J[1][1] - J[0][1] * J[1][0];
         const double det = J[0][0] * adj[0][0] + J[0][1] * adj[1][0] + J[0][2] * adj[2][0];
         if (!(det > 0.0)) ok = false;
-        const double s = 0.125 * kap / det;
         double G[3][3];
-#pragma unroll
-        for (int m = 0; m < 3; m++)
-#pragma unroll
-            for (int p = 0; p < 3; p++)
-                G[m][p] = s * (adj[m][0] * adj[p][0] + adj[m][1] * adj[p][1] + adj[m][2] * adj[p][2]);
+        coef.metric(adj, det, G);
         const double ga0 = G[0][0] * g[a][0] + G[0][1] * g[a][1] + G[0][2] * g[a][2];
         const double ga1 = G[1][0] * g[a][0] + G[1][1] * g[a][1] + G[1][2] * g[a][2];
         const double ga2 = G[2][0] * g[a][0] + G[2][1] * g[a][1] + G[2][2] * g[a][2];
@@ -83,8 +111,23 @@ __device__ __forceinline__ bool inner3(int n, int i, int j, int k) {
 
 // Gather assembly: one thread per node, the 8 surrounding cells, the
 // stored half of the 27-point row (14 planes).
+// coefficient of cell e: kappa[e], or the tensor planes D11, D12, D13, D22,
+// D23, D33 (ne cells each)
+template <bool TENSOR>
+__device__ __forceinline__ auto cell_coef3(const double* __restrict__ c, long long ne, long long e) {
+    if constexpr (TENSOR) {
+        const double d11 = c[e], d12 = c[ne + e], d13 = c[2 * ne + e], d22 = c[3 * ne + e], d23 = c[4 * ne + e],
+                     d33 = c[5 * ne + e];
+        return Tensor3{{{d11, d12, d13}, {d12, d22, d23}, {d13, d23, d33}}};
+    } else {
+        return Scalar3{c[e]};
+    }
+}
+
+template <bool TENSOR>
 __global__ void k_assemble3d(int n, int ld, long long pl, const double* __restrict__ coords,
                              const double* __restrict__ kappa, double* __restrict__ A, KState* st) {
+    const long long ne = (long long)(n - 1) * (n - 1) * (n - 1);
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     const int j = blockIdx.y, k = blockIdx.z;
     if (i >= n) return;
@@ -99,9 +142,9 @@ __global__ void k_assemble3d(int n, int ld, long long pl, const double* __restri
                 for (int cx = 0; cx < 2; cx++) {
                     const int ci = i - 1 + cx, cj = j - 1 + cy, ck = k - 1 + cz;
                     const int a = (1 - cx) + 2 * (1 - cy) + 4 * (1 - cz);
-                    const double kap = kappa[(long long)ci + (long long)(n - 1) * (cj + (long long)(n - 1) * ck)];
+                    const long long e = (long long)ci + (long long)(n - 1) * (cj + (long long)(n - 1) * ck);
                     double Kr[8];
-                    ok &= element_row3d(coords, n, ci, cj, ck, kap, a, Kr);
+                    ok &= element_row3d(coords, n, ci, cj, ck, cell_coef3<TENSOR>(kappa, ne, e), a, Kr);
                     for (int b = 0; b < 8; b++) {
                         const int dx = (b & 1) - (a & 1), dy = ((b >> 1) & 1) - ((a >> 1) & 1),
                                   dz = (b >> 2) - (a >> 2);
@@ -333,7 +376,7 @@ __global__ void k_adjoint_cells3d(int n, const double* __restrict__ coords, cons
     for (int a = 0; a < 8; a++) {
         if (le[a] == 0.0) continue;
         double Kr[8];
-        ok &= element_row3d(coords, n, ci, cj, ck, 1.0, a, Kr);
+        ok &= element_row3d(coords, n, ci, cj, ck, Scalar3{1.0}, a, Kr);
         double t = 0.0;
         for (int b = 0; b < 8; b++) t += Kr[b] * ue[b];
         s += le[a] * t;
@@ -348,7 +391,7 @@ inline dim3 grid3(int ni, int nj, int nk) { return dim3(cdiv(ni, 64), nj, nk); }
 
 bmg_status assemble3d(Ctx& c, const double* coords, const double* kappa) {
     Level& L = c.lev[0];
-    k_assemble3d<<<grid3(L.n, L.n, L.n), 64, 0, c.stream>>>(L.n, L.ld, L.plane, coords, kappa, L.A64, c.st);
+    k_assemble3d<false><<<grid3(L.n, L.n, L.n), 64, 0, c.stream>>>(L.n, L.ld, L.plane, coords, kappa, L.A64, c.st);
     c.launches++;
     BMG_CUDA(cudaGetLastError());
     return BMG_OK;
@@ -357,9 +400,17 @@ bmg_status assemble3d(Ctx& c, const double* coords, const double* kappa) {
 // As assemble_export2d: assembly into caller-given half planes, then export.
 bmg_status assemble_export3d(int n, int ld, long long pl, const double* coords, const double* kappa, double* A,
                              KState* st, double* out, cudaStream_t s) {
-    k_assemble3d<<<grid3(n, n, n), 64, 0, s>>>(n, ld, pl, coords, kappa, A, st);
+    k_assemble3d<false><<<grid3(n, n, n), 64, 0, s>>>(n, ld, pl, coords, kappa, A, st);
     BMG_CUDA(cudaGetLastError());
     k_export_stencil3d<<<grid3(n, n, n), 64, 0, s>>>(Sten3<double>{A, n, ld, pl}, out);
+    BMG_CUDA(cudaGetLastError());
+    return BMG_OK;
+}
+
+bmg_status assemble_tensor3d(Ctx& c, const double* coords, const double* D) {
+    Level& L = c.lev[0];
+    k_assemble3d<true><<<grid3(L.n, L.n, L.n), 64, 0, c.stream>>>(L.n, L.ld, L.plane, coords, D, L.A64, c.st);
+    c.launches++;
     BMG_CUDA(cudaGetLastError());
     return BMG_OK;
 }

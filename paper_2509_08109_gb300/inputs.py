@@ -260,6 +260,36 @@ def bump_batch(count: int = 512, seed: int = 5, kmin: int = 6, kmax: int = 10, n
     return probs
 
 
+def annulus_anisotropic(n: int = 257, eps: float = 0.1, seed: int = 6) -> Problem:
+    """Quarter annulus with an SPD diffusion tensor per cell (Sec. 2, Eq. pde):
+    D = e_r e_r^T + eps e_t e_t^T, radial diffusion eps^-1 times stronger than
+    tangential, e_r the radial unit vector at the cell centroid; planes
+    D11, D12, D22 in extra['D'] (kappa holds the trace / 2 for reference);
+    f ~ U[-1,1]."""
+    rng = np.random.default_rng(seed)
+    coords = coords_quarter_annulus(n)
+    cen = cell_centroids(coords)
+    phi = np.arctan2(cen[1], cen[0])
+    c, s = np.cos(phi), np.sin(phi)
+    D = np.stack([c * c + eps * s * s, (1.0 - eps) * c * s, s * s + eps * c * c])
+    f = rhs_uniform(rng, (n, n))
+    return Problem(f"annulus_anisotropic_n{n}", 2, n, coords, 0.5 * (D[0] + D[2]), f, {"D": D, "eps": eps})
+
+
+def shell_anisotropic(n: int = 33, eps: float = 0.1, seed: int = 7) -> Problem:
+    """Spherical-shell octant with D = e_r e_r^T + eps (I - e_r e_r^T) per
+    cell; planes D11, D12, D13, D22, D23, D33 in extra['D']; f ~ U[-1,1]."""
+    rng = np.random.default_rng(seed)
+    coords = coords_shell_octant(n)
+    cen = cell_centroids(coords)
+    r = np.sqrt((cen ** 2).sum(axis=0))
+    e = cen / r
+    M = [[eps * (a == b) + (1.0 - eps) * e[a] * e[b] for b in range(3)] for a in range(3)]
+    D = np.stack([M[0][0], M[0][1], M[0][2], M[1][1], M[1][2], M[2][2]])
+    f = rhs_uniform(rng, (n, n, n))
+    return Problem(f"shell_anisotropic_n{n}", 3, n, coords, (D[0] + D[3] + D[5]) / 3.0, f, {"D": D, "eps": eps})
+
+
 def identity_coefficient(n: int, kind: str, seed: int = 0) -> Problem:
     """Identity map on [0,1]^2 with a Sec. 4.1 coefficient evaluated at the
     cell centre: 'circle' (100 inside r < 3/5, else 1), 'checkerboard'

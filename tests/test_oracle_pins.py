@@ -551,3 +551,107 @@ def test_symmetric_solve_identity():
     xb = H.pcg(b, tol=1e-14, maxit=200)[0]
     s1, s2 = float(np.sum(xa * b)), float(np.sum(a * xb))
     assert abs(s1 - s2) <= 1e-12 * abs(s1)
+
+
+# ---------------------------------------------------------------- tensor coefficient
+def _spd(dim, rng):
+    B = rng.normal(size=(dim, dim))
+    return B @ B.T + 0.5 * np.eye(dim)
+
+
+def _tensor_planes(D, n):
+    dim = D.shape[0]
+    idx = [(0, 0), (0, 1), (1, 1)] if dim == 2 else [(0, 0), (0, 1), (0, 2), (1, 1), (1, 2), (2, 2)]
+    return np.stack([np.full((n - 1,) * dim, D[a, b]) for a, b in idx])
+
+
+@pytest.mark.parametrize("seed", [0, 1, 2])
+def test_tensor_stencil_closed_form_2d(seed):
+    """Identity map, constant SPD D: G = D, and the Q1 nine-point row of an
+    interior node is C = 4/3 (g11+g22), W = E = -2/3 g11 + 1/3 g22,
+    S = N = 1/3 g11 - 2/3 g22, SW = NE = -(g11+g22)/6 - g12/2,
+    NW = SE = -(g11+g22)/6 + g12/2 (exact element integrals)."""
+    D = _spd(2, np.random.default_rng(seed))
+    g11, g12, g22 = D[0, 0], D[0, 1], D[1, 1]
+    n = 7
+    A = oracle.assemble_tensor(inputs.coords_identity(n, 2), _tensor_planes(D, n))
+    row = A[3, 3]
+    corner_a, corner_b = -(g11 + g22) / 6 - g12 / 2, -(g11 + g22) / 6 + g12 / 2
+    want = np.array([corner_a, g11 / 3 - 2 * g22 / 3, corner_b,
+                     -2 * g11 / 3 + g22 / 3, 4 * (g11 + g22) / 3, -2 * g11 / 3 + g22 / 3,
+                     corner_b, g11 / 3 - 2 * g22 / 3, corner_a])
+    assert np.abs(row - want).max() <= 1e-14 * np.abs(want).max()
+
+
+def _kron_element(D, h):
+    """Exact trilinear element matrix on a cube of side h with constant D,
+    K[a][b] = h sum_pq D_pq prod_r f_r, from the 1-D factors int phi' phi'
+    (r = p = q), int phi_a' phi_b (r = p only), int phi_a phi_b' (r = q only)
+    and int phi_a phi_b (otherwise) on [0, 1]."""
+    k = np.array([[1.0, -1.0], [-1.0, 1.0]])
+    m = np.array([[1 / 3, 1 / 6], [1 / 6, 1 / 3]])
+    c = np.array([[-0.5, -0.5], [0.5, 0.5]])
+    K = np.zeros((8, 8))
+    for a in range(8):
+        for b in range(8):
+            s = 0.0
+            for p in range(3):
+                for q in range(3):
+                    t = D[p, q]
+                    for r in range(3):
+                        ar, br = (a >> r) & 1, (b >> r) & 1
+                        if r == p and r == q:
+                            t *= k[ar, br]
+                        elif r == p:
+                            t *= c[ar, br]
+                        elif r == q:
+                            t *= c[br, ar]
+                        else:
+                            t *= m[ar, br]
+                    s += t
+            K[a, b] = h * s
+    return K
+
+
+@pytest.mark.parametrize("seed", [0, 1])
+def test_tensor_stencil_kronecker_3d(seed):
+    """Identity map, constant SPD D in 3-D: the interior row equals the sum
+    of the Kronecker-built element matrices of the node's eight cells."""
+    D = _spd(3, np.random.default_rng(seed))
+    n = 5
+    h = 1.0 / (n - 1)
+    A = oracle.assemble_tensor(inputs.coords_identity(n, 3), _tensor_planes(D, n))
+    K = _kron_element(D, h)
+    row = np.zeros(27)
+    for cell in range(8):                        # the node is corner a of the cell
+        a = 7 - cell
+        for b in range(8):
+            d = [((b >> r) & 1) - ((a >> r) & 1) for r in range(3)]
+            row[(d[0] + 1) + 3 * (d[1] + 1) + 9 * (d[2] + 1)] += K[a, b]
+    got = A[2, 2, 2]
+    assert np.abs(got - row).max() <= 1e-14 * np.abs(row).max()
+
+
+@pytest.mark.parametrize("dim", [2, 3])
+def test_tensor_rotation_covariance(dim):
+    """A rotated grid x = R xi with the rotated tensor R D0 R^T has the
+    metric D0 of the unrotated one, so the stencils agree."""
+    rng = np.random.default_rng(5 + dim)
+    D0 = _spd(dim, rng)
+    Q, _ = np.linalg.qr(rng.normal(size=(dim, dim)))
+    if np.linalg.det(Q) < 0:
+        Q[:, 0] = -Q[:, 0]
+    n = 5
+    base = inputs.coords_identity(n, dim)
+    rot = np.einsum("rc,c...->r...", Q, base)
+    A0 = oracle.assemble_tensor(base, _tensor_planes(D0, n))
+    A1 = oracle.assemble_tensor(rot, _tensor_planes(Q @ D0 @ Q.T, n))
+    assert np.abs(A1 - A0).max() <= 1e-13 * np.abs(A0).max()
+
+
+def test_tensor_of_scalar_times_identity_is_the_scalar_assembly():
+    p = inputs.annulus_lognormal(17)
+    D = np.stack([p.kappa, np.zeros_like(p.kappa), p.kappa])
+    A1 = oracle.assemble(p.coords, p.kappa)
+    A2 = oracle.assemble_tensor(p.coords, D)
+    assert np.abs(A1 - A2).max() <= 1e-14 * np.abs(A1).max()
