@@ -139,6 +139,17 @@ bmg_status bmg_assemble(bmg_ctx* ctx, const double* coords, const double* kappa)
    a context. */
 bmg_status bmg_assemble_tensor(bmg_ctx* ctx, const double* coords, const double* D);
 
+/* Non-zero Dirichlet data (the lift term of Sec. 2, Eq. weak_computational):
+   out_i = -sum over boundary nodes j of A_ij g_j for every interior node i,
+   the couplings that bmg_assemble drops, from the same map and scalar
+   coefficient; out is zero on the boundary.  The solution with boundary
+   values g and right-hand side f is then x = A^-1 (f + out) in the interior
+   (bmg_solve) and g on the boundary.  coords, kappa: as bmg_assemble; g,
+   out: device, n^d doubles, i fastest (interior values of g are ignored).
+   Does not change the context's operator.  Errors: BMG_ERR_MAP_FOLDED. */
+bmg_status bmg_boundary_rhs(bmg_ctx* ctx, const double* coords, const double* kappa, const double* g,
+                            double* out);
+
 /* Sets the finest operator directly, the alternative Sec. 2.2 allows to
    assembling it from the coefficient.  stencil: device, n^d rows of 3^d
    doubles, entry (dx+1)+3(dy+1)[+9(dz+1)] = A[node, node+offset]; the

@@ -82,6 +82,7 @@ def _load():
             ("or_adjoint_grad", [I, I, P, P, P, P], I),
             ("or_element_tensor", [I, P, P, P], I),
             ("or_assemble_tensor", [I, I, P, P, P], I),
+            ("or_boundary_rhs", [I, I, P, P, P, P], I),
         ]:
             f = getattr(lib, name)
             f.argtypes = args
@@ -144,6 +145,19 @@ def assemble_tensor(coords, D) -> np.ndarray:
     A = np.zeros(coords.shape[1:] + (3 ** d,))
     _check(_load().or_assemble_tensor(d, n, _ptr(coords), _ptr(D), _ptr(A)))
     return A
+
+
+def boundary_rhs(coords, kappa, g) -> np.ndarray:
+    """-A_{I,B} g: the couplings of interior nodes to the boundary nodes,
+    which assembly drops, applied to Dirichlet data g (boundary values of a
+    grid vector; interior values ignored).  The lift term of Sec. 2."""
+    coords = _f64(coords)
+    kappa = _f64(kappa)
+    g = _f64(g)
+    d, n = _dim_n(coords.shape[1:])
+    out = np.zeros(coords.shape[1:])
+    _check(_load().or_boundary_rhs(d, n, _ptr(coords), _ptr(kappa), _ptr(g), _ptr(out)))
+    return out
 
 
 def metric(xe, kappa: float, h: float):

@@ -362,6 +362,35 @@ int or_assemble_tensor(int dim, int n, const double* coords, const double* Dt, d
     return OR_OK;
 }
 
+/* ------------------------------------------------------------------ */
+/* Dirichlet data (Sec. 2, Eq. weak_computational, the lift g term):    */
+/* out_i = -sum over boundary nodes j of A_ij g_j, for interior i        */
+/* ------------------------------------------------------------------ */
+int or_boundary_rhs(int dim, int n, const double* coords, const double* kappa, const double* g, double* out) {
+    if ((dim != 2 && dim != 3) || n < 3) return OR_ERR_ARG;
+    int na = 1 << dim;
+    long nn = pw_int(n, dim), ne = pw_int(n - 1, dim);
+    memset(out, 0, sizeof(double) * nn);
+    for (long e = 0; e < ne; e++) {
+        int cc[3];
+        double xe[24], K[64];
+        cell_coords(dim, n, e, cc);
+        gather_cell(dim, n, coords, cc, xe);
+        int st = or_element(dim, xe, kappa[e], K);
+        if (st) return st;
+        for (int a = 0; a < na; a++) {
+            int ca[3] = {cc[0] + (a & 1), cc[1] + ((a >> 1) & 1), cc[2] + ((a >> 2) & 1)};
+            if (!is_interior(dim, n, ca)) continue;
+            for (int b = 0; b < na; b++) {
+                int cb[3] = {cc[0] + (b & 1), cc[1] + ((b >> 1) & 1), cc[2] + ((b >> 2) & 1)};
+                if (is_interior(dim, n, cb)) continue;
+                out[node_id(dim, n, ca)] -= K[a * na + b] * g[node_id(dim, n, cb)];
+            }
+        }
+    }
+    return OR_OK;
+}
+
 /* Physical coordinates of every quadrature point: xq[(e*2^d + q)*dim + r] */
 int or_gauss_points(int dim, int n, const double* coords, double* xq) {
     if ((dim != 2 && dim != 3) || n < 2) return OR_ERR_ARG;

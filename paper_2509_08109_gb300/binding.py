@@ -93,6 +93,7 @@ def load() -> ctypes.CDLL:
         "bmg_status_str": ([I], ctypes.c_char_p),
         "bmg_assemble_noalloc": ([I, I, P, P, P, P], I),
         "bmg_assemble_tensor": ([P, P, P], I),
+        "bmg_boundary_rhs": ([P, P, P, P, P], I),
     }
     for name, (args, res) in sigs.items():
         f = getattr(lib, name)
@@ -108,7 +109,8 @@ def exported_symbols() -> list:
             "bmg_levels",
             "bmg_level_n", "bmg_get_stencil", "bmg_get_interp", "bmg_launch_count", "bmg_get_tiles",
             "bmg_set_tiles", "bmg_autotune", "bmg_profile",
-            "bmg_profile_read", "bmg_destroy", "bmg_status_str", "bmg_assemble_noalloc", "bmg_assemble_tensor"]
+            "bmg_profile_read", "bmg_destroy", "bmg_status_str", "bmg_assemble_noalloc", "bmg_assemble_tensor",
+            "bmg_boundary_rhs"]
 
 
 def _check(code: int, where: str):
@@ -249,6 +251,18 @@ class Solver:
             _check(load().bmg_assemble_tensor(self._h, _ptr(coords), _ptr(D)), "bmg_assemble_tensor")
         self._coords = coords
         return self
+
+    def boundary_rhs(self, coords, kappa, g) -> torch.Tensor:
+        """bmg_boundary_rhs: -A_{I,B} g for Dirichlet data g (grid shape)."""
+        coords = self._dev(torch.as_tensor(coords))
+        kappa = self._dev(torch.as_tensor(kappa))
+        g = self._dev(torch.as_tensor(g))
+        assert g.shape == self.grid_shape, g.shape
+        out = torch.empty_like(g)
+        with torch.cuda.device(self.device):
+            _check(load().bmg_boundary_rhs(self._h, _ptr(coords), _ptr(kappa), _ptr(g), _ptr(out)),
+                   "bmg_boundary_rhs")
+        return out
 
     def set_stencil(self, full):
         full = self._dev(torch.as_tensor(full))

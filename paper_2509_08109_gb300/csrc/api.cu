@@ -459,6 +459,20 @@ bmg_status bmg_assemble_tensor(bmg_ctx* ctx, const double* coords, const double*
     return BMG_OK;
 }
 
+bmg_status bmg_boundary_rhs(bmg_ctx* ctx, const double* coords, const double* kappa, const double* g,
+                            double* out) {
+    BMG_TRY(check_ready(ctx));
+    if (!coords || !kappa || !g || !out) return BMG_ERR_ARG;
+    Ctx& c = ctx->c;
+    if (!is_device_ptr(coords) || !is_device_ptr(kappa) || !is_device_ptr(g) || !is_device_ptr(out))
+        return BMG_ERR_ARG;
+    BMG_TRY(reset_state(c));
+    BMG_TRY(c.dim == 2 ? boundary_rhs2d(c, coords, kappa, g, out) : boundary_rhs3d(c, coords, kappa, g, out));
+    KState h;
+    BMG_TRY(read_state(c, h));
+    return h.err ? (bmg_status)h.err : BMG_OK;
+}
+
 bmg_status bmg_set_stencil(bmg_ctx* ctx, const double* stencil) {
     BMG_TRY(check_ready(ctx));
     if (!stencil || !is_device_ptr(stencil)) return BMG_ERR_ARG;

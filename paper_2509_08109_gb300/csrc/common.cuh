@@ -258,6 +258,7 @@ __device__ __forceinline__ bool grid_sum(double v, double* partials, unsigned in
 // setup2d.cu
 bmg_status assemble2d(Ctx& c, const double* coords, const double* kappa);
 bmg_status assemble_tensor2d(Ctx& c, const double* coords, const double* D);
+bmg_status boundary_rhs2d(Ctx& c, const double* coords, const double* kappa, const double* g, double* out);
 bmg_status set_stencil2d(Ctx& c, const double* full);
 bmg_status setup_level2d(Ctx& c, int l);
 bmg_status export_stencil2d(Ctx& c, int l, double* out);
@@ -266,6 +267,7 @@ bmg_status adjoint_cells2d(Ctx& c, const double* coords, const double* u, const 
 // setup3d.cu
 bmg_status assemble3d(Ctx& c, const double* coords, const double* kappa);
 bmg_status assemble_tensor3d(Ctx& c, const double* coords, const double* D);
+bmg_status boundary_rhs3d(Ctx& c, const double* coords, const double* kappa, const double* g, double* out);
 bmg_status set_stencil3d(Ctx& c, const double* full);
 bmg_status setup_level3d(Ctx& c, int l);
 bmg_status export_stencil3d(Ctx& c, int l, double* out);

@@ -321,6 +321,37 @@ __global__ void k_export_interp2d(const double* __restrict__ P, int nf, int ldc,
         row[s] = pweight2(P, ldc, plc, nf, i, j, (i >> 1) + (s & 1), (j >> 1) + (s >> 1));
 }
 
+// out_i = -sum over boundary nodes j of A_ij g_j at interior nodes i (the
+// couplings the assembly drops, applied to Dirichlet data g; Sec. 2, the
+// lift term of Eq. weak_computational); g and out in the caller's n^2
+// layout, out zero on the boundary.
+__global__ void k_boundary_rhs2d(int n, const double* __restrict__ coords, const double* __restrict__ kappa,
+                                 const double* __restrict__ g, double* __restrict__ out, KState* st) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    const int j = blockIdx.y;
+    if (i >= n) return;
+    double acc = 0.0;
+    if (i >= 1 && j >= 1 && i <= n - 2 && j <= n - 2) {
+        const double* X = coords;
+        const double* Y = coords + (long long)n * n;
+        bool ok = true;
+        for (int cy = 0; cy < 2; cy++)
+            for (int cx = 0; cx < 2; cx++) {
+                const int ci = i - 1 + cx, cj = j - 1 + cy;
+                const int a = (1 - cx) + 2 * (1 - cy);      // the node's corner in the cell
+                double K[4][4];
+                ok &= element2d(X, Y, n, ci, cj, Scalar2{kappa[(long long)cj * (n - 1) + ci]}, K);
+                for (int b = 0; b < 4; b++) {
+                    const int bi = ci + (b & 1), bj = cj + (b >> 1);
+                    if (bi >= 1 && bj >= 1 && bi <= n - 2 && bj <= n - 2) continue;
+                    acc -= K[a][b] * g[(long long)bj * n + bi];
+                }
+            }
+        if (!ok) set_err(st, BMG_ERR_MAP_FOLDED);
+    }
+    out[(long long)j * n + i] = acc;
+}
+
 // dL/dkappa_e = -lambda_e^T K_e^0 u_e (u, lambda in the caller's n^2 layout).
 __global__ void k_adjoint_cells2d(int n, const double* __restrict__ coords, const double* __restrict__ u,
                                   const double* __restrict__ lam, double* __restrict__ g, KState* st) {
@@ -375,6 +406,14 @@ bmg_status assemble_export2d(int n, int ld, long long pl, const double* coords, 
 bmg_status assemble_tensor2d(Ctx& c, const double* coords, const double* D) {
     Level& L = c.lev[0];
     k_assemble2d<true><<<grid_rows(L.n, L.n), 128, 0, c.stream>>>(L.n, L.ld, L.plane, coords, D, L.A64, c.st);
+    c.launches++;
+    BMG_CUDA(cudaGetLastError());
+    return BMG_OK;
+}
+
+bmg_status boundary_rhs2d(Ctx& c, const double* coords, const double* kappa, const double* g, double* out) {
+    const int n = c.lev[0].n;
+    k_boundary_rhs2d<<<grid_rows(n, n), 128, 0, c.stream>>>(n, coords, kappa, g, out, c.st);
     c.launches++;
     BMG_CUDA(cudaGetLastError());
     return BMG_OK;

@@ -358,6 +358,34 @@ __global__ void k_export_interp3d(const double* __restrict__ P, CoarseDims D, do
                           (k >> 1) + (s >> 2));
 }
 
+// out_i = -sum over boundary nodes j of A_ij g_j at interior nodes i, as in 2-D.
+__global__ void k_boundary_rhs3d(int n, const double* __restrict__ coords, const double* __restrict__ kappa,
+                                 const double* __restrict__ g, double* __restrict__ out, KState* st) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    const int j = blockIdx.y, k = blockIdx.z;
+    if (i >= n) return;
+    double acc = 0.0;
+    if (inner3(n, i, j, k)) {
+        bool ok = true;
+        for (int cz = 0; cz < 2; cz++)
+            for (int cy = 0; cy < 2; cy++)
+                for (int cx = 0; cx < 2; cx++) {
+                    const int ci = i - 1 + cx, cj = j - 1 + cy, ck = k - 1 + cz;
+                    const int a = (1 - cx) + 2 * (1 - cy) + 4 * (1 - cz);
+                    const double kap = kappa[(long long)ci + (long long)(n - 1) * (cj + (long long)(n - 1) * ck)];
+                    double Kr[8];
+                    ok &= element_row3d(coords, n, ci, cj, ck, Scalar3{kap}, a, Kr);
+                    for (int b = 0; b < 8; b++) {
+                        const int bi = ci + (b & 1), bj = cj + ((b >> 1) & 1), bk = ck + (b >> 2);
+                        if (inner3(n, bi, bj, bk)) continue;
+                        acc -= Kr[b] * g[(long long)bi + (long long)n * (bj + (long long)n * bk)];
+                    }
+                }
+        if (!ok) set_err(st, BMG_ERR_MAP_FOLDED);
+    }
+    out[(long long)i + (long long)n * (j + (long long)n * k)] = acc;
+}
+
 __global__ void k_adjoint_cells3d(int n, const double* __restrict__ coords, const double* __restrict__ u,
                                   const double* __restrict__ lam, double* __restrict__ g, KState* st) {
     const int ci = blockIdx.x * blockDim.x + threadIdx.x;
@@ -410,6 +438,14 @@ bmg_status assemble_export3d(int n, int ld, long long pl, const double* coords, 
 bmg_status assemble_tensor3d(Ctx& c, const double* coords, const double* D) {
     Level& L = c.lev[0];
     k_assemble3d<true><<<grid3(L.n, L.n, L.n), 64, 0, c.stream>>>(L.n, L.ld, L.plane, coords, D, L.A64, c.st);
+    c.launches++;
+    BMG_CUDA(cudaGetLastError());
+    return BMG_OK;
+}
+
+bmg_status boundary_rhs3d(Ctx& c, const double* coords, const double* kappa, const double* g, double* out) {
+    const int n = c.lev[0].n;
+    k_boundary_rhs3d<<<grid3(n, n, n), 64, 0, c.stream>>>(n, coords, kappa, g, out, c.st);
     c.launches++;
     BMG_CUDA(cudaGetLastError());
     return BMG_OK;

@@ -290,6 +290,36 @@ def shell_anisotropic(n: int = 33, eps: float = 0.1, seed: int = 7) -> Problem:
     return Problem(f"shell_anisotropic_n{n}", 3, n, coords, (D[0] + D[3] + D[5]) / 3.0, f, {"D": D, "eps": eps})
 
 
+def boundary_star(n: int, amp: float = 0.0, lobes: int = 5) -> np.ndarray:
+    """Boundary map phi from the unit square to the star-shaped curve
+    r(theta) = 1 + amp cos(lobes theta) around the origin (amp = 0: the unit
+    disk), as nodal values on the boundary of an n x n grid (interior zero),
+    shape (2, n, n).  The square's boundary is walked counterclockwise from
+    the corner (0, 0) at unit speed and the perimeter fraction tau goes to
+    theta = 2 pi tau - 3 pi / 4, so corners map to the diagonals; for a convex
+    curve this map is unimodal in each coordinate."""
+    g = np.zeros((2, n, n))
+    h = 1.0 / (n - 1)
+    for j in range(n):
+        for i in range(n):
+            if 0 < i < n - 1 and 0 < j < n - 1:
+                continue
+            x, y = i * h, j * h
+            if j == 0:
+                tau = x
+            elif i == n - 1:
+                tau = 1.0 + y
+            elif j == n - 1:
+                tau = 3.0 - x
+            else:
+                tau = 4.0 - y
+            th = 2.0 * math.pi * tau / 4.0 - 0.75 * math.pi
+            r = 1.0 + amp * math.cos(lobes * th)
+            g[0, j, i] = r * math.cos(th)
+            g[1, j, i] = r * math.sin(th)
+    return g
+
+
 def identity_coefficient(n: int, kind: str, seed: int = 0) -> Problem:
     """Identity map on [0,1]^2 with a Sec. 4.1 coefficient evaluated at the
     cell centre: 'circle' (100 inside r < 3/5, else 1), 'checkerboard'

@@ -655,3 +655,54 @@ def test_tensor_of_scalar_times_identity_is_the_scalar_assembly():
     A1 = oracle.assemble(p.coords, p.kappa)
     A2 = oracle.assemble_tensor(p.coords, D)
     assert np.abs(A1 - A2).max() <= 1e-14 * np.abs(A1).max()
+
+
+# ---------------------------------------------------------------- Dirichlet data
+def test_boundary_rhs_reproduces_linear_functions():
+    """Affine map, constant kappa: Q1 reproduces linear functions, so the
+    discrete harmonic extension of a linear function's boundary values is
+    that function (A_II x = -A_IB g solved densely)."""
+    n = 9
+    M = np.array([[1.1, 0.3], [-0.2, 0.8]])
+    coords = _affine_coords(n, M, [0.2, -0.1], 2)
+    kappa = np.full((n - 1, n - 1), 2.5)
+    u = 0.7 + 1.9 * coords[0] - 1.3 * coords[1]
+    rhs = oracle.boundary_rhs(coords, kappa, u)
+    m = oracle.interior_mask(n, 2)
+    x = np.linalg.solve(oracle.dense_operator(oracle.assemble(coords, kappa)), rhs[m])
+    assert np.abs(x - u[m]).max() <= 1e-12
+    assert np.all(rhs[~m] == 0.0)
+
+
+@pytest.mark.parametrize("dim", [2, 3])
+def test_boundary_rhs_equals_extended_grid_couplings(dim):
+    """Brute force: on a grid extended by one layer of nodes, the old
+    boundary nodes are interior, and the rows of the old interior nodes hold
+    exactly the couplings that the Dirichlet elimination drops."""
+    n = 7 if dim == 2 else 5
+    rng = np.random.default_rng(30 + dim)
+    if dim == 2:
+        coords = inputs.coords_bump(n, 0.1, -0.08)
+    else:   # an affine map with a small smooth distortion (its odd reflection stays unfolded)
+        base = inputs.coords_identity(n, 3)
+        bump = 0.05 * np.sin(np.pi * base[0]) * np.sin(np.pi * base[1]) * np.sin(np.pi * base[2])
+        coords = _affine_coords(n, [[1.0, 0.2, 0.0], [0.1, 0.9, 0.1], [0.0, -0.1, 1.1]], [0.0, 0.0, 0.0], 3)
+        coords = np.ascontiguousarray(coords + bump[None])
+    kappa = np.exp(rng.normal(0, 0.5, size=(n - 1,) * dim))
+    g = rng.uniform(-1, 1, size=(n,) * dim)
+    ext = np.pad(coords, [(0, 0)] + [(1, 1)] * dim, mode="reflect", reflect_type="odd")
+    kext = np.pad(kappa, [(1, 1)] * dim, mode="edge")
+    A = oracle.assemble(ext, kext)
+    inner = oracle.interior_mask(n, dim)
+    want = np.zeros((n,) * dim)
+    for idx in zip(*np.nonzero(inner)):
+        e = tuple(v + 1 for v in idx)
+        s = 0.0
+        for o in range(3 ** dim):
+            off = [(o % 3) - 1, (o // 3) % 3 - 1, o // 9 - 1][:dim][::-1]   # (dz,) dy, dx
+            nb = tuple(v + dv for v, dv in zip(idx, off))
+            if not inner[nb]:
+                s -= A[e + (o,)] * g[nb]
+        want[idx] = s
+    got = oracle.boundary_rhs(coords, kappa, g)
+    assert np.abs(got - want).max() <= 1e-13 * np.abs(want).max()
