@@ -29,6 +29,8 @@
 // outstanding copies (bounded) and returns.
 #include <cuda.h>
 
+#include <type_traits>
+
 #include "common.cuh"
 #include "fused2d.cuh"
 
@@ -213,13 +215,13 @@ struct Rows {
 };
 
 // ------------------------------------------------------------------ down kernel
-template <typename T, typename TF, int K>
-__global__ void __launch_bounds__(72 * K, sizeof(T) == 4 ? 3 : 1) k_vdown2d(const __grid_constant__ CUtensorMap tmA,
+template <typename T, typename TF, int K, int WC>
+__global__ void __launch_bounds__((WC + 8) * K, sizeof(T) == 4 ? 3 : 1) k_vdown2d(const __grid_constant__ CUtensorMap tmA,
                                                     const __grid_constant__ CUtensorMap tmF, FusedArgs p) {
     using LY = Lay<T, TF, K, false>;
     constexpr int RP = LY::RP;
     extern __shared__ unsigned char smem_raw[];
-    const LY L(p.wc);
+    const LY L(WC);   // strip width fixed at compile time: every shared-memory stride is a constant
     const int WW = L.WW, PL = 2 * WW;
     unsigned char* base = (unsigned char*)(((uintptr_t)smem_raw + 127) & ~(uintptr_t)127);
     Ring<T, TF, K, false> rg;
@@ -236,7 +238,7 @@ __global__ void __launch_bounds__(72 * K, sizeof(T) == 4 ? 3 : 1) k_vdown2d(cons
     rg.sXp = rg.sC = 0;
     const int tx = threadIdx.x, ty = threadIdx.y;
     const bool lead = tx == 0 && ty == 0;
-    const int I0 = 1 + blockIdx.x * p.wc, J0 = 1 + blockIdx.y * p.hc;
+    const int I0 = 1 + blockIdx.x * WC, J0 = 1 + blockIdx.y * p.hc;
     const int x0 = 2 * I0 - 10, xc0 = I0 - 5;
     rg.q0 = J0 - 2;
     const int npairs = p.hc + 2;
@@ -263,10 +265,10 @@ __global__ void __launch_bounds__(72 * K, sizeof(T) == 4 ? 3 : 1) k_vdown2d(cons
     const int ie = x0 + ce;
     const bool ve = ce >= 1 && ce <= WW - 2 && ie >= 1 && ie <= nf - 2;
     const bool vo = co <= WW - 2 && ie + 1 >= 1 && ie + 1 <= nf - 2;
-    const bool own_e = ve && ce >= 9 && ce < 9 + 2 * p.wc;
-    const bool own_o = vo && co >= 9 && co < 9 + 2 * p.wc;
+    const bool own_e = ve && ce >= 9 && ce < 9 + 2 * WC;
+    const bool own_o = vo && co >= 9 && co < 9 + 2 * WC;
     const int I = xc0 + tx;
-    const bool vres = tx >= 5 && tx < 5 + p.wc && I >= 1 && I <= nc - 2;
+    const bool vres = tx >= 5 && tx < 5 + WC && I >= 1 && I <= nc - 2;
     auto inrow = [&](int j) { return j >= 1 && j <= nf - 2; };
     auto X = [&](int j) { return sX + (int)((unsigned)j % XR) * WW; };
     auto R = [&](int j) { return sR + (int)((unsigned)j % XR) * WW; };
@@ -398,15 +400,15 @@ __global__ void __launch_bounds__(72 * K, sizeof(T) == 4 ? 3 : 1) k_vdown2d(cons
 }
 
 // ------------------------------------------------------------------ up kernel
-template <typename T, typename TF, typename TO, int K>
-__global__ void __launch_bounds__(72 * K, sizeof(T) == 4 ? 3 : 1) k_vup2d(const __grid_constant__ CUtensorMap tmA,
+template <typename T, typename TF, typename TO, int K, int WC>
+__global__ void __launch_bounds__((WC + 8) * K, sizeof(T) == 4 ? 3 : 1) k_vup2d(const __grid_constant__ CUtensorMap tmA,
                                                   const __grid_constant__ CUtensorMap tmF,
                                                   const __grid_constant__ CUtensorMap tmX,
                                                   const __grid_constant__ CUtensorMap tmC, FusedArgs p) {
     using LY = Lay<T, TF, K, true>;
     constexpr int RP = LY::RP;
     extern __shared__ unsigned char smem_raw[];
-    const LY L(p.wc);
+    const LY L(WC);   // strip width fixed at compile time: every shared-memory stride is a constant
     const int WW = L.WW, PL = 2 * WW;
     unsigned char* base = (unsigned char*)(((uintptr_t)smem_raw + 127) & ~(uintptr_t)127);
     Ring<T, TF, K, true> rg;
@@ -424,7 +426,7 @@ __global__ void __launch_bounds__(72 * K, sizeof(T) == 4 ? 3 : 1) k_vup2d(const 
     rg.sC = L.sC;
     const int tx = threadIdx.x, ty = threadIdx.y;
     const bool lead = tx == 0 && ty == 0;
-    const int I0 = 1 + blockIdx.x * p.wc, J0 = 1 + blockIdx.y * p.hc;
+    const int I0 = 1 + blockIdx.x * WC, J0 = 1 + blockIdx.y * p.hc;
     const int x0 = 2 * I0 - 10, xc0 = I0 - 5;
     rg.q0 = J0 - 2;
     const int npairs = p.hc + 2;
@@ -452,8 +454,8 @@ __global__ void __launch_bounds__(72 * K, sizeof(T) == 4 ? 3 : 1) k_vup2d(const 
     const int ie = x0 + ce;
     const bool ve = ce >= 1 && ce <= WW - 2 && ie >= 1 && ie <= nf - 2;
     const bool vo = co <= WW - 2 && ie + 1 >= 1 && ie + 1 <= nf - 2;
-    const bool own_e = ve && ce >= 9 && ce < 9 + 2 * p.wc;
-    const bool own_o = vo && co >= 9 && co < 9 + 2 * p.wc;
+    const bool own_e = ve && ce >= 9 && ce < 9 + 2 * WC;
+    const bool own_o = vo && co >= 9 && co < 9 + 2 * WC;
     const int I = xc0 + tx;                      // coarse column of the thread's column pair
     const bool vI = I >= 0 && I <= nc - 1;
     auto inrow = [&](int j) { return j >= 1 && j <= nf - 2; };
@@ -671,30 +673,68 @@ int down_smem(int wc) { return Lay<T, TF, k_of<T>(), false>(wc).bytes(); }
 template <typename T, typename TF>
 int up_smem(int wc) { return Lay<T, TF, k_of<T>(), true>(wc).bytes(); }
 
+// The strip widths the kernels are built for (multiples of 8 up to 64, so
+// that the TMA x coordinates stay 16-byte aligned); f(integral_constant<W>).
+template <class F>
+bmg_status with_wc(int wc, F&& f) {
+    switch (wc) {
+        case 8: return f(std::integral_constant<int, 8>{});
+        case 16: return f(std::integral_constant<int, 16>{});
+        case 24: return f(std::integral_constant<int, 24>{});
+        case 32: return f(std::integral_constant<int, 32>{});
+        case 40: return f(std::integral_constant<int, 40>{});
+        case 48: return f(std::integral_constant<int, 48>{});
+        case 56: return f(std::integral_constant<int, 56>{});
+        case 64: return f(std::integral_constant<int, 64>{});
+        default: return BMG_ERR_ARG;
+    }
+}
+
 template <typename T, typename TF>
 bmg_status launch_down(Ctx& c, const FusedLevel& F, cudaStream_t s) {
-    auto kern = k_vdown2d<T, TF, k_of<T>()>;
-    const int smem = down_smem<T, TF>(F.wc);
-    if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) != cudaSuccess)
-        return BMG_ERR_DEVICE;
-    kern<<<dim3(F.tiles_x, F.tiles_y), dim3(F.wc + 8, k_of<T>()), smem, s>>>(F.mA, F.mF, F.down);
-    c.launches++;
-    return cudaGetLastError() == cudaSuccess ? BMG_OK : BMG_ERR_DEVICE;
+    return with_wc(F.wc, [&](auto W) {
+        auto kern = k_vdown2d<T, TF, k_of<T>(), decltype(W)::value>;
+        const int smem = down_smem<T, TF>(F.wc);
+        if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) != cudaSuccess)
+            return BMG_ERR_DEVICE;
+        kern<<<dim3(F.tiles_x, F.tiles_y), dim3(F.wc + 8, k_of<T>()), smem, s>>>(F.mA, F.mF, F.down);
+        c.launches++;
+        return cudaGetLastError() == cudaSuccess ? BMG_OK : BMG_ERR_DEVICE;
+    });
 }
 
 template <typename T, typename TF, typename TO>
 bmg_status launch_up(Ctx& c, const FusedLevel& F, cudaStream_t s, void* out, const void* zold = nullptr) {
-    auto kern = k_vup2d<T, TF, TO, k_of<T>()>;
-    const int smem = up_smem<T, TF>(F.wc);
-    if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) != cudaSuccess)
-        return BMG_ERR_DEVICE;
-    FusedArgs a = F.up;
-    a.x = out;
-    a.zold = zold;
-    a.partials = zold ? c.partials : nullptr;
-    kern<<<dim3(F.tiles_x, F.tiles_y), dim3(F.wc + 8, k_of<T>()), smem, s>>>(F.mA, F.mF, F.mXp, F.mXc, a);
-    c.launches++;
-    return cudaGetLastError() == cudaSuccess ? BMG_OK : BMG_ERR_DEVICE;
+    return with_wc(F.wc, [&](auto W) {
+        auto kern = k_vup2d<T, TF, TO, k_of<T>(), decltype(W)::value>;
+        const int smem = up_smem<T, TF>(F.wc);
+        if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) != cudaSuccess)
+            return BMG_ERR_DEVICE;
+        FusedArgs a = F.up;
+        a.x = out;
+        a.zold = zold;
+        a.partials = zold ? c.partials : nullptr;
+        kern<<<dim3(F.tiles_x, F.tiles_y), dim3(F.wc + 8, k_of<T>()), smem, s>>>(F.mA, F.mF, F.mXp, F.mXc, a);
+        c.launches++;
+        return cudaGetLastError() == cudaSuccess ? BMG_OK : BMG_ERR_DEVICE;
+    });
+}
+
+template <typename T, typename TF, typename TO>
+bmg_status occupancy(int wc, int* down_blocks, int* up_blocks) {
+    return with_wc(wc, [&](auto W) {
+        constexpr int w = decltype(W)::value;
+        auto kd = k_vdown2d<T, TF, k_of<T>(), w>;
+        auto ku = k_vup2d<T, TF, TO, k_of<T>(), w>;
+        const int sd = down_smem<T, TF>(wc), su = up_smem<T, TF>(wc);
+        const int nt = (wc + 8) * k_of<T>();
+        if (cudaFuncSetAttribute(kd, cudaFuncAttributeMaxDynamicSharedMemorySize, sd) != cudaSuccess ||
+            cudaFuncSetAttribute(ku, cudaFuncAttributeMaxDynamicSharedMemorySize, su) != cudaSuccess ||
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(down_blocks, kd, nt, sd) != cudaSuccess ||
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(up_blocks, ku, nt, su) != cudaSuccess)
+            return BMG_ERR_DEVICE;
+        return BMG_OK;
+    });
 }
 
 }  // namespace
@@ -712,35 +752,9 @@ int fused_up_smem(bool f32, bool f64in, int wc) {
 }
 
 bmg_status fused_occupancy(bool f32, bool f64in, int wc, int* down_blocks, int* up_blocks) {
-    const int sd = fused_down_smem(f32, f64in, wc), su = fused_up_smem(f32, f64in, wc);
-    cudaError_t e1, e2, e3, e4;
-    if (!f32) {
-        auto kd = k_vdown2d<double, double, k_of<double>()>;
-        auto ku = k_vup2d<double, double, double, k_of<double>()>;
-        const int nt = (wc + 8) * k_of<double>();
-        e1 = cudaFuncSetAttribute(kd, cudaFuncAttributeMaxDynamicSharedMemorySize, sd);
-        e2 = cudaFuncSetAttribute(ku, cudaFuncAttributeMaxDynamicSharedMemorySize, su);
-        e3 = cudaOccupancyMaxActiveBlocksPerMultiprocessor(down_blocks, kd, nt, sd);
-        e4 = cudaOccupancyMaxActiveBlocksPerMultiprocessor(up_blocks, ku, nt, su);
-    } else if (f64in) {
-        auto kd = k_vdown2d<float, double, k_of<float>()>;
-        auto ku = k_vup2d<float, double, double, k_of<float>()>;
-        const int nt = (wc + 8) * k_of<float>();
-        e1 = cudaFuncSetAttribute(kd, cudaFuncAttributeMaxDynamicSharedMemorySize, sd);
-        e2 = cudaFuncSetAttribute(ku, cudaFuncAttributeMaxDynamicSharedMemorySize, su);
-        e3 = cudaOccupancyMaxActiveBlocksPerMultiprocessor(down_blocks, kd, nt, sd);
-        e4 = cudaOccupancyMaxActiveBlocksPerMultiprocessor(up_blocks, ku, nt, su);
-    } else {
-        auto kd = k_vdown2d<float, float, k_of<float>()>;
-        auto ku = k_vup2d<float, float, float, k_of<float>()>;
-        const int nt = (wc + 8) * k_of<float>();
-        e1 = cudaFuncSetAttribute(kd, cudaFuncAttributeMaxDynamicSharedMemorySize, sd);
-        e2 = cudaFuncSetAttribute(ku, cudaFuncAttributeMaxDynamicSharedMemorySize, su);
-        e3 = cudaOccupancyMaxActiveBlocksPerMultiprocessor(down_blocks, kd, nt, sd);
-        e4 = cudaOccupancyMaxActiveBlocksPerMultiprocessor(up_blocks, ku, nt, su);
-    }
-    if (e1 || e2 || e3 || e4) return BMG_ERR_DEVICE;
-    return BMG_OK;
+    if (!f32) return occupancy<double, double, double>(wc, down_blocks, up_blocks);
+    if (f64in) return occupancy<float, double, double>(wc, down_blocks, up_blocks);
+    return occupancy<float, float, float>(wc, down_blocks, up_blocks);
 }
 
 bmg_status fused_down(Ctx& c, int l, bool ir) {
