@@ -116,7 +116,9 @@ struct Lay {
     static constexpr int RP = K + 2 + D;
     // rows of the X / R rings: a step reads and writes fine rows 2J-1 .. 2J+2K
     // (2K+2 rows); consecutive steps are separated by a block barrier
-    static constexpr int XR = 2 * K + 4;
+    // (rounded up to a power of two in the down kernel, whose rings have the
+    // shared memory to spare, so that the row index wraps with a mask)
+    static constexpr int XR = UP ? 2 * K + 4 : (2 * K + 4 <= 8 ? 8 : 16);
     int WW, WWc, sA, sF, sXp, sC;
     __host__ __device__ Lay(int wc) {
         WW = 2 * wc + 16;
