@@ -303,14 +303,25 @@ __global__ void __launch_bounds__((WC + 8) * K, sizeof(T) == 4 ? 3 : 1) k_vdown2
         const Rows<T> r = rows(j);
         X(j)[co] = (vo && inrow(j)) ? divide<T>((T)rg.F(j)[co] - r.offdiag(co), r.diag(co)) : (T)0;
     };
+    // Residual after the forward sweep from a zero guess.  A point's own
+    // update zeroed its residual given the values of that moment, and the
+    // neighbours of later colours were still zero then, so what remains is
+    // minus their couplings times their new values:
+    //   colour 0 (even row, even column): all eight neighbours;
+    //   colour 1 (even row, odd column): the six on the odd rows above and below;
+    //   colour 2 (odd row, even column): the two colour-3 row neighbours;
+    //   colour 3 (odd row, odd column): none.
     auto resid = [&](int j) {
         const Rows<T> r = rows(j);
-        const TF* F = rg.F(j);
         T* Rj = R(j);
         const bool rj = inrow(j);
-        Rj[ce] = (ve && rj) ? (T)F[ce] - r.diag(ce) * r.x[ce] - r.offdiag(ce) : (T)0;
-        // the last colour (odd column on an odd row) has zero residual by construction
-        Rj[co] = (vo && rj && !(j & 1)) ? (T)F[co] - r.diag(co) * r.x[co] - r.offdiag(co) : (T)0;
+        if (!(j & 1)) {
+            Rj[ce] = (ve && rj) ? -r.offdiag(ce) : (T)0;
+            Rj[co] = (vo && rj) ? -r.offdiag_no_row(co) : (T)0;
+        } else {
+            Rj[ce] = (ve && rj) ? -(r.a[W2 * PL + ce] * r.x[ce - 1] + r.a[W2 * PL + ce + 1] * r.x[ce + 1]) : (T)0;
+            Rj[co] = (T)0;
+        }
     };
 
     bool ok = wait_pairs<RP>(rg.bars, 0, 2);
