@@ -83,13 +83,30 @@ __global__ void k_gs_colour3d_cb(const float* __restrict__ blk, long long nc, in
     x[o] = (f[o] - s) / blk[13 * nc + t];
 }
 
+// Residual after the forward 8-colour sweep from a zero guess: a point's own
+// update zeroed its residual while the neighbours of later colours were
+// still zero, so r = - sum over the neighbours of a later colour of a x.
+// The neighbour at offset d has colour col ^ m(d), m(d) the mask of the
+// non-zero components of d; same order of terms as offdiag3.
 template <typename T>
-__global__ void k_residual3d(L3<T> L, const T* __restrict__ f, const T* __restrict__ x, T* __restrict__ r) {
+__global__ void k_residual3d_sweep(L3<T> L, const T* __restrict__ x, T* __restrict__ r) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     const int j = blockIdx.y, k = blockIdx.z;
     if (i < 1 || j < 1 || k < 1 || i > L.n - 2 || j > L.n - 2 || k > L.n - 2) return;
+    const int col = (i & 1) | ((j & 1) << 1) | ((k & 1) << 2);
     const long long o = L.idx(i, j, k);
-    r[o] = f[o] - (L.A[13 * L.pl + o] * x[o] + offdiag3(L, x, i, j, k));
+    const long long sy = L.ld, sz = (long long)L.ld * L.n;
+    T s = 0;
+#pragma unroll
+    for (int t = 0; t < 13; t++) {
+        const int m = (off_x(t) != 0) | ((off_y(t) != 0) << 1) | ((off_z(t) != 0) << 2);
+        if ((col ^ m) > col) {
+            const long long d = off_x(t) + sy * off_y(t) + sz * off_z(t);
+            s += L.A[(long long)t * L.pl + o] * x[o + d];
+            s += L.A[(long long)t * L.pl + o - d] * x[o - d];
+        }
+    }
+    r[o] = -s;
 }
 
 // b_c(K) = sum over the 27 fine neighbours f = 2K + d of P(f, K) r_f, in the
@@ -335,7 +352,7 @@ bmg_status vcycle3d_impl(Ctx& c, const T* b0, T* x0, T* xout) {
         const double N = dofs3(c, l);
         for (int col = 0; col < 8; col++) BMG_TRY(colour_sweep<T>(c, l, v, bl(l), xl(l), col, h));
         prof_begin(c, BMG_PROF_RESIDUAL, l);
-        k_residual3d<T><<<g3(F.n, F.n, F.n), 64, 0, s>>>(v, bl(l), xl(l), (T*)F.r);
+        k_residual3d_sweep<T><<<g3(F.n, F.n, F.n), 64, 0, s>>>(v, xl(l), (T*)F.r);
         prof_end(c, BMG_PROF_RESIDUAL, l, (c.ns + 3) * sz * N);
         prof_begin(c, BMG_PROF_RESTRICT, l);
         k_restrict3d<T><<<g3(K.n, K.n, K.n), 64, 0, s>>>(F.n, F.ld, (const T*)F.r, P_of<T>(F), K.n, K.ld, K.plane,
