@@ -202,6 +202,16 @@ bmg_status bmg_adjoint_grad(bmg_ctx* ctx, const double* coords, const double* u,
                             const double* dLdu, double* lambda, double* dLdkappa,
                             double tol, int maxit, bmg_info* info);
 
+/* The per-cell contraction of bmg_adjoint_grad alone, for an adjoint
+   lambda the caller has already solved for (e.g. with bmg_solve_many over a
+   batch of problems): dLdkappa[e] = -lambda_e^T K_e^0 u_e, the derivative
+   of lambda^T A(kappa) u in kappa_e, A linear in each cell's coefficient
+   (Sec. 2, the assembly of Eq. pde by elements).  Arguments, layout and
+   requirements as for bmg_adjoint_grad; runs on the context's stream and
+   returns BMG_ERR_MAP_FOLDED if a Jacobian determinant is not positive. */
+bmg_status bmg_adjoint_cells(bmg_ctx* ctx, const double* coords, const double* u,
+                             const double* lambda, double* dLdkappa);
+
 /* Hierarchy queries (for diagnostics and parity checks). */
 int bmg_levels(const bmg_ctx* ctx);
 int bmg_level_n(const bmg_ctx* ctx, int level);

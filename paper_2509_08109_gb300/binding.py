@@ -78,6 +78,7 @@ def load() -> ctypes.CDLL:
         "bmg_vcycle": ([P, P, P], I),
         "bmg_solve": ([P, P, P, D, I, ctypes.POINTER(_Info)], I),
         "bmg_adjoint_grad": ([P, P, P, P, P, P, D, I, ctypes.POINTER(_Info)], I),
+        "bmg_adjoint_cells": ([P, P, P, P, P], I),
         "bmg_solve_many": ([P, I, I, P, P, D, I, P], I),
         "bmg_levels": ([P], I),
         "bmg_level_n": ([P, I], I),
@@ -106,7 +107,7 @@ def load() -> ctypes.CDLL:
 def exported_symbols() -> list:
     return ["bmg_default_opts", "bmg_create", "bmg_workspace_bytes", "bmg_attach", "bmg_assemble",
             "bmg_set_stencil", "bmg_setup", "bmg_vcycle", "bmg_solve", "bmg_solve_many", "bmg_adjoint_grad",
-            "bmg_levels",
+            "bmg_adjoint_cells", "bmg_levels",
             "bmg_level_n", "bmg_get_stencil", "bmg_get_interp", "bmg_launch_count", "bmg_get_tiles",
             "bmg_set_tiles", "bmg_autotune", "bmg_profile",
             "bmg_profile_read", "bmg_destroy", "bmg_status_str", "bmg_assemble_noalloc", "bmg_assemble_tensor",
@@ -317,6 +318,17 @@ class Solver:
                                            float(tol), int(maxit), ctypes.byref(info)), "bmg_adjoint_grad")
         return lam, dk, SolveInfo(info.iterations, info.levels, info.relres, info.true_relres, info.rho,
                                   info.grid_complexity, info.operator_complexity, info.status)
+
+    def adjoint_cells(self, u, lam) -> torch.Tensor:
+        """bmg_adjoint_cells: dL/dkappa per cell, -lambda_e^T K_e^0 u_e, for
+        an adjoint lambda solved elsewhere (e.g. by solve_many)."""
+        u = self._dev(torch.as_tensor(u))
+        lam = self._dev(torch.as_tensor(lam))
+        dk = torch.empty((self.n - 1,) * self.dim, dtype=torch.float64, device=self.device)
+        with torch.cuda.device(self.device):
+            _check(load().bmg_adjoint_cells(self._h, _ptr(self._coords), _ptr(u), _ptr(lam), _ptr(dk)),
+                   "bmg_adjoint_cells")
+        return dk
 
     # ------------------------------------------------------------ tile shapes
     def tiles(self) -> list:

@@ -87,6 +87,8 @@ size_t carve(Ctx& c, char* base) {
     c.stage_out = (double*)take(sizeof(double) * nn);
     c.partials = (double*)take(sizeof(double) * kMaxBlocks);
     c.st = (KState*)take(sizeof(KState));
+    const size_t tp = tail_pack_bytes(c);
+    c.tail_pack = tp ? take(tp) : nullptr;
     return align256(off);
 }
 
@@ -491,6 +493,7 @@ bmg_status bmg_setup(bmg_ctx* ctx) {
     BMG_TRY(reset_state(c));
     for (int l = 0; l < c.nlev - 1; l++) BMG_TRY(c.dim == 2 ? setup_level2d(c, l) : setup_level3d(c, l));
     BMG_TRY(demote_levels(c));
+    if (c.use_fused) BMG_TRY(tail_pack(c));
     if (c.rs32) BMG_TRY(k_row_sums32(c));
     BMG_TRY(pspmv_prepare(c));
     KState h;
@@ -549,6 +552,22 @@ bmg_status bmg_adjoint_grad(bmg_ctx* ctx, const double* coords, const double* u,
     BMG_TRY(read_state(c, h));
     if (h.err && st == BMG_OK) st = (bmg_status)h.err;
     return st;
+}
+
+bmg_status bmg_adjoint_cells(bmg_ctx* ctx, const double* coords, const double* u, const double* lambda,
+                             double* dLdkappa) {
+    BMG_TRY(check_ready(ctx));
+    if (!coords || !u || !lambda || !dLdkappa) return BMG_ERR_ARG;
+    Ctx& c = ctx->c;
+    if (!c.have_setup || c.op_tensor) return BMG_ERR_STATE;
+    if (!is_device_ptr(coords) || !is_device_ptr(u) || !is_device_ptr(lambda) || !is_device_ptr(dLdkappa))
+        return BMG_ERR_ARG;
+    BMG_CUDA(cudaMemsetAsync(&c.st->err, 0, sizeof(c.st->err), c.stream));
+    BMG_TRY(c.dim == 2 ? adjoint_cells2d(c, coords, u, lambda, dLdkappa)
+                       : adjoint_cells3d(c, coords, u, lambda, dLdkappa));
+    KState h;
+    BMG_TRY(read_state(c, h));
+    return h.err ? (bmg_status)h.err : BMG_OK;
 }
 
 bmg_status bmg_solve_many(bmg_ctx* const* ctxs, int count, int nrhs, const double* const* b, double* const* x,

@@ -109,6 +109,7 @@ struct Ctx {
     bool prof_on = false;
     ProfSlot prof[BMG_PROF_KINDS];
     bool use_fused = false;       // streaming V-cycle kernels (2-D)
+    void* tail_pack = nullptr;    // 2-D: operators and weights of the tail levels, packed (tail2d.cu)
     // CUDA graphs of one inner/outer iteration (two, for the alternating z buffers)
     cudaStream_t cap_stream = nullptr;
     cudaGraphExec_t it_exec[2] = {nullptr, nullptr};
@@ -306,6 +307,8 @@ __host__ __device__ inline long long cb_offset(int n, int col) {
 constexpr int kTailMaxN = 33;
 int tail_first_level(const Ctx& c);
 size_t tail_smem_bytes(const Ctx& c, int t);
+size_t tail_pack_bytes(const Ctx& c);             // packed tail operators (0 outside 2-D)
+bmg_status tail_pack(Ctx& c);                     // fills c.tail_pack (bmg_setup)
 bmg_status tail_vcycle(Ctx& c, int t);
 // z32 = M r32 (FP32 in and out); with zold and the streaming kernels the
 // finest up kernel also forms r.z, r.z_old and the flexible-CG beta

@@ -33,49 +33,12 @@
 
 #include "common.cuh"
 #include "fused2d.cuh"
+#include "mbar.cuh"
 
 namespace bmg {
 namespace {
 
-constexpr unsigned long long kWaitNs = 2000000000ull;   // 2 s
-
-__device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
-
-__device__ __forceinline__ void mbar_init(uint64_t* b, uint32_t count) {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(b)), "r"(count) : "memory");
-}
-
-__device__ __forceinline__ void fence_mbar_init() { asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory"); }
-
-__device__ __forceinline__ void mbar_expect_tx(uint64_t* b, uint32_t bytes) {
-    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(b)), "r"(bytes) : "memory");
-}
-
-__device__ __forceinline__ bool mbar_try(uint64_t* b, uint32_t parity) {
-    uint32_t ok;
-    asm volatile(
-        "{\n\t.reg .pred p;\n\t"
-        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
-        "selp.u32 %0, 1, 0, p;\n\t}"
-        : "=r"(ok)
-        : "r"(smem_u32(b)), "r"(parity)
-        : "memory");
-    return ok != 0;
-}
-
-__device__ __forceinline__ unsigned long long gtimer() {
-    unsigned long long t;
-    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
-    return t;
-}
-
-__device__ bool mbar_wait(uint64_t* b, uint32_t parity) {
-    if (mbar_try(b, parity)) return true;
-    const unsigned long long t0 = gtimer();
-    while (!mbar_try(b, parity))
-        if (gtimer() - t0 > kWaitNs) return false;
-    return true;
-}
+using mbar::smem_u32;
 
 __device__ __forceinline__ void tma2d(void* dst, const CUtensorMap* m, uint64_t* bar, int x, int y) {
     asm volatile(
@@ -167,7 +130,7 @@ struct Ring {
 template <int RP>
 __device__ __forceinline__ bool wait_pairs(uint64_t* bars, int qa, int qb) {
     bool mine = true;
-    for (int q = qa; q < qb; q++) mine = mine && mbar_wait(bars + ((unsigned)q % RP), ((unsigned)q / RP) & 1u);
+    for (int q = qa; q < qb; q++) mine = mine && mbar::wait(bars + ((unsigned)q % RP), ((unsigned)q / RP) & 1u);
     return __syncthreads_and(mine) != 0;
 }
 
@@ -249,13 +212,13 @@ __global__ void __launch_bounds__((WC + 8) * K, sizeof(T) == 4 ? 3 : 1) k_vdown2
     auto issue = [&](int q) {
         const int s = (int)((unsigned)q % RP), Jp = rg.q0 + q;
         uint64_t* bar = rg.bars + s;
-        mbar_expect_tx(bar, txb);
+        mbar::expect_tx(bar, txb);
         tma3d(rg.pA + s * L.sA, &tmA, bar, x0, 2 * Jp + 1, 0);
         tma2d(rg.pF + s * L.sF, &tmF, bar, x0, 2 * Jp + 1);
     };
     if (lead) {
-        for (int s = 0; s < RP; s++) mbar_init(rg.bars + s, 1);
-        fence_mbar_init();
+        for (int s = 0; s < RP; s++) mbar::init(rg.bars + s, 1);
+        mbar::fence_init();
     }
     __syncthreads();
     int issued = npairs < RP ? npairs : RP, waited = 0;
@@ -406,7 +369,7 @@ __global__ void __launch_bounds__((WC + 8) * K, sizeof(T) == 4 ? 3 : 1) k_vdown2
     if (!ok) {
         if (lead) {
             set_err(p.st, BMG_ERR_TIMEOUT);
-            for (int q = waited; q < issued; q++) mbar_wait(rg.bars + ((unsigned)q % RP), ((unsigned)q / RP) & 1u);
+            for (int q = waited; q < issued; q++) mbar::wait(rg.bars + ((unsigned)q % RP), ((unsigned)q / RP) & 1u);
         }
         __syncthreads();
     }
@@ -448,15 +411,15 @@ __global__ void __launch_bounds__((WC + 8) * K, sizeof(T) == 4 ? 3 : 1) k_vup2d(
     auto issue = [&](int q) {
         const int s = (int)((unsigned)q % RP), Jp = rg.q0 + q;
         uint64_t* bar = rg.bars + s;
-        mbar_expect_tx(bar, txb);
+        mbar::expect_tx(bar, txb);
         tma3d(rg.pA + s * L.sA, &tmA, bar, x0, 2 * Jp + 1, 0);
         tma2d(rg.pF + s * L.sF, &tmF, bar, x0, 2 * Jp + 1);
         tma2d(rg.pXp + s * L.sXp, &tmX, bar, x0, 2 * Jp + 1);
         tma2d(rg.pC + s * L.sC, &tmC, bar, xc0, Jp + 1);
     };
     if (lead) {
-        for (int s = 0; s < RP; s++) mbar_init(rg.bars + s, 1);
-        fence_mbar_init();
+        for (int s = 0; s < RP; s++) mbar::init(rg.bars + s, 1);
+        mbar::fence_init();
     }
     __syncthreads();
     int issued = npairs < RP ? npairs : RP, waited = 0;
@@ -610,7 +573,7 @@ __global__ void __launch_bounds__((WC + 8) * K, sizeof(T) == 4 ? 3 : 1) k_vup2d(
     if (!ok) {
         if (lead) {
             set_err(p.st, BMG_ERR_TIMEOUT);
-            for (int q = waited; q < issued; q++) mbar_wait(rg.bars + ((unsigned)q % RP), ((unsigned)q / RP) & 1u);
+            for (int q = waited; q < issued; q++) mbar::wait(rg.bars + ((unsigned)q % RP), ((unsigned)q / RP) & 1u);
         }
         __syncthreads();
         return;

@@ -54,6 +54,29 @@ __device__ __forceinline__ T apply_row(const T* __restrict__ A, long long pl, in
     }
 }
 
+// True when every x_j row o couples to is +-0 (bit test, no FP64 op): then
+// (A x)_o is zero and the FP64 products can be skipped, e.g. for a zero
+// initial guess, where the residual is b itself.
+template <int DIM, typename T>
+__device__ __forceinline__ bool row_x_zero(const T* __restrict__ x, int ld, int n, long long o) {
+    auto bits = [](T v) -> unsigned long long {
+        return sizeof(T) == 8 ? (unsigned long long)__double_as_longlong((double)v) << 1
+                              : (unsigned long long)__float_as_uint((float)v) << 1;
+    };
+    unsigned long long m = bits(x[o]);
+    if (DIM == 2) {
+        m |= bits(x[o - 1]) | bits(x[o + 1]) | bits(x[o - ld]) | bits(x[o + ld]);
+        m |= bits(x[o - ld - 1]) | bits(x[o + ld + 1]) | bits(x[o + ld - 1]) | bits(x[o - ld + 1]);
+    } else {
+#pragma unroll
+        for (int t = 0; t < 13; t++) {
+            const long long d = d3(t, ld, n);
+            m |= bits(x[o + d]) | bits(x[o - d]);
+        }
+    }
+    return m == 0;
+}
+
 // (A x)_i in difference form: s_i x_i + sum_{j != i} a_ij (x_j - x_i), with
 // the row sums s_i computed in FP64.  The operator's rows nearly sum to zero,
 // so the plain FP32 product loses the smooth part of A x to cancellation; the
@@ -128,7 +151,7 @@ __global__ void k_unpack_t(int n, int ld, const double* __restrict__ src, double
 }
 
 // ---------------------------------------------------------------- FP64 outer CG
-// r = b - A x ; st.rr = ||r||^2
+// r = b - A x ; st.rr = ||r||^2 (rows with a zero x neighbourhood: r = b)
 template <int DIM>
 __global__ void k_residual64(RowGrid<DIM> g, const double* __restrict__ A, long long pl, const double* __restrict__ b,
                              const double* __restrict__ x, double* __restrict__ r, double* partials, KState* st) {
@@ -136,7 +159,8 @@ __global__ void k_residual64(RowGrid<DIM> g, const double* __restrict__ A, long 
     FOR_ROWS(g) {
         const long long k = (long long)r_ * g.ld + i_;
         double v = 0.0;
-        if (g.row_inner(r_) && i_ >= 1 && i_ <= g.n - 2) v = b[k] - apply_row<DIM, double>(A, pl, g.ld, g.n, x, k);
+        if (g.row_inner(r_) && i_ >= 1 && i_ <= g.n - 2)
+            v = row_x_zero<DIM, double>(x, g.ld, g.n, k) ? b[k] : b[k] - apply_row<DIM, double>(A, pl, g.ld, g.n, x, k);
         r[k] = v;
         acc += v * v;
     }
@@ -228,6 +252,8 @@ __global__ void k_p_update64(long long tot, const double* __restrict__ z, double
 
 // ---------------------------------------------------------------- refinement (FP32 inner CG)
 // r32 = (float)(b - A x), ||r||^2 in FP64; resets the inner CG to its first step.
+// Rows whose x neighbourhood is zero take r = b without the FP64 products
+// (the FP64 rate, not HBM, bounds this kernel otherwise).
 template <int DIM>
 __global__ void k_residual_to32_t(RowGrid<DIM> g, const double* __restrict__ A, long long pl,
                                   const double* __restrict__ b, const double* __restrict__ x,
@@ -236,7 +262,8 @@ __global__ void k_residual_to32_t(RowGrid<DIM> g, const double* __restrict__ A, 
     FOR_ROWS(g) {
         const long long k = (long long)r_ * g.ld + i_;
         double v = 0.0;
-        if (g.row_inner(r_) && i_ >= 1 && i_ <= g.n - 2) v = b[k] - apply_row<DIM, double>(A, pl, g.ld, g.n, x, k);
+        if (g.row_inner(r_) && i_ >= 1 && i_ <= g.n - 2)
+            v = row_x_zero<DIM, double>(x, g.ld, g.n, k) ? b[k] : b[k] - apply_row<DIM, double>(A, pl, g.ld, g.n, x, k);
         r32[k] = (float)v;
         acc += v * v;
     }
