@@ -35,7 +35,8 @@ METRIC = "DoF/s to 1e-10 rel. residual, FP32-precond vs FP64 on same GB300; % HB
 UNIT = "DoF/s"
 TOL = 1e-10
 KERNEL_FILES = ["paper_2509_08109_gb300/csrc/vcycle.cu", "paper_2509_08109_gb300/csrc/krylov.cu",
-                "paper_2509_08109_gb300/csrc/fused2d.cu"]
+                "paper_2509_08109_gb300/csrc/fused2d.cu", "paper_2509_08109_gb300/csrc/fused2d.cuh",
+                "paper_2509_08109_gb300/csrc/mbar.cuh"]
 
 
 def parse():

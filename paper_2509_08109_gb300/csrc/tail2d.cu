@@ -28,7 +28,7 @@
 namespace bmg {
 namespace {
 
-constexpr int kTailThreads = 1024;
+constexpr int kTailThreads = 256;      // one thread per node of a colour at n = 33
 constexpr unsigned kTailChunk = 16384;    // bytes per bulk copy
 
 struct TailArgs {

@@ -153,7 +153,11 @@ bmg_status fused_prepare(Ctx& c) {
 // CUDA events, best of reps) and keeps the fastest.  Candidates: each legal
 // column width with the modelled row count, half and twice that count.
 // Runs the kernels on the context's scratch vectors (they hold no state
-// between V-cycles).
+// between V-cycles).  Before every timed rep the host staging buffers
+// (2 n^d doubles) are overwritten, which evicts the level's data from L2
+// when the problem is larger than L2: inside a V-cycle the finer levels
+// have evicted it too, and a warm L2 would hide the halo re-reads of narrow
+// strips.
 bmg_status fused_autotune(Ctx& c, int reps, double* best_ms_total) {
     if (!c.use_fused) return BMG_OK;
     const bool f32 = c.opts.precision == BMG_PREC_FP32;
@@ -164,6 +168,8 @@ bmg_status fused_autotune(Ctx& c, int reps, double* best_ms_total) {
     double total = 0.0;
     const bool ir = c.opts.outer == BMG_OUTER_REFINEMENT;
     void* out0 = ir ? (void*)c.z32[0] : (void*)c.z[0];
+    size_t stage_bytes = sizeof(double);
+    for (int d = 0; d < c.dim; d++) stage_bytes *= (size_t)c.lev[0].n;
     for (int l = 0; l + 1 < c.nlev; l++) {
         const int m = c.lev[l + 1].n - 1;
         int best_wc = c.fused[l].wc, best_hc = c.fused[l].hc;
@@ -182,6 +188,8 @@ bmg_status fused_autotune(Ctx& c, int reps, double* best_ms_total) {
                 BMG_TRY(fused_up(c, l, out, ir));
                 float tbest = -1.f;
                 for (int r = 0; r < reps; r++) {
+                    BMG_CUDA(cudaMemsetAsync(c.stage_in, 0, stage_bytes, c.stream));
+                    BMG_CUDA(cudaMemsetAsync(c.stage_out, 0, stage_bytes, c.stream));
                     BMG_CUDA(cudaEventRecord(e0, c.stream));
                     BMG_TRY(fused_down(c, l, ir));
                     BMG_TRY(fused_up(c, l, out, ir));
