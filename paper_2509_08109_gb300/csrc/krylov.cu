@@ -493,26 +493,34 @@ __global__ void __launch_bounds__(kThreads) k_pspmv2d_tiled(int n, int ld, long 
     const int i = i0 + t;
     const bool act = i <= n - 2;
     const int il = i0 - 1, ir = i0 + TW;    // halo columns (thread 0: left, thread 1: right)
+    // raw loads only: p = z + beta p_old is formed when the row is stored,
+    // a step later, so no instruction waits on these loads before the
+    // current row has been computed
     struct Row {
-        float p, w, sw, nw, s, r, hp, hw, hsw, hnw;
+        float z, po, w, sw, nw, s, r, hz, hpo, hw, hsw, hnw;
     };
     auto load = [&](int j, Row& v) {
-        v = Row{0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+        v = Row{0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
         if (j < 1 || j > n - 2) return;
         const long long kr = (long long)j * ld;
         if (act) {
             const long long k = kr + i;
-            v.p = z[k] + beta * pold[k];
+            v.z = z[k];
+            v.po = pold[k];
             v.w = A[W2 * pl + k];
             v.sw = A[SW2 * pl + k];
             v.nw = A[NW2 * pl + k];
             v.s = A[S2 * pl + k];
             v.r = rs[k];
         }
-        if (t == 0 && il >= 1) v.hp = z[kr + il] + beta * pold[kr + il];
+        if (t == 0 && il >= 1) {
+            v.hz = z[kr + il];
+            v.hpo = pold[kr + il];
+        }
         if (t == 1 && ir <= n - 2) {
             const long long k = kr + ir;
-            v.hp = z[k] + beta * pold[k];
+            v.hz = z[k];
+            v.hpo = pold[k];
             v.hw = A[W2 * pl + k];
             v.hsw = A[SW2 * pl + k];
             v.hnw = A[NW2 * pl + k];
@@ -520,13 +528,13 @@ __global__ void __launch_bounds__(kThreads) k_pspmv2d_tiled(int n, int ld, long 
     };
     auto put = [&](int j, const Row& v) {
         const int sl = j & 3;
-        sP[sl][t + 1] = v.p;
+        sP[sl][t + 1] = v.z + beta * v.po;
         sW[sl][t] = v.w;
         sSW[sl][t] = v.sw;
         sNW[sl][t] = v.nw;
-        if (t == 0) sP[sl][0] = v.hp;
+        if (t == 0) sP[sl][0] = v.hz + beta * v.hpo;
         if (t == 1) {
-            sP[sl][TW + 1] = v.hp;
+            sP[sl][TW + 1] = v.hz + beta * v.hpo;
             sW[sl][TW] = v.hw;
             sSW[sl][TW] = v.hsw;
             sNW[sl][TW] = v.hnw;
@@ -621,7 +629,8 @@ __global__ void __launch_bounds__(kThreads) k_pspmv3d_tiled(int n, int ld, long 
     const int k1 = min(k0 + H, n - 1);
     const long long sz = (long long)ld * n;
     // the thread's halo positions: (hi, hj) -> node (i0 - 1 + hi, j0 - 1 + hj)
-    float ra[kP3Per][13], rp[kP3Per];
+    // raw loads; p = z + beta p_old is formed in put(), a step later
+    float ra[kP3Per][13], rz[kP3Per], rpo[kP3Per];
     auto load = [&](int k) {
 #pragma unroll
         for (int u = 0; u < kP3Per; u++) {
@@ -632,7 +641,8 @@ __global__ void __launch_bounds__(kThreads) k_pspmv3d_tiled(int n, int ld, long 
             const long long o = in ? (long long)i + (long long)ld * j + sz * k : 0;
 #pragma unroll
             for (int t = 0; t < 13; t++) ra[u][t] = in ? A[t * pl + o] : 0.f;
-            rp[u] = in ? z[o] + beta * pold[o] : 0.f;
+            rz[u] = in ? z[o] : 0.f;
+            rpo[u] = in ? pold[o] : 0.f;
         }
     };
     auto put = [&](int k) {
@@ -644,7 +654,7 @@ __global__ void __launch_bounds__(kThreads) k_pspmv3d_tiled(int n, int ld, long 
             if (h >= kP3A) continue;
 #pragma unroll
             for (int t = 0; t < 13; t++) a[t * kP3A + h] = ra[u][t];
-            pp[h] = rp[u];
+            pp[h] = rz[u] + beta * rpo[u];
         }
     };
     const int ti_ = tid % kP3I, tj_ = tid / kP3I;

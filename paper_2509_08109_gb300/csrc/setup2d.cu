@@ -84,8 +84,6 @@ __device__ bool element2d(const double* __restrict__ X, const double* __restrict
     return ok;
 }
 
-// Gather assembly: one thread per node sums the element matrices of its
-// four cells (no atomics).  Couplings to boundary nodes are dropped.
 // coefficient of cell e: kappa[e], or the tensor planes D11, D12, D22 (ne cells each)
 template <bool TENSOR>
 __device__ __forceinline__ auto cell_coef2(const double* __restrict__ c, long long ne, long long e) {
@@ -95,39 +93,74 @@ __device__ __forceinline__ auto cell_coef2(const double* __restrict__ c, long lo
         return Scalar2{c[e]};
 }
 
+// Gather assembly (no atomics), tiled so that each cell's element matrix is
+// formed once per tile rather than once per node of the cell: a CTA of 256
+// threads owns kAsmTX x kAsmTY nodes, first forms the element matrices of
+// the (kAsmTX+1) x (kAsmTY+1) cells around them (one cell per thread) into
+// shared memory, then each node sums its four cells' entries in a fixed
+// order.  Couplings to boundary nodes are dropped; boundary rows are zero.
+constexpr int kAsmTX = 31, kAsmTY = 7;
+constexpr int kAsmCX = kAsmTX + 1, kAsmCells = (kAsmTX + 1) * (kAsmTY + 1);   // 256
+// the ten entries of a cell matrix the gather uses
+enum AsmEntry { E00, E11, E22, E33, E10, E12, E20, E30, E31, E32, NE2 };
+
 template <bool TENSOR>
-__global__ void k_assemble2d(int n, int ld, long long pl, const double* __restrict__ coords,
-                             const double* __restrict__ kappa, double* __restrict__ A, KState* st) {
+__global__ void __launch_bounds__(kAsmCells) k_assemble2d(int n, int ld, long long pl,
+                                                          const double* __restrict__ coords,
+                                                          const double* __restrict__ kappa, double* __restrict__ A,
+                                                          KState* st) {
+    __shared__ double sK[NE2][kAsmCells];
     const long long ne = (long long)(n - 1) * (n - 1);
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    const int j = blockIdx.y;
-    if (i >= n) return;
+    const int i0 = blockIdx.x * kAsmTX, j0 = blockIdx.y * kAsmTY;    // first node of the tile
+    const int t = threadIdx.x;
+    {
+        // cell (ci, cj) lies between nodes ci, ci+1 and cj, cj+1
+        const int ci = i0 - 1 + t % kAsmCX, cj = j0 - 1 + t / kAsmCX;
+        if (ci >= 0 && cj >= 0 && ci <= n - 2 && cj <= n - 2) {
+            double K[4][4];
+            const double* X = coords;
+            const double* Y = coords + (long long)n * n;
+            if (!element2d(X, Y, n, ci, cj, cell_coef2<TENSOR>(kappa, ne, (long long)cj * (n - 1) + ci), K))
+                set_err(st, BMG_ERR_MAP_FOLDED);
+            sK[E00][t] = K[0][0];
+            sK[E11][t] = K[1][1];
+            sK[E22][t] = K[2][2];
+            sK[E33][t] = K[3][3];
+            sK[E10][t] = K[1][0];
+            sK[E12][t] = K[1][2];
+            sK[E20][t] = K[2][0];
+            sK[E30][t] = K[3][0];
+            sK[E31][t] = K[3][1];
+            sK[E32][t] = K[3][2];
+        }
+    }
+    __syncthreads();
+    if (t >= kAsmTX * kAsmTY) return;
+    const int i = i0 + t % kAsmTX, j = j0 + t / kAsmTX;
+    if (i >= n || j >= n) return;
     const long long o = (long long)j * ld + i;
     double C = 0, W = 0, S = 0, SW = 0, NW = 0;
     if (i >= 1 && j >= 1 && i <= n - 2 && j <= n - 2) {
-        const double* X = coords;
-        const double* Y = coords + (long long)n * n;
-        double K[4][4];
-        bool ok = true;
+        // shared-memory slot of the cell whose lower-left node is (ci, cj)
+        auto cell = [&](int ci, int cj) { return (ci - i0 + 1) + kAsmCX * (cj - j0 + 1); };
         // cell (i-1,j-1): node is corner 3
-        ok &= element2d(X, Y, n, i - 1, j - 1, cell_coef2<TENSOR>(kappa, ne, (long long)(j - 1) * (n - 1) + (i - 1)), K);
-        C += K[3][3];
-        if (i - 1 >= 1) W += K[3][2];
-        if (j - 1 >= 1) S += K[3][1];
-        if (i - 1 >= 1 && j - 1 >= 1) SW += K[3][0];
+        int e = cell(i - 1, j - 1);
+        C += sK[E33][e];
+        if (i - 1 >= 1) W += sK[E32][e];
+        if (j - 1 >= 1) S += sK[E31][e];
+        if (i - 1 >= 1 && j - 1 >= 1) SW += sK[E30][e];
         // cell (i,j-1): node is corner 2
-        ok &= element2d(X, Y, n, i, j - 1, cell_coef2<TENSOR>(kappa, ne, (long long)(j - 1) * (n - 1) + i), K);
-        C += K[2][2];
-        if (j - 1 >= 1) S += K[2][0];
+        e = cell(i, j - 1);
+        C += sK[E22][e];
+        if (j - 1 >= 1) S += sK[E20][e];
         // cell (i-1,j): node is corner 1
-        ok &= element2d(X, Y, n, i - 1, j, cell_coef2<TENSOR>(kappa, ne, (long long)j * (n - 1) + (i - 1)), K);
-        C += K[1][1];
-        if (i - 1 >= 1) W += K[1][0];
-        if (i - 1 >= 1 && j + 1 <= n - 2) NW += K[1][2];
+        e = cell(i - 1, j);
+        C += sK[E11][e];
+        if (i - 1 >= 1) W += sK[E10][e];
+        if (i - 1 >= 1 && j + 1 <= n - 2) NW += sK[E12][e];
         // cell (i,j): node is corner 0
-        ok &= element2d(X, Y, n, i, j, cell_coef2<TENSOR>(kappa, ne, (long long)j * (n - 1) + i), K);
-        C += K[0][0];
-        if (!ok) set_err(st, BMG_ERR_MAP_FOLDED);
+        e = cell(i, j);
+        C += sK[E00][e];
     }
     A[C2 * pl + o] = C;
     A[W2 * pl + o] = W;
@@ -135,6 +168,8 @@ __global__ void k_assemble2d(int n, int ld, long long pl, const double* __restri
     A[SW2 * pl + o] = SW;
     A[NW2 * pl + o] = NW;
 }
+
+inline dim3 grid_asm(int n) { return dim3(cdiv(n, kAsmTX), cdiv(n, kAsmTY)); }
 
 // Full 9-entry rows -> symmetric half planes; couplings to boundary nodes
 // and boundary rows are forced to zero.
@@ -386,7 +421,7 @@ inline dim3 grid_rows(int ni, int nj) { return dim3(cdiv(ni, 128), nj); }
 
 bmg_status assemble2d(Ctx& c, const double* coords, const double* kappa) {
     Level& L = c.lev[0];
-    k_assemble2d<false><<<grid_rows(L.n, L.n), 128, 0, c.stream>>>(L.n, L.ld, L.plane, coords, kappa, L.A64, c.st);
+    k_assemble2d<false><<<grid_asm(L.n), kAsmCells, 0, c.stream>>>(L.n, L.ld, L.plane, coords, kappa, L.A64, c.st);
     c.launches++;
     BMG_CUDA(cudaGetLastError());
     return BMG_OK;
@@ -396,7 +431,7 @@ bmg_status assemble2d(Ctx& c, const double* coords, const double* kappa) {
 // storage: half planes A (row length ld, plane stride pl) and error word st.
 bmg_status assemble_export2d(int n, int ld, long long pl, const double* coords, const double* kappa, double* A,
                              KState* st, double* out, cudaStream_t s) {
-    k_assemble2d<false><<<grid_rows(n, n), 128, 0, s>>>(n, ld, pl, coords, kappa, A, st);
+    k_assemble2d<false><<<grid_asm(n), kAsmCells, 0, s>>>(n, ld, pl, coords, kappa, A, st);
     BMG_CUDA(cudaGetLastError());
     k_export_stencil2d<<<grid_rows(n, n), 128, 0, s>>>(Sten2<double>{A, ld, pl}, n, out);
     BMG_CUDA(cudaGetLastError());
@@ -405,7 +440,7 @@ bmg_status assemble_export2d(int n, int ld, long long pl, const double* coords, 
 
 bmg_status assemble_tensor2d(Ctx& c, const double* coords, const double* D) {
     Level& L = c.lev[0];
-    k_assemble2d<true><<<grid_rows(L.n, L.n), 128, 0, c.stream>>>(L.n, L.ld, L.plane, coords, D, L.A64, c.st);
+    k_assemble2d<true><<<grid_asm(L.n), kAsmCells, 0, c.stream>>>(L.n, L.ld, L.plane, coords, D, L.A64, c.st);
     c.launches++;
     BMG_CUDA(cudaGetLastError());
     return BMG_OK;
