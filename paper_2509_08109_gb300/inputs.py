@@ -339,3 +339,68 @@ def identity_coefficient(n: int, kind: str, seed: int = 0) -> Problem:
         raise ValueError(kind)
     f = rhs_uniform(rng, (n, n))
     return Problem(f"identity_{kind}_n{n}", 2, n, coords, kappa, f)
+
+
+# ------------------------------------------------------------------ physical meshes
+@dataclass
+class Mesh:
+    """A P1 triangulation of a physical domain and the images of its
+    vertices in the computational square.
+
+    xy:        (nv, 2) physical vertex coordinates
+    st:        (nv, 2) computational coordinates T(xy) of the vertices
+    tri:       (nt, 3) int32 vertex indices, counter-clockwise in both spaces
+    dirichlet: (nv,) bool, boundary vertices (eliminated)
+    kappa:     (nt,) diffusion coefficient per triangle
+    f:         (nv,) load vector, U[-1, 1] on interior vertices, 0 on the boundary
+    """
+    name: str
+    xy: np.ndarray
+    st: np.ndarray
+    tri: np.ndarray
+    dirichlet: np.ndarray
+    kappa: np.ndarray
+    f: np.ndarray
+
+
+def annulus_mesh(nr: int, nt: int, jitter: float = 0.3, seed: int = 8) -> Mesh:
+    """Jittered polar triangulation of the quarter annulus r in [1/2, 1],
+    theta in [0, pi/2] (the domain of coords_quarter_annulus): nr x nt
+    vertices on the lattice r_k = 1/2 + k / (2 (nr-1)), theta_l = pi l /
+    (2 (nt-1)); interior vertices moved by up to `jitter` lattice spacings
+    in r and theta (uniform, seed); each lattice quad split along the
+    diagonal (k+l) % 2 selects.  T maps (r, theta) to s = 2 r - 1,
+    t = 2 theta / pi, so boundary vertices land on the square's sides and
+    the mapped triangles tile [0, 1]^2.  kappa = 1 (the paper's default,
+    D = I); f ~ U[-1, 1] per interior vertex, drawn after the jitter."""
+    rng = np.random.default_rng(seed)
+    k = np.arange(nr)[None, :] * np.ones((nt, 1))
+    l = np.arange(nt)[:, None] * np.ones((1, nr))
+    dr = rng.uniform(-jitter, jitter, size=(nt, nr))
+    dt = rng.uniform(-jitter, jitter, size=(nt, nr))
+    inner = (k > 0) & (k < nr - 1) & (l > 0) & (l < nt - 1)
+    kk = k + np.where(inner, dr, 0.0)
+    ll = l + np.where(inner, dt, 0.0)
+    r = 0.5 + 0.5 * kk / (nr - 1)
+    th = 0.5 * math.pi * ll / (nt - 1)
+    xy = np.stack([r * np.cos(th), r * np.sin(th)], axis=-1).reshape(-1, 2)
+    st = np.stack([2.0 * r - 1.0, 2.0 * th / math.pi], axis=-1).reshape(-1, 2)
+    # exact images on the boundary
+    st = st.copy()
+    kf, lf = k.reshape(-1), l.reshape(-1)
+    st[kf == 0, 0] = 0.0
+    st[kf == nr - 1, 0] = 1.0
+    st[lf == 0, 1] = 0.0
+    st[lf == nt - 1, 1] = 1.0
+    dirichlet = ~inner.reshape(-1)
+    v = lambda kq, lq: lq * nr + kq
+    K, L = np.meshgrid(np.arange(nr - 1), np.arange(nt - 1))
+    K, L = K.reshape(-1), L.reshape(-1)
+    a, b, c, d = v(K, L), v(K + 1, L), v(K + 1, L + 1), v(K, L + 1)   # quad corners, counter-clockwise
+    alt = ((K + L) % 2) == 0
+    t1 = np.where(alt[:, None], np.stack([a, b, c], 1), np.stack([a, b, d], 1))
+    t2 = np.where(alt[:, None], np.stack([a, c, d], 1), np.stack([b, c, d], 1))
+    tri = np.concatenate([t1, t2]).astype(np.int32)
+    f = np.where(dirichlet, 0.0, rng.uniform(-1.0, 1.0, size=nr * nt))
+    kappa = np.ones(tri.shape[0])
+    return Mesh(f"annulus_mesh_{nr}x{nt}", xy, st, tri, dirichlet, kappa, f)
