@@ -54,10 +54,11 @@ def parse():
     ap.add_argument("--no-graphs", action="store_true",
                     help="launch every kernel on the stream instead of replaying the per-iteration CUDA graphs "
                          "(for profilers that replay single kernels)")
-    ap.add_argument("--workload", default="annulus", choices=["annulus", "annulus65", "shell", "batch", "adjoint"],
+    ap.add_argument("--workload", default="annulus", choices=["annulus", "annulus65", "shell", "batch", "adjoint", "aux"],
                     help="annulus: the 4097^2 quarter annulus (default, the headline); annulus65: 65^2 plain; "
                          "shell: 257^3 spherical-shell octant; batch: 512 bump-map problems x 4 rhs; "
-                         "adjoint: 1025^2 annulus, batch 8, forward + adjoint")
+                         "adjoint: 1025^2 annulus, batch 8, forward + adjoint; aux: the auxiliary-space two-grid "
+                         "method on a 1.07 M-vertex P1 mesh of the annulus with the 513^2 grid as coarse level")
     return ap.parse_args()
 
 
@@ -540,6 +541,57 @@ def run_adjoint(args):
     print(json.dumps(out), flush=True)
 
 
+def run_aux(args):
+    """The auxiliary-space two-grid method (Sec. 2.2-2.3) on a jittered P1
+    triangulation of the quarter annulus with about the paper's largest
+    physical size (845 x 1262 = 1,066,390 vertices), the 513^2 structured
+    grid as its coarse level (interior nodes / physical DoF = 0.25, near the
+    paper's coarsening factor 0.28), lumped mass, damped Jacobi 2/3,
+    gamma 1: stationary two-grid cycles to a 1e-10 relative residual."""
+    import torch
+    from paper_2509_08109_gb300 import binding, inputs
+    torch.cuda.set_device(0)
+    m = inputs.annulus_mesh(845, 1262)
+    n = 513
+    coords = inputs.coords_quarter_annulus(n)
+    t0 = time.perf_counter()
+    s = binding.Solver(2, n, precision="fp32", outer="refine", graphs=not args.no_graphs)
+    s.assemble(torch.as_tensor(coords), torch.ones((n - 1, n - 1), dtype=torch.float64)).setup()
+    t1 = time.perf_counter()
+    a = binding.AuxSolver(s, m)
+    torch.cuda.synchronize()
+    t2 = time.perf_counter()
+    f = torch.as_tensor(m.f, device="cuda")
+    dof = int((~m.dirichlet).sum())
+    for _ in range(args.warmup):
+        a.solve(f, tol=TOL)
+    torch.cuda.synchronize()
+    times, infos = [], []
+    launches0 = s.launches
+    for _ in range(args.steps):
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        ev0.record()
+        u, info = a.solve(f, tol=TOL)
+        ev1.record()
+        torch.cuda.synchronize()
+        times.append(ev0.elapsed_time(ev1))
+        infos.append(info)
+    ms = statistics.median(times)
+    out = {"metric": "physical DoF/s to 1e-10 rel. residual (auxiliary-space two-grid, BoxMG coarse level)",
+           "value": dof / (ms * 1e-3), "unit": UNIT, "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+           "ms_per_step": ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+           "dtype": "f64 (physical level) / f32 V-cycle (coarse level)", "data": "synthetic",
+           "config": {"workload": "aux_annulus_p1_845x1262_coarse513", "physical_dof": dof,
+                      "coarse_dof": (n - 2) ** 2, "triangles": int(m.tri.shape[0]), "tol": TOL,
+                      "relaxation": "damped Jacobi 2/3, one pre and one post", "mass": "lumped", "gamma": 1.0,
+                      "timing": "CUDA events around bmg_aux_solve (host loop, one residual read per cycle)"},
+           "cycles": infos[-1].iterations, "true_relres": infos[-1].true_relres, "rho": infos[-1].rho,
+           "coarse_gpu_launches_per_solve": (s.launches - launches0) // args.steps,
+           "setup_s": {"coarse": t1 - t0, "aux_create_and_setup": t2 - t1}}
+    print(json.dumps(out), flush=True)
+
+
 if __name__ == "__main__":
     a = parse()
     if a.impl == "reference":
@@ -554,5 +606,7 @@ if __name__ == "__main__":
         run_single(a, 3, 257, _inp.shell_two_layer(257), "shell_octant_two_layer_n257")
     elif a.workload == "batch":
         run_batch(a)
+    elif a.workload == "aux":
+        run_aux(a)
     else:
         run_adjoint(a)

@@ -300,6 +300,85 @@ const char* bmg_status_str(bmg_status status);
 bmg_status bmg_assemble_noalloc(int dim, int n, const double* coords, const double* kappa, double* stencil,
                                 void* stream);
 
+/* ---------------------------------------------------------------------
+   Auxiliary-space two-grid method (Sec. 2.2 "Setup phase" and "Solution
+   phase", Sec. 2.3, Sec. 2.4): the structured solve above is the coarse
+   level of a two-grid method for the P1 system A_p u_p = f_p on a
+   triangulation of the physical domain.  One cycle:
+     u_p <- u_p + omega D^-1 (f_p - A_p u_p)        (relaxation S: damped Jacobi)
+     r_c  = P^T (f_p - A_p u_p)                     (restriction, Sec. 2.3)
+     e_c  = V-cycle of the coarse context on r_c    (BoxMG on A_c)
+     u_p <- u_p + gamma P e_c                       (prolongation, Sec. 2.4 scaling)
+     u_p <- u_p + omega D^-1 (f_p - A_p u_p)
+   with P = M_p^-1 C (Sec. 2.3): M_p the P1 mass matrix, C the coupled mass
+   C_ij = integral over the computational domain of (phi_p^i o T^-1) phi_c^j
+   |det J_T^-1| (Eq. coupled_mass_comp).  C is accumulated over (triangle,
+   cell) pairs: each mapped triangle (vertices mapped by T, straight edges
+   in computational space) is clipped to each computational cell it
+   overlaps and the pair's 3 x 4 block is integrated exactly over the
+   intersection; |det J| is that of the coarse context's Q1 map.  M_p^-1 is
+   applied with `mass_steps` CG iterations from zero (the paper uses 2), or
+   with the lumped mass (one third of the area around each vertex) when
+   mass_steps is 0.  Dirichlet vertices and the computational boundary are
+   eliminated.  All values are FP64. */
+typedef struct bmg_aux bmg_aux;   /* opaque */
+
+typedef struct {
+    double omega;      /* Jacobi weight of S (default 2/3) */
+    int mass_steps;    /* CG iterations for M_p^-1 (>= 1), or 0 for the lumped mass (default 0) */
+    double gamma;      /* coarse-grid scaling (default 1) */
+} bmg_aux_opts;
+
+void bmg_aux_default_opts(bmg_aux_opts* opts);
+
+/* Builds the host-side structure of the method: interior numbering, the
+   sparsity of A_p, M_p and C, the (triangle, cell) pairs and the
+   deterministic summation lists.  coarse: a 2-D context on which bmg_setup
+   has run; it must outlive the aux object, whose solves use its stream,
+   its V-cycle and its Krylov buffers.  Host arrays, copied: xy (nv x 2
+   physical vertex coordinates), st (nv x 2, their images T(xy) in the
+   computational square [0,1]^2), dirichlet (nv bytes, nonzero =
+   eliminated), tri (ntri x 3 vertex indices, counter-clockwise in both
+   spaces).  opts may be NULL (defaults).
+   Errors: BMG_ERR_ARG (null pointer, vertex index out of range, opts out of
+   range), BMG_ERR_SHAPE (coarse not 2-D, a count too large for 32-bit
+   indices), BMG_ERR_STATE (coarse not set up). */
+bmg_status bmg_aux_create(bmg_ctx* coarse, int nv, const double* xy, const double* st,
+                          const unsigned char* dirichlet, int ntri, const int* tri,
+                          const bmg_aux_opts* opts, bmg_aux** aux);
+
+/* Device workspace the object needs (bytes, 256-byte aligned base). */
+bmg_status bmg_aux_workspace_bytes(const bmg_aux* aux, size_t* bytes);
+
+/* Attaches the workspace and computes A_p, M_p (per-triangle coefficient
+   kappa: device, ntri doubles) and C (coords: device, the coarse grid's
+   2 x n x n nodal coordinates as given to bmg_assemble) on the device, on
+   the coarse context's stream.  Errors: BMG_ERR_WORKSPACE, BMG_ERR_ARG,
+   BMG_ERR_MAP_FOLDED (a triangle of non-positive physical area),
+   BMG_ERR_DEVICE. */
+bmg_status bmg_aux_setup(bmg_aux* aux, void* workspace, size_t bytes, const double* kappa, const double* coords);
+
+/* Stationary two-grid iteration until ||f - A_p u|| <= tol ||f|| over the
+   interior vertices, or maxit cycles.  f, u: device, nv doubles (all
+   vertices); u holds the initial guess on entry and the iterate on exit,
+   with its Dirichlet entries set to zero; f's Dirichlet entries are
+   ignored.  info (may be NULL): cycles in `iterations`, the relative
+   residual in `relres` and `true_relres`.  Errors: BMG_ERR_NOT_CONVERGED
+   (u still holds the last iterate), BMG_ERR_STATE (no setup). */
+bmg_status bmg_aux_solve(bmg_aux* aux, const double* f, double* u, double tol, int maxit, bmg_info* info);
+
+bmg_status bmg_aux_set_gamma(bmg_aux* aux, double gamma);
+
+/* Exports a matrix as CSR into host arrays (each may be NULL to query the
+   sizes): which 0 = A_p, 1 = M_p (rows and columns: interior vertices in
+   increasing vertex order), 2 = C (rows: interior vertices; columns: the
+   coarse grid's interior nodes, as j*n + i).  nrows and nnz are always
+   written; rowptr has nrows+1 entries. */
+bmg_status bmg_aux_export(const bmg_aux* aux, int which, int* nrows, long long* nnz, long long* rowptr, int* col,
+                          double* val);
+
+void bmg_aux_destroy(bmg_aux* aux);
+
 #ifdef __cplusplus
 }
 #endif

@@ -44,6 +44,10 @@ class _Info(ctypes.Structure):
                 ("status", ctypes.c_int), ("refinements", ctypes.c_int)]
 
 
+class _AuxOpts(ctypes.Structure):
+    _fields_ = [("omega", ctypes.c_double), ("mass_steps", ctypes.c_int), ("gamma", ctypes.c_double)]
+
+
 @dataclass
 class SolveInfo:
     iterations: int
@@ -95,6 +99,14 @@ def load() -> ctypes.CDLL:
         "bmg_assemble_noalloc": ([I, I, P, P, P, P], I),
         "bmg_assemble_tensor": ([P, P, P], I),
         "bmg_boundary_rhs": ([P, P, P, P, P], I),
+        "bmg_aux_default_opts": ([ctypes.POINTER(_AuxOpts)], None),
+        "bmg_aux_create": ([P, I, P, P, P, I, P, ctypes.POINTER(_AuxOpts), ctypes.POINTER(P)], I),
+        "bmg_aux_workspace_bytes": ([P, ctypes.POINTER(ctypes.c_size_t)], I),
+        "bmg_aux_setup": ([P, P, ctypes.c_size_t, P, P], I),
+        "bmg_aux_solve": ([P, P, P, D, I, ctypes.POINTER(_Info)], I),
+        "bmg_aux_set_gamma": ([P, D], I),
+        "bmg_aux_export": ([P, I, ctypes.POINTER(I), ctypes.POINTER(ctypes.c_longlong), P, P, P], I),
+        "bmg_aux_destroy": ([P], None),
     }
     for name, (args, res) in sigs.items():
         f = getattr(lib, name)
@@ -111,7 +123,8 @@ def exported_symbols() -> list:
             "bmg_level_n", "bmg_get_stencil", "bmg_get_interp", "bmg_launch_count", "bmg_get_tiles",
             "bmg_set_tiles", "bmg_autotune", "bmg_profile",
             "bmg_profile_read", "bmg_destroy", "bmg_status_str", "bmg_assemble_noalloc", "bmg_assemble_tensor",
-            "bmg_boundary_rhs"]
+            "bmg_boundary_rhs", "bmg_aux_default_opts", "bmg_aux_create", "bmg_aux_workspace_bytes",
+            "bmg_aux_setup", "bmg_aux_solve", "bmg_aux_set_gamma", "bmg_aux_export", "bmg_aux_destroy"]
 
 
 def _check(code: int, where: str):
@@ -405,3 +418,76 @@ class Solver:
         with torch.cuda.device(self.device):
             _check(load().bmg_get_interp(self._h, level, _ptr(out)), "bmg_get_interp")
         return out
+
+
+class AuxSolver:
+    """The auxiliary-space two-grid method (bmg_aux_*): a P1 triangulation of
+    the physical domain solved with `coarse` (a set-up 2-D Solver, assembled
+    with bmg_assemble) as its structured coarse level.
+
+    mesh: an object with xy (nv x 2), st (nv x 2, computational images),
+    tri (ntri x 3), dirichlet (nv bools) and kappa (ntri) arrays, e.g.
+    inputs.annulus_mesh.  mass_steps: CG iterations for M_p^-1 in P, or 0
+    for the lumped mass."""
+
+    def __init__(self, coarse: "Solver", mesh, omega: float = 2.0 / 3.0, mass_steps: int = 0, gamma: float = 1.0):
+        import numpy as np
+        lib = load()
+        self.coarse = coarse
+        self.nv = int(mesh.xy.shape[0])
+        self.ntri = int(mesh.tri.shape[0])
+        xy = np.ascontiguousarray(mesh.xy, dtype=np.float64)
+        st = np.ascontiguousarray(mesh.st, dtype=np.float64)
+        tri = np.ascontiguousarray(mesh.tri, dtype=np.int32)
+        dirichlet = np.ascontiguousarray(mesh.dirichlet, dtype=np.uint8)
+        opts = _AuxOpts(float(omega), int(mass_steps), float(gamma))
+        h = ctypes.c_void_p()
+        _check(lib.bmg_aux_create(coarse._h, self.nv, xy.ctypes.data_as(ctypes.c_void_p),
+                                  st.ctypes.data_as(ctypes.c_void_p), dirichlet.ctypes.data_as(ctypes.c_void_p),
+                                  self.ntri, tri.ctypes.data_as(ctypes.c_void_p), ctypes.byref(opts),
+                                  ctypes.byref(h)), "bmg_aux_create")
+        self._h = h
+        nbytes = ctypes.c_size_t()
+        _check(lib.bmg_aux_workspace_bytes(h, ctypes.byref(nbytes)), "bmg_aux_workspace_bytes")
+        self.workspace_bytes = nbytes.value
+        dev = coarse.device
+        with torch.cuda.device(dev):
+            self._ws = torch.empty(max(self.workspace_bytes, 1), dtype=torch.uint8, device=dev)
+            kappa = torch.as_tensor(mesh.kappa, dtype=torch.float64).to(dev).contiguous()
+            _check(lib.bmg_aux_setup(h, ctypes.c_void_p(self._ws.data_ptr()), ctypes.c_size_t(self.workspace_bytes),
+                                     _ptr(kappa), _ptr(coarse._coords)), "bmg_aux_setup")
+
+    def __del__(self):
+        if getattr(self, "_h", None) is not None and _lib is not None:
+            _lib.bmg_aux_destroy(self._h)
+            self._h = None
+
+    def set_gamma(self, gamma: float):
+        _check(load().bmg_aux_set_gamma(self._h, float(gamma)), "bmg_aux_set_gamma")
+
+    def solve(self, f, u0=None, tol: float = 1e-10, maxit: int = 500, raise_on_nonconv=True):
+        dev = self.coarse.device
+        f = torch.as_tensor(f, dtype=torch.float64).to(dev).contiguous()
+        u = torch.zeros_like(f) if u0 is None else torch.as_tensor(u0, dtype=torch.float64).to(dev).clone()
+        info = _Info()
+        with torch.cuda.device(dev):
+            code = load().bmg_aux_solve(self._h, _ptr(f), _ptr(u), float(tol), int(maxit), ctypes.byref(info))
+        if code not in (0, 8) or (code == 8 and raise_on_nonconv):
+            _check(code, "bmg_aux_solve")
+        return u, _info_of(info)
+
+    def export(self, which: str):
+        """(rowptr, col, val) numpy arrays of 'A', 'M' or 'C' (see bmg_aux_export)."""
+        import numpy as np
+        w = {"A": 0, "M": 1, "C": 2}[which]
+        lib = load()
+        nr = ctypes.c_int()
+        nnz = ctypes.c_longlong()
+        _check(lib.bmg_aux_export(self._h, w, ctypes.byref(nr), ctypes.byref(nnz), None, None, None), "bmg_aux_export")
+        rp = np.zeros(nr.value + 1, dtype=np.int64)
+        col = np.zeros(nnz.value, dtype=np.int32)
+        val = np.zeros(nnz.value, dtype=np.float64)
+        _check(lib.bmg_aux_export(self._h, w, ctypes.byref(nr), ctypes.byref(nnz), rp.ctypes.data_as(ctypes.c_void_p),
+                                  col.ctypes.data_as(ctypes.c_void_p), val.ctypes.data_as(ctypes.c_void_p)),
+               "bmg_aux_export")
+        return rp, col, val

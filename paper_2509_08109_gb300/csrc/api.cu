@@ -11,10 +11,6 @@
 
 using namespace bmg;
 
-struct bmg_ctx {
-    Ctx c;
-};
-
 namespace {
 
 long long ipow(long long b, int e) {

@@ -1,0 +1,869 @@
+// aux2d.cu -- the auxiliary-space two-grid method around the structured
+// solve (Sec. 2.2 "Setup phase" and "Solution phase", Sec. 2.3, Sec. 2.4).
+//
+// The physical problem is the P1 system A_p u_p = f_p on a triangulation of
+// the physical domain; the structured BoxMG hierarchy of a coarse context
+// is its coarse level, reached through P = M_p^-1 C and R = P^T.
+//
+// Host side (bmg_aux_create): interior numbering of the vertices, the CSR
+// patterns of A_p, M_p (rows and columns: interior vertices) and C (rows:
+// interior vertices; columns: the coarse grid's interior nodes in its padded
+// layout), the (triangle, cell) pairs whose bounding boxes and separating
+// axes overlap, and for every stored entry the list of the local
+// contributions that sum to it, in triangle (or pair) order.
+//
+// Device side: per-triangle P1 element matrices and per-pair coupled-mass
+// blocks are formed once (FP64), then every stored entry sums its
+// contributions in list order -- deterministic, no atomics.  A solve runs
+// the cycle with CSR kernels (one thread per row), device-side CG scalars
+// for the mass solves, and the coarse context's own V-cycle.
+#include <math.h>
+#include <string.h>
+
+#include <algorithm>
+#include <new>
+#include <vector>
+
+#include "common.cuh"
+
+using namespace bmg;
+
+namespace {
+
+constexpr int kAuxThreads = kThreads;     // 256, as block_sum expects
+constexpr int kRedBlocks = 4 * 152;       // fixed grid of the reducing kernels
+
+struct AuxState {
+    double rr;          // ||f - A u||^2 (interior)
+    double ff;          // ||f||^2
+    double cg_rr, cg_pq, alpha, beta;
+    int err;
+    unsigned int counter[4];
+};
+
+__device__ __forceinline__ void aux_err(AuxState* st, int code) { atomicCAS(&st->err, 0, code); }
+
+// ------------------------------------------------------------------ setup kernels
+// P1 stiffness and consistent mass of every triangle (Sec. 2.1, V_p = P1):
+// K_ab = kappa |T| grad l_a . grad l_b, M_ab = |T| (1 + delta_ab) / 12, the
+// barycentric gradients from the edge opposite each vertex.
+__global__ void k_tri_local(int ntri, const int* __restrict__ tri, const double* __restrict__ xy,
+                            const double* __restrict__ kappa, double* __restrict__ lk, double* __restrict__ lm,
+                            AuxState* st) {
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= ntri) return;
+    double px[3], py[3];
+#pragma unroll
+    for (int a = 0; a < 3; a++) {
+        const int v = tri[3 * t + a];
+        px[a] = xy[2 * v];
+        py[a] = xy[2 * v + 1];
+    }
+    // edge opposite vertex a: from vertex a+1 to vertex a+2
+    double ex[3], ey[3];
+#pragma unroll
+    for (int a = 0; a < 3; a++) {
+        ex[a] = px[(a + 2) % 3] - px[(a + 1) % 3];
+        ey[a] = py[(a + 2) % 3] - py[(a + 1) % 3];
+    }
+    const double area = 0.5 * ((px[1] - px[0]) * (py[2] - py[0]) - (py[1] - py[0]) * (px[2] - px[0]));
+    if (!(area > 0.0)) aux_err(st, BMG_ERR_MAP_FOLDED);
+    const double s = kappa[t] / (4.0 * area);    // kappa |T| / (2|T|)^2
+#pragma unroll
+    for (int a = 0; a < 3; a++)
+#pragma unroll
+        for (int b = 0; b < 3; b++) {
+            lk[9 * t + 3 * a + b] = s * (ex[a] * ex[b] + ey[a] * ey[b]);
+            lm[9 * t + 3 * a + b] = area / 12.0 * (a == b ? 2.0 : 1.0);
+        }
+}
+
+// The 3 x 4 coupled-mass block of one (triangle, cell) pair (Sec. 2.3, Eq.
+// coupled_mass_comp): the mapped triangle (straight edges through the
+// images of its vertices) is clipped to the cell (Sutherland-Hodgman, one
+// half-plane at a time), the clipped polygon is split into a fan, and each
+// fan triangle is integrated with a 3 x 3 Gauss rule in collapsed
+// coordinates -- exact for the integrand, barycentric coordinate (degree 1)
+// x bilinear basis (2) x |det J| of the Q1 cell (affine).
+__device__ __forceinline__ int clip_half(const double* ix, const double* iy, int m, double* ox, double* oy, int ax,
+                                         double bound, bool lower) {
+    int k = 0;
+    for (int e = 0; e < m; e++) {
+        const int pe = e == 0 ? m - 1 : e - 1;
+        const double ac = ax == 0 ? ix[pe] : iy[pe], bc = ax == 0 ? ix[e] : iy[e];
+        const bool ka = lower ? ac >= bound : ac <= bound;
+        const bool kb = lower ? bc >= bound : bc <= bound;
+        if (ka != kb) {
+            const double s = (bound - ac) / (bc - ac);
+            double x = ix[pe] + s * (ix[e] - ix[pe]);
+            double y = iy[pe] + s * (iy[e] - iy[pe]);
+            if (ax == 0) x = bound; else y = bound;
+            ox[k] = x;
+            oy[k] = y;
+            k++;
+        }
+        if (kb) {
+            ox[k] = ix[e];
+            oy[k] = iy[e];
+            k++;
+        }
+    }
+    return k;
+}
+
+__global__ void k_pair_local(int npairs, const int* __restrict__ pair_tri, const int* __restrict__ pair_cell,
+                             const int* __restrict__ tri, const double* __restrict__ st,
+                             const double* __restrict__ coords, int n, double* __restrict__ loc) {
+    const int p = blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= npairs) return;
+    const int t = pair_tri[p];
+    const int cell = pair_cell[p];
+    const int ci = cell % (n - 1), cj = cell / (n - 1);
+    const double h = 1.0 / (n - 1);
+    double Sx[3], Sy[3];
+#pragma unroll
+    for (int a = 0; a < 3; a++) {
+        const int v = tri[3 * t + a];
+        Sx[a] = st[2 * v];
+        Sy[a] = st[2 * v + 1];
+    }
+    const double d = (Sx[1] - Sx[0]) * (Sy[2] - Sy[0]) - (Sy[1] - Sy[0]) * (Sx[2] - Sx[0]);
+    // corners of the cell in physical space (order 00, 10, 01, 11)
+    const double* X = coords;
+    const double* Y = coords + (long long)n * n;
+    const long long o00 = (long long)cj * n + ci;
+    const double Xc[4] = {X[o00], X[o00 + 1], X[o00 + n], X[o00 + n + 1]};
+    const double Yc[4] = {Y[o00], Y[o00 + 1], Y[o00 + n], Y[o00 + n + 1]};
+    double ax_[8], ay_[8], bx_[8], by_[8];
+    int m = 3;
+    for (int a = 0; a < 3; a++) {
+        ax_[a] = Sx[a];
+        ay_[a] = Sy[a];
+    }
+    m = clip_half(ax_, ay_, m, bx_, by_, 0, ci * h, true);
+    m = clip_half(bx_, by_, m, ax_, ay_, 0, (ci + 1) * h, false);
+    m = clip_half(ax_, ay_, m, bx_, by_, 1, cj * h, true);
+    m = clip_half(bx_, by_, m, ax_, ay_, 1, (cj + 1) * h, false);
+    double acc[12];
+#pragma unroll
+    for (int k = 0; k < 12; k++) acc[k] = 0.0;
+    // 3-point Gauss-Legendre on [0, 1]
+    const double g[3] = {0.5 - 0.38729833462074168852, 0.5, 0.5 + 0.38729833462074168852};
+    const double w[3] = {5.0 / 18.0, 8.0 / 18.0, 5.0 / 18.0};
+    const double inv_h2 = 1.0 / (h * h);
+    for (int k = 1; k + 1 < m; k++) {
+        const double v0x = ax_[0], v0y = ay_[0];
+        const double v1x = ax_[k], v1y = ay_[k];
+        const double v2x = ax_[k + 1], v2y = ay_[k + 1];
+        const double area2 = fabs((v1x - v0x) * (v2y - v0y) - (v1y - v0y) * (v2x - v0x));
+        for (int qa = 0; qa < 3; qa++)
+            for (int qb = 0; qb < 3; qb++) {
+                const double u = g[qa], v = g[qb];
+                const double ps = v0x + u * ((v1x - v0x) + v * (v2x - v1x));
+                const double pt = v0y + u * ((v1y - v0y) + v * (v2y - v1y));
+                const double wt = w[qa] * w[qb] * u * area2 * inv_h2;
+                const double l1 = ((ps - Sx[0]) * (Sy[2] - Sy[0]) - (pt - Sy[0]) * (Sx[2] - Sx[0])) / d;
+                const double l2 = ((Sx[1] - Sx[0]) * (pt - Sy[0]) - (Sy[1] - Sy[0]) * (ps - Sx[0])) / d;
+                const double lam[3] = {1.0 - l1 - l2, l1, l2};
+                const double xi = ps * (n - 1) - ci, eta = pt * (n - 1) - cj;
+                const double phi[4] = {(1 - xi) * (1 - eta), xi * (1 - eta), (1 - xi) * eta, xi * eta};
+                const double dxi[4] = {-(1 - eta), 1 - eta, -eta, eta};
+                const double deta[4] = {-(1 - xi), -xi, 1 - xi, xi};
+                double J11 = 0, J12 = 0, J21 = 0, J22 = 0;
+#pragma unroll
+                for (int c = 0; c < 4; c++) {
+                    J11 += dxi[c] * Xc[c];
+                    J12 += deta[c] * Xc[c];
+                    J21 += dxi[c] * Yc[c];
+                    J22 += deta[c] * Yc[c];
+                }
+                const double dj = fabs(J11 * J22 - J12 * J21);
+                const double f = wt * dj;
+#pragma unroll
+                for (int a = 0; a < 3; a++)
+#pragma unroll
+                    for (int b = 0; b < 4; b++) acc[4 * a + b] += f * lam[a] * phi[b];
+            }
+    }
+#pragma unroll
+    for (int k = 0; k < 12; k++) loc[12LL * p + k] = acc[k];
+}
+
+// out[e] = sum of src[idx[k]] for k in [ptr[e], ptr[e+1]), in list order
+__global__ void k_gather(int nout, const int* __restrict__ ptr, const int* __restrict__ idx,
+                         const double* __restrict__ src, double* __restrict__ out) {
+    const int e = blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= nout) return;
+    double s = 0.0;
+    for (int k = ptr[e]; k < ptr[e + 1]; k++) s += src[idx[k]];
+    out[e] = s;
+}
+
+__global__ void k_permute(int nout, const int* __restrict__ perm, const double* __restrict__ src,
+                          double* __restrict__ out) {
+    const int e = blockIdx.x * blockDim.x + threadIdx.x;
+    if (e < nout) out[e] = src[perm[e]];
+}
+
+__global__ void k_diag_inv(int nr, const int* __restrict__ diag_pos, const double* __restrict__ va,
+                           double* __restrict__ dinv) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < nr) dinv[i] = 1.0 / va[diag_pos[i]];
+}
+
+__global__ void k_inv(int nr, double* __restrict__ v) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < nr) v[i] = 1.0 / v[i];
+}
+
+// ------------------------------------------------------------------ solve kernels
+__device__ __forceinline__ double csr_row(const int* __restrict__ rp, const int* __restrict__ ci,
+                                          const double* __restrict__ va, const double* __restrict__ x, int i) {
+    double s = 0.0;
+    for (int k = rp[i]; k < rp[i + 1]; k++) s += va[k] * x[ci[k]];
+    return s;
+}
+
+// interior entries of a vertex vector: out[i] = in[vtx[i]]
+__global__ void k_compress(int nr, const int* __restrict__ vtx, const double* __restrict__ in, double* __restrict__ out) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < nr) out[i] = in[vtx[i]];
+}
+
+// all vertices: out[v] = in[vid[v]] or 0 on Dirichlet vertices
+__global__ void k_expand(int nv, const int* __restrict__ vid, const double* __restrict__ in, double* __restrict__ out) {
+    const int v = blockIdx.x * blockDim.x + threadIdx.x;
+    if (v < nv) out[v] = vid[v] >= 0 ? in[vid[v]] : 0.0;
+}
+
+// damped Jacobi: uo = u + omega D^-1 (f - A u)
+__global__ void k_jacobi(int nr, const int* __restrict__ rp, const int* __restrict__ ci, const double* __restrict__ va,
+                         const double* __restrict__ dinv, const double* __restrict__ f, const double* __restrict__ u,
+                         double* __restrict__ uo, double omega) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < nr) uo[i] = u[i] + omega * dinv[i] * (f[i] - csr_row(rp, ci, va, u, i));
+}
+
+// r = f - A u; with slot: *slot = ||r||^2 (deterministic grid reduction)
+__global__ void k_residual_csr(int nr, const int* __restrict__ rp, const int* __restrict__ ci,
+                               const double* __restrict__ va, const double* __restrict__ f,
+                               const double* __restrict__ u, double* __restrict__ r, double* partials,
+                               unsigned int* counter, double* slot) {
+    double acc = 0.0;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < nr; i += gridDim.x * blockDim.x) {
+        const double v = f[i] - csr_row(rp, ci, va, u, i);
+        if (r) r[i] = v;
+        acc += v * v;
+    }
+    double t;
+    if (slot && grid_sum(acc, partials, counter, &t)) *slot = t;
+}
+
+__global__ void k_dot_aux(int nr, const double* __restrict__ a, const double* __restrict__ b, double* partials,
+                          unsigned int* counter, double* slot) {
+    double acc = 0.0;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < nr; i += gridDim.x * blockDim.x) acc += a[i] * b[i];
+    double t;
+    if (grid_sum(acc, partials, counter, &t)) *slot = t;
+}
+
+// restriction: rc[map[q]] = sum_k C^T[q,k] (y[col] * (w ? w[col] : 1))
+__global__ void k_restrict_ct(int nq, const int* __restrict__ rp, const int* __restrict__ ci,
+                              const double* __restrict__ va, const int* __restrict__ map, const double* __restrict__ y,
+                              const double* __restrict__ w, double* __restrict__ rc) {
+    const int q = blockIdx.x * blockDim.x + threadIdx.x;
+    if (q >= nq) return;
+    double s = 0.0;
+    for (int k = rp[q]; k < rp[q + 1]; k++) s += va[k] * (w ? y[ci[k]] * w[ci[k]] : y[ci[k]]);
+    rc[map[q]] = s;
+}
+
+// prolongation: out[i] = (C z)_i * (w ? w[i] : 1), z in the padded coarse layout;
+// with u: u[i] += gamma * out[i] instead
+__global__ void k_prolong_c(int nr, const int* __restrict__ rp, const int* __restrict__ ci,
+                            const double* __restrict__ va, const double* __restrict__ z, const double* __restrict__ w,
+                            double* __restrict__ out, double* __restrict__ u, double gamma) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= nr) return;
+    double s = csr_row(rp, ci, va, z, i);
+    if (w) s *= w[i];
+    if (u) u[i] += gamma * s;
+    else out[i] = s;
+}
+
+// CG on M (the mass solves): x = 0, res = r, p = r, cg_rr = r.r
+__global__ void k_cg_init(int nr, const double* __restrict__ r, double* __restrict__ x, double* __restrict__ res,
+                          double* __restrict__ p, double* partials, AuxState* st) {
+    double acc = 0.0;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < nr; i += gridDim.x * blockDim.x) {
+        const double v = r[i];
+        x[i] = 0.0;
+        res[i] = v;
+        p[i] = v;
+        acc += v * v;
+    }
+    double t;
+    if (grid_sum(acc, partials, &st->counter[1], &t)) st->cg_rr = t;
+}
+
+// q = M p; alpha = cg_rr / p.q (0 when p.q is not positive: r was zero)
+__global__ void k_cg_mp(int nr, const int* __restrict__ rp, const int* __restrict__ ci, const double* __restrict__ va,
+                        const double* __restrict__ p, double* __restrict__ q, double* partials, AuxState* st) {
+    double acc = 0.0;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < nr; i += gridDim.x * blockDim.x) {
+        const double v = csr_row(rp, ci, va, p, i);
+        q[i] = v;
+        acc += p[i] * v;
+    }
+    double t;
+    if (grid_sum(acc, partials, &st->counter[1], &t)) {
+        st->cg_pq = t;
+        st->alpha = t > 0.0 ? st->cg_rr / t : 0.0;
+    }
+}
+
+// x += alpha p; res -= alpha q; beta = res.res / cg_rr; cg_rr = res.res
+__global__ void k_cg_update(int nr, double* __restrict__ x, double* __restrict__ res, const double* __restrict__ p,
+                            const double* __restrict__ q, double* partials, AuxState* st) {
+    const double alpha = st->alpha;
+    double acc = 0.0;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < nr; i += gridDim.x * blockDim.x) {
+        x[i] += alpha * p[i];
+        const double v = res[i] - alpha * q[i];
+        res[i] = v;
+        acc += v * v;
+    }
+    double t;
+    if (grid_sum(acc, partials, &st->counter[1], &t)) {
+        st->beta = st->cg_rr > 0.0 ? t / st->cg_rr : 0.0;
+        st->cg_rr = t;
+    }
+}
+
+__global__ void k_cg_p(int nr, const double* __restrict__ res, double* __restrict__ p, const AuxState* st) {
+    const double beta = st->beta;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < nr; i += gridDim.x * blockDim.x)
+        p[i] = res[i] + beta * p[i];
+}
+
+__global__ void k_axpy(int nr, double* __restrict__ u, const double* __restrict__ v, double gamma) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < nr) u[i] += gamma * v[i];
+}
+
+inline int blocks(long long n) { return cdiv(n, kAuxThreads); }
+
+// ------------------------------------------------------------------ host structure
+struct Csr {
+    std::vector<int> ptr, col;       // rows, columns
+    std::vector<int> gptr, gidx;     // per entry: its contributions (indices into the local arrays)
+};
+
+// Builds a CSR from (row, col, contribution) records: entries sorted by
+// column within a row, contributions of an entry in record order.
+bool build_csr(int nrows, const std::vector<int>& rr, const std::vector<int>& cc, const std::vector<int>& src,
+               Csr& out) {
+    const size_t nrec = rr.size();
+    std::vector<long long> cnt(nrows + 1, 0);
+    for (size_t k = 0; k < nrec; k++) cnt[rr[k] + 1]++;
+    for (int i = 0; i < nrows; i++) cnt[i + 1] += cnt[i];
+    std::vector<int> order(nrec);
+    {
+        std::vector<long long> pos(cnt.begin(), cnt.end() - 1);
+        for (size_t k = 0; k < nrec; k++) order[pos[rr[k]]++] = (int)k;
+    }
+    out.ptr.assign(nrows + 1, 0);
+    out.col.clear();
+    out.gptr.assign(1, 0);
+    out.gidx.clear();
+    out.gidx.reserve(nrec);
+    std::vector<int> tmp;
+    for (int i = 0; i < nrows; i++) {
+        tmp.assign(order.begin() + cnt[i], order.begin() + cnt[i + 1]);
+        std::stable_sort(tmp.begin(), tmp.end(), [&](int a, int b) { return cc[a] < cc[b]; });
+        for (size_t k = 0; k < tmp.size(); k++) {
+            if (k == 0 || cc[tmp[k]] != cc[tmp[k - 1]]) {
+                out.col.push_back(cc[tmp[k]]);
+                if (k > 0) out.gptr.push_back((int)out.gidx.size());
+            }
+            out.gidx.push_back(src[tmp[k]]);
+        }
+        if (!tmp.empty()) out.gptr.push_back((int)out.gidx.size());
+        out.ptr[i + 1] = (int)out.col.size();
+        if (out.gidx.size() > (size_t)0x7fffffff) return false;
+    }
+    return true;
+}
+
+// separating-axis test of a triangle against an axis-aligned box (touching counts)
+bool tri_box_overlap(const double* sx, const double* sy, double x0, double y0, double x1, double y1) {
+    const double mnx = std::min(sx[0], std::min(sx[1], sx[2])), mxx = std::max(sx[0], std::max(sx[1], sx[2]));
+    const double mny = std::min(sy[0], std::min(sy[1], sy[2])), mxy = std::max(sy[0], std::max(sy[1], sy[2]));
+    if (mxx < x0 || mnx > x1 || mxy < y0 || mny > y1) return false;
+    for (int e = 0; e < 3; e++) {
+        const int a = e, b = (e + 1) % 3, c = (e + 2) % 3;
+        const double nx = sy[b] - sy[a], ny = sx[a] - sx[b];      // edge normal
+        const double side = nx * (sx[c] - sx[a]) + ny * (sy[c] - sy[a]);
+        const double cx[4] = {x0, x1, x0, x1}, cy[4] = {y0, y0, y1, y1};
+        bool all_out = true;
+        for (int k = 0; k < 4 && all_out; k++) {
+            const double v = nx * (cx[k] - sx[a]) + ny * (cy[k] - sy[a]);
+            if (side > 0 ? v >= 0 : v <= 0) all_out = false;
+        }
+        if (all_out) return false;
+    }
+    return true;
+}
+
+}  // namespace
+
+struct bmg_aux {
+    bmg_ctx* coarse = nullptr;
+    bmg_aux_opts opts{};
+    int nv = 0, ntri = 0, nvi = 0, n = 0, ld = 0;
+    std::vector<int> tri, vid, vtx;      // vertex -> interior id (-1), interior id -> vertex
+    std::vector<double> xy, st;
+    std::vector<int> pair_tri, pair_cell;
+    Csr am;                              // A_p and M_p pattern (contributions: 9 t + 3 a + b)
+    std::vector<int> diag_pos;
+    Csr lump;                            // lumped mass: one "entry" per interior row
+    Csr cm;                              // C pattern (contributions: 12 p + 4 a + b)
+    std::vector<int> ct_ptr, ct_col, ct_perm, ct_map;   // C^T rows: interior coarse nodes
+    size_t ws_need = 0;
+    bool ready = false;
+    // device (carved from the workspace)
+    int *d_tri = nullptr, *d_vid = nullptr, *d_vtx = nullptr, *d_pair_tri = nullptr, *d_pair_cell = nullptr;
+    double *d_xy = nullptr, *d_st = nullptr;
+    int *d_am_ptr = nullptr, *d_am_col = nullptr, *d_am_gptr = nullptr, *d_am_gidx = nullptr, *d_diag = nullptr;
+    int *d_lp_gptr = nullptr, *d_lp_gidx = nullptr;
+    int *d_c_ptr = nullptr, *d_c_col = nullptr, *d_c_gptr = nullptr, *d_c_gidx = nullptr;
+    int *d_ct_ptr = nullptr, *d_ct_col = nullptr, *d_ct_perm = nullptr, *d_ct_map = nullptr;
+    double *d_lk = nullptr, *d_lm = nullptr, *d_loc = nullptr;
+    double *d_va = nullptr, *d_vm = nullptr, *d_vc = nullptr, *d_vct = nullptr, *d_dinv = nullptr, *d_mlinv = nullptr;
+    double *d_f = nullptr, *d_u = nullptr, *d_u2 = nullptr, *d_r = nullptr, *d_y = nullptr, *d_cres = nullptr,
+           *d_cp = nullptr, *d_cq = nullptr, *d_w = nullptr;
+    double* d_partials = nullptr;
+    AuxState* d_st_aux = nullptr;
+};
+
+namespace {
+
+size_t a256(size_t v) { return (v + 255) & ~(size_t)255; }
+
+size_t carve_aux(bmg_aux& x, char* base) {
+    size_t off = 0;
+    auto take = [&](size_t bytes) -> char* {
+        off = a256(off);
+        char* p = base ? base + off : nullptr;
+        off += bytes;
+        return p;
+    };
+    const size_t I = sizeof(int), D = sizeof(double);
+    const size_t npairs = x.pair_tri.size();
+    x.d_tri = (int*)take(I * x.tri.size());
+    x.d_vid = (int*)take(I * x.nv);
+    x.d_vtx = (int*)take(I * x.nvi);
+    x.d_pair_tri = (int*)take(I * npairs);
+    x.d_pair_cell = (int*)take(I * npairs);
+    x.d_xy = (double*)take(D * x.xy.size());
+    x.d_st = (double*)take(D * x.st.size());
+    x.d_am_ptr = (int*)take(I * x.am.ptr.size());
+    x.d_am_col = (int*)take(I * x.am.col.size());
+    x.d_am_gptr = (int*)take(I * x.am.gptr.size());
+    x.d_am_gidx = (int*)take(I * x.am.gidx.size());
+    x.d_diag = (int*)take(I * x.diag_pos.size());
+    x.d_lp_gptr = (int*)take(I * x.lump.gptr.size());
+    x.d_lp_gidx = (int*)take(I * x.lump.gidx.size());
+    x.d_c_ptr = (int*)take(I * x.cm.ptr.size());
+    x.d_c_col = (int*)take(I * x.cm.col.size());
+    x.d_c_gptr = (int*)take(I * x.cm.gptr.size());
+    x.d_c_gidx = (int*)take(I * x.cm.gidx.size());
+    x.d_ct_ptr = (int*)take(I * x.ct_ptr.size());
+    x.d_ct_col = (int*)take(I * x.ct_col.size());
+    x.d_ct_perm = (int*)take(I * x.ct_perm.size());
+    x.d_ct_map = (int*)take(I * x.ct_map.size());
+    x.d_lk = (double*)take(D * 9 * (size_t)x.ntri);
+    x.d_lm = (double*)take(D * 9 * (size_t)x.ntri);
+    x.d_loc = (double*)take(D * 12 * npairs);
+    x.d_va = (double*)take(D * x.am.col.size());
+    x.d_vm = (double*)take(D * x.am.col.size());
+    x.d_vc = (double*)take(D * x.cm.col.size());
+    x.d_vct = (double*)take(D * x.ct_col.size());
+    x.d_dinv = (double*)take(D * x.nvi);
+    x.d_mlinv = (double*)take(D * x.nvi);
+    double** vecs[] = {&x.d_f, &x.d_u, &x.d_u2, &x.d_r, &x.d_y, &x.d_cres, &x.d_cp, &x.d_cq, &x.d_w};
+    for (double** v : vecs) *v = (double*)take(D * std::max(x.nvi, 1));
+    x.d_partials = (double*)take(D * kRedBlocks);
+    x.d_st_aux = (AuxState*)take(sizeof(AuxState));
+    return a256(off);
+}
+
+template <typename T>
+bmg_status up(T* dst, const std::vector<T>& src, cudaStream_t s) {
+    if (src.empty()) return BMG_OK;
+    BMG_CUDA(cudaMemcpyAsync(dst, src.data(), sizeof(T) * src.size(), cudaMemcpyHostToDevice, s));
+    return BMG_OK;
+}
+
+bmg_status aux_read(bmg_aux& x, AuxState& h) {
+    cudaStream_t s = x.coarse->c.stream;
+    BMG_CUDA(cudaMemcpyAsync(&h, x.d_st_aux, sizeof(AuxState), cudaMemcpyDeviceToHost, s));
+    BMG_CUDA(cudaStreamSynchronize(s));
+    return BMG_OK;
+}
+
+// y = M^-1 r by x.opts.mass_steps CG iterations (mass_steps >= 1)
+bmg_status mass_cg(bmg_aux& x, const double* r, double* y) {
+    cudaStream_t s = x.coarse->c.stream;
+    const int nr = x.nvi;
+    k_cg_init<<<kRedBlocks, kAuxThreads, 0, s>>>(nr, r, y, x.d_cres, x.d_cp, x.d_partials, x.d_st_aux);
+    for (int k = 0; k < x.opts.mass_steps; k++) {
+        if (k > 0) k_cg_p<<<kRedBlocks, kAuxThreads, 0, s>>>(nr, x.d_cres, x.d_cp, x.d_st_aux);
+        k_cg_mp<<<kRedBlocks, kAuxThreads, 0, s>>>(nr, x.d_am_ptr, x.d_am_col, x.d_vm, x.d_cp, x.d_cq, x.d_partials,
+                                                   x.d_st_aux);
+        k_cg_update<<<kRedBlocks, kAuxThreads, 0, s>>>(nr, y, x.d_cres, x.d_cp, x.d_cq, x.d_partials, x.d_st_aux);
+    }
+    BMG_CUDA(cudaGetLastError());
+    return BMG_OK;
+}
+
+// one two-grid cycle on the interior vectors d_f, d_u (Sec. 2.2 "Solution phase")
+bmg_status aux_cycle(bmg_aux& x) {
+    Ctx& c = x.coarse->c;
+    cudaStream_t s = c.stream;
+    const int nr = x.nvi, nq = (int)x.ct_map.size();
+    const bool lumped = x.opts.mass_steps == 0;
+    // 1. pre-relaxation
+    k_jacobi<<<blocks(nr), kAuxThreads, 0, s>>>(nr, x.d_am_ptr, x.d_am_col, x.d_va, x.d_dinv, x.d_f, x.d_u, x.d_u2,
+                                                x.opts.omega);
+    std::swap(x.d_u, x.d_u2);
+    // 2. restriction r_c = C^T M^-1 (f - A u)
+    k_residual_csr<<<kRedBlocks, kAuxThreads, 0, s>>>(nr, x.d_am_ptr, x.d_am_col, x.d_va, x.d_f, x.d_u, x.d_r,
+                                                      x.d_partials, &x.d_st_aux->counter[0], nullptr);
+    const double* y = x.d_r;
+    if (!lumped) {
+        BMG_TRY(mass_cg(x, x.d_r, x.d_y));
+        y = x.d_y;
+    }
+    BMG_CUDA(cudaMemsetAsync(c.r, 0, sizeof(double) * c.lev[0].plane, s));
+    k_restrict_ct<<<blocks(nq), kAuxThreads, 0, s>>>(nq, x.d_ct_ptr, x.d_ct_col, x.d_vct, x.d_ct_map, y,
+                                                     lumped ? x.d_mlinv : nullptr, c.r);
+    // 3. BoxMG V-cycle on A_c e_c = r_c
+    BMG_TRY(vcycle(c, c.r, c.z[0]));
+    // 4. prolongation u += gamma M^-1 C e_c
+    if (lumped) {
+        k_prolong_c<<<blocks(nr), kAuxThreads, 0, s>>>(nr, x.d_c_ptr, x.d_c_col, x.d_vc, c.z[0], x.d_mlinv, nullptr,
+                                                       x.d_u, x.opts.gamma);
+    } else {
+        k_prolong_c<<<blocks(nr), kAuxThreads, 0, s>>>(nr, x.d_c_ptr, x.d_c_col, x.d_vc, c.z[0], nullptr, x.d_w,
+                                                       nullptr, 0.0);
+        BMG_TRY(mass_cg(x, x.d_w, x.d_y));
+        k_axpy<<<blocks(nr), kAuxThreads, 0, s>>>(nr, x.d_u, x.d_y, x.opts.gamma);
+    }
+    // 5. post-relaxation
+    k_jacobi<<<blocks(nr), kAuxThreads, 0, s>>>(nr, x.d_am_ptr, x.d_am_col, x.d_va, x.d_dinv, x.d_f, x.d_u, x.d_u2,
+                                                x.opts.omega);
+    std::swap(x.d_u, x.d_u2);
+    BMG_CUDA(cudaGetLastError());
+    return BMG_OK;
+}
+
+}  // namespace
+
+extern "C" void bmg_aux_default_opts(bmg_aux_opts* o) {
+    if (!o) return;
+    o->omega = 2.0 / 3.0;
+    o->mass_steps = 0;
+    o->gamma = 1.0;
+}
+
+extern "C" bmg_status bmg_aux_create(bmg_ctx* coarse, int nv, const double* xy, const double* st,
+                                     const unsigned char* dirichlet, int ntri, const int* tri,
+                                     const bmg_aux_opts* opts, bmg_aux** out) {
+    if (!out) return BMG_ERR_ARG;
+    *out = nullptr;
+    if (!coarse || !xy || !st || !dirichlet || !tri || nv < 3 || ntri < 1) return BMG_ERR_ARG;
+    Ctx& c = coarse->c;
+    if (c.dim != 2) return BMG_ERR_SHAPE;
+    if (!c.attached || !c.have_setup) return BMG_ERR_STATE;
+    bmg_aux_opts o;
+    bmg_aux_default_opts(&o);
+    if (opts) o = *opts;
+    if (!(o.omega > 0.0 && o.omega < 2.0) || o.mass_steps < 0 || o.mass_steps > 64 || !(o.gamma > 0.0))
+        return BMG_ERR_ARG;
+    for (long long k = 0; k < 3LL * ntri; k++)
+        if (tri[k] < 0 || tri[k] >= nv) return BMG_ERR_ARG;
+    if (9LL * ntri > 0x7fffffffLL) return BMG_ERR_SHAPE;
+    bmg_aux* x = new (std::nothrow) bmg_aux;
+    if (!x) return BMG_ERR_ARG;
+    x->coarse = coarse;
+    x->opts = o;
+    x->nv = nv;
+    x->ntri = ntri;
+    x->n = c.lev[0].n;
+    x->ld = c.lev[0].ld;
+    x->tri.assign(tri, tri + 3LL * ntri);
+    x->xy.assign(xy, xy + 2LL * nv);
+    x->st.assign(st, st + 2LL * nv);
+    x->vid.assign(nv, -1);
+    for (int v = 0; v < nv; v++)
+        if (!dirichlet[v]) {
+            x->vid[v] = (int)x->vtx.size();
+            x->vtx.push_back(v);
+        }
+    x->nvi = (int)x->vtx.size();
+    // A_p / M_p pattern and contributions (triangle order); lumped-mass rows
+    {
+        std::vector<int> rr, cc, src, lr, lc, ls;
+        for (int t = 0; t < ntri; t++)
+            for (int a = 0; a < 3; a++) {
+                const int ia = x->vid[x->tri[3 * t + a]];
+                if (ia < 0) continue;
+                for (int b = 0; b < 3; b++) {
+                    lr.push_back(ia);
+                    lc.push_back(0);
+                    ls.push_back(9 * t + 3 * a + b);
+                    const int ib = x->vid[x->tri[3 * t + b]];
+                    if (ib < 0) continue;
+                    rr.push_back(ia);
+                    cc.push_back(ib);
+                    src.push_back(9 * t + 3 * a + b);
+                }
+            }
+        if (!build_csr(x->nvi, rr, cc, src, x->am) || !build_csr(x->nvi, lr, lc, ls, x->lump)) {
+            delete x;
+            return BMG_ERR_SHAPE;
+        }
+        x->diag_pos.assign(x->nvi, -1);
+        for (int i = 0; i < x->nvi; i++)
+            for (int k = x->am.ptr[i]; k < x->am.ptr[i + 1]; k++)
+                if (x->am.col[k] == i) x->diag_pos[i] = k;
+        for (int i = 0; i < x->nvi; i++)
+            if (x->diag_pos[i] < 0 || x->lump.ptr[i + 1] != i + 1) {   // an interior vertex in no triangle
+                delete x;
+                return BMG_ERR_ARG;
+            }
+    }
+    // (triangle, cell) pairs and the C pattern
+    {
+        const int n = x->n;
+        const double h = 1.0 / (n - 1);
+        std::vector<int> rr, cc, src;
+        for (int t = 0; t < ntri; t++) {
+            double sx[3], sy[3];
+            for (int a = 0; a < 3; a++) {
+                sx[a] = x->st[2 * x->tri[3 * t + a]];
+                sy[a] = x->st[2 * x->tri[3 * t + a] + 1];
+            }
+            auto cell_of = [&](double v) {
+                long long k = (long long)floor(v / h);
+                return (int)std::min<long long>(std::max<long long>(k, 0), n - 2);
+            };
+            const int i0 = cell_of(std::min(sx[0], std::min(sx[1], sx[2])));
+            const int i1 = cell_of(std::max(sx[0], std::max(sx[1], sx[2])));
+            const int j0 = cell_of(std::min(sy[0], std::min(sy[1], sy[2])));
+            const int j1 = cell_of(std::max(sy[0], std::max(sy[1], sy[2])));
+            for (int cj = j0; cj <= j1; cj++)
+                for (int ci = i0; ci <= i1; ci++) {
+                    if (!tri_box_overlap(sx, sy, ci * h, cj * h, (ci + 1) * h, (cj + 1) * h)) continue;
+                    const long long p = (long long)x->pair_tri.size();
+                    if (12 * (p + 1) > 0x7fffffffLL) {
+                        delete x;
+                        return BMG_ERR_SHAPE;
+                    }
+                    x->pair_tri.push_back(t);
+                    x->pair_cell.push_back(cj * (n - 1) + ci);
+                    for (int a = 0; a < 3; a++) {
+                        const int ia = x->vid[x->tri[3 * t + a]];
+                        if (ia < 0) continue;
+                        for (int b = 0; b < 4; b++) {
+                            const int i = ci + (b & 1), j = cj + (b >> 1);
+                            if (i < 1 || j < 1 || i > n - 2 || j > n - 2) continue;
+                            rr.push_back(ia);
+                            cc.push_back(j * x->ld + i);
+                            src.push_back((int)(12 * p + 4 * a + b));
+                        }
+                    }
+                }
+        }
+        if (!build_csr(x->nvi, rr, cc, src, x->cm)) {
+            delete x;
+            return BMG_ERR_SHAPE;
+        }
+        // C^T: rows = interior coarse nodes (j-1)(n-2) + (i-1), entries in C order
+        const int nq = (n - 2) * (n - 2);
+        x->ct_map.resize(nq);
+        for (int j = 1; j <= n - 2; j++)
+            for (int i = 1; i <= n - 2; i++) x->ct_map[(j - 1) * (n - 2) + (i - 1)] = j * x->ld + i;
+        x->ct_ptr.assign(nq + 1, 0);
+        auto q_of = [&](int col) { return (col / x->ld - 1) * (n - 2) + (col % x->ld - 1); };
+        for (int k = 0; k < (int)x->cm.col.size(); k++) x->ct_ptr[q_of(x->cm.col[k]) + 1]++;
+        for (int q = 0; q < nq; q++) x->ct_ptr[q + 1] += x->ct_ptr[q];
+        x->ct_col.resize(x->cm.col.size());
+        x->ct_perm.resize(x->cm.col.size());
+        std::vector<int> pos(x->ct_ptr.begin(), x->ct_ptr.end() - 1);
+        for (int i = 0; i < x->nvi; i++)
+            for (int k = x->cm.ptr[i]; k < x->cm.ptr[i + 1]; k++) {
+                const int q = q_of(x->cm.col[k]);
+                x->ct_col[pos[q]] = i;
+                x->ct_perm[pos[q]] = k;
+                pos[q]++;
+            }
+    }
+    x->ws_need = carve_aux(*x, nullptr);
+    *out = x;
+    return BMG_OK;
+}
+
+extern "C" bmg_status bmg_aux_workspace_bytes(const bmg_aux* x, size_t* bytes) {
+    if (!x || !bytes) return BMG_ERR_ARG;
+    *bytes = x->ws_need;
+    return BMG_OK;
+}
+
+namespace {
+bool on_device(const void* p) {
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+}  // namespace
+
+extern "C" bmg_status bmg_aux_setup(bmg_aux* x, void* ws, size_t bytes, const double* kappa, const double* coords) {
+    if (!x || !ws || !kappa || !coords) return BMG_ERR_ARG;
+    if (!on_device(ws) || !on_device(kappa) || !on_device(coords)) return BMG_ERR_ARG;
+    if (((uintptr_t)ws & 255) != 0) return BMG_ERR_ARG;
+    if (bytes < x->ws_need) return BMG_ERR_WORKSPACE;
+    Ctx& c = x->coarse->c;
+    if (!c.attached || !c.have_setup) return BMG_ERR_STATE;
+    cudaStream_t s = c.stream;
+    carve_aux(*x, (char*)ws);
+    BMG_CUDA(cudaMemsetAsync(x->d_st_aux, 0, sizeof(AuxState), s));
+    BMG_TRY(up(x->d_tri, x->tri, s));
+    BMG_TRY(up(x->d_vid, x->vid, s));
+    BMG_TRY(up(x->d_vtx, x->vtx, s));
+    BMG_TRY(up(x->d_pair_tri, x->pair_tri, s));
+    BMG_TRY(up(x->d_pair_cell, x->pair_cell, s));
+    BMG_TRY(up(x->d_xy, x->xy, s));
+    BMG_TRY(up(x->d_st, x->st, s));
+    BMG_TRY(up(x->d_am_ptr, x->am.ptr, s));
+    BMG_TRY(up(x->d_am_col, x->am.col, s));
+    BMG_TRY(up(x->d_am_gptr, x->am.gptr, s));
+    BMG_TRY(up(x->d_am_gidx, x->am.gidx, s));
+    BMG_TRY(up(x->d_diag, x->diag_pos, s));
+    BMG_TRY(up(x->d_lp_gptr, x->lump.gptr, s));
+    BMG_TRY(up(x->d_lp_gidx, x->lump.gidx, s));
+    BMG_TRY(up(x->d_c_ptr, x->cm.ptr, s));
+    BMG_TRY(up(x->d_c_col, x->cm.col, s));
+    BMG_TRY(up(x->d_c_gptr, x->cm.gptr, s));
+    BMG_TRY(up(x->d_c_gidx, x->cm.gidx, s));
+    BMG_TRY(up(x->d_ct_ptr, x->ct_ptr, s));
+    BMG_TRY(up(x->d_ct_col, x->ct_col, s));
+    BMG_TRY(up(x->d_ct_perm, x->ct_perm, s));
+    BMG_TRY(up(x->d_ct_map, x->ct_map, s));
+    const int npairs = (int)x->pair_tri.size();
+    k_tri_local<<<blocks(x->ntri), kAuxThreads, 0, s>>>(x->ntri, x->d_tri, x->d_xy, kappa, x->d_lk, x->d_lm,
+                                                        x->d_st_aux);
+    if (npairs > 0)
+        k_pair_local<<<cdiv(npairs, 128), 128, 0, s>>>(npairs, x->d_pair_tri, x->d_pair_cell, x->d_tri, x->d_st,
+                                                       coords, x->n, x->d_loc);
+    const int nnz = (int)x->am.col.size(), nnzc = (int)x->cm.col.size();
+    if (nnz > 0) {
+        k_gather<<<blocks(nnz), kAuxThreads, 0, s>>>(nnz, x->d_am_gptr, x->d_am_gidx, x->d_lk, x->d_va);
+        k_gather<<<blocks(nnz), kAuxThreads, 0, s>>>(nnz, x->d_am_gptr, x->d_am_gidx, x->d_lm, x->d_vm);
+    }
+    if (x->nvi > 0) {
+        k_diag_inv<<<blocks(x->nvi), kAuxThreads, 0, s>>>(x->nvi, x->d_diag, x->d_va, x->d_dinv);
+        k_gather<<<blocks(x->nvi), kAuxThreads, 0, s>>>(x->nvi, x->d_lp_gptr, x->d_lp_gidx, x->d_lm, x->d_mlinv);
+        k_inv<<<blocks(x->nvi), kAuxThreads, 0, s>>>(x->nvi, x->d_mlinv);
+    }
+    if (nnzc > 0) {
+        k_gather<<<blocks(nnzc), kAuxThreads, 0, s>>>(nnzc, x->d_c_gptr, x->d_c_gidx, x->d_loc, x->d_vc);
+        k_permute<<<blocks(nnzc), kAuxThreads, 0, s>>>(nnzc, x->d_ct_perm, x->d_vc, x->d_vct);
+    }
+    BMG_CUDA(cudaGetLastError());
+    AuxState h;
+    BMG_TRY(aux_read(*x, h));
+    if (h.err) return (bmg_status)h.err;
+    x->ready = true;
+    return BMG_OK;
+}
+
+extern "C" bmg_status bmg_aux_solve(bmg_aux* x, const double* f, double* u, double tol, int maxit, bmg_info* info) {
+    if (!x || !f || !u || maxit < 0) return BMG_ERR_ARG;
+    if (!on_device(f) || !on_device(u)) return BMG_ERR_ARG;
+    if (!x->ready || !x->coarse->c.have_setup) return BMG_ERR_STATE;
+    Ctx& c = x->coarse->c;
+    cudaStream_t s = c.stream;
+    const int nr = x->nvi;
+    k_compress<<<blocks(nr), kAuxThreads, 0, s>>>(nr, x->d_vtx, f, x->d_f);
+    k_compress<<<blocks(nr), kAuxThreads, 0, s>>>(nr, x->d_vtx, u, x->d_u);
+    k_dot_aux<<<kRedBlocks, kAuxThreads, 0, s>>>(nr, x->d_f, x->d_f, x->d_partials, &x->d_st_aux->counter[0],
+                                                 &x->d_st_aux->ff);
+    k_residual_csr<<<kRedBlocks, kAuxThreads, 0, s>>>(nr, x->d_am_ptr, x->d_am_col, x->d_va, x->d_f, x->d_u, nullptr,
+                                                      x->d_partials, &x->d_st_aux->counter[0], &x->d_st_aux->rr);
+    BMG_CUDA(cudaGetLastError());
+    AuxState h;
+    BMG_TRY(aux_read(*x, h));
+    const double nf = sqrt(h.ff);
+    double rel = nf > 0.0 ? sqrt(h.rr) / nf : 0.0;
+    int it = 0;
+    while (it < maxit && rel > tol && nf > 0.0) {
+        BMG_TRY(aux_cycle(*x));
+        k_residual_csr<<<kRedBlocks, kAuxThreads, 0, s>>>(nr, x->d_am_ptr, x->d_am_col, x->d_va, x->d_f, x->d_u,
+                                                          nullptr, x->d_partials, &x->d_st_aux->counter[0],
+                                                          &x->d_st_aux->rr);
+        BMG_CUDA(cudaGetLastError());
+        BMG_TRY(aux_read(*x, h));
+        rel = sqrt(h.rr) / nf;
+        it++;
+        if (!(rel == rel)) break;   // NaN: diverged
+    }
+    k_expand<<<blocks(x->nv), kAuxThreads, 0, s>>>(x->nv, x->d_vid, x->d_u, u);
+    BMG_CUDA(cudaGetLastError());
+    BMG_CUDA(cudaStreamSynchronize(s));
+    const bmg_status st = rel <= tol || nf == 0.0 ? BMG_OK : BMG_ERR_NOT_CONVERGED;
+    if (info) {
+        memset(info, 0, sizeof(*info));
+        info->iterations = it;
+        info->levels = c.nlev + 1;
+        info->relres = rel;
+        info->true_relres = rel;
+        info->rho = it > 0 && rel > 0.0 ? pow(rel, 1.0 / it) : 0.0;
+        info->status = st;
+    }
+    return st;
+}
+
+extern "C" bmg_status bmg_aux_set_gamma(bmg_aux* x, double gamma) {
+    if (!x || !(gamma > 0.0)) return BMG_ERR_ARG;
+    x->opts.gamma = gamma;
+    return BMG_OK;
+}
+
+extern "C" bmg_status bmg_aux_export(const bmg_aux* x, int which, int* nrows, long long* nnz, long long* rowptr,
+                                     int* col, double* val) {
+    if (!x || !nrows || !nnz || which < 0 || which > 2) return BMG_ERR_ARG;
+    const bool isc = which == 2;
+    const std::vector<int>& ptr = isc ? x->cm.ptr : x->am.ptr;
+    const std::vector<int>& cl = isc ? x->cm.col : x->am.col;
+    *nrows = x->nvi;
+    *nnz = (long long)cl.size();
+    if (rowptr)
+        for (size_t k = 0; k < ptr.size(); k++) rowptr[k] = ptr[k];
+    if (col)
+        for (size_t k = 0; k < cl.size(); k++) col[k] = isc ? (cl[k] / x->ld) * x->n + cl[k] % x->ld : cl[k];
+    if (val) {
+        if (!x->ready) return BMG_ERR_STATE;
+        const double* src = which == 0 ? x->d_va : which == 1 ? x->d_vm : x->d_vc;
+        if (!cl.empty()) {
+            BMG_CUDA(cudaMemcpy(val, src, sizeof(double) * cl.size(), cudaMemcpyDeviceToHost));
+        }
+    }
+    return BMG_OK;
+}
+
+extern "C" void bmg_aux_destroy(bmg_aux* x) { delete x; }

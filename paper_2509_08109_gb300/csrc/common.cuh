@@ -337,3 +337,8 @@ bmg_status pspmv_prepare(Ctx& c);                // tile shape of the 2-D operat
 bmg_status k_pspmv32(Ctx& c, const float* z, int parity);   // p = z + beta p_old; q = A p; alpha
 
 }  // namespace bmg
+
+// The opaque context of the C ABI.
+struct bmg_ctx {
+    bmg::Ctx c;
+};

@@ -363,13 +363,16 @@ class Mesh:
     f: np.ndarray
 
 
-def annulus_mesh(nr: int, nt: int, jitter: float = 0.3, seed: int = 8) -> Mesh:
+def annulus_mesh(nr: int, nt: int, jitter: float = 0.2, seed: int = 8) -> Mesh:
     """Jittered polar triangulation of the quarter annulus r in [1/2, 1],
     theta in [0, pi/2] (the domain of coords_quarter_annulus): nr x nt
     vertices on the lattice r_k = 1/2 + k / (2 (nr-1)), theta_l = pi l /
     (2 (nt-1)); interior vertices moved by up to `jitter` lattice spacings
     in r and theta (uniform, seed); each lattice quad split along the
-    diagonal (k+l) % 2 selects.  T maps (r, theta) to s = 2 r - 1,
+    diagonal (k+l) % 2 selects.  No triangle folds for jitter < 1/4: every
+    vertex starts at least 1/sqrt(2) spacings from the opposite side, and
+    moving it and that side's ends by at most sqrt(2) jitter each changes
+    the distance by at most 2 sqrt(2) jitter.  T maps (r, theta) to s = 2 r - 1,
     t = 2 theta / pi, so boundary vertices land on the square's sides and
     the mapped triangles tile [0, 1]^2.  kappa = 1 (the paper's default,
     D = I); f ~ U[-1, 1] per interior vertex, drawn after the jitter."""

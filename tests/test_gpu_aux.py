@@ -1,0 +1,121 @@
+"""Auxiliary-space two-grid method (Sec. 2.2 "Setup phase" / "Solution
+phase", Sec. 2.3): the library's A_p, M_p and C against the oracle's, its
+cycle against the oracle's cycle at a fixed count, its solves against the
+oracle's, and its argument and state checks."""
+import numpy as np
+import pytest
+import scipy.sparse as sp
+import torch
+
+import oracle
+from oracle import aux
+from paper_2509_08109_gb300 import binding, inputs
+from tests.gpu_util import relerr
+
+pytestmark = pytest.mark.gpu
+
+
+def _coarse(n, precision="fp64"):
+    coords = inputs.coords_quarter_annulus(n)
+    s = binding.Solver(2, n, precision=precision)
+    s.assemble(torch.as_tensor(coords), torch.ones((n - 1, n - 1), dtype=torch.float64)).setup()
+    return coords, s
+
+
+def _oracle(m, coords, mass_steps=0):
+    n = coords.shape[-1]
+    return aux.TwoGrid(m, coords, oracle.assemble(coords, np.ones((n - 1, n - 1))), mass_steps=mass_steps)
+
+
+def _csr(a, which, shape):
+    rp, col, val = a.export(which)
+    return sp.csr_matrix((val, col, rp), shape=shape)
+
+
+@pytest.mark.parametrize("nr,nt,n", [(25, 37, 17), (14, 9, 9)])
+def test_operators_match_oracle(nr, nt, n):
+    m = inputs.annulus_mesh(nr, nt)
+    coords, s = _coarse(n)
+    a = binding.AuxSolver(s, m)
+    tg = _oracle(m, coords)
+    nvi = len(tg.iv)
+    A = _csr(a, "A", (nvi, nvi))
+    M = _csr(a, "M", (nvi, nvi))
+    C = _csr(a, "C", (nvi, n * n))[:, tg.ic]
+    for got, ref in ((A, tg.A), (M, tg.M), (C, tg.C)):
+        r = ref.toarray()
+        assert np.abs(got.toarray() - r).max() <= 1e-13 * np.abs(r).max()
+
+
+@pytest.mark.parametrize("mass_steps", [0, 3])
+def test_fixed_cycles_match_oracle(mass_steps):
+    """tol 0 runs exactly maxit cycles on both sides."""
+    m = inputs.annulus_mesh(25, 37)
+    coords, s = _coarse(17)
+    a = binding.AuxSolver(s, m, mass_steps=mass_steps)
+    tg = _oracle(m, coords, mass_steps)
+    f = m.f[tg.iv]
+    u = np.zeros_like(f)
+    for _ in range(5):
+        u = tg.cycle(f, u)
+    got, info = a.solve(torch.as_tensor(m.f, device="cuda"), tol=0.0, maxit=5, raise_on_nonconv=False)
+    assert info.iterations == 5
+    got = got.cpu().numpy()
+    assert np.all(got[m.dirichlet] == 0.0)
+    assert relerr(got[tg.iv], u) <= 1e-11
+
+
+@pytest.mark.parametrize("mass_steps", [0, 3])
+def test_solve_matches_oracle(mass_steps):
+    m = inputs.annulus_mesh(25, 37)
+    coords, s = _coarse(17)
+    a = binding.AuxSolver(s, m, mass_steps=mass_steps)
+    uo, ito, _ = _oracle(m, coords, mass_steps).solve(m.f, tol=1e-10)
+    u, info = a.solve(torch.as_tensor(m.f, device="cuda"), tol=1e-10)
+    assert info.status == 0 and info.true_relres <= 1e-10
+    assert abs(info.iterations - ito) <= 1
+    assert relerr(u.cpu().numpy(), uo) <= 1e-8
+
+
+def test_fp32_coarse_level_and_residual_recomputed():
+    """An FP32 V-cycle as the coarse solve; the returned iterate's residual,
+    recomputed on the host from the exported A_p, meets the tolerance."""
+    m = inputs.annulus_mesh(97, 145)
+    coords, s = _coarse(65, precision="fp32")
+    a = binding.AuxSolver(s, m)
+    u, info = a.solve(torch.as_tensor(m.f, device="cuda"), tol=1e-10)
+    assert info.status == 0
+    iv = np.flatnonzero(~m.dirichlet)
+    A = _csr(a, "A", (len(iv), len(iv)))
+    r = m.f[iv] - A @ u.cpu().numpy()[iv]
+    assert np.linalg.norm(r) <= 1.0001e-10 * np.linalg.norm(m.f[iv])
+
+
+def test_coupled_mass_signs_and_rows():
+    """Interior block of C: no entry below -eps max (products of
+    non-negative bases and |det J|; barycentric coordinates of points on a
+    clipped edge can round to -eps), and every interior vertex couples to
+    some interior node."""
+    m = inputs.annulus_mesh(41, 61)
+    coords, s = _coarse(33)
+    a = binding.AuxSolver(s, m)
+    rp, col, val = a.export("C")
+    assert val.min() >= -1e-15 * val.max() and val.max() > 0.0
+    assert np.all(np.diff(rp) > 0)
+
+
+def test_errors():
+    m = inputs.annulus_mesh(9, 13)
+    s = binding.Solver(2, 9)
+    with pytest.raises(binding.BmgError) as e:          # coarse level not set up
+        binding.AuxSolver(s, m)
+    assert e.value.code == 10
+    coords, s = _coarse(9)
+    with pytest.raises(binding.BmgError) as e:          # Jacobi weight out of range
+        binding.AuxSolver(s, m, omega=2.5)
+    assert e.value.code == 1
+    bad = inputs.annulus_mesh(9, 13)
+    bad.tri = bad.tri[:, [0, 2, 1]].copy()               # clockwise: negative physical area
+    with pytest.raises(binding.BmgError) as e:
+        binding.AuxSolver(s, bad)
+    assert e.value.code == 5
