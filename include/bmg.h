@@ -369,6 +369,23 @@ bmg_status bmg_aux_solve(bmg_aux* aux, const double* f, double* u, double tol, i
 
 bmg_status bmg_aux_set_gamma(bmg_aux* aux, double gamma);
 
+/* Coarse-grid scaling gamma (Sec. 2.4, Eqs. cgc_scaling_1 and gen_eigvalue):
+   the mean of the Ritz values of k steps of generalized Lanczos on the
+   pencil (P^T A_p P, A_c), i.e. on A_c^-1 P^T A_p P in the A_c inner
+   product, with the solver's own P and P^T.  The start vector is
+   A_c^-1 y0 (y0: device, the coarse grid's n x n layout, boundary
+   ignored).  The recurrence carries the dual vectors A_c q_j, so each step
+   costs one P^T A_p P product and one solve with the coarse context (to
+   relative residual tol; the context's Krylov buffers are overwritten).
+   The mean of the Ritz values is the mean of the Lanczos alpha_j (the
+   trace of the tridiagonal matrix over its order).  Outputs (host):
+   gamma; alpha (k doubles), beta (k-1 doubles) and steps (the number of
+   alphas written: fewer than k if the Krylov space became invariant), each
+   may be NULL.  Does not change the aux object's gamma (bmg_aux_set_gamma
+   does).  Errors: BMG_ERR_ARG, BMG_ERR_STATE, and the coarse solve's. */
+bmg_status bmg_aux_estimate_gamma(bmg_aux* aux, int k, const double* y0, double tol, double* gamma,
+                                  double* alpha, double* beta, int* steps);
+
 /* Exports a matrix as CSR into host arrays (each may be NULL to query the
    sizes): which 0 = A_p, 1 = M_p (rows and columns: interior vertices in
    increasing vertex order), 2 = C (rows: interior vertices; columns: the

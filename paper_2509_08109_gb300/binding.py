@@ -105,6 +105,7 @@ def load() -> ctypes.CDLL:
         "bmg_aux_setup": ([P, P, ctypes.c_size_t, P, P], I),
         "bmg_aux_solve": ([P, P, P, D, I, ctypes.POINTER(_Info)], I),
         "bmg_aux_set_gamma": ([P, D], I),
+        "bmg_aux_estimate_gamma": ([P, I, P, D, ctypes.POINTER(D), P, P, ctypes.POINTER(I)], I),
         "bmg_aux_export": ([P, I, ctypes.POINTER(I), ctypes.POINTER(ctypes.c_longlong), P, P, P], I),
         "bmg_aux_destroy": ([P], None),
     }
@@ -124,7 +125,8 @@ def exported_symbols() -> list:
             "bmg_set_tiles", "bmg_autotune", "bmg_profile",
             "bmg_profile_read", "bmg_destroy", "bmg_status_str", "bmg_assemble_noalloc", "bmg_assemble_tensor",
             "bmg_boundary_rhs", "bmg_aux_default_opts", "bmg_aux_create", "bmg_aux_workspace_bytes",
-            "bmg_aux_setup", "bmg_aux_solve", "bmg_aux_set_gamma", "bmg_aux_export", "bmg_aux_destroy"]
+            "bmg_aux_setup", "bmg_aux_solve", "bmg_aux_set_gamma", "bmg_aux_estimate_gamma", "bmg_aux_export",
+            "bmg_aux_destroy"]
 
 
 def _check(code: int, where: str):
@@ -464,6 +466,29 @@ class AuxSolver:
 
     def set_gamma(self, gamma: float):
         _check(load().bmg_aux_set_gamma(self._h, float(gamma)), "bmg_aux_set_gamma")
+
+    def estimate_gamma(self, k: int = 12, y0=None, seed: int = 9, tol: float = 1e-10, apply: bool = False):
+        """gamma = mean of the k Ritz values of generalized Lanczos on
+        (P^T A_p P, A_c) (bmg_aux_estimate_gamma); y0 defaults to U[-1, 1]
+        on the coarse grid (seeded).  Returns (gamma, alpha, beta)."""
+        import numpy as np
+        n = self.coarse.n
+        if y0 is None:
+            y0 = np.random.default_rng(seed).uniform(-1.0, 1.0, size=(n, n))
+        y0 = torch.as_tensor(y0, dtype=torch.float64).to(self.coarse.device).contiguous()
+        g = ctypes.c_double()
+        alpha = np.zeros(k)
+        beta = np.zeros(max(k - 1, 1))
+        steps = ctypes.c_int()
+        with torch.cuda.device(self.coarse.device):
+            _check(load().bmg_aux_estimate_gamma(self._h, int(k), _ptr(y0), float(tol), ctypes.byref(g),
+                                                 alpha.ctypes.data_as(ctypes.c_void_p),
+                                                 beta.ctypes.data_as(ctypes.c_void_p), ctypes.byref(steps)),
+                   "bmg_aux_estimate_gamma")
+        if apply:
+            self.set_gamma(g.value)
+        m = steps.value
+        return g.value, alpha[:m], beta[:max(m - 1, 0)]
 
     def solve(self, f, u0=None, tol: float = 1e-10, maxit: int = 500, raise_on_nonconv=True):
         dev = self.coarse.device

@@ -351,6 +351,54 @@ __global__ void k_axpy(int nr, double* __restrict__ u, const double* __restrict_
     if (i < nr) u[i] += gamma * v[i];
 }
 
+__global__ void k_spmv_csr(int nr, const int* __restrict__ rp, const int* __restrict__ ci,
+                           const double* __restrict__ va, const double* __restrict__ x, double* __restrict__ y) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < nr) y[i] = csr_row(rp, ci, va, x, i);
+}
+
+__global__ void k_scale(int nr, double* __restrict__ v, const double* __restrict__ w) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < nr) v[i] *= w[i];
+}
+
+// natural n x n grid vector <-> the coarse context's padded layout (interior only)
+__global__ void k_to_padded(int n, int ld, const double* __restrict__ src, double* __restrict__ dst) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x, j = blockIdx.y;
+    if (i >= ld) return;
+    const bool in = i >= 1 && j >= 1 && i <= n - 2 && j <= n - 2;
+    dst[(long long)j * ld + i] = in ? src[(long long)j * n + i] : 0.0;
+}
+
+__global__ void k_from_padded(int n, int ld, const double* __restrict__ src, double* __restrict__ dst) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x, j = blockIdx.y;
+    if (i >= n) return;
+    const bool in = i >= 1 && j >= 1 && i <= n - 2 && j <= n - 2;
+    dst[(long long)j * n + i] = in ? src[(long long)j * ld + i] : 0.0;
+}
+
+// Lanczos step: w -= alpha q + beta q_prev; v -= alpha b + beta b_prev
+__global__ void k_lanczos_orth(int nr, double* __restrict__ w, const double* __restrict__ q,
+                               const double* __restrict__ qp, double* __restrict__ v, const double* __restrict__ b,
+                               const double* __restrict__ bp, double alpha, double beta) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= nr) return;
+    w[i] -= alpha * q[i] + beta * qp[i];
+    v[i] -= alpha * b[i] + beta * bp[i];
+}
+
+// q_prev = q, q = w / beta; b_prev = b, b = v / beta
+__global__ void k_lanczos_shift(int nr, double* __restrict__ q, double* __restrict__ qp, const double* __restrict__ w,
+                                double* __restrict__ b, double* __restrict__ bp, const double* __restrict__ v,
+                                double inv_beta) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= nr) return;
+    qp[i] = q[i];
+    q[i] = w[i] * inv_beta;
+    bp[i] = b[i];
+    b[i] = v[i] * inv_beta;
+}
+
 inline int blocks(long long n) { return cdiv(n, kAuxThreads); }
 
 // ------------------------------------------------------------------ host structure
@@ -444,6 +492,9 @@ struct bmg_aux {
            *d_cp = nullptr, *d_cq = nullptr, *d_w = nullptr;
     double* d_partials = nullptr;
     AuxState* d_st_aux = nullptr;
+    // coarse-grid scaling (Lanczos): padded and natural coarse vectors
+    double *d_cpad = nullptr, *d_cpad2 = nullptr;
+    double *d_lq = nullptr, *d_lqp = nullptr, *d_lb = nullptr, *d_lbp = nullptr, *d_lv = nullptr, *d_lw = nullptr;
 };
 
 namespace {
@@ -495,6 +546,11 @@ size_t carve_aux(bmg_aux& x, char* base) {
     for (double** v : vecs) *v = (double*)take(D * std::max(x.nvi, 1));
     x.d_partials = (double*)take(D * kRedBlocks);
     x.d_st_aux = (AuxState*)take(sizeof(AuxState));
+    const size_t plane = (size_t)x.ld * x.n, nn = (size_t)x.n * x.n;
+    x.d_cpad = (double*)take(D * plane);
+    x.d_cpad2 = (double*)take(D * plane);
+    double** lv[] = {&x.d_lq, &x.d_lqp, &x.d_lb, &x.d_lbp, &x.d_lv, &x.d_lw};
+    for (double** v : lv) *v = (double*)take(D * nn);
     return a256(off);
 }
 
@@ -836,6 +892,114 @@ extern "C" bmg_status bmg_aux_solve(bmg_aux* x, const double* f, double* u, doub
         info->status = st;
     }
     return st;
+}
+
+namespace {
+
+__global__ void k_scale2(int nr, double* __restrict__ a, double* __restrict__ b, double s) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < nr) {
+        a[i] *= s;
+        b[i] *= s;
+    }
+}
+
+bmg_status dot_nat(bmg_aux& x, const double* a, const double* b, int len, double* out) {
+    cudaStream_t s = x.coarse->c.stream;
+    k_dot_aux<<<kRedBlocks, kAuxThreads, 0, s>>>(len, a, b, x.d_partials, &x.d_st_aux->counter[0], &x.d_st_aux->rr);
+    BMG_CUDA(cudaGetLastError());
+    AuxState h;
+    BMG_TRY(aux_read(x, h));
+    *out = h.rr;
+    return BMG_OK;
+}
+
+// v = P^T A_p P q on the coarse grid's natural n x n layout (boundary zero),
+// with the solver's own P = M_p^-1 C and P^T = C^T M_p^-1
+bmg_status apply_ptap(bmg_aux& x, const double* q, double* v) {
+    Ctx& c = x.coarse->c;
+    cudaStream_t s = c.stream;
+    const int nr = x.nvi, nq = (int)x.ct_map.size();
+    const bool lumped = x.opts.mass_steps == 0;
+    const dim3 gp(blocks(x.ld), x.n);
+    k_to_padded<<<gp, kAuxThreads, 0, s>>>(x.n, x.ld, q, x.d_cpad);
+    k_prolong_c<<<blocks(nr), kAuxThreads, 0, s>>>(nr, x.d_c_ptr, x.d_c_col, x.d_vc, x.d_cpad,
+                                                   lumped ? x.d_mlinv : nullptr, x.d_w, nullptr, 0.0);
+    const double* y = x.d_w;
+    if (!lumped) {
+        BMG_TRY(mass_cg(x, x.d_w, x.d_y));
+        y = x.d_y;
+    }
+    k_spmv_csr<<<blocks(nr), kAuxThreads, 0, s>>>(nr, x.d_am_ptr, x.d_am_col, x.d_va, y, x.d_r);
+    const double* z = x.d_r;
+    if (!lumped) {
+        BMG_TRY(mass_cg(x, x.d_r, x.d_y));
+        z = x.d_y;
+    }
+    BMG_CUDA(cudaMemsetAsync(x.d_cpad2, 0, sizeof(double) * (size_t)x.ld * x.n, s));
+    k_restrict_ct<<<blocks(nq), kAuxThreads, 0, s>>>(nq, x.d_ct_ptr, x.d_ct_col, x.d_vct, x.d_ct_map, z,
+                                                     lumped ? x.d_mlinv : nullptr, x.d_cpad2);
+    k_from_padded<<<gp, kAuxThreads, 0, s>>>(x.n, x.ld, x.d_cpad2, v);
+    BMG_CUDA(cudaGetLastError());
+    return BMG_OK;
+}
+
+bmg_status coarse_solve(bmg_aux& x, const double* b, double* w, double tol) {
+    BMG_CUDA(cudaMemsetAsync(w, 0, sizeof(double) * (size_t)x.n * x.n, x.coarse->c.stream));
+    bmg_info info;
+    return bmg_solve(x.coarse, b, w, tol, 2000, &info);
+}
+
+}  // namespace
+
+extern "C" bmg_status bmg_aux_estimate_gamma(bmg_aux* x, int k, const double* y0, double tol, double* gamma,
+                                             double* alpha, double* beta, int* steps) {
+    if (!x || !y0 || !gamma || k < 1 || k > 256 || !(tol > 0.0)) return BMG_ERR_ARG;
+    if (!on_device(y0)) return BMG_ERR_ARG;
+    if (!x->ready || !x->coarse->c.have_setup) return BMG_ERR_STATE;
+    cudaStream_t s = x->coarse->c.stream;
+    const int nn = x->n * x->n;
+    const dim3 gp(blocks(x->ld), x->n);
+    // b_0 = y0 on the interior nodes, q_0 = A_c^-1 b_0, both scaled to q_0^T A_c q_0 = 1
+    k_to_padded<<<gp, kAuxThreads, 0, s>>>(x->n, x->ld, y0, x->d_cpad);
+    k_from_padded<<<gp, kAuxThreads, 0, s>>>(x->n, x->ld, x->d_cpad, x->d_lb);
+    BMG_CUDA(cudaGetLastError());
+    BMG_TRY(coarse_solve(*x, x->d_lb, x->d_lq, tol));
+    double qq = 0.0;
+    BMG_TRY(dot_nat(*x, x->d_lq, x->d_lb, nn, &qq));
+    if (!(qq > 0.0)) return BMG_ERR_ARG;
+    k_scale2<<<blocks(nn), kAuxThreads, 0, s>>>(nn, x->d_lq, x->d_lb, 1.0 / sqrt(qq));
+    BMG_CUDA(cudaMemsetAsync(x->d_lqp, 0, sizeof(double) * nn, s));
+    BMG_CUDA(cudaMemsetAsync(x->d_lbp, 0, sizeof(double) * nn, s));
+    double bprev = 0.0, sum = 0.0;
+    int done = 0;
+    for (int j = 0; j < k; j++) {
+        // the vectors q_j (A_c-orthonormal) and their duals b_j = A_c q_j
+        BMG_TRY(apply_ptap(*x, x->d_lq, x->d_lv));                 // v = B q_j
+        double a = 0.0;
+        BMG_TRY(dot_nat(*x, x->d_lq, x->d_lv, nn, &a));           // alpha_j = q_j^T B q_j
+        BMG_TRY(coarse_solve(*x, x->d_lv, x->d_lw, tol));          // w = A_c^-1 B q_j
+        k_lanczos_orth<<<blocks(nn), kAuxThreads, 0, s>>>(nn, x->d_lw, x->d_lq, x->d_lqp, x->d_lv, x->d_lb, x->d_lbp,
+                                                          a, bprev);
+        BMG_CUDA(cudaGetLastError());
+        if (alpha) alpha[j] = a;
+        sum += a;
+        done = j + 1;
+        if (j + 1 == k) break;
+        double bb = 0.0;
+        BMG_TRY(dot_nat(*x, x->d_lw, x->d_lv, nn, &bb));           // ||w'||_{A_c}^2 = w'^T A_c w'
+        const double bj = sqrt(bb > 0.0 ? bb : 0.0);
+        if (beta) beta[j] = bj;
+        if (!(bj > 0.0)) break;                                     // invariant subspace
+        k_lanczos_shift<<<blocks(nn), kAuxThreads, 0, s>>>(nn, x->d_lq, x->d_lqp, x->d_lw, x->d_lb, x->d_lbp,
+                                                           x->d_lv, 1.0 / bj);
+        BMG_CUDA(cudaGetLastError());
+        bprev = bj;
+    }
+    BMG_CUDA(cudaStreamSynchronize(s));
+    *gamma = sum / done;
+    if (steps) *steps = done;
+    return BMG_OK;
 }
 
 extern "C" bmg_status bmg_aux_set_gamma(bmg_aux* x, double gamma) {

@@ -119,3 +119,26 @@ def test_errors():
     with pytest.raises(binding.BmgError) as e:
         binding.AuxSolver(s, bad)
     assert e.value.code == 5
+
+
+@pytest.mark.parametrize("mass_steps", [0, 3])
+def test_gamma_matches_oracle_lanczos(mass_steps):
+    """Coarse-grid scaling (Sec. 2.4): k = 12 steps of generalized Lanczos on
+    (P^T A_p P, A_c) from A_c^-1 y0.  The library's recurrence uses the dual
+    vectors A_c q_j and the coarse context's PCG; the oracle's uses A_c and
+    dense solves.  Same alphas, same gamma."""
+    m = inputs.annulus_mesh(25, 37)
+    coords, s = _coarse(17)
+    a = binding.AuxSolver(s, m, mass_steps=mass_steps)
+    tg = _oracle(m, coords, mass_steps)
+    y0 = np.random.default_rng(11).uniform(-1.0, 1.0, size=(17, 17))
+    g, alpha, beta = a.estimate_gamma(k=12, y0=y0, tol=1e-13)
+    Ac = oracle.dense_operator(oracle.assemble(coords, np.ones((16, 16))))
+    B = lambda x: tg.restrict(tg.A @ tg.prolong(x))
+    x0 = np.linalg.solve(Ac, y0.reshape(-1)[tg.ic])
+    go, ritz = aux.gamma_lanczos(B, lambda x: Ac @ x, lambda x: np.linalg.solve(Ac, x), x0, k=12)
+    assert len(alpha) == 12
+    assert abs(g - go) <= 1e-8 * abs(go)
+    assert abs(g - alpha.mean()) <= 1e-14 * abs(g)
+    T = np.diag(alpha) + np.diag(beta, 1) + np.diag(beta, -1)
+    assert np.allclose(np.sort(np.linalg.eigvalsh(T)), np.sort(ritz), rtol=1e-7, atol=0)
