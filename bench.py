@@ -547,7 +547,8 @@ def run_aux(args):
     physical size (845 x 1262 = 1,066,390 vertices), the 513^2 structured
     grid as its coarse level (interior nodes / physical DoF = 0.25, near the
     paper's coarsening factor 0.28), lumped mass, damped Jacobi 2/3,
-    gamma 1: stationary two-grid cycles to a 1e-10 relative residual."""
+    gamma 1, to a 1e-10 relative residual: the paper's stationary iteration
+    of cycles, and flexible CG with one cycle as the preconditioner."""
     import torch
     from paper_2509_08109_gb300 import binding, inputs
     torch.cuda.set_device(0)
@@ -558,37 +559,42 @@ def run_aux(args):
     s = binding.Solver(2, n, precision="fp32", outer="refine", graphs=not args.no_graphs)
     s.assemble(torch.as_tensor(coords), torch.ones((n - 1, n - 1), dtype=torch.float64)).setup()
     t1 = time.perf_counter()
-    a = binding.AuxSolver(s, m)
-    torch.cuda.synchronize()
-    t2 = time.perf_counter()
     f = torch.as_tensor(m.f, device="cuda")
     dof = int((~m.dirichlet).sum())
-    for _ in range(args.warmup):
-        a.solve(f, tol=TOL)
-    torch.cuda.synchronize()
-    times, infos = [], []
-    launches0 = s.launches
-    for _ in range(args.steps):
-        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    res = {}
+    for name, krylov in (("stationary", False), ("flexible_cg", True)):
+        t2 = time.perf_counter()
+        a = binding.AuxSolver(s, m, krylov=krylov)
         torch.cuda.synchronize()
-        ev0.record()
-        u, info = a.solve(f, tol=TOL)
-        ev1.record()
+        setup_s = time.perf_counter() - t2
+        for _ in range(args.warmup):
+            a.solve(f, tol=TOL)
         torch.cuda.synchronize()
-        times.append(ev0.elapsed_time(ev1))
-        infos.append(info)
-    ms = statistics.median(times)
+        times, infos = [], []
+        for _ in range(args.steps):
+            ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            torch.cuda.synchronize()
+            ev0.record()
+            u, info = a.solve(f, tol=TOL)
+            ev1.record()
+            torch.cuda.synchronize()
+            times.append(ev0.elapsed_time(ev1))
+            infos.append(info)
+        ms = statistics.median(times)
+        assert all(i.status == 0 and i.true_relres <= 1.01 * TOL for i in infos)
+        res[name] = {"value": dof / (ms * 1e-3), "ms_per_step": ms, "iterations": infos[-1].iterations,
+                     "true_relres": infos[-1].true_relres, "setup_s": setup_s}
+        del a
+    head = max(res, key=lambda k: res[k]["value"])
     out = {"metric": "physical DoF/s to 1e-10 rel. residual (auxiliary-space two-grid, BoxMG coarse level)",
-           "value": dof / (ms * 1e-3), "unit": UNIT, "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
-           "ms_per_step": ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-           "dtype": "f64 (physical level) / f32 V-cycle (coarse level)", "data": "synthetic",
+           "value": res[head]["value"], "unit": UNIT, "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+           "ms_per_step": res[head]["ms_per_step"], "higher_is_better": True, "scaling": "weak",
+           "vs_baseline": None, "dtype": "f64 (physical level) / f32 V-cycle (coarse level)", "data": "synthetic",
            "config": {"workload": "aux_annulus_p1_845x1262_coarse513", "physical_dof": dof,
                       "coarse_dof": (n - 2) ** 2, "triangles": int(m.tri.shape[0]), "tol": TOL,
                       "relaxation": "damped Jacobi 2/3, one pre and one post", "mass": "lumped", "gamma": 1.0,
-                      "timing": "CUDA events around bmg_aux_solve (host loop, one residual read per cycle)"},
-           "cycles": infos[-1].iterations, "true_relres": infos[-1].true_relres, "rho": infos[-1].rho,
-           "coarse_gpu_launches_per_solve": (s.launches - launches0) // args.steps,
-           "setup_s": {"coarse": t1 - t0, "aux_create_and_setup": t2 - t1}}
+                      "timing": "CUDA events around bmg_aux_solve (host loop, scalars read every iteration)"},
+           "headline_variant": head, "variants": res, "coarse_setup_s": t1 - t0}
     print(json.dumps(out), flush=True)
 
 

@@ -327,6 +327,8 @@ typedef struct {
     double omega;      /* Jacobi weight of S (default 2/3) */
     int mass_steps;    /* CG iterations for M_p^-1 (>= 1), or 0 for the lumped mass (default 0) */
     double gamma;      /* coarse-grid scaling (default 1) */
+    int krylov;        /* 0: the paper's stationary iteration of cycles (default); 1: flexible CG
+                          with one cycle from a zero guess as the preconditioner */
 } bmg_aux_opts;
 
 void bmg_aux_default_opts(bmg_aux_opts* opts);
@@ -358,8 +360,11 @@ bmg_status bmg_aux_workspace_bytes(const bmg_aux* aux, size_t* bytes);
    BMG_ERR_DEVICE. */
 bmg_status bmg_aux_setup(bmg_aux* aux, void* workspace, size_t bytes, const double* kappa, const double* coords);
 
-/* Stationary two-grid iteration until ||f - A_p u|| <= tol ||f|| over the
-   interior vertices, or maxit cycles.  f, u: device, nv doubles (all
+/* Stationary two-grid iteration (or flexible CG, opts.krylov = 1) until
+   ||f - A_p u|| <= tol ||f|| over the interior vertices, or maxit cycles
+   (CG iterations).  With flexible CG the reported residual is the true one
+   of the returned iterate, which can sit slightly above the recursive one
+   that stopped the loop.  f, u: device, nv doubles (all
    vertices); u holds the initial guess on entry and the iterate on exit,
    with its Dirichlet entries set to zero; f's Dirichlet entries are
    ignored.  info (may be NULL): cycles in `iterations`, the relative

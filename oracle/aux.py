@@ -241,6 +241,37 @@ class TwoGrid:
         return out, it, np.array(hist)
 
 
+    def solve_fcg(self, f_all, tol: float = 1e-10, maxit: int = 200):
+        """Flexible CG with one cycle from a zero guess as the preconditioner
+        (beta = r.(z - z_old) / r_old.z_old), until the recursive residual
+        meets tol; returns (u on all vertices, iterations, true relative
+        residual)."""
+        f = f_all[self.iv]
+        u = np.zeros_like(f)
+        r = f.copy()
+        nf = np.linalg.norm(f)
+        z = self.cycle(r, np.zeros_like(r))
+        p = z.copy()
+        rz = r @ z
+        it = 0
+        while it < maxit:
+            q = self.A @ p
+            alpha = rz / (p @ q)
+            u += alpha * p
+            r -= alpha * q
+            it += 1
+            if np.linalg.norm(r) <= tol * nf:
+                break
+            z_old = z
+            z = self.cycle(r, np.zeros_like(r))
+            beta = (r @ (z - z_old)) / rz
+            rz = r @ z
+            p = z + beta * p
+        out = np.zeros(self.mesh.xy.shape[0])
+        out[self.iv] = u
+        return out, it, np.linalg.norm(f - self.A @ u) / nf
+
+
 # ---------------------------------------------------------------- coarse-grid scaling
 def gamma_lanczos(B_apply, Ac_apply, Ac_solve, x0: np.ndarray, k: int = 12):
     """Generalized Lanczos on B x = lambda A_c x in the A_c inner product

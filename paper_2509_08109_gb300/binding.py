@@ -45,7 +45,8 @@ class _Info(ctypes.Structure):
 
 
 class _AuxOpts(ctypes.Structure):
-    _fields_ = [("omega", ctypes.c_double), ("mass_steps", ctypes.c_int), ("gamma", ctypes.c_double)]
+    _fields_ = [("omega", ctypes.c_double), ("mass_steps", ctypes.c_int), ("gamma", ctypes.c_double),
+                ("krylov", ctypes.c_int)]
 
 
 @dataclass
@@ -430,9 +431,11 @@ class AuxSolver:
     mesh: an object with xy (nv x 2), st (nv x 2, computational images),
     tri (ntri x 3), dirichlet (nv bools) and kappa (ntri) arrays, e.g.
     inputs.annulus_mesh.  mass_steps: CG iterations for M_p^-1 in P, or 0
-    for the lumped mass."""
+    for the lumped mass.  krylov: flexible CG with one cycle as the
+    preconditioner instead of the paper's stationary iteration."""
 
-    def __init__(self, coarse: "Solver", mesh, omega: float = 2.0 / 3.0, mass_steps: int = 0, gamma: float = 1.0):
+    def __init__(self, coarse: "Solver", mesh, omega: float = 2.0 / 3.0, mass_steps: int = 0, gamma: float = 1.0,
+                 krylov: bool = False):
         import numpy as np
         lib = load()
         self.coarse = coarse
@@ -442,7 +445,7 @@ class AuxSolver:
         st = np.ascontiguousarray(mesh.st, dtype=np.float64)
         tri = np.ascontiguousarray(mesh.tri, dtype=np.int32)
         dirichlet = np.ascontiguousarray(mesh.dirichlet, dtype=np.uint8)
-        opts = _AuxOpts(float(omega), int(mass_steps), float(gamma))
+        opts = _AuxOpts(float(omega), int(mass_steps), float(gamma), 1 if krylov else 0)
         h = ctypes.c_void_p()
         _check(lib.bmg_aux_create(coarse._h, self.nv, xy.ctypes.data_as(ctypes.c_void_p),
                                   st.ctypes.data_as(ctypes.c_void_p), dirichlet.ctypes.data_as(ctypes.c_void_p),

@@ -36,6 +36,7 @@ constexpr int kRedBlocks = 4 * 152;       // fixed grid of the reducing kernels
 struct AuxState {
     double rr;          // ||f - A u||^2 (interior)
     double ff;          // ||f||^2
+    double pq, rz, rzo; // the outer flexible CG's scalars
     double cg_rr, cg_pq, alpha, beta;
     int err;
     unsigned int counter[4];
@@ -346,6 +347,56 @@ __global__ void k_cg_p(int nr, const double* __restrict__ res, double* __restric
         p[i] = res[i] + beta * p[i];
 }
 
+// q = A p and p.q
+__global__ void k_spmv_dot(int nr, const int* __restrict__ rp, const int* __restrict__ ci, const double* __restrict__ va,
+                           const double* __restrict__ p, double* __restrict__ q, double* partials, unsigned int* counter,
+                           double* slot) {
+    double acc = 0.0;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < nr; i += gridDim.x * blockDim.x) {
+        const double v = csr_row(rp, ci, va, p, i);
+        q[i] = v;
+        acc += p[i] * v;
+    }
+    double t;
+    if (grid_sum(acc, partials, counter, &t)) *slot = t;
+}
+
+// u += alpha p; r -= alpha q; ||r||^2
+__global__ void k_update_ur(int nr, double* __restrict__ u, double* __restrict__ r, const double* __restrict__ p,
+                            const double* __restrict__ q, double alpha, double* partials, unsigned int* counter,
+                            double* slot) {
+    double acc = 0.0;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < nr; i += gridDim.x * blockDim.x) {
+        u[i] += alpha * p[i];
+        const double v = r[i] - alpha * q[i];
+        r[i] = v;
+        acc += v * v;
+    }
+    double t;
+    if (grid_sum(acc, partials, counter, &t)) *slot = t;
+}
+
+// r.z and r.zo
+__global__ void k_dot2_aux(int nr, const double* __restrict__ r, const double* __restrict__ z,
+                           const double* __restrict__ zo, double* partials, unsigned int* counter, double* s1,
+                           double* s2) {
+    double a = 0.0, b = 0.0;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < nr; i += gridDim.x * blockDim.x) {
+        a += r[i] * z[i];
+        b += r[i] * zo[i];
+    }
+    double t1, t2;
+    if (grid_sum2(a, b, partials, counter, &t1, &t2)) {
+        *s1 = t1;
+        *s2 = t2;
+    }
+}
+
+__global__ void k_p_update_aux(int nr, double* __restrict__ p, const double* __restrict__ z, double beta) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < nr) p[i] = z[i] + beta * p[i];
+}
+
 __global__ void k_axpy(int nr, double* __restrict__ u, const double* __restrict__ v, double gamma) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i < nr) u[i] += gamma * v[i];
@@ -490,6 +541,9 @@ struct bmg_aux {
     double *d_va = nullptr, *d_vm = nullptr, *d_vc = nullptr, *d_vct = nullptr, *d_dinv = nullptr, *d_mlinv = nullptr;
     double *d_f = nullptr, *d_u = nullptr, *d_u2 = nullptr, *d_r = nullptr, *d_y = nullptr, *d_cres = nullptr,
            *d_cp = nullptr, *d_cq = nullptr, *d_w = nullptr;
+    // outer flexible CG: residual, preconditioned residual (and its previous
+    // value and the cycle's scratch), search direction, A p
+    double *d_kr = nullptr, *d_kz = nullptr, *d_kzo = nullptr, *d_kz2 = nullptr, *d_kp = nullptr, *d_kq = nullptr;
     double* d_partials = nullptr;
     AuxState* d_st_aux = nullptr;
     // coarse-grid scaling (Lanczos): padded and natural coarse vectors
@@ -542,9 +596,10 @@ size_t carve_aux(bmg_aux& x, char* base) {
     x.d_vct = (double*)take(D * x.ct_col.size());
     x.d_dinv = (double*)take(D * x.nvi);
     x.d_mlinv = (double*)take(D * x.nvi);
-    double** vecs[] = {&x.d_f, &x.d_u, &x.d_u2, &x.d_r, &x.d_y, &x.d_cres, &x.d_cp, &x.d_cq, &x.d_w};
+    double** vecs[] = {&x.d_f, &x.d_u, &x.d_u2, &x.d_r, &x.d_y, &x.d_cres, &x.d_cp, &x.d_cq, &x.d_w,
+                       &x.d_kr, &x.d_kz, &x.d_kzo, &x.d_kz2, &x.d_kp, &x.d_kq};
     for (double** v : vecs) *v = (double*)take(D * std::max(x.nvi, 1));
-    x.d_partials = (double*)take(D * kRedBlocks);
+    x.d_partials = (double*)take(D * 2 * kRedBlocks);   // two per block for the paired reductions
     x.d_st_aux = (AuxState*)take(sizeof(AuxState));
     const size_t plane = (size_t)x.ld * x.n, nn = (size_t)x.n * x.n;
     x.d_cpad = (double*)take(D * plane);
@@ -583,18 +638,19 @@ bmg_status mass_cg(bmg_aux& x, const double* r, double* y) {
     return BMG_OK;
 }
 
-// one two-grid cycle on the interior vectors d_f, d_u (Sec. 2.2 "Solution phase")
-bmg_status aux_cycle(bmg_aux& x) {
+// one two-grid cycle (Sec. 2.2 "Solution phase") on interior vectors: u is
+// updated in place for right-hand side f; u2 is scratch of the same length
+bmg_status aux_cycle(bmg_aux& x, const double* f, double* u, double* u2) {
     Ctx& c = x.coarse->c;
     cudaStream_t s = c.stream;
     const int nr = x.nvi, nq = (int)x.ct_map.size();
     const bool lumped = x.opts.mass_steps == 0;
     // 1. pre-relaxation
-    k_jacobi<<<blocks(nr), kAuxThreads, 0, s>>>(nr, x.d_am_ptr, x.d_am_col, x.d_va, x.d_dinv, x.d_f, x.d_u, x.d_u2,
+    k_jacobi<<<blocks(nr), kAuxThreads, 0, s>>>(nr, x.d_am_ptr, x.d_am_col, x.d_va, x.d_dinv, f, u, u2,
                                                 x.opts.omega);
-    std::swap(x.d_u, x.d_u2);
+    std::swap(u, u2);
     // 2. restriction r_c = C^T M^-1 (f - A u)
-    k_residual_csr<<<kRedBlocks, kAuxThreads, 0, s>>>(nr, x.d_am_ptr, x.d_am_col, x.d_va, x.d_f, x.d_u, x.d_r,
+    k_residual_csr<<<kRedBlocks, kAuxThreads, 0, s>>>(nr, x.d_am_ptr, x.d_am_col, x.d_va, f, u, x.d_r,
                                                       x.d_partials, &x.d_st_aux->counter[0], nullptr);
     const double* y = x.d_r;
     if (!lumped) {
@@ -609,17 +665,17 @@ bmg_status aux_cycle(bmg_aux& x) {
     // 4. prolongation u += gamma M^-1 C e_c
     if (lumped) {
         k_prolong_c<<<blocks(nr), kAuxThreads, 0, s>>>(nr, x.d_c_ptr, x.d_c_col, x.d_vc, c.z[0], x.d_mlinv, nullptr,
-                                                       x.d_u, x.opts.gamma);
+                                                       u, x.opts.gamma);
     } else {
         k_prolong_c<<<blocks(nr), kAuxThreads, 0, s>>>(nr, x.d_c_ptr, x.d_c_col, x.d_vc, c.z[0], nullptr, x.d_w,
                                                        nullptr, 0.0);
         BMG_TRY(mass_cg(x, x.d_w, x.d_y));
-        k_axpy<<<blocks(nr), kAuxThreads, 0, s>>>(nr, x.d_u, x.d_y, x.opts.gamma);
+        k_axpy<<<blocks(nr), kAuxThreads, 0, s>>>(nr, u, x.d_y, x.opts.gamma);
     }
     // 5. post-relaxation
-    k_jacobi<<<blocks(nr), kAuxThreads, 0, s>>>(nr, x.d_am_ptr, x.d_am_col, x.d_va, x.d_dinv, x.d_f, x.d_u, x.d_u2,
+    k_jacobi<<<blocks(nr), kAuxThreads, 0, s>>>(nr, x.d_am_ptr, x.d_am_col, x.d_va, x.d_dinv, f, u, u2,
                                                 x.opts.omega);
-    std::swap(x.d_u, x.d_u2);
+    std::swap(u, u2);
     BMG_CUDA(cudaGetLastError());
     return BMG_OK;
 }
@@ -631,6 +687,7 @@ extern "C" void bmg_aux_default_opts(bmg_aux_opts* o) {
     o->omega = 2.0 / 3.0;
     o->mass_steps = 0;
     o->gamma = 1.0;
+    o->krylov = 0;
 }
 
 extern "C" bmg_status bmg_aux_create(bmg_ctx* coarse, int nv, const double* xy, const double* st,
@@ -645,7 +702,8 @@ extern "C" bmg_status bmg_aux_create(bmg_ctx* coarse, int nv, const double* xy, 
     bmg_aux_opts o;
     bmg_aux_default_opts(&o);
     if (opts) o = *opts;
-    if (!(o.omega > 0.0 && o.omega < 2.0) || o.mass_steps < 0 || o.mass_steps > 64 || !(o.gamma > 0.0))
+    if (!(o.omega > 0.0 && o.omega < 2.0) || o.mass_steps < 0 || o.mass_steps > 64 || !(o.gamma > 0.0) ||
+        (o.krylov != 0 && o.krylov != 1))
         return BMG_ERR_ARG;
     for (long long k = 0; k < 3LL * ntri; k++)
         if (tri[k] < 0 || tri[k] >= nv) return BMG_ERR_ARG;
@@ -867,16 +925,65 @@ extern "C" bmg_status bmg_aux_solve(bmg_aux* x, const double* f, double* u, doub
     const double nf = sqrt(h.ff);
     double rel = nf > 0.0 ? sqrt(h.rr) / nf : 0.0;
     int it = 0;
-    while (it < maxit && rel > tol && nf > 0.0) {
-        BMG_TRY(aux_cycle(*x));
+    unsigned int* cnt = &x->d_st_aux->counter[0];
+    if (x->opts.krylov == 0) {
+        // the paper's stationary iteration
+        while (it < maxit && rel > tol && nf > 0.0) {
+            BMG_TRY(aux_cycle(*x, x->d_f, x->d_u, x->d_u2));
+            k_residual_csr<<<kRedBlocks, kAuxThreads, 0, s>>>(nr, x->d_am_ptr, x->d_am_col, x->d_va, x->d_f, x->d_u,
+                                                              nullptr, x->d_partials, cnt, &x->d_st_aux->rr);
+            BMG_CUDA(cudaGetLastError());
+            BMG_TRY(aux_read(*x, h));
+            rel = sqrt(h.rr) / nf;
+            it++;
+            if (!(rel == rel)) break;   // NaN: diverged
+        }
+    } else if (rel > tol && nf > 0.0 && maxit > 0) {
+        // flexible CG with one two-grid cycle (zero initial guess) as the
+        // preconditioner z = B r; beta = r.(z - z_old) / (r_old.z_old)
+        const size_t vb = sizeof(double) * nr;
         k_residual_csr<<<kRedBlocks, kAuxThreads, 0, s>>>(nr, x->d_am_ptr, x->d_am_col, x->d_va, x->d_f, x->d_u,
-                                                          nullptr, x->d_partials, &x->d_st_aux->counter[0],
-                                                          &x->d_st_aux->rr);
+                                                          x->d_kr, x->d_partials, cnt, &x->d_st_aux->rr);
+        BMG_CUDA(cudaMemsetAsync(x->d_kz, 0, vb, s));
+        BMG_TRY(aux_cycle(*x, x->d_kr, x->d_kz, x->d_kz2));
+        BMG_CUDA(cudaMemsetAsync(x->d_kzo, 0, vb, s));
+        k_dot2_aux<<<kRedBlocks, kAuxThreads, 0, s>>>(nr, x->d_kr, x->d_kz, x->d_kzo, x->d_partials, cnt,
+                                                      &x->d_st_aux->rz, &x->d_st_aux->rzo);
+        BMG_CUDA(cudaMemcpyAsync(x->d_kp, x->d_kz, vb, cudaMemcpyDeviceToDevice, s));
+        BMG_CUDA(cudaGetLastError());
+        BMG_TRY(aux_read(*x, h));
+        double rz = h.rz;
+        while (it < maxit && rel > tol) {
+            k_spmv_dot<<<kRedBlocks, kAuxThreads, 0, s>>>(nr, x->d_am_ptr, x->d_am_col, x->d_va, x->d_kp, x->d_kq,
+                                                          x->d_partials, cnt, &x->d_st_aux->pq);
+            BMG_CUDA(cudaGetLastError());
+            BMG_TRY(aux_read(*x, h));
+            if (!(h.pq > 0.0) || !(rz > 0.0)) return BMG_ERR_NOT_SPD;
+            const double alpha = rz / h.pq;
+            k_update_ur<<<kRedBlocks, kAuxThreads, 0, s>>>(nr, x->d_u, x->d_kr, x->d_kp, x->d_kq, alpha,
+                                                           x->d_partials, cnt, &x->d_st_aux->rr);
+            BMG_CUDA(cudaGetLastError());
+            BMG_TRY(aux_read(*x, h));
+            rel = sqrt(h.rr) / nf;
+            it++;
+            if (rel <= tol || !(rel == rel)) break;
+            std::swap(x->d_kz, x->d_kzo);
+            BMG_CUDA(cudaMemsetAsync(x->d_kz, 0, vb, s));
+            BMG_TRY(aux_cycle(*x, x->d_kr, x->d_kz, x->d_kz2));
+            k_dot2_aux<<<kRedBlocks, kAuxThreads, 0, s>>>(nr, x->d_kr, x->d_kz, x->d_kzo, x->d_partials, cnt,
+                                                          &x->d_st_aux->rz, &x->d_st_aux->rzo);
+            BMG_CUDA(cudaGetLastError());
+            BMG_TRY(aux_read(*x, h));
+            const double beta = (h.rz - h.rzo) / rz;
+            rz = h.rz;
+            k_p_update_aux<<<blocks(nr), kAuxThreads, 0, s>>>(nr, x->d_kp, x->d_kz, beta);
+        }
+        // the recursive residual drifts from f - A u: report the true one
+        k_residual_csr<<<kRedBlocks, kAuxThreads, 0, s>>>(nr, x->d_am_ptr, x->d_am_col, x->d_va, x->d_f, x->d_u,
+                                                          nullptr, x->d_partials, cnt, &x->d_st_aux->rr);
         BMG_CUDA(cudaGetLastError());
         BMG_TRY(aux_read(*x, h));
         rel = sqrt(h.rr) / nf;
-        it++;
-        if (!(rel == rel)) break;   // NaN: diverged
     }
     k_expand<<<blocks(x->nv), kAuxThreads, 0, s>>>(x->nv, x->d_vid, x->d_u, u);
     BMG_CUDA(cudaGetLastError());

@@ -142,3 +142,15 @@ def test_gamma_matches_oracle_lanczos(mass_steps):
     assert abs(g - alpha.mean()) <= 1e-14 * abs(g)
     T = np.diag(alpha) + np.diag(beta, 1) + np.diag(beta, -1)
     assert np.allclose(np.sort(np.linalg.eigvalsh(T)), np.sort(ritz), rtol=1e-7, atol=0)
+
+
+@pytest.mark.parametrize("mass_steps", [0, 2])
+def test_flexible_cg_matches_oracle(mass_steps):
+    m = inputs.annulus_mesh(25, 37)
+    coords, s = _coarse(17)
+    a = binding.AuxSolver(s, m, mass_steps=mass_steps, krylov=True)
+    uo, ito, trr = _oracle(m, coords, mass_steps).solve_fcg(m.f, tol=1e-10)
+    u, info = a.solve(torch.as_tensor(m.f, device="cuda"), tol=1e-10, raise_on_nonconv=False)
+    assert abs(info.iterations - ito) <= 1
+    assert info.true_relres <= 2e-10
+    assert relerr(u.cpu().numpy(), uo) <= 1e-8

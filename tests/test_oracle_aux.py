@@ -164,3 +164,25 @@ def test_two_grid_converges_on_a_small_annulus(mass_steps):
     iv = tg.iv
     res = m.f[iv] - (A @ u)[iv]
     assert np.linalg.norm(res) <= 1e-10 * np.linalg.norm(m.f[iv]) * 1.0001
+
+
+def test_flexible_cg_around_the_cycle():
+    """With the lumped mass the cycle is a symmetric preconditioner: flexible
+    CG around it needs fewer iterations than the stationary iteration needs
+    cycles, and reaches the same solution.  With the paper's CG(2) mass
+    solve the stationary iteration diverges on this mesh (cond M_p about
+    10), while flexible CG around the same (non-linear) cycle converges."""
+    m = inputs.annulus_mesh(25, 37)
+    n = 17
+    coords = inputs.coords_quarter_annulus(n)
+    Ac = oracle.assemble(coords, np.ones((n - 1, n - 1)))
+    tg = aux.TwoGrid(m, coords, Ac, mass_steps=0)
+    us, its, _ = tg.solve(m.f, tol=1e-10)
+    uf, itf, trr = tg.solve_fcg(m.f, tol=1e-10)
+    assert itf < its / 2 and trr <= 2e-10
+    assert np.linalg.norm(uf - us) <= 1e-8 * np.linalg.norm(us)
+    tg2 = aux.TwoGrid(m, coords, Ac, mass_steps=2)
+    _, _, hist = tg2.solve(m.f, tol=1e-10, maxit=40)
+    assert hist[-1] > 1.0
+    u2, it2, trr2 = tg2.solve_fcg(m.f, tol=1e-10)
+    assert trr2 <= 2e-10 and np.linalg.norm(u2 - us) <= 1e-8 * np.linalg.norm(us)
