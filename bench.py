@@ -571,6 +571,7 @@ def run_aux(args):
             a.solve(f, tol=TOL)
         torch.cuda.synchronize()
         times, infos = [], []
+        torch.cuda.nvtx.range_push(f"aux_{name}")
         for _ in range(args.steps):
             ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             torch.cuda.synchronize()
@@ -580,6 +581,7 @@ def run_aux(args):
             torch.cuda.synchronize()
             times.append(ev0.elapsed_time(ev1))
             infos.append(info)
+        torch.cuda.nvtx.range_pop()
         ms = statistics.median(times)
         assert all(i.status == 0 and i.true_relres <= 1.01 * TOL for i in infos)
         res[name] = {"value": dof / (ms * 1e-3), "ms_per_step": ms, "iterations": infos[-1].iterations,

@@ -200,12 +200,6 @@ __global__ void k_gather(int nout, const int* __restrict__ ptr, const int* __res
     out[e] = s;
 }
 
-__global__ void k_permute(int nout, const int* __restrict__ perm, const double* __restrict__ src,
-                          double* __restrict__ out) {
-    const int e = blockIdx.x * blockDim.x + threadIdx.x;
-    if (e < nout) out[e] = src[perm[e]];
-}
-
 __global__ void k_diag_inv(int nr, const int* __restrict__ diag_pos, const double* __restrict__ va,
                            double* __restrict__ dinv) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
@@ -218,11 +212,25 @@ __global__ void k_inv(int nr, double* __restrict__ v) {
 }
 
 // ------------------------------------------------------------------ solve kernels
-__device__ __forceinline__ double csr_row(const int* __restrict__ rp, const int* __restrict__ ci,
+// Row i of a matrix in sliced ELLPACK with slices of 32 rows: slice s
+// holds its rows' entries column-major from so[s] (entry k of row 32 s + l
+// at so[s] + 32 k + l), padded with zeros to the slice's longest row, so
+// the 32 threads of a warp read consecutive words.  Entries keep their CSR
+// order, so the sum is the CSR row's, plus zero terms.
+__device__ __forceinline__ double csr_row(const int* __restrict__ so, const int* __restrict__ ci,
                                           const double* __restrict__ va, const double* __restrict__ x, int i) {
+    const int sl = i >> 5;
+    const int b = so[sl] + (i & 31), e = so[sl + 1];
     double s = 0.0;
-    for (int k = rp[i]; k < rp[i + 1]; k++) s += va[k] * x[ci[k]];
+    for (int k = b; k < e; k += 32) s += va[k] * x[ci[k]];
     return s;
+}
+
+// SELL values from CSR values: out[k] = src[map[k]], 0 for padding (map < 0)
+__global__ void k_sell_fill(int n, const int* __restrict__ map, const double* __restrict__ src,
+                            double* __restrict__ out) {
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k < n) out[k] = map[k] >= 0 ? src[map[k]] : 0.0;
 }
 
 // interior entries of a vertex vector: out[i] = in[vtx[i]]
@@ -268,14 +276,16 @@ __global__ void k_dot_aux(int nr, const double* __restrict__ a, const double* __
     if (grid_sum(acc, partials, counter, &t)) *slot = t;
 }
 
-// restriction: rc[map[q]] = sum_k C^T[q,k] (y[col] * (w ? w[col] : 1))
+// restriction: rc[map[q]] = sum_k C^T[q,k] (y[col] * (w ? w[col] : 1)), C^T in SELL-32
 __global__ void k_restrict_ct(int nq, const int* __restrict__ rp, const int* __restrict__ ci,
                               const double* __restrict__ va, const int* __restrict__ map, const double* __restrict__ y,
                               const double* __restrict__ w, double* __restrict__ rc) {
     const int q = blockIdx.x * blockDim.x + threadIdx.x;
     if (q >= nq) return;
+    const int sl = q >> 5;
+    const int b = rp[sl] + (q & 31), e = rp[sl + 1];
     double s = 0.0;
-    for (int k = rp[q]; k < rp[q + 1]; k++) s += va[k] * (w ? y[ci[k]] * w[ci[k]] : y[ci[k]]);
+    for (int k = b; k < e; k += 32) s += va[k] * (w ? y[ci[k]] * w[ci[k]] : y[ci[k]]);
     rc[map[q]] = s;
 }
 
@@ -494,6 +504,33 @@ bool build_csr(int nrows, const std::vector<int>& rr, const std::vector<int>& cc
     return true;
 }
 
+struct Sell {
+    std::vector<int> off, col, map;   // slice offsets, columns, CSR index of each slot (-1: padding)
+};
+
+// CSR (ptr, col) -> SELL-32; map[k] = CSR entry of slot k, composed with `through` if given
+void build_sell(const std::vector<int>& ptr, const std::vector<int>& col, const std::vector<int>* through,
+                Sell& out) {
+    const int nr = (int)ptr.size() - 1;
+    const int ns = (nr + 31) / 32;
+    out.off.assign(ns + 1, 0);
+    for (int sl = 0; sl < ns; sl++) {
+        int w = 0;
+        for (int i = sl * 32; i < std::min(nr, sl * 32 + 32); i++) w = std::max(w, ptr[i + 1] - ptr[i]);
+        out.off[sl + 1] = out.off[sl] + 32 * w;
+    }
+    out.col.assign(out.off[ns], 0);
+    out.map.assign(out.off[ns], -1);
+    for (int i = 0; i < nr; i++) {
+        const int sl = i / 32, l = i % 32;
+        for (int k = ptr[i]; k < ptr[i + 1]; k++) {
+            const int slot = out.off[sl] + 32 * (k - ptr[i]) + l;
+            out.col[slot] = col[k];
+            out.map[slot] = through ? (*through)[k] : k;
+        }
+    }
+}
+
 // separating-axis test of a triangle against an axis-aligned box (touching counts)
 bool tri_box_overlap(const double* sx, const double* sy, double x0, double y0, double x1, double y1) {
     const double mnx = std::min(sx[0], std::min(sx[1], sx[2])), mxx = std::max(sx[0], std::max(sx[1], sx[2]));
@@ -528,17 +565,18 @@ struct bmg_aux {
     Csr lump;                            // lumped mass: one "entry" per interior row
     Csr cm;                              // C pattern (contributions: 12 p + 4 a + b)
     std::vector<int> ct_ptr, ct_col, ct_perm, ct_map;   // C^T rows: interior coarse nodes
+    Sell s_am, s_c, s_ct;                // the products run on SELL-32 copies
     size_t ws_need = 0;
     bool ready = false;
     // device (carved from the workspace)
     int *d_tri = nullptr, *d_vid = nullptr, *d_vtx = nullptr, *d_pair_tri = nullptr, *d_pair_cell = nullptr;
     double *d_xy = nullptr, *d_st = nullptr;
-    int *d_am_ptr = nullptr, *d_am_col = nullptr, *d_am_gptr = nullptr, *d_am_gidx = nullptr, *d_diag = nullptr;
+    int *d_am_gptr = nullptr, *d_am_gidx = nullptr, *d_diag = nullptr;
     int *d_lp_gptr = nullptr, *d_lp_gidx = nullptr;
-    int *d_c_ptr = nullptr, *d_c_col = nullptr, *d_c_gptr = nullptr, *d_c_gidx = nullptr;
-    int *d_ct_ptr = nullptr, *d_ct_col = nullptr, *d_ct_perm = nullptr, *d_ct_map = nullptr;
+    int *d_c_gptr = nullptr, *d_c_gidx = nullptr;
+    int* d_ct_map = nullptr;
     double *d_lk = nullptr, *d_lm = nullptr, *d_loc = nullptr;
-    double *d_va = nullptr, *d_vm = nullptr, *d_vc = nullptr, *d_vct = nullptr, *d_dinv = nullptr, *d_mlinv = nullptr;
+    double *d_va = nullptr, *d_vm = nullptr, *d_vc = nullptr, *d_dinv = nullptr, *d_mlinv = nullptr;
     double *d_f = nullptr, *d_u = nullptr, *d_u2 = nullptr, *d_r = nullptr, *d_y = nullptr, *d_cres = nullptr,
            *d_cp = nullptr, *d_cq = nullptr, *d_w = nullptr;
     // outer flexible CG: residual, preconditioned residual (and its previous
@@ -546,6 +584,10 @@ struct bmg_aux {
     double *d_kr = nullptr, *d_kz = nullptr, *d_kzo = nullptr, *d_kz2 = nullptr, *d_kp = nullptr, *d_kq = nullptr;
     double* d_partials = nullptr;
     AuxState* d_st_aux = nullptr;
+    int *d_sam_off = nullptr, *d_sam_col = nullptr, *d_sam_map = nullptr;
+    int *d_sc_off = nullptr, *d_sc_col = nullptr, *d_sc_map = nullptr;
+    int *d_sct_off = nullptr, *d_sct_col = nullptr, *d_sct_map = nullptr;
+    double *d_sva = nullptr, *d_svm = nullptr, *d_svc = nullptr, *d_svct = nullptr;
     // coarse-grid scaling (Lanczos): padded and natural coarse vectors
     double *d_cpad = nullptr, *d_cpad2 = nullptr;
     double *d_lq = nullptr, *d_lqp = nullptr, *d_lb = nullptr, *d_lbp = nullptr, *d_lv = nullptr, *d_lw = nullptr;
@@ -572,20 +614,13 @@ size_t carve_aux(bmg_aux& x, char* base) {
     x.d_pair_cell = (int*)take(I * npairs);
     x.d_xy = (double*)take(D * x.xy.size());
     x.d_st = (double*)take(D * x.st.size());
-    x.d_am_ptr = (int*)take(I * x.am.ptr.size());
-    x.d_am_col = (int*)take(I * x.am.col.size());
     x.d_am_gptr = (int*)take(I * x.am.gptr.size());
     x.d_am_gidx = (int*)take(I * x.am.gidx.size());
     x.d_diag = (int*)take(I * x.diag_pos.size());
     x.d_lp_gptr = (int*)take(I * x.lump.gptr.size());
     x.d_lp_gidx = (int*)take(I * x.lump.gidx.size());
-    x.d_c_ptr = (int*)take(I * x.cm.ptr.size());
-    x.d_c_col = (int*)take(I * x.cm.col.size());
     x.d_c_gptr = (int*)take(I * x.cm.gptr.size());
     x.d_c_gidx = (int*)take(I * x.cm.gidx.size());
-    x.d_ct_ptr = (int*)take(I * x.ct_ptr.size());
-    x.d_ct_col = (int*)take(I * x.ct_col.size());
-    x.d_ct_perm = (int*)take(I * x.ct_perm.size());
     x.d_ct_map = (int*)take(I * x.ct_map.size());
     x.d_lk = (double*)take(D * 9 * (size_t)x.ntri);
     x.d_lm = (double*)take(D * 9 * (size_t)x.ntri);
@@ -593,7 +628,6 @@ size_t carve_aux(bmg_aux& x, char* base) {
     x.d_va = (double*)take(D * x.am.col.size());
     x.d_vm = (double*)take(D * x.am.col.size());
     x.d_vc = (double*)take(D * x.cm.col.size());
-    x.d_vct = (double*)take(D * x.ct_col.size());
     x.d_dinv = (double*)take(D * x.nvi);
     x.d_mlinv = (double*)take(D * x.nvi);
     double** vecs[] = {&x.d_f, &x.d_u, &x.d_u2, &x.d_r, &x.d_y, &x.d_cres, &x.d_cp, &x.d_cq, &x.d_w,
@@ -601,6 +635,19 @@ size_t carve_aux(bmg_aux& x, char* base) {
     for (double** v : vecs) *v = (double*)take(D * std::max(x.nvi, 1));
     x.d_partials = (double*)take(D * 2 * kRedBlocks);   // two per block for the paired reductions
     x.d_st_aux = (AuxState*)take(sizeof(AuxState));
+    x.d_sam_off = (int*)take(I * x.s_am.off.size());
+    x.d_sam_col = (int*)take(I * x.s_am.col.size());
+    x.d_sam_map = (int*)take(I * x.s_am.map.size());
+    x.d_sc_off = (int*)take(I * x.s_c.off.size());
+    x.d_sc_col = (int*)take(I * x.s_c.col.size());
+    x.d_sc_map = (int*)take(I * x.s_c.map.size());
+    x.d_sct_off = (int*)take(I * x.s_ct.off.size());
+    x.d_sct_col = (int*)take(I * x.s_ct.col.size());
+    x.d_sct_map = (int*)take(I * x.s_ct.map.size());
+    x.d_sva = (double*)take(D * x.s_am.col.size());
+    x.d_svm = (double*)take(D * x.s_am.col.size());
+    x.d_svc = (double*)take(D * x.s_c.col.size());
+    x.d_svct = (double*)take(D * x.s_ct.col.size());
     const size_t plane = (size_t)x.ld * x.n, nn = (size_t)x.n * x.n;
     x.d_cpad = (double*)take(D * plane);
     x.d_cpad2 = (double*)take(D * plane);
@@ -630,7 +677,7 @@ bmg_status mass_cg(bmg_aux& x, const double* r, double* y) {
     k_cg_init<<<kRedBlocks, kAuxThreads, 0, s>>>(nr, r, y, x.d_cres, x.d_cp, x.d_partials, x.d_st_aux);
     for (int k = 0; k < x.opts.mass_steps; k++) {
         if (k > 0) k_cg_p<<<kRedBlocks, kAuxThreads, 0, s>>>(nr, x.d_cres, x.d_cp, x.d_st_aux);
-        k_cg_mp<<<kRedBlocks, kAuxThreads, 0, s>>>(nr, x.d_am_ptr, x.d_am_col, x.d_vm, x.d_cp, x.d_cq, x.d_partials,
+        k_cg_mp<<<kRedBlocks, kAuxThreads, 0, s>>>(nr, x.d_sam_off, x.d_sam_col, x.d_svm, x.d_cp, x.d_cq, x.d_partials,
                                                    x.d_st_aux);
         k_cg_update<<<kRedBlocks, kAuxThreads, 0, s>>>(nr, y, x.d_cres, x.d_cp, x.d_cq, x.d_partials, x.d_st_aux);
     }
@@ -646,11 +693,11 @@ bmg_status aux_cycle(bmg_aux& x, const double* f, double* u, double* u2) {
     const int nr = x.nvi, nq = (int)x.ct_map.size();
     const bool lumped = x.opts.mass_steps == 0;
     // 1. pre-relaxation
-    k_jacobi<<<blocks(nr), kAuxThreads, 0, s>>>(nr, x.d_am_ptr, x.d_am_col, x.d_va, x.d_dinv, f, u, u2,
+    k_jacobi<<<blocks(nr), kAuxThreads, 0, s>>>(nr, x.d_sam_off, x.d_sam_col, x.d_sva, x.d_dinv, f, u, u2,
                                                 x.opts.omega);
     std::swap(u, u2);
     // 2. restriction r_c = C^T M^-1 (f - A u)
-    k_residual_csr<<<kRedBlocks, kAuxThreads, 0, s>>>(nr, x.d_am_ptr, x.d_am_col, x.d_va, f, u, x.d_r,
+    k_residual_csr<<<kRedBlocks, kAuxThreads, 0, s>>>(nr, x.d_sam_off, x.d_sam_col, x.d_sva, f, u, x.d_r,
                                                       x.d_partials, &x.d_st_aux->counter[0], nullptr);
     const double* y = x.d_r;
     if (!lumped) {
@@ -658,22 +705,22 @@ bmg_status aux_cycle(bmg_aux& x, const double* f, double* u, double* u2) {
         y = x.d_y;
     }
     BMG_CUDA(cudaMemsetAsync(c.r, 0, sizeof(double) * c.lev[0].plane, s));
-    k_restrict_ct<<<blocks(nq), kAuxThreads, 0, s>>>(nq, x.d_ct_ptr, x.d_ct_col, x.d_vct, x.d_ct_map, y,
+    k_restrict_ct<<<blocks(nq), kAuxThreads, 0, s>>>(nq, x.d_sct_off, x.d_sct_col, x.d_svct, x.d_ct_map, y,
                                                      lumped ? x.d_mlinv : nullptr, c.r);
     // 3. BoxMG V-cycle on A_c e_c = r_c
     BMG_TRY(vcycle(c, c.r, c.z[0]));
     // 4. prolongation u += gamma M^-1 C e_c
     if (lumped) {
-        k_prolong_c<<<blocks(nr), kAuxThreads, 0, s>>>(nr, x.d_c_ptr, x.d_c_col, x.d_vc, c.z[0], x.d_mlinv, nullptr,
+        k_prolong_c<<<blocks(nr), kAuxThreads, 0, s>>>(nr, x.d_sc_off, x.d_sc_col, x.d_svc, c.z[0], x.d_mlinv, nullptr,
                                                        u, x.opts.gamma);
     } else {
-        k_prolong_c<<<blocks(nr), kAuxThreads, 0, s>>>(nr, x.d_c_ptr, x.d_c_col, x.d_vc, c.z[0], nullptr, x.d_w,
+        k_prolong_c<<<blocks(nr), kAuxThreads, 0, s>>>(nr, x.d_sc_off, x.d_sc_col, x.d_svc, c.z[0], nullptr, x.d_w,
                                                        nullptr, 0.0);
         BMG_TRY(mass_cg(x, x.d_w, x.d_y));
         k_axpy<<<blocks(nr), kAuxThreads, 0, s>>>(nr, u, x.d_y, x.opts.gamma);
     }
     // 5. post-relaxation
-    k_jacobi<<<blocks(nr), kAuxThreads, 0, s>>>(nr, x.d_am_ptr, x.d_am_col, x.d_va, x.d_dinv, f, u, u2,
+    k_jacobi<<<blocks(nr), kAuxThreads, 0, s>>>(nr, x.d_sam_off, x.d_sam_col, x.d_sva, x.d_dinv, f, u, u2,
                                                 x.opts.omega);
     std::swap(u, u2);
     BMG_CUDA(cudaGetLastError());
@@ -824,6 +871,9 @@ extern "C" bmg_status bmg_aux_create(bmg_ctx* coarse, int nv, const double* xy, 
                 pos[q]++;
             }
     }
+    build_sell(x->am.ptr, x->am.col, nullptr, x->s_am);
+    build_sell(x->cm.ptr, x->cm.col, nullptr, x->s_c);
+    build_sell(x->ct_ptr, x->ct_col, &x->ct_perm, x->s_ct);
     x->ws_need = carve_aux(*x, nullptr);
     *out = x;
     return BMG_OK;
@@ -863,21 +913,23 @@ extern "C" bmg_status bmg_aux_setup(bmg_aux* x, void* ws, size_t bytes, const do
     BMG_TRY(up(x->d_pair_cell, x->pair_cell, s));
     BMG_TRY(up(x->d_xy, x->xy, s));
     BMG_TRY(up(x->d_st, x->st, s));
-    BMG_TRY(up(x->d_am_ptr, x->am.ptr, s));
-    BMG_TRY(up(x->d_am_col, x->am.col, s));
     BMG_TRY(up(x->d_am_gptr, x->am.gptr, s));
     BMG_TRY(up(x->d_am_gidx, x->am.gidx, s));
     BMG_TRY(up(x->d_diag, x->diag_pos, s));
     BMG_TRY(up(x->d_lp_gptr, x->lump.gptr, s));
     BMG_TRY(up(x->d_lp_gidx, x->lump.gidx, s));
-    BMG_TRY(up(x->d_c_ptr, x->cm.ptr, s));
-    BMG_TRY(up(x->d_c_col, x->cm.col, s));
     BMG_TRY(up(x->d_c_gptr, x->cm.gptr, s));
     BMG_TRY(up(x->d_c_gidx, x->cm.gidx, s));
-    BMG_TRY(up(x->d_ct_ptr, x->ct_ptr, s));
-    BMG_TRY(up(x->d_ct_col, x->ct_col, s));
-    BMG_TRY(up(x->d_ct_perm, x->ct_perm, s));
     BMG_TRY(up(x->d_ct_map, x->ct_map, s));
+    BMG_TRY(up(x->d_sam_off, x->s_am.off, s));
+    BMG_TRY(up(x->d_sam_col, x->s_am.col, s));
+    BMG_TRY(up(x->d_sam_map, x->s_am.map, s));
+    BMG_TRY(up(x->d_sc_off, x->s_c.off, s));
+    BMG_TRY(up(x->d_sc_col, x->s_c.col, s));
+    BMG_TRY(up(x->d_sc_map, x->s_c.map, s));
+    BMG_TRY(up(x->d_sct_off, x->s_ct.off, s));
+    BMG_TRY(up(x->d_sct_col, x->s_ct.col, s));
+    BMG_TRY(up(x->d_sct_map, x->s_ct.map, s));
     const int npairs = (int)x->pair_tri.size();
     k_tri_local<<<blocks(x->ntri), kAuxThreads, 0, s>>>(x->ntri, x->d_tri, x->d_xy, kappa, x->d_lk, x->d_lm,
                                                         x->d_st_aux);
@@ -896,8 +948,14 @@ extern "C" bmg_status bmg_aux_setup(bmg_aux* x, void* ws, size_t bytes, const do
     }
     if (nnzc > 0) {
         k_gather<<<blocks(nnzc), kAuxThreads, 0, s>>>(nnzc, x->d_c_gptr, x->d_c_gidx, x->d_loc, x->d_vc);
-        k_permute<<<blocks(nnzc), kAuxThreads, 0, s>>>(nnzc, x->d_ct_perm, x->d_vc, x->d_vct);
     }
+    const int na = (int)x->s_am.col.size(), nc = (int)x->s_c.col.size(), nt = (int)x->s_ct.col.size();
+    if (na > 0) {
+        k_sell_fill<<<blocks(na), kAuxThreads, 0, s>>>(na, x->d_sam_map, x->d_va, x->d_sva);
+        k_sell_fill<<<blocks(na), kAuxThreads, 0, s>>>(na, x->d_sam_map, x->d_vm, x->d_svm);
+    }
+    if (nc > 0) k_sell_fill<<<blocks(nc), kAuxThreads, 0, s>>>(nc, x->d_sc_map, x->d_vc, x->d_svc);
+    if (nt > 0) k_sell_fill<<<blocks(nt), kAuxThreads, 0, s>>>(nt, x->d_sct_map, x->d_vc, x->d_svct);
     BMG_CUDA(cudaGetLastError());
     AuxState h;
     BMG_TRY(aux_read(*x, h));
@@ -917,7 +975,7 @@ extern "C" bmg_status bmg_aux_solve(bmg_aux* x, const double* f, double* u, doub
     k_compress<<<blocks(nr), kAuxThreads, 0, s>>>(nr, x->d_vtx, u, x->d_u);
     k_dot_aux<<<kRedBlocks, kAuxThreads, 0, s>>>(nr, x->d_f, x->d_f, x->d_partials, &x->d_st_aux->counter[0],
                                                  &x->d_st_aux->ff);
-    k_residual_csr<<<kRedBlocks, kAuxThreads, 0, s>>>(nr, x->d_am_ptr, x->d_am_col, x->d_va, x->d_f, x->d_u, nullptr,
+    k_residual_csr<<<kRedBlocks, kAuxThreads, 0, s>>>(nr, x->d_sam_off, x->d_sam_col, x->d_sva, x->d_f, x->d_u, nullptr,
                                                       x->d_partials, &x->d_st_aux->counter[0], &x->d_st_aux->rr);
     BMG_CUDA(cudaGetLastError());
     AuxState h;
@@ -930,7 +988,7 @@ extern "C" bmg_status bmg_aux_solve(bmg_aux* x, const double* f, double* u, doub
         // the paper's stationary iteration
         while (it < maxit && rel > tol && nf > 0.0) {
             BMG_TRY(aux_cycle(*x, x->d_f, x->d_u, x->d_u2));
-            k_residual_csr<<<kRedBlocks, kAuxThreads, 0, s>>>(nr, x->d_am_ptr, x->d_am_col, x->d_va, x->d_f, x->d_u,
+            k_residual_csr<<<kRedBlocks, kAuxThreads, 0, s>>>(nr, x->d_sam_off, x->d_sam_col, x->d_sva, x->d_f, x->d_u,
                                                               nullptr, x->d_partials, cnt, &x->d_st_aux->rr);
             BMG_CUDA(cudaGetLastError());
             BMG_TRY(aux_read(*x, h));
@@ -942,7 +1000,7 @@ extern "C" bmg_status bmg_aux_solve(bmg_aux* x, const double* f, double* u, doub
         // flexible CG with one two-grid cycle (zero initial guess) as the
         // preconditioner z = B r; beta = r.(z - z_old) / (r_old.z_old)
         const size_t vb = sizeof(double) * nr;
-        k_residual_csr<<<kRedBlocks, kAuxThreads, 0, s>>>(nr, x->d_am_ptr, x->d_am_col, x->d_va, x->d_f, x->d_u,
+        k_residual_csr<<<kRedBlocks, kAuxThreads, 0, s>>>(nr, x->d_sam_off, x->d_sam_col, x->d_sva, x->d_f, x->d_u,
                                                           x->d_kr, x->d_partials, cnt, &x->d_st_aux->rr);
         BMG_CUDA(cudaMemsetAsync(x->d_kz, 0, vb, s));
         BMG_TRY(aux_cycle(*x, x->d_kr, x->d_kz, x->d_kz2));
@@ -954,7 +1012,7 @@ extern "C" bmg_status bmg_aux_solve(bmg_aux* x, const double* f, double* u, doub
         BMG_TRY(aux_read(*x, h));
         double rz = h.rz;
         while (it < maxit && rel > tol) {
-            k_spmv_dot<<<kRedBlocks, kAuxThreads, 0, s>>>(nr, x->d_am_ptr, x->d_am_col, x->d_va, x->d_kp, x->d_kq,
+            k_spmv_dot<<<kRedBlocks, kAuxThreads, 0, s>>>(nr, x->d_sam_off, x->d_sam_col, x->d_sva, x->d_kp, x->d_kq,
                                                           x->d_partials, cnt, &x->d_st_aux->pq);
             BMG_CUDA(cudaGetLastError());
             BMG_TRY(aux_read(*x, h));
@@ -979,7 +1037,7 @@ extern "C" bmg_status bmg_aux_solve(bmg_aux* x, const double* f, double* u, doub
             k_p_update_aux<<<blocks(nr), kAuxThreads, 0, s>>>(nr, x->d_kp, x->d_kz, beta);
         }
         // the recursive residual drifts from f - A u: report the true one
-        k_residual_csr<<<kRedBlocks, kAuxThreads, 0, s>>>(nr, x->d_am_ptr, x->d_am_col, x->d_va, x->d_f, x->d_u,
+        k_residual_csr<<<kRedBlocks, kAuxThreads, 0, s>>>(nr, x->d_sam_off, x->d_sam_col, x->d_sva, x->d_f, x->d_u,
                                                           nullptr, x->d_partials, cnt, &x->d_st_aux->rr);
         BMG_CUDA(cudaGetLastError());
         BMG_TRY(aux_read(*x, h));
@@ -1030,21 +1088,21 @@ bmg_status apply_ptap(bmg_aux& x, const double* q, double* v) {
     const bool lumped = x.opts.mass_steps == 0;
     const dim3 gp(blocks(x.ld), x.n);
     k_to_padded<<<gp, kAuxThreads, 0, s>>>(x.n, x.ld, q, x.d_cpad);
-    k_prolong_c<<<blocks(nr), kAuxThreads, 0, s>>>(nr, x.d_c_ptr, x.d_c_col, x.d_vc, x.d_cpad,
+    k_prolong_c<<<blocks(nr), kAuxThreads, 0, s>>>(nr, x.d_sc_off, x.d_sc_col, x.d_svc, x.d_cpad,
                                                    lumped ? x.d_mlinv : nullptr, x.d_w, nullptr, 0.0);
     const double* y = x.d_w;
     if (!lumped) {
         BMG_TRY(mass_cg(x, x.d_w, x.d_y));
         y = x.d_y;
     }
-    k_spmv_csr<<<blocks(nr), kAuxThreads, 0, s>>>(nr, x.d_am_ptr, x.d_am_col, x.d_va, y, x.d_r);
+    k_spmv_csr<<<blocks(nr), kAuxThreads, 0, s>>>(nr, x.d_sam_off, x.d_sam_col, x.d_sva, y, x.d_r);
     const double* z = x.d_r;
     if (!lumped) {
         BMG_TRY(mass_cg(x, x.d_r, x.d_y));
         z = x.d_y;
     }
     BMG_CUDA(cudaMemsetAsync(x.d_cpad2, 0, sizeof(double) * (size_t)x.ld * x.n, s));
-    k_restrict_ct<<<blocks(nq), kAuxThreads, 0, s>>>(nq, x.d_ct_ptr, x.d_ct_col, x.d_vct, x.d_ct_map, z,
+    k_restrict_ct<<<blocks(nq), kAuxThreads, 0, s>>>(nq, x.d_sct_off, x.d_sct_col, x.d_svct, x.d_ct_map, z,
                                                      lumped ? x.d_mlinv : nullptr, x.d_cpad2);
     k_from_padded<<<gp, kAuxThreads, 0, s>>>(x.n, x.ld, x.d_cpad2, v);
     BMG_CUDA(cudaGetLastError());
