@@ -328,7 +328,10 @@ typedef struct {
     int mass_steps;    /* CG iterations for M_p^-1 (>= 1), or 0 for the lumped mass (default 0) */
     double gamma;      /* coarse-grid scaling (default 1) */
     int krylov;        /* 0: the paper's stationary iteration of cycles (default); 1: flexible CG
-                          with one cycle from a zero guess as the preconditioner */
+                          with one cycle from a zero guess as the preconditioner.  With the
+                          lumped mass and an FP32 coarse context, that preconditioning cycle
+                          runs its physical level in FP32 too (A_p products in difference
+                          form with FP64 row sums); the CG itself stays FP64 */
 } bmg_aux_opts;
 
 void bmg_aux_default_opts(bmg_aux_opts* opts);

@@ -37,6 +37,7 @@ struct AuxState {
     double rr;          // ||f - A u||^2 (interior)
     double ff;          // ||f||^2
     double pq, rz, rzo; // the outer flexible CG's scalars
+    double alpha_o, beta_o;
     double cg_rr, cg_pq, alpha, beta;
     int err;
     unsigned int counter[4];
@@ -357,10 +358,9 @@ __global__ void k_cg_p(int nr, const double* __restrict__ res, double* __restric
         p[i] = res[i] + beta * p[i];
 }
 
-// q = A p and p.q
+// q = A p; alpha = rz / p.q (device-side, with a breakdown check)
 __global__ void k_spmv_dot(int nr, const int* __restrict__ rp, const int* __restrict__ ci, const double* __restrict__ va,
-                           const double* __restrict__ p, double* __restrict__ q, double* partials, unsigned int* counter,
-                           double* slot) {
+                           const double* __restrict__ p, double* __restrict__ q, double* partials, AuxState* st) {
     double acc = 0.0;
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < nr; i += gridDim.x * blockDim.x) {
         const double v = csr_row(rp, ci, va, p, i);
@@ -368,13 +368,19 @@ __global__ void k_spmv_dot(int nr, const int* __restrict__ rp, const int* __rest
         acc += p[i] * v;
     }
     double t;
-    if (grid_sum(acc, partials, counter, &t)) *slot = t;
+    if (grid_sum(acc, partials, &st->counter[2], &t)) {
+        st->pq = t;
+        const bool ok = t > 0.0 && st->rz > 0.0;
+        st->alpha_o = ok ? st->rz / t : 0.0;
+        if (!ok) aux_err(st, BMG_ERR_NOT_SPD);
+    }
 }
 
-// u += alpha p; r -= alpha q; ||r||^2
+// u += alpha p; r -= alpha q; ||r||^2 (alpha from the device state)
 __global__ void k_update_ur(int nr, double* __restrict__ u, double* __restrict__ r, const double* __restrict__ p,
-                            const double* __restrict__ q, double alpha, double* partials, unsigned int* counter,
+                            const double* __restrict__ q, const AuxState* stc, double* partials, unsigned int* counter,
                             double* slot) {
+    const double alpha = stc->alpha_o;
     double acc = 0.0;
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < nr; i += gridDim.x * blockDim.x) {
         u[i] += alpha * p[i];
@@ -386,25 +392,114 @@ __global__ void k_update_ur(int nr, double* __restrict__ u, double* __restrict__
     if (grid_sum(acc, partials, counter, &t)) *slot = t;
 }
 
-// r.z and r.zo
+// r.z and r.zo; beta = (r.z - r.zo) / rz_old and rz = r.z on the device
+// (first: only rz)
 __global__ void k_dot2_aux(int nr, const double* __restrict__ r, const double* __restrict__ z,
-                           const double* __restrict__ zo, double* partials, unsigned int* counter, double* s1,
-                           double* s2) {
+                           const double* __restrict__ zo, double* partials, AuxState* st, int first) {
     double a = 0.0, b = 0.0;
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < nr; i += gridDim.x * blockDim.x) {
         a += r[i] * z[i];
         b += r[i] * zo[i];
     }
     double t1, t2;
-    if (grid_sum2(a, b, partials, counter, &t1, &t2)) {
-        *s1 = t1;
-        *s2 = t2;
+    if (grid_sum2(a, b, partials, &st->counter[3], &t1, &t2)) {
+        st->rzo = t2;
+        st->beta_o = first ? 0.0 : (st->rz > 0.0 ? (t1 - t2) / st->rz : 0.0);
+        st->rz = t1;
     }
 }
 
-__global__ void k_p_update_aux(int nr, double* __restrict__ p, const double* __restrict__ z, double beta) {
+__global__ void k_p_update_aux(int nr, double* __restrict__ p, const double* __restrict__ z, const AuxState* st) {
+    const double beta = st->beta_o;
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i < nr) p[i] = z[i] + beta * p[i];
+}
+
+// ---- FP32 cycle (the flexible-CG preconditioner on an FP32 coarse context)
+// A_p products in difference form, rs_i u_i + sum_j a_ij (u_j - u_i) with
+// the row sums rs_i formed in FP64: a smooth u makes the plain FP32 product
+// lose A u to cancellation (the diagonal entry contributes a_ii * 0).
+__device__ __forceinline__ float sell_diff32(const int* __restrict__ so, const int* __restrict__ ci,
+                                            const float* __restrict__ va, const float* __restrict__ rs,
+                                            const float* __restrict__ x, int i) {
+    const int sl = i >> 5;
+    const int b = so[sl] + (i & 31), e = so[sl + 1];
+    const float xi = x[i];
+    float s = rs[i] * xi;
+    for (int k = b; k < e; k += 32) s += va[k] * (x[ci[k]] - xi);
+    return s;
+}
+
+__global__ void k_to32(int nr, const double* __restrict__ in, float* __restrict__ out) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < nr) out[i] = (float)in[i];
+}
+
+__global__ void k_to64(int nr, const float* __restrict__ in, double* __restrict__ out) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < nr) out[i] = (double)in[i];
+}
+
+// uo = u + omega D^-1 (f - A u); with u == nullptr, u = 0 (the first sweep)
+__global__ void k_jacobi32(int nr, const int* __restrict__ so, const int* __restrict__ ci, const float* __restrict__ va,
+                           const float* __restrict__ rs, const float* __restrict__ dinv, const float* __restrict__ f,
+                           const float* __restrict__ u, float* __restrict__ uo, float omega) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= nr) return;
+    if (!u) {
+        uo[i] = omega * dinv[i] * f[i];
+        return;
+    }
+    uo[i] = u[i] + omega * dinv[i] * (f[i] - sell_diff32(so, ci, va, rs, u, i));
+}
+
+// r = f - A u (FP32, difference form)
+__global__ void k_residual32(int nr, const int* __restrict__ so, const int* __restrict__ ci,
+                             const float* __restrict__ va, const float* __restrict__ rs, const float* __restrict__ f,
+                             const float* __restrict__ u, float* __restrict__ r) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < nr) r[i] = f[i] - sell_diff32(so, ci, va, rs, u, i);
+}
+
+// rc[map[q]] = sum_k C^T[q,k] y[col] w[col] (FP32 products, FP64 out for the coarse solve)
+__global__ void k_restrict_ct32(int nq, const int* __restrict__ so, const int* __restrict__ ci,
+                                const float* __restrict__ va, const int* __restrict__ map, const float* __restrict__ y,
+                                const float* __restrict__ w, double* __restrict__ rc) {
+    const int q = blockIdx.x * blockDim.x + threadIdx.x;
+    if (q >= nq) return;
+    const int sl = q >> 5;
+    const int b = so[sl] + (q & 31), e = so[sl + 1];
+    float s = 0.0f;
+    for (int k = b; k < e; k += 32) s += va[k] * (y[ci[k]] * w[ci[k]]);
+    rc[map[q]] = (double)s;
+}
+
+// u += gamma w (C z), z the coarse correction (FP64, padded layout)
+__global__ void k_prolong_c32(int nr, const int* __restrict__ so, const int* __restrict__ ci,
+                              const float* __restrict__ va, const double* __restrict__ z, const float* __restrict__ w,
+                              float* __restrict__ u, float gamma) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= nr) return;
+    const int sl = i >> 5;
+    const int b = so[sl] + (i & 31), e = so[sl + 1];
+    float s = 0.0f;
+    for (int k = b; k < e; k += 32) s += va[k] * (float)z[ci[k]];
+    u[i] += gamma * (s * w[i]);
+}
+
+__global__ void k_row_sums_sell(int nr, const int* __restrict__ so, const double* __restrict__ va,
+                                float* __restrict__ rs) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= nr) return;
+    const int sl = i >> 5;
+    double s = 0.0;
+    for (int k = so[sl] + (i & 31); k < so[sl + 1]; k += 32) s += va[k];
+    rs[i] = (float)s;
+}
+
+__global__ void k_d2f(int n, const double* __restrict__ in, float* __restrict__ out) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) out[i] = (float)in[i];
 }
 
 __global__ void k_axpy(int nr, double* __restrict__ u, const double* __restrict__ v, double gamma) {
@@ -588,6 +683,10 @@ struct bmg_aux {
     int *d_sc_off = nullptr, *d_sc_col = nullptr, *d_sc_map = nullptr;
     int *d_sct_off = nullptr, *d_sct_col = nullptr, *d_sct_map = nullptr;
     double *d_sva = nullptr, *d_svm = nullptr, *d_svc = nullptr, *d_svct = nullptr;
+    // FP32 preconditioner (flexible CG, lumped mass, FP32 coarse context)
+    bool fp32 = false;
+    float *d_sva32 = nullptr, *d_svc32 = nullptr, *d_svct32 = nullptr, *d_rs32 = nullptr, *d_dinv32 = nullptr,
+          *d_mlinv32 = nullptr, *d_f32 = nullptr, *d_u32 = nullptr, *d_u32b = nullptr, *d_r32 = nullptr;
     // coarse-grid scaling (Lanczos): padded and natural coarse vectors
     double *d_cpad = nullptr, *d_cpad2 = nullptr;
     double *d_lq = nullptr, *d_lqp = nullptr, *d_lb = nullptr, *d_lbp = nullptr, *d_lv = nullptr, *d_lw = nullptr;
@@ -648,6 +747,14 @@ size_t carve_aux(bmg_aux& x, char* base) {
     x.d_svm = (double*)take(D * x.s_am.col.size());
     x.d_svc = (double*)take(D * x.s_c.col.size());
     x.d_svct = (double*)take(D * x.s_ct.col.size());
+    if (x.fp32) {
+        const size_t F = sizeof(float);
+        x.d_sva32 = (float*)take(F * x.s_am.col.size());
+        x.d_svc32 = (float*)take(F * x.s_c.col.size());
+        x.d_svct32 = (float*)take(F * x.s_ct.col.size());
+        float** fv[] = {&x.d_rs32, &x.d_dinv32, &x.d_mlinv32, &x.d_f32, &x.d_u32, &x.d_u32b, &x.d_r32};
+        for (float** v : fv) *v = (float*)take(F * std::max(x.nvi, 1));
+    }
     const size_t plane = (size_t)x.ld * x.n, nn = (size_t)x.n * x.n;
     x.d_cpad = (double*)take(D * plane);
     x.d_cpad2 = (double*)take(D * plane);
@@ -725,6 +832,39 @@ bmg_status aux_cycle(bmg_aux& x, const double* f, double* u, double* u2) {
     std::swap(u, u2);
     BMG_CUDA(cudaGetLastError());
     return BMG_OK;
+}
+
+// One cycle from a zero guess as the preconditioner z = B r, with the
+// physical level in FP32 (the coarse context's V-cycle is FP32 too): r, z
+// are FP64 interior vectors.
+bmg_status aux_precond32(bmg_aux& x, const double* r, double* z) {
+    Ctx& c = x.coarse->c;
+    cudaStream_t s = c.stream;
+    const int nr = x.nvi, nq = (int)x.ct_map.size();
+    const float om = (float)x.opts.omega;
+    k_to32<<<blocks(nr), kAuxThreads, 0, s>>>(nr, r, x.d_f32);
+    k_jacobi32<<<blocks(nr), kAuxThreads, 0, s>>>(nr, x.d_sam_off, x.d_sam_col, x.d_sva32, x.d_rs32, x.d_dinv32,
+                                                  x.d_f32, nullptr, x.d_u32, om);
+    k_residual32<<<blocks(nr), kAuxThreads, 0, s>>>(nr, x.d_sam_off, x.d_sam_col, x.d_sva32, x.d_rs32, x.d_f32,
+                                                    x.d_u32, x.d_r32);
+    BMG_CUDA(cudaMemsetAsync(c.r, 0, sizeof(double) * c.lev[0].plane, s));
+    k_restrict_ct32<<<blocks(nq), kAuxThreads, 0, s>>>(nq, x.d_sct_off, x.d_sct_col, x.d_svct32, x.d_ct_map, x.d_r32,
+                                                       x.d_mlinv32, c.r);
+    BMG_TRY(vcycle(c, c.r, c.z[0]));
+    k_prolong_c32<<<blocks(nr), kAuxThreads, 0, s>>>(nr, x.d_sc_off, x.d_sc_col, x.d_svc32, c.z[0], x.d_mlinv32,
+                                                     x.d_u32, (float)x.opts.gamma);
+    k_jacobi32<<<blocks(nr), kAuxThreads, 0, s>>>(nr, x.d_sam_off, x.d_sam_col, x.d_sva32, x.d_rs32, x.d_dinv32,
+                                                  x.d_f32, x.d_u32, x.d_u32b, om);
+    k_to64<<<blocks(nr), kAuxThreads, 0, s>>>(nr, x.d_u32b, z);
+    BMG_CUDA(cudaGetLastError());
+    return BMG_OK;
+}
+
+// z = B r: one cycle from a zero guess (FP64, or the FP32 form above)
+bmg_status aux_precond(bmg_aux& x, const double* r, double* z) {
+    if (x.fp32) return aux_precond32(x, r, z);
+    BMG_CUDA(cudaMemsetAsync(z, 0, sizeof(double) * x.nvi, x.coarse->c.stream));
+    return aux_cycle(x, r, z, x.d_kz2);
 }
 
 }  // namespace
@@ -871,6 +1011,7 @@ extern "C" bmg_status bmg_aux_create(bmg_ctx* coarse, int nv, const double* xy, 
                 pos[q]++;
             }
     }
+    x->fp32 = o.krylov == 1 && o.mass_steps == 0 && c.opts.precision == BMG_PREC_FP32;
     build_sell(x->am.ptr, x->am.col, nullptr, x->s_am);
     build_sell(x->cm.ptr, x->cm.col, nullptr, x->s_c);
     build_sell(x->ct_ptr, x->ct_col, &x->ct_perm, x->s_ct);
@@ -956,6 +1097,14 @@ extern "C" bmg_status bmg_aux_setup(bmg_aux* x, void* ws, size_t bytes, const do
     }
     if (nc > 0) k_sell_fill<<<blocks(nc), kAuxThreads, 0, s>>>(nc, x->d_sc_map, x->d_vc, x->d_svc);
     if (nt > 0) k_sell_fill<<<blocks(nt), kAuxThreads, 0, s>>>(nt, x->d_sct_map, x->d_vc, x->d_svct);
+    if (x->fp32) {
+        k_d2f<<<blocks(na), kAuxThreads, 0, s>>>(na, x->d_sva, x->d_sva32);
+        k_d2f<<<blocks(nc), kAuxThreads, 0, s>>>(nc, x->d_svc, x->d_svc32);
+        k_d2f<<<blocks(nt), kAuxThreads, 0, s>>>(nt, x->d_svct, x->d_svct32);
+        k_row_sums_sell<<<blocks(x->nvi), kAuxThreads, 0, s>>>(x->nvi, x->d_sam_off, x->d_sva, x->d_rs32);
+        k_d2f<<<blocks(x->nvi), kAuxThreads, 0, s>>>(x->nvi, x->d_dinv, x->d_dinv32);
+        k_d2f<<<blocks(x->nvi), kAuxThreads, 0, s>>>(x->nvi, x->d_mlinv, x->d_mlinv32);
+    }
     BMG_CUDA(cudaGetLastError());
     AuxState h;
     BMG_TRY(aux_read(*x, h));
@@ -971,6 +1120,7 @@ extern "C" bmg_status bmg_aux_solve(bmg_aux* x, const double* f, double* u, doub
     Ctx& c = x->coarse->c;
     cudaStream_t s = c.stream;
     const int nr = x->nvi;
+    BMG_CUDA(cudaMemsetAsync(&x->d_st_aux->err, 0, sizeof(int), s));
     k_compress<<<blocks(nr), kAuxThreads, 0, s>>>(nr, x->d_vtx, f, x->d_f);
     k_compress<<<blocks(nr), kAuxThreads, 0, s>>>(nr, x->d_vtx, u, x->d_u);
     k_dot_aux<<<kRedBlocks, kAuxThreads, 0, s>>>(nr, x->d_f, x->d_f, x->d_partials, &x->d_st_aux->counter[0],
@@ -998,43 +1148,33 @@ extern "C" bmg_status bmg_aux_solve(bmg_aux* x, const double* f, double* u, doub
         }
     } else if (rel > tol && nf > 0.0 && maxit > 0) {
         // flexible CG with one two-grid cycle (zero initial guess) as the
-        // preconditioner z = B r; beta = r.(z - z_old) / (r_old.z_old)
+        // preconditioner z = B r; beta = r.(z - z_old) / (r_old.z_old).  The
+        // scalars stay on the device; the host reads ||r|| once per iteration.
         const size_t vb = sizeof(double) * nr;
+        AuxState* dst = x->d_st_aux;
         k_residual_csr<<<kRedBlocks, kAuxThreads, 0, s>>>(nr, x->d_sam_off, x->d_sam_col, x->d_sva, x->d_f, x->d_u,
-                                                          x->d_kr, x->d_partials, cnt, &x->d_st_aux->rr);
-        BMG_CUDA(cudaMemsetAsync(x->d_kz, 0, vb, s));
-        BMG_TRY(aux_cycle(*x, x->d_kr, x->d_kz, x->d_kz2));
+                                                          x->d_kr, x->d_partials, cnt, &dst->rr);
+        BMG_TRY(aux_precond(*x, x->d_kr, x->d_kz));
         BMG_CUDA(cudaMemsetAsync(x->d_kzo, 0, vb, s));
-        k_dot2_aux<<<kRedBlocks, kAuxThreads, 0, s>>>(nr, x->d_kr, x->d_kz, x->d_kzo, x->d_partials, cnt,
-                                                      &x->d_st_aux->rz, &x->d_st_aux->rzo);
+        k_dot2_aux<<<kRedBlocks, kAuxThreads, 0, s>>>(nr, x->d_kr, x->d_kz, x->d_kzo, x->d_partials, dst, 1);
         BMG_CUDA(cudaMemcpyAsync(x->d_kp, x->d_kz, vb, cudaMemcpyDeviceToDevice, s));
         BMG_CUDA(cudaGetLastError());
-        BMG_TRY(aux_read(*x, h));
-        double rz = h.rz;
         while (it < maxit && rel > tol) {
             k_spmv_dot<<<kRedBlocks, kAuxThreads, 0, s>>>(nr, x->d_sam_off, x->d_sam_col, x->d_sva, x->d_kp, x->d_kq,
-                                                          x->d_partials, cnt, &x->d_st_aux->pq);
+                                                          x->d_partials, dst);
+            k_update_ur<<<kRedBlocks, kAuxThreads, 0, s>>>(nr, x->d_u, x->d_kr, x->d_kp, x->d_kq, dst, x->d_partials,
+                                                           cnt, &dst->rr);
             BMG_CUDA(cudaGetLastError());
             BMG_TRY(aux_read(*x, h));
-            if (!(h.pq > 0.0) || !(rz > 0.0)) return BMG_ERR_NOT_SPD;
-            const double alpha = rz / h.pq;
-            k_update_ur<<<kRedBlocks, kAuxThreads, 0, s>>>(nr, x->d_u, x->d_kr, x->d_kp, x->d_kq, alpha,
-                                                           x->d_partials, cnt, &x->d_st_aux->rr);
-            BMG_CUDA(cudaGetLastError());
-            BMG_TRY(aux_read(*x, h));
+            if (h.err) return (bmg_status)h.err;
             rel = sqrt(h.rr) / nf;
             it++;
             if (rel <= tol || !(rel == rel)) break;
             std::swap(x->d_kz, x->d_kzo);
-            BMG_CUDA(cudaMemsetAsync(x->d_kz, 0, vb, s));
-            BMG_TRY(aux_cycle(*x, x->d_kr, x->d_kz, x->d_kz2));
-            k_dot2_aux<<<kRedBlocks, kAuxThreads, 0, s>>>(nr, x->d_kr, x->d_kz, x->d_kzo, x->d_partials, cnt,
-                                                          &x->d_st_aux->rz, &x->d_st_aux->rzo);
+            BMG_TRY(aux_precond(*x, x->d_kr, x->d_kz));
+            k_dot2_aux<<<kRedBlocks, kAuxThreads, 0, s>>>(nr, x->d_kr, x->d_kz, x->d_kzo, x->d_partials, dst, 0);
+            k_p_update_aux<<<blocks(nr), kAuxThreads, 0, s>>>(nr, x->d_kp, x->d_kz, dst);
             BMG_CUDA(cudaGetLastError());
-            BMG_TRY(aux_read(*x, h));
-            const double beta = (h.rz - h.rzo) / rz;
-            rz = h.rz;
-            k_p_update_aux<<<blocks(nr), kAuxThreads, 0, s>>>(nr, x->d_kp, x->d_kz, beta);
         }
         // the recursive residual drifts from f - A u: report the true one
         k_residual_csr<<<kRedBlocks, kAuxThreads, 0, s>>>(nr, x->d_sam_off, x->d_sam_col, x->d_sva, x->d_f, x->d_u,

@@ -154,3 +154,22 @@ def test_flexible_cg_matches_oracle(mass_steps):
     assert abs(info.iterations - ito) <= 1
     assert info.true_relres <= 2e-10
     assert relerr(u.cpu().numpy(), uo) <= 1e-8
+
+
+def test_flexible_cg_with_fp32_preconditioner():
+    """On an FP32 coarse context with the lumped mass, the preconditioning
+    cycle runs its physical level in FP32 (difference-form products); the
+    FP64 flexible CG still reaches the tolerance, checked on the host from
+    the exported A_p, in about the iterations of the all-FP64 cycle."""
+    m = inputs.annulus_mesh(97, 145)
+    _, s64 = _coarse(65)
+    coords, s32 = _coarse(65, precision="fp32")
+    f = torch.as_tensor(m.f, device="cuda")
+    _, i64 = binding.AuxSolver(s64, m, krylov=True).solve(f, tol=1e-10)
+    a = binding.AuxSolver(s32, m, krylov=True)
+    u, info = a.solve(f, tol=1e-10)
+    assert info.status == 0 and info.iterations <= i64.iterations + 3
+    iv = np.flatnonzero(~m.dirichlet)
+    A = _csr(a, "A", (len(iv), len(iv)))
+    r = m.f[iv] - A @ u.cpu().numpy()[iv]
+    assert np.linalg.norm(r) <= 1.0001e-10 * np.linalg.norm(m.f[iv])
