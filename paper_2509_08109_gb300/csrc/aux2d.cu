@@ -21,6 +21,7 @@
 #include <string.h>
 
 #include <algorithm>
+#include <memory>
 #include <new>
 #include <vector>
 
@@ -603,16 +604,20 @@ struct Sell {
     std::vector<int> off, col, map;   // slice offsets, columns, CSR index of each slot (-1: padding)
 };
 
-// CSR (ptr, col) -> SELL-32; map[k] = CSR entry of slot k, composed with `through` if given
-void build_sell(const std::vector<int>& ptr, const std::vector<int>& col, const std::vector<int>* through,
+// CSR (ptr, col) -> SELL-32; map[k] = CSR entry of slot k, composed with
+// `through` if given.  False if the padded size exceeds 32-bit indices.
+bool build_sell(const std::vector<int>& ptr, const std::vector<int>& col, const std::vector<int>* through,
                 Sell& out) {
     const int nr = (int)ptr.size() - 1;
     const int ns = (nr + 31) / 32;
     out.off.assign(ns + 1, 0);
+    long long total = 0;
     for (int sl = 0; sl < ns; sl++) {
         int w = 0;
         for (int i = sl * 32; i < std::min(nr, sl * 32 + 32); i++) w = std::max(w, ptr[i + 1] - ptr[i]);
-        out.off[sl + 1] = out.off[sl] + 32 * w;
+        total += 32LL * w;
+        if (total > 0x7fffffffLL) return false;
+        out.off[sl + 1] = (int)total;
     }
     out.col.assign(out.off[ns], 0);
     out.map.assign(out.off[ns], -1);
@@ -624,6 +629,7 @@ void build_sell(const std::vector<int>& ptr, const std::vector<int>& col, const 
             out.map[slot] = through ? (*through)[k] : k;
         }
     }
+    return true;
 }
 
 // separating-axis test of a triangle against an axis-aligned box (touching counts)
@@ -877,9 +883,27 @@ extern "C" void bmg_aux_default_opts(bmg_aux_opts* o) {
     o->krylov = 0;
 }
 
+namespace {
+bmg_status aux_create(bmg_ctx* coarse, int nv, const double* xy, const double* st, const unsigned char* dirichlet,
+                      int ntri, const int* tri, const bmg_aux_opts* opts, bmg_aux** out);
+}  // namespace
+
+// Host allocations of the build may fail for very large meshes; no C++
+// exception crosses the C ABI.
 extern "C" bmg_status bmg_aux_create(bmg_ctx* coarse, int nv, const double* xy, const double* st,
                                      const unsigned char* dirichlet, int ntri, const int* tri,
                                      const bmg_aux_opts* opts, bmg_aux** out) {
+    try {
+        return aux_create(coarse, nv, xy, st, dirichlet, ntri, tri, opts, out);
+    } catch (...) {
+        if (out) *out = nullptr;
+        return BMG_ERR_SHAPE;
+    }
+}
+
+namespace {
+bmg_status aux_create(bmg_ctx* coarse, int nv, const double* xy, const double* st, const unsigned char* dirichlet,
+                      int ntri, const int* tri, const bmg_aux_opts* opts, bmg_aux** out) {
     if (!out) return BMG_ERR_ARG;
     *out = nullptr;
     if (!coarse || !xy || !st || !dirichlet || !tri || nv < 3 || ntri < 1) return BMG_ERR_ARG;
@@ -895,7 +919,7 @@ extern "C" bmg_status bmg_aux_create(bmg_ctx* coarse, int nv, const double* xy, 
     for (long long k = 0; k < 3LL * ntri; k++)
         if (tri[k] < 0 || tri[k] >= nv) return BMG_ERR_ARG;
     if (9LL * ntri > 0x7fffffffLL) return BMG_ERR_SHAPE;
-    bmg_aux* x = new (std::nothrow) bmg_aux;
+    std::unique_ptr<bmg_aux> x(new (std::nothrow) bmg_aux);
     if (!x) return BMG_ERR_ARG;
     x->coarse = coarse;
     x->opts = o;
@@ -932,7 +956,6 @@ extern "C" bmg_status bmg_aux_create(bmg_ctx* coarse, int nv, const double* xy, 
                 }
             }
         if (!build_csr(x->nvi, rr, cc, src, x->am) || !build_csr(x->nvi, lr, lc, ls, x->lump)) {
-            delete x;
             return BMG_ERR_SHAPE;
         }
         x->diag_pos.assign(x->nvi, -1);
@@ -941,7 +964,6 @@ extern "C" bmg_status bmg_aux_create(bmg_ctx* coarse, int nv, const double* xy, 
                 if (x->am.col[k] == i) x->diag_pos[i] = k;
         for (int i = 0; i < x->nvi; i++)
             if (x->diag_pos[i] < 0 || x->lump.ptr[i + 1] != i + 1) {   // an interior vertex in no triangle
-                delete x;
                 return BMG_ERR_ARG;
             }
     }
@@ -969,7 +991,6 @@ extern "C" bmg_status bmg_aux_create(bmg_ctx* coarse, int nv, const double* xy, 
                     if (!tri_box_overlap(sx, sy, ci * h, cj * h, (ci + 1) * h, (cj + 1) * h)) continue;
                     const long long p = (long long)x->pair_tri.size();
                     if (12 * (p + 1) > 0x7fffffffLL) {
-                        delete x;
                         return BMG_ERR_SHAPE;
                     }
                     x->pair_tri.push_back(t);
@@ -988,7 +1009,6 @@ extern "C" bmg_status bmg_aux_create(bmg_ctx* coarse, int nv, const double* xy, 
                 }
         }
         if (!build_csr(x->nvi, rr, cc, src, x->cm)) {
-            delete x;
             return BMG_ERR_SHAPE;
         }
         // C^T: rows = interior coarse nodes (j-1)(n-2) + (i-1), entries in C order
@@ -1012,13 +1032,16 @@ extern "C" bmg_status bmg_aux_create(bmg_ctx* coarse, int nv, const double* xy, 
             }
     }
     x->fp32 = o.krylov == 1 && o.mass_steps == 0 && c.opts.precision == BMG_PREC_FP32;
-    build_sell(x->am.ptr, x->am.col, nullptr, x->s_am);
-    build_sell(x->cm.ptr, x->cm.col, nullptr, x->s_c);
-    build_sell(x->ct_ptr, x->ct_col, &x->ct_perm, x->s_ct);
+    if (!build_sell(x->am.ptr, x->am.col, nullptr, x->s_am) || !build_sell(x->cm.ptr, x->cm.col, nullptr, x->s_c) ||
+        !build_sell(x->ct_ptr, x->ct_col, &x->ct_perm, x->s_ct)) {
+        return BMG_ERR_SHAPE;
+    }
     x->ws_need = carve_aux(*x, nullptr);
-    *out = x;
+    *out = x.release();
     return BMG_OK;
 }
+
+}  // namespace
 
 extern "C" bmg_status bmg_aux_workspace_bytes(const bmg_aux* x, size_t* bytes) {
     if (!x || !bytes) return BMG_ERR_ARG;

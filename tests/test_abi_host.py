@@ -89,3 +89,19 @@ def test_noalloc_validates_before_device_work(lib, dim, n, code):
     """Shape and null-pointer checks of bmg_assemble_noalloc come before any
     CUDA call, so they answer without a device."""
     assert lib.bmg_assemble_noalloc(dim, n, None, None, None, None) == code
+
+
+def test_aux_defaults_and_null_arguments(lib):
+    """The auxiliary-space calls validate their arguments before any device
+    work: defaults of the options, null pointers, no coarse context."""
+    o = binding._AuxOpts()
+    lib.bmg_aux_default_opts(ctypes.byref(o))
+    assert abs(o.omega - 2.0 / 3.0) < 1e-15 and o.mass_steps == 0 and o.gamma == 1.0 and o.krylov == 0
+    h = ctypes.c_void_p()
+    assert lib.bmg_aux_create(None, 3, None, None, None, 1, None, None, ctypes.byref(h)) == 1
+    assert h.value is None
+    nb = ctypes.c_size_t()
+    assert lib.bmg_aux_workspace_bytes(None, ctypes.byref(nb)) == 1
+    assert lib.bmg_aux_solve(None, None, None, 1e-10, 10, None) == 1
+    g = ctypes.c_double()
+    assert lib.bmg_aux_estimate_gamma(None, 12, None, 1e-10, ctypes.byref(g), None, None, None) == 1
