@@ -407,3 +407,32 @@ def annulus_mesh(nr: int, nt: int, jitter: float = 0.2, seed: int = 8) -> Mesh:
     f = np.where(dirichlet, 0.0, rng.uniform(-1.0, 1.0, size=nr * nt))
     kappa = np.ones(tri.shape[0])
     return Mesh(f"annulus_mesh_{nr}x{nt}", xy, st, tri, dirichlet, kappa, f)
+
+
+def square_mesh(nx: int, ny: int, jitter: float = 0.2, seed: int = 10, kappa_sigma: float = 0.0) -> Mesh:
+    """Jittered triangulation of the unit square with the identity as T
+    (st = xy): nx x ny lattice vertices, interior ones moved by up to
+    `jitter` spacings, quads split along alternating diagonals; kappa per
+    triangle exp(N(0, kappa_sigma^2)) (1 when kappa_sigma is 0); f ~ U[-1, 1]
+    on interior vertices.  Drawn in that order from one seeded generator."""
+    rng = np.random.default_rng(seed)
+    k = np.arange(nx)[None, :] * np.ones((ny, 1))
+    l = np.arange(ny)[:, None] * np.ones((1, nx))
+    inner = (k > 0) & (k < nx - 1) & (l > 0) & (l < ny - 1)
+    dk = rng.uniform(-jitter, jitter, size=(ny, nx))
+    dl = rng.uniform(-jitter, jitter, size=(ny, nx))
+    x = (k + np.where(inner, dk, 0.0)) / (nx - 1)
+    y = (l + np.where(inner, dl, 0.0)) / (ny - 1)
+    xy = np.stack([x, y], axis=-1).reshape(-1, 2)
+    v = lambda kq, lq: lq * nx + kq
+    K, L = np.meshgrid(np.arange(nx - 1), np.arange(ny - 1))
+    K, L = K.reshape(-1), L.reshape(-1)
+    a, b, c, d = v(K, L), v(K + 1, L), v(K + 1, L + 1), v(K, L + 1)
+    alt = ((K + L) % 2) == 0
+    t1 = np.where(alt[:, None], np.stack([a, b, c], 1), np.stack([a, b, d], 1))
+    t2 = np.where(alt[:, None], np.stack([a, c, d], 1), np.stack([b, c, d], 1))
+    tri = np.concatenate([t1, t2]).astype(np.int32)
+    kappa = np.exp(rng.normal(0.0, kappa_sigma, size=tri.shape[0])) if kappa_sigma > 0 else np.ones(tri.shape[0])
+    dirichlet = ~inner.reshape(-1)
+    f = np.where(dirichlet, 0.0, rng.uniform(-1.0, 1.0, size=nx * ny))
+    return Mesh(f"square_mesh_{nx}x{ny}", xy, xy.copy(), tri, dirichlet, kappa, f)

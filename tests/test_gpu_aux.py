@@ -173,3 +173,26 @@ def test_flexible_cg_with_fp32_preconditioner():
     A = _csr(a, "A", (len(iv), len(iv)))
     r = m.f[iv] - A @ u.cpu().numpy()[iv]
     assert np.linalg.norm(r) <= 1.0001e-10 * np.linalg.norm(m.f[iv])
+
+
+def test_identity_map_with_rough_coefficient_matches_oracle():
+    """A second geometry: the unit square with T the identity (the coarse
+    grid's cells are then the square's own), a log-normal coefficient per
+    triangle; operators and the flexible-CG solve against the oracle."""
+    m = inputs.square_mesh(27, 23, kappa_sigma=0.5)
+    n = 17
+    coords = inputs.coords_identity(n, 2)
+    s = binding.Solver(2, n)
+    s.assemble(torch.as_tensor(coords), torch.ones((n - 1, n - 1), dtype=torch.float64)).setup()
+    a = binding.AuxSolver(s, m, krylov=True)
+    tg = aux.TwoGrid(m, coords, oracle.assemble(coords, np.ones((n - 1, n - 1))), mass_steps=0)
+    nvi = len(tg.iv)
+    for which, ref in (("A", tg.A), ("M", tg.M)):
+        got = _csr(a, which, (nvi, nvi)).toarray()
+        assert np.abs(got - ref.toarray()).max() <= 1e-13 * np.abs(ref.toarray()).max()
+    C = _csr(a, "C", (nvi, n * n))[:, tg.ic].toarray()
+    assert np.abs(C - tg.C.toarray()).max() <= 1e-13 * np.abs(tg.C.toarray()).max()
+    uo, ito, _ = tg.solve_fcg(m.f, tol=1e-10)
+    u, info = a.solve(torch.as_tensor(m.f, device="cuda"), tol=1e-10)
+    assert info.status == 0 and abs(info.iterations - ito) <= 1
+    assert relerr(u.cpu().numpy(), uo) <= 1e-8
