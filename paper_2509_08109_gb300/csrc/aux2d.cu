@@ -696,6 +696,18 @@ struct bmg_aux {
     // coarse-grid scaling (Lanczos): padded and natural coarse vectors
     double *d_cpad = nullptr, *d_cpad2 = nullptr;
     double *d_lq = nullptr, *d_lqp = nullptr, *d_lb = nullptr, *d_lbp = nullptr, *d_lv = nullptr, *d_lw = nullptr;
+    // iteration graphs: flexible CG, one per parity of the z buffers (0, 1),
+    // and the stationary cycle (2); valid for the coarse context's launch
+    // shapes of epoch g_epoch
+    cudaGraphExec_t g_exec[3] = {nullptr, nullptr, nullptr};
+    long long g_kernels[3] = {0, 0, 0};
+    unsigned long long g_epoch = 0;
+    cudaStream_t g_stream = nullptr;
+    ~bmg_aux() {
+        for (int p = 0; p < 3; p++)
+            if (g_exec[p]) cudaGraphExecDestroy(g_exec[p]);
+        if (g_stream) cudaStreamDestroy(g_stream);
+    }
 };
 
 namespace {
@@ -871,6 +883,85 @@ bmg_status aux_precond(bmg_aux& x, const double* r, double* z) {
     if (x.fp32) return aux_precond32(x, r, z);
     BMG_CUDA(cudaMemsetAsync(z, 0, sizeof(double) * x.nvi, x.coarse->c.stream));
     return aux_cycle(x, r, z, x.d_kz2);
+}
+
+// One flexible-CG iteration after the first (parity p: z_new in buffer p,
+// z_old in buffer p^1): z = B r; beta; p = z + beta p; q = A p, alpha;
+// u += alpha p, r -= alpha q, ||r||^2.  No host synchronisation inside.
+bmg_status fcg_body(bmg_aux& x, int par) {
+    cudaStream_t s = x.coarse->c.stream;
+    const int nr = x.nvi;
+    double* zb[2] = {x.d_kz, x.d_kzo};
+    AuxState* dst = x.d_st_aux;
+    BMG_TRY(aux_precond(x, x.d_kr, zb[par]));
+    k_dot2_aux<<<kRedBlocks, kAuxThreads, 0, s>>>(nr, x.d_kr, zb[par], zb[par ^ 1], x.d_partials, dst, 0);
+    k_p_update_aux<<<blocks(nr), kAuxThreads, 0, s>>>(nr, x.d_kp, zb[par], dst);
+    k_spmv_dot<<<kRedBlocks, kAuxThreads, 0, s>>>(nr, x.d_sam_off, x.d_sam_col, x.d_sva, x.d_kp, x.d_kq, x.d_partials,
+                                                  dst);
+    k_update_ur<<<kRedBlocks, kAuxThreads, 0, s>>>(nr, x.d_u, x.d_kr, x.d_kp, x.d_kq, dst, x.d_partials,
+                                                   &dst->counter[0], &dst->rr);
+    BMG_CUDA(cudaGetLastError());
+    return BMG_OK;
+}
+
+// one stationary iteration: a cycle, then ||f - A u||^2
+bmg_status stat_body(bmg_aux& x) {
+    BMG_TRY(aux_cycle(x, x.d_f, x.d_u, x.d_u2));
+    k_residual_csr<<<kRedBlocks, kAuxThreads, 0, x.coarse->c.stream>>>(x.nvi, x.d_sam_off, x.d_sam_col, x.d_sva,
+                                                                       x.d_f, x.d_u, nullptr, x.d_partials,
+                                                                       &x.d_st_aux->counter[0], &x.d_st_aux->rr);
+    BMG_CUDA(cudaGetLastError());
+    return BMG_OK;
+}
+
+void drop_graphs(bmg_aux& x) {
+    for (int p = 0; p < 3; p++)
+        if (x.g_exec[p]) {
+            cudaGraphExecDestroy(x.g_exec[p]);
+            x.g_exec[p] = nullptr;
+        }
+}
+
+bmg_status body(bmg_aux& x, int slot) { return slot < 2 ? fcg_body(x, slot) : stat_body(x); }
+
+// Runs body(slot) as a replay of its captured graph (captured on first
+// use, and again after the coarse context's launch shapes changed), or
+// directly when graphs are off or the context is profiling.
+bmg_status run_body(bmg_aux& x, int par) {
+    Ctx& c = x.coarse->c;
+    if (!c.use_graphs || c.prof_on) return body(x, par);
+    if (x.g_epoch != c.shape_epoch) {
+        drop_graphs(x);
+        x.g_epoch = c.shape_epoch;
+    }
+    if (!x.g_exec[par]) {
+        if (!x.g_stream) BMG_CUDA(cudaStreamCreateWithFlags(&x.g_stream, cudaStreamNonBlocking));
+        cudaStream_t user = c.stream;
+        c.stream = x.g_stream;
+        cudaGraph_t g = nullptr;
+        bmg_status st = cudaStreamBeginCapture(x.g_stream, cudaStreamCaptureModeRelaxed) == cudaSuccess
+                            ? BMG_OK
+                            : BMG_ERR_DEVICE;
+        const long long before = c.launches;
+        if (st == BMG_OK) st = body(x, par);
+        x.g_kernels[par] = c.launches - before;
+        c.launches = before;
+        const cudaError_t e = cudaStreamEndCapture(x.g_stream, &g);
+        c.stream = user;
+        if (st != BMG_OK || e != cudaSuccess) {
+            if (g) cudaGraphDestroy(g);
+            return st != BMG_OK ? st : BMG_ERR_DEVICE;
+        }
+        const cudaError_t ei = cudaGraphInstantiate(&x.g_exec[par], g, 0);
+        cudaGraphDestroy(g);
+        if (ei != cudaSuccess) {
+            x.g_exec[par] = nullptr;
+            return BMG_ERR_DEVICE;
+        }
+    }
+    BMG_CUDA(cudaGraphLaunch(x.g_exec[par], c.stream));
+    c.launches += x.g_kernels[par];
+    return BMG_OK;
 }
 
 }  // namespace
@@ -1160,10 +1251,7 @@ extern "C" bmg_status bmg_aux_solve(bmg_aux* x, const double* f, double* u, doub
     if (x->opts.krylov == 0) {
         // the paper's stationary iteration
         while (it < maxit && rel > tol && nf > 0.0) {
-            BMG_TRY(aux_cycle(*x, x->d_f, x->d_u, x->d_u2));
-            k_residual_csr<<<kRedBlocks, kAuxThreads, 0, s>>>(nr, x->d_sam_off, x->d_sam_col, x->d_sva, x->d_f, x->d_u,
-                                                              nullptr, x->d_partials, cnt, &x->d_st_aux->rr);
-            BMG_CUDA(cudaGetLastError());
+            BMG_TRY(run_body(*x, 2));
             BMG_TRY(aux_read(*x, h));
             rel = sqrt(h.rr) / nf;
             it++;
@@ -1172,7 +1260,8 @@ extern "C" bmg_status bmg_aux_solve(bmg_aux* x, const double* f, double* u, doub
     } else if (rel > tol && nf > 0.0 && maxit > 0) {
         // flexible CG with one two-grid cycle (zero initial guess) as the
         // preconditioner z = B r; beta = r.(z - z_old) / (r_old.z_old).  The
-        // scalars stay on the device; the host reads ||r|| once per iteration.
+        // scalars stay on the device; the host reads ||r|| once per
+        // iteration.  Iterations after the first replay a captured graph.
         const size_t vb = sizeof(double) * nr;
         AuxState* dst = x->d_st_aux;
         k_residual_csr<<<kRedBlocks, kAuxThreads, 0, s>>>(nr, x->d_sam_off, x->d_sam_col, x->d_sva, x->d_f, x->d_u,
@@ -1181,23 +1270,18 @@ extern "C" bmg_status bmg_aux_solve(bmg_aux* x, const double* f, double* u, doub
         BMG_CUDA(cudaMemsetAsync(x->d_kzo, 0, vb, s));
         k_dot2_aux<<<kRedBlocks, kAuxThreads, 0, s>>>(nr, x->d_kr, x->d_kz, x->d_kzo, x->d_partials, dst, 1);
         BMG_CUDA(cudaMemcpyAsync(x->d_kp, x->d_kz, vb, cudaMemcpyDeviceToDevice, s));
+        k_spmv_dot<<<kRedBlocks, kAuxThreads, 0, s>>>(nr, x->d_sam_off, x->d_sam_col, x->d_sva, x->d_kp, x->d_kq,
+                                                      x->d_partials, dst);
+        k_update_ur<<<kRedBlocks, kAuxThreads, 0, s>>>(nr, x->d_u, x->d_kr, x->d_kp, x->d_kq, dst, x->d_partials, cnt,
+                                                       &dst->rr);
         BMG_CUDA(cudaGetLastError());
-        while (it < maxit && rel > tol) {
-            k_spmv_dot<<<kRedBlocks, kAuxThreads, 0, s>>>(nr, x->d_sam_off, x->d_sam_col, x->d_sva, x->d_kp, x->d_kq,
-                                                          x->d_partials, dst);
-            k_update_ur<<<kRedBlocks, kAuxThreads, 0, s>>>(nr, x->d_u, x->d_kr, x->d_kp, x->d_kq, dst, x->d_partials,
-                                                           cnt, &dst->rr);
-            BMG_CUDA(cudaGetLastError());
+        while (true) {
             BMG_TRY(aux_read(*x, h));
             if (h.err) return (bmg_status)h.err;
             rel = sqrt(h.rr) / nf;
             it++;
-            if (rel <= tol || !(rel == rel)) break;
-            std::swap(x->d_kz, x->d_kzo);
-            BMG_TRY(aux_precond(*x, x->d_kr, x->d_kz));
-            k_dot2_aux<<<kRedBlocks, kAuxThreads, 0, s>>>(nr, x->d_kr, x->d_kz, x->d_kzo, x->d_partials, dst, 0);
-            k_p_update_aux<<<blocks(nr), kAuxThreads, 0, s>>>(nr, x->d_kp, x->d_kz, dst);
-            BMG_CUDA(cudaGetLastError());
+            if (rel <= tol || !(rel == rel) || it >= maxit) break;
+            BMG_TRY(run_body(*x, it & 1));
         }
         // the recursive residual drifts from f - A u: report the true one
         k_residual_csr<<<kRedBlocks, kAuxThreads, 0, s>>>(nr, x->d_sam_off, x->d_sam_col, x->d_sva, x->d_f, x->d_u,
@@ -1333,6 +1417,7 @@ extern "C" bmg_status bmg_aux_estimate_gamma(bmg_aux* x, int k, const double* y0
 extern "C" bmg_status bmg_aux_set_gamma(bmg_aux* x, double gamma) {
     if (!x || !(gamma > 0.0)) return BMG_ERR_ARG;
     x->opts.gamma = gamma;
+    drop_graphs(*x);   // gamma is a captured kernel argument
     return BMG_OK;
 }
 

@@ -115,6 +115,9 @@ struct Ctx {
     cudaGraphExec_t it_exec[2] = {nullptr, nullptr};
     long long it_kernels[2] = {0, 0};
     bool use_graphs = true;
+    // bumped whenever launch shapes change (tile choices): graphs that other
+    // objects capture around this context's kernels compare it
+    unsigned long long shape_epoch = 0;
     FusedLevel fused[kMaxLevels];
 };
 

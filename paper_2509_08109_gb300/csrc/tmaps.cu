@@ -111,6 +111,7 @@ bmg_status fused_configure(Ctx& c, int l, int wc, int hc) {
         if (!make_map(&G.mF, false, c.r32, Lf.ld, Lf.n, 1, Lf.plane, WW, 2)) return BMG_ERR_DEVICE;
     }
     // captured iteration graphs hold the old launch shapes
+    c.shape_epoch++;
     for (int p = 0; p < 2; p++)
         if (c.it_exec[p]) {
             cudaGraphExecDestroy(c.it_exec[p]);

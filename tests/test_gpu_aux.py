@@ -196,3 +196,25 @@ def test_identity_map_with_rough_coefficient_matches_oracle():
     u, info = a.solve(torch.as_tensor(m.f, device="cuda"), tol=1e-10)
     assert info.status == 0 and abs(info.iterations - ito) <= 1
     assert relerr(u.cpu().numpy(), uo) <= 1e-8
+
+
+@pytest.mark.parametrize("krylov", [True, False])
+def test_graph_replay_equals_direct_launches(krylov):
+    """Iterations (after the first, for flexible CG) replay a captured graph
+    when the coarse context uses graphs; the iterates are bitwise those of
+    direct launches, also after gamma changes (the graphs are recaptured)."""
+    m = inputs.annulus_mesh(49, 73)
+    f = torch.as_tensor(m.f, device="cuda")
+    out = []
+    for graphs in (True, False):
+        coords = inputs.coords_quarter_annulus(33)
+        s = binding.Solver(2, 33, precision="fp32", outer="refine", graphs=graphs)
+        s.assemble(torch.as_tensor(coords), torch.ones((32, 32), dtype=torch.float64)).setup()
+        a = binding.AuxSolver(s, m, krylov=krylov)
+        u1, i1 = a.solve(f, tol=1e-10)
+        a.set_gamma(0.9)
+        u2, i2 = a.solve(f, tol=1e-10)
+        out.append((u1.cpu().numpy(), i1.iterations, u2.cpu().numpy(), i2.iterations))
+    (a1, n1, b1, k1), (a2, n2, b2, k2) = out
+    assert n1 == n2 and k1 == k2
+    assert np.array_equal(a1, a2) and np.array_equal(b1, b2)
