@@ -431,11 +431,6 @@ __device__ __forceinline__ float sell_diff32(const int* __restrict__ so, const i
     return s;
 }
 
-__global__ void k_to32(int nr, const double* __restrict__ in, float* __restrict__ out) {
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i < nr) out[i] = (float)in[i];
-}
-
 __global__ void k_to64(int nr, const float* __restrict__ in, double* __restrict__ out) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i < nr) out[i] = (double)in[i];
@@ -512,11 +507,6 @@ __global__ void k_spmv_csr(int nr, const int* __restrict__ rp, const int* __rest
                            const double* __restrict__ va, const double* __restrict__ x, double* __restrict__ y) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i < nr) y[i] = csr_row(rp, ci, va, x, i);
-}
-
-__global__ void k_scale(int nr, double* __restrict__ v, const double* __restrict__ w) {
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i < nr) v[i] *= w[i];
 }
 
 // natural n x n grid vector <-> the coarse context's padded layout (interior only)
@@ -860,7 +850,7 @@ bmg_status aux_precond32(bmg_aux& x, const double* r, double* z) {
     cudaStream_t s = c.stream;
     const int nr = x.nvi, nq = (int)x.ct_map.size();
     const float om = (float)x.opts.omega;
-    k_to32<<<blocks(nr), kAuxThreads, 0, s>>>(nr, r, x.d_f32);
+    k_d2f<<<blocks(nr), kAuxThreads, 0, s>>>(nr, r, x.d_f32);
     k_jacobi32<<<blocks(nr), kAuxThreads, 0, s>>>(nr, x.d_sam_off, x.d_sam_col, x.d_sva32, x.d_rs32, x.d_dinv32,
                                                   x.d_f32, nullptr, x.d_u32, om);
     k_residual32<<<blocks(nr), kAuxThreads, 0, s>>>(nr, x.d_sam_off, x.d_sam_col, x.d_sva32, x.d_rs32, x.d_f32,
