@@ -78,6 +78,7 @@ def _load():
             ("or_hier_get_A", [P, I, P], None),
             ("or_hier_get_P", [P, I, P], None),
             ("or_vcycle", [P, P, P], None),
+            ("or_vcycle32", [P, P, P], None),
             ("or_pcg", [P, P, P, D, I, I, P, P, P], I),
             ("or_adjoint_grad", [I, I, P, P, P, P], I),
             ("or_element_tensor", [I, P, P, P], I),
@@ -299,14 +300,27 @@ class Hierarchy:
         _load().or_vcycle(self._h, _ptr(r), _ptr(z))
         return z
 
-    def pcg(self, b, x0=None, tol: float = 1e-10, maxit: int = 200, flexible: bool = False):
-        """Returns (x, iterations, residual history, true relative residual, status)."""
+    def vcycle32(self, r) -> np.ndarray:
+        """One V-cycle of the FP32 arm: float copies of every level's A and P,
+        float arithmetic, FP64 solve on the 3-node grid; r rounded to float
+        on entry, the result widened to FP64."""
+        r = _f64(r)
+        z = np.zeros_like(r)
+        _load().or_vcycle32(self._h, _ptr(r), _ptr(z))
+        return z
+
+    def pcg(self, b, x0=None, tol: float = 1e-10, maxit: int = 200, flexible: bool = False,
+            fp32: bool = False):
+        """Returns (x, iterations, residual history, true relative residual, status).
+        fp32: precondition with the FP32 V-cycle (use with flexible=True, the
+        mixed-precision form); the CG vectors and dots stay FP64."""
         b = _f64(b)
         x = np.zeros_like(b) if x0 is None else _f64(x0).copy()
         hist = np.zeros(maxit + 1)
         it = ctypes.c_int()
         trr = ctypes.c_double()
-        st = _load().or_pcg(self._h, _ptr(b), _ptr(x), float(tol), int(maxit), int(flexible),
+        mode = int(bool(flexible)) | (2 if fp32 else 0)
+        st = _load().or_pcg(self._h, _ptr(b), _ptr(x), float(tol), int(maxit), mode,
                             ctypes.byref(it), _ptr(hist), ctypes.byref(trr))
         return x, it.value, hist[: it.value + 1].copy(), trr.value, st
 

@@ -22,7 +22,11 @@
  *     operators;
  *   - multicolour Gauss-Seidel, colour = parity pattern of the node,
  *     forward colour order before the coarse correction, reverse after;
- *   - a conjugate-gradient outer loop preconditioned by one V-cycle.
+ *   - a conjugate-gradient outer loop preconditioned by one V-cycle;
+ *   - an FP32 arm of the V-cycle (float copies of every level's operator
+ *     and interpolation, float arithmetic throughout, FP64 solve on the
+ *     3-node grid) as the preconditioner of FP64 flexible CG, the
+ *     mixed-precision form of the solve.
  * Only the tests, the smoke check and the CPU-baseline leg of the
  * benchmark load this file.  It shares no code with the CUDA library.
  *
@@ -734,6 +738,13 @@ typedef struct {
     double* b[32];
     double* x[32];
     double* r[32];
+    /* FP32 arm: float copies of A and P and float level vectors, made on
+       the first FP32 V-cycle */
+    float* A32[32];
+    float* P32[32];
+    float* b32[32];
+    float* x32[32];
+    float* r32[32];
 } or_hier;
 
 static double dot(long nn, const double* a, const double* b) {
@@ -746,6 +757,7 @@ void or_hier_free(or_hier* h) {
     if (!h) return;
     for (int l = 0; l < h->nlev; l++) {
         free(h->A[l]); free(h->P[l]); free(h->b[l]); free(h->x[l]); free(h->r[l]);
+        free(h->A32[l]); free(h->P32[l]); free(h->b32[l]); free(h->x32[l]); free(h->r32[l]);
     }
     free(h);
 }
@@ -828,17 +840,164 @@ void or_vcycle(or_hier* h, const double* r, double* z) {
     memcpy(z, h->x[0], sizeof(double) * nn);
 }
 
+/* ------------------------------------------------------------------ */
+/* FP32 arm: the same V-cycle with single-precision arithmetic          */
+/* ------------------------------------------------------------------ */
+/* The FP32 preconditioner of the mixed-precision solve: every level's
+   operator and interpolation rounded once to float (round to nearest),
+   and every smoothing, residual, restriction and prolongation step
+   evaluated in float variables, so each product and each partial sum is
+   rounded to single precision.  The exact solve on the 3-node grid stays
+   in FP64 (the one unknown's equation, float right-hand side widened,
+   FP64 diagonal, result rounded to float).  The steps and their order are
+   those of the FP64 functions above. */
+static void apply32(int dim, int n, const float* A, const float* x, float* y) {
+    int S = (int)pw_int(3, dim);
+    long nn = pw_int(n, dim);
+    for (long id = 0; id < nn; id++) {
+        int c[3];
+        node_coords(dim, n, id, c);
+        if (!is_interior(dim, n, c)) { y[id] = 0.0f; continue; }
+        float s = 0.0f;
+        for (int o = 0; o < S; o++) {
+            int d[3];
+            offset_of(dim, o, d);
+            int cn[3] = {c[0] + d[0], c[1] + d[1], c[2] + d[2]};
+            float t = A[id * S + o] * x[node_id(dim, n, cn)];
+            s = s + t;
+        }
+        y[id] = s;
+    }
+}
+
+static void smooth32(int dim, int n, const float* A, const float* b, float* x, int reverse) {
+    int S = (int)pw_int(3, dim), C = 1 << dim, ctr = (S - 1) / 2;
+    long nn = pw_int(n, dim);
+    for (int cc = 0; cc < C; cc++) {
+        int col = reverse ? C - 1 - cc : cc;
+        for (long id = 0; id < nn; id++) {
+            int c[3];
+            node_coords(dim, n, id, c);
+            if (!is_interior(dim, n, c) || colour_of(dim, c) != col) continue;
+            float s = b[id];
+            for (int o = 0; o < S; o++) {
+                if (o == ctr) continue;
+                int d[3];
+                offset_of(dim, o, d);
+                int cn[3] = {c[0] + d[0], c[1] + d[1], c[2] + d[2]};
+                float t = A[id * S + o] * x[node_id(dim, n, cn)];
+                s = s - t;
+            }
+            x[id] = s / A[id * S + ctr];
+        }
+    }
+}
+
+static void restrict32(int dim, int nf, const float* pw, const float* r, float* bc) {
+    int ns = 1 << dim, nc = (nf + 1) / 2;
+    long nn = pw_int(nf, dim), ncn = pw_int(nc, dim);
+    for (long k = 0; k < ncn; k++) bc[k] = 0.0f;
+    for (long i = 0; i < nn; i++) {
+        int ci[3];
+        node_coords(dim, nf, i, ci);
+        if (!is_interior(dim, nf, ci)) continue;
+        for (int s = 0; s < ns; s++) {
+            float w = pw[i * ns + s];
+            if (w == 0.0f) continue;
+            int K[3] = {(ci[0] >> 1) + (s & 1), (ci[1] >> 1) + ((s >> 1) & 1), (ci[2] >> 1) + ((s >> 2) & 1)};
+            long k = node_id(dim, nc, K);
+            float t = w * r[i];
+            bc[k] = bc[k] + t;
+        }
+    }
+}
+
+static void prolong32(int dim, int nf, const float* pw, const float* xc, float* x) {
+    int ns = 1 << dim, nc = (nf + 1) / 2;
+    long nn = pw_int(nf, dim);
+    for (long i = 0; i < nn; i++) {
+        int ci[3];
+        node_coords(dim, nf, i, ci);
+        if (!is_interior(dim, nf, ci)) continue;
+        float s = 0.0f;
+        for (int sl = 0; sl < ns; sl++) {
+            float w = pw[i * ns + sl];
+            if (w == 0.0f) continue;
+            int K[3] = {(ci[0] >> 1) + (sl & 1), (ci[1] >> 1) + ((sl >> 1) & 1), (ci[2] >> 1) + ((sl >> 2) & 1)};
+            float t = w * xc[node_id(dim, nc, K)];
+            s = s + t;
+        }
+        x[i] = x[i] + s;
+    }
+}
+
+/* float copies of every level, rounded once from the FP64 hierarchy */
+static void make32(or_hier* h) {
+    if (h->A32[0]) return;
+    int dim = h->dim, S = (int)pw_int(3, dim), ns = 1 << dim;
+    for (int l = 0; l < h->nlev; l++) {
+        long nn = pw_int(h->n[l], dim);
+        h->A32[l] = (float*)malloc(sizeof(float) * nn * S);
+        for (long k = 0; k < nn * S; k++) h->A32[l][k] = (float)h->A[l][k];
+        if (l < h->nlev - 1) {
+            h->P32[l] = (float*)malloc(sizeof(float) * nn * ns);
+            for (long k = 0; k < nn * ns; k++) h->P32[l][k] = (float)h->P[l][k];
+        }
+        h->b32[l] = (float*)calloc(nn, sizeof(float));
+        h->x32[l] = (float*)calloc(nn, sizeof(float));
+        h->r32[l] = (float*)calloc(nn, sizeof(float));
+    }
+}
+
+static void vcycle32_level(or_hier* h, int l) {
+    int dim = h->dim, n = h->n[l], S = (int)pw_int(3, dim), ctr = (S - 1) / 2;
+    long nn = pw_int(n, dim);
+    for (long i = 0; i < nn; i++) h->x32[l][i] = 0.0f;
+    if (l == h->nlev - 1) {
+        int c[3] = {1, 1, 1};
+        long id = node_id(dim, n, c);
+        h->x32[l][id] = (float)((double)h->b32[l][id] / h->A[l][id * S + ctr]);
+        return;
+    }
+    smooth32(dim, n, h->A32[l], h->b32[l], h->x32[l], 0);
+    apply32(dim, n, h->A32[l], h->x32[l], h->r32[l]);
+    for (long i = 0; i < nn; i++) h->r32[l][i] = h->b32[l][i] - h->r32[l][i];
+    restrict32(dim, n, h->P32[l], h->r32[l], h->b32[l + 1]);
+    vcycle32_level(h, l + 1);
+    prolong32(dim, n, h->P32[l], h->x32[l + 1], h->x32[l]);
+    smooth32(dim, n, h->A32[l], h->b32[l], h->x32[l], 1);
+}
+
+/* z = M32 r: one FP32 V(1,1)-cycle from a zero initial guess; r is rounded
+   to float on entry and the result widened to double. */
+void or_vcycle32(or_hier* h, const double* r, double* z) {
+    make32(h);
+    int dim = h->dim, n = h->n[0];
+    long nn = pw_int(n, dim);
+    for (long i = 0; i < nn; i++) {
+        int c[3];
+        node_coords(dim, n, i, c);
+        h->b32[0][i] = is_interior(dim, n, c) ? (float)r[i] : 0.0f;
+    }
+    vcycle32_level(h, 0);
+    for (long i = 0; i < nn; i++) z[i] = (double)h->x32[0][i];
+}
+
 /* Preconditioned conjugate gradients with M = one V-cycle.
-   flexible = 0: beta = r_{k+1}.z_{k+1} / r_k.z_k;
-   flexible = 1: beta = r_{k+1}.(z_{k+1} - z_k) / r_k.z_k.
+   mode bit 0 clear: beta = r_{k+1}.z_{k+1} / r_k.z_k;
+   mode bit 0 set (flexible): beta = r_{k+1}.(z_{k+1} - z_k) / r_k.z_k;
+   mode bit 1 set: M is the FP32 V-cycle (or_vcycle32), every vector, dot
+   product and update of the CG itself staying FP64.
    Stops when ||r_k|| <= tol ||b|| for the recursive residual AND the true
    residual b - A x; when only the recursive one passes, r is replaced by
    the true residual and the iteration continues.  maxit caps the
    iterations; tol <= 0 runs exactly maxit iterations.
    hist[k] = ||r_k|| / ||b|| (recursive), k = 0..iters.  */
-int or_pcg(or_hier* h, const double* b, double* x, double tol, int maxit, int flexible,
+int or_pcg(or_hier* h, const double* b, double* x, double tol, int maxit, int mode,
            int* iters, double* hist, double* true_relres) {
     int dim = h->dim, n = h->n[0];
+    int flexible = mode & 1;
+    void (*precond)(or_hier*, const double*, double*) = (mode & 2) ? or_vcycle32 : or_vcycle;
     long nn = pw_int(n, dim);
     double* r = (double*)calloc(nn, sizeof(double));
     double* z = (double*)calloc(nn, sizeof(double));
@@ -860,7 +1019,7 @@ int or_pcg(or_hier* h, const double* b, double* x, double tol, int maxit, int fl
     if (hist) hist[0] = bnorm > 0 ? rn / bnorm : 0.0;
     if (bnorm == 0.0) { st = OR_OK; goto done; }
     if (tol > 0 && rn <= tol * bnorm) { st = OR_OK; goto done; }
-    or_vcycle(h, r, z);
+    precond(h, r, z);
     for (long i = 0; i < nn; i++) p[i] = z[i];
     double rz = dot(nn, r, z);
     for (k = 1; k <= maxit; k++) {
@@ -879,7 +1038,7 @@ int or_pcg(or_hier* h, const double* b, double* x, double tol, int maxit, int fl
         }
         if (k == maxit) break;
         if (flexible) memcpy(zo, z, sizeof(double) * nn);
-        or_vcycle(h, r, z);
+        precond(h, r, z);
         double rzn = dot(nn, r, z);
         double beta = flexible ? (rzn - dot(nn, r, zo)) / rz : rzn / rz;
         for (long i = 0; i < nn; i++) p[i] = z[i] + beta * p[i];

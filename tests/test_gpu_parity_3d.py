@@ -8,7 +8,7 @@ import torch
 
 import oracle
 from paper_2509_08109_gb300 import binding, inputs
-from tests.gpu_util import rel_to_diag, relerr, solver_for
+from tests.gpu_util import check_fp32_vcycle, rel_to_diag, relerr, solver_for
 
 pytestmark = pytest.mark.gpu
 
@@ -80,6 +80,8 @@ def test_vcycle_3d_matches_oracle(n, kind):
     r = inputs.rhs_uniform(np.random.default_rng(3), (n, n, n))
     z = s.vcycle(torch.as_tensor(r, device="cuda")).cpu().numpy()
     assert relerr(z, H.vcycle(r)) <= 1e-12
+    z32 = solver_for(p, precision="fp32").vcycle(torch.as_tensor(r, device="cuda")).cpu().numpy()
+    check_fp32_vcycle(z32, H, r, 3)
 
 
 @pytest.mark.parametrize("n,iters", [(9, 4), (17, 6)])
@@ -106,6 +108,9 @@ def test_pcg_3d_free_running(precision, outer):
     if precision == "fp64":
         xo10, it10, _, _, _ = H.pcg(p.rhs, tol=1e-10, maxit=500)
         assert abs(info.iterations - it10) <= 1
+    elif outer == "flexible":
+        _, it32, _, _, st32 = H.pcg(p.rhs, tol=1e-10, maxit=500, flexible=True, fp32=True)
+        assert st32 == 0 and abs(info.iterations - it32) <= 1
 
 
 def test_collapse_fallback_matches_oracle():

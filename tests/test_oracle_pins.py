@@ -282,6 +282,133 @@ def test_collapse_fallback_keeps_interpolation_defined():
     assert P[2, 1, 0] == 0.0          # the coarse node (0, 1) is a boundary node
 
 
+def _plane_equation(A, uf, ijk, even_axis, fallback):
+    """Residual of the collapsed plane equation at fine point ijk (i, j, k):
+    sum over in-plane offsets o of coef[o] u(ijk + o), coef[o] the stencil
+    summed over the offsets along even_axis (or, for the fallback, the
+    in-plane entries alone).  Returns (residual, scale)."""
+    dim = 3
+    coef = {}
+    for o in range(27):
+        off = [(o % 3) - 1, (o // 3) % 3 - 1, o // 9 - 1]
+        if fallback and off[even_axis] != 0:
+            continue
+        key = list(off)
+        key[even_axis] = 0
+        key = tuple(key)
+        coef[key] = coef.get(key, 0.0) + A[tuple(ijk[::-1]) + (o,)]
+    res, scale = 0.0, 0.0
+    for off, c in coef.items():
+        q = np.array(ijk) + np.array(off)
+        val = uf[tuple(q[::-1])]
+        res += c * val
+        scale += abs(c) * abs(val)
+    del dim
+    return res, scale
+
+
+def _collapsed_plane_diag(A, ijk, even_axis):
+    s = 0.0
+    for o in range(27):
+        off = [(o % 3) - 1, (o // 3) % 3 - 1, o // 9 - 1]
+        if all(off[a] == 0 for a in range(3) if a != even_axis):
+            s += A[tuple(ijk[::-1]) + (o,)]
+    return s
+
+
+@pytest.mark.parametrize("n,sigma", [(9, 1.0), (17, 0.7)])
+def test_interpolation_plane_points_3d(n, sigma):
+    """Operator-induced interpolation in 3-D (Sec. 2.2 with the hierarchical
+    collapse): at fine points with exactly two odd coordinates the
+    interpolated value satisfies the fine equation collapsed onto the point's
+    plane, i.e. summed over the one even axis, with the interpolated values
+    of its in-plane neighbours.  Where that collapsed diagonal is not positive
+    the point uses its own in-plane couplings (the fallback).  Checked on
+    every level of a shell-octant hierarchy with a rough coefficient (at
+    17^3 the input of the GPU fallback-parity test), where
+    the three axes carry very different couplings, so summing over the wrong
+    axis (or using the wrong neighbour set) fails; the test also confirms it
+    would."""
+    coords = inputs.coords_shell_octant(n)
+    kappa = np.exp(np.random.default_rng(n).normal(0, sigma, size=(n - 1,) * 3))
+    H = oracle.Hierarchy(oracle.assemble(coords, kappa))
+    rng = np.random.default_rng(40 + n)
+    checked = {False: 0, True: 0}
+    wrong_axis_fails = 0
+    for l in range(H.nlev - 1):
+        A, P, nl = H.A(l), H.P(l), H.level_n(l)
+        Pd = oracle.dense_interp(P)
+        m = oracle.interior_mask(nl, 3)
+        for _ in range(2):
+            uf = np.zeros((nl,) * 3)
+            uf[m] = Pd @ rng.normal(size=Pd.shape[1])
+            for k in range(1, nl - 1):
+                for j in range(1, nl - 1):
+                    for i in range(1, nl - 1):
+                        ijk = (i, j, k)
+                        odd = [c & 1 for c in ijk]
+                        if sum(odd) != 2:
+                            continue
+                        e = odd.index(0)
+                        fallback = not (_collapsed_plane_diag(A, ijk, e) > 0)
+                        res, scale = _plane_equation(A, uf, ijk, e, fallback)
+                        assert abs(res) <= 1e-12 * scale + 1e-300, (l, ijk, res, scale)
+                        checked[fallback] += 1
+                        for wrong in range(3):
+                            if wrong == e:
+                                continue
+                            wres, wscale = _plane_equation(A, uf, ijk, wrong, False)
+                            if abs(wres) > 1e-6 * wscale:
+                                wrong_axis_fails += 1
+    assert checked[False] > 0
+    assert wrong_axis_fails > 0.9 * 2 * (checked[False] + checked[True])
+    if n == 17:
+        assert checked[True] > 0      # the fallback occurs on this hierarchy (R4)
+
+
+def test_plane_point_fallback_hand_built_3d():
+    """A 3-D plane point whose plane-collapsed diagonal is not positive uses
+    its own in-plane couplings.  Hand-built operator on 5^3 nodes with the
+    same row everywhere: diagonal 3, couplings -2 along z, -1/2 to the four
+    in-plane edge neighbours, -1/10 to the in-plane corners and -1/100 to
+    the rest (collapsing over z gives 3 - 4 - ... < 0; collapsing a line
+    point onto its axis is negative too).  Worked by hand:
+      line point (2,1,2) (odd y): fallback weight -a(0,+1,0)/a00 = 1/6 to
+        coarse (1,1,1); likewise (1,2,2);
+      plane point (1,1,2) (even z): in-plane neighbours (2,1,2), (1,2,2)
+        (weight 1/6 each) and the coarse point (2,2,2) (weight 1), so its
+        weight to coarse (1,1,1) is (1/2 * 1/6 + 1/2 * 1/6 + 1/10 * 1) / 3
+        = 4/45."""
+    n = 5
+    row = np.zeros(27)
+    for o in range(27):
+        dx, dy, dz = (o % 3) - 1, (o // 3) % 3 - 1, o // 9 - 1
+        if (dx, dy, dz) == (0, 0, 0):
+            row[o] = 3.0
+        elif dx == 0 and dy == 0:
+            row[o] = -2.0
+        elif dz == 0 and abs(dx) + abs(dy) == 1:
+            row[o] = -0.5
+        elif dz == 0:
+            row[o] = -0.1
+        else:
+            row[o] = -0.01
+    A = np.zeros((n, n, n, 27))
+    for k in range(1, n - 1):
+        for j in range(1, n - 1):
+            for i in range(1, n - 1):
+                for o in range(27):
+                    dx, dy, dz = (o % 3) - 1, (o // 3) % 3 - 1, o // 9 - 1
+                    if 1 <= i + dx <= n - 2 and 1 <= j + dy <= n - 2 and 1 <= k + dz <= n - 2:
+                        A[k, j, i, o] = row[o]
+    P = oracle.interp(A)
+    # slot s = sx + 2 sy + 4 sz of coarse node (i>>1 + sx, j>>1 + sy, k>>1 + sz)
+    assert abs(P[2, 1, 2, 2] - 1.0 / 6.0) < 1e-15     # (2,1,2) -> (1,1,1): sx=0, sy=1, sz=0
+    assert abs(P[2, 2, 1, 1] - 1.0 / 6.0) < 1e-15     # (1,2,2) -> (1,1,1): sx=1
+    assert abs(P[2, 1, 1, 3] - 4.0 / 45.0) < 1e-15    # (1,1,2) -> (1,1,1): sx=sy=1
+    assert np.count_nonzero(P[2, 1, 1]) == 1           # its other coarse nodes are boundary nodes
+
+
 # ------------------------------------------------------------------ P6
 @pytest.mark.parametrize("dim,n", [(2, 9), (2, 17), (3, 9)])
 def test_rap_equals_dense_triple_product(dim, n):
@@ -414,6 +541,84 @@ def test_pcg_matches_brute_force_solve(dim, n, flexible):
     xs = np.linalg.solve(oracle.dense_operator(A), b[m])
     assert np.abs(x[m] - xs).max() / np.abs(xs).max() < 1e-12
     assert np.all(np.diff(hist[:3]) < 0)
+
+
+# ------------------------------------------------------------------ O7: the FP32 arm
+_U32 = 2.0 ** -24      # unit roundoff of float (round to nearest)
+
+
+def _gamma(m):
+    return m * _U32 / (1 - m * _U32)
+
+
+@pytest.mark.parametrize("dim,n", [(2, 9), (2, 17), (3, 9)])
+def test_fp32_vcycle_is_the_vcycle_to_float_rounding(dim, n):
+    """The FP32 arm evaluates the V-cycle (pinned above to its dense
+    error-propagation form) with float data and float arithmetic.  By the
+    standard backward-error argument each of its sums of at most m = 3^d
+    terms followed by a division is the exact operation on coefficients
+    perturbed by at most gamma_m = m u / (1 - m u) (u = 2^-24), and rounding
+    A and P to float perturbs them by u.  A per-level relative
+    perturbation of gamma_{m+1} with unit amplification through the L levels
+    bounds the deviation by L gamma_{m+1} max|z|; the arm must stay inside
+    that bound against the dense form, and above FP64 rounding (it really
+    computes in float)."""
+    rng = np.random.default_rng(19)
+    coords = inputs.coords_quarter_annulus(n) if dim == 2 else inputs.coords_shell_octant(n)
+    A = oracle.assemble(coords, np.exp(rng.normal(0, 0.5, size=(n - 1,) * dim)))
+    H = oracle.Hierarchy(A)
+    M = _dense_vcycle_matrix(H, 0)
+    m = oracle.interior_mask(n, dim)
+    bound = H.nlev * _gamma(3 ** dim + 1)
+    for _ in range(3):
+        r = inputs.zero_boundary(rng.normal(size=(n,) * dim))
+        z = H.vcycle32(r)
+        want = M @ r[m]
+        dev = np.abs(z[m] - want).max() / np.abs(want).max()
+        assert 1e-9 < dev <= bound, (dev, bound)
+        assert np.all(z[~m] == 0.0)
+
+
+@pytest.mark.parametrize("dim,n", [(2, 65), (2, 257), (3, 17)])
+def test_fp32_vcycle_rounding_bound_at_larger_sizes(dim, n):
+    """Same bound against the FP64 arm on the configurations' maps with
+    their coefficients (log-normal field; two-layer shell)."""
+    p = inputs.annulus_lognormal(n) if dim == 2 else inputs.shell_two_layer(n)
+    H = oracle.Hierarchy(oracle.assemble(p.coords, p.kappa))
+    r = inputs.rhs_uniform(np.random.default_rng(3), (n,) * dim)
+    z64, z32 = H.vcycle(r), H.vcycle32(r)
+    dev = np.abs(z32 - z64).max() / np.abs(z64).max()
+    assert 1e-9 < dev <= H.nlev * _gamma(3 ** dim + 1), dev
+
+
+@pytest.mark.parametrize("dim,n", [(2, 9), (3, 9)])
+def test_fp32_flexible_pcg_matches_brute_force_solve(dim, n):
+    """Flexible CG (beta = r_{k+1}.(z_{k+1} - z_k) / r_k.z_k) tolerates a
+    preconditioner that is not exactly symmetric or fixed: with the FP32
+    V-cycle it still reaches an FP64 residual of 1e-14 and the dense solve's
+    solution."""
+    rng = np.random.default_rng(31)
+    coords = inputs.coords_quarter_annulus(n) if dim == 2 else inputs.coords_shell_octant(n)
+    A = oracle.assemble(coords, np.exp(rng.normal(0, 0.5, size=(n - 1,) * dim)))
+    b = inputs.rhs_uniform(rng, (n,) * dim)
+    H = oracle.Hierarchy(A)
+    x, it, hist, trr, st = H.pcg(b, tol=1e-14, maxit=200, flexible=True, fp32=True)
+    assert st == 0 and trr <= 1e-14
+    m = oracle.interior_mask(n, dim)
+    xs = np.linalg.solve(oracle.dense_operator(A), b[m])
+    assert np.abs(x[m] - xs).max() / np.abs(xs).max() < 1e-12
+
+
+@pytest.mark.parametrize("dim,n", [(2, 65), (3, 17)])
+def test_fp32_flexible_pcg_iterations_match_fp64(dim, n):
+    """A preconditioner perturbed at the level of float rounding leaves the
+    flexible-CG iteration count to 1e-10 unchanged (within one)."""
+    p = inputs.annulus_lognormal(n) if dim == 2 else inputs.shell_two_layer(n)
+    H = oracle.Hierarchy(oracle.assemble(p.coords, p.kappa))
+    _, it32, _, trr32, st32 = H.pcg(p.rhs, tol=1e-10, maxit=500, flexible=True, fp32=True)
+    _, it64, _, trr64, st64 = H.pcg(p.rhs, tol=1e-10, maxit=500, flexible=True)
+    assert st32 == 0 and st64 == 0 and trr32 <= 1e-10
+    assert abs(it32 - it64) <= 1
 
 
 def test_pcg_zero_rhs_and_fixed_iterations():
