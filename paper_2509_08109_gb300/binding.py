@@ -145,9 +145,22 @@ def assemble_noalloc(dim: int, n: int, coords: torch.Tensor, kappa: torch.Tensor
     """bmg_assemble_noalloc: the finest operator as full 3^dim-entry rows,
     written into `out` (device, n^dim x 3^dim doubles), without a context or
     any allocation in the library.  All tensors must already be on the
-    current CUDA device; nothing is copied or allocated here either."""
+    current CUDA device; nothing is copied or allocated here either.
+    The C entry point takes no lengths, so the sizes are checked here:
+    coords dim * n^dim, kappa (n-1)^dim and out n^dim * 3^dim doubles
+    (ValueError otherwise, before any device work)."""
+    dim, n = int(dim), int(n)
+    if dim in (2, 3) and n >= 3:
+        for name, t, want in (("coords", coords, dim * n ** dim), ("kappa", kappa, (n - 1) ** dim),
+                              ("out", out, n ** dim * 3 ** dim)):
+            if t.numel() != want:
+                raise ValueError(f"bmg_assemble_noalloc: {name} has {t.numel()} elements, "
+                                 f"dim {dim}, n {n} needs {want}")
     for t in (coords, kappa, out):
-        assert t.is_cuda and t.dtype == torch.float64 and t.is_contiguous()
+        if not (t.dtype == torch.float64 and t.is_contiguous()):
+            raise ValueError("bmg_assemble_noalloc: tensors must be contiguous float64")
+        if not (t.is_cuda and t.device.index == torch.cuda.current_device()):
+            raise ValueError("bmg_assemble_noalloc: tensors must be on the current CUDA device")
     s = stream if stream is not None else torch.cuda.current_stream()
     code = load().bmg_assemble_noalloc(int(dim), int(n), _ptr(coords), _ptr(kappa), _ptr(out),
                                        ctypes.c_void_p(s.cuda_stream))

@@ -26,13 +26,28 @@ constexpr int kMaxDevices = 64;
 std::mutex g_mu;
 void* g_addr[kMaxDevices] = {};
 
-bool on_device(const void* p) {
+// True for device (or managed) memory of the calling thread's current
+// device; a pointer into another GPU's memory is refused rather than
+// dereferenced as a peer access.
+bool on_device(const void* p, int dev) {
     cudaPointerAttributes a;
     if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
         cudaGetLastError();
         return false;
     }
-    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+    if (a.type == cudaMemoryTypeDevice) return a.device == dev;
+    return a.type == cudaMemoryTypeManaged;
+}
+
+// Whether the half-plane operator of an n-node grid (2-D: 5 planes of ld*n
+// doubles; 3-D: 14 planes of ld*n*n) and the error word fit the static
+// array.  n is bounded first, so none of the products can overflow.
+bool fits_scratch(int dim, int n) {
+    if (n < 3 || n > 4096) return false;
+    const unsigned long long ld = ((unsigned long long)n + 31) & ~31ull;
+    const unsigned long long pl = dim == 2 ? ld * n : ld * n * (unsigned long long)n;
+    const unsigned long long planes = dim == 2 ? bmg::NS2 : bmg::NS3;
+    return kStateBytes + planes * pl * sizeof(double) <= (unsigned long long)BMG_NOALLOC_SCRATCH_BYTES;
 }
 
 // Address of the static array on the current device, resolved once per device.
@@ -54,14 +69,13 @@ bmg_status scratch_address(void** out) {
 extern "C" bmg_status bmg_assemble_noalloc(int dim, int n, const double* coords, const double* kappa,
                                            double* stencil, void* stream) {
     if (dim != 2 && dim != 3) return BMG_ERR_SHAPE;
-    if (n < 3) return BMG_ERR_SHAPE;
+    if (!fits_scratch(dim, n)) return BMG_ERR_SHAPE;   // checked on n before any size arithmetic
     const long long ld = (n + 31) & ~31;
     const long long pl = dim == 2 ? ld * n : ld * n * (long long)n;
-    const long long planes = dim == 2 ? bmg::NS2 : bmg::NS3;
-    const unsigned long long need = kStateBytes + (unsigned long long)(planes * pl) * sizeof(double);
-    if (need > (unsigned long long)BMG_NOALLOC_SCRATCH_BYTES) return BMG_ERR_SHAPE;
     if (!coords || !kappa || !stencil) return BMG_ERR_ARG;
-    if (!on_device(coords) || !on_device(kappa) || !on_device(stencil)) return BMG_ERR_ARG;
+    int dev = -1;
+    if (cudaGetDevice(&dev) != cudaSuccess) return BMG_ERR_DEVICE;
+    if (!on_device(coords, dev) || !on_device(kappa, dev) || !on_device(stencil, dev)) return BMG_ERR_ARG;
     void* base = nullptr;
     BMG_TRY(scratch_address(&base));
     bmg::KState* st = (bmg::KState*)base;
@@ -71,6 +85,9 @@ extern "C" bmg_status bmg_assemble_noalloc(int dim, int n, const double* coords,
     BMG_CUDA(cudaMemsetAsync(st, 0, sizeof(bmg::KState), s));
     BMG_TRY(dim == 2 ? bmg::assemble_export2d(n, (int)ld, pl, coords, kappa, A, st, stencil, s)
                      : bmg::assemble_export3d(n, (int)ld, pl, coords, kappa, A, st, stencil, s));
+    // `err` is pageable stack memory: the asynchronous copy into it is only
+    // complete, and `err` only safe to read or leave, after the stream
+    // synchronisation that follows.  Keep the two together.
     int err = 0;
     BMG_CUDA(cudaMemcpyAsync(&err, &st->err, sizeof(int), cudaMemcpyDeviceToHost, s));
     BMG_CUDA(cudaStreamSynchronize(s));

@@ -6,6 +6,7 @@ import os
 import re
 
 import pytest
+import torch
 
 from paper_2509_08109_gb300 import binding, build
 
@@ -84,11 +85,34 @@ def test_calls_before_attach_are_rejected(lib):
     lib.bmg_destroy(h)
 
 
-@pytest.mark.parametrize("dim,n,code", [(2, 641, 2), (3, 49, 2), (4, 9, 2), (2, 2, 2), (2, 640, 1), (3, 48, 1)])
+@pytest.mark.parametrize("dim,n,code", [(2, 641, 2), (3, 49, 2), (4, 9, 2), (2, 2, 2), (2, 640, 1), (3, 48, 1),
+                                        (3, 1 << 22, 2), (2, 1 << 22, 2), (2, 2 ** 31 - 1, 2),
+                                        (3, 2 ** 31 - 1, 2), (2, -5, 2)])
 def test_noalloc_validates_before_device_work(lib, dim, n, code):
     """Shape and null-pointer checks of bmg_assemble_noalloc come before any
-    CUDA call, so they answer without a device."""
+    CUDA call, so they answer without a device; n is bounded before any size
+    arithmetic, so huge n cannot wrap into an accepted size."""
     assert lib.bmg_assemble_noalloc(dim, n, None, None, None, None) == code
+
+
+@pytest.mark.parametrize("which", ["coords", "kappa", "out"])
+def test_noalloc_binding_rejects_wrong_sizes_on_the_host(which):
+    """The C entry point takes no lengths, so the binding checks every
+    buffer's size before the call (an undersized output would otherwise be
+    written past its end on the device)."""
+    n = 17
+    sizes = {"coords": 2 * n * n, "kappa": (n - 1) ** 2, "out": n * n * 9}
+    sizes[which] -= 1
+    t = {k: torch.zeros(v, dtype=torch.float64) for k, v in sizes.items()}
+    with pytest.raises(ValueError, match=which):
+        binding.assemble_noalloc(2, n, t["coords"], t["kappa"], t["out"])
+
+
+def test_noalloc_binding_rejects_host_tensors():
+    n = 17
+    t = [torch.zeros(k, dtype=torch.float64) for k in (2 * n * n, (n - 1) ** 2, n * n * 9)]
+    with pytest.raises(ValueError, match="current CUDA device"):
+        binding.assemble_noalloc(2, n, *t)
 
 
 def test_aux_defaults_and_null_arguments(lib):

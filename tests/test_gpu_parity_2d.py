@@ -204,8 +204,12 @@ def test_both_vcycle_paths_match_oracle(n, unfused):
 @pytest.mark.parametrize("n", [2049])
 def test_fused_matches_unfused_large(n):
     """64-column tiles (the benchmark's shape) against the per-colour path
-    and the oracle: FP64 to 1e-12, FP32 element by element against the
-    oracle's FP32 arm."""
+    and the oracle.  FP64: rounding in a residual b - A x is relative
+    eps |A| |x|, and the cycle's coarse correction carries it with up to
+    |A^-1|, so the first-order bound is eps cond(A), cond(A) ~ h^-2 =
+    (n-1)^2 for the Q1 operator (the oracle's own V-cycle moves by 6e-12 to
+    2.4e-11 at 2049^2 when its operator is perturbed by one ulp; the bound
+    is 9e-10).  FP32: element by element against the oracle's FP32 arm."""
     p = inputs.annulus_lognormal(n)
     fu = solver_for(p)
     un = solver_for(p, unfused=True)
@@ -215,7 +219,7 @@ def test_fused_matches_unfused_large(n):
     zb = un.vcycle(r)
     assert float((za - zb).norm() / zb.norm()) <= 1e-13
     H = oracle.Hierarchy(oracle.assemble(p.coords, p.kappa))
-    assert relerr(za.cpu().numpy(), H.vcycle(rh)) <= 1e-12
+    assert relerr(za.cpu().numpy(), H.vcycle(rh)) <= np.finfo(float).eps * (n - 1) ** 2
     for unfused in (False, True):
         z32 = solver_for(p, precision="fp32", unfused=unfused).vcycle(r).cpu().numpy()
         check_fp32_vcycle(z32, H, rh, 2)

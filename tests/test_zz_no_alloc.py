@@ -52,11 +52,37 @@ def test_largest_accepted_size_matches_oracle():
 
 @pytest.mark.parametrize("dim,n", [(2, 641), (3, 49)])
 def test_beyond_the_static_array_is_rejected(dim, n):
-    x = torch.zeros(8, dtype=torch.float64, device="cuda")
+    """Correctly sized buffers, one node per side beyond what the static
+    array holds: the library refuses the size itself."""
+    coords = torch.zeros(dim * n ** dim, dtype=torch.float64, device="cuda")
+    kappa = torch.ones((n - 1) ** dim, dtype=torch.float64, device="cuda")
+    out = torch.zeros(n ** dim * 3 ** dim, dtype=torch.float64, device="cuda")
     with pytest.raises(binding.BmgError) as e:
-        binding.assemble_noalloc(dim, n, x, x, x)
+        binding.assemble_noalloc(dim, n, coords, kappa, out)
     assert e.value.code == 2
     assert "static scratch" in str(e.value)
+
+
+def test_warm_call_allocates_no_device_memory():
+    """After a first call (which may load the library's module and with it
+    the static array), further calls change neither the device's free
+    memory nor torch's allocator state."""
+    n = 257
+    p = inputs.annulus_lognormal(n)
+    coords = torch.as_tensor(p.coords, device="cuda").contiguous()
+    kappa = torch.as_tensor(p.kappa, device="cuda").contiguous()
+    out = torch.empty((n, n, 9), dtype=torch.float64, device="cuda")
+    binding.assemble_noalloc(2, n, coords, kappa, out)
+    torch.cuda.synchronize()
+    free0, _ = torch.cuda.mem_get_info()
+    alloc0 = torch.cuda.memory_allocated()
+    reserved0 = torch.cuda.memory_reserved()
+    for _ in range(3):
+        binding.assemble_noalloc(2, n, coords, kappa, out)
+    torch.cuda.synchronize()
+    free1, _ = torch.cuda.mem_get_info()
+    assert free1 == free0
+    assert torch.cuda.memory_allocated() == alloc0 and torch.cuda.memory_reserved() == reserved0
 
 
 def test_folded_map_then_valid_map():
