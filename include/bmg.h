@@ -191,6 +191,76 @@ bmg_status bmg_solve(bmg_ctx* ctx, const double* b, double* x, double tol, int m
 bmg_status bmg_solve_many(bmg_ctx* const* ctxs, int count, int nrhs, const double* const* b, double* const* x,
                           double tol, int maxit, bmg_info* infos);
 
+/* ---------------------------------------------------------------------
+   Batched solve: many independent problems, up to 4 right-hand sides each,
+   with one stencil read per sweep for all right-hand sides of a problem
+   (the problem-and-right-hand-side batching of the solution phase of
+   Sec. 2.2, step 3, applied to every problem of a set).
+
+   Every context must be a 2-D context with precision BMG_PREC_FP32, outer
+   BMG_OUTER_REFINEMENT, the streaming kernels (no BMG_FLAG_UNFUSED), n >= 65,
+   attached on one device and set up (bmg_setup); the batch keeps pointers
+   into their hierarchies, so they must outlive it and must not be set up
+   again.  Each solve runs, for all problems and right-hand sides together
+   (lockstep), the refinement mode of bmg_solve: FP64 residual, inner FP32
+   flexible CG preconditioned by one FP32 V(1,1)-cycle per right-hand side,
+   updates into the FP64 iterate, until every system's FP64 residual meets
+   tol.  The V-cycle runs per size class: the levels of all problems with
+   the same n are stored together (copied from the contexts at attach) and
+   processed by one persistent launch that walks the class's work-list of
+   (problem, level, tile) items; the levels n <= 33 of every problem run in
+   one launch, one CTA per problem.  One inner iteration of the whole batch
+   is one CUDA graph (unless flags has BMG_FLAG_NO_GRAPHS).  Converged
+   systems stop updating; the slowest one sets the number of inner
+   iterations between refinements.  Right-hand sides of a problem are
+   interleaved in the batch's own storage (the caller's arrays keep their
+   n x n layout). */
+typedef struct bmg_batch bmg_batch;   /* opaque */
+
+/* Creates a batch over count set-up contexts (host memory only).
+   Errors: BMG_ERR_ARG (a context not eligible, see above, or on another
+   device), BMG_ERR_STATE (a context not set up). */
+bmg_status bmg_batch_create(int count, bmg_ctx* const* ctxs, int flags, bmg_batch** batch);
+
+/* Device workspace the batch needs (256-byte aligned base). */
+bmg_status bmg_batch_workspace_bytes(const bmg_batch* batch, size_t* bytes);
+
+/* Attaches the workspace and the stream the batch's work is ordered on,
+   copies the FP32 levels of every context into the size-class storage and
+   chooses tile shapes from the kernels' occupancy.  The device must be the
+   contexts' and current.  Errors: BMG_ERR_WORKSPACE, BMG_ERR_ARG,
+   BMG_ERR_DEVICE. */
+bmg_status bmg_batch_attach(bmg_batch* batch, void* workspace, size_t bytes, void* stream);
+
+/* Solves problem p's nrhs (1..4) right-hand sides b[p*nrhs + r] with initial
+   guesses and solutions x[p*nrhs + r] (n_p x n_p doubles each, host or
+   device; boundary entries ignored on input and 0 on output) to a relative
+   FP64 residual of tol (> 0), at most maxit inner iterations per system.
+   infos: count*nrhs entries or NULL (iterations = inner iterations of that
+   system, true_relres = its final FP64 residual).  Returns the first
+   non-OK status (BMG_ERR_NOT_CONVERGED, BMG_ERR_NOT_SPD, BMG_ERR_TIMEOUT). */
+bmg_status bmg_batch_solve(bmg_batch* batch, int nrhs, const double* const* b, double* const* x, double tol,
+                           int maxit, bmg_info* infos);
+
+/* Size classes (the fused levels by decreasing n, then the tails' first
+   level, n = 33); tile shape of class cls: n, strip width wc (16 or 32
+   coarse columns), hc coarse rows per item, and its member count (the tail
+   class reports wc = hc = 0). */
+int bmg_batch_classes(const bmg_batch* batch);
+bmg_status bmg_batch_get_tiles(const bmg_batch* batch, int cls, int* n, int* wc, int* hc, int* members);
+bmg_status bmg_batch_set_tiles(bmg_batch* batch, int cls, int wc, int hc);
+
+/* Autotuner: times each class's down and up kernels over all its members
+   for every strip width and the modelled, half and twice the rows (best of
+   reps after a warm-up run) and keeps the fastest; *ms (may be NULL): the
+   sum of the chosen times. */
+bmg_status bmg_batch_autotune(bmg_batch* batch, int reps, double* ms);
+
+/* Kernel launches the batch has issued (graph replays count their kernels). */
+long long bmg_batch_launch_count(const bmg_batch* batch);
+
+void bmg_batch_destroy(bmg_batch* batch);
+
 /* Adjoint gradient with respect to the per-cell coefficient for a loss
    L(u) of the solution u = A^-1 b: solves A lambda = dL/du with the same
    hierarchy (A is symmetric) and evaluates, per cell e,

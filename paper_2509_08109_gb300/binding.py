@@ -109,6 +109,17 @@ def load() -> ctypes.CDLL:
         "bmg_aux_estimate_gamma": ([P, I, P, D, ctypes.POINTER(D), P, P, ctypes.POINTER(I)], I),
         "bmg_aux_export": ([P, I, ctypes.POINTER(I), ctypes.POINTER(ctypes.c_longlong), P, P, P], I),
         "bmg_aux_destroy": ([P], None),
+        "bmg_batch_create": ([I, P, I, ctypes.POINTER(P)], I),
+        "bmg_batch_workspace_bytes": ([P, ctypes.POINTER(ctypes.c_size_t)], I),
+        "bmg_batch_attach": ([P, P, ctypes.c_size_t, P], I),
+        "bmg_batch_solve": ([P, I, P, P, D, I, P], I),
+        "bmg_batch_classes": ([P], I),
+        "bmg_batch_get_tiles": ([P, I, ctypes.POINTER(I), ctypes.POINTER(I), ctypes.POINTER(I),
+                                 ctypes.POINTER(I)], I),
+        "bmg_batch_set_tiles": ([P, I, I, I], I),
+        "bmg_batch_autotune": ([P, I, ctypes.POINTER(D)], I),
+        "bmg_batch_launch_count": ([P], ctypes.c_longlong),
+        "bmg_batch_destroy": ([P], None),
     }
     for name, (args, res) in sigs.items():
         f = getattr(lib, name)
@@ -127,7 +138,9 @@ def exported_symbols() -> list:
             "bmg_profile_read", "bmg_destroy", "bmg_status_str", "bmg_assemble_noalloc", "bmg_assemble_tensor",
             "bmg_boundary_rhs", "bmg_aux_default_opts", "bmg_aux_create", "bmg_aux_workspace_bytes",
             "bmg_aux_setup", "bmg_aux_solve", "bmg_aux_set_gamma", "bmg_aux_estimate_gamma", "bmg_aux_export",
-            "bmg_aux_destroy"]
+            "bmg_aux_destroy", "bmg_batch_create", "bmg_batch_workspace_bytes", "bmg_batch_attach",
+            "bmg_batch_solve", "bmg_batch_classes", "bmg_batch_get_tiles", "bmg_batch_set_tiles",
+            "bmg_batch_autotune", "bmg_batch_launch_count", "bmg_batch_destroy"]
 
 
 def _check(code: int, where: str):
@@ -202,6 +215,94 @@ def solve_many(solvers, bs, xs, tol: float = 1e-10, maxit: int = 500):
     code = lib.bmg_solve_many(hs, count, nrhs, bp, xp, float(tol), int(maxit), infos)
     _check(code, "bmg_solve_many")
     return [[_info_of(infos[p * nrhs + r]) for r in range(nrhs)] for p in range(count)]
+
+
+class Batch:
+    """bmg_batch_*: many set-up problems (Solver objects with
+    precision='fp32', outer='refine', 2-D, n >= 65, one device) solved
+    together, up to four right-hand sides each.  The solvers must stay alive
+    and unchanged while the batch is used."""
+
+    def __init__(self, solvers, graphs: bool = True, stream: torch.cuda.Stream | None = None):
+        lib = load()
+        self.solvers = list(solvers)
+        count = len(self.solvers)
+        hs = (ctypes.c_void_p * count)(*[s._h.value for s in self.solvers])
+        h = ctypes.c_void_p()
+        _check(lib.bmg_batch_create(count, hs, 0 if graphs else 2, ctypes.byref(h)), "bmg_batch_create")
+        self._h = h
+        nbytes = ctypes.c_size_t()
+        _check(lib.bmg_batch_workspace_bytes(h, ctypes.byref(nbytes)), "bmg_batch_workspace_bytes")
+        self.workspace_bytes = nbytes.value
+        self.device = self.solvers[0].device
+        with torch.cuda.device(self.device):
+            self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
+            self._ws = torch.empty(self.workspace_bytes, dtype=torch.uint8, device=self.device)
+            _check(lib.bmg_batch_attach(h, ctypes.c_void_p(self._ws.data_ptr()),
+                                        ctypes.c_size_t(self.workspace_bytes),
+                                        ctypes.c_void_p(self.stream.cuda_stream)), "bmg_batch_attach")
+
+    def __del__(self):
+        if getattr(self, "_h", None) is not None and _lib is not None:
+            _lib.bmg_batch_destroy(self._h)
+            self._h = None
+
+    @property
+    def launches(self) -> int:
+        return load().bmg_batch_launch_count(self._h)
+
+    def tiles(self):
+        """[(n, wc, hc, members)] per size class."""
+        lib = load()
+        out = []
+        for c in range(lib.bmg_batch_classes(self._h)):
+            n, wc, hc, m = ctypes.c_int(), ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+            _check(lib.bmg_batch_get_tiles(self._h, c, ctypes.byref(n), ctypes.byref(wc), ctypes.byref(hc),
+                                           ctypes.byref(m)), "bmg_batch_get_tiles")
+            out.append((n.value, wc.value, hc.value, m.value))
+        return out
+
+    def set_tiles(self, cls: int, wc: int, hc: int):
+        with torch.cuda.device(self.device):
+            _check(load().bmg_batch_set_tiles(self._h, int(cls), int(wc), int(hc)), "bmg_batch_set_tiles")
+
+    def autotune(self, reps: int = 3) -> float:
+        ms = ctypes.c_double()
+        with torch.cuda.device(self.device):
+            _check(load().bmg_batch_autotune(self._h, int(reps), ctypes.byref(ms)), "bmg_batch_autotune")
+        return ms.value
+
+    def solve(self, bs, xs, tol: float = 1e-10, maxit: int = 500, raise_on_nonconv: bool = True):
+        """bs[p] / xs[p]: lists of nrhs tensors (n_p x n_p float64, host or
+        device) of problem p; xs hold the initial guesses and receive the
+        solutions.  Returns (per problem) lists of SolveInfo."""
+        lib = load()
+        count = len(self.solvers)
+        assert len(bs) == count and len(xs) == count
+        nrhs = len(bs[0])
+        bp = (ctypes.c_void_p * (count * nrhs))()
+        xp = (ctypes.c_void_p * (count * nrhs))()
+        keep = []
+        for p in range(count):
+            assert len(bs[p]) == nrhs and len(xs[p]) == nrhs
+            n = self.solvers[p].n
+            for r in range(nrhs):
+                b, x = bs[p][r], xs[p][r]
+                for t in (b, x):
+                    if not (t.dtype == torch.float64 and t.is_contiguous() and t.numel() == n * n):
+                        raise ValueError(f"problem {p}: right-hand sides and solutions must be contiguous "
+                                         f"float64 {n}x{n} tensors")
+                keep += [b, x]
+                bp[p * nrhs + r] = b.data_ptr()
+                xp[p * nrhs + r] = x.data_ptr()
+        infos = (_Info * (count * nrhs))()
+        with torch.cuda.device(self.device):
+            code = lib.bmg_batch_solve(self._h, nrhs, bp, xp, float(tol), int(maxit), infos)
+        res = [[_info_of(infos[p * nrhs + r]) for r in range(nrhs)] for p in range(count)]
+        if code == 8 and not raise_on_nonconv:
+            return res
+        _check(code, "bmg_batch_solve")
+        return res
 
 
 class Solver:

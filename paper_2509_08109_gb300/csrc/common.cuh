@@ -59,6 +59,23 @@ struct KState {
     unsigned int counter[8];
 };
 
+// CG scalars of one system (one right-hand side of one problem) in a
+// batched solve; mirrors the fields of KState that the batched kernels use.
+struct SysState {
+    double bb;        // ||b||^2
+    double rr;        // ||r||^2 of the last FP64 residual
+    double rz;        // r.z of the previous inner iteration
+    double pq;        // p.Ap
+    double alpha, beta;
+    int first;        // 1: the next inner iteration takes p = z
+    int active;       // 0: converged, zero right-hand side or out of iterations: no updates
+};
+
+// Right-hand sides per problem and row pairs per step of the batched
+// streaming kernels (FP32 V-cycle).
+constexpr int kBatchR = 4;
+constexpr int kBatchK = 2;
+
 struct Level {
     int n = 0;            // nodes per side
     int ld = 0;           // padded row length
@@ -292,6 +309,13 @@ bmg_status fused_occupancy(bool f32, bool f64in, int wc, int* down_blocks, int* 
 bmg_status fused_down(Ctx& c, int l, bool ir = false);
 bmg_status fused_up(Ctx& c, int l, void* out, bool ir = false, const float* zold = nullptr);
 bmg_status vcycle_f32(Ctx& c, float* z32, const float* zold = nullptr);
+// batched streaming kernels (fused2d.cu): FP32, kBatchR right-hand sides, strip width 16 or 32
+int batch_down_smem(int wc);
+int batch_up_smem(int wc);
+bmg_status batch_occupancy(int wc, int* down_blocks, int* up_blocks);
+bmg_status batch_down(const CUtensorMap& mA, const CUtensorMap& mF, const FusedArgs& a, int grid, cudaStream_t s);
+bmg_status batch_up(const CUtensorMap& mA, const CUtensorMap& mF, const CUtensorMap& mXp, const CUtensorMap& mXc,
+                    const FusedArgs& a, int grid, cudaStream_t s);
 // vcycle3d.cu: colour-blocked full rows of the FP32 levels (after demotion)
 bmg_status colour_blocks3d(Ctx& c);
 // interior nodes of colour col (parities col&1, col>>1&1, col>>2) on an n-grid,
@@ -308,7 +332,21 @@ __host__ __device__ inline long long cb_offset(int n, int col) {
 // tail2d.cu: the levels from the first one with n <= kTailMaxN (at least
 // level 1) down to the coarsest, in one single-CTA launch
 constexpr int kTailMaxN = 33;
+struct TailArgs {
+    int nlev;                     // levels in the tail (the last one has 3 nodes)
+    int ns[kMaxLevels];           // nodes per side of each tail level
+    const void* pack;             // packed operators and weights (shared-memory image)
+    unsigned pack_bytes;          // its size, a multiple of 16
+    const void* b0;               // right-hand side of the first tail level
+    void* x0;                     // finished iterate of the first tail level
+    int ld0;                      // row length of b0 and x0 (in nodes)
+    const double* a64c;           // FP64 centre entry of the coarsest operator
+    KState* st;
+};
 int tail_first_level(const Ctx& c);
+bmg_status tail_args(const Ctx& c, const void* b0, void* x0, int ld0, KState* st, TailArgs* a);
+size_t batch_tail_smem(const int* ns, int L);
+bmg_status batch_tail(const TailArgs* args, int count, size_t smem, cudaStream_t s);
 size_t tail_smem_bytes(const Ctx& c, int t);
 size_t tail_pack_bytes(const Ctx& c);             // packed tail operators (0 outside 2-D)
 bmg_status tail_pack(Ctx& c);                     // fills c.tail_pack (bmg_setup)

@@ -27,6 +27,17 @@
 // registers (each is used by one thread).  Every mbarrier wait is bounded
 // by the global timer; on expiry the CTA records BMG_ERR_TIMEOUT, drains its
 // outstanding copies (bounded) and returns.
+//
+// Several right-hand sides (NR > 1).  Vectors are interleaved, NR values per
+// node, and a thread handles one column pair of one right-hand side; the
+// stencil and interpolation values are shared by the NR threads of a
+// column, so they are read once per sweep for all right-hand sides.
+// Batched form (BATCH).  All (problem, level) members of one size class
+// keep their arrays in class-contiguous storage with one more tensor
+// dimension (the member); a persistent grid walks the class's work-list of
+// (member, tile) items, carrying its ring's mbarrier phases from item to
+// item.  Per-member output pointers and interpolation weights come from a
+// device table (BatchMember).
 #include <cuda.h>
 
 #include <type_traits>
@@ -56,6 +67,22 @@ __device__ __forceinline__ void tma3d(void* dst, const CUtensorMap* m, uint64_t*
         : "memory");
 }
 
+__device__ __forceinline__ void tma4d(void* dst, const CUtensorMap* m, uint64_t* bar, int x, int y, int z, int w) {
+    asm volatile(
+        "cp.async.bulk.tensor.4d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4, %5}], "
+        "[%6];" ::"r"(smem_u32(dst)),
+        "l"((unsigned long long)m), "r"(x), "r"(y), "r"(z), "r"(w), "r"(smem_u32(bar))
+        : "memory");
+}
+
+// One row of an interleaved vector (NR values per node) as seen by one
+// right-hand side: element c is p[c * NR].
+template <typename T, int NR>
+struct VRow {
+    T* p;
+    __device__ __forceinline__ T& operator[](int c) const { return p[c * NR]; }
+};
+
 
 // ------------------------------------------------------------------ layout
 __host__ __device__ constexpr int r128(int b) { return (b + 127) & ~127; }
@@ -69,7 +96,7 @@ __device__ __forceinline__ float divide<float>(float s, float d) { return __fdiv
 // right-hand side, and for the up kernel the pre-smoothed iterate and one
 // coarse row of the coarse iterate), then a (2K+4)-row ring of the iterate X
 // and (down) an equal ring of the residual R, then the mbarriers.
-template <typename T, typename TF, int K, bool UP>
+template <typename T, typename TF, int K, bool UP, int NR = 1>
 struct Lay {
     // ring slots: the K pairs of the current step, the two pairs below it
     // (halo rows), and D = K pairs in flight (one step ahead; two steps ahead
@@ -87,50 +114,56 @@ struct Lay {
         WW = 2 * wc + 16;
         WWc = wc + 8;
         sA = r128(10 * WW * (int)sizeof(T));
-        sF = r128(2 * WW * (int)sizeof(TF));
-        sXp = UP ? r128(2 * WW * (int)sizeof(T)) : 0;
-        sC = UP ? r128(WWc * (int)sizeof(T)) : 0;
+        sF = r128(2 * WW * NR * (int)sizeof(TF));
+        sXp = UP ? r128(2 * WW * NR * (int)sizeof(T)) : 0;
+        sC = UP ? r128(WWc * NR * (int)sizeof(T)) : 0;
     }
     __host__ __device__ int slot() const { return sA + sF + sXp + sC; }
     __host__ __device__ int bytes() const {
-        return 128 + RP * slot() + (UP ? 1 : 2) * XR * WW * (int)sizeof(T) + RP * 8;
+        return 128 + RP * slot() + (UP ? 1 : 2) * XR * WW * NR * (int)sizeof(T) + RP * 8;
     }
     __host__ __device__ uint32_t tx() const {
-        return (uint32_t)(10 * WW * sizeof(T) + 2 * WW * sizeof(TF) +
-                          (UP ? 2 * WW * sizeof(T) + WWc * sizeof(T) : 0));
+        return (uint32_t)(10 * WW * sizeof(T) + 2 * WW * NR * sizeof(TF) +
+                          (UP ? 2 * WW * NR * sizeof(T) + WWc * NR * sizeof(T) : 0));
     }
 };
 
 // Row-pair ring shared by both kernels.  Pair q (local index, q >= 0) is
 // the fine rows 2(q0+q)+1 and 2(q0+q)+2 and, for the up kernel, coarse row
 // q0+q+1 of the coarse iterate.
-template <typename T, typename TF, int K, bool UP>
+// qb: pairs this CTA issued before the current item (the persistent batched
+// kernels carry the ring's slots and mbarrier phases from item to item);
+// rh: the thread's right-hand side.
+template <typename T, typename TF, int K, bool UP, int NR = 1>
 struct Ring {
+    static constexpr unsigned RPu = (unsigned)Lay<T, TF, K, UP, NR>::RP;
     unsigned char *pA, *pF, *pXp, *pC;
     uint64_t* bars;
-    int q0, WW, sA, sF, sXp, sC;
+    int q0, WW, sA, sF, sXp, sC, rh;
+    unsigned qb;
     __device__ __forceinline__ int slot_of_row(int j) const {
-        return (int)((unsigned)(((j - 1) >> 1) - q0) % (unsigned)Lay<T, TF, K, UP>::RP);
+        return (int)((qb + (unsigned)(((j - 1) >> 1) - q0)) % RPu);
     }
     __device__ __forceinline__ const T* A(int j) const {      // plane 0 of fine row j
         return (const T*)(pA + slot_of_row(j) * sA) + ((j - 1) & 1) * WW;
     }
-    __device__ __forceinline__ const TF* F(int j) const {
-        return (const TF*)(pF + slot_of_row(j) * sF) + ((j - 1) & 1) * WW;
+    __device__ __forceinline__ VRow<const TF, NR> F(int j) const {
+        return {(const TF*)(pF + slot_of_row(j) * sF) + ((j - 1) & 1) * WW * NR + rh};
     }
-    __device__ __forceinline__ const T* Xp(int j) const {
-        return (const T*)(pXp + slot_of_row(j) * sXp) + ((j - 1) & 1) * WW;
+    __device__ __forceinline__ VRow<const T, NR> Xp(int j) const {
+        return {(const T*)(pXp + slot_of_row(j) * sXp) + ((j - 1) & 1) * WW * NR + rh};
     }
-    __device__ __forceinline__ const T* C(int J) const {      // coarse row J (carried by pair J-1)
-        return (const T*)(pC + (int)((unsigned)(J - 1 - q0) % (unsigned)Lay<T, TF, K, UP>::RP) * sC);
+    __device__ __forceinline__ VRow<const T, NR> C(int J) const {      // coarse row J (carried by pair J-1)
+        return {(const T*)(pC + (int)((qb + (unsigned)(J - 1 - q0)) % RPu) * sC) + rh};
     }
 };
 
-// bounded wait for pairs [qa, qb); returns false (in every thread) on expiry
+// bounded wait for the pairs with ring indices [qa, qb); returns false (in
+// every thread) on expiry
 template <int RP>
-__device__ __forceinline__ bool wait_pairs(uint64_t* bars, int qa, int qb) {
+__device__ __forceinline__ bool wait_pairs(uint64_t* bars, unsigned qa, unsigned qb) {
     bool mine = true;
-    for (int q = qa; q < qb; q++) mine = mine && mbar::wait(bars + ((unsigned)q % RP), ((unsigned)q / RP) & 1u);
+    for (unsigned q = qa; q < qb; q++) mine = mine && mbar::wait(bars + (q % RP), (q / RP) & 1u);
     return __syncthreads_and(mine) != 0;
 }
 
@@ -150,11 +183,11 @@ struct Acc32f {
 // Offsets: W(c) couples (c-1), W(c+1) couples (c+1) of the row; S(j) couples
 // row j-1, S(j+1) row j+1; SW(j,c) couples (c-1, j-1), SW(j+1,c+1) (c+1, j+1);
 // NW(j,c) couples (c-1, j+1), NW(j-1,c+1) (c+1, j-1).
-template <typename T>
+template <typename T, int NR = 1>
 struct Rows {
-    const T *a, *an, *as;   // stencil rows j, j+1, j-1 (plane 0)
-    const T *x, *xn, *xs;   // iterate rows j, j+1, j-1
-    int PL;                 // plane stride
+    const T *a, *an, *as;          // stencil rows j, j+1, j-1 (plane 0)
+    VRow<T, NR> x, xn, xs;         // iterate rows j, j+1, j-1
+    int PL;                        // plane stride
     __device__ __forceinline__ T offdiag(int c) const {
         T s = a[W2 * PL + c] * x[c - 1];
         s += a[W2 * PL + c + 1] * x[c + 1];
@@ -180,47 +213,69 @@ struct Rows {
 };
 
 // ------------------------------------------------------------------ down kernel
-template <typename T, typename TF, int K, int WC>
-__global__ void __launch_bounds__((WC + 8) * K, sizeof(T) == 4 ? 3 : 1) k_vdown2d(const __grid_constant__ CUtensorMap tmA,
-                                                    const __grid_constant__ CUtensorMap tmF, FusedArgs p) {
-    using LY = Lay<T, TF, K, false>;
+template <typename T, typename TF, int K, int WC, int NR = 1, bool BATCH = false>
+__global__ void __launch_bounds__((WC + 8) * K * NR, sizeof(T) == 4 ? 3 : 1)
+    k_vdown2d(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmF, FusedArgs p) {
+    using LY = Lay<T, TF, K, false, NR>;
     constexpr int RP = LY::RP;
     extern __shared__ unsigned char smem_raw[];
     const LY L(WC);   // strip width fixed at compile time: every shared-memory stride is a constant
     const int WW = L.WW, PL = 2 * WW;
     unsigned char* base = (unsigned char*)(((uintptr_t)smem_raw + 127) & ~(uintptr_t)127);
-    Ring<T, TF, K, false> rg;
+    Ring<T, TF, K, false, NR> rg;
     rg.pA = base;
     rg.pF = base + RP * L.sA;
     rg.pXp = rg.pC = nullptr;
     constexpr int XR = LY::XR;
     T* sX = (T*)(base + RP * L.slot());
-    T* sR = sX + XR * WW;
-    rg.bars = (uint64_t*)(sR + XR * WW);
+    T* sR = sX + XR * WW * NR;
+    rg.bars = (uint64_t*)(sR + XR * WW * NR);
     rg.WW = WW;
     rg.sA = L.sA;
     rg.sF = L.sF;
     rg.sXp = rg.sC = 0;
-    const int tx = threadIdx.x, ty = threadIdx.y;
-    const bool lead = tx == 0 && ty == 0;
-    const int I0 = 1 + blockIdx.x * WC, J0 = 1 + blockIdx.y * p.hc;
-    const int x0 = 2 * I0 - 10, xc0 = I0 - 5;
-    rg.q0 = J0 - 2;
-    const int npairs = p.hc + 2;
+    const int rh = NR == 1 ? 0 : (int)threadIdx.x % NR;          // right-hand side of this thread
+    const int tx = NR == 1 ? (int)threadIdx.x : (int)threadIdx.x / NR, ty = threadIdx.y;
+    rg.rh = rh;
+    const bool lead = threadIdx.x == 0 && ty == 0;
     const int nf = p.nf, nc = p.nc;
     const uint32_t txb = L.tx();
-    auto issue = [&](int q) {
-        const int s = (int)((unsigned)q % RP), Jp = rg.q0 + q;
-        uint64_t* bar = rg.bars + s;
-        mbar::expect_tx(bar, txb);
-        tma3d(rg.pA + s * L.sA, &tmA, bar, x0, 2 * Jp + 1, 0);
-        tma2d(rg.pF + s * L.sF, &tmF, bar, x0, 2 * Jp + 1);
-    };
     if (lead) {
         for (int s = 0; s < RP; s++) mbar::init(rg.bars + s, 1);
         mbar::fence_init();
     }
     __syncthreads();
+    const int nitems = BATCH ? p.nmem * p.tiles_x * p.tiles_y : 1;
+    unsigned qb = 0;
+    for (int item = BATCH ? (int)blockIdx.x : 0; item < nitems; item += BATCH ? (int)gridDim.x : 1) {
+    int bx, by, mi = 0;
+    if (BATCH) {
+        const int tpm = p.tiles_x * p.tiles_y;
+        mi = item / tpm;
+        const int t = item - mi * tpm;
+        by = t / p.tiles_x;
+        bx = t - by * p.tiles_x;
+    } else {
+        bx = blockIdx.x;
+        by = blockIdx.y;
+    }
+    const int I0 = 1 + bx * WC, J0 = 1 + by * p.hc;
+    const int x0 = 2 * I0 - 10, xc0 = I0 - 5;
+    rg.q0 = J0 - 2;
+    rg.qb = qb;
+    const int npairs = p.hc + 2;
+    auto issue = [&](int q) {
+        const int s = (int)((qb + (unsigned)q) % (unsigned)RP), Jp = rg.q0 + q;
+        uint64_t* bar = rg.bars + s;
+        mbar::expect_tx(bar, txb);
+        if constexpr (BATCH) {
+            tma4d(rg.pA + s * L.sA, &tmA, bar, x0, 2 * Jp + 1, 0, mi);
+            tma4d(rg.pF + s * L.sF, &tmF, bar, 0, x0, 2 * Jp + 1, mi);
+        } else {
+            tma3d(rg.pA + s * L.sA, &tmA, bar, x0, 2 * Jp + 1, 0);
+            tma2d(rg.pF + s * L.sF, &tmF, bar, x0, 2 * Jp + 1);
+        }
+    };
     int issued = npairs < RP ? npairs : RP, waited = 0;
     if (lead)
         for (int q = 0; q < issued; q++) issue(q);
@@ -235,22 +290,23 @@ __global__ void __launch_bounds__((WC + 8) * K, sizeof(T) == 4 ? 3 : 1) k_vdown2
     const int I = xc0 + tx;
     const bool vres = tx >= 5 && tx < 5 + WC && I >= 1 && I <= nc - 2;
     auto inrow = [&](int j) { return j >= 1 && j <= nf - 2; };
-    auto X = [&](int j) { return sX + (int)((unsigned)j % XR) * WW; };
-    auto R = [&](int j) { return sR + (int)((unsigned)j % XR) * WW; };
+    auto X = [&](int j) { return VRow<T, NR>{sX + (int)((unsigned)j % XR) * WW * NR + rh}; };
+    auto RR = [&](int j) { return VRow<T, NR>{sR + (int)((unsigned)j % XR) * WW * NR + rh}; };
     auto rows = [&](int j) {
-        return Rows<T>{rg.A(j), rg.A(j + 1), rg.A(j - 1), X(j), X(j + 1), X(j - 1), PL};
+        return Rows<T, NR>{rg.A(j), rg.A(j + 1), rg.A(j - 1), X(j), X(j + 1), X(j - 1), PL};
     };
-    const T* Pg = (const T*)p.P;
-    T* xg = (T*)p.x;
-    T* bcg = (T*)p.bc;
+    const BatchMember* M = BATCH ? p.mem + mi : nullptr;
+    const T* Pg = BATCH ? (const T*)M->P : (const T*)p.P;
+    T* xg = BATCH ? (T*)M->x[0] : (T*)p.x;
+    T* bcg = BATCH ? (T*)M->bc : (T*)p.bc;
 
     // colour 0 / 1 of even row j, colour 2 / 3 of odd row j, residual of row j
     auto c0 = [&](int j) {
-        const Rows<T> r = rows(j);
+        const Rows<T, NR> r = rows(j);
         X(j)[ce] = (ve && inrow(j)) ? divide<T>((T)rg.F(j)[ce], r.diag(ce)) : (T)0;
     };
     auto c1 = [&](int j) {
-        const Rows<T> r = rows(j);
+        const Rows<T, NR> r = rows(j);
         T v = 0;
         if (vo && inrow(j)) {
             const T s = (T)rg.F(j)[co] - r.a[W2 * PL + co] * r.x[co - 1] - r.a[W2 * PL + co + 1] * r.x[co + 1];
@@ -259,11 +315,11 @@ __global__ void __launch_bounds__((WC + 8) * K, sizeof(T) == 4 ? 3 : 1) k_vdown2
         X(j)[co] = v;
     };
     auto c2 = [&](int j) {
-        const Rows<T> r = rows(j);
+        const Rows<T, NR> r = rows(j);
         X(j)[ce] = (ve && inrow(j)) ? divide<T>((T)rg.F(j)[ce] - r.offdiag_no_row(ce), r.diag(ce)) : (T)0;
     };
     auto c3 = [&](int j) {
-        const Rows<T> r = rows(j);
+        const Rows<T, NR> r = rows(j);
         X(j)[co] = (vo && inrow(j)) ? divide<T>((T)rg.F(j)[co] - r.offdiag(co), r.diag(co)) : (T)0;
     };
     // Residual after the forward sweep from a zero guess.  A point's own
@@ -275,8 +331,8 @@ __global__ void __launch_bounds__((WC + 8) * K, sizeof(T) == 4 ? 3 : 1) k_vdown2
     //   colour 2 (odd row, even column): the two colour-3 row neighbours;
     //   colour 3 (odd row, odd column): none.
     auto resid = [&](int j) {
-        const Rows<T> r = rows(j);
-        T* Rj = R(j);
+        const Rows<T, NR> r = rows(j);
+        const VRow<T, NR> Rj = RR(j);
         const bool rj = inrow(j);
         if (!(j & 1)) {
             Rj[ce] = (ve && rj) ? -r.offdiag(ce) : (T)0;
@@ -287,7 +343,7 @@ __global__ void __launch_bounds__((WC + 8) * K, sizeof(T) == 4 ? 3 : 1) k_vdown2
         }
     };
 
-    bool ok = wait_pairs<RP>(rg.bars, 0, 2);
+    bool ok = wait_pairs<RP>(rg.bars, qb, qb + 2);
     waited = ok ? 2 : 0;
     if (ok) {   // pre-roll: rows 2J0-2 .. 2J0 final, residual of row 2J0-1
         if (ty == 0) { c0(2 * J0 - 2); c0(2 * J0); }
@@ -316,7 +372,7 @@ __global__ void __launch_bounds__((WC + 8) * K, sizeof(T) == 4 ? 3 : 1) k_vdown2
     load_w(J0 + ty);
     for (int J = J0; ok && J < J0 + p.hc; J += K) {
         const int qa = J - rg.q0;
-        ok = wait_pairs<RP>(rg.bars, qa, qa + K);
+        ok = wait_pairs<RP>(rg.bars, qb + qa, qb + qa + K);
         if (!ok) break;
         waited = qa + K;
         // every thread is past the previous step: refill the freed slots
@@ -339,28 +395,28 @@ __global__ void __launch_bounds__((WC + 8) * K, sizeof(T) == 4 ? 3 : 1) k_vdown2
         resid(jo);
         __syncthreads();
         if (do_res) {
-            const T* Rm = R(jm);
-            const T* Rs = R(jm - 1);
-            const T* Rn = R(jo);
+            const VRow<T, NR> Rm = RR(jm);
+            const VRow<T, NR> Rs = RR(jm - 1);
+            const VRow<T, NR> Rn = RR(jo);
             const int c = ce;
             T b = Rm[c];
             b += w[0] * Rm[c - 1];
             b += w[1] * Rm[c + 1];
             b += w[2] * Rs[c];
             b += w[3] * Rn[c];
-            bcg[(long long)Jp * p.ldc + I] = b;
+            bcg[((long long)Jp * p.ldc + I) * NR + rh] = b;
         }
         load_w(Jp + K);
         // finished rows 2Jp-1 and 2Jp of the owned columns
         if (inrow(jm - 1)) {
-            const T* Xr = X(jm - 1);
-            if (own_e) xg[(long long)(jm - 1) * p.ldf + ie] = Xr[ce];
-            if (own_o) xg[(long long)(jm - 1) * p.ldf + ie + 1] = Xr[co];
+            const VRow<T, NR> Xr = X(jm - 1);
+            if (own_e) xg[((long long)(jm - 1) * p.ldf + ie) * NR + rh] = Xr[ce];
+            if (own_o) xg[((long long)(jm - 1) * p.ldf + ie + 1) * NR + rh] = Xr[co];
         }
         if (inrow(jm)) {
-            const T* Xr = X(jm);
-            if (own_e) xg[(long long)jm * p.ldf + ie] = Xr[ce];
-            if (own_o) xg[(long long)jm * p.ldf + ie + 1] = Xr[co];
+            const VRow<T, NR> Xr = X(jm);
+            if (own_e) xg[((long long)jm * p.ldf + ie) * NR + rh] = Xr[ce];
+            if (own_o) xg[((long long)jm * p.ldf + ie + 1) * NR + rh] = Xr[co];
         }
         // no barrier here: the next step's writes (rows 2Jp+2K+1.. of the X and R
         // rings) do not alias rows read above, and slots are refilled only after
@@ -369,59 +425,92 @@ __global__ void __launch_bounds__((WC + 8) * K, sizeof(T) == 4 ? 3 : 1) k_vdown2
     if (!ok) {
         if (lead) {
             set_err(p.st, BMG_ERR_TIMEOUT);
-            for (int q = waited; q < issued; q++) mbar::wait(rg.bars + ((unsigned)q % RP), ((unsigned)q / RP) & 1u);
+            for (int q = waited; q < issued; q++) {
+                const unsigned g = qb + (unsigned)q;
+                mbar::wait(rg.bars + (g % RP), (g / RP) & 1u);
+            }
         }
         __syncthreads();
+        return;
+    }
+    qb += (unsigned)npairs;
+    if (BATCH) __syncthreads();   // the next item's copies reuse the ring and the rows
     }
 }
 
 // ------------------------------------------------------------------ up kernel
-template <typename T, typename TF, typename TO, int K, int WC>
-__global__ void __launch_bounds__((WC + 8) * K, sizeof(T) == 4 ? 3 : 1) k_vup2d(const __grid_constant__ CUtensorMap tmA,
-                                                  const __grid_constant__ CUtensorMap tmF,
-                                                  const __grid_constant__ CUtensorMap tmX,
-                                                  const __grid_constant__ CUtensorMap tmC, FusedArgs p) {
-    using LY = Lay<T, TF, K, true>;
+template <typename T, typename TF, typename TO, int K, int WC, int NR = 1, bool BATCH = false>
+__global__ void __launch_bounds__((WC + 8) * K * NR, sizeof(T) == 4 ? 3 : 1)
+    k_vup2d(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmF,
+            const __grid_constant__ CUtensorMap tmX, const __grid_constant__ CUtensorMap tmC, FusedArgs p) {
+    using LY = Lay<T, TF, K, true, NR>;
     constexpr int RP = LY::RP;
     extern __shared__ unsigned char smem_raw[];
     const LY L(WC);   // strip width fixed at compile time: every shared-memory stride is a constant
     const int WW = L.WW, PL = 2 * WW;
     unsigned char* base = (unsigned char*)(((uintptr_t)smem_raw + 127) & ~(uintptr_t)127);
-    Ring<T, TF, K, true> rg;
+    Ring<T, TF, K, true, NR> rg;
     rg.pA = base;
     rg.pF = rg.pA + RP * L.sA;
     rg.pXp = rg.pF + RP * L.sF;
     rg.pC = rg.pXp + RP * L.sXp;
     constexpr int XR = LY::XR;
     T* sX = (T*)(base + RP * L.slot());
-    rg.bars = (uint64_t*)(sX + XR * WW);
+    rg.bars = (uint64_t*)(sX + XR * WW * NR);
     rg.WW = WW;
     rg.sA = L.sA;
     rg.sF = L.sF;
     rg.sXp = L.sXp;
     rg.sC = L.sC;
-    const int tx = threadIdx.x, ty = threadIdx.y;
-    const bool lead = tx == 0 && ty == 0;
-    const int I0 = 1 + blockIdx.x * WC, J0 = 1 + blockIdx.y * p.hc;
-    const int x0 = 2 * I0 - 10, xc0 = I0 - 5;
-    rg.q0 = J0 - 2;
-    const int npairs = p.hc + 2;
+    const int rh = NR == 1 ? 0 : (int)threadIdx.x % NR;          // right-hand side of this thread
+    const int tx = NR == 1 ? (int)threadIdx.x : (int)threadIdx.x / NR, ty = threadIdx.y;
+    rg.rh = rh;
+    const bool lead = threadIdx.x == 0 && ty == 0;
     const int nf = p.nf, nc = p.nc;
     const uint32_t txb = L.tx();
-    auto issue = [&](int q) {
-        const int s = (int)((unsigned)q % RP), Jp = rg.q0 + q;
-        uint64_t* bar = rg.bars + s;
-        mbar::expect_tx(bar, txb);
-        tma3d(rg.pA + s * L.sA, &tmA, bar, x0, 2 * Jp + 1, 0);
-        tma2d(rg.pF + s * L.sF, &tmF, bar, x0, 2 * Jp + 1);
-        tma2d(rg.pXp + s * L.sXp, &tmX, bar, x0, 2 * Jp + 1);
-        tma2d(rg.pC + s * L.sC, &tmC, bar, xc0, Jp + 1);
-    };
+    const int tid = ty * blockDim.x + threadIdx.x, nthr = blockDim.x * blockDim.y;
     if (lead) {
         for (int s = 0; s < RP; s++) mbar::init(rg.bars + s, 1);
         mbar::fence_init();
     }
     __syncthreads();
+    const int nitems = BATCH ? p.nmem * p.tiles_x * p.tiles_y : 1;
+    unsigned qb = 0;
+    for (int item = BATCH ? (int)blockIdx.x : 0; item < nitems; item += BATCH ? (int)gridDim.x : 1) {
+    int bx, by, mi = 0;
+    if (BATCH) {
+        const int tpm = p.tiles_x * p.tiles_y;
+        mi = item / tpm;
+        const int t = item - mi * tpm;
+        by = t / p.tiles_x;
+        bx = t - by * p.tiles_x;
+    } else {
+        bx = blockIdx.x;
+        by = blockIdx.y;
+    }
+    const BatchMember* M = BATCH ? p.mem + mi : nullptr;
+    const int cmi = BATCH ? M->cmem : 0;
+    const int I0 = 1 + bx * WC, J0 = 1 + by * p.hc;
+    const int x0 = 2 * I0 - 10, xc0 = I0 - 5;
+    rg.q0 = J0 - 2;
+    rg.qb = qb;
+    const int npairs = p.hc + 2;
+    auto issue = [&](int q) {
+        const int s = (int)((qb + (unsigned)q) % (unsigned)RP), Jp = rg.q0 + q;
+        uint64_t* bar = rg.bars + s;
+        mbar::expect_tx(bar, txb);
+        if constexpr (BATCH) {
+            tma4d(rg.pA + s * L.sA, &tmA, bar, x0, 2 * Jp + 1, 0, mi);
+            tma4d(rg.pF + s * L.sF, &tmF, bar, 0, x0, 2 * Jp + 1, mi);
+            tma4d(rg.pXp + s * L.sXp, &tmX, bar, 0, x0, 2 * Jp + 1, mi);
+            tma4d(rg.pC + s * L.sC, &tmC, bar, 0, xc0, Jp + 1, cmi);
+        } else {
+            tma3d(rg.pA + s * L.sA, &tmA, bar, x0, 2 * Jp + 1, 0);
+            tma2d(rg.pF + s * L.sF, &tmF, bar, x0, 2 * Jp + 1);
+            tma2d(rg.pXp + s * L.sXp, &tmX, bar, x0, 2 * Jp + 1);
+            tma2d(rg.pC + s * L.sC, &tmC, bar, xc0, Jp + 1);
+        }
+    };
     int issued = npairs < RP ? npairs : RP, waited = 0;
     if (lead)
         for (int q = 0; q < issued; q++) issue(q);
@@ -435,13 +524,14 @@ __global__ void __launch_bounds__((WC + 8) * K, sizeof(T) == 4 ? 3 : 1) k_vup2d(
     const int I = xc0 + tx;                      // coarse column of the thread's column pair
     const bool vI = I >= 0 && I <= nc - 1;
     auto inrow = [&](int j) { return j >= 1 && j <= nf - 2; };
-    auto X = [&](int j) { return sX + (int)((unsigned)j % XR) * WW; };
+    auto X = [&](int j) { return VRow<T, NR>{sX + (int)((unsigned)j % XR) * WW * NR + rh}; };
     auto rows = [&](int j) {
-        return Rows<T>{rg.A(j), rg.A(j + 1), rg.A(j - 1), X(j), X(j + 1), X(j - 1), PL};
+        return Rows<T, NR>{rg.A(j), rg.A(j + 1), rg.A(j - 1), X(j), X(j + 1), X(j - 1), PL};
     };
-    const T* Pg = (const T*)p.P;
-    TO* out = (TO*)p.x;
-    const float* zold = (const float*)p.zold;   // finest level of the refinement mode only
+    const T* Pg = BATCH ? (const T*)M->P : (const T*)p.P;
+    TO* out = BATCH ? (TO*)M->x[p.parity] : (TO*)p.x;
+    // finest level of the refinement mode only
+    const float* zold = BATCH ? (const float*)M->zold[p.parity] : (const float*)p.zold;
     Acc32f rz, rzo;
     auto pw = [&](int plane, int Jc) -> T {
         return (vI && Jc >= 0 && Jc <= nc - 1) ? Pg[plane * p.plc + (long long)Jc * p.ldc + I] : (T)0;
@@ -452,29 +542,29 @@ __global__ void __launch_bounds__((WC + 8) * K, sizeof(T) == 4 ? 3 : 1) k_vup2d(
     // PSW, PSE, PNW, PNE of coarse row (j-1)/2)
     auto corr_even = [&](int j, T wxl, T wxr) {
         const bool rj = inrow(j);
-        const T* C0 = rg.C(j >> 1);
-        const T* xp = rg.Xp(j);
-        T* x = X(j);
+        const VRow<const T, NR> C0 = rg.C(j >> 1);
+        const VRow<const T, NR> xp = rg.Xp(j);
+        const VRow<T, NR> x = X(j);
         x[ce] = (ve && rj) ? xp[ce] + C0[tx] : (T)0;
         x[co] = (vo && rj) ? xp[co] + wxl * C0[tx] + wxr * C0[tx + 1] : (T)0;
     };
     auto corr_odd = [&](int j, const T* wy) {
         const bool rj = inrow(j);
-        const T* C0 = rg.C(j >> 1);
-        const T* C1 = rg.C((j >> 1) + 1);
-        const T* xp = rg.Xp(j);
-        T* x = X(j);
+        const VRow<const T, NR> C0 = rg.C(j >> 1);
+        const VRow<const T, NR> C1 = rg.C((j >> 1) + 1);
+        const VRow<const T, NR> xp = rg.Xp(j);
+        const VRow<T, NR> x = X(j);
         x[ce] = (ve && rj) ? xp[ce] + wy[0] * C0[tx] + wy[1] * C1[tx] : (T)0;
         x[co] = (vo && rj) ? xp[co] + wy[2] * C0[tx] + wy[3] * C0[tx + 1] + wy[4] * C1[tx] + wy[5] * C1[tx + 1]
                            : (T)0;
     };
     auto gs = [&](int j, int c, bool v) {      // one Gauss-Seidel update
         if (!(v && inrow(j))) return;
-        const Rows<T> r = rows(j);
+        const Rows<T, NR> r = rows(j);
         X(j)[c] = divide<T>((T)rg.F(j)[c] - r.offdiag(c), r.diag(c));
     };
 
-    bool ok = wait_pairs<RP>(rg.bars, 0, 2);
+    bool ok = wait_pairs<RP>(rg.bars, qb, qb + 2);
     waited = ok ? 2 : 0;
     if (ok) {   // pre-roll: corrected rows 2J0-2 .. 2J0, odd row 2J0-1 smoothed
         if (ty == 0) {
@@ -511,15 +601,15 @@ __global__ void __launch_bounds__((WC + 8) * K, sizeof(T) == 4 ? 3 : 1) k_vup2d(
             const int j = 2 * Jp - 1 + rr;
             const long long o = (long long)j * p.ldf + ie;
             const bool rj = inrow(j);
-            zo_nx[rr][0] = (rj && own_e) ? zold[o] : 0.f;
-            zo_nx[rr][1] = (rj && own_o) ? zold[o + 1] : 0.f;
+            zo_nx[rr][0] = (rj && own_e) ? zold[o * NR + rh] : 0.f;
+            zo_nx[rr][1] = (rj && own_o) ? zold[(o + 1) * NR + rh] : 0.f;
         }
     };
     if (zold) load_zo(J0 + ty);
     for (int J = J0; ok && J < J0 + p.hc; J += K) {
         const int qa = J - rg.q0;
         const int Jp = J + ty, jm = 2 * Jp, jo = jm + 1, je = jm + 2;
-        ok = wait_pairs<RP>(rg.bars, qa, qa + K);
+        ok = wait_pairs<RP>(rg.bars, qb + qa, qb + qa + K);
         if (!ok) break;
         waited = qa + K;
         // every thread is past the previous step: refill the freed slots
@@ -546,7 +636,7 @@ __global__ void __launch_bounds__((WC + 8) * K, sizeof(T) == 4 ? 3 : 1) k_vup2d(
         float fr[2][2] = {{0.f, 0.f}, {0.f, 0.f}};
         if (zold)
             for (int rr = 0; rr < 2; rr++) {
-                const TF* Fr = rg.F(jm - 1 + rr);
+                const VRow<const TF, NR> Fr = rg.F(jm - 1 + rr);
                 fr[rr][0] = (float)Fr[ce];
                 fr[rr][1] = (float)Fr[co];
             }
@@ -554,10 +644,10 @@ __global__ void __launch_bounds__((WC + 8) * K, sizeof(T) == 4 ? 3 : 1) k_vup2d(
         for (int rr = 0; rr < 2; rr++) {
             const int j = jm - 1 + rr;
             if (!inrow(j)) continue;
-            const T* Xr = X(j);
+            const VRow<T, NR> Xr = X(j);
             const long long o = (long long)j * p.ldf + ie;
-            if (own_e) out[o] = (TO)Xr[ce];
-            if (own_o) out[o + 1] = (TO)Xr[co];
+            if (own_e) out[o * NR + rh] = (TO)Xr[ce];
+            if (own_o) out[(o + 1) * NR + rh] = (TO)Xr[co];
             if (zold) {
                 if (own_e) {
                     rz.add(fr[rr][0] * (float)Xr[ce]);
@@ -573,19 +663,25 @@ __global__ void __launch_bounds__((WC + 8) * K, sizeof(T) == 4 ? 3 : 1) k_vup2d(
     if (!ok) {
         if (lead) {
             set_err(p.st, BMG_ERR_TIMEOUT);
-            for (int q = waited; q < issued; q++) mbar::wait(rg.bars + ((unsigned)q % RP), ((unsigned)q / RP) & 1u);
+            for (int q = waited; q < issued; q++) {
+                const unsigned g = qb + (unsigned)q;
+                mbar::wait(rg.bars + (g % RP), (g / RP) & 1u);
+            }
         }
         __syncthreads();
         return;
     }
+    qb += (unsigned)npairs;
     if (zold) {
-        // deterministic grid reduction of (r.z, r.z_old); the last CTA forms
-        // the flexible-CG beta.  Every copy into the rings has completed, so
-        // after the barrier the A ring is free to hold the per-thread sums.
-        const int tid = ty * blockDim.x + tx, nthr = blockDim.x * blockDim.y;
+        // Deterministic reduction of (r.z, r.z_old) per right-hand side; the
+        // last CTA (of the grid, or of the problem's tiles when batched)
+        // forms the flexible-CG beta.  Every copy into the rings has
+        // completed, so after the barrier the A ring is free to hold the
+        // per-thread sums.  Thread tid carries right-hand side tid % NR.
         double* red = (double*)rg.pA;
         int* last = (int*)(red + 2 * nthr);
-        // sum of v1 / v2 over the CTA's threads, in a fixed order; valid in thread 0
+        // sums of v1 / v2 over the threads of each right-hand side in a fixed
+        // order; valid in threads 0 .. NR-1 (thread rh holds right-hand side rh)
         auto block_sum2 = [&](double v1, double v2, double& s1, double& s2) {
             __syncthreads();
             red[tid] = v1;
@@ -597,7 +693,7 @@ __global__ void __launch_bounds__((WC + 8) * K, sizeof(T) == 4 ? 3 : 1) k_vup2d(
                     a1 += red[k];
                     a2 += red[nthr + k];
                 }
-                for (int o = 16; o > 0; o >>= 1) {
+                for (int o = 16; o >= NR; o >>= 1) {
                     a1 += __shfl_down_sync(0xffffffffu, a1, o);
                     a2 += __shfl_down_sync(0xffffffffu, a2, o);
                 }
@@ -607,36 +703,75 @@ __global__ void __launch_bounds__((WC + 8) * K, sizeof(T) == 4 ? 3 : 1) k_vup2d(
         };
         double b1 = 0.0, b2 = 0.0;
         block_sum2(rz.value(), rzo.value(), b1, b2);
-        const int nb = gridDim.x * gridDim.y;
-        if (tid == 0) {
-            const int bid = blockIdx.y * gridDim.x + blockIdx.x;
-            p.partials[2 * bid] = b1;
-            p.partials[2 * bid + 1] = b2;
-            __threadfence();
-            *last = atomicAdd(&p.st->counter[6], 1u) == (unsigned)nb - 1;
-        }
-        __syncthreads();
-        if (*last) {
-            __threadfence();
-            double v1 = 0.0, v2 = 0.0;
-            for (int k = tid; k < nb; k += nthr) {
-                v1 += ((volatile double*)p.partials)[2 * k];
-                v2 += ((volatile double*)p.partials)[2 * k + 1];
-            }
-            double t1 = 0.0, t2 = 0.0;
-            block_sum2(v1, v2, t1, t2);
+        if constexpr (!BATCH) {
+            const int nb = gridDim.x * gridDim.y;
             if (tid == 0) {
-                p.st->counter[6] = 0u;
-                KState* st = p.st;
-                if (st->first) {
-                    st->beta = 0.0;
-                    st->first = 0;
-                } else {
-                    st->beta = (t1 - t2) / st->rz;
+                const int bid = blockIdx.y * gridDim.x + blockIdx.x;
+                p.partials[2 * bid] = b1;
+                p.partials[2 * bid + 1] = b2;
+                __threadfence();
+                *last = atomicAdd(&p.st->counter[6], 1u) == (unsigned)nb - 1;
+            }
+            __syncthreads();
+            if (*last) {
+                __threadfence();
+                double v1 = 0.0, v2 = 0.0;
+                for (int k = tid; k < nb; k += nthr) {
+                    v1 += ((volatile double*)p.partials)[2 * k];
+                    v2 += ((volatile double*)p.partials)[2 * k + 1];
                 }
-                st->rz = t1;
+                double t1 = 0.0, t2 = 0.0;
+                block_sum2(v1, v2, t1, t2);
+                if (tid == 0) {
+                    p.st->counter[6] = 0u;
+                    KState* st = p.st;
+                    if (st->first) {
+                        st->beta = 0.0;
+                        st->first = 0;
+                    } else {
+                        st->beta = (t1 - t2) / st->rz;
+                    }
+                    st->rz = t1;
+                }
+            }
+        } else {
+            const int tpm = p.tiles_x * p.tiles_y;
+            double* part = p.partials + (M->part + (by * p.tiles_x + bx)) * 2 * NR;
+            if (tid < NR) {
+                part[2 * tid] = b1;
+                part[2 * tid + 1] = b2;
+            }
+            __threadfence();
+            __syncthreads();
+            if (tid == 0) *last = atomicAdd(&p.counters[M->prob], 1u) == (unsigned)tpm - 1;
+            __syncthreads();
+            if (*last) {
+                __threadfence();
+                // thread tid sums the tiles k = tid/ NR-strided... in a fixed order:
+                // tiles tid / NR, tid / NR + nthr / NR, ... of right-hand side tid % NR
+                const double* base_p = p.partials + M->part * 2 * NR;
+                double v1 = 0.0, v2 = 0.0;
+                for (int k = tid / NR; k < tpm; k += nthr / NR) {
+                    v1 += ((volatile const double*)base_p)[(long long)k * 2 * NR + 2 * rh];
+                    v2 += ((volatile const double*)base_p)[(long long)k * 2 * NR + 2 * rh + 1];
+                }
+                double t1 = 0.0, t2 = 0.0;
+                block_sum2(v1, v2, t1, t2);
+                if (tid < NR) {
+                    SysState& sy = p.sys[(long long)M->prob * NR + tid];
+                    if (sy.first || !sy.active || !(sy.rz != 0.0)) {
+                        sy.beta = 0.0;
+                        sy.first = 0;
+                    } else {
+                        sy.beta = (t1 - t2) / sy.rz;
+                    }
+                    if (sy.active) sy.rz = t1;
+                }
+                if (tid == 0) p.counters[M->prob] = 0u;
             }
         }
+    }
+    if (BATCH) __syncthreads();   // the next item's copies reuse the ring and the rows
     }
 }
 
@@ -713,7 +848,62 @@ bmg_status occupancy(int wc, int* down_blocks, int* up_blocks) {
     });
 }
 
+// Batched kernels: FP32, kBatchR right-hand sides, kBatchK row pairs per
+// step, strip widths 16 or 32 coarse columns.
+template <class F>
+bmg_status with_batch_wc(int wc, F&& f) {
+    switch (wc) {
+        case 16: return f(std::integral_constant<int, 16>{});
+        case 32: return f(std::integral_constant<int, 32>{});
+        default: return BMG_ERR_ARG;
+    }
+}
+
 }  // namespace
+
+int batch_down_smem(int wc) { return Lay<float, float, kBatchK, false, kBatchR>(wc).bytes(); }
+int batch_up_smem(int wc) { return Lay<float, float, kBatchK, true, kBatchR>(wc).bytes(); }
+
+bmg_status batch_occupancy(int wc, int* down_blocks, int* up_blocks) {
+    return with_batch_wc(wc, [&](auto W) {
+        constexpr int w = decltype(W)::value;
+        auto kd = k_vdown2d<float, float, kBatchK, w, kBatchR, true>;
+        auto ku = k_vup2d<float, float, float, kBatchK, w, kBatchR, true>;
+        const int sd = batch_down_smem(wc), su = batch_up_smem(wc);
+        const int nt = (wc + 8) * kBatchK * kBatchR;
+        if (cudaFuncSetAttribute(kd, cudaFuncAttributeMaxDynamicSharedMemorySize, sd) != cudaSuccess ||
+            cudaFuncSetAttribute(ku, cudaFuncAttributeMaxDynamicSharedMemorySize, su) != cudaSuccess ||
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(down_blocks, kd, nt, sd) != cudaSuccess ||
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(up_blocks, ku, nt, su) != cudaSuccess)
+            return BMG_ERR_DEVICE;
+        return BMG_OK;
+    });
+}
+
+// One persistent launch over the work-list of a size class (grid CTAs).
+bmg_status batch_down(const CUtensorMap& mA, const CUtensorMap& mF, const FusedArgs& a, int grid,
+                      cudaStream_t s) {
+    return with_batch_wc(a.wc, [&](auto W) {
+        auto kern = k_vdown2d<float, float, kBatchK, decltype(W)::value, kBatchR, true>;
+        const int smem = batch_down_smem(a.wc);
+        if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) != cudaSuccess)
+            return BMG_ERR_DEVICE;
+        kern<<<grid, dim3((a.wc + 8) * kBatchR, kBatchK), smem, s>>>(mA, mF, a);
+        return cudaGetLastError() == cudaSuccess ? BMG_OK : BMG_ERR_DEVICE;
+    });
+}
+
+bmg_status batch_up(const CUtensorMap& mA, const CUtensorMap& mF, const CUtensorMap& mXp, const CUtensorMap& mXc,
+                    const FusedArgs& a, int grid, cudaStream_t s) {
+    return with_batch_wc(a.wc, [&](auto W) {
+        auto kern = k_vup2d<float, float, float, kBatchK, decltype(W)::value, kBatchR, true>;
+        const int smem = batch_up_smem(a.wc);
+        if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) != cudaSuccess)
+            return BMG_ERR_DEVICE;
+        kern<<<grid, dim3((a.wc + 8) * kBatchR, kBatchK), smem, s>>>(mA, mF, mXp, mXc, a);
+        return cudaGetLastError() == cudaSuccess ? BMG_OK : BMG_ERR_DEVICE;
+    });
+}
 
 int fused_rows_per_step(bool f32) { return f32 ? k_of<float>() : k_of<double>(); }
 

@@ -31,18 +31,6 @@ namespace {
 constexpr int kTailThreads = 256;      // one thread per node of a colour at n = 33
 constexpr unsigned kTailChunk = 16384;    // bytes per bulk copy
 
-struct TailArgs {
-    int nlev;                     // levels in the tail (the last one has 3 nodes)
-    int ns[kMaxLevels];           // nodes per side of each tail level
-    const void* pack;             // packed operators and weights (shared-memory image)
-    unsigned pack_bytes;          // its size, a multiple of 16
-    const void* b0;               // right-hand side of the first tail level
-    void* x0;                     // finished iterate of the first tail level
-    int ld0;                      // row length of b0 and x0
-    const double* a64c;           // FP64 centre entry of the coarsest operator
-    KState* st;
-};
-
 template <typename T>
 __device__ __forceinline__ T tdiv(T s, T d) { return s / d; }
 template <>
@@ -84,8 +72,11 @@ __global__ void k_tail_pack(const T* __restrict__ src, int planes, int m, int ld
     }
 }
 
-template <typename T>
-__global__ void __launch_bounds__(kTailThreads) k_vtail2d(TailArgs a) {
+// NR right-hand sides: vectors interleaved, NR values per node, operators
+// and weights shared.  BATCH: one CTA per problem, arguments from targs.
+template <typename T, int NR = 1, bool BATCH = false>
+__global__ void __launch_bounds__(kTailThreads) k_vtail2d(TailArgs a0, const TailArgs* __restrict__ targs) {
+    const TailArgs& a = BATCH ? targs[blockIdx.x] : a0;
     extern __shared__ unsigned char smem_raw[];
     __shared__ uint64_t bar;
     // per level: nodes per side and element offsets (from base) of A, P and
@@ -119,7 +110,7 @@ __global__ void __launch_bounds__(kTailThreads) k_vtail2d(TailArgs a) {
         const int v0 = q;
         for (int l = 0; l < L; l++) {
             s_oB[l] = q;
-            q += 3 * s_n[l] * s_n[l];
+            q += 3 * s_n[l] * s_n[l] * NR;
         }
         s_nvec = q - v0;
     }
@@ -135,9 +126,10 @@ __global__ void __launch_bounds__(kTailThreads) k_vtail2d(TailArgs a) {
         const int m = s_n[0];
         T* b = base + s_oB[0];
         const T* bg = (const T*)a.b0;
-        for (int k = tid; k < m * m; k += nth) {
-            const int j = k / m, i = k - j * m;
-            b[k] = bg[(long long)j * a.ld0 + i];
+        for (int k = tid; k < m * m * NR; k += nth) {
+            const int kn = k / NR, rh = k - kn * NR;
+            const int j = kn / m, i = kn - j * m;
+            b[k] = bg[((long long)j * a.ld0 + i) * NR + rh];
         }
     }
     const bool staged = mbar::wait(&bar, 0);
@@ -151,18 +143,19 @@ __global__ void __launch_bounds__(kTailThreads) k_vtail2d(TailArgs a) {
     __syncthreads();
 
     // off-diagonal part of row (i, j) of the level with operator A (row
-    // length m, plane stride m2) on iterate x, in the order of the streaming
-    // kernels (W, E, S, N, SW, NE, NW, SE)
-    auto offdiag = [&](const T* A, int m, int m2, const T* x, int i, int j) {
+    // length m, plane stride m2) on iterate x (NR values per node, right-hand
+    // side rh), in the order of the streaming kernels (W, E, S, N, SW, NE, NW, SE)
+    auto offdiag = [&](const T* A, int m, int m2, const T* x, int i, int j, int rh) {
         const int o = j * m + i;
-        T s = A[W2 * m2 + o] * x[o - 1];
-        s += A[W2 * m2 + o + 1] * x[o + 1];
-        s += A[S2 * m2 + o] * x[o - m];
-        s += A[S2 * m2 + o + m] * x[o + m];
-        s += A[SW2 * m2 + o] * x[o - m - 1];
-        s += A[SW2 * m2 + o + m + 1] * x[o + m + 1];
-        s += A[NW2 * m2 + o] * x[o + m - 1];
-        s += A[NW2 * m2 + o - m + 1] * x[o - m + 1];
+        auto X = [&](int q) { return x[q * NR + rh]; };
+        T s = A[W2 * m2 + o] * X(o - 1);
+        s += A[W2 * m2 + o + 1] * X(o + 1);
+        s += A[S2 * m2 + o] * X(o - m);
+        s += A[S2 * m2 + o + m] * X(o + m);
+        s += A[SW2 * m2 + o] * X(o - m - 1);
+        s += A[SW2 * m2 + o + m + 1] * X(o + m + 1);
+        s += A[NW2 * m2 + o] * X(o + m - 1);
+        s += A[NW2 * m2 + o - m + 1] * X(o - m + 1);
         return s;
     };
     // every interior node of colour c of level l
@@ -172,11 +165,12 @@ __global__ void __launch_bounds__(kTailThreads) k_vtail2d(TailArgs a) {
         // index of that parity i0, j0, and ni x nj such nodes
         const int i0 = 1 + ((c & 1) ^ 1), j0 = 1 + (((c >> 1) & 1) ^ 1);
         const int ni = (m - i0) / 2, nj = (m - j0) / 2;
-        for (int k = tid; k < ni * nj; k += nth) {
+        for (int kk = tid; kk < ni * nj * NR; kk += nth) {
+            const int k = kk / NR, rh = kk - k * NR;
             const int jj = k / ni, ii = k - jj * ni;
             const int i = i0 + 2 * ii, j = j0 + 2 * jj;
             const int o = j * m + i;
-            x[o] = tdiv<T>(f[o] - offdiag(A, m, m2, x, i, j), A[C2 * m2 + o]);
+            x[o * NR + rh] = tdiv<T>(f[o * NR + rh] - offdiag(A, m, m2, x, i, j, rh), A[C2 * m2 + o]);
         }
     };
 
@@ -193,50 +187,54 @@ __global__ void __launch_bounds__(kTailThreads) k_vtail2d(TailArgs a) {
         const int m2 = m * m, mc2 = mc * mc, nb = (m - 1) >> 1;
         const T* A = base + s_oA[l];
         const T* f = base + s_oB[l];
-        T* x = base + s_oB[l] + m2;
+        T* x = base + s_oB[l] + m2 * NR;
         // colours 0 and 1, one thread per colour-1 point (2I+1, 2J), J >= 1:
         // a colour-0 point sees only zero neighbours, x = f / a_c; the
         // thread stores the colour-0 point (2I, 2J) of its block
-        for (int k = tid; k < nb * (nb - 1); k += nth) {
+        for (int kk = tid; kk < nb * (nb - 1) * NR; kk += nth) {
+            const int k = kk / NR, rh = kk - k * NR;
             const int J = 1 + k / nb, I = k - (J - 1) * nb;
             const int o = 2 * J * m + 2 * I + 1;
-            const T xl = I >= 1 ? tdiv<T>(f[o - 1], A[C2 * m2 + o - 1]) : (T)0;
-            const T xr = I + 1 < nb ? tdiv<T>(f[o + 1], A[C2 * m2 + o + 1]) : (T)0;
+            const T xl = I >= 1 ? tdiv<T>(f[(o - 1) * NR + rh], A[C2 * m2 + o - 1]) : (T)0;
+            const T xr = I + 1 < nb ? tdiv<T>(f[(o + 1) * NR + rh], A[C2 * m2 + o + 1]) : (T)0;
             T sum = A[W2 * m2 + o] * xl;
             sum += A[W2 * m2 + o + 1] * xr;
-            if (I >= 1) x[o - 1] = xl;
-            x[o] = tdiv<T>(f[o] - sum, A[C2 * m2 + o]);
+            if (I >= 1) x[(o - 1) * NR + rh] = xl;
+            x[o * NR + rh] = tdiv<T>(f[o * NR + rh] - sum, A[C2 * m2 + o]);
         }
         __syncthreads();
         // colours 2 and 3, one thread per colour-3 point: the colour-2 row
         // neighbours (whose own row neighbours, colour 3, are still zero)
         // are formed in registers; the thread stores the left one and itself
-        auto c2val = [&](int o) {
+        auto c2val = [&](int o, int rh) {
+            auto X = [&](int q) { return x[q * NR + rh]; };
             T sum = A[W2 * m2 + o] * (T)0;
             sum += A[W2 * m2 + o + 1] * (T)0;
-            sum += A[S2 * m2 + o] * x[o - m];
-            sum += A[S2 * m2 + o + m] * x[o + m];
-            sum += A[SW2 * m2 + o] * x[o - m - 1];
-            sum += A[SW2 * m2 + o + m + 1] * x[o + m + 1];
-            sum += A[NW2 * m2 + o] * x[o + m - 1];
-            sum += A[NW2 * m2 + o - m + 1] * x[o - m + 1];
-            return tdiv<T>(f[o] - sum, A[C2 * m2 + o]);
+            sum += A[S2 * m2 + o] * X(o - m);
+            sum += A[S2 * m2 + o + m] * X(o + m);
+            sum += A[SW2 * m2 + o] * X(o - m - 1);
+            sum += A[SW2 * m2 + o + m + 1] * X(o + m + 1);
+            sum += A[NW2 * m2 + o] * X(o + m - 1);
+            sum += A[NW2 * m2 + o - m + 1] * X(o - m + 1);
+            return tdiv<T>(f[o * NR + rh] - sum, A[C2 * m2 + o]);
         };
-        for (int k = tid; k < nb * nb; k += nth) {
+        for (int kk = tid; kk < nb * nb * NR; kk += nth) {
+            const int k = kk / NR, rh = kk - k * NR;
+            auto X = [&](int q) { return x[q * NR + rh]; };
             const int J = k / nb, I = k - J * nb;
             const int o = (2 * J + 1) * m + 2 * I + 1;
-            const T xl = I >= 1 ? c2val(o - 1) : (T)0;
-            const T xr = I + 1 < nb ? c2val(o + 1) : (T)0;
+            const T xl = I >= 1 ? c2val(o - 1, rh) : (T)0;
+            const T xr = I + 1 < nb ? c2val(o + 1, rh) : (T)0;
             T sum = A[W2 * m2 + o] * xl;
             sum += A[W2 * m2 + o + 1] * xr;
-            sum += A[S2 * m2 + o] * x[o - m];
-            sum += A[S2 * m2 + o + m] * x[o + m];
-            sum += A[SW2 * m2 + o] * x[o - m - 1];
-            sum += A[SW2 * m2 + o + m + 1] * x[o + m + 1];
-            sum += A[NW2 * m2 + o] * x[o + m - 1];
-            sum += A[NW2 * m2 + o - m + 1] * x[o - m + 1];
-            if (I >= 1) x[o - 1] = xl;
-            x[o] = tdiv<T>(f[o] - sum, A[C2 * m2 + o]);
+            sum += A[S2 * m2 + o] * X(o - m);
+            sum += A[S2 * m2 + o + m] * X(o + m);
+            sum += A[SW2 * m2 + o] * X(o - m - 1);
+            sum += A[SW2 * m2 + o + m + 1] * X(o + m + 1);
+            sum += A[NW2 * m2 + o] * X(o + m - 1);
+            sum += A[NW2 * m2 + o - m + 1] * X(o - m + 1);
+            if (I >= 1) x[(o - 1) * NR + rh] = xl;
+            x[o * NR + rh] = tdiv<T>(f[o * NR + rh] - sum, A[C2 * m2 + o]);
         }
         __syncthreads();
         // residual and restriction, one thread per interior coarse node.
@@ -247,35 +245,37 @@ __global__ void __launch_bounds__(kTailThreads) k_vtail2d(TailArgs a) {
         // colour 3 none (so its weights are not needed)
         const T* P = base + s_oP[l];
         T* bc = base + s_oB[l + 1];
-        auto r1 = [&](int o) {   // colour 1 (odd i, even j)
-            T sum = A[S2 * m2 + o] * x[o - m];
-            sum += A[S2 * m2 + o + m] * x[o + m];
-            sum += A[SW2 * m2 + o] * x[o - m - 1];
-            sum += A[SW2 * m2 + o + m + 1] * x[o + m + 1];
-            sum += A[NW2 * m2 + o] * x[o + m - 1];
-            sum += A[NW2 * m2 + o - m + 1] * x[o - m + 1];
+        auto r1 = [&](int o, int rh) {   // colour 1 (odd i, even j)
+            auto X = [&](int q) { return x[q * NR + rh]; };
+            T sum = A[S2 * m2 + o] * X(o - m);
+            sum += A[S2 * m2 + o + m] * X(o + m);
+            sum += A[SW2 * m2 + o] * X(o - m - 1);
+            sum += A[SW2 * m2 + o + m + 1] * X(o + m + 1);
+            sum += A[NW2 * m2 + o] * X(o + m - 1);
+            sum += A[NW2 * m2 + o - m + 1] * X(o - m + 1);
             return -sum;
         };
-        auto r2 = [&](int o) {   // colour 2 (even i, odd j)
-            return -(A[W2 * m2 + o] * x[o - 1] + A[W2 * m2 + o + 1] * x[o + 1]);
+        auto r2 = [&](int o, int rh) {   // colour 2 (even i, odd j)
+            return -(A[W2 * m2 + o] * x[(o - 1) * NR + rh] + A[W2 * m2 + o + 1] * x[(o + 1) * NR + rh]);
         };
-        for (int k = tid; k < (mc - 2) * (mc - 2); k += nth) {
+        for (int kk = tid; kk < (mc - 2) * (mc - 2) * NR; kk += nth) {
+            const int k = kk / NR, rh = kk - k * NR;
             const int J = 1 + k / (mc - 2), I = 1 + k % (mc - 2);
             const int O = J * mc + I, o = 2 * J * m + 2 * I;
-            T b = -offdiag(A, m, m2, x, 2 * I, 2 * J);
-            b += P[PXR * mc2 + O - 1] * r1(o - 1);
-            b += P[PXL * mc2 + O] * r1(o + 1);
-            b += P[PYN * mc2 + O - mc] * r2(o - m);
-            b += P[PYS * mc2 + O] * r2(o + m);
-            bc[O] = b;
+            T b = -offdiag(A, m, m2, x, 2 * I, 2 * J, rh);
+            b += P[PXR * mc2 + O - 1] * r1(o - 1, rh);
+            b += P[PXL * mc2 + O] * r1(o + 1, rh);
+            b += P[PYN * mc2 + O - mc] * r2(o - m, rh);
+            b += P[PYS * mc2 + O] * r2(o + m, rh);
+            bc[O * NR + rh] = b;
         }
         __syncthreads();
     }
     // ---- coarsest: one unknown, exact in FP64
-    if (tid == 0) {
+    if (tid < NR) {
         const int m = s_n[L - 1];
         const int o = m + 1;
-        base[s_oB[L - 1] + 2 * m * m + o] = (T)((double)base[s_oB[L - 1] + o] / *a.a64c);
+        base[s_oB[L - 1] + (2 * m * m + o) * NR + tid] = (T)((double)base[s_oB[L - 1] + o * NR + tid] / *a.a64c);
     }
     __syncthreads();
     // ---- up: correction x_pre + P x_c, reverse colours 3..0
@@ -283,31 +283,33 @@ __global__ void __launch_bounds__(kTailThreads) k_vtail2d(TailArgs a) {
         const int m = s_n[l], mc = s_n[l + 1];
         const int m2 = m * m, mc2 = mc * mc, nb = (m - 1) >> 1;
         const T* P = base + s_oP[l];
-        const T* xc = base + s_oB[l + 1] + 2 * mc2;
-        const T* xpre = base + s_oB[l] + m2;
+        const T* xc = base + s_oB[l + 1] + 2 * mc2 * NR;
+        const T* xpre = base + s_oB[l] + m2 * NR;
         const T* A = base + s_oA[l];
         const T* f = base + s_oB[l];
-        T* x = base + s_oB[l] + 2 * m2;
+        T* x = base + s_oB[l] + 2 * m2 * NR;
         // corrected value of interior point (i, j); zero on the boundary
-        auto corr = [&](int i, int j) -> T {
+        auto corr = [&](int i, int j, int rh) -> T {
             if (i < 1 || j < 1 || i > m - 2 || j > m - 2) return (T)0;
             const int o = j * m + i;
             const int I = i >> 1, J = j >> 1, O = J * mc + I;
-            const T xp = xpre[o];
-            if (!(i & 1) && !(j & 1)) return xp + xc[O];
-            if (!(j & 1)) return xp + P[PXL * mc2 + O] * xc[O] + P[PXR * mc2 + O] * xc[O + 1];   // (2I+1, 2J)
-            return xp + P[PYS * mc2 + O] * xc[O] + P[PYN * mc2 + O] * xc[O + mc];              // (2I, 2J+1)
+            auto XC = [&](int q) { return xc[q * NR + rh]; };
+            const T xp = xpre[o * NR + rh];
+            if (!(i & 1) && !(j & 1)) return xp + XC(O);
+            if (!(j & 1)) return xp + P[PXL * mc2 + O] * XC(O) + P[PXR * mc2 + O] * XC(O + 1);   // (2I+1, 2J)
+            return xp + P[PYS * mc2 + O] * XC(O) + P[PYN * mc2 + O] * XC(O + mc);              // (2I, 2J+1)
         };
         // correction and colour 3, one thread per colour-3 point: its eight
         // corrected neighbours in registers; stores the corrected points of
         // its block and its own new value
-        for (int k = tid; k < nb * nb; k += nth) {
+        for (int kk = tid; kk < nb * nb * NR; kk += nth) {
+            const int k = kk / NR, rh = kk - k * NR;
             const int J = k / nb, I = k - J * nb;
             const int i = 2 * I + 1, j = 2 * J + 1, o = j * m + i;
-            const T w = corr(i - 1, j), e = corr(i + 1, j);
-            const T so = corr(i, j - 1), no = corr(i, j + 1);
-            const T sw = corr(i - 1, j - 1), ne = corr(i + 1, j + 1);
-            const T nw = corr(i - 1, j + 1), se = corr(i + 1, j - 1);
+            const T w = corr(i - 1, j, rh), e = corr(i + 1, j, rh);
+            const T so = corr(i, j - 1, rh), no = corr(i, j + 1, rh);
+            const T sw = corr(i - 1, j - 1, rh), ne = corr(i + 1, j + 1, rh);
+            const T nw = corr(i - 1, j + 1, rh), se = corr(i + 1, j - 1, rh);
             T sum = A[W2 * m2 + o] * w;
             sum += A[W2 * m2 + o + 1] * e;
             sum += A[S2 * m2 + o] * so;
@@ -316,10 +318,10 @@ __global__ void __launch_bounds__(kTailThreads) k_vtail2d(TailArgs a) {
             sum += A[SW2 * m2 + o + m + 1] * ne;
             sum += A[NW2 * m2 + o] * nw;
             sum += A[NW2 * m2 + o - m + 1] * se;
-            if (I >= 1 && J >= 1) x[o - m - 1] = sw;
-            if (J >= 1) x[o - m] = so;
-            if (I >= 1) x[o - 1] = w;
-            x[o] = tdiv<T>(f[o] - sum, A[C2 * m2 + o]);
+            if (I >= 1 && J >= 1) x[(o - m - 1) * NR + rh] = sw;
+            if (J >= 1) x[(o - m) * NR + rh] = so;
+            if (I >= 1) x[(o - 1) * NR + rh] = w;
+            x[o * NR + rh] = tdiv<T>(f[o * NR + rh] - sum, A[C2 * m2 + o]);
         }
         __syncthreads();
         for (int c = 2; c >= 0; c--) {
@@ -329,11 +331,12 @@ __global__ void __launch_bounds__(kTailThreads) k_vtail2d(TailArgs a) {
     }
     {
         const int m = s_n[0];
-        const T* x = base + s_oB[0] + 2 * m * m;
+        const T* x = base + s_oB[0] + 2 * m * m * NR;
         T* xg = (T*)a.x0;
-        for (int k = tid; k < (m - 2) * (m - 2); k += nth) {
+        for (int kk = tid; kk < (m - 2) * (m - 2) * NR; kk += nth) {
+            const int k = kk / NR, rh = kk - k * NR;
             const int j = 1 + k / (m - 2), i = 1 + k % (m - 2);
-            xg[(long long)j * a.ld0 + i] = x[j * m + i];
+            xg[((long long)j * a.ld0 + i) * NR + rh] = x[(j * m + i) * NR + rh];
         }
     }
 }
@@ -402,6 +405,40 @@ bmg_status tail_pack(Ctx& c) {
     return c.opts.precision == BMG_PREC_FP32 ? tail_pack_impl<float>(c) : tail_pack_impl<double>(c);
 }
 
+// Arguments of the tail kernel of an FP32 context whose first tail level
+// reads its right-hand side from b0 and writes its iterate to x0 (row
+// length ld0, nr values per node).
+bmg_status tail_args(const Ctx& c, const void* b0, void* x0, int ld0, KState* st, TailArgs* a) {
+    if (!c.tail_pack || c.opts.precision != BMG_PREC_FP32) return BMG_ERR_STATE;
+    const int t = tail_first_level(c);
+    *a = TailArgs{};
+    a->nlev = tail_sizes(c, t, a->ns);
+    a->pack = c.tail_pack;
+    a->pack_bytes = (unsigned)tail_pack_bytes(c);
+    a->b0 = b0;
+    a->x0 = x0;
+    a->ld0 = ld0;
+    const Level& C = c.lev[c.nlev - 1];
+    a->a64c = C.A64 + (long long)C2 * C.plane + C.ld + 1;
+    a->st = st;
+    return BMG_OK;
+}
+
+// Shared memory of the batched tail kernel for tail levels ns[0..L).
+size_t batch_tail_smem(const int* ns, int L) {
+    return 16 + tail_pack_bytes_of<float>(ns, L) + (size_t)tail_vec_elems(ns, L) * kBatchR * sizeof(float);
+}
+
+// One CTA per problem, kBatchR right-hand sides; args: device array of count
+// entries whose tails all have the sizes the smem bound was computed for.
+bmg_status batch_tail(const TailArgs* args, int count, size_t smem, cudaStream_t s) {
+    auto kern = k_vtail2d<float, kBatchR, true>;
+    if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
+        return BMG_ERR_DEVICE;
+    kern<<<count, kTailThreads, smem, s>>>(TailArgs{}, args);
+    return cudaGetLastError() == cudaSuccess ? BMG_OK : BMG_ERR_DEVICE;
+}
+
 // Levels t .. nlev-1 in one launch: reads lev[t].b, writes lev[t].r.
 bmg_status tail_vcycle(Ctx& c, int t) {
     const bool f32 = c.opts.precision == BMG_PREC_FP32;
@@ -421,12 +458,12 @@ bmg_status tail_vcycle(Ctx& c, int t) {
         if (cudaFuncSetAttribute(k_vtail2d<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
             cudaSuccess)
             return BMG_ERR_DEVICE;
-        k_vtail2d<float><<<1, kTailThreads, smem, c.stream>>>(a);
+        k_vtail2d<float><<<1, kTailThreads, smem, c.stream>>>(a, nullptr);
     } else {
         if (cudaFuncSetAttribute(k_vtail2d<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
             cudaSuccess)
             return BMG_ERR_DEVICE;
-        k_vtail2d<double><<<1, kTailThreads, smem, c.stream>>>(a);
+        k_vtail2d<double><<<1, kTailThreads, smem, c.stream>>>(a, nullptr);
     }
     c.launches++;
     BMG_CUDA(cudaGetLastError());
