@@ -89,6 +89,12 @@ typedef struct {
     int precision;    /* BMG_PREC_FP64 or BMG_PREC_FP32 */
     int outer;        /* BMG_OUTER_CG, BMG_OUTER_FLEXIBLE_CG or BMG_OUTER_REFINEMENT */
     int flags;        /* BMG_FLAG_* bits, 0 by default */
+    int max_rhs;      /* 1 (default) to 4: on a 2-D context with BMG_PREC_FP32,
+                         BMG_OUTER_REFINEMENT, the streaming kernels and n >= 65,
+                         values above 1 reserve workspace for solving up to 4
+                         right-hand sides together (bmg_solve with nrhs > 1:
+                         one stencil read per sweep for all of them); other
+                         contexts ignore it */
 } bmg_opts;
 
 typedef struct {
@@ -171,10 +177,17 @@ bmg_status bmg_vcycle(bmg_ctx* ctx, const double* r, double* z);
 /* Preconditioned CG, M = one V-cycle, until ||r_k|| <= tol ||b|| for the
    recursive and then the true residual (when only the recursive one
    passes, r is replaced by the true residual and CG continues), or maxit
-   iterations.  tol <= 0 runs exactly maxit iterations.  b, x: n^d doubles,
-   host or device; x holds the initial guess on entry and the iterate on
-   exit (also on BMG_ERR_NOT_CONVERGED).  info may be NULL. */
-bmg_status bmg_solve(bmg_ctx* ctx, const double* b, double* x, double tol, int maxit,
+   iterations.  tol <= 0 runs exactly maxit iterations.  nrhs >= 1
+   right-hand sides with the same operator (the solution phase of Sec. 2.2
+   applied to each): b, x: nrhs consecutive vectors of n^d doubles, host or
+   device; x holds the initial guesses on entry and the iterates on exit
+   (also on BMG_ERR_NOT_CONVERGED).  info: NULL or nrhs entries.  With
+   nrhs > 1 on a context created with max_rhs >= 2 (and eligible, see
+   bmg_opts), groups of up to max_rhs right-hand sides are solved together
+   (the lockstep refinement of bmg_batch_solve, tol > 0 required); otherwise
+   the right-hand sides are solved one after the other.  Returns the first
+   non-OK status. */
+bmg_status bmg_solve(bmg_ctx* ctx, int nrhs, const double* b, double* x, double tol, int maxit,
                      bmg_info* info);
 
 /* Solves count independent problems, nrhs right-hand sides each, to a
@@ -210,9 +223,11 @@ bmg_status bmg_solve_many(bmg_ctx* const* ctxs, int count, int nrhs, const doubl
    processed by one persistent launch that walks the class's work-list of
    (problem, level, tile) items; the levels n <= 33 of every problem run in
    one launch, one CTA per problem.  One inner iteration of the whole batch
-   is one CUDA graph (unless flags has BMG_FLAG_NO_GRAPHS).  Converged
-   systems stop updating; the slowest one sets the number of inner
-   iterations between refinements.  Right-hand sides of a problem are
+   is one CUDA graph (unless flags has BMG_FLAG_NO_GRAPHS).  Between two
+   FP64 residuals every active system takes the number of inner iterations
+   the single-problem refinement would give it and then freezes until the
+   run of the slowest one ends; converged systems stop updating.
+   Right-hand sides of a problem are
    interleaved in the batch's own storage (the caller's arrays keep their
    n x n layout). */
 typedef struct bmg_batch bmg_batch;   /* opaque */
@@ -265,10 +280,14 @@ void bmg_batch_destroy(bmg_batch* batch);
    L(u) of the solution u = A^-1 b: solves A lambda = dL/du with the same
    hierarchy (A is symmetric) and evaluates, per cell e,
    dLdkappa[e] = -lambda_e^T K_e^0 u_e, K_e^0 the element matrix at
-   kappa = 1.  (dL/db = lambda.)  u, dLdu, lambda: n^d doubles (device);
-   dLdkappa: (n-1)^d doubles (device); coords: the coordinates given to
-   bmg_assemble (device).  Needs a context built by bmg_assemble. */
-bmg_status bmg_adjoint_grad(bmg_ctx* ctx, const double* coords, const double* u,
+   kappa = 1.  (dL/db = lambda.)  nrhs >= 1 independent losses with the same
+   operator (their adjoint solves go through bmg_solve with nrhs, so they
+   share the stencil reads as bmg_solve describes): u, dLdu, lambda: nrhs
+   consecutive vectors of n^d doubles (device); dLdkappa: nrhs consecutive
+   arrays of (n-1)^d doubles (device); coords: the coordinates given to
+   bmg_assemble (device); info: NULL or nrhs entries.  Needs a context built
+   by bmg_assemble. */
+bmg_status bmg_adjoint_grad(bmg_ctx* ctx, int nrhs, const double* coords, const double* u,
                             const double* dLdu, double* lambda, double* dLdkappa,
                             double tol, int maxit, bmg_info* info);
 

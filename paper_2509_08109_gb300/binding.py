@@ -34,7 +34,7 @@ class BmgError(RuntimeError):
 
 class _Opts(ctypes.Structure):
     _fields_ = [("dim", ctypes.c_int), ("n", ctypes.c_int), ("precision", ctypes.c_int),
-                ("outer", ctypes.c_int), ("flags", ctypes.c_int)]
+                ("outer", ctypes.c_int), ("flags", ctypes.c_int), ("max_rhs", ctypes.c_int)]
 
 
 class _Info(ctypes.Structure):
@@ -81,8 +81,8 @@ def load() -> ctypes.CDLL:
         "bmg_set_stencil": ([P, P], I),
         "bmg_setup": ([P], I),
         "bmg_vcycle": ([P, P, P], I),
-        "bmg_solve": ([P, P, P, D, I, ctypes.POINTER(_Info)], I),
-        "bmg_adjoint_grad": ([P, P, P, P, P, P, D, I, ctypes.POINTER(_Info)], I),
+        "bmg_solve": ([P, I, P, P, D, I, P], I),
+        "bmg_adjoint_grad": ([P, I, P, P, P, P, P, D, I, P], I),
         "bmg_adjoint_cells": ([P, P, P, P, P], I),
         "bmg_solve_many": ([P, I, I, P, P, D, I, P], I),
         "bmg_levels": ([P], I),
@@ -316,14 +316,15 @@ class Solver:
 
     def __init__(self, dim: int, n: int, precision: str = "fp64", outer: str | None = None,
                  device=None, stream: torch.cuda.Stream | None = None, unfused: bool = False,
-                 graphs: bool = True):
+                 graphs: bool = True, max_rhs: int = 1):
         lib = load()
         self.dim, self.n, self.precision = dim, n, precision
         if outer is None:
             outer = "flexible" if precision == "fp32" else "cg"
         self.outer = outer
         self.device = torch.device(device) if device is not None else torch.device("cuda", torch.cuda.current_device())
-        opts = _Opts(dim, n, PREC[precision], OUTER[outer], (1 if unfused else 0) | (0 if graphs else 2))
+        opts = _Opts(dim, n, PREC[precision], OUTER[outer], (1 if unfused else 0) | (0 if graphs else 2),
+                     int(max_rhs))
         h = ctypes.c_void_p()
         _check(lib.bmg_create(ctypes.byref(opts), ctypes.byref(h)), "bmg_create")
         self._h = h
@@ -417,37 +418,53 @@ class Solver:
             _check(load().bmg_vcycle(self._h, _ptr(r), _ptr(out)), "bmg_vcycle")
         return out
 
+    def _nrhs_of(self, t: torch.Tensor) -> int:
+        if t.dim() == self.dim:
+            return 0
+        if t.dim() == self.dim + 1 and tuple(t.shape[1:]) == self.grid_shape:
+            return t.shape[0]
+        raise ValueError(f"expected shape {self.grid_shape} or (nrhs,) + {self.grid_shape}, got {tuple(t.shape)}")
+
     def solve(self, b, x0=None, tol: float = 1e-10, maxit: int = 500, out=None, raise_on_nonconv=True):
         """x such that ||b - A x|| <= tol ||b||.  b (and out) may live on the
-        host or the device; the result has b's device."""
+        host or the device; the result has b's device.  b of shape
+        (nrhs, n, ...) solves nrhs right-hand sides in one bmg_solve call
+        (together on a context created with max_rhs >= 2) and returns a
+        list of SolveInfo."""
         b = torch.as_tensor(b, dtype=torch.float64)
         b = b.contiguous() if b.device.type == "cpu" else self._dev(b)
+        nrhs = self._nrhs_of(b)
         if out is None:
             out = torch.zeros_like(b) if x0 is None else torch.as_tensor(x0, dtype=torch.float64).to(b.device).clone()
         elif x0 is not None:
             out.copy_(torch.as_tensor(x0))
         elif x0 is None:
             out.zero_()
-        info = _Info()
+        infos = (_Info * max(nrhs, 1))()
         with torch.cuda.device(self.device):
-            code = load().bmg_solve(self._h, _ptr(b), _ptr(out), float(tol), int(maxit), ctypes.byref(info))
+            code = load().bmg_solve(self._h, max(nrhs, 1), _ptr(b), _ptr(out), float(tol), int(maxit), infos)
         if code not in (0, 8) or (code == 8 and raise_on_nonconv):
             _check(code, "bmg_solve")
-        return out, SolveInfo(info.iterations, info.levels, info.relres, info.true_relres, info.rho,
-                              info.grid_complexity, info.operator_complexity, info.status, info.refinements)
+        res = [_info_of(i) for i in infos]
+        return out, (res if nrhs else res[0])
 
     def adjoint_grad(self, u, dLdu, tol: float = 1e-10, maxit: int = 500):
-        """(lambda, dL/dkappa per cell, info) for A lambda = dL/du."""
+        """(lambda, dL/dkappa per cell, info) for A lambda = dL/du; u and
+        dLdu of shape (nrhs, n, ...) give nrhs independent gradients (one
+        bmg_adjoint_grad call; info is then a list)."""
         u = self._dev(torch.as_tensor(u))
         g = self._dev(torch.as_tensor(dLdu))
+        nrhs = self._nrhs_of(g)
+        assert u.shape == g.shape, (u.shape, g.shape)
         lam = torch.zeros_like(g)
-        dk = torch.empty((self.n - 1,) * self.dim, dtype=torch.float64, device=self.device)
-        info = _Info()
+        cells = (self.n - 1,) * self.dim
+        dk = torch.empty(((nrhs,) if nrhs else ()) + cells, dtype=torch.float64, device=self.device)
+        infos = (_Info * max(nrhs, 1))()
         with torch.cuda.device(self.device):
-            _check(load().bmg_adjoint_grad(self._h, _ptr(self._coords), _ptr(u), _ptr(g), _ptr(lam), _ptr(dk),
-                                           float(tol), int(maxit), ctypes.byref(info)), "bmg_adjoint_grad")
-        return lam, dk, SolveInfo(info.iterations, info.levels, info.relres, info.true_relres, info.rho,
-                                  info.grid_complexity, info.operator_complexity, info.status)
+            _check(load().bmg_adjoint_grad(self._h, max(nrhs, 1), _ptr(self._coords), _ptr(u), _ptr(g), _ptr(lam),
+                                           _ptr(dk), float(tol), int(maxit), infos), "bmg_adjoint_grad")
+        res = [_info_of(i) for i in infos]
+        return lam, dk, (res if nrhs else res[0])
 
     def adjoint_cells(self, u, lam) -> torch.Tensor:
         """bmg_adjoint_cells: dL/dkappa per cell, -lambda_e^T K_e^0 u_e, for

@@ -85,7 +85,17 @@ size_t carve(Ctx& c, char* base) {
     c.st = (KState*)take(sizeof(KState));
     const size_t tp = tail_pack_bytes(c);
     c.tail_pack = tp ? take(tp) : nullptr;
+    c.mrhs_ws = c.mrhs_bytes ? take(c.mrhs_bytes) : nullptr;
     return align256(off);
+}
+
+// Drops the one-problem batch of several right-hand sides (its class views
+// and tile shapes follow the hierarchy, so it is rebuilt after a setup).
+void drop_mrhs(Ctx& c) {
+    if (c.mrhs) {
+        batch_destroy(c.mrhs);
+        c.mrhs = nullptr;
+    }
 }
 
 bmg_status read_state(Ctx& c, KState& h) {
@@ -350,6 +360,7 @@ void bmg_default_opts(bmg_opts* o) {
     o->precision = BMG_PREC_FP64;
     o->outer = BMG_OUTER_CG;
     o->flags = 0;
+    o->max_rhs = 1;
 }
 
 bmg_status bmg_create(const bmg_opts* opts, bmg_ctx** out) {
@@ -363,6 +374,7 @@ bmg_status bmg_create(const bmg_opts* opts, bmg_ctx** out) {
     if (opts->outer != BMG_OUTER_CG && opts->outer != BMG_OUTER_FLEXIBLE_CG && opts->outer != BMG_OUTER_REFINEMENT)
         return BMG_ERR_ARG;
     if (opts->outer == BMG_OUTER_REFINEMENT && opts->precision != BMG_PREC_FP32) return BMG_ERR_ARG;
+    if (opts->max_rhs < 0 || opts->max_rhs > kBatchR) return BMG_ERR_ARG;
     bmg_ctx* ctx = new (std::nothrow) bmg_ctx();
     if (!ctx) return BMG_ERR_ARG;
     Ctx& c = ctx->c;
@@ -385,6 +397,8 @@ bmg_status bmg_create(const bmg_opts* opts, bmg_ctx** out) {
         nl = (nl + 1) / 2;
     }
     c.nlev = l;
+    if (c.opts.max_rhs < 1) c.opts.max_rhs = 1;
+    c.mrhs_bytes = c.opts.max_rhs > 1 ? batch_single_bytes(c) : 0;
     c.ws_need = carve(c, nullptr);
     const long long rows = ipow(c.lev[0].n, c.dim - 1);
     c.red_blocks = (int)(rows > 152 * 8 ? 152 * 8 : rows);
@@ -405,6 +419,7 @@ bmg_status bmg_attach(bmg_ctx* ctx, void* ws, size_t bytes, void* stream) {
     if (bytes < c.ws_need) return BMG_ERR_WORKSPACE;
     if (!is_device_ptr(ws)) return BMG_ERR_ARG;
     BMG_CUDA(cudaGetDevice(&c.device));
+    drop_mrhs(c);
     c.stream = (cudaStream_t)stream;
     if (!c.st_host) BMG_CUDA(cudaMallocHost((void**)&c.st_host, sizeof(KState)));
     c.ws = (char*)ws;
@@ -486,6 +501,7 @@ bmg_status bmg_setup(bmg_ctx* ctx) {
     BMG_TRY(check_ready(ctx));
     Ctx& c = ctx->c;
     if (!c.have_op) return BMG_ERR_STATE;
+    drop_mrhs(c);
     BMG_TRY(reset_state(c));
     for (int l = 0; l < c.nlev - 1; l++) BMG_TRY(c.dim == 2 ? setup_level2d(c, l) : setup_level3d(c, l));
     BMG_TRY(demote_levels(c));
@@ -514,11 +530,12 @@ bmg_status bmg_vcycle(bmg_ctx* ctx, const double* r, double* z) {
     return BMG_OK;
 }
 
-bmg_status bmg_solve(bmg_ctx* ctx, const double* b, double* x, double tol, int maxit, bmg_info* info) {
-    BMG_TRY(check_ready(ctx));
-    if (!b || !x || maxit < 0) return BMG_ERR_ARG;
-    Ctx& c = ctx->c;
-    if (!c.have_setup) return BMG_ERR_STATE;
+}  // extern "C"
+
+namespace {
+
+// One right-hand side through the single-problem path.
+bmg_status solve_one(Ctx& c, const double* b, double* x, double tol, int maxit, bmg_info* info) {
     BMG_TRY(stage_in(c, b, c.bvec));
     BMG_TRY(stage_in(c, x, c.x));
     bmg_status st = pcg(c, tol, maxit, info);
@@ -528,22 +545,73 @@ bmg_status bmg_solve(bmg_ctx* ctx, const double* b, double* x, double tol, int m
     return st;
 }
 
-bmg_status bmg_adjoint_grad(bmg_ctx* ctx, const double* coords, const double* u, const double* dLdu,
+// nrhs right-hand sides b + r n^d: together (groups of max_rhs, the
+// one-problem batch) where the context has room for it, else in turn.
+bmg_status solve_rhs(Ctx& c, int nrhs, const double* b, double* x, double tol, int maxit, bmg_info* info) {
+    const long long nn = ipow(c.lev[0].n, c.dim);
+    bmg_status first = BMG_OK;
+    if (nrhs > 1 && c.mrhs_bytes && c.opts.max_rhs > 1 && tol > 0) {
+        if (!c.mrhs) {
+            BMG_TRY(batch_single_create(c, &c.mrhs));
+            const bmg_status a = batch_attach(*c.mrhs, c.mrhs_ws, c.mrhs_bytes, c.stream);
+            if (a != BMG_OK) {
+                drop_mrhs(c);
+                return a;
+            }
+        }
+        for (int r0 = 0; r0 < nrhs; r0 += c.opts.max_rhs) {
+            const int g = nrhs - r0 < c.opts.max_rhs ? nrhs - r0 : c.opts.max_rhs;
+            const double* bp[kBatchR];
+            double* xp[kBatchR];
+            for (int r = 0; r < g; r++) {
+                bp[r] = b + (r0 + r) * nn;
+                xp[r] = x + (r0 + r) * nn;
+            }
+            const bmg_status st = batch_solve(*c.mrhs, g, bp, xp, tol, maxit, info ? info + r0 : nullptr);
+            if (st == BMG_ERR_DEVICE || st == BMG_ERR_ARG) return st;
+            if (first == BMG_OK) first = st;
+        }
+        return first;
+    }
+    for (int r = 0; r < nrhs; r++) {
+        const bmg_status st = solve_one(c, b + r * nn, x + r * nn, tol, maxit, info ? info + r : nullptr);
+        if (st == BMG_ERR_DEVICE) return st;
+        if (first == BMG_OK) first = st;
+    }
+    return first;
+}
+
+}  // namespace
+
+extern "C" {
+
+bmg_status bmg_solve(bmg_ctx* ctx, int nrhs, const double* b, double* x, double tol, int maxit, bmg_info* info) {
+    BMG_TRY(check_ready(ctx));
+    if (!b || !x || maxit < 0 || nrhs < 1) return BMG_ERR_ARG;
+    Ctx& c = ctx->c;
+    if (!c.have_setup) return BMG_ERR_STATE;
+    return solve_rhs(c, nrhs, b, x, tol, maxit, info);
+}
+
+bmg_status bmg_adjoint_grad(bmg_ctx* ctx, int nrhs, const double* coords, const double* u, const double* dLdu,
                             double* lambda, double* dLdkappa, double tol, int maxit, bmg_info* info) {
     BMG_TRY(check_ready(ctx));
-    if (!coords || !u || !dLdu || !lambda || !dLdkappa) return BMG_ERR_ARG;
+    if (!coords || !u || !dLdu || !lambda || !dLdkappa || nrhs < 1) return BMG_ERR_ARG;
     Ctx& c = ctx->c;
     if (!c.have_setup || c.op_tensor) return BMG_ERR_STATE;
     if (!is_device_ptr(coords) || !is_device_ptr(u) || !is_device_ptr(dLdu) || !is_device_ptr(lambda) ||
         !is_device_ptr(dLdkappa))
         return BMG_ERR_ARG;
-    BMG_TRY(stage_in(c, dLdu, c.bvec));
-    BMG_CUDA(cudaMemsetAsync(c.x, 0, sizeof(double) * c.lev[0].plane, c.stream));
-    bmg_status st = pcg(c, tol, maxit, info);
-    if (st == BMG_ERR_DEVICE) return st;
-    BMG_TRY(stage_out(c, c.x, lambda));
-    BMG_TRY(c.dim == 2 ? adjoint_cells2d(c, coords, u, lambda, dLdkappa)
-                       : adjoint_cells3d(c, coords, u, lambda, dLdkappa));
+    const long long nn = ipow(c.lev[0].n, c.dim);
+    const long long ne = ipow(c.lev[0].n - 1, c.dim);
+    // A lambda = dL/du from a zero guess, for every right-hand side
+    BMG_CUDA(cudaMemsetAsync(lambda, 0, sizeof(double) * nn * nrhs, c.stream));
+    bmg_status st = solve_rhs(c, nrhs, dLdu, lambda, tol, maxit, info);
+    if (st == BMG_ERR_DEVICE || st == BMG_ERR_ARG) return st;
+    BMG_CUDA(cudaMemsetAsync(&c.st->err, 0, sizeof(c.st->err), c.stream));
+    for (int r = 0; r < nrhs; r++)
+        BMG_TRY(c.dim == 2 ? adjoint_cells2d(c, coords, u + r * nn, lambda + r * nn, dLdkappa + r * ne)
+                           : adjoint_cells3d(c, coords, u + r * nn, lambda + r * nn, dLdkappa + r * ne));
     KState h;
     BMG_TRY(read_state(c, h));
     if (h.err && st == BMG_OK) st = (bmg_status)h.err;
@@ -680,6 +748,7 @@ long long bmg_launch_count(const bmg_ctx* ctx) { return ctx ? ctx->c.launches : 
 
 void bmg_destroy(bmg_ctx* ctx) {
     if (!ctx) return;
+    drop_mrhs(ctx->c);
     for (int p = 0; p < 2; p++)
         if (ctx->c.it_exec[p]) cudaGraphExecDestroy(ctx->c.it_exec[p]);
     if (ctx->c.cap_stream) cudaStreamDestroy(ctx->c.cap_stream);

@@ -1349,7 +1349,7 @@ bmg_status apply_ptap(bmg_aux& x, const double* q, double* v) {
 bmg_status coarse_solve(bmg_aux& x, const double* b, double* w, double tol) {
     BMG_CUDA(cudaMemsetAsync(w, 0, sizeof(double) * (size_t)x.n * x.n, x.coarse->c.stream));
     bmg_info info;
-    return bmg_solve(x.coarse, b, w, tol, 2000, &info);
+    return bmg_solve(x.coarse, 1, b, w, tol, 2000, &info);
 }
 
 }  // namespace

@@ -22,8 +22,11 @@
 // update x += alpha p, r -= alpha q.  That sequence is captured once as a
 // CUDA graph (per parity of the alternating z buffers) and replayed.  All
 // systems iterate in lockstep; between refinements the host reads every
-// system's FP64 residual, retires the converged ones (their updates stop)
-// and sizes the next inner run from the slowest active system.
+// system's FP64 residual, retires the converged ones, and gives every
+// active system its own number of inner iterations for the next run (the
+// single-problem rule); the run lasts as long as the largest, and a system
+// whose count is used up freezes (no further updates) until the next
+// refinement.
 //
 // Reductions are deterministic: per-tile partial sums, summed in a fixed
 // order by the last CTA of each problem (arrival counter per problem).
@@ -397,8 +400,9 @@ __global__ void __launch_bounds__(kBThreads) k_bpspmv(const BProbDev* __restrict
     s = block_sum_r(s, red);
     if (threadIdx.x < R) {
         SysState& sy = sys[(long long)it.prob * R + threadIdx.x];
+        const bool live = sy.active && sy.left > 0;
         sy.pq = s;
-        if (!sy.active || sy.rz == 0.0) {
+        if (!live || sy.rz == 0.0) {
             sy.alpha = 0.0;
         } else if (!(s > 0.0)) {
             set_err(st, BMG_ERR_NOT_SPD);
@@ -406,20 +410,21 @@ __global__ void __launch_bounds__(kBThreads) k_bpspmv(const BProbDev* __restrict
         } else {
             sy.alpha = sy.rz / s;
         }
+        if (live) sy.left--;
     }
     if (threadIdx.x == 0) counters[it.prob] = 0u;
 }
 
 // x += alpha p straight into the FP64 iterate, r -= alpha q in FP32, for the
-// active systems of problem blockIdx.y.
+// systems of problem blockIdx.y that took this iteration (alpha != 0).
 __global__ void __launch_bounds__(kBThreads) k_bupdate(const BProbDev* __restrict__ probs, int parity,
                                                        const SysState* __restrict__ sys) {
     const int pi = blockIdx.y;
     const BProbDev P = probs[pi];
     const int rh = threadIdx.x % R;
     const SysState& sy = sys[(long long)pi * R + rh];
-    if (!sy.active) return;
     const double alpha = sy.alpha;
+    if (!sy.active || alpha == 0.0) return;     // frozen systems take no update
     const float a32 = (float)alpha;
     const float* p = P.p[parity];
     const long long tot = P.plane * R;
@@ -480,6 +485,7 @@ struct Batch {
     long long exec_kernels[2] = {0, 0};
     long long launches = 0;
     bool use_graphs = true;
+    bool alias = false;                 // one problem: the classes view the context's own FP32 levels
 };
 
 namespace {
@@ -503,8 +509,10 @@ size_t carve_batch(Batch& B, char* base) {
     for (BClass& K : B.cls) {
         const long long nm = (long long)K.prob.size();
         if (!K.tail) {
-            K.A = (float*)take(sizeof(float) * NS2 * K.plane * nm);
-            K.P = (float*)take(sizeof(float) * NP2 * K.cplane * nm);
+            if (!B.alias) {
+                K.A = (float*)take(sizeof(float) * NS2 * K.plane * nm);
+                K.P = (float*)take(sizeof(float) * NP2 * K.cplane * nm);
+            }
             K.xp = (float*)take(sizeof(float) * R * K.plane * nm);
         }
         K.b = (float*)take(sizeof(float) * R * K.plane * nm);
@@ -744,12 +752,21 @@ bmg_status read_sys(Batch& B) {
 }  // namespace
 
 // ---------------------------------------------------------------- entry points
-bmg_status batch_create(int count, Ctx* const* ctxs, int flags, Batch** out) {
+// Eligibility of a context from its options and shape alone.
+bool batch_eligible_shape(const Ctx& c) {
+    return c.dim == 2 && c.opts.precision == BMG_PREC_FP32 && c.opts.outer == BMG_OUTER_REFINEMENT &&
+           !(c.opts.flags & BMG_FLAG_UNFUSED) && c.nlev >= 2 && c.lev[0].n >= 65;
+}
+
+// sizing: lay out from the contexts' shapes only (no attach or setup needed).
+bmg_status batch_build(int count, Ctx* const* ctxs, int flags, bool sizing, bool alias, Batch** out) {
     *out = nullptr;
     if (count < 1) return BMG_ERR_ARG;
+    if (alias && count != 1) return BMG_ERR_ARG;
     Batch* B = new (std::nothrow) Batch();
     if (!B) return BMG_ERR_ARG;
     B->count = count;
+    B->alias = alias;
     B->use_graphs = !(flags & BMG_FLAG_NO_GRAPHS);
     B->ctx.assign(ctxs, ctxs + count);
     B->cls_of.assign((size_t)count * kMaxLevels, -1);
@@ -763,12 +780,12 @@ bmg_status batch_create(int count, Ctx* const* ctxs, int flags, Batch** out) {
     std::vector<int> sizes;
     for (int p = 0; p < count; p++) {
         const Ctx* c = ctxs[p];
-        if (!c || !c->attached) return fail(BMG_ERR_ARG);
-        if (!c->have_setup) return fail(BMG_ERR_STATE);
-        if (c->dim != 2 || c->opts.precision != BMG_PREC_FP32 || c->opts.outer != BMG_OUTER_REFINEMENT ||
-            !c->use_fused || !c->tail_pack || c->lev[0].n < 65)
-            return fail(BMG_ERR_ARG);
-        if (p > 0 && c->device != ctxs[0]->device) return fail(BMG_ERR_ARG);
+        if (!c || !batch_eligible_shape(*c)) return fail(BMG_ERR_ARG);
+        if (!sizing) {
+            if (!c->attached || !c->use_fused || !c->tail_pack) return fail(BMG_ERR_ARG);
+            if (!c->have_setup) return fail(BMG_ERR_STATE);
+            if (p > 0 && c->device != ctxs[0]->device) return fail(BMG_ERR_ARG);
+        }
         const int t = tail_first_level(*c);
         if (c->lev[t].n != kTailMaxN) return fail(BMG_ERR_SHAPE);
         for (int l = 0; l < t; l++)
@@ -840,7 +857,28 @@ bmg_status batch_create(int count, Ctx* const* ctxs, int flags, Batch** out) {
     return BMG_OK;
 }
 
+bmg_status batch_create(int count, Ctx* const* ctxs, int flags, Batch** out) {
+    return batch_build(count, ctxs, flags, false, false, out);
+}
+
 size_t batch_ws_bytes(const Batch& B) { return B.ws_need; }
+
+// Workspace of the one-problem batch a context uses for several right-hand
+// sides (0 if the context is not eligible); shapes only.
+size_t batch_single_bytes(Ctx& c) {
+    if (!batch_eligible_shape(c)) return 0;
+    Ctx* cs[1] = {&c};
+    Batch* B = nullptr;
+    if (batch_build(1, cs, c.opts.flags, true, true, &B) != BMG_OK) return 0;
+    const size_t n = B->ws_need;
+    delete B;
+    return n;
+}
+
+bmg_status batch_single_create(Ctx& c, Batch** out) {
+    Ctx* cs[1] = {&c};
+    return batch_build(1, cs, c.opts.flags, false, true, out);
+}
 
 bmg_status batch_attach(Batch& B, void* ws, size_t bytes, void* stream) {
     if (!ws || ((uintptr_t)ws & 255) != 0) return BMG_ERR_ARG;
@@ -856,9 +894,16 @@ bmg_status batch_attach(Batch& B, void* ws, size_t bytes, void* stream) {
     if (!B.sys_h) BMG_CUDA(cudaMallocHost((void**)&B.sys_h, sizeof(SysState) * B.count * R));
     if (!B.st_h) BMG_CUDA(cudaMallocHost((void**)&B.st_h, sizeof(KState)));
     BMG_CUDA(cudaMemsetAsync(B.ws, 0, B.ws_need, B.stream));
-    // class copies of the FP32 operators and weights, in member order
+    // class copies of the FP32 operators and weights, in member order (one
+    // problem: the classes view the context's own levels)
     for (BClass& K : B.cls) {
         if (K.tail) continue;
+        if (B.alias) {
+            const Level& L = B.ctx[0]->lev[K.level[0]];
+            K.A = L.A32;
+            K.P = L.P32;
+            continue;
+        }
         for (size_t m = 0; m < K.prob.size(); m++) {
             const Ctx& c = *B.ctx[K.prob[m]];
             const Level& L = c.lev[K.level[m]];
@@ -1063,9 +1108,11 @@ bmg_status batch_solve(Batch& B, int nrhs, const double* const* b, double* const
     }
     bmg_status first_err = BMG_OK;
     int global_it = 0;
+    std::vector<int> m_of(S, 0);
     while (true) {
         int m_need = 0;
         for (int s = 0; s < S; s++) {
+            m_of[s] = 0;
             if (!act[s]) continue;
             const double lim = tol * tol * bb[s];
             if (rr[s] <= lim) {
@@ -1083,10 +1130,14 @@ bmg_status batch_solve(Batch& B, int nrhs, const double* const* b, double* const
             if (m < 2) m = 2;
             if (m > kMaxInner) m = kMaxInner;
             if (m > maxit - it[s]) m = maxit - it[s];
+            m_of[s] = m;
             m_need = std::max(m_need, m);
         }
         if (m_need == 0) break;
-        for (int s = 0; s < S; s++) B.sys_h[s].active = act[s];
+        for (int s = 0; s < S; s++) {
+            B.sys_h[s].active = act[s];
+            B.sys_h[s].left = act[s] ? m_of[s] : 0;
+        }
         BMG_CUDA(cudaMemcpyAsync(B.sys, B.sys_h, sizeof(SysState) * S, cudaMemcpyHostToDevice, B.stream));
         for (int k = 0; k < m_need; k++) BMG_TRY(run_iteration(B, (global_it + k) & 1));
         global_it += m_need;
@@ -1098,13 +1149,13 @@ bmg_status batch_solve(Batch& B, int nrhs, const double* const* b, double* const
         }
         for (int s = 0; s < S; s++) {
             if (!act[s]) continue;
-            const int m = std::min(m_need, maxit - it[s]);
+            const int m = m_of[s];
             it[s] += m;
             refs[s]++;
             const double nr = B.sys_h[s].rr;
             const double red = sqrt(nr / rr[s]);
             if (red > 0 && red < 1) {
-                const double r1 = pow(red, 1.0 / m_need);
+                const double r1 = pow(red, 1.0 / m);
                 if (r1 > 0.02 && r1 < 0.999) rho[s] = r1;
             }
             rr[s] = nr;

@@ -69,6 +69,8 @@ struct SysState {
     double alpha, beta;
     int first;        // 1: the next inner iteration takes p = z
     int active;       // 0: converged, zero right-hand side or out of iterations: no updates
+    int left;         // inner iterations this system still takes in the current run (its own
+                      // count, as the single-problem refinement sizes it); at 0 it freezes
 };
 
 // Right-hand sides per problem and row pairs per step of the batched
@@ -95,6 +97,8 @@ struct ProfSlot {
     int used = 0;
     double bytes = 0.0;
 };
+
+struct Batch;
 
 struct Ctx {
     bmg_opts opts{};
@@ -136,6 +140,11 @@ struct Ctx {
     // objects capture around this context's kernels compare it
     unsigned long long shape_epoch = 0;
     FusedLevel fused[kMaxLevels];
+    // several right-hand sides (opts.max_rhs > 1 on an eligible context): a
+    // one-problem batch in a reserved part of the workspace, built on first use
+    Batch* mrhs = nullptr;
+    char* mrhs_ws = nullptr;
+    size_t mrhs_bytes = 0;
 };
 
 // Event brackets around profiled launches (finest level only).
@@ -299,6 +308,13 @@ bmg_status assemble_export2d(int n, int ld, long long pl, const double* coords, 
                              KState* st, double* out, cudaStream_t s);
 bmg_status assemble_export3d(int n, int ld, long long pl, const double* coords, const double* kappa, double* A,
                              KState* st, double* out, cudaStream_t s);
+// batch2d.cu
+bmg_status batch_attach(Batch& B, void* ws, size_t bytes, void* stream);
+bmg_status batch_solve(Batch& B, int nrhs, const double* const* b, double* const* x, double tol, int maxit,
+                       bmg_info* infos);
+void batch_destroy(Batch* B);
+size_t batch_single_bytes(Ctx& c);
+bmg_status batch_single_create(Ctx& c, Batch** out);
 // vcycle.cu: z = M r on the finest level (FP64 in/out, internal layout)
 bmg_status vcycle(Ctx& c, const double* r, double* z);
 // fused2d.cu / tmaps.cu

@@ -759,13 +759,16 @@ __global__ void __launch_bounds__((WC + 8) * K * NR, sizeof(T) == 4 ? 3 : 1)
                 block_sum2(v1, v2, t1, t2);
                 if (tid < NR) {
                     SysState& sy = p.sys[(long long)M->prob * NR + tid];
-                    if (sy.first || !sy.active || !(sy.rz != 0.0)) {
+                    const bool live = sy.active && sy.left > 0;
+                    if (live && sy.first) {
                         sy.beta = 0.0;
                         sy.first = 0;
+                    } else if (!live || !(sy.rz != 0.0)) {
+                        sy.beta = 0.0;
                     } else {
                         sy.beta = (t1 - t2) / sy.rz;
                     }
-                    if (sy.active) sy.rz = t1;
+                    if (live) sy.rz = t1;
                 }
                 if (tid == 0) p.counters[M->prob] = 0u;
             }

@@ -75,11 +75,11 @@ def test_workspace_fp32_larger_than_fp64(lib):
 
 
 def test_calls_before_attach_are_rejected(lib):
-    opts = binding._Opts(2, 17, 0, 0, 0)
+    opts = binding._Opts(2, 17, 0, 0, 0, 1)
     h = ctypes.c_void_p()
     assert lib.bmg_create(ctypes.byref(opts), ctypes.byref(h)) == 0
     assert lib.bmg_setup(h) == 4            # no workspace
-    assert lib.bmg_solve(h, None, None, ctypes.c_double(1e-10), 10, None) == 4
+    assert lib.bmg_solve(h, 1, None, None, ctypes.c_double(1e-10), 10, None) == 4
     assert lib.bmg_create(None, ctypes.byref(h)) == 1
     assert lib.bmg_status_str(6).decode().startswith("setup breakdown")
     lib.bmg_destroy(h)
@@ -129,3 +129,26 @@ def test_aux_defaults_and_null_arguments(lib):
     assert lib.bmg_aux_solve(None, None, None, 1e-10, 10, None) == 1
     g = ctypes.c_double()
     assert lib.bmg_aux_estimate_gamma(None, 12, None, 1e-10, ctypes.byref(g), None, None, None) == 1
+
+
+def test_max_rhs_reserves_workspace_only_where_eligible(lib):
+    """max_rhs > 1 adds room for solving right-hand sides together on a 2-D
+    FP32 refinement-mode context with n >= 65, and nothing elsewhere; values
+    outside 0..4 are refused."""
+    def ws(dim, n, prec, outer, max_rhs):
+        opts = binding._Opts(dim, n, prec, outer, 0, max_rhs)
+        h = ctypes.c_void_p()
+        assert lib.bmg_create(ctypes.byref(opts), ctypes.byref(h)) == 0
+        nb = ctypes.c_size_t()
+        assert lib.bmg_workspace_bytes(h, ctypes.byref(nb)) == 0
+        lib.bmg_destroy(h)
+        return nb.value
+    assert ws(2, 129, 1, 2, 4) > ws(2, 129, 1, 2, 1)
+    assert ws(2, 129, 1, 2, 1) == ws(2, 129, 1, 2, 0)
+    assert ws(2, 129, 0, 0, 4) == ws(2, 129, 0, 0, 1)       # FP64: right-hand sides in turn
+    assert ws(3, 33, 1, 2, 4) == ws(3, 33, 1, 2, 1)         # 3-D
+    assert ws(2, 33, 1, 2, 4) == ws(2, 33, 1, 2, 1)         # below the streamed sizes
+    for bad in (-1, 5):
+        opts = binding._Opts(2, 129, 1, 2, 0, bad)
+        h = ctypes.c_void_p()
+        assert lib.bmg_create(ctypes.byref(opts), ctypes.byref(h)) == 1

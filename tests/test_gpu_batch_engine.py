@@ -151,3 +151,56 @@ def test_batch_engine_rejects_ineligible_contexts():
     s2.assemble(torch.as_tensor(q.coords), torch.as_tensor(q.kappa)).setup()
     with pytest.raises(binding.BmgError):
         binding.Batch([s2])
+
+
+@pytest.mark.parametrize("n,nrhs,max_rhs", [(129, 4, 4), (257, 3, 4), (129, 6, 4), (65, 2, 1)])
+def test_bmg_solve_with_several_right_hand_sides(n, nrhs, max_rhs):
+    """bmg_solve with nrhs > 1: solved together (max_rhs >= 2; six right-hand
+    sides go as groups of four and two) or in turn (max_rhs 1); every
+    solution against the single-right-hand-side solve and the oracle's
+    operator."""
+    p = inputs.bump_batch(count=1, kmin=7, kmax=7, nrhs=nrhs, seed=n)[0] if n == 129 else None
+    if p is None:
+        k = {65: 6, 257: 8}[n]
+        p = inputs.bump_batch(count=1, kmin=k, kmax=k, nrhs=nrhs, seed=n)[0]
+    s = binding.Solver(2, n, precision="fp32", outer="refine", max_rhs=max_rhs)
+    s.assemble(torch.as_tensor(p.coords), torch.as_tensor(p.kappa)).setup()
+    b = torch.as_tensor(p.rhs, device="cuda").contiguous()
+    x, infos = s.solve(b, tol=1e-10)
+    torch.cuda.synchronize()
+    assert len(infos) == nrhs
+    A = oracle.assemble(p.coords, p.kappa)
+    for r in range(nrhs):
+        assert infos[r].true_relres <= 1e-10
+        assert _true_relres(A, x[r].cpu().numpy(), p.rhs[r]) <= 1.01e-10
+        x1, _ = s.solve(b[r], tol=1e-10)
+        assert float((x[r] - x1).norm() / x1.norm()) <= 1e-8
+    # host buffers through the same call
+    xh, _ = s.solve(b.cpu(), tol=1e-10)
+    assert xh.device.type == "cpu"
+    assert float((xh - x.cpu()).norm() / x.norm()) <= 1e-12
+
+
+def test_adjoint_grad_with_several_right_hand_sides():
+    """bmg_adjoint_grad with nrhs = 3 against three single calls and the
+    oracle's contraction of the oracle's solves.  The adjoint solves ask for
+    1e-12: on this smooth adjoint right-hand side the FP32-preconditioned
+    refinement reaches about 3e-13 and no further (an inner FP32 CG run on a
+    residual at that floor breaks down, on the single-problem path alike)."""
+    n = 129
+    p = inputs.bump_batch(count=1, kmin=7, kmax=7, nrhs=3, seed=4)[0]
+    s = binding.Solver(2, n, precision="fp32", outer="refine", max_rhs=4)
+    s.assemble(torch.as_tensor(p.coords), torch.as_tensor(p.kappa)).setup()
+    f = torch.as_tensor(p.rhs, device="cuda").contiguous()
+    u, _ = s.solve(f, tol=1e-13, maxit=600)
+    g = (u - 0.3 * f).contiguous()
+    lam, dk, infos = s.adjoint_grad(u, g, tol=1e-12, maxit=600)
+    assert lam.shape == f.shape and dk.shape == (3, n - 1, n - 1) and len(infos) == 3
+    H = oracle.Hierarchy(oracle.assemble(p.coords, p.kappa))
+    for r in range(3):
+        l1, d1, _ = s.adjoint_grad(u[r], g[r], tol=1e-12, maxit=600)
+        assert float((dk[r] - d1).norm() / d1.norm()) <= 1e-8
+        uo = H.pcg(p.rhs[r], tol=1e-13, maxit=300)[0]
+        lo = H.pcg(uo - 0.3 * p.rhs[r], tol=1e-13, maxit=300)[0]
+        go = oracle.adjoint_grad(p.coords, uo, lo)
+        assert relerr(dk[r].cpu().numpy(), go) <= 1e-8
