@@ -49,6 +49,9 @@ def parse():
     ap.add_argument("--n", type=int, default=4097)
     ap.add_argument("--cpu-sample-n", type=int, default=1025)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-configs", action="store_true",
+                    help="skip the compact runs of the other configurations (65^2 annulus, 257^3 shell, "
+                         "512-problem batch, 1025^2 adjoint batch) that the default line carries")
     ap.add_argument("--no-autotune", action="store_true",
                     help="keep the occupancy-model tile shapes instead of the device-timed ones")
     ap.add_argument("--no-graphs", action="store_true",
@@ -93,6 +96,7 @@ class Clocks:
         self.index = index
         self.proc = None
         self.path = None
+        self.result = None
 
     def start(self):
         try:
@@ -275,6 +279,7 @@ def run_own(args):
     # iteration graphs, so each launch can be bracketed)
     _, _, _, profir, _ = timed(sir, args.steps, profile=True)
     _, _, _, proff, _ = timed(s32, args.steps, profile=True)
+    _, _, _, prof64, _ = timed(s64, max(1, min(args.steps, 3)), profile=True)
     assert all(i.true_relres <= TOL for i in infosir + infosf + infos64)
     variants = {"refine": (msir, launchesir, infosir, profir, ckir, sir),
                 "flexible": (msf, launchesf, infosf, proff, ckf, s32)}
@@ -336,12 +341,91 @@ def run_own(args):
                         "fp32_flexible": {"assemble": asm32, "setup": set32},
                         "fp64": {"assemble": asm64, "setup": set64}},
            "roofline": roof, "kernel_classes_finest_level": kclasses, "clocks": ck}
+    out["fp64"]["roofline"] = fp64_roofline(prof64, max(1, min(args.steps, 3)), dof)
+    del sir, s32, s64
+    torch.cuda.empty_cache()
+    if rank == 0 and world == 1 and not args.no_configs:
+        out["configs"] = other_configs(args)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline(args.cpu_sample_n)
     if rank == 0:
         print(json.dumps(out), flush=True)
     if world > 1:
         dist.destroy_process_group()
+
+
+# FP64 floating-point operations per interior node of one launch of each
+# finest-level class of the plain FP64 solve, counted by ncu
+# (smsp__sass_thread_inst_executed_op_{dfma,dmul,dadd}_pred_on, an FMA as two)
+# on the 2049^2 annulus: profiles/vdown64_annulus2049_fp64.md.  The FP64
+# kernels of this path are bound by the FP64 rate rather than by HBM; their
+# roofline is the FP64 peak.
+FP64_FLOPS_PER_NODE = {"vdown": 36.81, "spmv": 19.45, "update": 6.52}
+# GB300 FP64 (non-tensor) peak, nominal: 1.25 TFLOP/s
+FP64_PEAK_GFLOPS = 1250.0
+
+
+def fp64_roofline(prof, steps, dof):
+    """Per finest-level class of the FP64 solve: time per solve, algorithmic
+    bytes against the HBM peak and, where the FP64 operation count per node
+    was measured, FLOP/s against the FP64 peak; the dominant class names the
+    bound that is nearer."""
+    if not prof:
+        return None
+    hbm, kind = peaks()
+    classes = {}
+    for k, (kms, nl, kbytes) in prof.items():
+        gbs = kbytes / (kms * 1e-3) / 1e9
+        e = {"ms_per_solve": round(kms / steps, 4), "launches": nl, "GB/s": round(gbs, 1),
+             "hbm_frac": round(gbs / hbm, 4)}
+        if k in FP64_FLOPS_PER_NODE:
+            gfl = FP64_FLOPS_PER_NODE[k] * dof * nl / (kms * 1e-3) / 1e9
+            e["GFLOP/s"] = round(gfl, 1)
+            e["fp64_frac"] = round(gfl / FP64_PEAK_GFLOPS, 4)
+        classes[k] = e
+    dom = max(prof, key=lambda k: prof[k][0])
+    d = classes[dom]
+    if "fp64_frac" in d and d["fp64_frac"] > d["hbm_frac"]:
+        roof = {"bound": "alu", "kernel": dom, "achieved": d["GFLOP/s"], "peak": FP64_PEAK_GFLOPS,
+                "unit": "GFLOP/s", "frac": d["fp64_frac"], "peak_source": "nominal FP64 rate (1.25 TFLOP/s)"}
+    else:
+        roof = {"bound": "hbm", "kernel": dom, "achieved": d["GB/s"], "peak": hbm, "unit": "GB/s",
+                "frac": d["hbm_frac"], "peak_source": f"{kind} hbm_gbs"}
+    roof["classes"] = classes
+    return roof
+
+
+def other_configs(args) -> dict:
+    """Compact runs of the other configurations, each with its clocks, so
+    that one default bench line carries every configuration's number."""
+    from paper_2509_08109_gb300 import inputs as _inp
+    out = {}
+
+    def keep(r, extra=()):
+        d = {k: r.get(k) for k in ("value", "unit", "ms_per_step", "steps", "warmup", "headline_variant",
+                                    "fp32_over_fp64", "clocks", "gpu_launches") if k in r}
+        d["workload"] = r["config"]["workload"]
+        for k in extra:
+            if k in r:
+                d[k] = r[k]
+        return d
+
+    r1 = run_single(args, 2, 65, _inp.annulus_plain(65), "quarter_annulus_plain_n65", steps=10, warmup=3, emit=False)
+    out["annulus65_plain"] = keep(r1)
+    out["annulus65_plain"]["variants"] = {k: {"value": v["value"], "ms_per_step": v["ms_per_step"],
+                                              "iterations": v["iterations"]} for k, v in r1["variants"].items()}
+    r3 = run_single(args, 3, 257, _inp.shell_two_layer(257), "shell_octant_two_layer_n257", steps=1, warmup=1,
+                    emit=False)
+    out["shell257"] = keep(r3)
+    out["shell257"]["variants"] = {k: {"value": v["value"], "ms_per_step": v["ms_per_step"],
+                                       "iterations": v["iterations"], "clocks": v["clocks"]}
+                                   for k, v in r3["variants"].items()}
+    r4 = run_batch(args, steps=2, warmup=1, emit=False)
+    out["batch512x4"] = keep(r4, ("e2e", "iterations_min_max", "worst_true_relres"))
+    r5 = run_adjoint(args, steps=2, warmup=1, emit=False)
+    out["adjoint1025x8"] = keep(r5, ("fp64_serial", "grad_rel_diff_between_legs"))
+    out["adjoint1025x8"]["metric"] = r5["metric"]
+    return out
 
 
 # ---------------------------------------------------------------- reference arm
@@ -376,7 +460,7 @@ def run_reference(args):
 
 
 # ---------------------------------------------------------------- other workloads
-def _timed_solves(torch, s, f, steps, warmup, tol=TOL, maxit=500):
+def _timed_solves(torch, s, f, steps, warmup, tol=TOL, maxit=500, clocks=None):
     x = torch.zeros_like(f)
     for _ in range(warmup):
         s.solve(f, tol=tol, out=x, maxit=maxit)
@@ -385,23 +469,31 @@ def _timed_solves(torch, s, f, steps, warmup, tol=TOL, maxit=500):
     a = torch.cuda.Event(enable_timing=True)
     b = torch.cuda.Event(enable_timing=True)
     infos = []
-    a.record()
+    if clocks:
+        clocks.start()
+    a.record(s.stream)
     for _ in range(steps):
         _, info = s.solve(f, tol=tol, out=x, maxit=maxit)
         infos.append(info)
-    b.record()
+    b.record(s.stream)
     torch.cuda.synchronize()
+    if clocks:
+        clocks.result = clocks.stop()
     return a.elapsed_time(b) / steps, s.launches - l0, infos
 
 
-def run_single(args, dim, n, problem, name):
-    """FP32-preconditioned (refinement) against plain FP64 on one problem."""
+def run_single(args, dim, n, problem, name, steps=None, warmup=None, emit=True):
+    """FP32-preconditioned (refinement, flexible CG) against plain FP64 on
+    one problem; clocks sampled during each variant's timed solves."""
     import torch
     from paper_2509_08109_gb300 import binding
     torch.cuda.set_device(0)
-    out = {"metric": METRIC, "unit": UNIT, "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+    steps = args.steps if steps is None else steps
+    warmup = args.warmup if warmup is None else warmup
+    out = {"metric": METRIC, "unit": UNIT, "n_gpus": 1, "steps": steps, "warmup": warmup,
            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "data": "synthetic",
-           "config": {"workload": name, "nodes_per_side": n, "dim": dim, "dof": (n - 2) ** dim, "tol": TOL}}
+           "config": {"workload": name, "nodes_per_side": n, "dim": dim, "dof": (n - 2) ** dim, "tol": TOL,
+                      "timing": "CUDA events around the timed solves (mean over steps)"}}
     f = torch.as_tensor(problem.rhs, device="cuda")
     res = {}
     for prec, outer in (("fp32", "refine"), ("fp32", "flexible"), ("fp64", "cg")):
@@ -412,20 +504,23 @@ def run_single(args, dim, n, problem, name):
         setup_s = time.perf_counter() - t0
         # point Gauss-Seidel on the shell octant loses h-independence (cells
         # degenerate at the polar edge): PCG iterations double per refinement
-        ms, launches, infos = _timed_solves(torch, s, f, args.steps, args.warmup, maxit=500 if dim == 2 else 4000)
+        clk = Clocks(0)
+        ms, launches, infos = _timed_solves(torch, s, f, steps, warmup, maxit=500 if dim == 2 else 4000, clocks=clk)
         assert all(i.true_relres <= TOL for i in infos)
         res[f"{prec}_{outer}"] = {"value": (n - 2) ** dim / (ms * 1e-3), "ms_per_step": ms,
                                   "iterations": infos[-1].iterations, "true_relres": infos[-1].true_relres,
-                                  "gpu_launches": launches, "setup_s": setup_s}
+                                  "gpu_launches": launches, "setup_s": setup_s, "clocks": clk.result}
         del s
     head = max(("fp32_refine", "fp32_flexible"), key=lambda k: res[k]["value"])
     out.update({"value": res[head]["value"], "ms_per_step": res[head]["ms_per_step"], "headline_variant": head,
-                "dtype": "f32 V-cycle / f64 residual", "variants": res,
+                "dtype": "f32 V-cycle / f64 residual", "variants": res, "clocks": res[head]["clocks"],
                 "fp32_over_fp64": res["fp64_cg"]["ms_per_step"] / res[head]["ms_per_step"]})
-    print(json.dumps(out), flush=True)
+    if emit:
+        print(json.dumps(out), flush=True)
+    return out
 
 
-def run_batch(args):
+def run_batch(args, steps=None, warmup=None, emit=True):
     """512 independent bump-map problems (n = 2^k+1, k in 6..10), 4 rhs each,
     FP32 V-cycle with FP64 refinement, solved together by the batch engine
     (bmg_batch_solve: size-class persistent kernels over a device work-list,
@@ -434,6 +529,8 @@ def run_batch(args):
     import torch
     from paper_2509_08109_gb300 import binding, inputs
     torch.cuda.set_device(0)
+    steps = args.steps if steps is None else steps
+    warmup = args.warmup if warmup is None else warmup
     probs = inputs.bump_batch(count=512, nrhs=4)
     t0 = time.perf_counter()
     solvers = []
@@ -460,7 +557,7 @@ def run_batch(args):
             for x in row:
                 x.zero_()
 
-    for _ in range(args.warmup):
+    for _ in range(warmup):
         zero()
         B.solve(bs, xs, tol=TOL)
     torch.cuda.synchronize()
@@ -468,7 +565,7 @@ def run_batch(args):
     clk.start()
     times, infos = [], None
     l0 = B.launches
-    for _ in range(args.steps):
+    for _ in range(steps):
         zero()
         torch.cuda.synchronize()
         a = torch.cuda.Event(enable_timing=True)
@@ -479,7 +576,7 @@ def run_batch(args):
         torch.cuda.synchronize()
         times.append(a.elapsed_time(b))
     ck = clk.stop()
-    launches = (B.launches - l0) // args.steps
+    launches = (B.launches - l0) // steps
     worst = max(i.true_relres for row in infos for i in row)
     assert worst <= TOL
     its = [i.iterations for row in infos for i in row]
@@ -493,7 +590,7 @@ def run_batch(args):
             x.zero_()
     B.solve(bh, xh, tol=TOL)
     e2e_t = []
-    for _ in range(max(1, min(args.steps, 3))):
+    for _ in range(max(1, min(steps, 3))):
         for row in xh:
             for x in row:
                 x.zero_()
@@ -504,8 +601,8 @@ def run_batch(args):
         e2e_t.append(time.perf_counter() - t)
     e2e_s = statistics.median(e2e_t)
     nbytes = sum(t.numel() * 8 for row in bh for t in row)
-    out = {"metric": METRIC, "value": dof / (ms * 1e-3), "unit": UNIT, "n_gpus": 1, "steps": args.steps,
-           "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+    out = {"metric": METRIC, "value": dof / (ms * 1e-3), "unit": UNIT, "n_gpus": 1, "steps": steps,
+           "warmup": warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
            "vs_baseline": None, "dtype": "f32 V-cycle / f64 residual", "data": "synthetic",
            "config": {"workload": "bump_batch_512x4", "problems": 512, "rhs_per_problem": 4,
                       "dof_total_all_rhs": dof, "sizes": "n=2^k+1, k~U{6..10}, seed 5", "tol": TOL,
@@ -519,10 +616,14 @@ def run_batch(args):
            "gpu_launches": launches, "iterations_min_max": [min(its), max(its)],
            "worst_true_relres": worst, "setup_s": setup_s, "batch_attach_s": batch_setup_s,
            "autotune_ms": tune_ms, "clocks": ck}
-    print(json.dumps(out), flush=True)
+    del B, solvers, bs, xs, bh, xh
+    torch.cuda.empty_cache()
+    if emit:
+        print(json.dumps(out), flush=True)
+    return out
 
 
-def run_adjoint(args):
+def run_adjoint(args, steps=None, warmup=None, emit=True):
     """1025^2 annulus, per-cell m ~ N(0, 0.5^2), kappa = exp(m), batch 8:
     forward solve + adjoint gradient per member through torch.autograd.
     Timed leg: the members run concurrently (one stream and one solver per
@@ -532,6 +633,8 @@ def run_adjoint(args):
     import torch
     from paper_2509_08109_gb300 import autograd, binding, inputs
     torch.cuda.set_device(0)
+    steps = args.steps if steps is None else steps
+    warmup = args.warmup if warmup is None else warmup
     probs = inputs.annulus_adjoint(1025, batch=8)
     coords = torch.as_tensor(probs[0].coords, device="cuda")
     ms_ = [torch.as_tensor(p.extra["m"], device="cuda") for p in probs]
@@ -548,7 +651,7 @@ def run_adjoint(args):
         return [m.grad for m in ms]
 
     def timed(solvers, steps):
-        for _ in range(args.warmup):
+        for _ in range(warmup):
             step(solvers)
         torch.cuda.synchronize()
         times = []
@@ -562,9 +665,9 @@ def run_adjoint(args):
 
     clk = Clocks(0)
     clk.start()
-    ms, launches = timed(conc, args.steps)
+    ms, launches = timed(conc, steps)
     ck = clk.stop()
-    ms64, _ = timed(serial, max(1, min(args.steps, 3)))
+    ms64, _ = timed(serial, max(1, min(steps, 3)))
     g_c = step(conc)
     g_s = step(serial)
     # both legs solve to the same FP64 residual; their gradients agree to
@@ -572,7 +675,7 @@ def run_adjoint(args):
     agree = max((torch.linalg.vector_norm(a - b) / torch.linalg.vector_norm(b)).item() for a, b in zip(g_c, g_s))
     dof = 8 * 1023 ** 2
     out = {"metric": "forward+adjoint DoF/s (batch 8, each member: assemble, setup, solve, adjoint solve, dA/dkappa)",
-           "value": dof / (ms * 1e-3), "unit": UNIT, "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+           "value": dof / (ms * 1e-3), "unit": UNIT, "n_gpus": 1, "steps": steps, "warmup": warmup,
            "ms_per_step": ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
            "dtype": "f32 V-cycle / f64 residual", "data": "synthetic",
            "config": {"workload": "annulus_adjoint_n1025_batch8", "tol": TOL,
@@ -582,7 +685,11 @@ def run_adjoint(args):
            "fp64_serial": {"ms_per_step": ms64, "value": dof / (ms64 * 1e-3), "dtype": "f64",
                            "launch": "members one after the other, plain FP64 PCG"},
            "grad_rel_diff_between_legs": agree}
-    print(json.dumps(out), flush=True)
+    del conc, serial
+    torch.cuda.empty_cache()
+    if emit:
+        print(json.dumps(out), flush=True)
+    return out
 
 
 def run_aux(args):

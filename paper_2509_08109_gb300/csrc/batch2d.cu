@@ -195,6 +195,45 @@ __global__ void __launch_bounds__(kBThreads) k_bclear(const BProbDev* __restrict
         P.x[k] = 0.0;
 }
 
+// Table-driven forms for right-hand sides and solutions in device memory:
+// one launch for every problem (blockIdx.y).
+struct PackEnt {
+    const double* src[4];
+    double* dst[4];
+};
+
+__global__ void k_bpack_all(const BProbDev* __restrict__ probs, const PackEnt* __restrict__ tab, int which) {
+    const int pi = blockIdx.y;
+    const BProbDev P = probs[pi];
+    const PackEnt e = tab[pi];
+    double* dst = which == 0 ? (double*)P.b : P.x;
+    const int n = P.n, ld = P.ld;
+    const long long tot = P.plane * R;
+    for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < tot;
+         k += (long long)gridDim.x * blockDim.x) {
+        const int rh = (int)(k % R);
+        const long long node = k / R;
+        const int j = (int)(node / ld), i = (int)(node - (long long)j * ld);
+        const bool in = i >= 1 && i <= n - 2 && j >= 1 && j <= n - 2;
+        dst[k] = (in && e.src[rh]) ? e.src[rh][(long long)j * n + i] : 0.0;
+    }
+}
+
+__global__ void k_bunpack_all(const BProbDev* __restrict__ probs, const PackEnt* __restrict__ tab) {
+    const int pi = blockIdx.y;
+    const BProbDev P = probs[pi];
+    const PackEnt e = tab[pi];
+    const int n = P.n, ld = P.ld;
+    const long long tot = (long long)n * n * R;
+    for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < tot;
+         k += (long long)gridDim.x * blockDim.x) {
+        const int rh = (int)(k % R);
+        const long long node = k / R;
+        const int j = (int)(node / n), i = (int)(node - (long long)j * n);
+        if (e.dst[rh]) e.dst[rh][node] = P.x[((long long)j * ld + i) * R + rh];
+    }
+}
+
 // ---------------------------------------------------------------- FP64 residual
 // r = (float)(b - A x) for every right-hand side of problem blockIdx.y,
 // ||r||^2 (and, with bb, ||b||^2) per system; the last block of the problem
@@ -267,19 +306,33 @@ __global__ void __launch_bounds__(kBThreads) k_bresidual(const BProbDev* __restr
 }
 
 // ---------------------------------------------------------------- operator product
+__device__ __forceinline__ float4 f4(float a) { return make_float4(a, a, a, a); }
+__device__ __forceinline__ float4 operator+(float4 a, float4 b) {
+    return make_float4(a.x + b.x, a.y + b.y, a.z + b.z, a.w + b.w);
+}
+__device__ __forceinline__ float4 operator-(float4 a, float4 b) {
+    return make_float4(a.x - b.x, a.y - b.y, a.z - b.z, a.w - b.w);
+}
+__device__ __forceinline__ float4 operator*(float a, float4 b) { return make_float4(a * b.x, a * b.y, a * b.z, a * b.w); }
+__device__ __forceinline__ float4 operator*(float4 a, float4 b) {
+    return make_float4(a.x * b.x, a.y * b.y, a.z * b.z, a.w * b.w);
+}
+
 // p = z + beta p_old, then q = A p in difference form (FP64 row sums), p.q
 // per system; the last tile of a problem forms alpha = r.z / p.q for each of
-// its systems.  One CTA per item: kBCols interior columns x H rows of one
-// problem, R right-hand sides; a four-row ring of p (one halo column per
-// side) and of the W, SW, NW planes (one halo column on the right), the
-// loads of row j+2 in flight while row j is formed.  The arithmetic and its
-// order are those of the single-problem kernel, per right-hand side.
-__global__ void __launch_bounds__(kBThreads) k_bpspmv(const BProbDev* __restrict__ probs,
+// its systems.  One CTA per item: kBThreads interior columns x H rows of
+// one problem, a thread per column with the R right-hand sides of a node as
+// one float4; a four-row ring of p (one halo column per side) and of the W,
+// SW, NW planes (one halo column on the right), the loads of row j+2 in
+// flight while row j is formed.  The arithmetic and its order are those of
+// the single-problem kernel, per right-hand side.
+static_assert(R == 4, "the batched vector kernels carry the right-hand sides of a node as a float4");
+__global__ void __launch_bounds__(kBThreads, 3) k_bpspmv(const BProbDev* __restrict__ probs,
                                                       const SpItem* __restrict__ items, int H, int parity,
                                                       SysState* sys, double* partials, unsigned* counters,
                                                       KState* st) {
-    constexpr int TW = kBCols;
-    __shared__ float sP[4][TW + 2][R];
+    constexpr int TW = kBThreads;
+    __shared__ float4 sP[4][TW + 2];
     __shared__ float sW[4][TW + 1];
     __shared__ float sSW[4][TW + 1];
     __shared__ float sNW[4][TW + 1];
@@ -287,15 +340,16 @@ __global__ void __launch_bounds__(kBThreads) k_bpspmv(const BProbDev* __restrict
     __shared__ bool last;
     const SpItem it = items[blockIdx.x];
     const BProbDev P = probs[it.prob];
-    const int rh = threadIdx.x % R, t = threadIdx.x / R;
+    const int t = threadIdx.x;
     const int n = P.n, ld = P.ld;
     const long long pl = P.plane;
     const float* A = P.A32;
-    const float* z = P.z[parity];
-    const float* pold = P.p[parity ^ 1];
-    float* pnew = P.p[parity];
-    float* q = P.q;
-    const float beta = (float)sys[(long long)it.prob * R + rh].beta;
+    const float4* z = (const float4*)P.z[parity];
+    const float4* pold = (const float4*)P.p[parity ^ 1];
+    float4* pnew = (float4*)P.p[parity];
+    float4* q = (float4*)P.q;
+    const SysState* sy = sys + (long long)it.prob * R;
+    const float4 beta = make_float4((float)sy[0].beta, (float)sy[1].beta, (float)sy[2].beta, (float)sy[3].beta);
     const int tx = it.tile % P.sp_tiles_x, ty = it.tile / P.sp_tiles_x;
     const int i0 = 1 + tx * TW;
     const int j0 = 1 + ty * H;
@@ -304,16 +358,19 @@ __global__ void __launch_bounds__(kBThreads) k_bpspmv(const BProbDev* __restrict
     const bool act = i <= n - 2;
     const int il = i0 - 1, ir = i0 + TW;
     struct Row {
-        float z, po, w, sw, nw, s, r, hz, hpo, hw, hsw, hnw;
+        float4 z, po, hz, hpo;
+        float w, sw, nw, s, r, hw, hsw, hnw;
     };
+    const float4 zero4 = f4(0.f);
     auto load = [&](int j, Row& v) {
-        v = Row{0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+        v.z = v.po = v.hz = v.hpo = zero4;
+        v.w = v.sw = v.nw = v.s = v.r = v.hw = v.hsw = v.hnw = 0.f;
         if (j < 1 || j > n - 2) return;
         const long long kr = (long long)j * ld;
         if (act) {
             const long long k = kr + i;
-            v.z = z[k * R + rh];
-            v.po = pold[k * R + rh];
+            v.z = z[k];
+            v.po = pold[k];
             v.w = A[W2 * pl + k];
             v.sw = A[SW2 * pl + k];
             v.nw = A[NW2 * pl + k];
@@ -321,13 +378,13 @@ __global__ void __launch_bounds__(kBThreads) k_bpspmv(const BProbDev* __restrict
             v.r = P.rs[k];
         }
         if (t == 0 && il >= 1) {
-            v.hz = z[(kr + il) * R + rh];
-            v.hpo = pold[(kr + il) * R + rh];
+            v.hz = z[kr + il];
+            v.hpo = pold[kr + il];
         }
         if (t == 1 && ir <= n - 2) {
             const long long k = kr + ir;
-            v.hz = z[k * R + rh];
-            v.hpo = pold[k * R + rh];
+            v.hz = z[k];
+            v.hpo = pold[k];
             v.hw = A[W2 * pl + k];
             v.hsw = A[SW2 * pl + k];
             v.hnw = A[NW2 * pl + k];
@@ -335,20 +392,16 @@ __global__ void __launch_bounds__(kBThreads) k_bpspmv(const BProbDev* __restrict
     };
     auto put = [&](int j, const Row& v) {
         const int sl = j & 3;
-        sP[sl][t + 1][rh] = v.z + beta * v.po;
-        if (rh == 0) {
-            sW[sl][t] = v.w;
-            sSW[sl][t] = v.sw;
-            sNW[sl][t] = v.nw;
-        }
-        if (t == 0) sP[sl][0][rh] = v.hz + beta * v.hpo;
+        sP[sl][t + 1] = v.z + beta * v.po;
+        sW[sl][t] = v.w;
+        sSW[sl][t] = v.sw;
+        sNW[sl][t] = v.nw;
+        if (t == 0) sP[sl][0] = v.hz + beta * v.hpo;
         if (t == 1) {
-            sP[sl][TW + 1][rh] = v.hz + beta * v.hpo;
-            if (rh == 0) {
-                sW[sl][TW] = v.hw;
-                sSW[sl][TW] = v.hsw;
-                sNW[sl][TW] = v.hnw;
-            }
+            sP[sl][TW + 1] = v.hz + beta * v.hpo;
+            sW[sl][TW] = v.hw;
+            sSW[sl][TW] = v.hsw;
+            sNW[sl][TW] = v.hnw;
         }
     };
     Row nx;
@@ -358,7 +411,7 @@ __global__ void __launch_bounds__(kBThreads) k_bpspmv(const BProbDev* __restrict
     put(j0, nx);
     float rs_j = nx.r, s_j = nx.s;
     load(j0 + 1, nx);
-    AccB acc;
+    AccB acc[R];
     for (int j = j0; j < j1; j++) {
         put(j + 1, nx);
         const float s_n = nx.s, rs_n = nx.r;
@@ -366,72 +419,103 @@ __global__ void __launch_bounds__(kBThreads) k_bpspmv(const BProbDev* __restrict
         __syncthreads();
         if (act) {
             const int sm = (j - 1) & 3, s0 = j & 3, sp = (j + 1) & 3;
-            const float pv = sP[s0][t + 1][rh];
-            float v = rs_j * pv;
-            v += sW[s0][t] * (sP[s0][t][rh] - pv);
-            v += sW[s0][t + 1] * (sP[s0][t + 2][rh] - pv);
-            v += s_j * (sP[sm][t + 1][rh] - pv);
-            v += s_n * (sP[sp][t + 1][rh] - pv);
-            v += sSW[s0][t] * (sP[sm][t][rh] - pv);
-            v += sSW[sp][t + 1] * (sP[sp][t + 2][rh] - pv);
-            v += sNW[s0][t] * (sP[sp][t][rh] - pv);
-            v += sNW[sm][t + 1] * (sP[sm][t + 2][rh] - pv);
+            const float4 pv = sP[s0][t + 1];
+            float4 v = rs_j * pv;
+            v = v + sW[s0][t] * (sP[s0][t] - pv);
+            v = v + sW[s0][t + 1] * (sP[s0][t + 2] - pv);
+            v = v + s_j * (sP[sm][t + 1] - pv);
+            v = v + s_n * (sP[sp][t + 1] - pv);
+            v = v + sSW[s0][t] * (sP[sm][t] - pv);
+            v = v + sSW[sp][t + 1] * (sP[sp][t + 2] - pv);
+            v = v + sNW[s0][t] * (sP[sp][t] - pv);
+            v = v + sNW[sm][t + 1] * (sP[sm][t + 2] - pv);
             const long long k = (long long)j * ld + i;
-            pnew[k * R + rh] = pv;
-            q[k * R + rh] = v;
-            acc.add(pv * v);
+            pnew[k] = pv;
+            q[k] = v;
+            const float4 pq = pv * v;
+            acc[0].add(pq.x);
+            acc[1].add(pq.y);
+            acc[2].add(pq.z);
+            acc[3].add(pq.w);
         }
         rs_j = rs_n;
         s_j = s_n;
     }
-    const double tot = block_sum_r(acc.value(), red);
+    // per right-hand side: warp shuffle trees, then the warps' sums in order
+    // (a fixed order: deterministic), then the tile partial
+    double v[R];
+    for (int r = 0; r < R; r++) {
+        v[r] = acc[r].value();
+        for (int o = 16; o > 0; o >>= 1) v[r] += __shfl_down_sync(0xffffffffu, v[r], o);
+    }
+    const int warp = t >> 5, lane = t & 31;
+    if (lane == 0)
+        for (int r = 0; r < R; r++) red[warp * R + r] = v[r];
+    __syncthreads();
     double* part = partials + P.sp_part * R;
-    if (threadIdx.x < R) part[(long long)it.tile * R + threadIdx.x] = tot;
+    if (t < R) {
+        double sum = 0.0;
+        for (int w = 0; w < kBThreads / 32; w++) sum += red[w * R + t];
+        part[(long long)it.tile * R + t] = sum;
+    }
     __threadfence();
     __syncthreads();
-    if (threadIdx.x == 0) last = atomicAdd(&counters[it.prob], 1u) == (unsigned)P.sp_tiles - 1;
+    if (t == 0) last = atomicAdd(&counters[it.prob], 1u) == (unsigned)P.sp_tiles - 1;
     __syncthreads();
     if (!last) return;
     __threadfence();
     // fixed-order sum over the problem's tiles, per right-hand side
+    const int rh = t % R;
     double s = 0.0;
-    for (int k = threadIdx.x / R; k < P.sp_tiles; k += kBThreads / R)
+    for (int k = t / R; k < P.sp_tiles; k += kBThreads / R)
         s += ((volatile const double*)part)[(long long)k * R + rh];
     s = block_sum_r(s, red);
-    if (threadIdx.x < R) {
-        SysState& sy = sys[(long long)it.prob * R + threadIdx.x];
-        const bool live = sy.active && sy.left > 0;
-        sy.pq = s;
-        if (!live || sy.rz == 0.0) {
-            sy.alpha = 0.0;
+    if (t < R) {
+        SysState& sw = sys[(long long)it.prob * R + t];
+        const bool live = sw.active && sw.left > 0;
+        sw.pq = s;
+        if (!live || sw.rz == 0.0) {
+            sw.alpha = 0.0;
         } else if (!(s > 0.0)) {
             set_err(st, BMG_ERR_NOT_SPD);
-            sy.alpha = 0.0;
+            sw.alpha = 0.0;
         } else {
-            sy.alpha = sy.rz / s;
+            sw.alpha = sw.rz / s;
         }
-        if (live) sy.left--;
+        if (live) sw.left--;
     }
-    if (threadIdx.x == 0) counters[it.prob] = 0u;
+    if (t == 0) counters[it.prob] = 0u;
 }
 
 // x += alpha p straight into the FP64 iterate, r -= alpha q in FP32, for the
-// systems of problem blockIdx.y that took this iteration (alpha != 0).
+// systems of problem blockIdx.y that took this iteration (alpha != 0; a
+// frozen system has alpha = 0 and keeps x and r).  A thread per node, the R
+// right-hand sides as vectors.
 __global__ void __launch_bounds__(kBThreads) k_bupdate(const BProbDev* __restrict__ probs, int parity,
                                                        const SysState* __restrict__ sys) {
     const int pi = blockIdx.y;
     const BProbDev P = probs[pi];
-    const int rh = threadIdx.x % R;
-    const SysState& sy = sys[(long long)pi * R + rh];
-    const double alpha = sy.alpha;
-    if (!sy.active || alpha == 0.0) return;     // frozen systems take no update
-    const float a32 = (float)alpha;
-    const float* p = P.p[parity];
-    const long long tot = P.plane * R;
-    for (long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x; k < tot;
+    const SysState* sy = sys + (long long)pi * R;
+    double al[R];
+    for (int r = 0; r < R; r++) al[r] = sy[r].active ? sy[r].alpha : 0.0;
+    if (al[0] == 0.0 && al[1] == 0.0 && al[2] == 0.0 && al[3] == 0.0) return;
+    const float4 a32 = make_float4((float)al[0], (float)al[1], (float)al[2], (float)al[3]);
+    const float4* p = (const float4*)P.p[parity];
+    const float4* q = (const float4*)P.q;
+    float4* rr = (float4*)P.r;
+    double2* x = (double2*)P.x;
+    for (long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x; k < P.plane;
          k += (long long)gridDim.x * blockDim.x) {
-        P.x[k] += alpha * (double)p[k];
-        P.r[k] -= a32 * P.q[k];
+        const float4 pv = p[k];
+        const float4 qv = q[k];
+        double2 x0 = x[2 * k], x1 = x[2 * k + 1];
+        x0.x += al[0] * (double)pv.x;
+        x0.y += al[1] * (double)pv.y;
+        x1.x += al[2] * (double)pv.z;
+        x1.y += al[3] * (double)pv.w;
+        x[2 * k] = x0;
+        x[2 * k + 1] = x1;
+        rr[k] = rr[k] - a32 * qv;
     }
 }
 
@@ -479,6 +563,8 @@ struct Batch {
     double* part_sp = nullptr;          // operator product partials
     double* part_res = nullptr;         // residual partials (count * kRowBlocks * 2R)
     double* stage = nullptr;            // host staging (largest n^2 * R doubles)
+    PackEnt* ptab = nullptr;            // device: 3 * count pack/unpack entries
+    PackEnt* ptab_h = nullptr;          // pinned mirror
     long long stage_elems = 0;
     cudaStream_t cap = nullptr;
     cudaGraphExec_t exec[2] = {nullptr, nullptr};
@@ -544,6 +630,7 @@ size_t carve_batch(Batch& B, char* base) {
     B.part_sp = (double*)take(sizeof(double) * R * (parts_sp > 0 ? parts_sp : 1));
     B.part_res = (double*)take(sizeof(double) * 2 * R * kRowBlocks * B.count);
     B.stage = (double*)take(sizeof(double) * B.stage_elems);
+    B.ptab = (PackEnt*)take(sizeof(PackEnt) * 3 * B.count);
     return a256(off);
 }
 
@@ -696,7 +783,7 @@ bmg_status enqueue_iteration(Batch& B, int parity) {
     k_bpspmv<<<(int)B.sp_h.size(), kBThreads, 0, B.stream>>>(B.prob_d, B.sp_d, B.sp_h_rows, parity, B.sys,
                                                              B.part_sp, B.counters + B.count, B.st);
     int maxblk = 1;
-    for (const BProbDev& P : B.prob_h) maxblk = std::max(maxblk, cdiv(P.plane * R, kBThreads * 8));
+    for (const BProbDev& P : B.prob_h) maxblk = std::max(maxblk, cdiv(P.plane, kBThreads * 4));
     k_bupdate<<<dim3(std::min(maxblk, 512), B.count), kBThreads, 0, B.stream>>>(B.prob_d, parity, B.sys);
     B.launches += 2;
     BMG_CUDA(cudaGetLastError());
@@ -837,7 +924,7 @@ bmg_status batch_build(int count, Ctx* const* ctxs, int flags, bool sizing, bool
         K.tiles_x = cdiv(K.nc - 1, K.wc);   // rows per tile are modelled at attach
     }
     // per problem: the operator-product tiles and the staging size
-    int H = 16;
+    int H = 32;
     B->sp_h_rows = H;
     for (int p = 0; p < count; p++) {
         const Ctx* c = ctxs[p];
@@ -847,7 +934,7 @@ bmg_status batch_build(int count, Ctx* const* ctxs, int flags, bool sizing, bool
         P.ld = c->lev[0].ld;
         P.plane = c->lev[0].plane;
         const int m = P.n - 2;
-        P.sp_tiles_x = cdiv(m, kBCols);
+        P.sp_tiles_x = cdiv(m, kBThreads);
         P.sp_tiles = P.sp_tiles_x * cdiv(m, H);
         for (int t = 0; t < P.sp_tiles; t++) B->sp_h.push_back(SpItem{p, t});
         B->stage_elems = std::max<long long>(B->stage_elems, (long long)P.n * P.n * R);
@@ -893,6 +980,7 @@ bmg_status batch_attach(Batch& B, void* ws, size_t bytes, void* stream) {
     carve_batch(B, B.ws);
     if (!B.sys_h) BMG_CUDA(cudaMallocHost((void**)&B.sys_h, sizeof(SysState) * B.count * R));
     if (!B.st_h) BMG_CUDA(cudaMallocHost((void**)&B.st_h, sizeof(KState)));
+    if (!B.ptab_h) BMG_CUDA(cudaMallocHost((void**)&B.ptab_h, sizeof(PackEnt) * 3 * B.count));
     BMG_CUDA(cudaMemsetAsync(B.ws, 0, B.ws_need, B.stream));
     // class copies of the FP32 operators and weights, in member order (one
     // problem: the classes view the context's own levels)
@@ -1045,8 +1133,31 @@ bmg_status batch_solve(Batch& B, int nrhs, const double* const* b, double* const
     if (!B.attached) return BMG_ERR_WORKSPACE;
     if (nrhs < 1 || nrhs > R || !b || !x || maxit < 0 || !(tol > 0)) return BMG_ERR_ARG;
     const int S = B.count * R;
-    // right-hand sides and initial guesses into the interleaved FP64 vectors
-    for (int p = 0; p < B.count; p++) {
+    // right-hand sides and initial guesses into the interleaved FP64 vectors:
+    // one table-driven launch when every array is in device memory, else
+    // per problem through the staging buffer
+    bool all_dev = true;
+    for (long long k = 0; k < (long long)B.count * nrhs && all_dev; k++) {
+        if (!b[k] || !x[k]) return BMG_ERR_ARG;
+        all_dev = dev_ptr(b[k]) && dev_ptr(x[k]);
+    }
+    int maxpk = 1;
+    for (const BProbDev& P : B.prob_h) maxpk = std::max(maxpk, cdiv(P.plane * R, kBThreads * 4));
+    maxpk = std::min(maxpk, 256);
+    if (all_dev) {
+        for (int p = 0; p < B.count; p++)
+            for (int r = 0; r < R; r++) {
+                const bool have = r < nrhs;
+                B.ptab_h[p].src[r] = have ? b[(long long)p * nrhs + r] : nullptr;
+                B.ptab_h[B.count + p].src[r] = have ? x[(long long)p * nrhs + r] : nullptr;
+                B.ptab_h[2 * B.count + p].dst[r] = have ? x[(long long)p * nrhs + r] : nullptr;
+            }
+        BMG_CUDA(cudaMemcpyAsync(B.ptab, B.ptab_h, sizeof(PackEnt) * 3 * B.count, cudaMemcpyHostToDevice, B.stream));
+        k_bpack_all<<<dim3(maxpk, B.count), kBThreads, 0, B.stream>>>(B.prob_d, B.ptab, 0);
+        k_bpack_all<<<dim3(maxpk, B.count), kBThreads, 0, B.stream>>>(B.prob_d, B.ptab + B.count, 1);
+        B.launches += 2;
+    }
+    for (int p = 0; p < B.count && !all_dev; p++) {
         BProbDev& P = B.prob_h[p];
         const long long nn = (long long)P.n * P.n;
         const double* src[R] = {nullptr, nullptr, nullptr, nullptr};
@@ -1163,7 +1274,11 @@ bmg_status batch_solve(Batch& B, int nrhs, const double* const* b, double* const
         }
     }
     // solutions back to the caller
-    for (int p = 0; p < B.count; p++) {
+    if (all_dev) {
+        k_bunpack_all<<<dim3(maxpk, B.count), kBThreads, 0, B.stream>>>(B.prob_d, B.ptab + 2 * B.count);
+        B.launches++;
+    }
+    for (int p = 0; p < B.count && !all_dev; p++) {
         BProbDev& P = B.prob_h[p];
         const long long nn = (long long)P.n * P.n;
         double* d[R] = {nullptr, nullptr, nullptr, nullptr};
@@ -1222,6 +1337,7 @@ void batch_destroy(Batch* B) {
     if (B->cap) cudaStreamDestroy(B->cap);
     if (B->sys_h) cudaFreeHost(B->sys_h);
     if (B->st_h) cudaFreeHost(B->st_h);
+    if (B->ptab_h) cudaFreeHost(B->ptab_h);
     delete B;
 }
 
