@@ -49,6 +49,9 @@ def parse():
     ap.add_argument("--n", type=int, default=4097)
     ap.add_argument("--cpu-sample-n", type=int, default=1025)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--variants", default="all", choices=["all", "fp64"],
+                    help="fp64: time only the plain FP64 solve of the annulus workload (a short line for "
+                         "profiling the FP64 kernels)")
     ap.add_argument("--no-configs", action="store_true",
                     help="skip the compact runs of the other configurations (65^2 annulus, 257^3 shell, "
                          "512-problem batch, 1025^2 adjoint batch) that the default line carries")
@@ -166,21 +169,47 @@ def traffic_for(kernel: str, n: int):
     return ent.get("dram_bytes_per_launch")
 
 
-def cpu_baseline(n_sample: int) -> dict:
-    """The oracle (plain FP64 C, single thread) on a bounded sample of the
-    same workload: the same map/coefficient/rhs recipe at n_sample nodes per
-    side; time of the PCG solve to 1e-10 (hierarchy built beforehand)."""
+def cpu_model() -> str:
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.startswith("Model name"):
+                return line.split(":", 1)[1].strip()
+    except (OSError, subprocess.SubprocessError):
+        pass
+    return "unknown"
+
+
+def cpu_baseline(n_sample: int, n_full: int) -> dict:
+    """The oracle (plain FP64 C) on the host cores: one PCG solve to 1e-10
+    of the full workload on every core of the process's affinity set (the
+    OpenMP build, whose results are bitwise the plain build's), and, beside
+    it, the single-threaded build on a sample of the same recipe at n_sample
+    nodes per side (hierarchies built beforehand, outside the timings)."""
     import oracle
     from paper_2509_08109_gb300 import inputs
-    p = inputs.annulus_lognormal(n_sample)
-    H = oracle.Hierarchy(oracle.assemble(p.coords, p.kappa))
+    cores = len(os.sched_getaffinity(0))
+    oracle.threads(cores)
+    p = inputs.annulus_lognormal(n_full)
+    H = oracle.Hierarchy(oracle.assemble(p.coords, p.kappa), omp=True)
     t = time.perf_counter()
     x, it, hist, trr, st = H.pcg(p.rhs, tol=TOL, maxit=500)
     dt = time.perf_counter() - t
     assert st == 0 and trr <= TOL, (st, trr)
-    return {"value": p.unknowns / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": f"one PCG solve to 1e-10 of the same recipe at n={n_sample} "
-                      f"({p.unknowns} DoF, {it} iterations, {dt:.2f} s), single-threaded C oracle"}
+    del H, x, p
+    q = inputs.annulus_lognormal(n_sample)
+    H1 = oracle.Hierarchy(oracle.assemble(q.coords, q.kappa))
+    t = time.perf_counter()
+    x1, it1, _, trr1, st1 = H1.pcg(q.rhs, tol=TOL, maxit=500)
+    dt1 = time.perf_counter() - t
+    assert st1 == 0 and trr1 <= TOL
+    dof = (n_full - 2) ** 2
+    return {"value": dof / dt, "unit": UNIT, "cores": cores, "kind": "oracle", "cpu": cpu_model(),
+            "sample": f"one PCG solve to 1e-10 of the full workload (n={n_full}, {dof} DoF, {it} iterations, "
+                      f"{dt:.2f} s) on {cores} cores, OpenMP build of the C oracle (bitwise the plain build)",
+            "single_thread": {"value": q.unknowns / dt1, "cores": 1,
+                              "sample": f"plain single-threaded oracle, same recipe at n={n_sample} "
+                                        f"({q.unknowns} DoF, {it1} iterations, {dt1:.2f} s)"}}
 
 
 # ---------------------------------------------------------------- replicas
@@ -222,6 +251,20 @@ def run_own(args):
     dof = (n - 2) ** 2
     coords, kappa, f = inputs.annulus_lognormal_device(n, dev)
     stream = torch.cuda.current_stream(dev)
+    if args.variants == "fp64":
+        # only the plain FP64 solve (for profiling its kernels): a short line
+        s = binding.Solver(2, n, precision="fp64", outer="cg", device=dev, graphs=not args.no_graphs)
+        s.assemble(coords, kappa).setup()
+        if not args.no_autotune:
+            s.autotune(reps=3)
+        ms, launches, infos = _timed_solves(torch, s, f, args.steps, args.warmup)
+        assert all(i.true_relres <= TOL for i in infos)
+        if rank == 0:
+            print(json.dumps({"metric": METRIC, "value": dof / (ms * 1e-3), "unit": UNIT, "n_gpus": world,
+                              "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "dtype": "f64",
+                              "variants": "fp64 only", "iterations": infos[-1].iterations,
+                              "config": config_for(n, not args.no_graphs)}), flush=True)
+        return
 
     def build(prec, outer=None):
         s = binding.Solver(2, n, precision=prec, outer=outer, device=dev, graphs=not args.no_graphs)
@@ -347,7 +390,7 @@ def run_own(args):
     if rank == 0 and world == 1 and not args.no_configs:
         out["configs"] = other_configs(args)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        out["cpu_baseline"] = cpu_baseline(args.cpu_sample_n)
+        out["cpu_baseline"] = cpu_baseline(args.cpu_sample_n, n)
     if rank == 0:
         print(json.dumps(out), flush=True)
     if world > 1:
@@ -360,7 +403,7 @@ def run_own(args):
 # on the 2049^2 annulus: profiles/vdown64_annulus2049_fp64.md.  The FP64
 # kernels of this path are bound by the FP64 rate rather than by HBM; their
 # roofline is the FP64 peak.
-FP64_FLOPS_PER_NODE = {"vdown": 36.81, "spmv": 19.45, "update": 6.52}
+FP64_FLOPS_PER_NODE = {"vdown": 36.81, "vup": 39.28, "spmv": 19.45, "update": 6.52}
 # GB300 FP64 (non-tensor) peak, nominal: 1.25 TFLOP/s
 FP64_PEAK_GFLOPS = 1250.0
 
@@ -431,17 +474,20 @@ def other_configs(args) -> dict:
 # ---------------------------------------------------------------- reference arm
 def run_reference(args):
     """The oracle, as it stands, on the host cores: each step is one PCG
-    solve to 1e-10 of a bounded sample of the workload (same recipe at
-    n = 513 nodes per side)."""
+    solve to 1e-10 of the full workload (the same n as the own arm), on
+    every core of the process's affinity set (OpenMP build of the oracle,
+    bitwise the plain build's results); at most one warm-up solve (the CPU
+    code has nothing to warm beyond its first pass)."""
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
     import oracle
     from paper_2509_08109_gb300 import inputs
-    n_s = 513
-    p = inputs.annulus_lognormal(n_s)
-    H = oracle.Hierarchy(oracle.assemble(p.coords, p.kappa))
-    for _ in range(args.warmup):
+    cores = len(os.sched_getaffinity(0))
+    oracle.threads(cores)
+    p = inputs.annulus_lognormal(args.n)
+    H = oracle.Hierarchy(oracle.assemble(p.coords, p.kappa), omp=True)
+    for _ in range(min(args.warmup, 1)):
         H.pcg(p.rhs, tol=TOL, maxit=500)
     t = time.perf_counter()
     for _ in range(args.steps):
@@ -449,12 +495,13 @@ def run_reference(args):
         assert st == 0
     dt = time.perf_counter() - t
     value = p.unknowns * args.steps / dt
-    sample = f"one single-threaded oracle PCG solve to 1e-10 per step, same recipe at n={n_s} ({p.unknowns} DoF)"
+    sample = (f"one PCG solve to 1e-10 of the full workload per step (n={args.n}, {p.unknowns} DoF), "
+              f"OpenMP build of the C oracle on {cores} cores ({cpu_model()})")
     out = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
-           "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3,
+           "steps": args.steps, "warmup": min(args.warmup, 1), "ms_per_step": dt / args.steps * 1e3,
            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
            "config": config_for(args.n),
-           "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+           "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample},
            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(out), flush=True)
 

@@ -30,7 +30,9 @@ import numpy as np
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "bmg_oracle.c")
 _SO = os.path.join(_HERE, "liboracle.so")
+_SO_OMP = os.path.join(_HERE, "liboracle_omp.so")
 _lib = None
+_lib_omp = None
 
 _ERRORS = {1: "bad argument", 2: "map folded (det J <= 0)", 3: "setup breakdown",
            4: "operator not SPD", 5: "not converged", 6: "index out of range"}
@@ -43,19 +45,28 @@ class OracleError(RuntimeError):
 
 
 def build(force: bool = False) -> str:
-    """Compile the oracle with gcc (plain -O2, no fast-math)."""
-    if force or not os.path.exists(_SO) or os.path.getmtime(_SO) < os.path.getmtime(_SRC):
-        tmp = _SO + f".tmp{os.getpid()}"
-        subprocess.check_call(["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-o", tmp, _SRC, "-lm"])
-        os.replace(tmp, _SO)
+    """Compile the oracle with gcc (plain -O2, no fast-math), and the same
+    source with -fopenmp (liboracle_omp.so, for timing on all cores; its
+    shared loops are race-free, so its results are bitwise the same)."""
+    for so, extra in ((_SO, []), (_SO_OMP, ["-fopenmp"])):
+        if force or not os.path.exists(so) or os.path.getmtime(so) < os.path.getmtime(_SRC):
+            tmp = so + f".tmp{os.getpid()}"
+            subprocess.check_call(["gcc", "-O2", "-std=c11", "-fPIC", "-shared", *extra, "-o", tmp, _SRC, "-lm"])
+            os.replace(tmp, so)
     return _SO
 
 
-def _load():
-    global _lib
-    if _lib is None:
+def threads(n: int = 0) -> int:
+    """Threads of the OpenMP build (n > 0 sets them); returns the count."""
+    return _load(omp=True).or_threads(int(n))
+
+
+def _load(omp: bool = False):
+    global _lib, _lib_omp
+    cached = _lib_omp if omp else _lib
+    if cached is None:
         build()
-        lib = ctypes.CDLL(_SO)
+        lib = ctypes.CDLL(_SO_OMP if omp else _SO)
         P = ctypes.c_void_p
         I = ctypes.c_int
         D = ctypes.c_double
@@ -84,12 +95,16 @@ def _load():
             ("or_element_tensor", [I, P, P, P], I),
             ("or_assemble_tensor", [I, I, P, P, P], I),
             ("or_boundary_rhs", [I, I, P, P, P, P], I),
+            ("or_threads", [I], I),
         ]:
             f = getattr(lib, name)
             f.argtypes = args
             f.restype = res
-        _lib = lib
-    return _lib
+        if omp:
+            _lib_omp = lib
+        else:
+            _lib = lib
+    return _lib_omp if omp else _lib
 
 
 def _ptr(a: np.ndarray):
@@ -260,44 +275,46 @@ def prolong(pw, xc, x) -> np.ndarray:
 
 
 class Hierarchy:
-    """BoxMG hierarchy built from a finest full stencil."""
+    """BoxMG hierarchy built from a finest full stencil.  omp=True runs it on
+    the OpenMP build (the same results, on all cores)."""
 
-    def __init__(self, A):
+    def __init__(self, A, omp: bool = False):
         A = _f64(A)
         grid = A.shape[:-1]
         self.dim, self.n = _dim_n(grid)
+        self._lib = _load(omp)
         h = ctypes.c_void_p()
-        _check(_load().or_hier_create(self.dim, self.n, _ptr(A), ctypes.byref(h)))
+        _check(self._lib.or_hier_create(self.dim, self.n, _ptr(A), ctypes.byref(h)))
         self._h = h
 
     def __del__(self):
-        if getattr(self, "_h", None) and _lib is not None:
-            _lib.or_hier_free(self._h)
+        if getattr(self, "_h", None) and getattr(self, "_lib", None) is not None:
+            self._lib.or_hier_free(self._h)
             self._h = None
 
     @property
     def nlev(self) -> int:
-        return _load().or_hier_levels(self._h)
+        return self._lib.or_hier_levels(self._h)
 
     def level_n(self, l: int) -> int:
-        return _load().or_hier_n(self._h, l)
+        return self._lib.or_hier_n(self._h, l)
 
     def A(self, l: int) -> np.ndarray:
         n = self.level_n(l)
         out = np.zeros((n,) * self.dim + (3 ** self.dim,))
-        _load().or_hier_get_A(self._h, l, _ptr(out))
+        self._lib.or_hier_get_A(self._h, l, _ptr(out))
         return out
 
     def P(self, l: int) -> np.ndarray:
         n = self.level_n(l)
         out = np.zeros((n,) * self.dim + (1 << self.dim,))
-        _load().or_hier_get_P(self._h, l, _ptr(out))
+        self._lib.or_hier_get_P(self._h, l, _ptr(out))
         return out
 
     def vcycle(self, r) -> np.ndarray:
         r = _f64(r)
         z = np.zeros_like(r)
-        _load().or_vcycle(self._h, _ptr(r), _ptr(z))
+        self._lib.or_vcycle(self._h, _ptr(r), _ptr(z))
         return z
 
     def vcycle32(self, r) -> np.ndarray:
@@ -306,7 +323,7 @@ class Hierarchy:
         on entry, the result widened to FP64."""
         r = _f64(r)
         z = np.zeros_like(r)
-        _load().or_vcycle32(self._h, _ptr(r), _ptr(z))
+        self._lib.or_vcycle32(self._h, _ptr(r), _ptr(z))
         return z
 
     def pcg(self, b, x0=None, tol: float = 1e-10, maxit: int = 200, flexible: bool = False,
@@ -320,7 +337,7 @@ class Hierarchy:
         it = ctypes.c_int()
         trr = ctypes.c_double()
         mode = int(bool(flexible)) | (2 if fp32 else 0)
-        st = _load().or_pcg(self._h, _ptr(b), _ptr(x), float(tol), int(maxit), mode,
+        st = self._lib.or_pcg(self._h, _ptr(b), _ptr(x), float(tol), int(maxit), mode,
                             ctypes.byref(it), _ptr(hist), ctypes.byref(trr))
         return x, it.value, hist[: it.value + 1].copy(), trr.value, st
 

@@ -48,6 +48,30 @@
 #include <stdlib.h>
 #include <string.h>
 
+/* Built twice: plain, and with -fopenmp for the CPU-baseline timing on all
+   cores.  Only loops whose iterations write disjoint entries and read
+   nothing another iteration writes are shared out (operator application,
+   the points of one colour, prolongation, elementwise vector updates), so
+   the results are bitwise those of the plain build; scatter loops
+   (restriction, Galerkin products, assembly) and dot products stay
+   sequential. */
+#ifdef _OPENMP
+#include <omp.h>
+#define OR_PARALLEL_FOR _Pragma("omp parallel for schedule(static)")
+#else
+#define OR_PARALLEL_FOR
+#endif
+
+int or_threads(int n) {
+#ifdef _OPENMP
+    if (n > 0) omp_set_num_threads(n);
+    return omp_get_max_threads();
+#else
+    (void)n;
+    return 1;
+#endif
+}
+
 enum { OR_OK = 0, OR_ERR_ARG = 1, OR_ERR_FOLDED = 2, OR_ERR_BREAKDOWN = 3,
        OR_ERR_NOT_SPD = 4, OR_ERR_NOT_CONVERGED = 5, OR_ERR_RANGE = 6 };
 
@@ -452,6 +476,7 @@ int or_load(int dim, int n, const double* coords, const double* fq, double* b) {
 void or_apply(int dim, int n, const double* A, const double* x, double* y) {
     int S = (int)pw_int(3, dim);
     long nn = pw_int(n, dim);
+    OR_PARALLEL_FOR
     for (long id = 0; id < nn; id++) {
         int c[3];
         node_coords(dim, n, id, c);
@@ -480,6 +505,7 @@ void or_smooth(int dim, int n, const double* A, const double* b, double* x, int 
     long nn = pw_int(n, dim);
     for (int cc = 0; cc < C; cc++) {
         int col = reverse ? C - 1 - cc : cc;
+        OR_PARALLEL_FOR
         for (long id = 0; id < nn; id++) {
             int c[3];
             node_coords(dim, n, id, c);
@@ -712,6 +738,7 @@ void or_restrict(int dim, int nf, const double* pw, const double* r, double* bc)
 void or_prolong(int dim, int nf, const double* pw, const double* xc, double* x) {
     int ns = 1 << dim, nc = (nf + 1) / 2;
     long nn = pw_int(nf, dim);
+    OR_PARALLEL_FOR
     for (long i = 0; i < nn; i++) {
         int ci[3];
         node_coords(dim, nf, i, ci);
@@ -819,6 +846,7 @@ static void vcycle_level(or_hier* h, int l) {
     }
     or_smooth(dim, n, h->A[l], h->b[l], h->x[l], 0);
     or_apply(dim, n, h->A[l], h->x[l], h->r[l]);
+    OR_PARALLEL_FOR
     for (long i = 0; i < nn; i++) h->r[l][i] = h->b[l][i] - h->r[l][i];
     or_restrict(dim, n, h->P[l], h->r[l], h->b[l + 1]);
     vcycle_level(h, l + 1);
@@ -1027,6 +1055,7 @@ int or_pcg(or_hier* h, const double* b, double* x, double tol, int maxit, int mo
         double pq = dot(nn, p, q);
         if (!(pq > 0.0)) { st = OR_ERR_NOT_SPD; break; }
         double alpha = rz / pq;
+        OR_PARALLEL_FOR
         for (long i = 0; i < nn; i++) { x[i] += alpha * p[i]; r[i] -= alpha * q[i]; }
         rn = sqrt(dot(nn, r, r));
         if (hist) hist[k] = rn / bnorm;
@@ -1041,6 +1070,7 @@ int or_pcg(or_hier* h, const double* b, double* x, double tol, int maxit, int mo
         precond(h, r, z);
         double rzn = dot(nn, r, z);
         double beta = flexible ? (rzn - dot(nn, r, zo)) / rz : rzn / rz;
+        OR_PARALLEL_FOR
         for (long i = 0; i < nn; i++) p[i] = z[i] + beta * p[i];
         rz = rzn;
     }

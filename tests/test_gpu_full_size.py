@@ -145,6 +145,33 @@ def test_adjoint_1025_gradient_and_differences():
         assert abs(fd - g[c]) <= 1e-5 * max(abs(g[c]), 1e-3 * scale), (c, fd, g[c])
 
 
+def test_adjoint_1025_gradient_against_oracle_solves():
+    """End to end at the full size: the oracle solves u and lambda itself
+    (FP64 PCG to 1e-10, its OpenMP build) and contracts them; the library's
+    gradient through torch.autograd (its own solves to 1e-10) must match that
+    to 1e-8 relative, and u and lambda to 1e-9 (the PCG bound).  Both sides'
+    solutions agree far closer than their residuals alone guarantee, because
+    both iterate the same preconditioned recursion on the same operator."""
+    (prob,) = inputs.annulus_adjoint(1025, batch=1)
+    dev = "cuda"
+    coords = torch.as_tensor(prob.coords, device=dev)
+    m = torch.as_tensor(prob.extra["m"], device=dev).requires_grad_(True)
+    f = torch.as_tensor(prob.rhs, device=dev).requires_grad_(True)
+    u_obs = torch.as_tensor(prob.extra["u_obs"], device=dev)
+    s = binding.Solver(2, prob.n)
+    u = autograd.solve(m, f, coords, s, tol=1e-10, maxit=1000)
+    (0.5 * ((u - u_obs) ** 2).sum()).backward()
+    g = m.grad.cpu().numpy()
+    H = oracle.Hierarchy(oracle.assemble(prob.coords, prob.kappa), omp=True)
+    uo, _, _, tru, stu = H.pcg(prob.rhs, tol=1e-10, maxit=1000)
+    lo, _, _, trl, stl = H.pcg(uo - prob.extra["u_obs"], tol=1e-10, maxit=1000)
+    assert stu == 0 and stl == 0
+    go = prob.kappa * oracle.adjoint_grad(prob.coords, uo, lo)
+    assert relerr(u.detach().cpu().numpy(), uo) <= 1e-9
+    assert relerr(f.grad.cpu().numpy(), lo) <= 1e-9
+    assert relerr(g, go) <= 1e-8
+
+
 def test_batch_stream_first_32_problems():
     probs = inputs.bump_batch(count=512, nrhs=4, limit=32)
     solvers = []

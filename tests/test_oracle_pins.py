@@ -911,3 +911,20 @@ def test_boundary_rhs_equals_extended_grid_couplings(dim):
         want[idx] = s
     got = oracle.boundary_rhs(coords, kappa, g)
     assert np.abs(got - want).max() <= 1e-13 * np.abs(want).max()
+
+
+# ------------------------------------------------------------------ the OpenMP build
+@pytest.mark.parametrize("dim,n", [(2, 129), (3, 17)])
+def test_openmp_build_gives_the_same_bits(dim, n):
+    """The OpenMP build shares out only loops whose iterations are
+    independent, so its V-cycles and CG iterates are bitwise those of the
+    plain build (it exists to time the oracle on all host cores)."""
+    oracle.threads(4)
+    p = inputs.annulus_lognormal(n) if dim == 2 else inputs.shell_two_layer(n)
+    A = oracle.assemble(p.coords, p.kappa)
+    H1, H2 = oracle.Hierarchy(A), oracle.Hierarchy(A, omp=True)
+    r = inputs.rhs_uniform(np.random.default_rng(2), (n,) * dim)
+    assert np.array_equal(H1.vcycle(r), H2.vcycle(r))
+    x1, it1, h1, t1, s1 = H1.pcg(p.rhs, tol=1e-10, maxit=400)
+    x2, it2, h2, t2, s2 = H2.pcg(p.rhs, tol=1e-10, maxit=400)
+    assert it1 == it2 and np.array_equal(x1, x2) and np.array_equal(h1, h2)
