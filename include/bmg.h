@@ -344,7 +344,7 @@ bmg_status bmg_profile_read(bmg_ctx* ctx, int kind, double* ms, long long* launc
 /* Tile shape of the streaming 2-D V-cycle kernels on level `level` (the
    kernels that go from level to level+1 and back): wc coarse columns and
    hc coarse rows per CTA.  set: wc a multiple of 8 in [8, 64], hc a positive multiple
-   of the rows per step (4 in FP32, 2 in FP64); BMG_ERR_ARG otherwise or when
+   of the rows per step (2); BMG_ERR_ARG otherwise or when
    the context does not use the streaming kernels. */
 bmg_status bmg_get_tiles(const bmg_ctx* ctx, int level, int* wc, int* hc);
 bmg_status bmg_set_tiles(bmg_ctx* ctx, int level, int wc, int hc);

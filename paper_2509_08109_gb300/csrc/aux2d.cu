@@ -6,17 +6,26 @@
 // is its coarse level, reached through P = M_p^-1 C and R = P^T.
 //
 // Host side (bmg_aux_create): interior numbering of the vertices, the CSR
-// patterns of A_p, M_p (rows and columns: interior vertices) and C (rows:
-// interior vertices; columns: the coarse grid's interior nodes in its padded
-// layout), the (triangle, cell) pairs whose bounding boxes and separating
-// axes overlap, and for every stored entry the list of the local
-// contributions that sum to it, in triangle (or pair) order.
+// patterns of A_p and M_p (rows and columns: interior vertices) with, for
+// every stored entry, the list of the element contributions that sum to it
+// (triangle order), the vertex-to-triangle incidence, and bounds (from the
+// triangles' bounding boxes in computational space) that size the
+// workspace of the coupled mass.
 //
-// Device side: per-triangle P1 element matrices and per-pair coupled-mass
-// blocks are formed once (FP64), then every stored entry sums its
-// contributions in list order -- deterministic, no atomics.  A solve runs
-// the cycle with CSR kernels (one thread per row), device-side CG scalars
-// for the mass solves, and the coarse context's own V-cycle.
+// Device side, setup: the rasterisation of the mapped triangles over the
+// computational cells (Sec. 2.3.1's cell-wise evaluation): one thread per
+// triangle counts the cells of its bounding box that no edge separates from
+// it, a prefix sum numbers the (triangle, cell) pairs in triangle order and
+// a second pass writes them; one thread per interior vertex then lists the
+// contributions (pair, local vertex, cell corner) of its row of C in that
+// order, sorts them by column (stably) and writes C's CSR pattern and the
+// contribution list of every entry; C^T and the sliced-ELLPACK copies of C
+// and C^T follow by counting and prefix sums.  Then per-triangle P1 element
+// matrices and per-pair coupled-mass blocks are formed once (FP64) and every
+// stored entry sums its contributions in list order -- deterministic, no
+// atomics in any value.  A solve runs the cycle with CSR kernels (one thread
+// per row), device-side CG scalars for the mass solves, and the coarse
+// context's own V-cycle.
 #include <math.h>
 #include <string.h>
 
@@ -548,6 +557,254 @@ __global__ void k_lanczos_shift(int nr, double* __restrict__ q, double* __restri
 
 inline int blocks(long long n) { return cdiv(n, kAuxThreads); }
 
+// ------------------------------------------------------------------ rasterisation (device setup)
+// Cell range of the bounding box of triangle t's image (s, t coordinates in
+// [0,1]^2), clamped to the n-1 cells per side; the same arithmetic as the
+// host bound.
+__host__ __device__ inline int cell_of(double v, double h, int n) {
+    long long k = (long long)floor(v / h);
+    if (k < 0) k = 0;
+    if (k > n - 2) k = n - 2;
+    return (int)k;
+}
+
+// Separating-axis test of a triangle against an axis-aligned box (touching
+// counts).  Products and sums rounded one by one (no fused multiply-add),
+// as on the host.
+__device__ bool tri_box_overlap_d(const double* sx, const double* sy, double x0, double y0, double x1, double y1) {
+    const double mnx = fmin(sx[0], fmin(sx[1], sx[2])), mxx = fmax(sx[0], fmax(sx[1], sx[2]));
+    const double mny = fmin(sy[0], fmin(sy[1], sy[2])), mxy = fmax(sy[0], fmax(sy[1], sy[2]));
+    if (mxx < x0 || mnx > x1 || mxy < y0 || mny > y1) return false;
+    for (int e = 0; e < 3; e++) {
+        const int a = e, b = (e + 1) % 3, c = (e + 2) % 3;
+        const double nx = __dsub_rn(sy[b], sy[a]), ny = __dsub_rn(sx[a], sx[b]);
+        const double side = __dadd_rn(__dmul_rn(nx, __dsub_rn(sx[c], sx[a])), __dmul_rn(ny, __dsub_rn(sy[c], sy[a])));
+        const double cx[4] = {x0, x1, x0, x1}, cy[4] = {y0, y0, y1, y1};
+        bool all_out = true;
+        for (int k = 0; k < 4 && all_out; k++) {
+            const double v =
+                __dadd_rn(__dmul_rn(nx, __dsub_rn(cx[k], sx[a])), __dmul_rn(ny, __dsub_rn(cy[k], sy[a])));
+            if (side > 0 ? v >= 0 : v <= 0) all_out = false;
+        }
+        if (all_out) return false;
+    }
+    return true;
+}
+
+// Pairs of triangle t: the cells (ci, cj) of its bounding box, cj then ci
+// ascending, that the separating-axis test keeps.  count only, or write
+// them from pair index p0.
+__device__ int tri_pairs(int t, const int* __restrict__ tri, const double* __restrict__ st, int n, int* pair_tri,
+                         int* pair_cell, int p0) {
+    const double h = 1.0 / (n - 1);
+    double sx[3], sy[3];
+    for (int a = 0; a < 3; a++) {
+        sx[a] = st[2 * tri[3 * t + a]];
+        sy[a] = st[2 * tri[3 * t + a] + 1];
+    }
+    const int i0 = cell_of(fmin(sx[0], fmin(sx[1], sx[2])), h, n), i1 = cell_of(fmax(sx[0], fmax(sx[1], sx[2])), h, n);
+    const int j0 = cell_of(fmin(sy[0], fmin(sy[1], sy[2])), h, n), j1 = cell_of(fmax(sy[0], fmax(sy[1], sy[2])), h, n);
+    int k = 0;
+    for (int cj = j0; cj <= j1; cj++)
+        for (int ci = i0; ci <= i1; ci++) {
+            if (!tri_box_overlap_d(sx, sy, ci * h, cj * h, (ci + 1) * h, (cj + 1) * h)) continue;
+            if (pair_tri) {
+                pair_tri[p0 + k] = t;
+                pair_cell[p0 + k] = cj * (n - 1) + ci;
+            }
+            k++;
+        }
+    return k;
+}
+
+__global__ void k_pair_count(int ntri, const int* __restrict__ tri, const double* __restrict__ st, int n,
+                             int* __restrict__ cnt) {
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t < ntri) cnt[t] = tri_pairs(t, tri, st, n, nullptr, nullptr, 0);
+}
+
+__global__ void k_pair_fill(int ntri, const int* __restrict__ tri, const double* __restrict__ st, int n,
+                            const int* __restrict__ poff, int* __restrict__ pair_tri, int* __restrict__ pair_cell) {
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t < ntri) tri_pairs(t, tri, st, n, pair_tri, pair_cell, poff[t]);
+}
+
+// Row i of C: the contributions (12 p + 4 a + b: pair p, local vertex a of
+// its triangle, cell corner b) of the pairs of the triangles incident to
+// vertex i (triangle order, then pair order, then corner), to the interior
+// coarse nodes (column j*ld + i), sorted stably by column in the row's
+// scratch; counts the distinct columns.
+__global__ void k_crow_records(int nvi, const int* __restrict__ vt_ptr, const int* __restrict__ vt_tri,
+                               const int* __restrict__ vt_a, const int* __restrict__ poff,
+                               const int* __restrict__ pair_cell, int n, int ld, const long long* __restrict__ rec_off,
+                               int* __restrict__ rec_col, int* __restrict__ rec_src, int* __restrict__ rec_cnt,
+                               int* __restrict__ uniq) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= nvi) return;
+    int* col = rec_col + rec_off[i];
+    int* src = rec_src + rec_off[i];
+    int m = 0;
+    for (int e = vt_ptr[i]; e < vt_ptr[i + 1]; e++) {
+        const int t = vt_tri[e], a = vt_a[e];
+        for (int p = poff[t]; p < poff[t + 1]; p++) {
+            const int cell = pair_cell[p];
+            const int ci = cell % (n - 1), cj = cell / (n - 1);
+            for (int b = 0; b < 4; b++) {
+                const int ii = ci + (b & 1), jj = cj + (b >> 1);
+                if (ii < 1 || jj < 1 || ii > n - 2 || jj > n - 2) continue;
+                // stable insertion by column
+                const int c = jj * ld + ii, v = 12 * p + 4 * a + b;
+                int q = m;
+                while (q > 0 && col[q - 1] > c) {
+                    col[q] = col[q - 1];
+                    src[q] = src[q - 1];
+                    q--;
+                }
+                col[q] = c;
+                src[q] = v;
+                m++;
+            }
+        }
+    }
+    int u = 0;
+    for (int q = 0; q < m; q++)
+        if (q == 0 || col[q] != col[q - 1]) u++;
+    rec_cnt[i] = m;
+    uniq[i] = u;
+}
+
+// C's CSR pattern (columns, row of every entry) and the contribution lists:
+// entry e of row i sums gidx[gptr[e] .. gptr[e+1]).
+__global__ void k_crow_write(int nvi, const long long* __restrict__ rec_off, const int* __restrict__ rec_col,
+                             const int* __restrict__ rec_src, const int* __restrict__ rec_cnt,
+                             const int* __restrict__ c_ptr, const int* __restrict__ g_off, int* __restrict__ c_col,
+                             int* __restrict__ c_row, int* __restrict__ c_gptr, int* __restrict__ c_gidx) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= nvi) return;
+    const int* col = rec_col + rec_off[i];
+    const int* src = rec_src + rec_off[i];
+    const int m = rec_cnt[i];
+    int e = c_ptr[i] - 1;
+    const int g = g_off[i];
+    for (int q = 0; q < m; q++) {
+        if (q == 0 || col[q] != col[q - 1]) {
+            e++;
+            c_col[e] = col[q];
+            c_row[e] = i;
+            c_gptr[e] = g + q;
+        }
+        c_gidx[g + q] = src[q];
+    }
+}
+
+// C^T: rows are the interior coarse nodes q = (j-1)(n-2) + (i-1); its
+// entries are C's, in C order within a row (counted, placed, then each row
+// sorted by C index, so the placement order does not matter).
+__device__ __forceinline__ int q_of_col(int col, int ld, int n) { return (col / ld - 1) * (n - 2) + (col % ld - 1); }
+
+__global__ void k_ct_count(int nnz, const int* __restrict__ c_col, int ld, int n, int* __restrict__ cnt) {
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k < nnz) atomicAdd(&cnt[q_of_col(c_col[k], ld, n)], 1);
+}
+
+__global__ void k_ct_fill(int nnz, const int* __restrict__ c_col, const int* __restrict__ c_row, int ld, int n,
+                          const int* __restrict__ ct_ptr, int* __restrict__ fill, int* __restrict__ ct_col,
+                          int* __restrict__ ct_perm) {
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= nnz) return;
+    const int q = q_of_col(c_col[k], ld, n);
+    const int pos = ct_ptr[q] + atomicAdd(&fill[q], 1);
+    ct_col[pos] = c_row[k];
+    ct_perm[pos] = k;
+}
+
+__global__ void k_ct_sort(int nq, const int* __restrict__ ct_ptr, int* __restrict__ ct_col, int* __restrict__ ct_perm) {
+    const int q = blockIdx.x * blockDim.x + threadIdx.x;
+    if (q >= nq) return;
+    for (int e = ct_ptr[q] + 1; e < ct_ptr[q + 1]; e++) {
+        const int k = ct_perm[e], c = ct_col[e];
+        int f = e;
+        while (f > ct_ptr[q] && ct_perm[f - 1] > k) {
+            ct_perm[f] = ct_perm[f - 1];
+            ct_col[f] = ct_col[f - 1];
+            f--;
+        }
+        ct_perm[f] = k;
+        ct_col[f] = c;
+    }
+}
+
+// Sliced ELLPACK (32-row slices, entries column-major in a slice, rows
+// padded with column 0 / map -1 to the slice's longest row): slot counts per
+// slice, then the pattern; map[slot] = the CSR entry (through `through` if given).
+__global__ void k_sell_width(int nr, const int* __restrict__ ptr, int* __restrict__ slots) {
+    const int sl = blockIdx.x * blockDim.x + threadIdx.x;
+    if (sl >= (nr + 31) / 32) return;
+    int w = 0;
+    for (int i = sl * 32; i < min(nr, sl * 32 + 32); i++) w = max(w, ptr[i + 1] - ptr[i]);
+    slots[sl] = 32 * w;
+}
+
+__global__ void k_sell_pattern(int nr, const int* __restrict__ ptr, const int* __restrict__ col,
+                               const int* __restrict__ through, const int* __restrict__ off, int* __restrict__ scol,
+                               int* __restrict__ smap) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= nr) return;
+    const int sl = i / 32, l = i % 32;
+    for (int k = ptr[i]; k < ptr[i + 1]; k++) {
+        const int slot = off[sl] + 32 * (k - ptr[i]) + l;
+        scol[slot] = col[k];
+        smap[slot] = through ? through[k] : k;
+    }
+}
+
+// Exclusive prefix sum of n ints (out[n] = total), three passes over
+// kScanB-element blocks; totals fit an int (the callers check the bounds).
+constexpr int kScanB = 1024;
+
+__global__ void k_scan_local(const int* __restrict__ in, int n, int* __restrict__ out, int* __restrict__ bsum) {
+    __shared__ int sh[kScanB];
+    const int base = blockIdx.x * kScanB;
+    const int t = threadIdx.x;   // kScanB / 4 threads, four elements each
+    int v[4], s = 0;
+    for (int k = 0; k < 4; k++) {
+        const int idx = base + 4 * t + k;
+        v[k] = idx < n ? in[idx] : 0;
+        s += v[k];
+    }
+    sh[t] = s;
+    __syncthreads();
+    for (int o = 1; o < kScanB / 4; o <<= 1) {   // inclusive scan of the per-thread sums (Hillis-Steele)
+        const int add = t >= o ? sh[t - o] : 0;
+        __syncthreads();
+        sh[t] += add;
+        __syncthreads();
+    }
+    int run = sh[t] - s;
+    for (int k = 0; k < 4; k++) {
+        const int idx = base + 4 * t + k;
+        if (idx < n) out[idx] = run;
+        run += v[k];
+    }
+    if (t == kScanB / 4 - 1) bsum[blockIdx.x] = sh[t];
+}
+
+__global__ void k_scan_blocks(int* __restrict__ bsum, int nb, int* __restrict__ total) {
+    if (threadIdx.x != 0) return;
+    int run = 0;
+    for (int b = 0; b < nb; b++) {
+        const int v = bsum[b];
+        bsum[b] = run;
+        run += v;
+    }
+    *total = run;
+}
+
+__global__ void k_scan_add(int* __restrict__ out, int n, const int* __restrict__ bsum) {
+    const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx < n) out[idx] += bsum[idx / kScanB];
+}
+
 // ------------------------------------------------------------------ host structure
 struct Csr {
     std::vector<int> ptr, col;       // rows, columns
@@ -622,26 +879,6 @@ bool build_sell(const std::vector<int>& ptr, const std::vector<int>& col, const 
     return true;
 }
 
-// separating-axis test of a triangle against an axis-aligned box (touching counts)
-bool tri_box_overlap(const double* sx, const double* sy, double x0, double y0, double x1, double y1) {
-    const double mnx = std::min(sx[0], std::min(sx[1], sx[2])), mxx = std::max(sx[0], std::max(sx[1], sx[2]));
-    const double mny = std::min(sy[0], std::min(sy[1], sy[2])), mxy = std::max(sy[0], std::max(sy[1], sy[2]));
-    if (mxx < x0 || mnx > x1 || mxy < y0 || mny > y1) return false;
-    for (int e = 0; e < 3; e++) {
-        const int a = e, b = (e + 1) % 3, c = (e + 2) % 3;
-        const double nx = sy[b] - sy[a], ny = sx[a] - sx[b];      // edge normal
-        const double side = nx * (sx[c] - sx[a]) + ny * (sy[c] - sy[a]);
-        const double cx[4] = {x0, x1, x0, x1}, cy[4] = {y0, y0, y1, y1};
-        bool all_out = true;
-        for (int k = 0; k < 4 && all_out; k++) {
-            const double v = nx * (cx[k] - sx[a]) + ny * (cy[k] - sy[a]);
-            if (side > 0 ? v >= 0 : v <= 0) all_out = false;
-        }
-        if (all_out) return false;
-    }
-    return true;
-}
-
 }  // namespace
 
 struct bmg_aux {
@@ -650,17 +887,28 @@ struct bmg_aux {
     int nv = 0, ntri = 0, nvi = 0, n = 0, ld = 0;
     std::vector<int> tri, vid, vtx;      // vertex -> interior id (-1), interior id -> vertex
     std::vector<double> xy, st;
-    std::vector<int> pair_tri, pair_cell;
     Csr am;                              // A_p and M_p pattern (contributions: 9 t + 3 a + b)
     std::vector<int> diag_pos;
     Csr lump;                            // lumped mass: one "entry" per interior row
-    Csr cm;                              // C pattern (contributions: 12 p + 4 a + b)
-    std::vector<int> ct_ptr, ct_col, ct_perm, ct_map;   // C^T rows: interior coarse nodes
-    Sell s_am, s_c, s_ct;                // the products run on SELL-32 copies
+    std::vector<int> ct_map;             // C^T rows (interior coarse nodes) -> padded coarse index
+    Sell s_am;                           // the products run on SELL-32 copies
+    // coupled mass, built on the device at setup: vertex-to-triangle
+    // incidence (triangle order) and the workspace bounds
+    std::vector<int> vt_ptr, vt_tri, vt_a;
+    std::vector<long long> rec_off;      // per interior row: first slot of its record scratch
+    long long cap_pairs = 0, cap_rec = 0, cap_sell_c = 0, cap_sell_ct = 0;
+    int npairs = 0, nnz_c = 0, nrec_c = 0, nsell_c = 0, nsell_ct = 0;   // actual sizes (after setup)
+    mutable std::vector<int> c_ptr_h, c_col_h;                          // C pattern, read back on export
     size_t ws_need = 0;
     bool ready = false;
     // device (carved from the workspace)
     int *d_tri = nullptr, *d_vid = nullptr, *d_vtx = nullptr, *d_pair_tri = nullptr, *d_pair_cell = nullptr;
+    int *d_vt_ptr = nullptr, *d_vt_tri = nullptr, *d_vt_a = nullptr, *d_pcnt = nullptr, *d_poff = nullptr;
+    long long* d_rec_off = nullptr;
+    int *d_rec_col = nullptr, *d_rec_src = nullptr, *d_rec_cnt = nullptr, *d_uniq = nullptr, *d_c_ptr = nullptr,
+        *d_g_off = nullptr, *d_c_col = nullptr, *d_c_row = nullptr;
+    int *d_ct_ptr = nullptr, *d_ct_cnt = nullptr, *d_ct_col = nullptr, *d_ct_perm = nullptr, *d_sl = nullptr,
+        *d_scan = nullptr, *d_total = nullptr;
     double *d_xy = nullptr, *d_st = nullptr;
     int *d_am_gptr = nullptr, *d_am_gidx = nullptr, *d_diag = nullptr;
     int *d_lp_gptr = nullptr, *d_lp_gidx = nullptr;
@@ -713,12 +961,35 @@ size_t carve_aux(bmg_aux& x, char* base) {
         return p;
     };
     const size_t I = sizeof(int), D = sizeof(double);
-    const size_t npairs = x.pair_tri.size();
+    const size_t npairs = (size_t)x.cap_pairs, nrec = (size_t)x.cap_rec;
+    const size_t nq = x.ct_map.size();
     x.d_tri = (int*)take(I * x.tri.size());
     x.d_vid = (int*)take(I * x.nv);
     x.d_vtx = (int*)take(I * x.nvi);
     x.d_pair_tri = (int*)take(I * npairs);
     x.d_pair_cell = (int*)take(I * npairs);
+    x.d_vt_ptr = (int*)take(I * x.vt_ptr.size());
+    x.d_vt_tri = (int*)take(I * x.vt_tri.size());
+    x.d_vt_a = (int*)take(I * x.vt_a.size());
+    x.d_pcnt = (int*)take(I * (x.ntri + 1));
+    x.d_poff = (int*)take(I * (x.ntri + 1));
+    x.d_rec_off = (long long*)take(sizeof(long long) * x.rec_off.size());
+    x.d_rec_col = (int*)take(I * nrec);
+    x.d_rec_src = (int*)take(I * nrec);
+    x.d_rec_cnt = (int*)take(I * (x.nvi + 1));
+    x.d_uniq = (int*)take(I * (x.nvi + 1));
+    x.d_c_ptr = (int*)take(I * (x.nvi + 1));
+    x.d_g_off = (int*)take(I * (x.nvi + 1));
+    x.d_c_col = (int*)take(I * nrec);
+    x.d_c_row = (int*)take(I * nrec);
+    x.d_ct_ptr = (int*)take(I * (nq + 1));
+    x.d_ct_cnt = (int*)take(I * (nq + 1));
+    x.d_ct_col = (int*)take(I * nrec);
+    x.d_ct_perm = (int*)take(I * nrec);
+    const size_t nsl = std::max<size_t>((size_t)(x.nvi + 31) / 32, (nq + 31) / 32) + 1;
+    x.d_sl = (int*)take(I * nsl);
+    x.d_scan = (int*)take(I * (std::max<size_t>({(size_t)x.ntri, (size_t)x.nvi, nq, nsl}) / kScanB + 2));
+    x.d_total = (int*)take(I * 4);
     x.d_xy = (double*)take(D * x.xy.size());
     x.d_st = (double*)take(D * x.st.size());
     x.d_am_gptr = (int*)take(I * x.am.gptr.size());
@@ -726,15 +997,15 @@ size_t carve_aux(bmg_aux& x, char* base) {
     x.d_diag = (int*)take(I * x.diag_pos.size());
     x.d_lp_gptr = (int*)take(I * x.lump.gptr.size());
     x.d_lp_gidx = (int*)take(I * x.lump.gidx.size());
-    x.d_c_gptr = (int*)take(I * x.cm.gptr.size());
-    x.d_c_gidx = (int*)take(I * x.cm.gidx.size());
+    x.d_c_gptr = (int*)take(I * (nrec + 1));
+    x.d_c_gidx = (int*)take(I * nrec);
     x.d_ct_map = (int*)take(I * x.ct_map.size());
     x.d_lk = (double*)take(D * 9 * (size_t)x.ntri);
     x.d_lm = (double*)take(D * 9 * (size_t)x.ntri);
     x.d_loc = (double*)take(D * 12 * npairs);
     x.d_va = (double*)take(D * x.am.col.size());
     x.d_vm = (double*)take(D * x.am.col.size());
-    x.d_vc = (double*)take(D * x.cm.col.size());
+    x.d_vc = (double*)take(D * nrec);
     x.d_dinv = (double*)take(D * x.nvi);
     x.d_mlinv = (double*)take(D * x.nvi);
     double** vecs[] = {&x.d_f, &x.d_u, &x.d_u2, &x.d_r, &x.d_y, &x.d_cres, &x.d_cp, &x.d_cq, &x.d_w,
@@ -745,21 +1016,21 @@ size_t carve_aux(bmg_aux& x, char* base) {
     x.d_sam_off = (int*)take(I * x.s_am.off.size());
     x.d_sam_col = (int*)take(I * x.s_am.col.size());
     x.d_sam_map = (int*)take(I * x.s_am.map.size());
-    x.d_sc_off = (int*)take(I * x.s_c.off.size());
-    x.d_sc_col = (int*)take(I * x.s_c.col.size());
-    x.d_sc_map = (int*)take(I * x.s_c.map.size());
-    x.d_sct_off = (int*)take(I * x.s_ct.off.size());
-    x.d_sct_col = (int*)take(I * x.s_ct.col.size());
-    x.d_sct_map = (int*)take(I * x.s_ct.map.size());
+    x.d_sc_off = (int*)take(I * ((x.nvi + 31) / 32 + 1));
+    x.d_sc_col = (int*)take(I * (size_t)x.cap_sell_c);
+    x.d_sc_map = (int*)take(I * (size_t)x.cap_sell_c);
+    x.d_sct_off = (int*)take(I * ((nq + 31) / 32 + 1));
+    x.d_sct_col = (int*)take(I * (size_t)x.cap_sell_ct);
+    x.d_sct_map = (int*)take(I * (size_t)x.cap_sell_ct);
     x.d_sva = (double*)take(D * x.s_am.col.size());
     x.d_svm = (double*)take(D * x.s_am.col.size());
-    x.d_svc = (double*)take(D * x.s_c.col.size());
-    x.d_svct = (double*)take(D * x.s_ct.col.size());
+    x.d_svc = (double*)take(D * (size_t)x.cap_sell_c);
+    x.d_svct = (double*)take(D * (size_t)x.cap_sell_ct);
     if (x.fp32) {
         const size_t F = sizeof(float);
         x.d_sva32 = (float*)take(F * x.s_am.col.size());
-        x.d_svc32 = (float*)take(F * x.s_c.col.size());
-        x.d_svct32 = (float*)take(F * x.s_ct.col.size());
+        x.d_svc32 = (float*)take(F * (size_t)x.cap_sell_c);
+        x.d_svct32 = (float*)take(F * (size_t)x.cap_sell_ct);
         float** fv[] = {&x.d_rs32, &x.d_dinv32, &x.d_mlinv32, &x.d_f32, &x.d_u32, &x.d_u32b, &x.d_r32};
         for (float** v : fv) *v = (float*)take(F * std::max(x.nvi, 1));
     }
@@ -1048,75 +1319,96 @@ bmg_status aux_create(bmg_ctx* coarse, int nv, const double* xy, const double* s
                 return BMG_ERR_ARG;
             }
     }
-    // (triangle, cell) pairs and the C pattern
+    // The coupled mass C is built on the device at setup.  Here: the
+    // incidence lists (interior vertex -> (triangle, local vertex), triangle
+    // order), the C^T row map, and bounds from the triangles' bounding boxes
+    // in computational space for every array the device build fills.
     {
         const int n = x->n;
         const double h = 1.0 / (n - 1);
-        std::vector<int> rr, cc, src;
+        std::vector<int> bcount(ntri);
+        std::vector<int> cellcov((size_t)(n - 1) * (n - 1), 0);
+        long long cap_pairs = 0;
         for (int t = 0; t < ntri; t++) {
             double sx[3], sy[3];
             for (int a = 0; a < 3; a++) {
                 sx[a] = x->st[2 * x->tri[3 * t + a]];
                 sy[a] = x->st[2 * x->tri[3 * t + a] + 1];
             }
-            auto cell_of = [&](double v) {
-                long long k = (long long)floor(v / h);
-                return (int)std::min<long long>(std::max<long long>(k, 0), n - 2);
-            };
-            const int i0 = cell_of(std::min(sx[0], std::min(sx[1], sx[2])));
-            const int i1 = cell_of(std::max(sx[0], std::max(sx[1], sx[2])));
-            const int j0 = cell_of(std::min(sy[0], std::min(sy[1], sy[2])));
-            const int j1 = cell_of(std::max(sy[0], std::max(sy[1], sy[2])));
+            const int i0 = cell_of(std::min(sx[0], std::min(sx[1], sx[2])), h, n);
+            const int i1 = cell_of(std::max(sx[0], std::max(sx[1], sx[2])), h, n);
+            const int j0 = cell_of(std::min(sy[0], std::min(sy[1], sy[2])), h, n);
+            const int j1 = cell_of(std::max(sy[0], std::max(sy[1], sy[2])), h, n);
+            bcount[t] = (i1 - i0 + 1) * (j1 - j0 + 1);
+            cap_pairs += bcount[t];
             for (int cj = j0; cj <= j1; cj++)
-                for (int ci = i0; ci <= i1; ci++) {
-                    if (!tri_box_overlap(sx, sy, ci * h, cj * h, (ci + 1) * h, (cj + 1) * h)) continue;
-                    const long long p = (long long)x->pair_tri.size();
-                    if (12 * (p + 1) > 0x7fffffffLL) {
-                        return BMG_ERR_SHAPE;
-                    }
-                    x->pair_tri.push_back(t);
-                    x->pair_cell.push_back(cj * (n - 1) + ci);
-                    for (int a = 0; a < 3; a++) {
-                        const int ia = x->vid[x->tri[3 * t + a]];
-                        if (ia < 0) continue;
-                        for (int b = 0; b < 4; b++) {
-                            const int i = ci + (b & 1), j = cj + (b >> 1);
-                            if (i < 1 || j < 1 || i > n - 2 || j > n - 2) continue;
-                            rr.push_back(ia);
-                            cc.push_back(j * x->ld + i);
-                            src.push_back((int)(12 * p + 4 * a + b));
-                        }
-                    }
+                for (int ci = i0; ci <= i1; ci++) cellcov[(size_t)cj * (n - 1) + ci]++;
+        }
+        if (12 * cap_pairs > 0x7fffffffLL) return BMG_ERR_SHAPE;
+        x->cap_pairs = cap_pairs;
+        // incidence, counting sort by vertex (triangles ascending within a vertex)
+        x->vt_ptr.assign(x->nvi + 1, 0);
+        for (int t = 0; t < ntri; t++)
+            for (int a = 0; a < 3; a++) {
+                const int ia = x->vid[x->tri[3 * t + a]];
+                if (ia >= 0) x->vt_ptr[ia + 1]++;
+            }
+        for (int i = 0; i < x->nvi; i++) x->vt_ptr[i + 1] += x->vt_ptr[i];
+        x->vt_tri.resize(x->vt_ptr[x->nvi]);
+        x->vt_a.resize(x->vt_ptr[x->nvi]);
+        {
+            std::vector<int> pos(x->vt_ptr.begin(), x->vt_ptr.end() - 1);
+            for (int t = 0; t < ntri; t++)
+                for (int a = 0; a < 3; a++) {
+                    const int ia = x->vid[x->tri[3 * t + a]];
+                    if (ia < 0) continue;
+                    x->vt_tri[pos[ia]] = t;
+                    x->vt_a[pos[ia]] = a;
+                    pos[ia]++;
                 }
         }
-        if (!build_csr(x->nvi, rr, cc, src, x->cm)) {
-            return BMG_ERR_SHAPE;
+        // records of row i: at most 4 per bounding-box cell of each incident triangle
+        x->rec_off.assign(x->nvi + 1, 0);
+        long long sell_c = 0;
+        int slice_w = 0;
+        for (int i = 0; i < x->nvi; i++) {
+            long long rb = 0;
+            for (int e = x->vt_ptr[i]; e < x->vt_ptr[i + 1]; e++) rb += 4LL * bcount[x->vt_tri[e]];
+            x->rec_off[i + 1] = x->rec_off[i] + rb;
+            if (rb > 0x7fffffffLL) return BMG_ERR_SHAPE;
+            slice_w = std::max(slice_w, (int)rb);
+            if (i % 32 == 31 || i == x->nvi - 1) {
+                sell_c += 32LL * slice_w;
+                slice_w = 0;
+            }
         }
-        // C^T: rows = interior coarse nodes (j-1)(n-2) + (i-1), entries in C order
+        x->cap_rec = x->rec_off[x->nvi];
+        if (x->cap_rec > 0x7fffffffLL || sell_c > 0x7fffffffLL) return BMG_ERR_SHAPE;
+        x->cap_sell_c = sell_c;
+        // C^T rows: interior coarse nodes; entries at most 3 per triangle whose
+        // bounding box covers one of the node's four cells
         const int nq = (n - 2) * (n - 2);
         x->ct_map.resize(nq);
         for (int j = 1; j <= n - 2; j++)
             for (int i = 1; i <= n - 2; i++) x->ct_map[(j - 1) * (n - 2) + (i - 1)] = j * x->ld + i;
-        x->ct_ptr.assign(nq + 1, 0);
-        auto q_of = [&](int col) { return (col / x->ld - 1) * (n - 2) + (col % x->ld - 1); };
-        for (int k = 0; k < (int)x->cm.col.size(); k++) x->ct_ptr[q_of(x->cm.col[k]) + 1]++;
-        for (int q = 0; q < nq; q++) x->ct_ptr[q + 1] += x->ct_ptr[q];
-        x->ct_col.resize(x->cm.col.size());
-        x->ct_perm.resize(x->cm.col.size());
-        std::vector<int> pos(x->ct_ptr.begin(), x->ct_ptr.end() - 1);
-        for (int i = 0; i < x->nvi; i++)
-            for (int k = x->cm.ptr[i]; k < x->cm.ptr[i + 1]; k++) {
-                const int q = q_of(x->cm.col[k]);
-                x->ct_col[pos[q]] = i;
-                x->ct_perm[pos[q]] = k;
-                pos[q]++;
+        long long sell_ct = 0;
+        long long w = 0;
+        for (int q = 0; q < nq; q++) {
+            const int I = q % (n - 2) + 1, J = q / (n - 2) + 1;
+            long long rb = 0;
+            for (int cj = J - 1; cj <= J; cj++)
+                for (int ci = I - 1; ci <= I; ci++) rb += 3LL * cellcov[(size_t)cj * (n - 1) + ci];
+            w = std::max(w, rb);
+            if (q % 32 == 31 || q == nq - 1) {
+                sell_ct += 32LL * w;
+                w = 0;
             }
+        }
+        if (sell_ct > 0x7fffffffLL) return BMG_ERR_SHAPE;
+        x->cap_sell_ct = sell_ct;
     }
     x->fp32 = o.krylov == 1 && o.mass_steps == 0 && c.opts.precision == BMG_PREC_FP32;
-    if (!build_sell(x->am.ptr, x->am.col, nullptr, x->s_am) || !build_sell(x->cm.ptr, x->cm.col, nullptr, x->s_c) ||
-        !build_sell(x->ct_ptr, x->ct_col, &x->ct_perm, x->s_ct)) {
-        return BMG_ERR_SHAPE;
-    }
+    if (!build_sell(x->am.ptr, x->am.col, nullptr, x->s_am)) return BMG_ERR_SHAPE;
     x->ws_need = carve_aux(*x, nullptr);
     *out = x.release();
     return BMG_OK;
@@ -1131,6 +1423,82 @@ extern "C" bmg_status bmg_aux_workspace_bytes(const bmg_aux* x, size_t* bytes) {
 }
 
 namespace {
+// Exclusive prefix sum on the stream: out[0..n) and out[n] = total (also
+// copied to *host_total, after a synchronisation).
+bmg_status scan_ints(bmg_aux& x, const int* in, int n, int* out, int* host_total, cudaStream_t s) {
+    const int nb = (n + kScanB - 1) / kScanB;
+    if (nb > 0) {
+        k_scan_local<<<nb, kScanB / 4, 0, s>>>(in, n, out, x.d_scan);
+        k_scan_blocks<<<1, 32, 0, s>>>(x.d_scan, nb, x.d_total);
+        k_scan_add<<<blocks(n), kAuxThreads, 0, s>>>(out, n, x.d_scan);
+        BMG_CUDA(cudaMemcpyAsync(out + n, x.d_total, sizeof(int), cudaMemcpyDeviceToDevice, s));
+    } else {
+        BMG_CUDA(cudaMemsetAsync(out, 0, sizeof(int), s));
+    }
+    if (host_total) {
+        BMG_CUDA(cudaMemcpyAsync(host_total, out + n, sizeof(int), cudaMemcpyDeviceToHost, s));
+        BMG_CUDA(cudaStreamSynchronize(s));
+    }
+    return BMG_OK;
+}
+
+// The rasterisation and the coupled mass's sparsity on the device: (triangle,
+// cell) pairs, C's CSR pattern with contribution lists, C^T, and the SELL
+// patterns of C and C^T (see the kernels above).
+bmg_status build_coupled_pattern(bmg_aux& x, cudaStream_t s) {
+    const int ntri = x.ntri, nvi = x.nvi, n = x.n, ld = x.ld;
+    const int nq = (int)x.ct_map.size();
+    k_pair_count<<<blocks(ntri), kAuxThreads, 0, s>>>(ntri, x.d_tri, x.d_st, n, x.d_pcnt);
+    BMG_TRY(scan_ints(x, x.d_pcnt, ntri, x.d_poff, &x.npairs, s));
+    if (x.npairs > x.cap_pairs) return BMG_ERR_SHAPE;   // cannot happen: pairs lie in bounding boxes
+    k_pair_fill<<<blocks(ntri), kAuxThreads, 0, s>>>(ntri, x.d_tri, x.d_st, n, x.d_poff, x.d_pair_tri, x.d_pair_cell);
+    if (nvi > 0) {
+        k_crow_records<<<blocks(nvi), kAuxThreads, 0, s>>>(nvi, x.d_vt_ptr, x.d_vt_tri, x.d_vt_a, x.d_poff,
+                                                           x.d_pair_cell, n, ld, x.d_rec_off, x.d_rec_col,
+                                                           x.d_rec_src, x.d_rec_cnt, x.d_uniq);
+    }
+    BMG_TRY(scan_ints(x, x.d_uniq, nvi, x.d_c_ptr, &x.nnz_c, s));
+    BMG_TRY(scan_ints(x, x.d_rec_cnt, nvi, x.d_g_off, &x.nrec_c, s));
+    if (nvi > 0) {
+        k_crow_write<<<blocks(nvi), kAuxThreads, 0, s>>>(nvi, x.d_rec_off, x.d_rec_col, x.d_rec_src, x.d_rec_cnt,
+                                                         x.d_c_ptr, x.d_g_off, x.d_c_col, x.d_c_row, x.d_c_gptr,
+                                                         x.d_c_gidx);
+    }
+    BMG_CUDA(cudaMemcpyAsync(x.d_c_gptr + x.nnz_c, x.d_g_off + nvi, sizeof(int), cudaMemcpyDeviceToDevice, s));
+    // C^T
+    BMG_CUDA(cudaMemsetAsync(x.d_ct_cnt, 0, sizeof(int) * (nq + 1), s));
+    if (x.nnz_c > 0) k_ct_count<<<blocks(x.nnz_c), kAuxThreads, 0, s>>>(x.nnz_c, x.d_c_col, ld, n, x.d_ct_cnt);
+    BMG_TRY(scan_ints(x, x.d_ct_cnt, nq, x.d_ct_ptr, nullptr, s));
+    BMG_CUDA(cudaMemsetAsync(x.d_ct_cnt, 0, sizeof(int) * (nq + 1), s));
+    if (x.nnz_c > 0)
+        k_ct_fill<<<blocks(x.nnz_c), kAuxThreads, 0, s>>>(x.nnz_c, x.d_c_col, x.d_c_row, ld, n, x.d_ct_ptr, x.d_ct_cnt,
+                                                          x.d_ct_col, x.d_ct_perm);
+    if (nq > 0) k_ct_sort<<<blocks(nq), kAuxThreads, 0, s>>>(nq, x.d_ct_ptr, x.d_ct_col, x.d_ct_perm);
+    // SELL copies: slot counts per slice, offsets, then the patterns over a
+    // cleared slot range (padding: column 0, map -1)
+    const int ns_c = (nvi + 31) / 32, ns_t = (nq + 31) / 32;
+    if (ns_c > 0) k_sell_width<<<blocks(ns_c), kAuxThreads, 0, s>>>(nvi, x.d_c_ptr, x.d_sl);
+    BMG_TRY(scan_ints(x, x.d_sl, ns_c, x.d_sc_off, &x.nsell_c, s));
+    if (x.nsell_c > x.cap_sell_c) return BMG_ERR_SHAPE;
+    BMG_CUDA(cudaMemsetAsync(x.d_sc_col, 0, sizeof(int) * (size_t)x.nsell_c, s));
+    BMG_CUDA(cudaMemsetAsync(x.d_sc_map, 0xff, sizeof(int) * (size_t)x.nsell_c, s));
+    if (nvi > 0)
+        k_sell_pattern<<<blocks(nvi), kAuxThreads, 0, s>>>(nvi, x.d_c_ptr, x.d_c_col, nullptr, x.d_sc_off,
+                                                           x.d_sc_col, x.d_sc_map);
+    if (ns_t > 0) k_sell_width<<<blocks(ns_t), kAuxThreads, 0, s>>>(nq, x.d_ct_ptr, x.d_sl);
+    BMG_TRY(scan_ints(x, x.d_sl, ns_t, x.d_sct_off, &x.nsell_ct, s));
+    if (x.nsell_ct > x.cap_sell_ct) return BMG_ERR_SHAPE;
+    BMG_CUDA(cudaMemsetAsync(x.d_sct_col, 0, sizeof(int) * (size_t)x.nsell_ct, s));
+    BMG_CUDA(cudaMemsetAsync(x.d_sct_map, 0xff, sizeof(int) * (size_t)x.nsell_ct, s));
+    if (nq > 0)
+        k_sell_pattern<<<blocks(nq), kAuxThreads, 0, s>>>(nq, x.d_ct_ptr, x.d_ct_col, x.d_ct_perm, x.d_sct_off,
+                                                          x.d_sct_col, x.d_sct_map);
+    BMG_CUDA(cudaGetLastError());
+    x.c_ptr_h.clear();
+    x.c_col_h.clear();
+    return BMG_OK;
+}
+
 bool on_device(const void* p) {
     cudaPointerAttributes a;
     if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
@@ -1154,8 +1522,6 @@ extern "C" bmg_status bmg_aux_setup(bmg_aux* x, void* ws, size_t bytes, const do
     BMG_TRY(up(x->d_tri, x->tri, s));
     BMG_TRY(up(x->d_vid, x->vid, s));
     BMG_TRY(up(x->d_vtx, x->vtx, s));
-    BMG_TRY(up(x->d_pair_tri, x->pair_tri, s));
-    BMG_TRY(up(x->d_pair_cell, x->pair_cell, s));
     BMG_TRY(up(x->d_xy, x->xy, s));
     BMG_TRY(up(x->d_st, x->st, s));
     BMG_TRY(up(x->d_am_gptr, x->am.gptr, s));
@@ -1163,25 +1529,22 @@ extern "C" bmg_status bmg_aux_setup(bmg_aux* x, void* ws, size_t bytes, const do
     BMG_TRY(up(x->d_diag, x->diag_pos, s));
     BMG_TRY(up(x->d_lp_gptr, x->lump.gptr, s));
     BMG_TRY(up(x->d_lp_gidx, x->lump.gidx, s));
-    BMG_TRY(up(x->d_c_gptr, x->cm.gptr, s));
-    BMG_TRY(up(x->d_c_gidx, x->cm.gidx, s));
     BMG_TRY(up(x->d_ct_map, x->ct_map, s));
     BMG_TRY(up(x->d_sam_off, x->s_am.off, s));
     BMG_TRY(up(x->d_sam_col, x->s_am.col, s));
     BMG_TRY(up(x->d_sam_map, x->s_am.map, s));
-    BMG_TRY(up(x->d_sc_off, x->s_c.off, s));
-    BMG_TRY(up(x->d_sc_col, x->s_c.col, s));
-    BMG_TRY(up(x->d_sc_map, x->s_c.map, s));
-    BMG_TRY(up(x->d_sct_off, x->s_ct.off, s));
-    BMG_TRY(up(x->d_sct_col, x->s_ct.col, s));
-    BMG_TRY(up(x->d_sct_map, x->s_ct.map, s));
-    const int npairs = (int)x->pair_tri.size();
+    BMG_TRY(up(x->d_vt_ptr, x->vt_ptr, s));
+    BMG_TRY(up(x->d_vt_tri, x->vt_tri, s));
+    BMG_TRY(up(x->d_vt_a, x->vt_a, s));
+    BMG_TRY(up(x->d_rec_off, x->rec_off, s));
+    BMG_TRY(build_coupled_pattern(*x, s));
+    const int npairs = x->npairs;
     k_tri_local<<<blocks(x->ntri), kAuxThreads, 0, s>>>(x->ntri, x->d_tri, x->d_xy, kappa, x->d_lk, x->d_lm,
                                                         x->d_st_aux);
     if (npairs > 0)
         k_pair_local<<<cdiv(npairs, 128), 128, 0, s>>>(npairs, x->d_pair_tri, x->d_pair_cell, x->d_tri, x->d_st,
                                                        coords, x->n, x->d_loc);
-    const int nnz = (int)x->am.col.size(), nnzc = (int)x->cm.col.size();
+    const int nnz = (int)x->am.col.size(), nnzc = x->nnz_c;
     if (nnz > 0) {
         k_gather<<<blocks(nnz), kAuxThreads, 0, s>>>(nnz, x->d_am_gptr, x->d_am_gidx, x->d_lk, x->d_va);
         k_gather<<<blocks(nnz), kAuxThreads, 0, s>>>(nnz, x->d_am_gptr, x->d_am_gidx, x->d_lm, x->d_vm);
@@ -1194,7 +1557,7 @@ extern "C" bmg_status bmg_aux_setup(bmg_aux* x, void* ws, size_t bytes, const do
     if (nnzc > 0) {
         k_gather<<<blocks(nnzc), kAuxThreads, 0, s>>>(nnzc, x->d_c_gptr, x->d_c_gidx, x->d_loc, x->d_vc);
     }
-    const int na = (int)x->s_am.col.size(), nc = (int)x->s_c.col.size(), nt = (int)x->s_ct.col.size();
+    const int na = (int)x->s_am.col.size(), nc = x->nsell_c, nt = x->nsell_ct;
     if (na > 0) {
         k_sell_fill<<<blocks(na), kAuxThreads, 0, s>>>(na, x->d_sam_map, x->d_va, x->d_sva);
         k_sell_fill<<<blocks(na), kAuxThreads, 0, s>>>(na, x->d_sam_map, x->d_vm, x->d_svm);
@@ -1415,8 +1778,16 @@ extern "C" bmg_status bmg_aux_export(const bmg_aux* x, int which, int* nrows, lo
                                      int* col, double* val) {
     if (!x || !nrows || !nnz || which < 0 || which > 2) return BMG_ERR_ARG;
     const bool isc = which == 2;
-    const std::vector<int>& ptr = isc ? x->cm.ptr : x->am.ptr;
-    const std::vector<int>& cl = isc ? x->cm.col : x->am.col;
+    if (isc && !x->ready) return BMG_ERR_STATE;   // C's pattern is built on the device at setup
+    if (isc && x->c_ptr_h.empty()) {
+        x->c_ptr_h.resize(x->nvi + 1);
+        x->c_col_h.resize(x->nnz_c);
+        BMG_CUDA(cudaMemcpy(x->c_ptr_h.data(), x->d_c_ptr, sizeof(int) * (x->nvi + 1), cudaMemcpyDeviceToHost));
+        if (x->nnz_c > 0)
+            BMG_CUDA(cudaMemcpy(x->c_col_h.data(), x->d_c_col, sizeof(int) * x->nnz_c, cudaMemcpyDeviceToHost));
+    }
+    const std::vector<int>& ptr = isc ? x->c_ptr_h : x->am.ptr;
+    const std::vector<int>& cl = isc ? x->c_col_h : x->am.col;
     *nrows = x->nvi;
     *nnz = (long long)cl.size();
     if (rowptr)

@@ -19,7 +19,7 @@
 // of 8-9 fine points (recomputed by both neighbours) covers the horizontal
 // dependencies.  A step handles K row pairs at once: thread (x, y) owns
 // the column pair (2x, 2x+1) of row pair y, so every colour phase keeps all
-// threads busy and a step costs six block barriers for 2K fine rows.  Rows
+// threads busy and a step costs six block barriers for 2K fine rows (K = 2).  Rows
 // arrive by TMA (cp.async.bulk.tensor) into a ring of RP = K+2+D row-pair
 // slots, each completed by an mbarrier with an expected byte count; the
 // next D = K pairs are in flight while a step computes; one thread issues all
@@ -780,7 +780,12 @@ __global__ void __launch_bounds__((WC + 8) * K * NR, sizeof(T) == 4 ? 3 : 1)
 
 // ------------------------------------------------------------------ host side
 template <typename T>
-constexpr int k_of() { return sizeof(T) == 4 ? 3 : 2; }   // FP32: ring of 8 slots, 3 CTAs/SM
+// Row pairs per step, 2 in both precisions.  Measured on the 4097^2
+// refinement-mode solve (autotuned strips): FP32 with 2 pairs (rings of 6
+// slots, 4 CTAs per SM) took 3.52 / 2.61 ms per solve in the up / down
+// kernels, against 3.69 / 2.75 with 3 pairs (3 CTAs per SM), 4.20 / 2.97
+// with 4 and 3.83 / 2.79 with 1.
+constexpr int k_of() { return sizeof(T) == 4 ? 2 : 2; }
 
 template <typename T, typename TF>
 int down_smem(int wc) { return Lay<T, TF, k_of<T>(), false>(wc).bytes(); }
