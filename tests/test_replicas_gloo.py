@@ -38,7 +38,7 @@ def _rank(rank, world, port, out):
 def test_two_replicas_report_slowest_rank_and_total_work():
     world = 2
     port = _free_port()
-    mgr = mp.Manager()
+    mgr = mp.get_context("spawn").Manager()   # no fork of a process that may hold threads
     out = mgr.dict()
     mp.spawn(_rank, args=(world, port, out), nprocs=world, join=True)
     assert out[0] == out[1]
