@@ -52,6 +52,9 @@ def parse():
     ap.add_argument("--variants", default="all", choices=["all", "fp64"],
                     help="fp64: time only the plain FP64 solve of the annulus workload (a short line for "
                          "profiling the FP64 kernels)")
+    ap.add_argument("--batch-count", type=int, default=512,
+                    help="problems of the batch workload (512 is the configuration; fewer: the first problems of "
+                         "the same stream, for profiling captures on a small device footprint)")
     ap.add_argument("--no-configs", action="store_true",
                     help="skip the compact runs of the other configurations (65^2 annulus, 257^3 shell, "
                          "512-problem batch, 1025^2 adjoint batch) that the default line carries")
@@ -578,7 +581,7 @@ def run_batch(args, steps=None, warmup=None, emit=True):
     torch.cuda.set_device(0)
     steps = args.steps if steps is None else steps
     warmup = args.warmup if warmup is None else warmup
-    probs = inputs.bump_batch(count=512, nrhs=4)
+    probs = inputs.bump_batch(count=512, nrhs=4, limit=args.batch_count)
     t0 = time.perf_counter()
     solvers = []
     for p in probs:
@@ -651,7 +654,8 @@ def run_batch(args, steps=None, warmup=None, emit=True):
     out = {"metric": METRIC, "value": dof / (ms * 1e-3), "unit": UNIT, "n_gpus": 1, "steps": steps,
            "warmup": warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
            "vs_baseline": None, "dtype": "f32 V-cycle / f64 residual", "data": "synthetic",
-           "config": {"workload": "bump_batch_512x4", "problems": 512, "rhs_per_problem": 4,
+           "config": {"workload": "bump_batch_512x4" if len(probs) == 512 else f"bump_batch_first{len(probs)}x4",
+                      "problems": len(probs), "rhs_per_problem": 4,
                       "dof_total_all_rhs": dof, "sizes": "n=2^k+1, k~U{6..10}, seed 5", "tol": TOL,
                       "engine": "bmg_batch_solve (size-class persistent kernels, 4 rhs per stencil read, "
                                 "one graph per batch iteration)" + (" [no graphs]" if args.no_graphs else ""),

@@ -89,14 +89,18 @@ bool map_planes(CUtensorMap* m, const float* base, int ld, int n, int planes, lo
               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
-// Interleaved vectors of a class: (right-hand side, column, row, member),
-// box of all right-hand sides, box_x columns, box_y rows, one member.
-bool map_vec(CUtensorMap* m, const float* base, int ld, int n, long long plane, int members, int box_x, int box_y) {
+// Interleaved vectors of a class, viewed as (g nodes x R values, column
+// group, row, member) so that the innermost box extent is g * R floats
+// (128 bytes for g = 8) rather than one node's R values; box of box_x
+// columns (a multiple of g), box_y rows, one member.  The shared-memory
+// image is the same as the rows' natural order.
+bool map_vec(CUtensorMap* m, const float* base, int ld, int n, long long plane, int members, int box_x, int box_y,
+             int g) {
     auto fn = encode_fn();
-    if (!fn) return false;
-    cuuint64_t dims[4] = {(cuuint64_t)R, (cuuint64_t)ld, (cuuint64_t)n, (cuuint64_t)members};
-    cuuint64_t strides[3] = {(cuuint64_t)R * 4, (cuuint64_t)ld * R * 4, (cuuint64_t)plane * R * 4};
-    cuuint32_t box[4] = {(cuuint32_t)R, (cuuint32_t)box_x, (cuuint32_t)box_y, 1};
+    if (!fn || box_x % g || ld % g) return false;
+    cuuint64_t dims[4] = {(cuuint64_t)g * R, (cuuint64_t)(ld / g), (cuuint64_t)n, (cuuint64_t)members};
+    cuuint64_t strides[3] = {(cuuint64_t)g * R * 4, (cuuint64_t)ld * R * 4, (cuuint64_t)plane * R * 4};
+    cuuint32_t box[4] = {(cuuint32_t)(g * R), (cuuint32_t)(box_x / g), (cuuint32_t)box_y, 1};
     cuuint32_t estr[4] = {1, 1, 1, 1};
     return fn(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, const_cast<float*>(base), dims, strides, box, estr,
               CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
@@ -660,10 +664,10 @@ bmg_status make_maps(Batch& B, BClass& K) {
     const int WW = 2 * K.wc + 16, WWc = K.wc + 8;
     const int nm = (int)K.prob.size();
     bool ok = map_planes(&K.mA, K.A, K.ld, K.n, NS2, K.plane, nm, WW);
-    ok = ok && map_vec(&K.mF, K.b, K.ld, K.n, K.plane, nm, WW, 2);
-    ok = ok && map_vec(&K.mXp, K.xp, K.ld, K.n, K.plane, nm, WW, 2);
+    ok = ok && map_vec(&K.mF, K.b, K.ld, K.n, K.plane, nm, WW, 2, 8);
+    ok = ok && map_vec(&K.mXp, K.xp, K.ld, K.n, K.plane, nm, WW, 2, 8);
     const BClass& C = B.cls[K.coarse];
-    ok = ok && map_vec(&K.mXc, C.xf, C.ld, C.n, C.plane, (int)C.prob.size(), WWc, 1);
+    ok = ok && map_vec(&K.mXc, C.xf, C.ld, C.n, C.plane, (int)C.prob.size(), WWc, 1, 4);
     return ok ? BMG_OK : BMG_ERR_DEVICE;
 }
 

@@ -28,10 +28,10 @@
 // by the global timer; on expiry the CTA records BMG_ERR_TIMEOUT, drains its
 // outstanding copies (bounded) and returns.
 //
-// Several right-hand sides (NR > 1).  Vectors are interleaved, NR values per
-// node, and a thread handles one column pair of one right-hand side; the
-// stencil and interpolation values are shared by the NR threads of a
-// column, so they are read once per sweep for all right-hand sides.
+// Several right-hand sides (NR = 4).  Vectors are interleaved, NR values per
+// node, and a thread handles one column pair for all right-hand sides, its
+// values as a float4: every stencil and interpolation value is read once
+// per sweep (from global memory and from shared memory) for all of them.
 // Batched form (BATCH).  All (problem, level) members of one size class
 // keep their arrays in class-contiguous storage with one more tensor
 // dimension (the member); a persistent grid walks the class's work-list of
@@ -75,14 +75,64 @@ __device__ __forceinline__ void tma4d(void* dst, const CUtensorMap* m, uint64_t*
         : "memory");
 }
 
-// One row of an interleaved vector (NR values per node) as seen by one
-// right-hand side: element c is p[c * NR].
+// The values of a node's NR right-hand sides: T itself for one, a float4
+// for four (FP32); vectors are interleaved in memory, so a row of them is
+// an array of these.
 template <typename T, int NR>
-struct VRow {
-    T* p;
-    __device__ __forceinline__ T& operator[](int c) const { return p[c * NR]; }
+struct VecOf {
+    using type = T;
+};
+template <>
+struct VecOf<float, 4> {
+    using type = float4;
 };
 
+__device__ __forceinline__ float4 operator+(float4 a, float4 b) {
+    return make_float4(a.x + b.x, a.y + b.y, a.z + b.z, a.w + b.w);
+}
+__device__ __forceinline__ float4 operator-(float4 a, float4 b) {
+    return make_float4(a.x - b.x, a.y - b.y, a.z - b.z, a.w - b.w);
+}
+__device__ __forceinline__ float4 operator-(float4 a) { return make_float4(-a.x, -a.y, -a.z, -a.w); }
+__device__ __forceinline__ float4 operator*(float s, float4 b) { return make_float4(s * b.x, s * b.y, s * b.z, s * b.w); }
+__device__ __forceinline__ float4& operator+=(float4& a, float4 b) {
+    a = a + b;
+    return a;
+}
+
+template <typename V>
+__device__ __forceinline__ V vzero() { return (V)0; }
+template <>
+__device__ __forceinline__ float4 vzero<float4>() { return make_float4(0.f, 0.f, 0.f, 0.f); }
+
+// conversions between the value types (precision casts for one right-hand side)
+template <typename D, typename S>
+__device__ __forceinline__ D vcast(S s) { return (D)s; }
+template <>
+__device__ __forceinline__ float4 vcast<float4, float4>(float4 s) { return s; }
+
+// a row of values: element c is p[c]
+template <typename V>
+struct RowV {
+    V* p;
+    __device__ __forceinline__ V& operator[](int c) const { return p[c]; }
+};
+
+// A row of the iterate and residual rings, which the threads write
+// themselves: the even columns first, then the odd ones (HALF of each), so
+// that the column pairs the threads of a warp own map to consecutive words
+// (no bank conflicts on the neighbour reads).
+template <typename V, int HALF>
+struct SRow {
+    V* p;
+    __device__ __forceinline__ V& operator[](int c) const { return p[(c & 1) * HALF + (c >> 1)]; }
+};
+
+// NR compensated FP32 accumulators (one per right-hand side); add(f, x)
+// accumulates f * x per right-hand side.
+struct Acc32f;
+template <int NR>
+struct AccN;
 
 // ------------------------------------------------------------------ layout
 __host__ __device__ constexpr int r128(int b) { return (b + 127) & ~127; }
@@ -91,6 +141,9 @@ template <typename T>
 __device__ __forceinline__ T divide(T s, T d) { return s / d; }
 template <>
 __device__ __forceinline__ float divide<float>(float s, float d) { return __fdividef(s, d); }
+__device__ __forceinline__ float4 divide(float4 s, float d) {
+    return make_float4(__fdividef(s.x, d), __fdividef(s.y, d), __fdividef(s.z, d), __fdividef(s.w, d));
+}
 
 // Shared-memory layout: RP ring slots of one row pair each (stencil planes,
 // right-hand side, and for the up kernel the pre-smoothed iterate and one
@@ -132,14 +185,15 @@ struct Lay {
 // the fine rows 2(q0+q)+1 and 2(q0+q)+2 and, for the up kernel, coarse row
 // q0+q+1 of the coarse iterate.
 // qb: pairs this CTA issued before the current item (the persistent batched
-// kernels carry the ring's slots and mbarrier phases from item to item);
-// rh: the thread's right-hand side.
+// kernels carry the ring's slots and mbarrier phases from item to item).
 template <typename T, typename TF, int K, bool UP, int NR = 1>
 struct Ring {
+    using V = typename VecOf<T, NR>::type;
+    using VF = typename VecOf<TF, NR>::type;
     static constexpr unsigned RPu = (unsigned)Lay<T, TF, K, UP, NR>::RP;
     unsigned char *pA, *pF, *pXp, *pC;
     uint64_t* bars;
-    int q0, WW, sA, sF, sXp, sC, rh;
+    int q0, WW, sA, sF, sXp, sC;
     unsigned qb;
     __device__ __forceinline__ int slot_of_row(int j) const {
         return (int)((qb + (unsigned)(((j - 1) >> 1) - q0)) % RPu);
@@ -147,14 +201,14 @@ struct Ring {
     __device__ __forceinline__ const T* A(int j) const {      // plane 0 of fine row j
         return (const T*)(pA + slot_of_row(j) * sA) + ((j - 1) & 1) * WW;
     }
-    __device__ __forceinline__ VRow<const TF, NR> F(int j) const {
-        return {(const TF*)(pF + slot_of_row(j) * sF) + ((j - 1) & 1) * WW * NR + rh};
+    __device__ __forceinline__ RowV<const VF> F(int j) const {
+        return {(const VF*)(pF + slot_of_row(j) * sF) + ((j - 1) & 1) * WW};
     }
-    __device__ __forceinline__ VRow<const T, NR> Xp(int j) const {
-        return {(const T*)(pXp + slot_of_row(j) * sXp) + ((j - 1) & 1) * WW * NR + rh};
+    __device__ __forceinline__ RowV<const V> Xp(int j) const {
+        return {(const V*)(pXp + slot_of_row(j) * sXp) + ((j - 1) & 1) * WW};
     }
-    __device__ __forceinline__ VRow<const T, NR> C(int J) const {      // coarse row J (carried by pair J-1)
-        return {(const T*)(pC + (int)((qb + (unsigned)(J - 1 - q0)) % RPu) * sC) + rh};
+    __device__ __forceinline__ RowV<const V> C(int J) const {      // coarse row J (carried by pair J-1)
+        return {(const V*)(pC + (int)((qb + (unsigned)(J - 1 - q0)) % RPu) * sC)};
     }
 };
 
@@ -178,18 +232,34 @@ struct Acc32f {
     __device__ __forceinline__ double value() const { return (double)s + (double)c; }
 };
 
+template <>
+struct AccN<1> {
+    Acc32f a[1];
+    __device__ __forceinline__ void add(float f, float x) { a[0].add(f * x); }
+};
+template <>
+struct AccN<4> {
+    Acc32f a[4];
+    __device__ __forceinline__ void add(float4 f, float4 x) {
+        a[0].add(f.x * x.x);
+        a[1].add(f.y * x.y);
+        a[2].add(f.z * x.z);
+        a[3].add(f.w * x.w);
+    }
+};
+
 // ------------------------------------------------------------------ node updates
 // Symmetric-half stencil rows: plane p of row j is A(j) + p * 2 * WW.
 // Offsets: W(c) couples (c-1), W(c+1) couples (c+1) of the row; S(j) couples
 // row j-1, S(j+1) row j+1; SW(j,c) couples (c-1, j-1), SW(j+1,c+1) (c+1, j+1);
 // NW(j,c) couples (c-1, j+1), NW(j-1,c+1) (c+1, j-1).
-template <typename T, int NR = 1>
+template <typename T, typename V, typename XA>
 struct Rows {
     const T *a, *an, *as;          // stencil rows j, j+1, j-1 (plane 0)
-    VRow<T, NR> x, xn, xs;         // iterate rows j, j+1, j-1
+    XA x, xn, xs;                  // iterate rows j, j+1, j-1
     int PL;                        // plane stride
-    __device__ __forceinline__ T offdiag(int c) const {
-        T s = a[W2 * PL + c] * x[c - 1];
+    __device__ __forceinline__ V offdiag(int c) const {
+        V s = a[W2 * PL + c] * x[c - 1];
         s += a[W2 * PL + c + 1] * x[c + 1];
         s += a[S2 * PL + c] * xs[c];
         s += an[S2 * PL + c] * xn[c];
@@ -200,8 +270,8 @@ struct Rows {
         return s;
     }
     // forward sweep, colour 2: the (c +- 1, j) neighbours are still zero
-    __device__ __forceinline__ T offdiag_no_row(int c) const {
-        T s = a[S2 * PL + c] * xs[c];
+    __device__ __forceinline__ V offdiag_no_row(int c) const {
+        V s = a[S2 * PL + c] * xs[c];
         s += an[S2 * PL + c] * xn[c];
         s += a[SW2 * PL + c] * xs[c - 1];
         s += an[SW2 * PL + c + 1] * xn[c + 1];
@@ -214,9 +284,10 @@ struct Rows {
 
 // ------------------------------------------------------------------ down kernel
 template <typename T, typename TF, int K, int WC, int NR = 1, bool BATCH = false>
-__global__ void __launch_bounds__((WC + 8) * K * NR, sizeof(T) == 4 ? 3 : 1)
+__global__ void __launch_bounds__((WC + 8) * K, sizeof(T) == 4 ? 3 : 1)
     k_vdown2d(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmF, FusedArgs p) {
     using LY = Lay<T, TF, K, false, NR>;
+    using V = typename VecOf<T, NR>::type;       // a node's values, all right-hand sides
     constexpr int RP = LY::RP;
     extern __shared__ unsigned char smem_raw[];
     const LY L(WC);   // strip width fixed at compile time: every shared-memory stride is a constant
@@ -227,17 +298,15 @@ __global__ void __launch_bounds__((WC + 8) * K * NR, sizeof(T) == 4 ? 3 : 1)
     rg.pF = base + RP * L.sA;
     rg.pXp = rg.pC = nullptr;
     constexpr int XR = LY::XR;
-    T* sX = (T*)(base + RP * L.slot());
-    T* sR = sX + XR * WW * NR;
-    rg.bars = (uint64_t*)(sR + XR * WW * NR);
+    V* sX = (V*)(base + RP * L.slot());
+    V* sR = sX + XR * WW;
+    rg.bars = (uint64_t*)(sR + XR * WW);
     rg.WW = WW;
     rg.sA = L.sA;
     rg.sF = L.sF;
     rg.sXp = rg.sC = 0;
-    const int rh = NR == 1 ? 0 : (int)threadIdx.x % NR;          // right-hand side of this thread
-    const int tx = NR == 1 ? (int)threadIdx.x : (int)threadIdx.x / NR, ty = threadIdx.y;
-    rg.rh = rh;
-    const bool lead = threadIdx.x == 0 && ty == 0;
+    const int tx = threadIdx.x, ty = threadIdx.y;
+    const bool lead = tx == 0 && ty == 0;
     const int nf = p.nf, nc = p.nc;
     const uint32_t txb = L.tx();
     if (lead) {
@@ -269,8 +338,10 @@ __global__ void __launch_bounds__((WC + 8) * K * NR, sizeof(T) == 4 ? 3 : 1)
         uint64_t* bar = rg.bars + s;
         mbar::expect_tx(bar, txb);
         if constexpr (BATCH) {
+            // vector maps group 8 nodes x NR values into their innermost
+            // dimension (x0 is a multiple of 8)
             tma4d(rg.pA + s * L.sA, &tmA, bar, x0, 2 * Jp + 1, 0, mi);
-            tma4d(rg.pF + s * L.sF, &tmF, bar, 0, x0, 2 * Jp + 1, mi);
+            tma4d(rg.pF + s * L.sF, &tmF, bar, 0, x0 / 8, 2 * Jp + 1, mi);
         } else {
             tma3d(rg.pA + s * L.sA, &tmA, bar, x0, 2 * Jp + 1, 0);
             tma2d(rg.pF + s * L.sF, &tmF, bar, x0, 2 * Jp + 1);
@@ -290,37 +361,39 @@ __global__ void __launch_bounds__((WC + 8) * K * NR, sizeof(T) == 4 ? 3 : 1)
     const int I = xc0 + tx;
     const bool vres = tx >= 5 && tx < 5 + WC && I >= 1 && I <= nc - 2;
     auto inrow = [&](int j) { return j >= 1 && j <= nf - 2; };
-    auto X = [&](int j) { return VRow<T, NR>{sX + (int)((unsigned)j % XR) * WW * NR + rh}; };
-    auto RR = [&](int j) { return VRow<T, NR>{sR + (int)((unsigned)j % XR) * WW * NR + rh}; };
+    using XA = SRow<V, WC + 8>;
+    auto X = [&](int j) { return XA{sX + (int)((unsigned)j % XR) * WW}; };
+    auto RR = [&](int j) { return XA{sR + (int)((unsigned)j % XR) * WW}; };
     auto rows = [&](int j) {
-        return Rows<T, NR>{rg.A(j), rg.A(j + 1), rg.A(j - 1), X(j), X(j + 1), X(j - 1), PL};
+        return Rows<T, V, XA>{rg.A(j), rg.A(j + 1), rg.A(j - 1), X(j), X(j + 1), X(j - 1), PL};
     };
     const BatchMember* M = BATCH ? p.mem + mi : nullptr;
     const T* Pg = BATCH ? (const T*)M->P : (const T*)p.P;
-    T* xg = BATCH ? (T*)M->x[0] : (T*)p.x;
-    T* bcg = BATCH ? (T*)M->bc : (T*)p.bc;
+    V* xg = (V*)(BATCH ? M->x[0] : p.x);
+    V* bcg = (V*)(BATCH ? M->bc : p.bc);
+    const V z0 = vzero<V>();
 
     // colour 0 / 1 of even row j, colour 2 / 3 of odd row j, residual of row j
     auto c0 = [&](int j) {
-        const Rows<T, NR> r = rows(j);
-        X(j)[ce] = (ve && inrow(j)) ? divide<T>((T)rg.F(j)[ce], r.diag(ce)) : (T)0;
+        const Rows<T, V, XA> r = rows(j);
+        X(j)[ce] = (ve && inrow(j)) ? divide(vcast<V>(rg.F(j)[ce]), r.diag(ce)) : z0;
     };
     auto c1 = [&](int j) {
-        const Rows<T, NR> r = rows(j);
-        T v = 0;
+        const Rows<T, V, XA> r = rows(j);
+        V v = z0;
         if (vo && inrow(j)) {
-            const T s = (T)rg.F(j)[co] - r.a[W2 * PL + co] * r.x[co - 1] - r.a[W2 * PL + co + 1] * r.x[co + 1];
-            v = divide<T>(s, r.diag(co));
+            const V s = vcast<V>(rg.F(j)[co]) - r.a[W2 * PL + co] * r.x[co - 1] - r.a[W2 * PL + co + 1] * r.x[co + 1];
+            v = divide(s, r.diag(co));
         }
         X(j)[co] = v;
     };
     auto c2 = [&](int j) {
-        const Rows<T, NR> r = rows(j);
-        X(j)[ce] = (ve && inrow(j)) ? divide<T>((T)rg.F(j)[ce] - r.offdiag_no_row(ce), r.diag(ce)) : (T)0;
+        const Rows<T, V, XA> r = rows(j);
+        X(j)[ce] = (ve && inrow(j)) ? divide(vcast<V>(rg.F(j)[ce]) - r.offdiag_no_row(ce), r.diag(ce)) : z0;
     };
     auto c3 = [&](int j) {
-        const Rows<T, NR> r = rows(j);
-        X(j)[co] = (vo && inrow(j)) ? divide<T>((T)rg.F(j)[co] - r.offdiag(co), r.diag(co)) : (T)0;
+        const Rows<T, V, XA> r = rows(j);
+        X(j)[co] = (vo && inrow(j)) ? divide(vcast<V>(rg.F(j)[co]) - r.offdiag(co), r.diag(co)) : z0;
     };
     // Residual after the forward sweep from a zero guess.  A point's own
     // update zeroed its residual given the values of that moment, and the
@@ -331,15 +404,15 @@ __global__ void __launch_bounds__((WC + 8) * K * NR, sizeof(T) == 4 ? 3 : 1)
     //   colour 2 (odd row, even column): the two colour-3 row neighbours;
     //   colour 3 (odd row, odd column): none.
     auto resid = [&](int j) {
-        const Rows<T, NR> r = rows(j);
-        const VRow<T, NR> Rj = RR(j);
+        const Rows<T, V, XA> r = rows(j);
+        const XA Rj = RR(j);
         const bool rj = inrow(j);
         if (!(j & 1)) {
-            Rj[ce] = (ve && rj) ? -r.offdiag(ce) : (T)0;
-            Rj[co] = (vo && rj) ? -r.offdiag_no_row(co) : (T)0;
+            Rj[ce] = (ve && rj) ? -r.offdiag(ce) : z0;
+            Rj[co] = (vo && rj) ? -r.offdiag_no_row(co) : z0;
         } else {
-            Rj[ce] = (ve && rj) ? -(r.a[W2 * PL + ce] * r.x[ce - 1] + r.a[W2 * PL + ce + 1] * r.x[ce + 1]) : (T)0;
-            Rj[co] = (T)0;
+            Rj[ce] = (ve && rj) ? -(r.a[W2 * PL + ce] * r.x[ce - 1] + r.a[W2 * PL + ce + 1] * r.x[ce + 1]) : z0;
+            Rj[co] = z0;
         }
     };
 
@@ -395,28 +468,28 @@ __global__ void __launch_bounds__((WC + 8) * K * NR, sizeof(T) == 4 ? 3 : 1)
         resid(jo);
         __syncthreads();
         if (do_res) {
-            const VRow<T, NR> Rm = RR(jm);
-            const VRow<T, NR> Rs = RR(jm - 1);
-            const VRow<T, NR> Rn = RR(jo);
+            const XA Rm = RR(jm);
+            const XA Rs = RR(jm - 1);
+            const XA Rn = RR(jo);
             const int c = ce;
-            T b = Rm[c];
+            V b = Rm[c];
             b += w[0] * Rm[c - 1];
             b += w[1] * Rm[c + 1];
             b += w[2] * Rs[c];
             b += w[3] * Rn[c];
-            bcg[((long long)Jp * p.ldc + I) * NR + rh] = b;
+            bcg[(long long)Jp * p.ldc + I] = b;
         }
         load_w(Jp + K);
         // finished rows 2Jp-1 and 2Jp of the owned columns
         if (inrow(jm - 1)) {
-            const VRow<T, NR> Xr = X(jm - 1);
-            if (own_e) xg[((long long)(jm - 1) * p.ldf + ie) * NR + rh] = Xr[ce];
-            if (own_o) xg[((long long)(jm - 1) * p.ldf + ie + 1) * NR + rh] = Xr[co];
+            const XA Xr = X(jm - 1);
+            if (own_e) xg[(long long)(jm - 1) * p.ldf + ie] = Xr[ce];
+            if (own_o) xg[(long long)(jm - 1) * p.ldf + ie + 1] = Xr[co];
         }
         if (inrow(jm)) {
-            const VRow<T, NR> Xr = X(jm);
-            if (own_e) xg[((long long)jm * p.ldf + ie) * NR + rh] = Xr[ce];
-            if (own_o) xg[((long long)jm * p.ldf + ie + 1) * NR + rh] = Xr[co];
+            const XA Xr = X(jm);
+            if (own_e) xg[(long long)jm * p.ldf + ie] = Xr[ce];
+            if (own_o) xg[(long long)jm * p.ldf + ie + 1] = Xr[co];
         }
         // no barrier here: the next step's writes (rows 2Jp+2K+1.. of the X and R
         // rings) do not alias rows read above, and slots are refilled only after
@@ -440,10 +513,13 @@ __global__ void __launch_bounds__((WC + 8) * K * NR, sizeof(T) == 4 ? 3 : 1)
 
 // ------------------------------------------------------------------ up kernel
 template <typename T, typename TF, typename TO, int K, int WC, int NR = 1, bool BATCH = false>
-__global__ void __launch_bounds__((WC + 8) * K * NR, sizeof(T) == 4 ? 3 : 1)
+__global__ void __launch_bounds__((WC + 8) * K, sizeof(T) == 4 ? 3 : 1)
     k_vup2d(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmF,
             const __grid_constant__ CUtensorMap tmX, const __grid_constant__ CUtensorMap tmC, FusedArgs p) {
     using LY = Lay<T, TF, K, true, NR>;
+    using V = typename VecOf<T, NR>::type;        // a node's values, all right-hand sides
+    using VO = typename VecOf<TO, NR>::type;
+    using VZ = typename VecOf<float, NR>::type;   // FP32 values of the fused dot products
     constexpr int RP = LY::RP;
     extern __shared__ unsigned char smem_raw[];
     const LY L(WC);   // strip width fixed at compile time: every shared-memory stride is a constant
@@ -455,20 +531,18 @@ __global__ void __launch_bounds__((WC + 8) * K * NR, sizeof(T) == 4 ? 3 : 1)
     rg.pXp = rg.pF + RP * L.sF;
     rg.pC = rg.pXp + RP * L.sXp;
     constexpr int XR = LY::XR;
-    T* sX = (T*)(base + RP * L.slot());
-    rg.bars = (uint64_t*)(sX + XR * WW * NR);
+    V* sX = (V*)(base + RP * L.slot());
+    rg.bars = (uint64_t*)(sX + XR * WW);
     rg.WW = WW;
     rg.sA = L.sA;
     rg.sF = L.sF;
     rg.sXp = L.sXp;
     rg.sC = L.sC;
-    const int rh = NR == 1 ? 0 : (int)threadIdx.x % NR;          // right-hand side of this thread
-    const int tx = NR == 1 ? (int)threadIdx.x : (int)threadIdx.x / NR, ty = threadIdx.y;
-    rg.rh = rh;
-    const bool lead = threadIdx.x == 0 && ty == 0;
+    const int tx = threadIdx.x, ty = threadIdx.y;
+    const bool lead = tx == 0 && ty == 0;
     const int nf = p.nf, nc = p.nc;
     const uint32_t txb = L.tx();
-    const int tid = ty * blockDim.x + threadIdx.x, nthr = blockDim.x * blockDim.y;
+    const int tid = ty * blockDim.x + tx, nthr = blockDim.x * blockDim.y;
     if (lead) {
         for (int s = 0; s < RP; s++) mbar::init(rg.bars + s, 1);
         mbar::fence_init();
@@ -500,10 +574,13 @@ __global__ void __launch_bounds__((WC + 8) * K * NR, sizeof(T) == 4 ? 3 : 1)
         uint64_t* bar = rg.bars + s;
         mbar::expect_tx(bar, txb);
         if constexpr (BATCH) {
+            // vector maps group 8 nodes x NR values (fine rows; x0 is a
+            // multiple of 8) or 4 nodes (the coarse row; xc0 a multiple of 4)
+            // into their innermost dimension
             tma4d(rg.pA + s * L.sA, &tmA, bar, x0, 2 * Jp + 1, 0, mi);
-            tma4d(rg.pF + s * L.sF, &tmF, bar, 0, x0, 2 * Jp + 1, mi);
-            tma4d(rg.pXp + s * L.sXp, &tmX, bar, 0, x0, 2 * Jp + 1, mi);
-            tma4d(rg.pC + s * L.sC, &tmC, bar, 0, xc0, Jp + 1, cmi);
+            tma4d(rg.pF + s * L.sF, &tmF, bar, 0, x0 / 8, 2 * Jp + 1, mi);
+            tma4d(rg.pXp + s * L.sXp, &tmX, bar, 0, x0 / 8, 2 * Jp + 1, mi);
+            tma4d(rg.pC + s * L.sC, &tmC, bar, 0, xc0 / 4, Jp + 1, cmi);
         } else {
             tma3d(rg.pA + s * L.sA, &tmA, bar, x0, 2 * Jp + 1, 0);
             tma2d(rg.pF + s * L.sF, &tmF, bar, x0, 2 * Jp + 1);
@@ -524,15 +601,17 @@ __global__ void __launch_bounds__((WC + 8) * K * NR, sizeof(T) == 4 ? 3 : 1)
     const int I = xc0 + tx;                      // coarse column of the thread's column pair
     const bool vI = I >= 0 && I <= nc - 1;
     auto inrow = [&](int j) { return j >= 1 && j <= nf - 2; };
-    auto X = [&](int j) { return VRow<T, NR>{sX + (int)((unsigned)j % XR) * WW * NR + rh}; };
+    using XA = SRow<V, WC + 8>;
+    auto X = [&](int j) { return XA{sX + (int)((unsigned)j % XR) * WW}; };
     auto rows = [&](int j) {
-        return Rows<T, NR>{rg.A(j), rg.A(j + 1), rg.A(j - 1), X(j), X(j + 1), X(j - 1), PL};
+        return Rows<T, V, XA>{rg.A(j), rg.A(j + 1), rg.A(j - 1), X(j), X(j + 1), X(j - 1), PL};
     };
     const T* Pg = BATCH ? (const T*)M->P : (const T*)p.P;
-    TO* out = BATCH ? (TO*)M->x[p.parity] : (TO*)p.x;
+    VO* out = (VO*)(BATCH ? M->x[p.parity] : p.x);
     // finest level of the refinement mode only
-    const float* zold = BATCH ? (const float*)M->zold[p.parity] : (const float*)p.zold;
-    Acc32f rz, rzo;
+    const VZ* zold = (const VZ*)(BATCH ? M->zold[p.parity] : p.zold);
+    AccN<NR> rz, rzo;
+    const V z0 = vzero<V>();
     auto pw = [&](int plane, int Jc) -> T {
         return (vI && Jc >= 0 && Jc <= nc - 1) ? Pg[plane * p.plc + (long long)Jc * p.ldc + I] : (T)0;
     };
@@ -542,26 +621,26 @@ __global__ void __launch_bounds__((WC + 8) * K * NR, sizeof(T) == 4 ? 3 : 1)
     // PSW, PSE, PNW, PNE of coarse row (j-1)/2)
     auto corr_even = [&](int j, T wxl, T wxr) {
         const bool rj = inrow(j);
-        const VRow<const T, NR> C0 = rg.C(j >> 1);
-        const VRow<const T, NR> xp = rg.Xp(j);
-        const VRow<T, NR> x = X(j);
-        x[ce] = (ve && rj) ? xp[ce] + C0[tx] : (T)0;
-        x[co] = (vo && rj) ? xp[co] + wxl * C0[tx] + wxr * C0[tx + 1] : (T)0;
+        const RowV<const V> C0 = rg.C(j >> 1);
+        const RowV<const V> xp = rg.Xp(j);
+        const XA x = X(j);
+        x[ce] = (ve && rj) ? xp[ce] + C0[tx] : z0;
+        x[co] = (vo && rj) ? xp[co] + wxl * C0[tx] + wxr * C0[tx + 1] : z0;
     };
     auto corr_odd = [&](int j, const T* wy) {
         const bool rj = inrow(j);
-        const VRow<const T, NR> C0 = rg.C(j >> 1);
-        const VRow<const T, NR> C1 = rg.C((j >> 1) + 1);
-        const VRow<const T, NR> xp = rg.Xp(j);
-        const VRow<T, NR> x = X(j);
-        x[ce] = (ve && rj) ? xp[ce] + wy[0] * C0[tx] + wy[1] * C1[tx] : (T)0;
+        const RowV<const V> C0 = rg.C(j >> 1);
+        const RowV<const V> C1 = rg.C((j >> 1) + 1);
+        const RowV<const V> xp = rg.Xp(j);
+        const XA x = X(j);
+        x[ce] = (ve && rj) ? xp[ce] + wy[0] * C0[tx] + wy[1] * C1[tx] : z0;
         x[co] = (vo && rj) ? xp[co] + wy[2] * C0[tx] + wy[3] * C0[tx + 1] + wy[4] * C1[tx] + wy[5] * C1[tx + 1]
-                           : (T)0;
+                           : z0;
     };
     auto gs = [&](int j, int c, bool v) {      // one Gauss-Seidel update
         if (!(v && inrow(j))) return;
-        const Rows<T, NR> r = rows(j);
-        X(j)[c] = divide<T>((T)rg.F(j)[c] - r.offdiag(c), r.diag(c));
+        const Rows<T, V, XA> r = rows(j);
+        X(j)[c] = divide(vcast<V>(rg.F(j)[c]) - r.offdiag(c), r.diag(c));
     };
 
     bool ok = wait_pairs<RP>(rg.bars, qb, qb + 2);
@@ -595,14 +674,15 @@ __global__ void __launch_bounds__((WC + 8) * K * NR, sizeof(T) == 4 ? 3 : 1)
     load_w(J0 + ty);
     // previous preconditioned residual at this thread's stored nodes of the
     // rows 2Jp-1, 2Jp, also loaded one step ahead (refinement mode only)
-    float zo_nx[2][2] = {{0.f, 0.f}, {0.f, 0.f}};
+    const VZ zz = vzero<VZ>();
+    VZ zo_nx[2][2] = {{zz, zz}, {zz, zz}};
     auto load_zo = [&](int Jp) {
         for (int rr = 0; rr < 2; rr++) {
             const int j = 2 * Jp - 1 + rr;
             const long long o = (long long)j * p.ldf + ie;
             const bool rj = inrow(j);
-            zo_nx[rr][0] = (rj && own_e) ? zold[o * NR + rh] : 0.f;
-            zo_nx[rr][1] = (rj && own_o) ? zold[(o + 1) * NR + rh] : 0.f;
+            zo_nx[rr][0] = (rj && own_e) ? zold[o] : zz;
+            zo_nx[rr][1] = (rj && own_o) ? zold[o + 1] : zz;
         }
     };
     if (zold) load_zo(J0 + ty);
@@ -621,7 +701,7 @@ __global__ void __launch_bounds__((WC + 8) * K * NR, sizeof(T) == 4 ? 3 : 1)
         corr_odd(jo, wy);
         corr_even(je, wxl, wxr);
         load_w(Jp + K);
-        float zo_now[2][2] = {{zo_nx[0][0], zo_nx[0][1]}, {zo_nx[1][0], zo_nx[1][1]}};
+        VZ zo_now[2][2] = {{zo_nx[0][0], zo_nx[0][1]}, {zo_nx[1][0], zo_nx[1][1]}};
         if (zold) load_zo(Jp + K);
         __syncthreads();
         gs(jo, co, vo);      // colour 3
@@ -633,29 +713,29 @@ __global__ void __launch_bounds__((WC + 8) * K * NR, sizeof(T) == 4 ? 3 : 1)
         gs(jm, ce, ve);      // colour 0
         // right-hand side of the stored rows, read while their ring slots
         // cannot yet be refilled (the next refill follows the next barrier)
-        float fr[2][2] = {{0.f, 0.f}, {0.f, 0.f}};
+        VZ fr[2][2] = {{zz, zz}, {zz, zz}};
         if (zold)
             for (int rr = 0; rr < 2; rr++) {
-                const VRow<const TF, NR> Fr = rg.F(jm - 1 + rr);
-                fr[rr][0] = (float)Fr[ce];
-                fr[rr][1] = (float)Fr[co];
+                const RowV<const typename Ring<T, TF, K, true, NR>::VF> Fr = rg.F(jm - 1 + rr);
+                fr[rr][0] = vcast<VZ>(Fr[ce]);
+                fr[rr][1] = vcast<VZ>(Fr[co]);
             }
         __syncthreads();
         for (int rr = 0; rr < 2; rr++) {
             const int j = jm - 1 + rr;
             if (!inrow(j)) continue;
-            const VRow<T, NR> Xr = X(j);
+            const XA Xr = X(j);
             const long long o = (long long)j * p.ldf + ie;
-            if (own_e) out[o * NR + rh] = (TO)Xr[ce];
-            if (own_o) out[(o + 1) * NR + rh] = (TO)Xr[co];
+            if (own_e) out[o] = vcast<VO>(Xr[ce]);
+            if (own_o) out[o + 1] = vcast<VO>(Xr[co]);
             if (zold) {
                 if (own_e) {
-                    rz.add(fr[rr][0] * (float)Xr[ce]);
-                    rzo.add(fr[rr][0] * zo_now[rr][0]);
+                    rz.add(fr[rr][0], vcast<VZ>(Xr[ce]));
+                    rzo.add(fr[rr][0], zo_now[rr][0]);
                 }
                 if (own_o) {
-                    rz.add(fr[rr][1] * (float)Xr[co]);
-                    rzo.add(fr[rr][1] * zo_now[rr][1]);
+                    rz.add(fr[rr][1], vcast<VZ>(Xr[co]));
+                    rzo.add(fr[rr][1], zo_now[rr][1]);
                 }
             }
         }
@@ -677,11 +757,10 @@ __global__ void __launch_bounds__((WC + 8) * K * NR, sizeof(T) == 4 ? 3 : 1)
         // last CTA (of the grid, or of the problem's tiles when batched)
         // forms the flexible-CG beta.  Every copy into the rings has
         // completed, so after the barrier the A ring is free to hold the
-        // per-thread sums.  Thread tid carries right-hand side tid % NR.
+        // per-thread sums.
         double* red = (double*)rg.pA;
         int* last = (int*)(red + 2 * nthr);
-        // sums of v1 / v2 over the threads of each right-hand side in a fixed
-        // order; valid in threads 0 .. NR-1 (thread rh holds right-hand side rh)
+        // sums of v1 / v2 over the CTA's threads in a fixed order; valid in thread 0
         auto block_sum2 = [&](double v1, double v2, double& s1, double& s2) {
             __syncthreads();
             red[tid] = v1;
@@ -693,7 +772,7 @@ __global__ void __launch_bounds__((WC + 8) * K * NR, sizeof(T) == 4 ? 3 : 1)
                     a1 += red[k];
                     a2 += red[nthr + k];
                 }
-                for (int o = 16; o >= NR; o >>= 1) {
+                for (int o = 16; o > 0; o >>= 1) {
                     a1 += __shfl_down_sync(0xffffffffu, a1, o);
                     a2 += __shfl_down_sync(0xffffffffu, a2, o);
                 }
@@ -701,14 +780,14 @@ __global__ void __launch_bounds__((WC + 8) * K * NR, sizeof(T) == 4 ? 3 : 1)
                 s2 = a2;
             }
         };
-        double b1 = 0.0, b2 = 0.0;
-        block_sum2(rz.value(), rzo.value(), b1, b2);
+        double b1[NR], b2[NR];
+        for (int r = 0; r < NR; r++) block_sum2(rz.a[r].value(), rzo.a[r].value(), b1[r], b2[r]);
         if constexpr (!BATCH) {
             const int nb = gridDim.x * gridDim.y;
             if (tid == 0) {
                 const int bid = blockIdx.y * gridDim.x + blockIdx.x;
-                p.partials[2 * bid] = b1;
-                p.partials[2 * bid + 1] = b2;
+                p.partials[2 * bid] = b1[0];
+                p.partials[2 * bid + 1] = b2[0];
                 __threadfence();
                 *last = atomicAdd(&p.st->counter[6], 1u) == (unsigned)nb - 1;
             }
@@ -737,40 +816,44 @@ __global__ void __launch_bounds__((WC + 8) * K * NR, sizeof(T) == 4 ? 3 : 1)
         } else {
             const int tpm = p.tiles_x * p.tiles_y;
             double* part = p.partials + (M->part + (by * p.tiles_x + bx)) * 2 * NR;
-            if (tid < NR) {
-                part[2 * tid] = b1;
-                part[2 * tid + 1] = b2;
+            if (tid == 0) {
+                for (int r = 0; r < NR; r++) {
+                    part[2 * r] = b1[r];
+                    part[2 * r + 1] = b2[r];
+                }
+                __threadfence();
+                *last = atomicAdd(&p.counters[M->prob], 1u) == (unsigned)tpm - 1;
             }
-            __threadfence();
-            __syncthreads();
-            if (tid == 0) *last = atomicAdd(&p.counters[M->prob], 1u) == (unsigned)tpm - 1;
             __syncthreads();
             if (*last) {
                 __threadfence();
-                // thread tid sums the tiles k = tid/ NR-strided... in a fixed order:
-                // tiles tid / NR, tid / NR + nthr / NR, ... of right-hand side tid % NR
+                // fixed-order sums over the problem's tiles, per right-hand side
                 const double* base_p = p.partials + M->part * 2 * NR;
-                double v1 = 0.0, v2 = 0.0;
-                for (int k = tid / NR; k < tpm; k += nthr / NR) {
-                    v1 += ((volatile const double*)base_p)[(long long)k * 2 * NR + 2 * rh];
-                    v2 += ((volatile const double*)base_p)[(long long)k * 2 * NR + 2 * rh + 1];
-                }
-                double t1 = 0.0, t2 = 0.0;
-                block_sum2(v1, v2, t1, t2);
-                if (tid < NR) {
-                    SysState& sy = p.sys[(long long)M->prob * NR + tid];
-                    const bool live = sy.active && sy.left > 0;
-                    if (live && sy.first) {
-                        sy.beta = 0.0;
-                        sy.first = 0;
-                    } else if (!live || !(sy.rz != 0.0)) {
-                        sy.beta = 0.0;
-                    } else {
-                        sy.beta = (t1 - t2) / sy.rz;
+                double v1[NR], v2[NR];
+                for (int r = 0; r < NR; r++) v1[r] = v2[r] = 0.0;
+                for (int k = tid; k < tpm; k += nthr)
+                    for (int r = 0; r < NR; r++) {
+                        v1[r] += ((volatile const double*)base_p)[(long long)k * 2 * NR + 2 * r];
+                        v2[r] += ((volatile const double*)base_p)[(long long)k * 2 * NR + 2 * r + 1];
                     }
-                    if (live) sy.rz = t1;
+                double t1[NR], t2[NR];
+                for (int r = 0; r < NR; r++) block_sum2(v1[r], v2[r], t1[r], t2[r]);
+                if (tid == 0) {
+                    for (int r = 0; r < NR; r++) {
+                        SysState& sy = p.sys[(long long)M->prob * NR + r];
+                        const bool live = sy.active && sy.left > 0;
+                        if (live && sy.first) {
+                            sy.beta = 0.0;
+                            sy.first = 0;
+                        } else if (!live || !(sy.rz != 0.0)) {
+                            sy.beta = 0.0;
+                        } else {
+                            sy.beta = (t1[r] - t2[r]) / sy.rz;
+                        }
+                        if (live) sy.rz = t1[r];
+                    }
+                    p.counters[M->prob] = 0u;
                 }
-                if (tid == 0) p.counters[M->prob] = 0u;
             }
         }
     }
@@ -878,7 +961,7 @@ bmg_status batch_occupancy(int wc, int* down_blocks, int* up_blocks) {
         auto kd = k_vdown2d<float, float, kBatchK, w, kBatchR, true>;
         auto ku = k_vup2d<float, float, float, kBatchK, w, kBatchR, true>;
         const int sd = batch_down_smem(wc), su = batch_up_smem(wc);
-        const int nt = (wc + 8) * kBatchK * kBatchR;
+        const int nt = (wc + 8) * kBatchK;
         if (cudaFuncSetAttribute(kd, cudaFuncAttributeMaxDynamicSharedMemorySize, sd) != cudaSuccess ||
             cudaFuncSetAttribute(ku, cudaFuncAttributeMaxDynamicSharedMemorySize, su) != cudaSuccess ||
             cudaOccupancyMaxActiveBlocksPerMultiprocessor(down_blocks, kd, nt, sd) != cudaSuccess ||
@@ -896,7 +979,7 @@ bmg_status batch_down(const CUtensorMap& mA, const CUtensorMap& mF, const FusedA
         const int smem = batch_down_smem(a.wc);
         if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) != cudaSuccess)
             return BMG_ERR_DEVICE;
-        kern<<<grid, dim3((a.wc + 8) * kBatchR, kBatchK), smem, s>>>(mA, mF, a);
+        kern<<<grid, dim3(a.wc + 8, kBatchK), smem, s>>>(mA, mF, a);
         return cudaGetLastError() == cudaSuccess ? BMG_OK : BMG_ERR_DEVICE;
     });
 }
@@ -908,7 +991,7 @@ bmg_status batch_up(const CUtensorMap& mA, const CUtensorMap& mF, const CUtensor
         const int smem = batch_up_smem(a.wc);
         if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) != cudaSuccess)
             return BMG_ERR_DEVICE;
-        kern<<<grid, dim3((a.wc + 8) * kBatchR, kBatchK), smem, s>>>(mA, mF, mXp, mXc, a);
+        kern<<<grid, dim3(a.wc + 8, kBatchK), smem, s>>>(mA, mF, mXp, mXc, a);
         return cudaGetLastError() == cudaSuccess ? BMG_OK : BMG_ERR_DEVICE;
     });
 }
