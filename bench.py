@@ -615,6 +615,7 @@ def run_batch(args, steps=None, warmup=None, emit=True):
     clk.start()
     times, infos = [], None
     l0 = B.launches
+    torch.cuda.nvtx.range_push("timed_batch")
     for _ in range(steps):
         zero()
         torch.cuda.synchronize()
@@ -625,6 +626,7 @@ def run_batch(args, steps=None, warmup=None, emit=True):
         b.record(stream)
         torch.cuda.synchronize()
         times.append(a.elapsed_time(b))
+    torch.cuda.nvtx.range_pop()
     ck = clk.stop()
     launches = (B.launches - l0) // steps
     worst = max(i.true_relres for row in infos for i in row)

@@ -77,10 +77,10 @@ __global__ void k_gs_colour3d_cb(const float* __restrict__ blk, long long nc, in
 #pragma unroll
     for (int e = 0; e < 13; e++) {
         const long long d = off_x(e) + sy * off_y(e) + sz * off_z(e);
-        s += blk[e * nc + t] * x[o + d];
-        s += blk[(26 - e) * nc + t] * x[o - d];
+        s += __ldcs(&blk[e * nc + t]) * x[o + d];
+        s += __ldcs(&blk[(26 - e) * nc + t]) * x[o - d];
     }
-    x[o] = (f[o] - s) / blk[13 * nc + t];
+    x[o] = (__ldcs(&f[o]) - s) / __ldcs(&blk[13 * nc + t]);
 }
 
 // Residual after the forward 8-colour sweep from a zero guess: a point's own
