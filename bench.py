@@ -49,6 +49,9 @@ def parse():
     ap.add_argument("--n", type=int, default=4097)
     ap.add_argument("--cpu-sample-n", type=int, default=1025)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-table", action="store_true",
+                    help="time the oracle (plain C, FP64 PCG to 1e-10) on the host cores for every configuration, "
+                         "single-threaded and on all cores of the affinity set; prints one JSON line, no GPU work")
     ap.add_argument("--variants", default="all", choices=["all", "fp64"],
                     help="fp64: time only the plain FP64 solve of the annulus workload (a short line for "
                          "profiling the FP64 kernels)")
@@ -215,6 +218,96 @@ def cpu_baseline(n_sample: int, n_full: int) -> dict:
                                         f"({q.unknowns} DoF, {it1} iterations, {dt1:.2f} s)"}}
 
 
+def cpu_table(args) -> dict:
+    """The oracle on the host cores for every configuration: the OpenMP build
+    on every core of the affinity set (bitwise the plain build's results)
+    and the plain single-threaded build, each solving to a verified 1e-10
+    with FP64 PCG. The solve times exclude assembly and hierarchy setup,
+    which are reported beside them, except for the adjoint workload, whose
+    metric counts each member's assembly, setup, forward solve, adjoint
+    solve and contraction, as the library's timing of it does. Where a
+    single-threaded run of the full workload would take many minutes, it is
+    timed on a named sample of the same recipe and says so."""
+    import oracle
+    from paper_2509_08109_gb300 import inputs
+    cores = len(os.sched_getaffinity(0))
+    oracle.threads(cores)
+    out = {"cpu": cpu_model(), "cores": cores, "unit": UNIT, "tol": TOL}
+
+    def solve(p, omp, reps=1, maxit=500):
+        t = time.perf_counter()
+        H = oracle.Hierarchy(oracle.assemble(p.coords, p.kappa), omp=omp)
+        setup = time.perf_counter() - t
+        times = []
+        for _ in range(reps):
+            t = time.perf_counter()
+            x, it, _, trr, st = H.pcg(p.rhs, tol=TOL, maxit=maxit)
+            times.append(time.perf_counter() - t)
+            assert st == 0 and trr <= TOL, (p.name, st, trr)
+        dt = statistics.median(times)
+        return {"value": p.unknowns / dt, "solve_s": dt, "iterations": it, "setup_s": setup, "dof": p.unknowns,
+                "workload": p.name}
+
+    p1 = inputs.annulus_plain(65)
+    out["annulus65_plain"] = {"all_cores": solve(p1, True, reps=5), "single_thread": solve(p1, False, reps=5)}
+    p2 = inputs.annulus_lognormal(4097)
+    out["annulus4097_lognormal"] = {"all_cores": solve(p2, True)}
+    del p2
+    s2 = solve(inputs.annulus_lognormal(1025), False)
+    s2["sample"] = "same recipe at n=1025"
+    out["annulus4097_lognormal"]["single_thread"] = s2
+    p3 = inputs.shell_two_layer(257)
+    out["shell257"] = {"all_cores": solve(p3, True, maxit=4000)}
+    del p3
+    s3 = solve(inputs.shell_two_layer(65), False, maxit=4000)
+    s3["sample"] = "same recipe at n=65 (iterations double per refinement on this map)"
+    out["shell257"]["single_thread"] = s3
+
+    probs = inputs.bump_batch(count=512, nrhs=4, limit=32)
+    for key, omp in (("all_cores", True), ("single_thread", False)):
+        dof = 0
+        solve_s = setup_s = 0.0
+        its = []
+        for p in probs:
+            t = time.perf_counter()
+            H = oracle.Hierarchy(oracle.assemble(p.coords, p.kappa), omp=omp)
+            setup_s += time.perf_counter() - t
+            for r in range(p.rhs.shape[0]):
+                t = time.perf_counter()
+                x, it, _, trr, st = H.pcg(p.rhs[r], tol=TOL, maxit=500)
+                solve_s += time.perf_counter() - t
+                assert st == 0 and trr <= TOL
+                its.append(it)
+                dof += p.unknowns
+            del H
+        out.setdefault("batch_first32x4", {})[key] = {
+            "value": dof / solve_s, "solve_s": solve_s, "setup_s": setup_s, "dof_rhs": dof,
+            "iterations_min_max": [min(its), max(its)],
+            "workload": "problems 0-31 of the 512-problem bump batch, 4 rhs each, solved one by one (no extrapolation)"}
+
+    members = inputs.annulus_adjoint(1025, batch=8)
+    for key, omp, mem in (("all_cores", True, members), ("single_thread", False, members[:1])):
+        its = []
+        t = time.perf_counter()
+        for p in mem:
+            H = oracle.Hierarchy(oracle.assemble(p.coords, p.kappa), omp=omp)
+            u, iu, _, tru, stu = H.pcg(p.rhs, tol=TOL, maxit=1000)
+            lam, il, _, trl, stl = H.pcg(u - p.extra["u_obs"], tol=TOL, maxit=1000)
+            assert stu == 0 and stl == 0 and tru <= TOL and trl <= TOL
+            g = p.kappa * oracle.adjoint_grad(p.coords, u, lam)
+            assert all(map(math.isfinite, g.ravel().tolist()))
+            its.append([iu, il])
+            del H
+        dt = time.perf_counter() - t
+        d = {"value": len(mem) * 1023 ** 2 / dt, "wall_s": dt, "members": len(mem), "iterations": its,
+             "workload": "1025^2 annulus adjoint: per member assembly, setup, forward solve, adjoint solve, "
+                         "gradient contraction"}
+        if len(mem) < len(members):
+            d["sample"] = f"member 0 of {len(members)}"
+        out.setdefault("adjoint1025x8", {})[key] = d
+    return out
+
+
 # ---------------------------------------------------------------- replicas
 def whole_job_throughput(local_ms: float, dof_per_rank: int, steps: int, world: int, reduce_max) -> tuple:
     """Weak-scaling replicas: every rank solves its own copy; the job's time
@@ -372,7 +465,7 @@ def run_own(args):
            "vs_baseline": None, "dtype": "f32 V-cycle / f64 residual", "data": "synthetic",
            "config": dict(config_for(n, not args.no_graphs),
                           tiles=("autotuned" if not args.no_autotune else "occupancy model") +
-                          f", finest level wc x hc = {sir.tiles()[0][0]} x {sir.tiles()[0][1]}"),
+                          ", finest level wc x hc (down, up) = {} x ({}, {})".format(*sir.tiles()[0])),
            "e2e": e2e, "gpu_launches": launches32,
            "headline_variant": head,
            "iterations": infos32[-1].iterations, "true_relres": infos32[-1].true_relres,
@@ -820,6 +913,8 @@ if __name__ == "__main__":
     a = parse()
     if a.impl == "reference":
         run_reference(a)
+    elif a.cpu_table:
+        print(json.dumps({"cpu_table": cpu_table(a)}), flush=True)
     elif a.workload == "annulus":
         run_own(a)
     elif a.workload == "annulus65":

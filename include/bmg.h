@@ -225,8 +225,11 @@ bmg_status bmg_solve_many(bmg_ctx* const* ctxs, int count, int nrhs, const doubl
    one launch, one CTA per problem.  One inner iteration of the whole batch
    is one CUDA graph (unless flags has BMG_FLAG_NO_GRAPHS).  Between two
    FP64 residuals every active system takes the number of inner iterations
-   the single-problem refinement would give it and then freezes until the
-   run of the slowest one ends; converged systems stop updating.
+   the single-problem refinement would give it, or fewer: it stops as soon
+   as its r.z (the recursive residual in the V-cycle's norm) has fallen by
+   the square of the reduction that run aims at.  It then freezes until the
+   run of the slowest one ends; converged systems stop updating, and a
+   problem whose systems are all frozen is skipped by the batch's kernels.
    Right-hand sides of a problem are
    interleaved in the batch's own storage (the caller's arrays keep their
    n x n layout). */
@@ -342,16 +345,19 @@ bmg_status bmg_profile(bmg_ctx* ctx, int enable);
 bmg_status bmg_profile_read(bmg_ctx* ctx, int kind, double* ms, long long* launches, double* bytes);
 
 /* Tile shape of the streaming 2-D V-cycle kernels on level `level` (the
-   kernels that go from level to level+1 and back): wc coarse columns and
-   hc coarse rows per CTA.  set: wc a multiple of 8 in [8, 64], hc a positive multiple
-   of the rows per step (2); BMG_ERR_ARG otherwise or when
-   the context does not use the streaming kernels. */
-bmg_status bmg_get_tiles(const bmg_ctx* ctx, int level, int* wc, int* hc);
-bmg_status bmg_set_tiles(bmg_ctx* ctx, int level, int wc, int hc);
+   kernels that go from level to level+1 and back): wc coarse columns per
+   CTA, common to both kernels, and the coarse rows per CTA of the down
+   kernel (hc) and of the up kernel (hc_up).  set: wc a multiple of 8 in
+   [8, 64], hc and hc_up positive multiples of the rows per step (2);
+   BMG_ERR_ARG otherwise or when the context does not use the streaming
+   kernels. */
+bmg_status bmg_get_tiles(const bmg_ctx* ctx, int level, int* wc, int* hc, int* hc_up);
+bmg_status bmg_set_tiles(bmg_ctx* ctx, int level, int wc, int hc, int hc_up);
 
 /* Autotuner: after bmg_setup, times candidate tile shapes of every level on
-   the device (the level's down and up kernels, best of reps runs) and keeps
-   the fastest; *ms (may be NULL) receives the sum of the chosen times.  The
+   the device (the level's down and up kernels, best of reps runs each) and
+   keeps the fastest width and, for that width, each kernel's fastest row
+   count; *ms (may be NULL) receives the sum of the chosen times.  The
    choice can be read back with bmg_get_tiles and cached by the caller. */
 bmg_status bmg_autotune(bmg_ctx* ctx, int reps, double* ms);
 

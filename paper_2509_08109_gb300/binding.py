@@ -90,8 +90,8 @@ def load() -> ctypes.CDLL:
         "bmg_get_stencil": ([P, I, P], I),
         "bmg_get_interp": ([P, I, P], I),
         "bmg_launch_count": ([P], ctypes.c_longlong),
-        "bmg_get_tiles": ([P, I, ctypes.POINTER(I), ctypes.POINTER(I)], I),
-        "bmg_set_tiles": ([P, I, I, I], I),
+        "bmg_get_tiles": ([P, I, ctypes.POINTER(I), ctypes.POINTER(I), ctypes.POINTER(I)], I),
+        "bmg_set_tiles": ([P, I, I, I, I], I),
         "bmg_autotune": ([P, I, ctypes.POINTER(D)], I),
         "bmg_profile": ([P, I], I),
         "bmg_profile_read": ([P, I, ctypes.POINTER(D), ctypes.POINTER(ctypes.c_longlong), ctypes.POINTER(D)], I),
@@ -479,18 +479,22 @@ class Solver:
 
     # ------------------------------------------------------------ tile shapes
     def tiles(self) -> list:
-        """[(wc, hc)] per level pair of the streaming kernels ([] if unused)."""
+        """[(wc, hc, hc_up)] per level pair of the streaming kernels ([] if
+        unused): strip width, rows per CTA of the down and the up kernel."""
         out = []
         for l in range(self.levels - 1):
-            wc, hc = ctypes.c_int(), ctypes.c_int()
-            if load().bmg_get_tiles(self._h, l, ctypes.byref(wc), ctypes.byref(hc)) != 0:
+            wc, hc, hu = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+            if load().bmg_get_tiles(self._h, l, ctypes.byref(wc), ctypes.byref(hc), ctypes.byref(hu)) != 0:
                 return []
-            out.append((wc.value, hc.value))
+            out.append((wc.value, hc.value, hu.value))
         return out
 
     def set_tiles(self, tiles):
-        for l, (wc, hc) in enumerate(tiles):
-            _check(load().bmg_set_tiles(self._h, l, int(wc), int(hc)), "bmg_set_tiles")
+        """tiles: per level (wc, hc) or (wc, hc, hc_up); hc_up defaults to hc."""
+        for l, t in enumerate(tiles):
+            wc, hc = t[0], t[1]
+            hu = t[2] if len(t) > 2 else hc
+            _check(load().bmg_set_tiles(self._h, l, int(wc), int(hc), int(hu)), "bmg_set_tiles")
 
     def autotune(self, reps: int = 3, cache: str | None = None) -> list:
         """Device-timed choice of the tile shapes (bmg_autotune).  With a

@@ -711,21 +711,22 @@ bmg_status bmg_profile_read(bmg_ctx* ctx, int kind, double* ms, long long* launc
     return BMG_OK;
 }
 
-bmg_status bmg_get_tiles(const bmg_ctx* ctx, int level, int* wc, int* hc) {
-    if (!ctx || !wc || !hc) return BMG_ERR_ARG;
+bmg_status bmg_get_tiles(const bmg_ctx* ctx, int level, int* wc, int* hc, int* hc_up) {
+    if (!ctx || !wc || !hc || !hc_up) return BMG_ERR_ARG;
     const Ctx& c = ctx->c;
     if (!c.use_fused || level < 0 || level >= c.nlev - 1) return BMG_ERR_ARG;
     *wc = c.fused[level].wc;
     *hc = c.fused[level].hc;
+    *hc_up = c.fused[level].hc_up;
     return BMG_OK;
 }
 
-bmg_status bmg_set_tiles(bmg_ctx* ctx, int level, int wc, int hc) {
+bmg_status bmg_set_tiles(bmg_ctx* ctx, int level, int wc, int hc, int hc_up) {
     BMG_TRY(check_ready(ctx));
     Ctx& c = ctx->c;
     if (!c.use_fused || level < 0 || level >= c.nlev - 1) return BMG_ERR_ARG;
     BMG_CUDA(cudaStreamSynchronize(c.stream));
-    return fused_configure(c, level, wc, hc);
+    return fused_configure(c, level, wc, hc, hc_up);
 }
 
 bmg_status bmg_autotune(bmg_ctx* ctx, int reps, double* ms) {

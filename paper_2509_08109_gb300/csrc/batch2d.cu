@@ -25,8 +25,9 @@
 // system's FP64 residual, retires the converged ones, and gives every
 // active system its own number of inner iterations for the next run (the
 // single-problem rule); the run lasts as long as the largest, and a system
-// whose count is used up freezes (no further updates) until the next
-// refinement.
+// whose count is used up, or whose r.z has fallen by the run's goal, freezes
+// (no further updates) until the next refinement.  A problem whose systems
+// are all frozen is skipped by every batched kernel of the iteration.
 //
 // Reductions are deterministic: per-tile partial sums, summed in a fixed
 // order by the last CTA of each problem (arrival counter per problem).
@@ -408,6 +409,10 @@ __global__ void __launch_bounds__(kBThreads, 3) k_bpspmv(const BProbDev* __restr
             sNW[sl][TW] = v.hnw;
         }
     };
+    AccB acc[R];
+    // a problem none of whose systems takes this iteration contributes zero
+    // partials (its systems get alpha = 0 below)
+    if (!batch_frozen(sys, it.prob)) {
     Row nx;
     load(j0 - 1, nx);
     put(j0 - 1, nx);
@@ -415,7 +420,6 @@ __global__ void __launch_bounds__(kBThreads, 3) k_bpspmv(const BProbDev* __restr
     put(j0, nx);
     float rs_j = nx.r, s_j = nx.s;
     load(j0 + 1, nx);
-    AccB acc[R];
     for (int j = j0; j < j1; j++) {
         put(j + 1, nx);
         const float s_n = nx.s, rs_n = nx.r;
@@ -444,6 +448,7 @@ __global__ void __launch_bounds__(kBThreads, 3) k_bpspmv(const BProbDev* __restr
         }
         rs_j = rs_n;
         s_j = s_n;
+    }
     }
     // per right-hand side: warp shuffle trees, then the warps' sums in order
     // (a fixed order: deterministic), then the tile partial
@@ -486,7 +491,10 @@ __global__ void __launch_bounds__(kBThreads, 3) k_bpspmv(const BProbDev* __restr
         } else {
             sw.alpha = sw.rz / s;
         }
-        if (live) sw.left--;
+        if (live) {
+            sw.left--;
+            sw.taken++;
+        }
     }
     if (t == 0) counters[it.prob] = 0u;
 }
@@ -1031,6 +1039,7 @@ bmg_status batch_attach(Batch& B, void* ws, size_t bytes, void* stream) {
             const int m = B.mem_of[p * kMaxLevels + t];
             BMG_TRY(tail_args(c, T.b + (long long)m * R * T.plane, T.xf + (long long)m * R * T.plane, T.ld, B.st,
                               &ta[p]));
+            ta[p].sys = B.sys + (long long)p * R;
             if (p == 0) B.tail_smem = batch_tail_smem(ta[0].ns, ta[0].nlev);
         }
         BMG_CUDA(cudaMemcpyAsync(B.targs, ta.data(), sizeof(TailArgs) * B.count, cudaMemcpyHostToDevice, B.stream));
@@ -1076,6 +1085,15 @@ bmg_status batch_autotune(Batch& B, int reps, double* ms_total) {
     BMG_CUDA(cudaEventCreate(&e1));
     int sms = 0;
     BMG_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, B.device));
+    // every system live, so that the kernels skip no problem while timed
+    // (batch_solve sets the states afresh)
+    const int S = B.count * R;
+    for (int s = 0; s < S; s++) {
+        B.sys_h[s] = SysState{};
+        B.sys_h[s].active = 1;
+        B.sys_h[s].left = 1 << 30;
+    }
+    BMG_CUDA(cudaMemcpyAsync(B.sys, B.sys_h, sizeof(SysState) * S, cudaMemcpyHostToDevice, B.stream));
     double total = 0.0;
     for (size_t ci = 0; ci < B.cls.size(); ci++) {
         BClass& K = B.cls[ci];
@@ -1224,6 +1242,7 @@ bmg_status batch_solve(Batch& B, int nrhs, const double* const* b, double* const
     bmg_status first_err = BMG_OK;
     int global_it = 0;
     std::vector<int> m_of(S, 0);
+    std::vector<double> want_of(S, 1.0);
     while (true) {
         int m_need = 0;
         for (int s = 0; s < S; s++) {
@@ -1246,12 +1265,21 @@ bmg_status batch_solve(Batch& B, int nrhs, const double* const* b, double* const
             if (m > kMaxInner) m = kMaxInner;
             if (m > maxit - it[s]) m = maxit - it[s];
             m_of[s] = m;
+            want_of[s] = want;
             m_need = std::max(m_need, m);
         }
         if (m_need == 0) break;
         for (int s = 0; s < S; s++) {
             B.sys_h[s].active = act[s];
             B.sys_h[s].left = act[s] ? m_of[s] : 0;
+            // the run also ends for a system once its r.z has fallen by the
+            // square of the reduction it aims at (the recursive residual in
+            // the preconditioner's norm): a fast system stops there instead
+            // of iterating past what its FP32 inner solve can deliver
+            // (not after a run in which it took no iteration: then it takes
+            // its full count, which maxit bounds)
+            B.sys_h[s].stop = act[s] && !(refs[s] > 0 && lastm[s] == 0) ? want_of[s] * want_of[s] : 0.0;
+            B.sys_h[s].taken = 0;
         }
         BMG_CUDA(cudaMemcpyAsync(B.sys, B.sys_h, sizeof(SysState) * S, cudaMemcpyHostToDevice, B.stream));
         for (int k = 0; k < m_need; k++) BMG_TRY(run_iteration(B, (global_it + k) & 1));
@@ -1264,12 +1292,12 @@ bmg_status batch_solve(Batch& B, int nrhs, const double* const* b, double* const
         }
         for (int s = 0; s < S; s++) {
             if (!act[s]) continue;
-            const int m = m_of[s];
+            const int m = B.sys_h[s].taken;
             it[s] += m;
             refs[s]++;
             const double nr = B.sys_h[s].rr;
             const double red = sqrt(nr / rr[s]);
-            if (red > 0 && red < 1) {
+            if (m > 0 && red > 0 && red < 1) {
                 const double r1 = pow(red, 1.0 / m);
                 if (r1 > 0.02 && r1 < 0.999) rho[s] = r1;
             }

@@ -67,16 +67,29 @@ struct SysState {
     double rz;        // r.z of the previous inner iteration
     double pq;        // p.Ap
     double alpha, beta;
+    double rz0;       // r.z of the first inner iteration of the current run
+    double stop;      // the run ends for this system once r.z <= stop * rz0 (0: it takes its full count)
     int first;        // 1: the next inner iteration takes p = z
     int active;       // 0: converged, zero right-hand side or out of iterations: no updates
     int left;         // inner iterations this system still takes in the current run (its own
                       // count, as the single-problem refinement sizes it); at 0 it freezes
+    int taken;        // inner iterations it took in the current run
 };
 
 // Right-hand sides per problem and row pairs per step of the batched
 // streaming kernels (FP32 V-cycle).
 constexpr int kBatchR = 4;
 constexpr int kBatchK = 2;
+
+// True when no system of problem p takes the current inner iteration: the
+// batched kernels then skip the problem's work (its results would not be
+// used: every one of its systems has alpha = 0 for the iteration).
+__device__ __forceinline__ bool batch_frozen(const SysState* sys, int p) {
+    const SysState* s = sys + (long long)p * kBatchR;
+    for (int r = 0; r < kBatchR; r++)
+        if (s[r].active && s[r].left > 0) return false;
+    return true;
+}
 
 struct Level {
     int n = 0;            // nodes per side
@@ -358,6 +371,7 @@ struct TailArgs {
     int ld0;                      // row length of b0 and x0 (in nodes)
     const double* a64c;           // FP64 centre entry of the coarsest operator
     KState* st;
+    const SysState* sys = nullptr;   // batched: the problem's systems (skips a frozen problem)
 };
 int tail_first_level(const Ctx& c);
 bmg_status tail_args(const Ctx& c, const void* b0, void* x0, int ld0, KState* st, TailArgs* a);
@@ -373,7 +387,7 @@ bool vcycle_forms_beta(const Ctx& c);
 template <typename T>
 bmg_status vcycle3d_impl(Ctx& c, const T* b0, T* x0, T* xout);
 bmg_status fused_prepare(Ctx& c);
-bmg_status fused_configure(Ctx& c, int l, int wc, int hc);
+bmg_status fused_configure(Ctx& c, int l, int wc, int hc, int hc_up);
 bmg_status fused_autotune(Ctx& c, int reps, double* best_ms_total);
 bmg_status demote_levels(Ctx& c);
 // krylov.cu

@@ -20,7 +20,7 @@
 // dependencies.  A step handles K row pairs at once: thread (x, y) owns
 // the column pair (2x, 2x+1) of row pair y, so every colour phase keeps all
 // threads busy and a step costs six block barriers for 2K fine rows (K = 2).  Rows
-// arrive by TMA (cp.async.bulk.tensor) into a ring of RP = K+2+D row-pair
+// arrive by TMA (cp.async.bulk.tensor) into a ring of RP = K+1+D row-pair
 // slots, each completed by an mbarrier with an expected byte count; the
 // next D = K pairs are in flight while a step computes; one thread issues all
 // copies.  Interpolation weights go straight from global memory into
@@ -151,12 +151,16 @@ __device__ __forceinline__ float4 divide(float4 s, float d) {
 // and (down) an equal ring of the residual R, then the mbarriers.
 template <typename T, typename TF, int K, bool UP, int NR = 1>
 struct Lay {
-    // ring slots: the K pairs of the current step, the two pairs below it
-    // (halo rows), and D = K pairs in flight (one step ahead; two steps ahead
+    // ring slots: the K pairs of the current step, the pair below it (halo
+    // rows), and D = K pairs in flight (one step ahead; two steps ahead
     // measured no faster on the 4097^2 refinement solve, with the wider ring
-    // costing strip width or occupancy)
+    // costing strip width or occupancy).  The one-right-hand-side up kernel
+    // keeps one more slot, which it fills one pair further ahead: measured
+    // on the 4097^2 refinement solve it runs faster that way at 4 CTAs per
+    // SM (3.46 ms per solve) than with the smaller ring at 5 (3.52 ms), while
+    // the down kernel gains from the fifth CTA (2.36 ms against 2.51 ms).
     static constexpr int D = K;
-    static constexpr int RP = K + 2 + D;
+    static constexpr int RP = K + 1 + D + (UP && NR == 1 ? 1 : 0);
     // rows of the X / R rings: a step reads and writes fine rows 2J-1 .. 2J+2K
     // (2K+2 rows); consecutive steps are separated by a block barrier
     // (rounded up to a power of two in the down kernel, whose rings have the
@@ -324,6 +328,9 @@ __global__ void __launch_bounds__((WC + 8) * K, sizeof(T) == 4 ? 3 : 1)
         const int t = item - mi * tpm;
         by = t / p.tiles_x;
         bx = t - by * p.tiles_x;
+        // a problem none of whose systems takes this iteration: no copies,
+        // no stores, no arrival (the same decision in every CTA)
+        if (p.sys && batch_frozen(p.sys, p.mem[mi].prob)) continue;
     } else {
         bx = blockIdx.x;
         by = blockIdx.y;
@@ -449,8 +456,9 @@ __global__ void __launch_bounds__((WC + 8) * K, sizeof(T) == 4 ? 3 : 1)
         if (!ok) break;
         waited = qa + K;
         // every thread is past the previous step: refill the freed slots
-        // (pairs up to qa - 3 are done) with the pairs D ahead
-        const int lim = min(npairs, qa - 2 + RP);
+        // (a step reads pairs qa - 1 .. qa + K - 1, so pairs up to qa - 2 are
+        // done) with the pairs D ahead
+        const int lim = min(npairs, qa - 1 + RP);
         if (lead)
             for (int q = issued; q < lim; q++) issue(q);
         issued = max(issued, lim);
@@ -558,6 +566,9 @@ __global__ void __launch_bounds__((WC + 8) * K, sizeof(T) == 4 ? 3 : 1)
         const int t = item - mi * tpm;
         by = t / p.tiles_x;
         bx = t - by * p.tiles_x;
+        // a problem none of whose systems takes this iteration: no copies,
+        // no stores, no arrival (the same decision in every CTA)
+        if (p.sys && batch_frozen(p.sys, p.mem[mi].prob)) continue;
     } else {
         bx = blockIdx.x;
         by = blockIdx.y;
@@ -693,8 +704,9 @@ __global__ void __launch_bounds__((WC + 8) * K, sizeof(T) == 4 ? 3 : 1)
         if (!ok) break;
         waited = qa + K;
         // every thread is past the previous step: refill the freed slots
-        // (pairs up to qa - 3 are done) with the pairs D ahead
-        const int lim = min(npairs, qa - 2 + RP);
+        // (a step reads pairs qa - 1 .. qa + K - 1, so pairs up to qa - 2 are
+        // done) with the pairs D ahead
+        const int lim = min(npairs, qa - 1 + RP);
         if (lead)
             for (int q = issued; q < lim; q++) issue(q);
         issued = max(issued, lim);
@@ -845,12 +857,19 @@ __global__ void __launch_bounds__((WC + 8) * K, sizeof(T) == 4 ? 3 : 1)
                         if (live && sy.first) {
                             sy.beta = 0.0;
                             sy.first = 0;
+                            sy.rz0 = t1[r];
                         } else if (!live || !(sy.rz != 0.0)) {
                             sy.beta = 0.0;
                         } else {
                             sy.beta = (t1[r] - t2[r]) / sy.rz;
                         }
-                        if (live) sy.rz = t1[r];
+                        if (live) {
+                            sy.rz = t1[r];
+                            // the run's goal reached (r.z fell by the factor
+                            // the host set): the system stops before this
+                            // iteration's update and waits for the refinement
+                            if (sy.stop > 0.0 && !(t1[r] > sy.stop * sy.rz0)) sy.left = 0;
+                        }
                     }
                     p.counters[M->prob] = 0u;
                 }
@@ -916,7 +935,7 @@ bmg_status launch_up(Ctx& c, const FusedLevel& F, cudaStream_t s, void* out, con
         a.x = out;
         a.zold = zold;
         a.partials = zold ? c.partials : nullptr;
-        kern<<<dim3(F.tiles_x, F.tiles_y), dim3(F.wc + 8, k_of<T>()), smem, s>>>(F.mA, F.mF, F.mXp, F.mXc, a);
+        kern<<<dim3(F.tiles_x, F.tiles_y_up), dim3(F.wc + 8, k_of<T>()), smem, s>>>(F.mA, F.mF, F.mXp, F.mXc, a);
         c.launches++;
         return cudaGetLastError() == cudaSuccess ? BMG_OK : BMG_ERR_DEVICE;
     });

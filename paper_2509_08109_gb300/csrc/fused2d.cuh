@@ -50,7 +50,9 @@ struct FusedArgs {
 // Per fine level: tile shape and TMA descriptors (built at attach time).
 struct FusedLevel {
     bool ready = false;
-    int wc = 0, hc = 0, tiles_x = 0, tiles_y = 0;
+    // one strip width for both kernels (the TMA boxes depend on it); rows per
+    // CTA for each kernel (hc: down, hc_up: up)
+    int wc = 0, hc = 0, tiles_x = 0, tiles_y = 0, hc_up = 0, tiles_y_up = 0;
     CUtensorMap mA;    // stencil planes, 3-D box (2*wc+16) x 2 rows x planes
     CUtensorMap mF;    // right-hand side rows
     CUtensorMap mXp;   // pre-smoothed iterate rows

@@ -77,6 +77,7 @@ __global__ void k_tail_pack(const T* __restrict__ src, int planes, int m, int ld
 template <typename T, int NR = 1, bool BATCH = false>
 __global__ void __launch_bounds__(kTailThreads) k_vtail2d(TailArgs a0, const TailArgs* __restrict__ targs) {
     const TailArgs& a = BATCH ? targs[blockIdx.x] : a0;
+    if (BATCH && a.sys && batch_frozen(a.sys, 0)) return;
     extern __shared__ unsigned char smem_raw[];
     __shared__ uint64_t bar;
     // per level: nodes per side and element offsets (from base) of A, P and

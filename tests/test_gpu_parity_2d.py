@@ -284,5 +284,11 @@ def test_autotune_keeps_results_bitwise(tmp_path):
             assert relerr(x1.cpu().numpy(), x0.cpu().numpy()) <= 1e-8
         s2 = solver_for(p, precision=prec, outer=outer)
         assert s2.autotune(cache=cache) == after
+        # the up kernel's rows per CTA are independent of the down kernel's
+        s2.set_tiles([(wc, hc, max(2, hu // 4 * 2)) for wc, hc, hu in after])
+        assert [t[2] for t in s2.tiles()] == [max(2, hu // 4 * 2) for _, _, hu in after]
+        assert torch.equal(s2.vcycle(r), z0)
     with pytest.raises(binding.BmgError):
         s.set_tiles([(20, 4)])     # strip widths are multiples of 8
+    with pytest.raises(binding.BmgError):
+        s.set_tiles([(16, 4, 3)])  # rows per CTA are multiples of the rows per step
