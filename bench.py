@@ -614,12 +614,14 @@ def _timed_solves(torch, s, f, steps, warmup, tol=TOL, maxit=500, clocks=None):
     infos = []
     if clocks:
         clocks.start()
+    torch.cuda.nvtx.range_push(f"timed_{s.precision}_{s.outer}")
     a.record(s.stream)
     for _ in range(steps):
         _, info = s.solve(f, tol=tol, out=x, maxit=maxit)
         infos.append(info)
     b.record(s.stream)
     torch.cuda.synchronize()
+    torch.cuda.nvtx.range_pop()
     if clocks:
         clocks.result = clocks.stop()
     return a.elapsed_time(b) / steps, s.launches - l0, infos
