@@ -55,6 +55,8 @@ def parse():
     ap.add_argument("--variants", default="all", choices=["all", "fp64"],
                     help="fp64: time only the plain FP64 solve of the annulus workload (a short line for "
                          "profiling the FP64 kernels)")
+    ap.add_argument("--shell-n", type=int, default=257,
+                    help="nodes per side of the shell workload (smaller values for profiling captures)")
     ap.add_argument("--batch-count", type=int, default=512,
                     help="problems of the batch workload (512 is the configuration; fewer: the first problems of "
                          "the same stream, for profiling captures on a small device footprint)")
@@ -924,7 +926,7 @@ if __name__ == "__main__":
         run_single(a, 2, 65, _inp.annulus_plain(65), "quarter_annulus_plain_n65")
     elif a.workload == "shell":
         from paper_2509_08109_gb300 import inputs as _inp
-        run_single(a, 3, 257, _inp.shell_two_layer(257), "shell_octant_two_layer_n257")
+        run_single(a, 3, a.shell_n, _inp.shell_two_layer(a.shell_n), f"shell_octant_two_layer_n{a.shell_n}")
     elif a.workload == "batch":
         run_batch(a)
     elif a.workload == "aux":

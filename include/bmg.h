@@ -76,7 +76,9 @@ enum {
 enum {
     BMG_FLAG_UNFUSED = 1,          /* V-cycle from separate per-colour, residual,
                                       restriction and prolongation kernels instead
-                                      of the streaming fused kernels (2-D) */
+                                      of the streaming fused kernels (2-D) or the
+                                      half-sweep smoother kernels, one launch per
+                                      colour parity of k (3-D) */
     BMG_FLAG_NO_GRAPHS = 2         /* launch every kernel of an iteration directly
                                       instead of replaying a CUDA graph of the
                                       iteration (graphs are also bypassed while

@@ -53,7 +53,8 @@ size_t carve(Ctx& c, char* base) {
             L.P64 = nullptr;
             L.P32 = nullptr;
         }
-        L.cb = (f32 && c.dim == 3 && l < c.nlev - 1)
+        // colour-blocked rows serve only the per-colour 3-D smoother
+        L.cb = (f32 && c.dim == 3 && l < c.nlev - 1 && (c.opts.flags & BMG_FLAG_UNFUSED))
                    ? (float*)take(sizeof(float) * 27 * ipow(L.n - 2, 3))
                    : nullptr;
         L.b = (l > 0 || f32) ? take(vt * L.plane) : nullptr;
@@ -427,6 +428,9 @@ bmg_status bmg_attach(bmg_ctx* ctx, void* ws, size_t bytes, void* stream) {
     BMG_CUDA(cudaMemsetAsync(c.ws, 0, c.ws_need, c.stream));
     BMG_CUDA(cudaStreamSynchronize(c.stream));
     c.use_fused = c.dim == 2 && !(c.opts.flags & BMG_FLAG_UNFUSED) && c.nlev >= 2;
+    // FP64 3-D V-cycles are bound by FP64 arithmetic: the half sweeps'
+    // recomputed halo would cost more than their saved traffic
+    c.use_hs3 = c.dim == 3 && c.opts.precision == BMG_PREC_FP32 && !(c.opts.flags & BMG_FLAG_UNFUSED);
     c.use_graphs = !(c.opts.flags & BMG_FLAG_NO_GRAPHS);
     if (c.use_fused) BMG_TRY(fused_prepare(c));
     c.attached = true;

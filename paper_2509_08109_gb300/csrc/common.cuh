@@ -143,6 +143,7 @@ struct Ctx {
     bool prof_on = false;
     ProfSlot prof[BMG_PROF_KINDS];
     bool use_fused = false;       // streaming V-cycle kernels (2-D)
+    bool use_hs3 = false;         // 3-D: half-sweep kernels (one launch per colour parity of k)
     void* tail_pack = nullptr;    // 2-D: operators and weights of the tail levels, packed (tail2d.cu)
     // CUDA graphs of one inner/outer iteration (two, for the alternating z buffers)
     cudaStream_t cap_stream = nullptr;

@@ -284,6 +284,260 @@ __global__ void __launch_bounds__(kTail3Threads) k_vtail3d(Tail3Args<T> a) {
 
 
 
+// ---------------------------------------------------------------- half sweeps
+// The 8-colour order visits all colours of the even k-planes (0..3) before
+// those of the odd planes (4..7), and the only couplings between planes are
+// the 18 z-couplings of a point, which all join planes of opposite parity.
+// So each half of a sweep is, plane by plane, an independent 4-colour sweep
+// of the plane with the couplings to its two neighbouring planes (whose
+// values do not change during that half) taken as they stand:
+//   forward (pre-smoothing, zero guess): the even planes first, whose odd
+//     neighbours are still zero (in-plane couplings only), then the odd
+//     planes against the finished even planes;
+//   reverse (post-smoothing): the odd planes against the corrected even
+//     planes, then the even planes against the finished odd planes.
+// k_hsweep3d runs one such half for every plane of one parity at once: a
+// CTA per (tile, plane) holds the plane's iterate over its tile and a halo
+// in shared memory, with the two neighbouring planes' iterates beside it.
+// Within a plane, colour (i&1) + 2(j&1) of the last phase depends on the
+// first through a chain of at most three column steps and one row step, so
+// a tile of kHsTI x TJ owned points computes (kHsTI + 6) x (TJ + 2) points
+// and neighbouring tiles recompute each other's halo.  Each point's update
+// is the per-colour kernels' update: the same 26 products summed in the
+// same order (offset t, then its mirror), the same division.
+//
+// Threads.  Lane p of a warp owns the column pair (ib + 2p, ib + 2p + 1) of
+// a row; the two points of a pair have consecutive colours, so a thread
+// loads both points' stencils with 2-wide vector loads when it updates the
+// first and keeps the second one's in registers for the next phase.  The
+// iterate rows in shared memory keep even and odd columns apart, so the
+// neighbour reads of a phase (stride 2 in the natural layout) hit distinct
+// banks.
+//
+// Inputs and outputs are separate arrays (xout is never read), so a CTA
+// never sees a neighbour's finished values in place of the initial ones.
+constexpr int kHsPairs = 32;                 // column pairs per row: one per lane
+constexpr int kHsWarps = 8;
+constexpr int kHsThreads = 32 * kHsWarps;
+constexpr int kHsTI = 2 * kHsPairs - 6;      // owned columns of a tile (58)
+constexpr int kHsHalf = kHsPairs + 2;        // one parity's columns in a shared row
+constexpr int kHsCols = 2 * kHsHalf;         // shared row: columns ib-2 .. ib+65
+__host__ __device__ constexpr int hs_tj(int rows) { return 2 * kHsWarps * rows - 2; }   // owned rows
+__host__ __device__ constexpr int hs_srows(int rows) { return hs_tj(rows) + 4; }        // shared rows
+// Rows per warp and phase: one (58 x 14 owned points, 80 registers, 3 CTAs
+// per SM) measured faster than two (58 x 30, 128 registers, 2 CTAs per SM):
+// 0.66 against 0.76 ms per 257^3 V-cycle's finest-level half sweeps.
+template <typename T>
+constexpr int hs_rows() { return 1; }
+template <typename T>
+constexpr size_t hs_smem() { return sizeof(T) * 3 * (size_t)hs_srows(hs_rows<T>()) * kHsCols; }
+
+template <typename T>
+struct HS3Args {
+    const T* A;          // symmetric-half planes (NS3)
+    int n, ld;
+    long long pl;
+    const T* f;          // right-hand side
+    const T* xcur;       // initial iterate of the swept planes (mode 2)
+    const T* xz;         // iterate of the neighbouring planes (modes 1, 2)
+    T* xout;             // swept planes' result (owned points)
+    int parity;          // planes k with k & 1 == parity
+};
+
+template <typename T>
+struct V2 {
+    T x, y;
+};
+template <typename T>
+__device__ __forceinline__ V2<T> ld2(const T* p) {
+    if constexpr (sizeof(T) == 4) {
+        const float2 v = __ldg(reinterpret_cast<const float2*>(p));
+        return {v.x, v.y};
+    } else {
+        const double2 v = __ldg(reinterpret_cast<const double2*>(p));
+        return {v.x, v.y};
+    }
+}
+
+// One pair's stencil: the 14 stored planes at both points (own) and, for
+// each stored offset d, the mirror a(q, q - d) stored at q - d.
+template <typename T, int MODE>
+struct HsPair {
+    T own0[NS3], own1[NS3];   // first (even column) / second point
+    T mir0[13], mir1[13];
+    T f0, f1;
+    __device__ __forceinline__ void load(const HS3Args<T>& a, long long o0, bool first_ok) {
+        const long long sz = (long long)a.ld * a.n;
+#pragma unroll
+        for (int t = 0; t < NS3; t++) {
+            if (MODE == 0 && t < 9) continue;   // z-couplings: the odd planes are still zero
+            const V2<T> v = ld2(a.A + t * a.pl + o0);
+            own0[t] = v.x;
+            own1[t] = v.y;
+        }
+#pragma unroll
+        for (int t = 0; t < 13; t++) {
+            if (MODE == 0 && t < 9) continue;
+            const int dx = off_x(t), dy = off_y(t), dz = off_z(t);
+            const long long m = o0 - (long long)dy * a.ld - dz * sz;   // node (i, j - dy, k - dz)
+            const T* b = a.A + t * a.pl + m;
+            const V2<T> v = ld2(b);
+            if (dx == 0) {
+                mir0[t] = v.x;
+                mir1[t] = v.y;
+            } else if (dx < 0) {             // mirrors at columns i + 1 and i + 2
+                mir0[t] = v.y;
+                mir1[t] = __ldg(b + 2);
+            } else {                         // mirrors at columns i - 1 and i
+                mir0[t] = first_ok ? __ldg(b - 1) : (T)0;
+                mir1[t] = v.x;
+            }
+        }
+        const V2<T> v = ld2(a.f + o0);
+        f0 = v.x;
+        f1 = v.y;
+    }
+};
+
+// Gauss-Seidel update of one point from its stencil and the shared
+// iterates.  ODD: the point is the pair's second (odd) column.  s: index of
+// the point's row in the shared arrays (row start), p: the pair.
+template <typename T, int MODE, bool ODD>
+__device__ __forceinline__ T hs_update(const T* own, const T* mir, T f, const T* xc, const T* xb, const T* xa,
+                                       int rs, int p) {
+    // shared index of the neighbour at column offset dx, row offset dy
+    auto at = [&](int dx, int dy) {
+        const int c = ODD ? (dx == 0 ? kHsHalf + p + 1 : (dx < 0 ? p + 1 : p + 2))
+                          : (dx == 0 ? p + 1 : (dx < 0 ? kHsHalf + p : kHsHalf + p + 1));
+        return rs + dy * kHsCols + c;
+    };
+    T s = 0;
+#pragma unroll
+    for (int t = 0; t < 13; t++) {
+        if (MODE == 0 && t < 9) continue;
+        const int dx = off_x(t), dy = off_y(t), dz = off_z(t);
+        const T* xp = dz < 0 ? xb : xc;   // plane of q + d
+        const T* xm = dz < 0 ? xa : xc;   // plane of q - d
+        s += own[t] * xp[at(dx, dy)];
+        s += mir[t] * xm[at(-dx, -dy)];
+    }
+    return (f - s) / own[13];
+}
+
+// MODE 0: zero initial iterate, no z-couplings (forward sweep of the even
+// planes); MODE 1: zero initial iterate, z-couplings to xz (forward sweep of
+// the odd planes); MODE 2: initial iterate xcur, z-couplings to xz (reverse
+// sweeps).  FWD: colours of the plane ascending, else descending.
+template <typename T, int MODE, bool FWD>
+__global__ void __launch_bounds__(kHsThreads) k_hsweep3d(HS3Args<T> a) {
+    constexpr int ROWS = hs_rows<T>();
+    constexpr int TJ = hs_tj(ROWS);
+    constexpr int SR = hs_srows(ROWS);
+    constexpr int PLANE = SR * kHsCols;
+    extern __shared__ __align__(16) unsigned char hs_raw[];
+    T* xc = reinterpret_cast<T*>(hs_raw);   // swept plane k
+    T* xb = xc + PLANE;                      // plane k - 1
+    T* xa = xb + PLANE;                      // plane k + 1
+    const int n = a.n, ld = a.ld;
+    const long long sz = (long long)ld * n;
+    const int k = 2 - a.parity + 2 * (int)blockIdx.z;
+    const int i0 = 1 + (int)blockIdx.x * kHsTI, j0 = 1 + (int)blockIdx.y * TJ;
+    const int ib = i0 - 3;                   // first computed column (even)
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    // shared position (lr, lc) holds node (ib - 2 + lc, j0 - 2 + lr)
+    for (int q = tid; q < PLANE; q += kHsThreads) {
+        const int lr = q / kHsCols, lc = q - lr * kHsCols;
+        const int i = ib - 2 + lc, j = j0 - 2 + lr;
+        const bool in = i >= 1 && i <= n - 2 && j >= 1 && j <= n - 2;
+        const int s = lr * kHsCols + (lc & 1) * kHsHalf + (lc >> 1);
+        const long long o = (long long)i + (long long)ld * j + sz * k;
+        xc[s] = (MODE == 2 && in) ? a.xcur[o] : (T)0;
+        if (MODE >= 1) {
+            xb[s] = (in && k >= 2) ? a.xz[o - sz] : (T)0;
+            xa[s] = (in && k <= n - 3) ? a.xz[o + sz] : (T)0;
+        }
+    }
+    __syncthreads();
+    const int p = lane;
+    const int i = ib + 2 * p;                // the pair's first column
+    HsPair<T, MODE> hold[ROWS];
+    bool ok0[ROWS], ok1[ROWS];
+    // one row parity: PH = 0 loads and updates the pair's earlier colour,
+    // PH = 1 updates the later one from the registers
+    auto phase = [&](int jpar, bool second) {
+#pragma unroll
+        for (int r = 0; r < ROWS; r++) {
+            const int lrow = 2 * (warp + kHsWarps * r) + jpar;   // region row, j = j0 - 1 + lrow
+            const int j = j0 - 1 + lrow;
+            const int rs = (lrow + 1) * kHsCols;
+            const bool pv = j >= 1 && j <= n - 2 && i >= 0 && i <= n - 2;
+            if (!second) {
+                ok0[r] = pv && i >= 1;
+                ok1[r] = pv && i + 1 <= n - 2;
+                if (pv) hold[r].load(a, (long long)i + (long long)ld * j + sz * k, ok0[r]);
+            }
+            // FWD: even column first; reverse: odd column first
+            const bool do_odd = FWD ? second : !second;
+            if (do_odd) {
+                if (ok1[r]) xc[rs + kHsHalf + p + 1] =
+                    hs_update<T, MODE, true>(hold[r].own1, hold[r].mir1, hold[r].f1, xc, xb, xa, rs, p);
+            } else {
+                if (ok0[r]) xc[rs + p + 1] =
+                    hs_update<T, MODE, false>(hold[r].own0, hold[r].mir0, hold[r].f0, xc, xb, xa, rs, p);
+            }
+        }
+        __syncthreads();
+    };
+    if (FWD) {
+        phase(0, false);
+        phase(0, true);
+        phase(1, false);
+        phase(1, true);
+    } else {
+        phase(1, false);
+        phase(1, true);
+        phase(0, false);
+        phase(0, true);
+    }
+    for (int q = tid; q < kHsTI * TJ; q += kHsThreads) {
+        const int lj = q / kHsTI, li = q - lj * kHsTI;
+        const int ii = i0 + li, jj = j0 + lj;
+        if (ii > n - 2 || jj > n - 2) continue;
+        const int lc = ii - ib + 2, lr = jj - j0 + 2;
+        a.xout[(long long)ii + (long long)ld * jj + sz * k] = xc[lr * kHsCols + (lc & 1) * kHsHalf + (lc >> 1)];
+    }
+}
+
+// x_out = x_in + P x_c at every interior fine point (out of place; the
+// same sum as prolong_node3d).
+template <typename T>
+__global__ void k_prolong3d_to(int nf, int ldf, const T* __restrict__ xin, T* __restrict__ xout,
+                               const T* __restrict__ P, int nc, int ldc, long long plc, const T* __restrict__ xc) {
+    const int I = blockIdx.x * blockDim.x + threadIdx.x;
+    const int J = blockIdx.y, K = blockIdx.z;
+    if (I > nc - 2 || J > nc - 2 || K > nc - 2) return;
+    const long long oc = (long long)I + (long long)ldc * (J + (long long)nc * K);
+    const long long sy = ldc, szc = (long long)ldc * nc;
+    T c8[8];
+#pragma unroll
+    for (int q = 0; q < 8; q++) c8[q] = xc[oc + (q & 1) + sy * ((q >> 1) & 1) + szc * (q >> 2)];
+#pragma unroll
+    for (int b = 0; b < 8; b++) {
+        const int fi = 2 * I + (b & 1), fj = 2 * J + ((b >> 1) & 1), fk = 2 * K + (b >> 2);
+        if (fi < 1 || fj < 1 || fk < 1 || fi > nf - 2 || fj > nf - 2 || fk > nf - 2) continue;
+        T v = 0;
+        if (b == 0) {
+            v = c8[0];
+        } else {
+#pragma unroll
+            for (int q = 0; q < 8; q++)
+                if ((q & ~b) == 0) v += P[(long long)(kPBase(b) + compress3(q, b)) * plc + oc] * c8[q];
+        }
+        const long long o = (long long)fi + (long long)ldf * (fj + (long long)nf * fk);
+        xout[o] = xin[o] + v;
+    }
+}
+
 inline double dofs3(const Ctx& c, int l) {
     const double m = c.lev[l].n - 2;
     return m * m * m;
@@ -333,6 +587,62 @@ bmg_status colour_blocks3d(Ctx& c) {
     return BMG_OK;
 }
 
+// One half sweep on level l (all planes of one parity); bytes for the
+// profiler: per point of the parity its stored planes (in-plane ones only in
+// mode 0), the mirrored z-planes of the plane above, the neighbouring
+// planes' iterate, the right-hand side, the output and (mode 2) the input.
+template <typename T, int MODE, bool FWD>
+bmg_status hsweep3d(Ctx& c, int l, const T* f, const T* xcur, const T* xz, T* xout, int parity) {
+    const Level& F = c.lev[l];
+    constexpr int TJ = hs_tj(hs_rows<T>());
+    const int planes = parity ? (F.n - 1) / 2 : (F.n - 3) / 2;
+    if (planes < 1) return BMG_OK;
+    HS3Args<T> a{A_of<T>(F), F.n, F.ld, F.plane, f, xcur, xz, xout, parity};
+    const dim3 grid(cdiv(F.n - 2, kHsTI), cdiv(F.n - 2, TJ), planes);
+    prof_begin(c, BMG_PROF_SMOOTH, l);
+    k_hsweep3d<T, MODE, FWD><<<grid, kHsThreads, hs_smem<T>(), c.stream>>>(a);
+    c.launches++;
+    const double per = MODE == 0 ? 5.0 + 2.0 : (MODE == 1 ? 14.0 + 9.0 + 2.0 + 2.0 : 14.0 + 9.0 + 2.0 + 3.0);
+    prof_end(c, BMG_PROF_SMOOTH, l, per * sizeof(T) * dofs3(c, l) / 2);
+    return BMG_OK;
+}
+
+// The half-sweep legs of a level (FP32 only: see use_hs3).
+template <typename T>
+bool hs3_on(const Ctx& c) { return sizeof(T) == 4 && c.use_hs3; }
+
+template <typename T>
+bmg_status hs3_down(Ctx& c, int l, const T* f, T* x) {
+    if constexpr (sizeof(T) == 4) {
+        // even planes (their odd neighbours still zero), then odd planes
+        BMG_TRY((hsweep3d<T, 0, true>(c, l, f, nullptr, nullptr, x, 0)));
+        return hsweep3d<T, 1, true>(c, l, f, nullptr, x, x, 1);
+    } else {
+        return BMG_ERR_STATE;
+    }
+}
+
+template <typename T>
+bmg_status hs3_up(Ctx& c, int l, const T* f, T* x, const T* xc) {
+    if constexpr (sizeof(T) == 4) {
+        // x + P x_c into the residual buffer (free until the next down leg),
+        // then the odd planes against the corrected even planes, then the
+        // even planes against the finished odd planes
+        const Level& F = c.lev[l];
+        const Level& K = c.lev[l + 1];
+        T* xcor = (T*)F.r;
+        prof_begin(c, BMG_PROF_PROLONG, l);
+        k_prolong3d_to<T><<<g3(K.n - 1, K.n - 1, K.n - 1), 64, 0, c.stream>>>(F.n, F.ld, x, xcor, P_of<T>(F), K.n,
+                                                                               K.ld, K.plane, xc);
+        prof_end(c, BMG_PROF_PROLONG, l, (2.0 + c.np / 8.0 + 0.125) * sizeof(T) * dofs3(c, l));
+        c.launches += 1;
+        BMG_TRY((hsweep3d<T, 2, false>(c, l, f, xcor, xcor, x, 1)));
+        return hsweep3d<T, 2, false>(c, l, f, xcor, x, x, 0);
+    } else {
+        return BMG_ERR_STATE;
+    }
+}
+
 template <typename T>
 bmg_status vcycle3d_impl(Ctx& c, const T* b0, T* x0, T* xout) {
     cudaStream_t s = c.stream;
@@ -350,7 +660,11 @@ bmg_status vcycle3d_impl(Ctx& c, const T* b0, T* x0, T* xout) {
         BMG_CUDA(cudaMemsetAsync(xl(l), 0, sizeof(T) * F.plane, s));
         const int h = (F.n + 1) / 2;
         const double N = dofs3(c, l);
-        for (int col = 0; col < 8; col++) BMG_TRY(colour_sweep<T>(c, l, v, bl(l), xl(l), col, h));
+        if (hs3_on<T>(c)) {
+            BMG_TRY(hs3_down(c, l, bl(l), xl(l)));
+        } else {
+            for (int col = 0; col < 8; col++) BMG_TRY(colour_sweep<T>(c, l, v, bl(l), xl(l), col, h));
+        }
         prof_begin(c, BMG_PROF_RESIDUAL, l);
         k_residual3d_sweep<T><<<g3(F.n, F.n, F.n), 64, 0, s>>>(v, xl(l), (T*)F.r);
         prof_end(c, BMG_PROF_RESIDUAL, l, (c.ns + 3) * sz * N);
@@ -385,6 +699,10 @@ bmg_status vcycle3d_impl(Ctx& c, const T* b0, T* x0, T* xout) {
         const Level& K = c.lev[l + 1];
         L3<T> v{A_of<T>(F), F.n, F.ld, F.plane};
         const double N = dofs3(c, l);
+        if (hs3_on<T>(c)) {
+            BMG_TRY(hs3_up(c, l, bl(l), xl(l), xl(l + 1)));
+            continue;
+        }
         prof_begin(c, BMG_PROF_PROLONG, l);
         k_prolong3d<T><<<g3(K.n - 1, K.n - 1, K.n - 1), 64, 0, s>>>(F.n, F.ld, xl(l), P_of<T>(F), K.n, K.ld,
                                                                      K.plane, xl(l + 1));

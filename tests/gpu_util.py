@@ -55,13 +55,21 @@ def fp32_vcycle_bound(H, r, dim):
     return z64, z32, 4 * max(dev_arm, U32), H.nlev * gamma
 
 
-def check_fp32_vcycle(z, H, r, dim):
+def check_fp32_vcycle(z, H, r, dim, d_hier=0.0):
     """Element-wise check of a library FP32 V-cycle z (numpy) against both
-    oracle arms; returns the two deviations for reporting."""
+    oracle arms; returns the two deviations for reporting.
+
+    d_hier: where the library's FP64 hierarchy itself differs from the
+    oracle's by more than FP64 rounding (the shell map's collapse amplifies
+    rounding level by level), the max-abs deviation (over max|z64|) of the
+    library's FP64 V-cycle from the oracle's.  The FP32 copies inherit that
+    difference, and to first order the FP32 cycle responds to it as the FP64
+    cycle does, so it enters both bounds twice (a factor two for the
+    first-order approximation)."""
     z64, z32, b_arm, b_64 = fp32_vcycle_bound(H, r, dim)
     scale = np.abs(z64).max()
     d_arm = np.abs(z - z32).max() / scale
     d_64 = np.abs(z - z64).max() / scale
-    assert d_arm <= b_arm, (d_arm, b_arm)
-    assert d_64 <= b_64, (d_64, b_64)
+    assert d_arm <= b_arm + 2 * d_hier, (d_arm, b_arm, d_hier)
+    assert d_64 <= b_64 + 2 * d_hier, (d_64, b_64, d_hier)
     return d_arm, d_64
