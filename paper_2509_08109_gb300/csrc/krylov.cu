@@ -601,26 +601,30 @@ bmg_status k_rz_beta32(Ctx& c, const float* z, const float* zo) {
 }
 
 // 3-D form of k_pspmv32_t: one CTA per tile of 32 x 8 (i, j) interior nodes
-// and a band of k-planes, marching up k.  The 13 stored planes and p of the
-// next k-plane, with a one-node halo in i and j, go from registers (loaded a
-// step ahead) into shared rings (3 stencil slots, 4 p slots, so one barrier
-// per plane suffices); every value is loaded once per tile.  The products
-// and their order are those of k_pspmv32_t<3> (offset t, then its mirror).
+// and a band of k-planes, marching up k; p of the next k-plane, with a
+// one-node halo in i and j, goes from registers (loaded a step ahead) into a
+// shared ring of 4 slots, so one barrier per plane suffices.
 constexpr int kP3I = 32, kP3J = 8;
 constexpr int kP3W = kP3I + 2, kP3H = kP3J + 2, kP3A = kP3W * kP3H;   // halo tile
 constexpr int kP3Per = (kP3A + kThreads - 1) / kThreads;              // halo positions per thread
 
-inline size_t pspmv3d_smem() { return sizeof(float) * (3 * 13 * kP3A + 4 * kP3A); }
-
-__global__ void __launch_bounds__(kThreads) k_pspmv3d_tiled(int n, int ld, long long pl, int H, int tiles_i,
-                                                            int tiles_j, const float* __restrict__ A,
-                                                            const float* __restrict__ rs,
-                                                            const float* __restrict__ z,
-                                                            const float* __restrict__ pold, float* __restrict__ p,
-                                                            float* __restrict__ q, double* partials, KState* st) {
-    extern __shared__ float sm3[];
-    float* sA = sm3;                  // [3][13][kP3A]
-    float* sP = sm3 + 3 * 13 * kP3A;  // [4][kP3A]
+// The stencil is read straight from global memory: each thread loads its
+// node's 13 stored planes and the 13 mirrors a(-d) (stored at the node - d)
+// into registers before the step's barrier, so the loads overlap the wait;
+// the mirrors of the CTA's interior are its own threads' loads of a
+// neighbouring row or of the next plane, served by L1 and L2.  Only p lives
+// in shared memory, so the CTA's footprint is a few KB and occupancy is set
+// by registers (64 per thread, 4 CTAs per SM).  A version that staged the 13
+// planes in shared rings as well (58 KB per CTA, 3 CTAs per SM) took 349
+// instead of 253 us per 257^3 product.  Same products in the same order as
+// k_pspmv32_t<3>.
+__global__ void __launch_bounds__(kThreads) k_pspmv3d_direct(int n, int ld, long long pl, int H, int tiles_i,
+                                                             int tiles_j, const float* __restrict__ A,
+                                                             const float* __restrict__ rs,
+                                                             const float* __restrict__ z,
+                                                             const float* __restrict__ pold, float* __restrict__ p,
+                                                             float* __restrict__ q, double* partials, KState* st) {
+    __shared__ float sP[4][kP3A];
     const float beta = (float)st->beta;
     const int tid = threadIdx.x;
     const int tile = blockIdx.x;
@@ -628,9 +632,7 @@ __global__ void __launch_bounds__(kThreads) k_pspmv3d_tiled(int n, int ld, long 
     const int i0 = 1 + ti * kP3I, j0 = 1 + tj * kP3J, k0 = 1 + tk * H;
     const int k1 = min(k0 + H, n - 1);
     const long long sz = (long long)ld * n;
-    // the thread's halo positions: (hi, hj) -> node (i0 - 1 + hi, j0 - 1 + hj)
-    // raw loads; p = z + beta p_old is formed in put(), a step later
-    float ra[kP3Per][13], rz[kP3Per], rpo[kP3Per];
+    float rz[kP3Per], rpo[kP3Per];
     auto load = [&](int k) {
 #pragma unroll
         for (int u = 0; u < kP3Per; u++) {
@@ -639,28 +641,22 @@ __global__ void __launch_bounds__(kThreads) k_pspmv3d_tiled(int n, int ld, long 
             const int i = i0 - 1 + hi, j = j0 - 1 + hj;
             const bool in = h < kP3A && i <= n - 1 && j <= n - 1 && k >= 0 && k <= n - 1;
             const long long o = in ? (long long)i + (long long)ld * j + sz * k : 0;
-#pragma unroll
-            for (int t = 0; t < 13; t++) ra[u][t] = in ? A[t * pl + o] : 0.f;
             rz[u] = in ? z[o] : 0.f;
             rpo[u] = in ? pold[o] : 0.f;
         }
     };
     auto put = [&](int k) {
-        float* a = sA + (k % 3) * 13 * kP3A;
-        float* pp = sP + (k & 3) * kP3A;
+        float* pp = sP[k & 3];
 #pragma unroll
         for (int u = 0; u < kP3Per; u++) {
             const int h = tid + u * kThreads;
-            if (h >= kP3A) continue;
-#pragma unroll
-            for (int t = 0; t < 13; t++) a[t * kP3A + h] = ra[u][t];
-            pp[h] = rz[u] + beta * rpo[u];
+            if (h < kP3A) pp[h] = rz[u] + beta * rpo[u];
         }
     };
     const int ti_ = tid % kP3I, tj_ = tid / kP3I;
     const int i = i0 + ti_, j = j0 + tj_;
     const bool act = i <= n - 2 && j <= n - 2;
-    const int hc = (tj_ + 1) * kP3W + (ti_ + 1);    // the thread's node in the halo tile
+    const int hc = (tj_ + 1) * kP3W + (ti_ + 1);
     load(k0 - 1);
     put(k0 - 1);
     load(k0);
@@ -670,26 +666,32 @@ __global__ void __launch_bounds__(kThreads) k_pspmv3d_tiled(int n, int ld, long 
     for (int k = k0; k < k1; k++) {
         put(k + 1);
         load(k + 2);
+        const long long o = (long long)i + (long long)ld * j + sz * k;
+        float a0[13], am[13], rsv = 0.f;
+        if (act) {
+#pragma unroll
+            for (int t = 0; t < 13; t++) {
+                const long long d = (t % 3 - 1) + (long long)ld * ((t / 3) % 3 - 1) + sz * (t / 9 - 1);
+                a0[t] = __ldg(A + t * pl + o);
+                am[t] = __ldg(A + t * pl + o - d);
+            }
+            rsv = __ldg(rs + o);
+        }
         __syncthreads();
         if (act) {
-            const float* a0 = sA + (k % 3) * 13 * kP3A;          // plane k
-            const float* a1 = sA + ((k + 1) % 3) * 13 * kP3A;    // plane k+1
-            const float* pm = sP + ((k + 3) & 3) * kP3A;         // p at k-1
-            const float* p0 = sP + (k & 3) * kP3A;               // p at k
-            const float* pp = sP + ((k + 1) & 3) * kP3A;         // p at k+1
+            const float* pm = sP[(k + 3) & 3];   // p at k-1
+            const float* p0 = sP[k & 3];         // p at k
+            const float* pp = sP[(k + 1) & 3];   // p at k+1
             const float pv = p0[hc];
-            const long long o = (long long)i + (long long)ld * j + sz * k;
-            float s = rs[o] * pv;
+            float s = rsv * pv;
 #pragma unroll
             for (int t = 0; t < 13; t++) {
                 const int dx = t % 3 - 1, dy = (t / 3) % 3 - 1, dz = t / 9 - 1;
                 const int dh = dx + dy * kP3W;
-                // a(d) at the node times p(node + d); then a(-d), stored at node - d
                 const float* pn = dz < 0 ? pm : p0;
                 const float* pr = dz < 0 ? pp : p0;
-                const float* ar = dz < 0 ? a1 : a0;
-                s += a0[t * kP3A + hc] * (pn[hc + dh] - pv);
-                s += ar[t * kP3A + hc - dh] * (pr[hc - dh] - pv);
+                s += a0[t] * (pn[hc + dh] - pv);
+                s += am[t] * (pr[hc - dh] - pv);
             }
             p[o] = pv;
             q[o] = s;
@@ -715,10 +717,8 @@ bmg_status pspmv_prepare(Ctx& c) {
     if (c.dim == 3) {
         // bands of k-planes: minimise waves x (planes + 2) with at most kMaxBlocks tiles
         int sms = 0, occ = 0;
-        const size_t smem = pspmv3d_smem();
         BMG_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, c.device));
-        BMG_CUDA(cudaFuncSetAttribute(k_pspmv3d_tiled, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-        BMG_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_pspmv3d_tiled, kThreads, smem));
+        BMG_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_pspmv3d_direct, kThreads, 0));
         if (occ < 1) return BMG_ERR_DEVICE;
         const int m = c.lev[0].n - 2;
         const int ti = cdiv(m, kP3I), tj = cdiv(m, kP3J);
@@ -769,9 +769,9 @@ bmg_status k_pspmv32(Ctx& c, const float* z, int parity) {
         c.launches++;
     } else if (c.dim == 3 && c.spmv_h > 0) {
         const int tj = cdiv(L.n - 2, kP3J);
-        k_pspmv3d_tiled<<<c.spmv_tiles, kThreads, pspmv3d_smem(), c.stream>>>(
-            L.n, L.ld, L.plane, c.spmv_h, c.spmv_tiles_x, tj, L.A32, c.rs32, z, c.p32s[parity ^ 1],
-            c.p32s[parity], c.q32, c.partials, c.st);
+        k_pspmv3d_direct<<<c.spmv_tiles, kThreads, 0, c.stream>>>(L.n, L.ld, L.plane, c.spmv_h, c.spmv_tiles_x, tj,
+                                                                 L.A32, c.rs32, z, c.p32s[parity ^ 1],
+                                                                 c.p32s[parity], c.q32, c.partials, c.st);
         c.launches++;
     } else {
         DISPATCH_DIM(c, k_pspmv32_t, L.A32, c.rs32, L.plane, z, c.p32s[parity ^ 1], c.p32s[parity], c.q32,
