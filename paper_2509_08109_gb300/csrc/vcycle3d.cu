@@ -115,10 +115,12 @@ __global__ void k_residual3d_sweep(L3<T> L, const T* __restrict__ x, T* __restri
 // direction where d = -1), in the plane of f's parity mask m and of the
 // corner K - owner.  All of that is fixed by d, so the loop unrolls to plain
 // loads.
+// ldv: row length of the coarse vector bc (ldc, that of the weight planes,
+// unless the coarse level lives in another layout).
 template <typename T>
 __device__ __forceinline__ void restrict_node3d(int nf, int ldf, const T* __restrict__ r, const T* __restrict__ P,
-                                                int nc, int ldc, long long plc, T* __restrict__ bc, int I, int J,
-                                                int K) {
+                                                int nc, int ldc, long long plc, T* __restrict__ bc, int ldv, int I,
+                                                int J, int K) {
     const long long oc = (long long)I + (long long)ldc * (J + (long long)nc * K);
     const long long of = 2LL * I + (long long)ldf * (2 * J + (long long)nf * 2 * K);
     T s = 0;
@@ -134,7 +136,7 @@ __device__ __forceinline__ void restrict_node3d(int nf, int ldf, const T* __rest
         }
         s += w * r[of + dx + (long long)ldf * (dy + (long long)nf * dz)];
     }
-    bc[oc] = s;
+    bc[(long long)I + (long long)ldv * (J + (long long)nc * K)] = s;
 }
 
 template <typename T>
@@ -143,7 +145,7 @@ __global__ void k_restrict3d(int nf, int ldf, const T* __restrict__ r, const T* 
     const int I = blockIdx.x * blockDim.x + threadIdx.x;
     const int J = blockIdx.y, K = blockIdx.z;
     if (I < 1 || J < 1 || K < 1 || I > nc - 2 || J > nc - 2 || K > nc - 2) return;
-    restrict_node3d<T>(nf, ldf, r, P, nc, ldc, plc, bc, I, J, K);
+    restrict_node3d<T>(nf, ldf, r, P, nc, ldc, plc, bc, ldc, I, J, K);
 }
 
 // x_f += sum over s subset of m of P(f, (I,J,K) + s) x_c((I,J,K) + s) for the
@@ -151,14 +153,17 @@ __global__ void k_restrict3d(int nf, int ldf, const T* __restrict__ r, const T* 
 // (I,J,K) owns: one thread per coarse node, the 26 weights of its cell read
 // once and contiguously across the warp.  Summation over s ascending, as the
 // weights' own numbering.
+// ldv: row length of the coarse vector xc (as in restrict_node3d).
 template <typename T>
 __device__ __forceinline__ void prolong_node3d(int nf, int ldf, T* __restrict__ x, const T* __restrict__ P, int nc,
-                                               int ldc, long long plc, const T* __restrict__ xc, int I, int J, int K) {
+                                               int ldc, long long plc, const T* __restrict__ xc, int ldv, int I,
+                                               int J, int K) {
     const long long oc = (long long)I + (long long)ldc * (J + (long long)nc * K);
-    const long long sy = ldc, sz = (long long)ldc * nc;
+    const long long ov = (long long)I + (long long)ldv * (J + (long long)nc * K);
+    const long long sy = ldv, sz = (long long)ldv * nc;
     T c8[8];
 #pragma unroll
-    for (int q = 0; q < 8; q++) c8[q] = xc[oc + (q & 1) + sy * ((q >> 1) & 1) + sz * (q >> 2)];
+    for (int q = 0; q < 8; q++) c8[q] = xc[ov + (q & 1) + sy * ((q >> 1) & 1) + sz * (q >> 2)];
 #pragma unroll
     for (int b = 0; b < 8; b++) {
         const int fi = 2 * I + (b & 1), fj = 2 * J + ((b >> 1) & 1), fk = 2 * K + (b >> 2);
@@ -181,7 +186,7 @@ __global__ void k_prolong3d(int nf, int ldf, T* __restrict__ x, const T* __restr
     const int I = blockIdx.x * blockDim.x + threadIdx.x;
     const int J = blockIdx.y, K = blockIdx.z;
     if (I > nc - 2 || J > nc - 2 || K > nc - 2) return;
-    prolong_node3d<T>(nf, ldf, x, P, nc, ldc, plc, xc, I, J, K);
+    prolong_node3d<T>(nf, ldf, x, P, nc, ldc, plc, xc, ldc, I, J, K);
 }
 
 template <typename T>
@@ -193,12 +198,24 @@ __global__ void k_coarsest3d(L3<T> L, const double* __restrict__ A64, const T* _
 inline dim3 g3(int ni, int nj, int nk) { return dim3(cdiv(ni, 64), nj, nk); }
 
 // ---------------------------------------------------------------- tail
-// The coarse end of the 3-D V-cycle (levels with n <= kTail3MaxN down to the
+// The coarse end of the 3-D V-cycle (levels with n <= tail3_max_n down to the
 // 3^3 grid and back) in one launch of one CTA: the same per-node steps as the
-// kernels above, each phase a block-strided loop followed by a block barrier,
-// on the levels' arrays in global memory (a few hundred KB, L2-resident).
+// kernels above, each phase a block-strided loop followed by a block barrier.
+// Each phase waits on its loads, so the tail's time is about its number of
+// phases times the latency of the memory it reads.  In FP32 the tail starts
+// at 9^3 and all its levels (9^3, 5^3, 3^3: about 76 KB in a compact layout,
+// n in place of the padded row length) live in shared memory for the launch:
+// operators and weights copied from their arrays at the start, the first
+// level's right-hand side copied in and its iterate copied out; the 17^3
+// level runs the half-sweep kernels instead.  In FP64 the tail starts at
+// 17^3 (its operator alone is 550 KB) and works on the levels' arrays in
+// global memory (L2-resident).  Measured on the 257^3 shell (FP32
+// refinement solve): 1.052 s with a 17^3 tail in global memory, 1.045 s with
+// its lower levels staged.
 constexpr int kTail3Threads = 1024;
-constexpr int kTail3MaxN = 17;   // first tail level: n <= 17
+template <typename T>
+constexpr int tail3_max_n() { return sizeof(T) == 4 ? 9 : 17; }   // first tail level: n <= this
+constexpr int kTail3Lev = 4;     // levels of a tail: 17, 9, 5, 3 at most
 
 template <typename T>
 struct Tail3Level {
@@ -214,14 +231,88 @@ struct Tail3Level {
 template <typename T>
 struct Tail3Args {
     int nlev;
-    Tail3Level<T> lv[kMaxLevels];
+    Tail3Level<T> lv[kTail3Lev];
     const double* a64c;    // FP64 centre entry of the coarsest operator at (1,1,1)
 };
 
+// Elements of shared memory for the staged levels (all of them, FP32 only).
+template <typename T>
+__host__ __device__ constexpr bool tail3_stages() { return sizeof(T) == 4; }
+inline size_t tail3_smem_elems(const int* ns, int nlev) {
+    size_t e = 0;
+    for (int q = 0; q < nlev; q++) {
+        const size_t n3 = (size_t)ns[q] * ns[q] * ns[q];
+        e += (NS3 + 3) * n3;
+        if (q + 1 < nlev) e += (size_t)NP3 * ns[q + 1] * ns[q + 1] * ns[q + 1];
+    }
+    return e;
+}
+
 template <typename T>
 __global__ void __launch_bounds__(kTail3Threads) k_vtail3d(Tail3Args<T> a) {
+    extern __shared__ __align__(16) unsigned char t3_raw[];
+    __shared__ Tail3Level<T> lv[kTail3Lev];
     const int tid = threadIdx.x, nth = blockDim.x;
     const int L = a.nlev;
+    if (tid == 0) {
+        T* sp = reinterpret_cast<T*>(t3_raw);
+        for (int q = 0; q < L; q++) {
+            lv[q] = a.lv[q];
+            if (tail3_stages<T>()) {
+                const int n = a.lv[q].A.n;
+                const long long n3 = (long long)n * n * n;
+                lv[q].A = L3<T>{sp, n, n, n3};
+                sp += NS3 * n3;
+                if (q + 1 < L) {
+                    const int nc = a.lv[q + 1].A.n;
+                    lv[q].P = sp;
+                    lv[q].ldc = nc;
+                    lv[q].plc = (long long)nc * nc * nc;
+                    sp += NP3 * lv[q].plc;
+                }
+                lv[q].b = sp;
+                lv[q].x = sp + n3;
+                lv[q].r = sp + 2 * n3;
+                sp += 3 * n3;
+            }
+        }
+    }
+    __syncthreads();
+    if (tail3_stages<T>()) {
+        // operators (NS3 planes) and weights (NP3 planes on the next grid),
+        // from the padded layout into the compact one; the first level's
+        // right-hand side
+        {
+            const Tail3Level<T>& g = a.lv[0];
+            const int n = g.A.n, n3 = n * n * n;
+            T* db = const_cast<T*>(lv[0].b);
+            for (int u = tid; u < n3; u += nth) {
+                const int i = u % n, j = (u / n) % n, k = u / (n * n);
+                db[u] = g.b[g.A.idx(i, j, k)];
+            }
+        }
+        for (int q = 0; q < L; q++) {
+            const Tail3Level<T>& g = a.lv[q];
+            const int n = g.A.n;
+            const int n3 = n * n * n;
+            T* dA = const_cast<T*>(lv[q].A.A);
+            for (int e = tid; e < NS3 * n3; e += nth) {
+                const int t = e / n3, u = e - t * n3;
+                const int i = u % n, j = (u / n) % n, k = u / (n * n);
+                dA[e] = g.A.A[t * g.A.pl + g.A.idx(i, j, k)];
+            }
+            if (q + 1 < L) {
+                const int nc = a.lv[q + 1].A.n, nc3 = nc * nc * nc;
+                T* dP = const_cast<T*>(lv[q].P);
+                for (int e = tid; e < NP3 * nc3; e += nth) {
+                    const int t = e / nc3, u = e - t * nc3;
+                    const int i = u % nc, j = (u / nc) % nc, k = u / (nc * nc);
+                    dP[e] = g.P[t * g.plc + (long long)i + (long long)g.ldc * (j + (long long)nc * k)];
+                }
+            }
+        }
+        __syncthreads();
+    }
     auto colour = [&](const Tail3Level<T>& v, int col) {
         const int n = v.A.n;
         const int pi = col & 1, pj = (col >> 1) & 1, pk = col >> 2;
@@ -233,8 +324,8 @@ __global__ void __launch_bounds__(kTail3Threads) k_vtail3d(Tail3Args<T> a) {
         }
     };
     for (int l = 0; l + 1 < L; l++) {
-        const Tail3Level<T>& v = a.lv[l];
-        const Tail3Level<T>& w = a.lv[l + 1];
+        const Tail3Level<T>& v = lv[l];
+        const Tail3Level<T>& w = lv[l + 1];
         const int n = v.A.n, m = n - 2;
         for (long long q = tid; q < (long long)v.A.ld * n * n; q += nth) v.x[q] = (T)0;
         __syncthreads();
@@ -251,12 +342,12 @@ __global__ void __launch_bounds__(kTail3Threads) k_vtail3d(Tail3Args<T> a) {
         const int nc = w.A.n, mc = nc - 2;
         for (int q = tid; q < mc * mc * mc; q += nth) {
             const int I = 1 + q % mc, J = 1 + (q / mc) % mc, K = 1 + q / (mc * mc);
-            restrict_node3d<T>(n, v.A.ld, v.r, v.P, nc, v.ldc, v.plc, (T*)w.b, I, J, K);
+            restrict_node3d<T>(n, v.A.ld, v.r, v.P, nc, v.ldc, v.plc, (T*)w.b, w.A.ld, I, J, K);
         }
         __syncthreads();
     }
     {   // coarsest: one unknown, exact in FP64; the rest of its iterate is zero
-        const Tail3Level<T>& v = a.lv[L - 1];
+        const Tail3Level<T>& v = lv[L - 1];
         const int n = v.A.n;
         for (long long q = tid; q < (long long)v.A.ld * n * n; q += nth) v.x[q] = (T)0;
         __syncthreads();
@@ -267,12 +358,12 @@ __global__ void __launch_bounds__(kTail3Threads) k_vtail3d(Tail3Args<T> a) {
         __syncthreads();
     }
     for (int l = L - 2; l >= 0; l--) {
-        const Tail3Level<T>& v = a.lv[l];
-        const Tail3Level<T>& w = a.lv[l + 1];
+        const Tail3Level<T>& v = lv[l];
+        const Tail3Level<T>& w = lv[l + 1];
         const int n = v.A.n, nc = w.A.n, mc = nc - 1;
         for (int q = tid; q < mc * mc * mc; q += nth) {
             const int I = q % mc, J = (q / mc) % mc, K = q / (mc * mc);
-            prolong_node3d<T>(n, v.A.ld, v.x, v.P, nc, v.ldc, v.plc, w.x, I, J, K);
+            prolong_node3d<T>(n, v.A.ld, v.x, v.P, nc, v.ldc, v.plc, w.x, w.A.ld, I, J, K);
         }
         __syncthreads();
         for (int col = 7; col >= 0; col--) {
@@ -280,9 +371,15 @@ __global__ void __launch_bounds__(kTail3Threads) k_vtail3d(Tail3Args<T> a) {
             __syncthreads();
         }
     }
+    if (tail3_stages<T>()) {   // the first level's iterate back to its array
+        const Tail3Level<T>& g = a.lv[0];
+        const int n = g.A.n, n3 = n * n * n;
+        for (int u = tid; u < n3; u += nth) {
+            const int i = u % n, j = (u / n) % n, k = u / (n * n);
+            g.x[g.A.idx(i, j, k)] = lv[0].x[u];
+        }
+    }
 }
-
-
 
 // ---------------------------------------------------------------- half sweeps
 // The 8-colour order visits all colours of the even k-planes (0..3) before
@@ -650,9 +747,9 @@ bmg_status vcycle3d_impl(Ctx& c, const T* b0, T* x0, T* xout) {
     const double sz = sizeof(T);
     auto bl = [&](int l) { return l == 0 ? b0 : (const T*)c.lev[l].b; };
     auto xl = [&](int l) { return l == 0 ? x0 : (T*)c.lev[l].x; };
-    // levels t .. L-1 (n <= kTail3MaxN) run in the single-CTA tail
+    // levels t .. L-1 (n <= tail3_max_n) run in the single-CTA tail
     int t = L - 1;
-    while (t > 0 && c.lev[t - 1].n <= kTail3MaxN) t--;
+    while (t > 0 && c.lev[t - 1].n <= tail3_max_n<T>()) t--;
     for (int l = 0; l < t; l++) {
         const Level& F = c.lev[l];
         const Level& K = c.lev[l + 1];
@@ -677,6 +774,7 @@ bmg_status vcycle3d_impl(Ctx& c, const T* b0, T* x0, T* xout) {
     {
         Tail3Args<T> a{};
         a.nlev = L - t;
+        if (a.nlev > kTail3Lev) return BMG_ERR_STATE;   // n <= 17 has at most kTail3Lev levels
         for (int q = 0; q < a.nlev; q++) {
             const int l = t + q;
             const Level& F = c.lev[l];
@@ -691,7 +789,14 @@ bmg_status vcycle3d_impl(Ctx& c, const T* b0, T* x0, T* xout) {
         }
         const Level& C = c.lev[L - 1];
         a.a64c = C.A64 + 13 * C.plane + (long long)C.ld * (1 + (long long)C.n) + 1;
-        k_vtail3d<T><<<1, kTail3Threads, 0, s>>>(a);
+        size_t smem = 0;
+        if (tail3_stages<T>()) {
+            int ns[kTail3Lev];
+            for (int q = 0; q < a.nlev; q++) ns[q] = c.lev[t + q].n;
+            smem = sizeof(T) * tail3_smem_elems(ns, a.nlev);
+            BMG_CUDA(cudaFuncSetAttribute(k_vtail3d<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        }
+        k_vtail3d<T><<<1, kTail3Threads, smem, s>>>(a);
         c.launches++;
     }
     for (int l = t - 1; l >= 0; l--) {

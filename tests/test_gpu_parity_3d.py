@@ -146,11 +146,13 @@ def test_adjoint_3d_matches_oracle():
 
 
 # ------------------------------------------------------------------ half-sweep 3-D V-cycle
-# FP32 levels above 17^3 smooth with one launch per colour parity of k (the
+# FP32 levels from 17^3 up smooth with one launch per colour parity of k (the
 # half-sweep kernels: 58 x 14 owned points per CTA, with a 3-column, 1-row
 # halo).  At 65^3 the 63 interior columns make a full and a ragged tile, the
 # 63 rows five tiles with a ragged fifth; at 129^3, three column tiles and
-# ten row tiles.  FP64 levels keep the per-colour kernels.
+# ten row tiles.  FP64 levels keep the per-colour kernels.  The FP32 coarse
+# end (9^3 and below) runs in one CTA from shared memory, so the V-cycle tests
+# at 3^3..9^3 exercise it whole and those at 17^3 and up behind half sweeps.
 @pytest.mark.parametrize("n", [33, 65])
 def test_halfsweep_vcycle_3d_matches_oracle_well_conditioned(n):
     """Identity map, log-normal kappa: the FP64 V-cycle to 1e-12 of the
