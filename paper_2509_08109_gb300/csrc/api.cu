@@ -1,6 +1,7 @@
 // api.cu -- the C ABI (include/bmg.h): context, workspace carving, the
 // setup/solve sequence of Sec. 2.2 ("Setup phase", "Solution phase") with a
 // preconditioned-CG outer loop, host/device staging, diagnostics.
+#include <algorithm>
 #include <math.h>
 #include <string.h>
 
@@ -238,7 +239,12 @@ namespace {
 // on A d = r for m iterations whose updates go straight into the FP64 iterate
 // x; m is chosen from the contraction seen
 // so far so that one inner solve aims at the remaining reduction (bounded
-// below by what FP32 can deliver).  maxit caps the total inner iterations.
+// below by what FP32 can deliver).  A run whose r.z is still more than 100
+// times above its goal (want^2 times its first r.z) after the predicted m
+// goes on in steps of max(8, m/4) instead of restarting: the first run's
+// prediction has no contraction to go by (on the 257^3 shell the restarts
+// after it cost 604 inner iterations against 532).  maxit caps the total
+// inner iterations.
 bmg_status pcg_ir(Ctx& c, double tol, int maxit, bmg_info* info) {
     KState h;
     BMG_TRY(reset_state(c));
@@ -264,8 +270,23 @@ bmg_status pcg_ir(Ctx& c, double tol, int maxit, bmg_info* info) {
             if (m < 2) m = 2;
             if (m > kMaxInner) m = kMaxInner;
             if (m > maxit - it) m = maxit - it;
-            for (int k = 0; k < m; k++) BMG_TRY(run_iteration(c, (it + k) & 1));
-            it += m;
+            // the predicted run; while r.z stays far above the run's goal
+            // (more than 100x want^2 times its first value) the run goes on
+            BMG_TRY(run_iteration(c, it & 1));
+            it++;
+            BMG_TRY(read_state(c, h));
+            const double rz0 = h.rz;
+            int done = 1, mm = m - 1;
+            for (;;) {
+                for (int k = 0; k < mm; k++) BMG_TRY(run_iteration(c, (it + k) & 1));
+                it += mm;
+                done += mm;
+                if (done >= kMaxInner || it >= maxit) break;
+                BMG_TRY(read_state(c, h));
+                if (h.err || !(h.rz > 100.0 * want * want * rz0)) break;
+                mm = std::min(std::max(8, m / 4), std::min(kMaxInner - done, maxit - it));
+            }
+            m = done;
             BMG_TRY(k_residual_to32(c));
             BMG_TRY(read_state(c, h));
             refinements++;
