@@ -239,12 +239,12 @@ namespace {
 // on A d = r for m iterations whose updates go straight into the FP64 iterate
 // x; m is chosen from the contraction seen
 // so far so that one inner solve aims at the remaining reduction (bounded
-// below by what FP32 can deliver).  A run whose r.z is still more than 100
-// times above its goal (want^2 times its first r.z) after the predicted m
-// goes on in steps of max(8, m/4) instead of restarting: the first run's
-// prediction has no contraction to go by (on the 257^3 shell the restarts
-// after it cost 604 inner iterations against 532).  maxit caps the total
-// inner iterations.
+// below by what FP32 can deliver).  The first run, whose prediction has no
+// contraction to go by, goes on in steps of max(8, m/4) instead of
+// restarting while its r.z is still more than 100 times above its goal
+// (want^2 times its first r.z): on the 257^3 shell the solve took 520 inner
+// iterations instead of 604 (532 when every run could go on).  maxit caps
+// the total inner iterations.
 bmg_status pcg_ir(Ctx& c, double tol, int maxit, bmg_info* info) {
     KState h;
     BMG_TRY(reset_state(c));
@@ -270,20 +270,21 @@ bmg_status pcg_ir(Ctx& c, double tol, int maxit, bmg_info* info) {
             if (m < 2) m = 2;
             if (m > kMaxInner) m = kMaxInner;
             if (m > maxit - it) m = maxit - it;
-            // the predicted run; while r.z stays far above the run's goal
-            // (more than 100x want^2 times its first value) the run goes on
+            // the predicted run.  The first run has no contraction to go by:
+            // while its r.z stays far above the run's goal (more than 100x
+            // want^2 times its first value, kept on the device in rzn) it
+            // goes on instead of restarting
             BMG_TRY(run_iteration(c, it & 1));
             it++;
-            BMG_TRY(read_state(c, h));
-            const double rz0 = h.rz;
+            BMG_CUDA(cudaMemcpyAsync(&c.st->rzn, &c.st->rz, sizeof(double), cudaMemcpyDeviceToDevice, c.stream));
             int done = 1, mm = m - 1;
             for (;;) {
                 for (int k = 0; k < mm; k++) BMG_TRY(run_iteration(c, (it + k) & 1));
                 it += mm;
                 done += mm;
-                if (done >= kMaxInner || it >= maxit) break;
+                if (done >= kMaxInner || it >= maxit || refinements > 0) break;
                 BMG_TRY(read_state(c, h));
-                if (h.err || !(h.rz > 100.0 * want * want * rz0)) break;
+                if (h.err || !(h.rz > 100.0 * want * want * h.rzn)) break;
                 mm = std::min(std::max(8, m / 4), std::min(kMaxInner - done, maxit - it));
             }
             m = done;
