@@ -55,7 +55,14 @@ def test_hierarchy_3d_matches_oracle(n, kind):
     """Shell map (polar degeneracy, kappa contrast 1000): the collapse
     amplifies rounding level by level, so the bound per level is the
     oracle's own response to a 2e-16 relative perturbation of its input
-    (times 20), and never below 1e-12."""
+    (times 20), and never below 1e-12.  The factor: the library rounds
+    differently from the oracle in every operation of the collapse and of
+    the Galerkin product, not only once per input entry; a coarse entry
+    collects up to 27 x 8 weighted products per level, and independent
+    relative errors of one unit roundoff in m operations move the result
+    by about sqrt(m) times the response to one such error at the input
+    (sqrt(216) ~ 15), so 20 covers one level's worth with margin.  A
+    well-conditioned map is held to 1e-12 without scaling (the test above)."""
     p = _problem(n, kind)
     s = solver_for(p)
     A = oracle.assemble(p.coords, p.kappa)
