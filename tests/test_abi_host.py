@@ -152,3 +152,29 @@ def test_max_rhs_reserves_workspace_only_where_eligible(lib):
         opts = binding._Opts(2, 129, 1, 2, 0, bad)
         h = ctypes.c_void_p()
         assert lib.bmg_create(ctypes.byref(opts), ctypes.byref(h)) == 1
+
+
+def _ws_bytes(lib, dim, n, prec, outer, flags):
+    opts = binding._Opts(dim, n, binding.PREC[prec], binding.OUTER[outer], flags, 1)
+    h = ctypes.c_void_p()
+    assert lib.bmg_create(ctypes.byref(opts), ctypes.byref(h)) == 0
+    nb = ctypes.c_size_t()
+    assert lib.bmg_workspace_bytes(h, ctypes.byref(nb)) == 0
+    sizes = [lib.bmg_level_n(h, l) for l in range(lib.bmg_levels(h))]
+    lib.bmg_destroy(h)
+    return nb.value, sizes
+
+
+@pytest.mark.parametrize("n", [17, 33, 65, 257])
+def test_colour_blocked_rows_only_for_the_per_colour_3d_path(lib, n):
+    """The FP32 3-D half sweeps read the symmetric planes; the full 27-entry
+    rows grouped by colour (27 (n_l - 2)^3 floats per level but the coarsest,
+    each block 256-byte aligned in the workspace) exist only for the
+    per-colour smoother that BMG_FLAG_UNFUSED selects.  FP64 and 2-D
+    workspaces do not depend on the flag."""
+    fused, sizes = _ws_bytes(lib, 3, n, "fp32", "refine", 0)
+    unfused, _ = _ws_bytes(lib, 3, n, "fp32", "refine", 1)
+    blocks = sum(-(-27 * (m - 2) ** 3 * 4 // 256) * 256 for m in sizes[:-1])
+    assert unfused - fused == blocks
+    assert _ws_bytes(lib, 3, n, "fp64", "cg", 0)[0] == _ws_bytes(lib, 3, n, "fp64", "cg", 1)[0]
+    assert _ws_bytes(lib, 2, 4 * n - 3, "fp32", "refine", 0)[0] == _ws_bytes(lib, 2, 4 * n - 3, "fp32", "refine", 1)[0]
